@@ -1,0 +1,131 @@
+"""Pins for the oracle's objective, gradient, majorant and 2x2 pseudo-inverse (CPU only)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_02328_gb300 import synth
+from tests.golden_io import load_cases
+
+
+def _tiny(seed=0, **kw):
+    p = synth.tiny_problem(seed=seed, **kw)
+    return p, oracle.OracleProblem.from_synth(p)
+
+
+def test_objective_hand_case_A():
+    c = load_cases()["A"]
+    op = oracle.OracleProblem(c["shape"], c["psf"], **c["params"])
+    f, parts = oracle.objective(op, c["y"], c["x"], parts=True)
+    np.testing.assert_allclose(parts, [c["f1"], c["f2"], c["f3"]], rtol=1e-15)
+    np.testing.assert_allclose(oracle.gradient(op, c["y"], c["x"]), c["grad"], rtol=1e-15)
+
+
+def test_objective_hand_case_B():
+    c = load_cases()["B"]
+    op = oracle.OracleProblem(c["shape"], c["psf"], **c["params"])
+    f, parts = oracle.objective(op, c["y"], c["x"], parts=True)
+    assert abs(parts[0] - c["f1"]) < 1e-15 and parts[1] == 0.0
+    np.testing.assert_allclose(oracle.gradient(op, c["y"], c["x"]), c["grad"], atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_central_differences(seed):
+    p, op = _tiny(seed=seed, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(10 + seed)
+    x = p.y.astype(np.float64) + 0.3 * rng.standard_normal(p.shape)      # some voxels outside the box
+    g = oracle.gradient(op, p.y, x)
+    h = 1e-6
+    idx = rng.choice(x.size, size=40, replace=False)
+    for k in idx:
+        e = np.zeros(x.size)
+        e[k] = h
+        e = e.reshape(x.shape)
+        fd = (oracle.objective(op, p.y, x + e) - oracle.objective(op, p.y, x - e)) / (2 * h)
+        assert abs(fd - g.ravel()[k]) <= 2e-7 * max(1.0, abs(g.ravel()[k])), (k, fd, g.ravel()[k])
+
+
+def test_gradient_at_matches_full_gradient():
+    p, op = _tiny(seed=3, shape=(5, 7, 8), psf_shape=(5, 3, 3))
+    x = synth.uniform_start(p.y, seed=3).astype(np.float64)
+    g = oracle.gradient(op, p.y, x)
+    idx = np.array([0, 1, 7, 8 * 7 - 1, 100, x.size - 1, x.size // 2])
+    np.testing.assert_allclose(oracle.gradient_at(op, p.y, x, idx), g.ravel()[idx], rtol=1e-12, atol=1e-14)
+
+
+def _q(op, y, x, xp):
+    g = oracle.gradient(op, y, x)
+    dx = xp - x
+    return oracle.objective(op, y, x) + np.vdot(g, dx) + 0.5 * np.vdot(dx, oracle.apply_A(op, x, dx))
+
+
+def test_majorant_exact_for_pure_least_squares():
+    # lambda = 0, eta = 0: f is quadratic with Hessian H^T H, so Q equals f everywhere.
+    p, _ = _tiny(seed=4)
+    op = oracle.OracleProblem(p.shape, p.psf, lam=0.0, delta=0.1, eta=0.0)
+    rng = np.random.default_rng(5)
+    for _ in range(5):
+        x = rng.standard_normal(p.shape)
+        xp = rng.standard_normal(p.shape)
+        f = oracle.objective(op, p.y, xp)
+        assert abs(_q(op, p.y, x, xp) - f) <= 1e-11 * abs(f)
+
+
+def test_majorant_exact_for_box_on_one_side():
+    # Pure box term with x, x' both above xmax: eta*(x-xmax)^2 is exactly quadratic with curvature 2*eta.
+    shape = (3, 4, 5)
+    psf = np.zeros((3, 1, 1, 1), np.float32)        # H = 0
+    op = oracle.OracleProblem(shape, psf, lam=0.0, delta=0.1, eta=1.7, xmin=0.0, xmax=1.0)
+    rng = np.random.default_rng(6)
+    x = 1.0 + rng.uniform(0.1, 2.0, shape)
+    xp = 1.0 + rng.uniform(0.1, 2.0, shape)
+    y = np.zeros(shape, np.float32)
+    assert abs(_q(op, y, x, xp) - oracle.objective(op, y, xp)) < 1e-12
+
+
+def test_majorization_inequality_random_points():
+    p, op = _tiny(seed=7, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        x = rng.uniform(-0.5, 1.5, p.shape)
+        xp = x + rng.standard_normal(p.shape) * rng.choice([1e-3, 1e-1, 1.0])
+        q = _q(op, p.y, x, xp)
+        f = oracle.objective(op, p.y, xp)
+        assert f <= q + 1e-12 * abs(q)
+
+
+def test_majorant_curvature_is_tight_for_penalty():
+    # With H = 0 and eta = 0 only the hyperbolic penalty remains.  Near flat
+    # regions (t ~ 0) the half-quadratic weight 1/sqrt(delta^2 + t^2) equals
+    # psi''(t), so shrinking the curvature by 30% must break the majorisation
+    # for small steps: this pins the weights (a larger A would also pass).
+    shape = (3, 4, 5)
+    op = oracle.OracleProblem(shape, np.zeros((3, 1, 1, 1), np.float32), lam=1.0, delta=0.5, eta=0.0)
+    y = np.zeros(shape, np.float32)
+    rng = np.random.default_rng(9)
+    violated = False
+    for _ in range(50):
+        x = 0.3 + 1e-4 * rng.standard_normal(shape)
+        dx = 1e-3 * rng.standard_normal(shape)
+        g = oracle.gradient(op, y, x)
+        q_small = oracle.objective(op, y, x) + np.vdot(g, dx) + 0.35 * np.vdot(dx, oracle.apply_A(op, x, dx))
+        if oracle.objective(op, y, x + dx) > q_small:
+            violated = True
+            break
+    assert violated
+
+
+def test_pinv2_against_numpy():
+    rng = np.random.default_rng(11)
+    mats = []
+    for _ in range(20):
+        m = rng.standard_normal((2, 2))
+        mats.append(m @ m.T)                         # SPD
+    v = rng.standard_normal(2)
+    mats.append(np.outer(v, v))                      # rank 1
+    mats.append(np.zeros((2, 2)))                    # zero
+    mats.append(np.diag([3.0, 0.0]))                 # first 3MG iteration (d = 0)
+    mats.append(np.diag([2.0, 2.0]))                 # repeated eigenvalue
+    for B in mats:
+        c = rng.standard_normal(2)
+        u, _ = oracle.pinv2_solve(B, c)
+        np.testing.assert_allclose(u, -np.linalg.pinv(B, rcond=1e-12, hermitian=True) @ c, rtol=1e-10, atol=1e-12)
