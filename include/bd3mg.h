@@ -1,0 +1,168 @@
+/*
+ * bd3mg.h -- C ABI of the GB300 block 3MG (BD3MG) deblurring library.
+ *
+ * The library minimises, on one GPU, the penalised least-squares objective of
+ * Section 3.1 (Eq. "crit") for a 3D volume degraded by a depth-variant blur
+ * (Eq. "model"):
+ *
+ *   f(x) = 1/2 ||H x - y||^2                                   (data term)
+ *        + eta * sum_n dist(x_n, [xmin, xmax])^2              (box term)
+ *        + lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
+ *
+ * with the Majorize-Minimize Memory Gradient iteration run block by block
+ * (Sections 2.2-2.3): at each step a block S (a slab of depth slices) builds
+ * the half-quadratic majorant Q_(S) (Eq. "maj"), the memory-gradient subspace
+ * D_(S) = [-grad_(S) f | d_(S)] and the 2x2 minimiser (Eq. "minimizer"), and
+ * moves x_(S) by D_(S) u (Master box step (2)).  Blocks that cannot interact
+ * are processed together; the result equals visiting the blocks one after the
+ * other in colour-major order (synchronous case of Section 2.4).
+ *
+ * Conventions (all entry points):
+ *   - Volumes are float32, C order [nz][ny][nx] (x fastest).  The PSF is
+ *     float32 [nz][pz][py][px]: entry (z, c+rz, b+ry, a+rx) is the tap
+ *     h_z(a, b, c) of the PSF attached to OUTPUT depth z, applied as
+ *     (Hx)(i,j,z) = sum_{a,b,c} h_z(a,b,c) x(i-a, j-b, z-c), zero outside.
+ *   - V^a is the forward difference along axis a with a zero last row.
+ *   - Every call returns a bd3mg_status and never throws.  After an error the
+ *     context is poisoned: later calls return BD3MG_ESTATE until destroyed;
+ *     bd3mg_error_string gives the first error's text.
+ *   - All device work is ordered on the stream given at creation (a
+ *     cudaStream_t passed as void*; NULL = the legacy default stream).  Calls
+ *     that return host values synchronise that stream.  One host thread per
+ *     context at a time.
+ *   - Inputs are copied; the caller keeps ownership of its buffers.  The
+ *     context owns its device state, obtained through the optional allocator
+ *     (else cudaMallocAsync on the context stream).
+ */
+#ifndef BD3MG_H
+#define BD3MG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bd3mg_ctx bd3mg_ctx;
+
+typedef enum {
+    BD3MG_OK = 0,
+    BD3MG_EINVAL = 1,        /* invalid argument (message says which) */
+    BD3MG_ENOMEM = 2,        /* device allocation failed */
+    BD3MG_ECUDA = 3,         /* a CUDA runtime call failed */
+    BD3MG_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    BD3MG_ENONFINITE = 5,    /* NaN/Inf met in a subspace matrix or objective */
+    BD3MG_ESTATE = 6,        /* context poisoned by an earlier error */
+    BD3MG_EUNSUPPORTED = 7   /* valid request the build does not implement */
+} bd3mg_status;
+
+/* Device memory hook: alloc returns device memory of `bytes` usable on `stream`
+ * (NULL on failure); free releases it.  Both are called from the thread that
+ * calls the library. */
+typedef struct {
+    void *(*alloc)(void *user, size_t bytes, void *stream);
+    void (*free)(void *user, void *ptr, size_t bytes, void *stream);
+    void *user;
+} bd3mg_allocator;
+
+enum { BD3MG_FP32 = 0, BD3MG_BF16_DIRECTIONS = 1 };
+
+typedef struct {
+    int nx, ny, nz;           /* volume extents, each >= 1 */
+    int px, py, pz;           /* PSF extents, odd, >= 1 */
+    const float *psf;         /* HOST pointer, nz*pz*py*px floats, copied at creation */
+    double lambda;            /* > 0 penalty weight */
+    double delta;             /* > 0 hyperbolic smoothing */
+    double eta;               /* >= 0 box weight */
+    double xmin, xmax;        /* box bounds, xmin <= xmax */
+    int precision;            /* BD3MG_FP32 or BD3MG_BF16_DIRECTIONS */
+    int nslabs;               /* number of depth blocks; 0 or 1 = plain 3MG on the whole volume */
+    const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
+    double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
+    int zchunk;               /* output slices per work item; 0 -> chosen by the library */
+} bd3mg_params;
+
+/* Fill *p with defaults (plain FP32, lambda = delta = 1e-2, eta = 1, box [0, 1],
+ * no slabs, extents zero: the caller must set nx..pz and psf). */
+void bd3mg_params_default(bd3mg_params *p);
+
+/* Create a context: validates *p, factors each depth's PSF (the fast path
+ * needs h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c) to FP64 relative residual <=
+ * 1e-6; otherwise BD3MG_EUNSUPPORTED), plans the slab colouring, copies y and
+ * x0 (NULL -> x0 = y) into library memory, sets d = 0 and captures the
+ * per-iteration CUDA graph.  data_on_device: y and x0 are device pointers
+ * (else host).  stream: cudaStream_t as void*.  alloc may be NULL. */
+bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
+                          void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);
+
+/* Run n >= 0 iterations (one iteration = one sweep over all slabs).  If
+ * f_trace is not NULL it receives n+1 host doubles: f(x^k) before each sweep
+ * and f after the last.  Synchronises the stream. */
+bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
+
+/* Enqueue n iterations without synchronising and without reading anything back
+ * (for timing and overlap).  Errors raised on the device surface at the next
+ * synchronising call. */
+bd3mg_status bd3mg_iterate_async(bd3mg_ctx *ctx, int n);
+
+/* Objective at the current iterate; parts (optional, 3 doubles) = data term,
+ * box term, penalty term.  Synchronises. */
+bd3mg_status bd3mg_objective(bd3mg_ctx *ctx, double *f, double *parts);
+
+/* Gradient of f at the current iterate (full volume) written to g (nx*ny*nz
+ * floats; device pointer if on_device else host); f (optional) receives f.
+ * Synchronises. */
+bd3mg_status bd3mg_gradient(bd3mg_ctx *ctx, float *g, int on_device, double *f);
+
+/* Copy the current iterate x (or the memory direction d) out / in.  set_x
+ * also resets d to zero.  Pointers are device if on_device else host. */
+bd3mg_status bd3mg_get_x(bd3mg_ctx *ctx, float *x, int on_device);
+bd3mg_status bd3mg_get_d(bd3mg_ctx *ctx, float *d, int on_device);
+bd3mg_status bd3mg_set_x(bd3mg_ctx *ctx, const float *x, int on_device);
+
+/* Diagnostics of the most recent block steps: for each slab s (in slab order),
+ * 8 doubles {B00, B01, B11, c0, c1, u0, u1, rank} of the 2x2 system of its
+ * last update (B = D^T A D, c = D^T grad f, u = -B^+ c).  info must hold
+ * 8*max(nslabs,1) doubles.  Synchronises. */
+bd3mg_status bd3mg_last_step(bd3mg_ctx *ctx, double *info);
+
+/* Apply the blur H or its adjoint H^T of this context to a device volume
+ * (in and out: device pointers, nx*ny*nz floats, must not alias).  Used to
+ * check the operators; does not touch the iterate. */
+bd3mg_status bd3mg_apply_H(bd3mg_ctx *ctx, const float *in, float *out);
+bd3mg_status bd3mg_apply_HT(bd3mg_ctx *ctx, const float *in, float *out);
+
+/* Slab colouring chosen at creation: colour[s] for each slab (nslabs ints,
+ * host) and the number of colours.  Slabs of one colour are at least
+ * max(pz-1, 1) slices apart, so their steps do not interact. */
+bd3mg_status bd3mg_slab_colours(bd3mg_ctx *ctx, int *colour, int *ncolours);
+
+/* Host-only planning helpers (no GPU needed).
+ * bd3mg_plan_slab_colours: greedy colouring, in increasing z, of the slabs
+ * [bounds[s], bounds[s+1]) so that two slabs of one colour are at least
+ * max(pz-1, 1) slices apart (a slab's step reads r on its slices +- (pz-1)/2
+ * and x one slice beyond; its update changes r on the same reach), which makes
+ * a colour's simultaneous steps equal to the sequential block order of
+ * Section 3.1.  colour: nslabs ints out; returns BD3MG_EINVAL on bad bounds.
+ * bd3mg_factor_psf: rank-1 factoring h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c) of
+ * each depth's PSF in FP64; fx [nz*px], fy [nz*py], fz [nz*pz] out (may be
+ * NULL); *residual = max over depths of max|h - fx fy fz| / max|h|; returns
+ * BD3MG_EUNSUPPORTED when that exceeds 1e-6. */
+bd3mg_status bd3mg_plan_slab_colours(int nslabs, const int *bounds, int pz, int *colour, int *ncolours);
+bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, float *fx, float *fy, float *fz,
+                              double *residual);
+
+/* Number of kernel launches one iteration enqueues. */
+int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
+
+const char *bd3mg_error_string(bd3mg_ctx *ctx);
+const char *bd3mg_status_string(bd3mg_status s);
+
+/* Release the context and its device memory (NULL is a no-op). */
+void bd3mg_destroy(bd3mg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BD3MG_H */

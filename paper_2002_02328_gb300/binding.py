@@ -1,0 +1,336 @@
+"""Thin ctypes binding of the C ABI in include/bd3mg.h.
+
+Argument marshalling only: every step of the iteration runs in the CUDA
+library `libbd3mg.so` built in-tree by `paper_2002_02328_gb300.build`.  There is
+no CPU fallback: if the library is missing, `load()` raises.  PyTorch supplies
+device memory (through the allocator hook) and streams.
+
+The functions named like the C entry points (`bd3mg_create`, `bd3mg_iterate`,
+...) take and return Python objects; `Solver` wraps one context.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libbd3mg.so")
+_lock = threading.Lock()
+_lib = None
+
+STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA", 4: "BD3MG_ETIMEOUT",
+          5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
+FP32, BF16_DIRECTIONS = 0, 1
+
+# Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
+EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
+            "bd3mg_gradient", "bd3mg_get_x", "bd3mg_get_d", "bd3mg_set_x", "bd3mg_last_step", "bd3mg_apply_H",
+            "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
+            "bd3mg_launches_per_iteration", "bd3mg_error_string",
+            "bd3mg_status_string", "bd3mg_destroy"]
+
+
+class Bd3mgError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int),
+                ("psf", ctypes.c_void_p),
+                ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("eta", ctypes.c_double),
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("precision", ctypes.c_int), ("nslabs", ctypes.c_int), ("slab_bounds", ctypes.c_void_p),
+                ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+def load(path: str = LIB_PATH):
+    """Load libbd3mg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(path)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        P = ctypes.POINTER(Params)
+        sig = {
+            "bd3mg_params_default": (None, [P]),
+            "bd3mg_create": (ip, [P, vp, vp, ip, vp, ctypes.POINTER(Allocator), ctypes.POINTER(vp)]),
+            "bd3mg_iterate": (ip, [vp, ip, vp]),
+            "bd3mg_iterate_async": (ip, [vp, ip]),
+            "bd3mg_objective": (ip, [vp, vp, vp]),
+            "bd3mg_gradient": (ip, [vp, vp, ip, vp]),
+            "bd3mg_get_x": (ip, [vp, vp, ip]),
+            "bd3mg_get_d": (ip, [vp, vp, ip]),
+            "bd3mg_set_x": (ip, [vp, vp, ip]),
+            "bd3mg_last_step": (ip, [vp, vp]),
+            "bd3mg_apply_H": (ip, [vp, vp, vp]),
+            "bd3mg_apply_HT": (ip, [vp, vp, vp]),
+            "bd3mg_slab_colours": (ip, [vp, vp, vp]),
+            "bd3mg_plan_slab_colours": (ip, [ip, vp, ip, vp, vp]),
+            "bd3mg_factor_psf": (ip, [ip, ip, ip, ip, vp, vp, vp, vp, vp]),
+            "bd3mg_launches_per_iteration": (ip, [vp]),
+            "bd3mg_error_string": (ctypes.c_char_p, [vp]),
+            "bd3mg_status_string": (ctypes.c_char_p, [ip]),
+            "bd3mg_destroy": (None, [vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(ctx, status: int):
+    if status != 0:
+        lib = load()
+        msg = lib.bd3mg_error_string(ctx).decode() if ctx else lib.bd3mg_status_string(status).decode()
+        raise Bd3mgError(status, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _torch_allocator():
+    """Allocator hook backed by PyTorch's caching allocator (device memory from torch)."""
+    torch = _torch()
+
+    def _alloc(user, nbytes, stream):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                          stream if stream else 0))
+        except Exception:
+            return None
+
+    def _free(user, ptr, nbytes, stream):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    fa, ff = _ALLOC_FN(_alloc), _FREE_FN(_free)
+    return Allocator(fa, ff, None), (fa, ff)
+
+
+def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
+                slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
+                zchunk: int = 0):
+    """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
+    nz, ny, nx = (int(s) for s in shape)
+    psf = np.ascontiguousarray(psf, dtype=np.float32)
+    assert psf.ndim == 4 and psf.shape[0] == nz, psf.shape
+    pz, py, px = psf.shape[1:]
+    p = Params()
+    load().bd3mg_params_default(ctypes.byref(p))
+    p.nx, p.ny, p.nz, p.px, p.py, p.pz = nx, ny, nz, px, py, pz
+    p.psf = psf.ctypes.data
+    p.lambda_, p.delta, p.eta, p.xmin, p.xmax = float(lam), float(delta), float(eta), float(xmin), float(xmax)
+    p.precision = int(precision)
+    p.pinv_rtol = float(pinv_rtol)
+    p.zchunk = int(zchunk)
+    keep = [psf]
+    if slabs is not None and len(slabs) > 2:
+        b = np.ascontiguousarray(slabs, dtype=np.int32)
+        p.nslabs = len(slabs) - 1
+        p.slab_bounds = b.ctypes.data
+        keep.append(b)
+    else:
+        p.nslabs = 1
+    return p, keep
+
+
+def bd3mg_plan_slab_colours(bounds: Sequence[int], pz: int):
+    """Host-only slab colouring; returns (colour array, number of colours)."""
+    b = np.ascontiguousarray(bounds, dtype=np.int32)
+    col = np.zeros(len(bounds) - 1, np.int32)
+    nc = ctypes.c_int()
+    st = load().bd3mg_plan_slab_colours(len(bounds) - 1, b.ctypes.data, int(pz), col.ctypes.data, ctypes.byref(nc))
+    _check(None, st)
+    return col, nc.value
+
+
+def bd3mg_factor_psf(psf: np.ndarray):
+    """Host-only rank-1 factoring; returns (fx, fy, fz, residual) or raises Bd3mgError."""
+    psf = np.ascontiguousarray(psf, dtype=np.float32)
+    nz, pz, py, px = psf.shape
+    fx, fy, fz = np.zeros((nz, px), np.float32), np.zeros((nz, py), np.float32), np.zeros((nz, pz), np.float32)
+    res = ctypes.c_double()
+    st = load().bd3mg_factor_psf(nz, px, py, pz, psf.ctypes.data, fx.ctypes.data, fy.ctypes.data, fz.ctypes.data,
+                                 ctypes.byref(res))
+    if st != 0:
+        raise Bd3mgError(st, f"PSF not separable (residual {res.value:.3g})")
+    return fx, fy, fz, res.value
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def bd3mg_create(params: Params, y, x0=None, stream=None, use_torch_allocator: bool = True):
+    """Create a context from torch tensors y (and x0), on the GPU or on the host.
+
+    Returns (ctx handle, keepalive).  Host tensors are copied from host memory.
+    """
+    torch = _torch()
+    lib = load()
+    on_dev = bool(y.is_cuda)
+    y = y.contiguous()
+    if x0 is not None:
+        x0 = x0.contiguous()
+        assert bool(x0.is_cuda) == on_dev
+    s = stream if stream is not None else (torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0)
+    keep = [y, x0]
+    alloc_p = None
+    if use_torch_allocator:
+        al, cbs = _torch_allocator()
+        keep += [al, cbs]
+        alloc_p = ctypes.byref(al)
+    ctx = ctypes.c_void_p()
+    st = lib.bd3mg_create(ctypes.byref(params), ctypes.c_void_p(_ptr(y)),
+                          ctypes.c_void_p(_ptr(x0)) if x0 is not None else None, int(on_dev),
+                          ctypes.c_void_p(int(s)), alloc_p, ctypes.byref(ctx))
+    if st != 0:
+        msg = lib.bd3mg_error_string(ctx).decode() if ctx.value else lib.bd3mg_status_string(st).decode()
+        if ctx.value:
+            lib.bd3mg_destroy(ctx)
+        raise Bd3mgError(st, msg)
+    return ctx, keep
+
+
+class Solver:
+    """One block-3MG context over a single volume (plain or slab form)."""
+
+    def __init__(self, shape, psf, y, x0=None, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
+                 slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
+                 use_torch_allocator: bool = True):
+        torch = _torch()
+        self.shape = tuple(int(s) for s in shape)
+        self.n = int(np.prod(self.shape))
+        self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
+        params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk)
+        if not isinstance(y, torch.Tensor):
+            y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
+        if x0 is not None and not isinstance(x0, torch.Tensor):
+            x0 = torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32))
+        self.device = y.device
+        self._ctx, self._keep = bd3mg_create(params, y, x0, stream, use_torch_allocator)
+        self._keep.append(keep)
+        self._lib = load()
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.bd3mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, st):
+        _check(self._ctx, st)
+
+    # -- iteration
+    def iterate(self, n: int, trace: bool = True):
+        """Run n sweeps; returns the FP64 objective trace (n+1 values) or None."""
+        buf = np.zeros(n + 1) if trace else None
+        self._c(self._lib.bd3mg_iterate(self._ctx, int(n), buf.ctypes.data if trace else None))
+        return buf
+
+    def iterate_async(self, n: int):
+        self._c(self._lib.bd3mg_iterate_async(self._ctx, int(n)))
+
+    def objective(self, parts: bool = False):
+        f = ctypes.c_double()
+        pr = np.zeros(3)
+        self._c(self._lib.bd3mg_objective(self._ctx, ctypes.byref(f), pr.ctypes.data))
+        return (f.value, pr) if parts else f.value
+
+    def gradient(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        f = ctypes.c_double()
+        self._c(self._lib.bd3mg_gradient(self._ctx, ctypes.c_void_p(_ptr(out)), int(out.is_cuda), ctypes.byref(f)))
+        return out, f.value
+
+    def get_x(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        self._c(self._lib.bd3mg_get_x(self._ctx, ctypes.c_void_p(_ptr(out)), int(out.is_cuda)))
+        return out
+
+    def get_d(self, out=None):
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shape, dtype=torch.float32, device="cuda")
+        self._c(self._lib.bd3mg_get_d(self._ctx, ctypes.c_void_p(_ptr(out)), int(out.is_cuda)))
+        return out
+
+    def set_x(self, x):
+        torch = _torch()
+        if not isinstance(x, torch.Tensor):
+            x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        x = x.contiguous()
+        self._c(self._lib.bd3mg_set_x(self._ctx, ctypes.c_void_p(_ptr(x)), int(x.is_cuda)))
+
+    def last_step(self) -> np.ndarray:
+        """Per slab: [B00, B01, B11, c0, c1, u0, u1, rank] of its latest update."""
+        buf = np.zeros((self.nslabs, 8))
+        self._c(self._lib.bd3mg_last_step(self._ctx, buf.ctypes.data))
+        return buf
+
+    def apply_H(self, t, adjoint: bool = False):
+        torch = _torch()
+        t = t.contiguous()
+        out = torch.empty_like(t)
+        fn = self._lib.bd3mg_apply_HT if adjoint else self._lib.bd3mg_apply_H
+        self._c(fn(self._ctx, ctypes.c_void_p(_ptr(t)), ctypes.c_void_p(_ptr(out))))
+        return out
+
+    def colours(self):
+        col = np.zeros(self.nslabs, np.int32)
+        nc = ctypes.c_int()
+        self._c(self._lib.bd3mg_slab_colours(self._ctx, col.ctypes.data, ctypes.byref(nc)))
+        return col, nc.value
+
+    def launches_per_iteration(self) -> int:
+        return int(self._lib.bd3mg_launches_per_iteration(self._ctx))
+
+    @classmethod
+    def from_problem(cls, prob, x0=None, device="cuda", slabs="auto", **kw):
+        torch = _torch()
+        y = torch.from_numpy(prob.y).to(device)
+        if x0 is not None:
+            x0 = torch.from_numpy(np.ascontiguousarray(x0, np.float32)).to(device)
+        sl = prob.slabs if slabs == "auto" else slabs
+        return cls(prob.shape, prob.psf, y, x0, lam=prob.lam, delta=prob.delta, eta=prob.eta, xmin=prob.xmin,
+                   xmax=prob.xmax, slabs=sl, **kw)

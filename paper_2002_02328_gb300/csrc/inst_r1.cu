@@ -1,0 +1,12 @@
+// inst_r1.cu -- tile kernels instantiated for xy PSF radius 1.
+#include "launchers.cuh"
+
+namespace bd3mg {
+static const KernelSet kSets[] = {
+    BD3MG_KERNEL_SET(1,1),
+};
+int kernel_sets_r1(const KernelSet **out) {
+    *out = kSets;
+    return (int)(sizeof(kSets) / sizeof(kSets[0]));
+}
+}  // namespace bd3mg

@@ -1,0 +1,13 @@
+// inst_r2.cu -- tile kernels instantiated for xy PSF radius 2.
+#include "launchers.cuh"
+
+namespace bd3mg {
+static const KernelSet kSets[] = {
+    BD3MG_KERNEL_SET(2,1),
+    BD3MG_KERNEL_SET(2,2),
+};
+int kernel_sets_r2(const KernelSet **out) {
+    *out = kSets;
+    return (int)(sizeof(kSets) / sizeof(kSets[0]));
+}
+}  // namespace bd3mg

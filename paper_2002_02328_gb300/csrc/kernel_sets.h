@@ -1,0 +1,36 @@
+// kernel_sets.h -- registry of the compiled (R, RZ) instantiations of the tile
+// kernels.  R is the xy PSF radius, RZ the z radius the kernels are built for;
+// a context pads its PSF factors with zero taps up to the chosen set.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace bd3mg {
+
+struct KArgs;
+struct VolDev;
+struct SegDev;
+typedef void (*launch_fn)(const KArgs &, cudaStream_t);
+typedef cudaError_t (*prep_fn)();
+
+struct KernelSet {
+    int R, RZ;
+    launch_fn residual, gradient, curvature;
+    prep_fn prepare;               // raises the dynamic shared-memory limit
+    size_t smem_residual, smem_gradient, smem_curvature;
+};
+
+// Smallest compiled set with R' >= R and RZ' >= RZ (fewest padded taps), or null.
+const KernelSet *find_kernel_set(int R, int RZ);
+
+// Block update over the slabs listed in seg_list (grid.y = number of slabs).
+void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, dim3 grid,
+                   cudaStream_t s);
+
+int kernel_sets_r1(const KernelSet **out);
+int kernel_sets_r2(const KernelSet **out);
+int kernel_sets_r3(const KernelSet **out);
+int kernel_sets_r4(const KernelSet **out);
+int kernel_sets_r5(const KernelSet **out);
+
+}  // namespace bd3mg
