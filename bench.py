@@ -1,0 +1,488 @@
+#!/usr/bin/env python
+"""Benchmark of the block 3MG deblurring library on one GB300 (or N replicas).
+
+Workload (the block form): 256x256x64 phantom (200 ellipsoids, seed 0), per-depth
+7x7x7 Gaussian PSF with sigma_xy 0.5 -> 3.0 and sigma_z = 1, noise 0.02,
+lambda = delta = 1e-2, eta = 1, box [0, 1], 8 depth slabs of 4,14,6,10,5,12,7,6
+slices (3 colours).  Synthetic data stands in for the paper's microscopy volumes.
+
+One step = one sweep of block 3MG over all slabs (objective pass + for each
+colour: residual, gradient, curvature + 2x2 solve, update), launched as one
+CUDA graph.  `value` is sweeps per second over all ranks (each rank solves its
+own replica: weak scaling, no collective on the data path).  L2 is flushed
+(256 MiB write) before every timed step; each step is bracketed by CUDA events
+on the library's stream.
+
+Extra keys: the plain FP32 single-block form on the same volume, iterations and
+device time to relative objective gap 1e-4 for both forms (f* from a long run),
+the per-kernel roofline, e2e through host buffers, and the FP64 CPU oracle
+timed on a bounded sample (`cpu_baseline`).
+
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "3MG iterations/s and time to rel. objective gap 1e-4 vs plain FP32, at 1 GB300"
+UNIT = "iterations/s"
+GAP = 1e-4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fstar-iters", type=int, default=10000)
+    ap.add_argument("--profile-iters", type=int, default=50, help=">= 1")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--quick", action="store_true", help="skip f*, time-to-gap and e2e (for profiling runs)")
+    return ap.parse_args()
+
+
+def env_rank():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload():
+    from paper_2002_02328_gb300 import synth
+    return synth.workload_slabs(seed=0)
+
+
+def workload_config(prob, extra=None):
+    cfg = {"workload": "block-3MG slabs 256x256x64, PSF 7x7x7 depth-variant Gaussian, 8 slabs [4,14,6,10,5,12,7,6]",
+           "volume": list(prob.shape[::-1]), "psf": [7, 7, 7], "slabs": prob.slabs, "lambda": prob.lam,
+           "delta": prob.delta, "eta": prob.eta, "box": [prob.xmin, prob.xmax], "precision": "fp32",
+           "step": "one sweep over all slabs", "l2": "flushed (256 MiB write) before every timed step"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ---------------------------------------------------------------------------
+# oracle sample (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _tap_work(shape, psf_shape):
+    """Inner-loop iterations of one plain dense convolution over `shape` (valid taps only)."""
+    tot = 1.0
+    for n, p in zip(shape, psf_shape):
+        r = (p - 1) // 2
+        i = np.arange(n)[:, None] - np.arange(-r, r + 1)[None, :]
+        tot *= float(np.count_nonzero((i >= 0) & (i < n)))
+    return tot
+
+
+class OracleSample:
+    """The FP64 oracle timed on an x/y crop (all depth slices) of the workload.
+
+    One sample = one oracle slab step (gradient + two majorant products + the
+    2x2 solve, all full-crop plain convolutions) plus one oracle objective.  A
+    sweep of the workload is 8 slab steps + 1 objective over the full volume
+    (each oracle step works on the whole volume), so the sweep time is the
+    sample time scaled by the ratio of valid PSF taps (full / crop)."""
+
+    def __init__(self, prob, budget_s: float, threads: int):
+        import oracle
+        oracle.set_threads(threads)
+        self.prob = prob
+        self.threads = threads
+        nz, ny, nx = prob.shape
+        t16 = self._run(16)[2]
+        c = int(16 * np.sqrt(max(budget_s, 1e-3) / max(t16, 1e-6)))
+        self.c = int(max(8, min(min(nx, ny), c)))
+
+    def _run(self, c):
+        import oracle
+        p = self.prob
+        y = np.ascontiguousarray(p.y[:, :c, :c])
+        op = oracle.OracleProblem(y.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax)
+        x = y.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.step(op, y, x, np.zeros_like(x))
+        t1 = time.perf_counter()
+        oracle.objective(op, y, x)
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, t2 - t0
+
+    def measure(self):
+        """Returns (sweeps/s estimate, sample seconds)."""
+        ts, to, tt = self._run(self.c)
+        p = self.prob
+        pz, py, px = p.psf.shape[1:]
+        scale = _tap_work(p.shape, (pz, py, px)) / _tap_work((p.shape[0], self.c, self.c), (pz, py, px))
+        return 1.0 / (scale * (8 * ts + to)), tt
+
+    def text(self, secs):
+        nz = self.prob.shape[0]
+        return (f"FP64 oracle slab step + objective on a {self.c}x{self.c}x{nz} x/y crop ({secs:.2f} s per sample), "
+                f"scaled to one 8-slab sweep of the full volume by the count of valid PSF taps")
+
+
+def reference_arm(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    prob = workload()
+    threads = len(os.sched_getaffinity(0))
+    budget = max(0.02, 120.0 / max(1, args.steps + args.warmup))
+    smp = OracleSample(prob, budget, threads)
+    rates, secs = [], []
+    for k in range(args.warmup + args.steps):
+        r, t = smp.measure()
+        if k >= args.warmup:
+            rates.append(r)
+            secs.append(t)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(prob, {"precision": "fp64 (CPU oracle)"}),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": smp.text(float(np.mean(secs)))},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["timestamp", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", gpu_id, "--query-gpu=" + ",".join(self.FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        self.windows = []
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc is None:
+            return {"unavailable": "nvidia-smi not runnable"}
+        time.sleep(0.1)
+        self.proc.terminate()
+        out = self.proc.communicate(timeout=10)[0]
+        import datetime as dt
+        sm, smax, reasons = [], None, set()
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(self.FIELDS):
+                continue
+            try:
+                ts = dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            if not any(a - 0.06 <= ts <= b + 0.06 for a, b in self.windows):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"],
+                                 parts[5:9]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"unavailable": "no nvidia-smi sample fell inside the timed region"}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_id_for(device_index: int) -> str:
+    import torch
+    props = torch.cuda.get_device_properties(device_index)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        s = str(uuid)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    return str(device_index)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(name: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{name}.txt")
+    src = os.path.join(ROOT, "paper_2002_02328_gb300", "csrc", "kernels.cuh")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("kernels_cuh_sha256") != sha:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic_bytes(prob, slabs, rz):
+    """Per-class algorithmic bytes of one sweep (FP32 words per voxel, halos excluded):
+    objective 2 (x, y), residual 3 per output voxel (x, y in; r out), gradient 3 (r, x in; g out),
+    curvature 3 (g, d, x in), update 5 (x, g, d in; x, d out)."""
+    nz, ny, nx = prob.shape
+    plane = nx * ny
+    n = prob.n
+    if slabs is None or len(slabs) <= 2:
+        return {"objective": 0.0, "residual": 12.0 * n, "gradient": 12.0 * n, "curvature": 12.0 * n,
+                "update": 20.0 * n}
+    res = sum(min(nz, slabs[s + 1] + rz) - max(0, slabs[s] - rz) for s in range(len(slabs) - 1)) * plane
+    return {"objective": 8.0 * n, "residual": 12.0 * res, "gradient": 12.0 * n, "curvature": 12.0 * n,
+            "update": 20.0 * n}
+
+
+def time_steps(solver, steps, flush, stream, sampler=None):
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0 = time.time()
+    for k in range(steps):
+        flush.fill_(float(k & 7))
+        starts[k].record(stream)
+        solver.iterate_async(1)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if sampler is not None:
+        sampler.mark(t0, t1)
+    return float(sum(s.elapsed_time(e) for s, e in zip(starts, ends)))
+
+
+def fstar_of(prob, iters):
+    """f* from a long FP32 run of the plain form (accepted if the last 10% moved < 1e-6 |f*|)."""
+    from paper_2002_02328_gb300 import binding
+    with binding.Solver.from_problem(prob, slabs=None) as s:
+        tr = s.iterate(iters)
+    f = float(tr[-1])
+    settle = float(tr[int(0.9 * iters)] - tr[-1]) / abs(f)
+    return f, settle
+
+
+def time_to_gap(prob, slabs, fstar, max_iters, stream):
+    """Iterations to gap <= 1e-4 (from the trace), then the device time of exactly that many."""
+    import torch
+    from paper_2002_02328_gb300 import binding
+    with binding.Solver.from_problem(prob, slabs=slabs) as s:
+        tr = s.iterate(max_iters)
+    gap = (tr - fstar) / abs(fstar)
+    hit = np.nonzero(gap <= GAP)[0]
+    if hit.size == 0:
+        return None, None, float(gap[-1])
+    k = int(hit[0])
+    with binding.Solver.from_problem(prob, slabs=slabs) as s:
+        s.iterate(2)                         # warm the graph, then restart from y
+        s.set_x(torch.from_numpy(prob.y).cuda())
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.iterate(k, trace=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+    return k, ms / 1e3, float(gap[k])
+
+
+def e2e_run(prob, n_iter, stream):
+    """Whole solve through the public API with host buffers: H2D of y from pinned memory,
+    context creation, n_iter sweeps with the f trace read back, D2H of x to pinned memory."""
+    import torch
+    from paper_2002_02328_gb300 import binding
+    y_host = torch.from_numpy(prob.y).pin_memory()
+    x_host = torch.empty(prob.shape, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with binding.Solver(prob.shape, prob.psf, y_host, lam=prob.lam, delta=prob.delta, eta=prob.eta,
+                        xmin=prob.xmin, xmax=prob.xmax, slabs=prob.slabs) as s:
+        tr = s.iterate(n_iter)
+        s.get_x(x_host)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    h2d = prob.y.nbytes + prob.psf.nbytes
+    d2h = x_host.numel() * 4 + tr.nbytes
+    return n_iter / dt, h2d / n_iter, d2h / n_iter, dt
+
+
+def ours(args):
+    import torch
+    args.profile_iters = max(1, args.profile_iters)
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2002_02328_gb300 import binding, build
+    build.build()
+    binding.load()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    prob = workload()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+    sampler = ClockSampler(gpu_id_for(dev)) if rank == 0 else None
+    time.sleep(0.3)
+
+    with binding.Solver.from_problem(prob) as s:
+        lpi = s.launches_per_iteration()
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            s.iterate_async(1)
+        barrier()
+        ms_total = time_steps(s, args.steps, flush, stream, sampler)
+        barrier()
+        # per-kernel device times (events around every launch), L2 flushed before each iteration
+        prof = {k: [0.0, 0] for k in binding.Solver.KERNEL_CLASSES}
+        for _ in range(args.profile_iters):
+            flush.fill_(2.0)
+            for k, (ms, cnt) in s.profile_iteration().items():
+                prof[k][0] += ms
+                prof[k][1] += cnt
+        tr = s.iterate(0)
+    # plain FP32 single block, same volume
+    with binding.Solver.from_problem(prob, slabs=None) as sp:
+        lpi_plain = sp.launches_per_iteration()
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            sp.iterate_async(1)
+        barrier()
+        ms_plain = time_steps(sp, max(10, args.steps // 2), flush, stream, sampler)
+        barrier()
+        prof_plain = {k: [0.0, 0] for k in binding.Solver.KERNEL_CLASSES}
+        for _ in range(args.profile_iters):
+            flush.fill_(2.0)
+            for k, (ms, cnt) in sp.profile_iteration().items():
+                prof_plain[k][0] += ms
+                prof_plain[k][1] += cnt
+    clocks = sampler.stop() if sampler is not None else None
+
+    ms_per_step = ms_total / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_per_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    value = world * 1e3 / ms_per_step
+    plain_rate = 1e3 / (ms_plain / max(10, args.steps // 2))
+
+    # roofline of the dominant kernel (largest device time per sweep)
+    peaks, peak_kind = measured_peaks()
+    alg = algorithmic_bytes(prob, prob.slabs, 3)
+    per_it = {k: v[0] / args.profile_iters for k, v in prof.items()}
+    dom = max(per_it, key=per_it.get)
+    launches_dom = prof[dom][1] / args.profile_iters
+    avg_launch_ms = per_it[dom] / launches_dom
+    achieved = (alg[dom] / launches_dom) / (avg_launch_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    traffic = kernel_traffic(f"k_{dom}")
+    roofline = {"bound": "hbm", "kernel": f"k_{dom}", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} hbm_gbs",
+                "alg_bytes_per_launch": alg[dom] / launches_dom, "avg_launch_ms": avg_launch_ms,
+                "kernel_ms_per_sweep": per_it}
+    # whole sweep against the 7-word (28 B/voxel) lower bound of one fused pass
+    sweep_lb_ms = 28.0 * prob.n / (peak * 1e9) * 1e3
+    alg_plain = algorithmic_bytes(prob, None, 3)
+    per_it_plain = {k: v[0] / args.profile_iters for k, v in prof_plain.items()}
+
+    extra = {"sweep_vs_28B_lower_bound": sweep_lb_ms / ms_per_step,
+             "plain_fp32": {"iterations_per_s": plain_rate, "launches_per_iteration": lpi_plain,
+                            "kernel_ms_per_iteration": per_it_plain,
+                            "alg_bytes_per_iteration": sum(alg_plain.values())}}
+
+    cpu = None
+    if not args.quick:
+        fstar, settle = fstar_of(prob, args.fstar_iters)
+        k_b, t_b, g_b = time_to_gap(prob, prob.slabs, fstar, 3000, stream)
+        k_p, t_p, g_p = time_to_gap(prob, None, fstar, 3000, stream)
+        extra["time_to_gap"] = {"gap": GAP, "fstar": fstar, "fstar_iters": args.fstar_iters,
+                                "fstar_settle_rel": settle,
+                                "block": {"iterations": k_b, "seconds": t_b},
+                                "plain_fp32": {"iterations": k_p, "seconds": t_p}}
+        e2e_rate, h2d, d2h, e2e_s = e2e_run(prob, 500, stream)
+        e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}
+    else:
+        e2e = None
+    if not args.no_cpu_baseline and world == 1:
+        threads = len(os.sched_getaffinity(0))
+        smp = OracleSample(prob, args.cpu_seconds, threads)
+        r, secs = smp.measure()
+        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": smp.text(secs)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(prob, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * lpi + 0, "clocks": clocks, "extra": extra}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
