@@ -152,6 +152,23 @@ bd3mg_status bd3mg_plan_slab_colours(int nslabs, const int *bounds, int pz, int 
 bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, float *fx, float *fy, float *fz,
                               double *residual);
 
+/* Kernel classes reported by bd3mg_profile_iteration. */
+enum {
+    BD3MG_K_OBJECTIVE = 0,   /* objective pass of the block form (one per sweep) */
+    BD3MG_K_RESIDUAL = 1,    /* r = H x - y (plain form: fused with the objective) */
+    BD3MG_K_GRADIENT = 2,    /* g = H^T r + box + penalty gradient */
+    BD3MG_K_CURVATURE = 3,   /* H g_S, H d_S, weights, inner products, 2x2 solve */
+    BD3MG_K_UPDATE = 4,      /* x_S += D u, d_S = D u */
+    BD3MG_K_CLASSES = 5
+};
+
+/* Run ONE iteration without the CUDA graph, with CUDA events recorded on the
+ * context stream around every launch, and synchronise.  ms[k] receives the
+ * summed device time of class k and launches[k] its launch count (arrays of
+ * BD3MG_K_CLASSES; either may be NULL).  The iterate advances exactly as with
+ * bd3mg_iterate_async(ctx, 1). */
+bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
+
 /* Number of kernel launches one iteration enqueues. */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 

@@ -30,7 +30,7 @@ FP32, BF16_DIRECTIONS = 0, 1
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
             "bd3mg_gradient", "bd3mg_get_x", "bd3mg_get_d", "bd3mg_set_x", "bd3mg_last_step", "bd3mg_apply_H",
             "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
-            "bd3mg_launches_per_iteration", "bd3mg_error_string",
+            "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
             "bd3mg_plan_slab_colours": (ip, [ip, vp, ip, vp, vp]),
             "bd3mg_factor_psf": (ip, [ip, ip, ip, ip, vp, vp, vp, vp, vp]),
             "bd3mg_launches_per_iteration": (ip, [vp]),
+            "bd3mg_profile_iteration": (ip, [vp, vp, vp]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
             "bd3mg_destroy": (None, [vp]),
@@ -321,6 +322,15 @@ class Solver:
         nc = ctypes.c_int()
         self._c(self._lib.bd3mg_slab_colours(self._ctx, col.ctypes.data, ctypes.byref(nc)))
         return col, nc.value
+
+    KERNEL_CLASSES = ("objective", "residual", "gradient", "curvature", "update")
+
+    def profile_iteration(self):
+        """One iteration with CUDA events around every launch: {class: (ms, launches)}."""
+        ms = np.zeros(5)
+        cnt = np.zeros(5, np.int32)
+        self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
 
     def launches_per_iteration(self) -> int:
         return int(self._lib.bd3mg_launches_per_iteration(self._ctx))

@@ -3,6 +3,8 @@
 // Planning (PSF factoring, slab colouring, work lists), device state, CUDA
 // graph capture of one iteration, and the entry points.  No device arithmetic
 // lives here; every step of the iteration runs in the kernels of kernels.cuh.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,10 +49,14 @@ struct bd3mg_ctx {
     int ncolours = 1;
     long long n = 0;
 
-    // device state
+    // device state (volumes pitched: rows of `pitch` floats, pitch % 4 == 0)
+    int pitch = 0;
+    size_t np = 0;                // pitch*ny*nz
     float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
+    float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch (lazy)
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev *vols = nullptr;       // [0] = problem, [1] = scratch for operator calls
+    VolMaps *maps = nullptr;      // TMA descriptors, same indexing as vols
     SegDev *segs = nullptr;       // [0..nslabs-1] slabs, [nslabs] full volume
     Item *items = nullptr;
     int *slot_beg = nullptr, *slot_id = nullptr;
@@ -69,10 +75,15 @@ struct bd3mg_ctx {
     Launch L_obj, L_res_full, L_grad_full;
     std::vector<Launch> L_res, L_grad, L_curv;
     int max_items = 0;
-    int zchunk = 8;
+    int sms = 152;                // SM count of the device
+    int occ[3] = {1, 1, 1};       // resident CTAs per SM: residual, gradient, curvature
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // profiling: when prof_on, every launch is bracketed by events (not in graphs)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_cls;
     long long iterations = 0;
 };
 
@@ -116,6 +127,53 @@ bd3mg_status dalloc(bd3mg_ctx *c, void **p, size_t bytes) {
 template <typename T>
 bd3mg_status dalloc_n(bd3mg_ctx *c, T **p, size_t count) {
     return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D tile map over a pitched float32 volume: dims (nx, ny, nz), box (bx, by, 1),
+// zero fill outside the volume.
+bool encode_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int pitch, int bx, int by) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * (cuuint64_t)ny};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Staged-tile extents of a kernel set (must match Geo<R,RZ> in kernels.cuh).
+int set_xh(const KernelSet *k) { return k->R <= 4 ? 4 : 8; }
+
+// Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
+int tile_y(int kind) { return kind == 2 ? TY_C : TY_A; }
+
+bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const float *x, const float *r, const float *g, const float *d) {
+    const bd3mg_params &p = c->p;
+    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks);
+    std::memset(vm, 0, sizeof(*vm));
+    bool ok = true;
+    if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, p.nx, p.ny, p.nz, c->pitch, bx, TY_A + 2 * R);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, p.nx, p.ny, p.nz, c->pitch, BX1, TY_A + 2);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, p.nx, p.ny, p.nz, c->pitch, BX1, TY_C + 2);
+    if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, p.nx, p.ny, p.nz, c->pitch, bx, TY_A + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
+    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
+    return ok;
 }
 
 // Rank-1 factoring of each depth's PSF in FP64: with m_x(a) = sum_{b,c} h,
@@ -183,18 +241,60 @@ int colour_slabs(const std::vector<int> &bounds, int gap, std::vector<int> &colo
     return (int)last_end.size();
 }
 
-void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi) {
-    const int ntx = (c->p.nx + TX - 1) / TX, nty = (c->p.ny + TY - 1) / TY;
-    for (int z = zlo; z < zhi; z += c->zchunk) {
-        const int z1 = std::min(zhi, z + c->zchunk);
-        for (int ty = 0; ty < nty; ++ty)
-            for (int tx = 0; tx < ntx; ++tx) c->items_h.push_back(Item{seg, tx * TX, ty * TY, z, z1});
+int ntiles(const bd3mg_ctx *c, int ty) { return ((c->p.nx + TX - 1) / TX) * ((c->p.ny + ty - 1) / ty); }
+
+// Items of one segment: its output range split into nch balanced z-chunks,
+// each chunk crossed with every xy tile (chunk-major, so concurrently running
+// CTAs share halo slices in L2).
+void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi, int zc, int ty) {
+    const int ntx = (c->p.nx + TX - 1) / TX, nty = (c->p.ny + ty - 1) / ty;
+    const int len = zhi - zlo;
+    if (len <= 0) return;
+    const int nch = (len + zc - 1) / zc;
+    for (int k = 0; k < nch; ++k) {
+        const int z0 = zlo + (int)((long long)len * k / nch), z1 = zlo + (int)((long long)len * (k + 1) / nch);
+        for (int t = 0; t < nty; ++t)
+            for (int tx = 0; tx < ntx; ++tx) c->items_h.push_back(Item{seg, tx * TX, t * ty, z0, z1});
     }
+}
+
+// z-chunk for a launch: minimise (waves of resident CTAs) x (longest chunk +
+// z halo), the makespan of equal-cost items; ties go to longer chunks.
+int choose_zchunk(const bd3mg_ctx *c, const std::vector<std::pair<int, int>> &ranges, int kind) {
+    if (c->p.zchunk > 0) return std::min(c->p.zchunk, ZC_MAX);
+    const long long slots = (long long)c->sms * std::max(1, c->occ[kind]);
+    const int halo = 2 * c->ks->RZ;
+    long long best_cost = -1;
+    int best = 4;
+    for (int zc = 4; zc <= ZC_MAX; ++zc) {
+        long long items = 0;
+        int longest = 0;
+        for (auto &r : ranges) {
+            const int len = r.second - r.first;
+            if (len <= 0) continue;
+            const int nch = (len + zc - 1) / zc;
+            items += (long long)nch * ntiles(c, tile_y(kind));
+            longest = std::max(longest, (len + nch - 1) / nch);
+        }
+        const long long cost = ((items + slots - 1) / slots) * (longest + halo);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
 }
 
 // Build one launch over the given segments, each with output range f(seg).
 template <typename F>
-Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slots, int slot_of_vol) {
+Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slots, int slot_of_vol, int kind) {
+    std::vector<std::pair<int, int>> ranges;
+    for (int s : segs) {
+        int lo, hi;
+        range(s, &lo, &hi);
+        ranges.emplace_back(lo, hi);
+    }
+    const int zc = choose_zchunk(c, ranges, kind);
     Launch L;
     L.item_off = (int)c->items_h.size();
     L.beg_off = (int)c->slot_beg_h.size();
@@ -204,7 +304,7 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slo
         for (int s : segs) {
             int lo, hi;
             range(s, &lo, &hi);
-            add_items(c, s, lo, hi);
+            add_items(c, s, lo, hi, zc, tile_y(kind));
         }
         if (slots) {
             c->slot_beg_h.push_back(0);
@@ -217,7 +317,7 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slo
             int lo, hi;
             range(s, &lo, &hi);
             const int beg = (int)c->items_h.size() - base;
-            add_items(c, s, lo, hi);
+            add_items(c, s, lo, hi, zc, tile_y(kind));
             if (slots) {
                 c->slot_beg_h.push_back(beg);
                 c->slot_id_h.push_back(s);
@@ -236,6 +336,7 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slo
 KArgs make_args(bd3mg_ctx *c, const Launch &L, int mode, const VolDev *vols) {
     KArgs a{};
     a.vols = vols ? vols : c->vols;
+    a.maps = vols ? c->maps + (vols - c->vols) : c->maps;
     a.segs = c->segs;
     a.items = c->items + L.item_off;
     a.nitems = L.nitems;
@@ -275,20 +376,37 @@ static bd3mg_status upload_plan(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+// Event bracket of one launch while profiling (never inside a graph capture).
+static bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
+    if (!c->prof_on) return BD3MG_OK;
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->prof_ev.push_back(e);
+    c->prof_cls.push_back(cls);
+    CK(cudaEventRecord(e, s));
+    return BD3MG_OK;
+}
+
 static bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
     KArgs a = make_args(c, L, mode, vols);
+    bd3mg_status st = prof_mark(c, s, (mode & M_STORE_R) ? BD3MG_K_RESIDUAL : BD3MG_K_OBJECTIVE);
+    if (st) return st;
     c->ks->residual(a, s);
     return check_launch(c);
 }
 
 static bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
     KArgs a = make_args(c, L, mode, vols);
+    bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
+    if (st) return st;
     c->ks->gradient(a, s);
     return check_launch(c);
 }
 
 static bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     KArgs a = make_args(c, L, 0, nullptr);
+    bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
+    if (st) return st;
     c->ks->curvature(a, s);
     return check_launch(c);
 }
@@ -298,11 +416,13 @@ static bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     long long maxlen = 0;
     for (int k = 0; k < cnt; ++k) {
         const int sidx = c->seg_lists_h[off + k];
-        maxlen = std::max<long long>(maxlen, (long long)(c->bounds[sidx + 1] - c->bounds[sidx]) * c->p.nx * c->p.ny);
+        maxlen = std::max<long long>(maxlen, (long long)(c->bounds[sidx + 1] - c->bounds[sidx]) * c->pitch * c->p.ny);
     }
     long long blocks = (maxlen / 4 + NT - 1) / NT;
     blocks = std::max<long long>(1, std::min<long long>(blocks, 2048));
     dim3 grid((unsigned)blocks, (unsigned)cnt);
+    bd3mg_status st = prof_mark(c, s, BD3MG_K_UPDATE);
+    if (st) return st;
     launch_update(c->vols, c->segs, c->seg_lists + off, c->u, grid, s);
     return check_launch(c);
 }
@@ -343,6 +463,7 @@ static bd3mg_status check_status(bd3mg_ctx *c) {
     int st = 0;
     CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    if (st & ST_TIMEOUT) return fail(c, BD3MG_ETIMEOUT, "a TMA slice copy did not complete within the wait limit");
     if (st & ST_NONFINITE) return fail(c, BD3MG_ENONFINITE, "non-finite value in a subspace matrix or objective");
     return BD3MG_OK;
 }
@@ -460,25 +581,26 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
     // colouring: slabs of one colour at least max(2*rz, 1) slices apart
     c->ncolours = colour_slabs(c->bounds, std::max(2 * c->rz, 1), c->colour);
 
+    // occupancy of the chosen kernels (drives the z-chunk choice)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = c->ks->prepare();
+        if (e != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e)));
+        for (int k = 0; k < 3; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+    }
+
     // work lists
     const int RZk = c->ks->RZ;          // kernel z radius (padded), governs halos
     const int Lk = std::max(RZk, 1);
-    {
-        const long long ntiles = (long long)((p.nx + TX - 1) / TX) * ((p.ny + TY - 1) / TY);
-        if (p.zchunk > 0) c->zchunk = p.zchunk;
-        else {
-            const long long target = 152LL * 6;
-            long long zc = (ntiles * p.nz + target - 1) / target;
-            c->zchunk = (int)std::max<long long>(4, std::min<long long>(32, zc));
-        }
-    }
     const int nz = p.nz;
     std::vector<int> all_slabs;
     for (int s = 0; s < c->nslabs; ++s) all_slabs.push_back(s);
     const int FULL = c->nslabs;          // full-volume segment index
-    c->L_obj = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0);
-    c->L_res_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0);
-    c->L_grad_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, false, 0);
+    c->L_obj = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0);
+    c->L_res_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0);
+    c->L_grad_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, false, 0, 1);
     c->seg_list_off.push_back(0);
     for (int col = 0; col < c->ncolours; ++col) {
         std::vector<int> segs;
@@ -486,14 +608,14 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
             if (c->colour[s] == col) segs.push_back(s);
         auto &B = c->bounds;
         if (c->nslabs == 1)
-            c->L_res.push_back(make_launch(c, segs, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0));
+            c->L_res.push_back(make_launch(c, segs, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0));
         else
             c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-                *lo = std::max(0, B[s] - RZk); *hi = std::min(nz, B[s + 1] + RZk); }, false, -1));
+                *lo = std::max(0, B[s] - RZk); *hi = std::min(nz, B[s + 1] + RZk); }, false, -1, 0));
         c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) { *lo = B[s]; *hi = B[s + 1]; },
-                                        false, -1));
+                                        false, -1, 1));
         c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = std::max(0, B[s] - Lk); *hi = std::min(nz, B[s + 1] + RZk); }, true, -1));
+            *lo = std::max(0, B[s] - Lk); *hi = std::min(nz, B[s + 1] + RZk); }, true, -1, 2));
         for (int s : segs) c->seg_lists_h.push_back(s);
         c->seg_list_off.push_back((int)c->seg_lists_h.size());
     }
@@ -504,16 +626,16 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
         c->alloc = *alloc;
         c->has_alloc = true;
     }
-    ce = c->ks->prepare();
-    if (ce != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(ce)));
 
     // device allocations
-    const size_t N = (size_t)c->n;
+    c->pitch = (p.nx + 3) & ~3;
+    c->np = (size_t)c->pitch * p.ny * p.nz;
+    const size_t N = c->np;
     bd3mg_status st = BD3MG_OK;
 #define AL(ptr, cnt) if ((st = dalloc_n(c, &(ptr), (cnt)))) return bail(st)
     AL(c->x, N); AL(c->d, N); AL(c->g, N); AL(c->r, N); AL(c->y, N);
     AL(c->fx, fx.size()); AL(c->fy, fy.size()); AL(c->fz, fz.size());
-    AL(c->vols, 2); AL(c->segs, c->nslabs + 1);
+    AL(c->vols, 2); AL(c->maps, 2); AL(c->segs, c->nslabs + 1);
     AL(c->items, c->items_h.size());
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, c->seg_lists_h.size());
@@ -529,8 +651,13 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
             fail(cc, BD3MG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
             return false;
         };
-        if (!ck(cudaMemcpyAsync(c->y, y, N * 4, kin, c->stream), "copy y")) return bail(c->sticky);
-        if (!ck(cudaMemcpyAsync(c->x, x0 ? x0 : y, N * 4, kin, c->stream), "copy x0")) return bail(c->sticky);
+        const size_t wb = (size_t)p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)p.ny * p.nz;
+        if (!ck(cudaMemsetAsync(c->y, 0, N * 4, c->stream), "zero y") ||
+            !ck(cudaMemsetAsync(c->x, 0, N * 4, c->stream), "zero x"))
+            return bail(c->sticky);
+        if (!ck(cudaMemcpy2DAsync(c->y, pb, y, wb, wb, rows, kin, c->stream), "copy y")) return bail(c->sticky);
+        if (!ck(cudaMemcpy2DAsync(c->x, pb, x0 ? x0 : y, wb, wb, rows, kin, c->stream), "copy x0"))
+            return bail(c->sticky);
         if (!ck(cudaMemsetAsync(c->d, 0, N * 4, c->stream), "zero d")) return bail(c->sticky);
         if (!ck(cudaMemsetAsync(c->g, 0, N * 4, c->stream), "zero g")) return bail(c->sticky);
         if (!ck(cudaMemsetAsync(c->r, 0, N * 4, c->stream), "zero r")) return bail(c->sticky);
@@ -539,9 +666,9 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
             !ck(cudaMemcpyAsync(c->fz, fz.data(), fz.size() * 4, cudaMemcpyHostToDevice, c->stream), "copy fz"))
             return bail(c->sticky);
         VolDev v{};
-        v.nx = p.nx; v.ny = p.ny; v.nz = p.nz;
+        v.nx = p.nx; v.ny = p.ny; v.nz = p.nz; v.pitch = c->pitch;
         v.kxy = 2 * c->ks->R + 1; v.kz = 2 * c->ks->RZ + 1;
-        v.plane = (long long)p.nx * p.ny;
+        v.plane = (long long)c->pitch * p.ny;
         v.x = c->x; v.d = c->d; v.g = c->g; v.r = c->r; v.y = c->y;
         v.fx = c->fx; v.fy = c->fy; v.fz = c->fz;
         v.lam = (float)p.lambda; v.delta2 = (float)(p.delta * p.delta); v.eta2 = (float)(2.0 * p.eta);
@@ -552,7 +679,12 @@ bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x
         std::vector<SegDev> sg;
         for (int s = 0; s < c->nslabs; ++s) sg.push_back(SegDev{0, c->bounds[s], c->bounds[s + 1], s});
         sg.push_back(SegDev{0, 0, nz, c->nslabs});
-        if (!ck(cudaMemcpyAsync(c->vols, vv, sizeof(vv), cudaMemcpyHostToDevice, c->stream), "copy vols") ||
+        VolMaps vm[2];
+        if (!encode_vol_maps(&vm[0], c, c->x, c->r, c->g, c->d))
+            return bail(fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)"));
+        vm[1] = vm[0];
+        if (!ck(cudaMemcpyAsync(c->maps, vm, sizeof(vm), cudaMemcpyHostToDevice, c->stream), "copy maps") ||
+            !ck(cudaMemcpyAsync(c->vols, vv, sizeof(vv), cudaMemcpyHostToDevice, c->stream), "copy vols") ||
             !ck(cudaMemcpyAsync(c->segs, sg.data(), sizeof(SegDev) * sg.size(), cudaMemcpyHostToDevice, c->stream),
                 "copy segs"))
             return bail(c->sticky);
@@ -623,8 +755,11 @@ bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     bd3mg_status st;
     if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R | M_OBJ))) return st;
     if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
-    if (g) CK(cudaMemcpyAsync(g, c->g, (size_t)c->n * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                              c->stream));
+    if (g) {
+        const size_t wb = (size_t)c->p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)c->p.ny * c->p.nz;
+        CK(cudaMemcpy2DAsync(g, wb, c->g, pb, wb, rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+    }
     double h[4];
     CK(cudaMemcpyAsync(h, c->fout, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     if ((st = check_status(c))) return st;
@@ -632,9 +767,12 @@ bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     return BD3MG_OK;
 }
 
+// Copy between a caller volume (rows of nx floats) and a library volume (rows of pitch floats).
 static bd3mg_status copy_vol(bd3mg_ctx *c, float *dst, const float *src, int on_device, bool to_lib) {
     cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_lib ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
-    CK(cudaMemcpyAsync(dst, src, (size_t)c->n * 4, k, c->stream));
+    const size_t wb = (size_t)c->p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)c->p.ny * c->p.nz;
+    if (to_lib) CK(cudaMemcpy2DAsync(dst, pb, src, wb, wb, rows, k, c->stream));
+    else CK(cudaMemcpy2DAsync(dst, wb, src, pb, wb, rows, k, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return BD3MG_OK;
 }
@@ -654,7 +792,7 @@ bd3mg_status bd3mg_get_d(bd3mg_ctx *c, float *d, int on_device) {
 bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     GUARD(c);
     if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
-    CK(cudaMemsetAsync(c->d, 0, (size_t)c->n * 4, c->stream));
+    CK(cudaMemsetAsync(c->d, 0, c->np * 4, c->stream));
     return copy_vol(c, c->x, x, on_device, true);
 }
 
@@ -669,16 +807,27 @@ bd3mg_status bd3mg_last_step(bd3mg_ctx *c, double *info) {
 static bd3mg_status apply_op(bd3mg_ctx *c, const float *in, float *out, bool adjoint) {
     GUARD(c);
     if (!in || !out || in == out) return fail(c, BD3MG_EINVAL, "apply: in/out NULL or aliased");
+    bd3mg_status st;
+    if (!c->scr_in) {
+        if ((st = dalloc_n(c, &c->scr_in, c->np)) || (st = dalloc_n(c, &c->scr_out, c->np))) return st;
+        CK(cudaMemsetAsync(c->scr_in, 0, c->np * 4, c->stream));
+        CK(cudaMemsetAsync(c->scr_out, 0, c->np * 4, c->stream));
+    }
+    if ((st = copy_vol(c, c->scr_in, in, 1, true))) return st;
     VolDev v = c->vol_h;
     v.y = nullptr;
-    if (adjoint) { v.r = const_cast<float *>(in); v.g = out; }
-    else { v.x = const_cast<float *>(in); v.r = out; }
+    VolMaps vm;
+    bool ok;
+    if (adjoint) { v.r = c->scr_in; v.g = c->scr_out; ok = encode_vol_maps(&vm, c, nullptr, c->scr_in, nullptr, nullptr); }
+    else { v.x = c->scr_in; v.r = c->scr_out; ok = encode_vol_maps(&vm, c, c->scr_in, nullptr, nullptr, nullptr); }
+    if (!ok) return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed");
     CK(cudaMemcpyAsync(c->vols + 1, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
-    bd3mg_status st = adjoint ? run_gradient(c, c->stream, c->L_grad_full, M_HT_ONLY, c->vols + 1)
-                              : run_residual(c, c->stream, c->L_res_full, M_STORE_R, c->vols + 1);
+    CK(cudaMemcpyAsync(c->maps + 1, &vm, sizeof(vm), cudaMemcpyHostToDevice, c->stream));
+    st = adjoint ? run_gradient(c, c->stream, c->L_grad_full, M_HT_ONLY, c->vols + 1)
+                 : run_residual(c, c->stream, c->L_res_full, M_STORE_R, c->vols + 1);
     if (st) return st;
-    CK(cudaStreamSynchronize(c->stream));
-    return BD3MG_OK;
+    if ((st = copy_vol(c, out, c->scr_out, 1, false))) return st;
+    return check_status(c);
 }
 
 bd3mg_status bd3mg_apply_H(bd3mg_ctx *c, const float *in, float *out) { return apply_op(c, in, out, false); }
@@ -722,6 +871,35 @@ bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, 
         if (fz) for (int c = 0; c < pz; ++c) fz[(size_t)z * pz + c] = vz[(size_t)z * kz + c - (pz - 1) / 2 + RZ];
     }
     return BD3MG_OK;
+}
+
+bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
+    GUARD(c);
+    c->prof_on = true;
+    c->prof_ev.clear();
+    c->prof_cls.clear();
+    bd3mg_status st = enqueue_iteration(c, c->stream);
+    if (!st) st = prof_mark(c, c->stream, -1);          // closing event
+    c->prof_on = false;
+    if (st) return st;
+    c->iterations += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    double tot[BD3MG_K_CLASSES] = {0};
+    int cnt[BD3MG_K_CLASSES] = {0};
+    for (size_t k = 0; k + 1 < c->prof_ev.size(); ++k) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, c->prof_ev[k], c->prof_ev[k + 1]));
+        tot[c->prof_cls[k]] += t;
+        cnt[c->prof_cls[k]] += 1;
+    }
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    c->prof_ev.clear();
+    c->prof_cls.clear();
+    for (int k = 0; k < BD3MG_K_CLASSES; ++k) {
+        if (ms) ms[k] = tot[k];
+        if (launches) launches[k] = cnt[k];
+    }
+    return check_status(c);
 }
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {

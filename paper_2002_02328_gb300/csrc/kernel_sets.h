@@ -18,6 +18,7 @@ struct KernelSet {
     launch_fn residual, gradient, curvature;
     prep_fn prepare;               // raises the dynamic shared-memory limit
     size_t smem_residual, smem_gradient, smem_curvature;
+    int (*occupancy)(int kind);    // resident CTAs per SM of kernel kind (0 residual, 1 gradient, 2 curvature)
 };
 
 // Smallest compiled set with R' >= R and RZ' >= RZ (fewest padded taps), or null.

@@ -13,32 +13,53 @@
 //               D^T A D and D^T grad f (Eq. "maj", D = [-g_S | d_S]); the last
 //               CTA to finish sums the per-CTA partials per slab in a fixed
 //               order and solves the 2x2 system u = -B^+ c (Eq. "minimizer")
-//   k_update    x_S += D u, d_S = D u (Master box step (2))
+//   k_update    x_S += D u, d_S = D u (Master box step (2)), in update.cu
 //
 // The blur H is depth-variant with a separable PSF per OUTPUT depth z:
 // h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c).  Forward: z-combine the input slices
 // with fz of the output depth, then an x-pass and a y-pass with fx_z, fy_z.
 // Adjoint: correlate each INPUT slice zi with fx_zi, fy_zi, then z-combine
-// with fz of the input depths.  Slices are staged in shared memory as tiles of
-// TX x TY outputs plus a halo; a ring of raw slices lets each loaded slice
-// serve 2*RZ+1 output slices, so every input is read once per item.
+// with fz of the input depths.
+//
+// Data movement: every input slice of a tile (TX x TY outputs plus halo) is
+// brought into shared memory by a TMA tile copy (cp.async.bulk.tensor.3d,
+// zero fill outside the volume) into a ring of slots, PREF slices ahead of
+// use, each slot guarded by an mbarrier (bounded waits: a wait that exceeds
+// WAIT_NS sets ST_TIMEOUT and the CTA drains its copies and leaves).  Slices
+// outside the volume or the slab mask are zero-filled slots, so the consumers
+// read every tap unconditionally.  The forward z-combine reads the 2*RZ+1
+// resident slices of its window with float4 shared loads (4 halo columns per
+// unit), the x-pass is register-blocked by 4 outputs (float4 shared loads),
+// the y-pass by TY/8 outputs; two CTA barriers per slice.  The PSF factor rows
+// of an item's depth range are staged once in shared memory.  Residual and
+// gradient use 32x32 tiles; the curvature kernel, which stages two arrays,
+// uses 32x16 tiles.
+//
+// Volumes are stored with a row pitch that is a multiple of 4 floats (16-byte
+// TMA strides); padding columns stay zero and are never outputs.
 //
 // Per-voxel arithmetic is FP32; per-thread partial sums are FP32 over at most
-// 2*zchunk terms; CTA and global sums are FP64 in a fixed order (bitwise
+// TY/8*zchunk terms; CTA and global sums are FP64 in a fixed order (bitwise
 // deterministic run to run).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace bd3mg {
 
 constexpr int TX = 32;            // tile width  (x, one warp lane per column)
-constexpr int TY = 16;            // tile height (y)
+constexpr int TY_A = 32;          // tile height of k_residual / k_gradient
+constexpr int TY_C = 16;          // tile height of k_curvature
 constexpr int NT = 256;           // threads per CTA
 constexpr int NWARP = NT / 32;
-constexpr int RPW = TY / NWARP;   // output rows per warp
-constexpr int XW = TX + 2;        // x-tile (1-voxel halo) row pitch
-constexpr int XSZ = XW * (TY + 2);
+constexpr int PREF = 2;           // slices in flight ahead of the consumer (>= 2, see Pipe)
+constexpr int ZC_MAX = 48;        // max output slices per work item
+constexpr int XH1 = 4;            // x halo of the 1-voxel-halo x tiles (rounded to 4 floats)
+constexpr int BX1 = TX + 2 * XH1;
+constexpr int NSX = PREF + 3;     // slots of the 1-halo x pipeline
+
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier wait (2 s)
 
 // Modes
 constexpr int M_STORE_R = 1;      // k_residual: store r
@@ -49,16 +70,25 @@ constexpr int M_HT_ONLY = 16;     // k_gradient: output H^T r only
 
 // Status bits (device word)
 constexpr int ST_NONFINITE = 1;
+constexpr int ST_TIMEOUT = 2;
 
 struct VolDev {
-    int nx, ny, nz, kxy, kz;      // kxy = 2R+1, kz = 2RZ+1 (factor rows, zero padded)
-    long long plane;              // nx*ny
+    int nx, ny, nz, pitch;        // pitch: row stride in floats (multiple of 4)
+    int kxy, kz;                  // factor row lengths 2R+1, 2RZ+1 (zero padded)
+    long long plane;              // pitch*ny
     float *x, *d, *g, *r;
     const float *y;               // null -> 0
     const float *fx, *fy, *fz;    // [nz][kxy], [nz][kxy], [nz][kz]
     float lam, delta2, eta2, xmin, xmax;
     double lam_d, eta_d;
 };
+
+// TMA descriptors of one volume (global memory, 64-byte aligned).
+//   X_R: x, halo R, 32-row tiles (k_residual)    R_R: r, halo R, 32-row tiles (k_gradient)
+//   X_1A: x, halo 1, 32-row tiles (k_gradient)   G_R, D_R: g, d, halo R, 16-row tiles (k_curvature)
+//   X_1C: x, halo 1, 16-row tiles (k_curvature)
+enum { TM_X_R = 0, TM_R_R = 1, TM_X_1A = 2, TM_G_R = 3, TM_D_R = 4, TM_X_1C = 5, TM_COUNT = 6 };
+struct VolMaps { CUtensorMap m[TM_COUNT]; };
 
 struct SegDev { int vol, z0, z1, slot; };
 struct Item { int seg, tx0, ty0, zo0, zo1; };
@@ -73,6 +103,7 @@ struct Shared {                   // device-resident context words (graph-stable
 
 struct KArgs {
     const VolDev *vols;
+    const VolMaps *maps;
     const SegDev *segs;
     const Item *items;
     int nitems;
@@ -89,37 +120,187 @@ struct KArgs {
     double pinv_rtol;
 };
 
-template <int R, int RZ>
+template <int R, int RZ, int TY>
 struct Geo {
-    static constexpr int RH = R > 1 ? R : 1;          // halo of staged slices (>= 1 for V)
-    static constexpr int HW = TX + 2 * RH;
-    static constexpr int HH = TY + 2 * RH;
-    static constexpr int HC = HW * HH;
-    static constexpr int L = RZ > 1 ? RZ : 1;         // look-ahead (>= 1 for V^Z)
-    static constexpr int NRING = RZ + L + 1;          // raw slices zo-RZ .. zo+L
+    static constexpr int RPW = TY / NWARP;            // y-pass outputs per thread
+    static constexpr int XH = R <= 4 ? 4 : 8;         // staged x halo (>= R, multiple of 4)
+    static constexpr int BX = TX + 2 * XH;            // staged tile width (TMA box x)
+    static constexpr int BY = TY + 2 * R;             // staged tile height (TMA box y)
+    static constexpr int SLOT = ((BX * BY + 31) / 32) * 32;
+    static constexpr int BY1 = TY + 2;                // 1-halo x tile height
+    static constexpr int SLOT1 = ((BX1 * BY1 + 31) / 32) * 32;
+    static constexpr int ZUNITS = BY * (BX / 4);      // z-combine units of 4 staged columns
     static constexpr int KXY = 2 * R + 1;
     static constexpr int KZ = 2 * RZ + 1;
-    static constexpr size_t smem_residual = sizeof(float) * (NRING * HC + HC + HH * TX);
-    static constexpr size_t smem_gradient = sizeof(float) * (HC + HH * TX + KZ * TY * TX + 3 * XSZ);
-    static constexpr size_t smem_curvature = sizeof(float) * (2 * NRING * HC + 2 * HC + 2 * HH * TX + 2 * XSZ);
+    static constexpr int NSF = PREF + KZ;             // forward pipelines: the whole z window stays resident
+    static constexpr int NSA = PREF + 1;              // adjoint r pipeline
+    // x-pass register blocking: outputs x0..x0+3 read staged columns
+    // [x0+XH-R, x0+XH+3+R]; loaded as XNV float4 from x0+XA0.
+    static constexpr int XA0 = (XH - R) & ~3;
+    static constexpr int XNV = (XH + 3 + R - XA0) / 4 + 1;
+    static constexpr int XUNITS = BY * (TX / 4);
+    // staged PSF factor rows: [fx (KXYP) | fy (KXYP) | fz (KZP)] per slice of the item range
+    static constexpr int KXYP = (KXY + 3) & ~3;
+    static constexpr int KZP = (KZ + 3) & ~3;
+    static constexpr int CFS = 2 * KXYP + KZP;
+    static constexpr int CF_ROWS = ZC_MAX + 2 * RZ;
+    static constexpr int CF_FLOATS = ((CF_ROWS * CFS + 31) / 32) * 32;
+    static constexpr size_t bars_bytes(int n) { return ((n * 8 + 127) / 128) * 128; }
 };
 
-__device__ __forceinline__ int ring_slot(int z, int n) { return (z + 64 * n) % n; }
+template <int R, int RZ>
+struct Smem {
+    using A = Geo<R, RZ, TY_A>;
+    using C = Geo<R, RZ, TY_C>;
+    static constexpr size_t residual =
+        sizeof(float) * (A::NSF * A::SLOT + A::BY * A::BX + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::NSF);
+    static constexpr size_t gradient =
+        sizeof(float) * (A::NSA * A::SLOT + NSX * A::SLOT1 + A::BY * TX + A::CF_FLOATS) +
+        A::bars_bytes(A::NSA + NSX);
+    static constexpr size_t curvature =
+        sizeof(float) * (2 * C::NSF * C::SLOT + NSX * C::SLOT1 + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
+        C::bars_bytes(2 * C::NSF + NSX);
+};
 
-// Stage slice z of src (tile origin tx0,ty0, halo rh) into dst[hh][hw];
-// zero outside the volume and outside the slice mask [zlo, zhi).
-template <int HW, int HH>
-__device__ __forceinline__ void stage_slice(float *dst, const float *__restrict__ src, const VolDev &v,
-                                            int tx0, int ty0, int rh, int z, int zlo, int zhi) {
-    const bool zin = z >= zlo && z < zhi && z >= 0 && z < v.nz;
-    const float *base = src + (long long)(zin ? z : 0) * v.plane;
-    for (int i = threadIdx.x; i < HW * HH; i += NT) {
-        const int hy = i / HW, hx = i - hy * HW;
-        const int gx = tx0 - rh + hx, gy = ty0 - rh + hy;
-        float val = 0.f;
-        if (zin && gx >= 0 && gx < v.nx && gy >= 0 && gy < v.ny) val = __ldg(base + (long long)gy * v.nx + gx);
-        dst[i] = val;
+// ---------------------------------------------------------------------------
+// mbarrier / TMA primitives (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity; false after WAIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - t0 > WAIT_NS) return false;
+        __nanosleep(64);
     }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// A ring of NS shared-memory slots fed by TMA slice copies.  Slice z lives in
+// slot (z - first) mod NS.  Counters and parity bits are uniform across the
+// CTA; thread 0 issues the copies.  Slices outside [zlo, zhi) are zero-filled
+// by all threads when issued; with PREF >= 2 a CTA barrier always separates
+// that fill from the first read of the slot.
+template <int NS, int SLOTF>
+struct Pipe {
+    float *buf;
+    uint64_t *bar;
+    const CUtensorMap *map;
+    int x0, y0;                   // box origin (x0 is a multiple of 4)
+    int zlo, zhi;                 // slices [zlo, zhi) are copied; others are zero-filled
+    int first;                    // slice in slot 0
+    uint32_t bytes;               // bytes per copy (box size)
+    int fill;                     // floats to zero-fill per slot
+    uint32_t par;
+    int next_issue, next_wait, issue_slot, wait_slot;
+
+    __device__ void init(float *b, uint64_t *br, const CUtensorMap *m, int bx0, int by0, int lo, int hi,
+                         uint32_t nbytes, int first_slice) {
+        buf = b;
+        bar = br;
+        map = m;
+        x0 = bx0;
+        y0 = by0;
+        zlo = lo;
+        zhi = hi;
+        first = first_slice;
+        bytes = nbytes;
+        fill = (int)(nbytes / 4);
+        par = 0u;
+        next_issue = next_wait = first_slice;
+        issue_slot = wait_slot = 0;
+    }
+    __device__ __forceinline__ bool loaded(int z) const { return z >= zlo && z < zhi; }
+    __device__ __forceinline__ int slot(int z) const { return (z - first) % NS; }
+    __device__ __forceinline__ const float *at(int z) const { return buf + slot(z) * SLOTF; }
+    // slot of slice z - back when s is the slot of z (0 <= back < NS)
+    __device__ __forceinline__ static int back_slot(int s, int back) {
+        const int t = s - back;
+        return t < 0 ? t + NS : t;
+    }
+    // All threads call; issues (or zero-fills) every slice in [next_issue, upto].
+    __device__ void issue_upto(int upto) {
+        for (; next_issue <= upto; ++next_issue) {
+            const int s = issue_slot;
+            issue_slot = (s + 1 == NS) ? 0 : s + 1;
+            if (loaded(next_issue)) {
+                if (threadIdx.x == 0) {
+                    uint64_t *b = bar + s;
+                    mbar_expect_tx(b, bytes);
+                    tma_load_3d(buf + s * SLOTF, map, x0, y0, next_issue, b);
+                }
+            } else {
+                float4 *d = reinterpret_cast<float4 *>(buf + s * SLOTF);
+                for (int i = threadIdx.x; i < fill / 4; i += NT) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    // All threads call; waits for every copied slice in [next_wait, upto]; false on timeout.
+    __device__ bool wait_upto(int upto) {
+        bool ok = true;
+        for (; next_wait <= upto; ++next_wait) {
+            const int s = wait_slot;
+            wait_slot = (s + 1 == NS) ? 0 : s + 1;
+            if (loaded(next_wait)) {
+                ok = mbar_wait(bar + s, (par >> s) & 1u) && ok;
+                par ^= 1u << s;
+            }
+        }
+        return ok;
+    }
+    // Bounded wait for every copy issued and not yet consumed (used before leaving early).
+    __device__ void drain() { wait_upto(next_issue - 1); }
+};
+
+// Initialise n mbarriers (count 1).  Returns false (all threads) if the
+// dynamic shared memory is not 128-byte aligned, which TMA destinations need.
+__device__ __forceinline__ bool init_bars(uint64_t *bar, int n, const void *smem_base, int *status) {
+    if (smem_u32(smem_base) & 127u) {
+        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        return false;
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) mbar_init(bar + i, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    return true;
 }
 
 // FP64 CTA reduction of NP per-thread FP32 partials into partials[blockIdx.x],
@@ -201,89 +382,203 @@ __device__ __forceinline__ int solve2x2_pinv(double b00, double b01, double b11,
 }
 
 // ---------------------------------------------------------------------------
+// Shared building blocks of the tile kernels
+// ---------------------------------------------------------------------------
+
+// Stage the PSF factor rows of slices [z0, z0 + rows) into CF (zero outside the volume).
+template <class G>
+__device__ __forceinline__ void stage_coeffs(float *CF, const VolDev &V, int z0, int rows) {
+    for (int i = threadIdx.x; i < rows * G::CFS; i += NT) {
+        const int row = i / G::CFS, c = i - row * G::CFS, z = z0 + row;
+        float v = 0.f;
+        if (z >= 0 && z < V.nz) {
+            if (c < G::KXY) v = __ldg(V.fx + (long long)z * V.kxy + c);
+            else if (c >= G::KXYP && c < G::KXYP + G::KXY) v = __ldg(V.fy + (long long)z * V.kxy + c - G::KXYP);
+            else if (c >= 2 * G::KXYP && c < 2 * G::KXYP + G::KZ) v = __ldg(V.fz + (long long)z * V.kz + c - 2 * G::KXYP);
+        }
+        CF[i] = v;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void row_coeffs(float (&c)[N], const float *p) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) c[i] = p[i];
+}
+
+// Forward z-combine of one unit (4 staged columns of one row) for the output
+// whose newest input slice sits in slot s:  W = sum_t fz[t] * v(zi - t).
+template <class G, int NS, int SLOTF>
+__device__ __forceinline__ void zcomb_unit(const Pipe<NS, SLOTF> &p, int s, int u, const float (&fzc)[G::KZ],
+                                           float *W) {
+    const int off = u * 4;                     // units tile the staged rows exactly (BX % 4 == 0)
+    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+#pragma unroll
+    for (int t = 0; t < G::KZ; ++t) {
+        const float4 v = *reinterpret_cast<const float4 *>(p.buf + Pipe<NS, SLOTF>::back_slot(s, t) * SLOTF + off);
+        float4 &a = (t & 1) ? acc1 : acc0;
+        a.x = fmaf(fzc[t], v.x, a.x);
+        a.y = fmaf(fzc[t], v.y, a.y);
+        a.z = fmaf(fzc[t], v.z, a.z);
+        a.w = fmaf(fzc[t], v.w, a.w);
+    }
+    *reinterpret_cast<float4 *>(W + off) =
+        make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
+}
+
+// x-pass over staged rows: T1[row][x] = sum_a fx[a+R] * S[row][x + XH + SGN*a]
+// (SGN = -1: convolution for H; SGN = +1: correlation for H^T), 4 outputs per unit.
+template <class G, int R, int SGN>
+__device__ __forceinline__ void xpass_unit(const float *S, float *T1, int u, const float (&fxc)[2 * R + 1]) {
+    const int row = u / (TX / 4), x0 = (u - row * (TX / 4)) * 4;
+    const float4 *sp = reinterpret_cast<const float4 *>(S + row * G::BX + x0 + G::XA0);
+    float w[4 * G::XNV];
+#pragma unroll
+    for (int v = 0; v < G::XNV; ++v) {
+        const float4 q = sp[v];
+        w[4 * v] = q.x;
+        w[4 * v + 1] = q.y;
+        w[4 * v + 2] = q.z;
+        w[4 * v + 3] = q.w;
+    }
+    float o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int a = -R; a <= R; a += 2) s0 = fmaf(fxc[a + R], w[i + SGN * a + G::XH - G::XA0], s0);
+#pragma unroll
+        for (int a = -R + 1; a <= R; a += 2) s1 = fmaf(fxc[a + R], w[i + SGN * a + G::XH - G::XA0], s1);
+        o[i] = s0 + s1;
+    }
+    *reinterpret_cast<float4 *>(T1 + row * TX + x0) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+// y-pass for this thread's RPW outputs (column lane, rows y0..y0+RPW-1):
+// out[k] = sum_b fy[b+R] * T1[y0 + k + R + SGN*b][lane].
+template <int R, int RPW, int SGN>
+__device__ __forceinline__ void ypass(const float *T1, int y0, int lane, const float (&fyc)[2 * R + 1],
+                                      float (&out)[RPW]) {
+    float t[RPW + 2 * R];
+#pragma unroll
+    for (int j = 0; j < RPW + 2 * R; ++j) t[j] = T1[(y0 + j) * TX + lane];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int b = -R; b <= R; b += 2) s0 = fmaf(fyc[b + R], t[k + R + SGN * b], s0);
+#pragma unroll
+        for (int b = -R + 1; b <= R; b += 2) s1 = fmaf(fyc[b + R], t[k + R + SGN * b], s1);
+        out[k] = s0 + s1;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ).
 // ---------------------------------------------------------------------------
 template <int R, int RZ>
-__global__ void __launch_bounds__(NT) k_residual(KArgs a) {
-    using G = Geo<R, RZ>;
-    extern __shared__ __align__(16) float smem[];
-    float *ring = smem;
-    float *W = ring + G::NRING * G::HC;
-    float *T1 = W + G::HC;
-    __shared__ float cf[3][G::KXY > G::KZ ? G::KXY : G::KZ];
+__global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
+    using G = Geo<R, RZ, TY_A>;
+    constexpr int RPW = G::RPW;
+    extern __shared__ __align__(128) float smem[];
+    float *stg = smem;
+    float *W = stg + G::NSF * G::SLOT;
+    float *T1 = W + G::BY * G::BX;
+    float *CF = T1 + G::BY * TX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
     const SegDev sg = a.segs[it.seg];
-    const VolDev v = a.vols[sg.vol];
+    const VolDev &V = a.vols[sg.vol];
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane;
+    const float *yp = V.y;
+    float *rp = V.r;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool store_r = (a.mode & M_STORE_R) != 0;
     const bool obj = (a.mode & M_OBJ) != 0;
-    float acc[3] = {0.f, 0.f, 0.f};
 
-    for (int zi = it.zo0 - RZ; zi <= it.zo1 - 1 + G::L; ++zi) {
-        stage_slice<G::HW, G::HH>(ring + ring_slot(zi, G::NRING) * G::HC, v.x, v, it.tx0, it.ty0, G::RH, zi, 0, v.nz);
-        const int zo = zi - G::L;
-        if (zo < it.zo0) continue;
-        if (tid < G::KXY) {
-            cf[0][tid] = v.fx[(long long)zo * v.kxy + tid];
-            cf[1][tid] = v.fy[(long long)zo * v.kxy + tid];
-        }
-        if (tid < G::KZ) cf[2][tid] = v.fz[(long long)zo * v.kz + tid];
-        __syncthreads();
-        for (int i = tid; i < G::HC; i += NT) {
-            float s = 0.f;
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    if (!init_bars(bar, G::NSF, smem, a.sh->status)) return;
+    Pipe<G::NSF, G::SLOT> px;
+    px.init(stg, bar, &a.maps[sg.vol].m[TM_X_R], it.tx0 - G::XH, it.ty0 - R, max(0, zbeg), min(nz, zend),
+            (uint32_t)(G::BX * G::BY * sizeof(float)), zbeg);
+    px.issue_upto(zbeg + PREF - 1);
+    __syncthreads();
+
+    float acc[3] = {0.f, 0.f, 0.f};
+    const int y0 = warp * RPW;
+    const int gx = it.tx0 + lane;
+    const bool colin = gx < nx;
+
+    for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
+        const bool ok = px.wait_upto(zi);
+        const int zo = zi - RZ;
+        const bool emit = zo >= it.zo0;
+        const float *cfr = CF + (zo - zbeg) * G::CFS;
+        float yv[RPW];
+        if (emit) {
+            // observation values of this thread's outputs, fetched early to hide latency
 #pragma unroll
-            for (int c = -RZ; c <= RZ; ++c) s = fmaf(cf[2][c + RZ], ring[ring_slot(zo - c, G::NRING) * G::HC + i], s);
-            W[i] = s;
+            for (int k = 0; k < RPW; ++k) {
+                const int gy = it.ty0 + y0 + k;
+                yv[k] = (yp && colin && gy < ny) ? __ldg(yp + (long long)zo * plane + (long long)gy * pitch + gx) : 0.f;
+            }
+            float fzc[G::KZ];
+            row_coeffs(fzc, cfr + 2 * G::KXYP);
+            for (int u = tid; u < G::ZUNITS; u += NT) zcomb_unit<G>(px, s, u, fzc, W);
+        }
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) { px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
+            return;
+        }
+        px.issue_upto(zi + PREF);
+        if (!emit) continue;
+        {
+            float fxc[G::KXY];
+            row_coeffs(fxc, cfr);
+            for (int u = tid; u < G::XUNITS; u += NT) xpass_unit<G, R, -1>(W, T1, u, fxc);
         }
         __syncthreads();
-        for (int i = tid; i < G::HH * TX; i += NT) {
-            const int hy = i / TX, xo = i - hy * TX;
-            const float *w = W + hy * G::HW + xo + G::RH;
-            float s = 0.f;
-#pragma unroll
-            for (int aa = -R; aa <= R; ++aa) s = fmaf(cf[0][aa + R], w[-aa], s);
-            T1[i] = s;
-        }
-        __syncthreads();
+        float fyc[G::KXY];
+        row_coeffs(fyc, cfr + G::KXYP);
+        float hx[RPW];
+        ypass<R, RPW, -1>(T1, y0, lane, fyc, hx);
+        const float *xz = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ) * G::SLOT;       // slice zo
+        const float *xz1 = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ - 1) * G::SLOT;  // slice zo+1
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
-            const int yo = warp * RPW + k, xo = lane;
-            const float *t = T1 + (yo + G::RH) * TX + xo;
-            float s = 0.f;
-#pragma unroll
-            for (int b = -R; b <= R; ++b) s = fmaf(cf[1][b + R], t[-b * TX], s);
-            const int gx = it.tx0 + xo, gy = it.ty0 + yo;
-            if (gx < v.nx && gy < v.ny) {
-                const long long n = (long long)zo * v.plane + (long long)gy * v.nx + gx;
-                const float rr = s - (v.y ? __ldg(v.y + n) : 0.f);
-                if (store_r) v.r[n] = rr;
+            const int yo = y0 + k, gy = it.ty0 + yo;
+            if (colin && gy < ny) {
+                const long long n = (long long)zo * plane + (long long)gy * pitch + gx;
+                const float rr = hx[k] - yv[k];
+                if (store_r) rp[n] = rr;
                 if (obj) {
-                    const int ci = (yo + G::RH) * G::HW + xo + G::RH;
-                    const float *xr = ring + ring_slot(zo, G::NRING) * G::HC + ci;
-                    const float xc = xr[0];
+                    const int ci = (yo + R) * G::BX + lane + G::XH;
+                    const float xc = xz[ci];
                     acc[0] = fmaf(0.5f * rr, rr, acc[0]);
-                    const float dist = xc - fminf(fmaxf(xc, v.xmin), v.xmax);
+                    const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
                     acc[1] = fmaf(dist, dist, acc[1]);
-                    const float tx = gx < v.nx - 1 ? xr[1] - xc : 0.f;
-                    const float ty = gy < v.ny - 1 ? xr[G::HW] - xc : 0.f;
-                    const float tz = zo < v.nz - 1 ? ring[ring_slot(zo + 1, G::NRING) * G::HC + ci] - xc : 0.f;
-                    acc[2] += sqrtf(fmaf(tx, tx, v.delta2)) + sqrtf(fmaf(ty, ty, v.delta2)) + sqrtf(fmaf(tz, tz, v.delta2));
+                    const float tx = gx < nx - 1 ? xz[ci + 1] - xc : 0.f;
+                    const float ty = gy < ny - 1 ? xz[ci + G::BX] - xc : 0.f;
+                    const float tz = zo < nz - 1 ? xz1[ci] - xc : 0.f;
+                    acc[2] += sqrtf(fmaf(tx, tx, delta2)) + sqrtf(fmaf(ty, ty, delta2)) + sqrtf(fmaf(tz, tz, delta2));
                 }
             }
         }
-        __syncthreads();
     }
     if (!obj) return;
     if (!publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) return;
     // Last CTA: objective per volume slot, trace, counter.
     __shared__ double tot[3];
     const int k = *a.sh->counter;
-    for (int s = 0; s < a.nslots; ++s) {
-        sum_slot<3>(a.partials, a.slot_beg[s], a.slot_beg[s + 1], tot);
+    for (int sl = 0; sl < a.nslots; ++sl) {
+        sum_slot<3>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
         if (tid == 0) {
-            const int vid = a.slot_id[s];
-            const VolDev vv = a.vols[vid];
+            const int vid = a.slot_id[sl];
+            const VolDev &vv = a.vols[vid];
             const double f1 = tot[0], f2 = vv.eta_d * tot[1], f3 = vv.lam_d * tot[2];
             const double f = f1 + f2 + f3;
             a.fout[vid * 4 + 0] = f;
@@ -306,92 +601,118 @@ __global__ void __launch_bounds__(NT) k_residual(KArgs a) {
 // slabs' own slices.
 // ---------------------------------------------------------------------------
 template <int R, int RZ>
-__global__ void __launch_bounds__(NT) k_gradient(KArgs a) {
-    using G = Geo<R, RZ>;
-    extern __shared__ __align__(16) float smem[];
-    float *RB = smem;
-    float *T1 = RB + G::HC;
-    float *U = T1 + G::HH * TX;                 // [KZ][TY*TX]
-    float *XS = U + G::KZ * TY * TX;            // [3][XSZ]
-    __shared__ float cf[2][G::KXY];
+__global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
+    using G = Geo<R, RZ, TY_A>;
+    constexpr int RPW = G::RPW;
+    extern __shared__ __align__(128) float smem[];
+    float *stg = smem;                                   // NSA * SLOT (r)
+    float *xs = stg + G::NSA * G::SLOT;                  // NSX * SLOT1 (x, 1-voxel halo)
+    float *T1 = xs + NSX * G::SLOT1;
+    float *CF = T1 + G::BY * TX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
     const SegDev sg = a.segs[it.seg];
-    const VolDev v = a.vols[sg.vol];
+    const VolDev &V = a.vols[sg.vol];
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane;
+    float *gp = V.g;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool full = (a.mode & M_HT_ONLY) == 0;
 
-    if (full) {
-        stage_slice<XW, TY + 2>(XS + ring_slot(it.zo0 - 1, 3) * XSZ, v.x, v, it.tx0, it.ty0, 1, it.zo0 - 1, 0, v.nz);
-        stage_slice<XW, TY + 2>(XS + ring_slot(it.zo0, 3) * XSZ, v.x, v, it.tx0, it.ty0, 1, it.zo0, 0, v.nz);
-    }
-    for (int zi = it.zo0 - RZ; zi <= it.zo1 - 1 + RZ; ++zi) {
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    if (!init_bars(bar, G::NSA + NSX, smem, a.sh->status)) return;
+    Pipe<G::NSA, G::SLOT> pr;
+    pr.init(stg, bar, &a.maps[sg.vol].m[TM_R_R], it.tx0 - G::XH, it.ty0 - R, max(0, zbeg), min(nz, zend),
+            (uint32_t)(G::BX * G::BY * sizeof(float)), zbeg);
+    Pipe<NSX, G::SLOT1> px;
+    px.init(xs, bar + G::NSA, &a.maps[sg.vol].m[TM_X_1A], it.tx0 - XH1, it.ty0 - 1, max(0, it.zo0 - 1),
+            min(nz, it.zo1 + 1), (uint32_t)(BX1 * G::BY1 * sizeof(float)), it.zo0 - 1);
+    pr.issue_upto(zbeg + PREF - 1);
+    if (full) px.issue_upto(zbeg - RZ + PREF);
+    __syncthreads();
+
+    // uring[k][j]: u of slice zi - (KZ-1) + j for this thread's outputs (j = KZ-1 newest)
+    float uring[RPW][G::KZ];
+#pragma unroll
+    for (int k = 0; k < RPW; ++k)
+#pragma unroll
+        for (int j = 0; j < G::KZ; ++j) uring[k][j] = 0.f;
+    const int y0 = warp * RPW;
+    const int gx = it.tx0 + lane;
+    const bool colin = gx < nx;
+
+    for (int zi = zbeg; zi < zend; ++zi) {
         const int zo = zi - RZ;
         const bool emit = zo >= it.zo0;
-        stage_slice<G::HW, G::HH>(RB, v.r, v, it.tx0, it.ty0, G::RH, zi, 0, v.nz);
-        if (emit && full)
-            stage_slice<XW, TY + 2>(XS + ring_slot(zo + 1, 3) * XSZ, v.x, v, it.tx0, it.ty0, 1, zo + 1, 0, v.nz);
-        if (tid < G::KXY) {
-            const bool zin = zi >= 0 && zi < v.nz;
-            cf[0][tid] = zin ? v.fx[(long long)zi * v.kxy + tid] : 0.f;
-            cf[1][tid] = zin ? v.fy[(long long)zi * v.kxy + tid] : 0.f;
+        bool ok = pr.wait_upto(zi);
+        if (full) ok = px.wait_upto(zo + 1) && ok;
+        const bool ld = pr.loaded(zi);
+        const float *cfi = CF + (zi - zbeg) * G::CFS;
+        if (ld) {
+            float fxc[G::KXY];
+            row_coeffs(fxc, cfi);
+            const float *src = pr.at(zi);
+            for (int u = tid; u < G::XUNITS; u += NT) xpass_unit<G, R, +1>(src, T1, u, fxc);
         }
-        __syncthreads();
-        for (int i = tid; i < G::HH * TX; i += NT) {
-            const int hy = i / TX, xo = i - hy * TX;
-            const float *w = RB + hy * G::HW + xo + G::RH;
-            float s = 0.f;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) { pr.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
+            return;
+        }
+        pr.issue_upto(zi + PREF);
+        if (full) px.issue_upto(zo + 1 + PREF);
+        float u[RPW];
+        if (ld) {
+            float fyc[G::KXY];
+            row_coeffs(fyc, cfi + G::KXYP);
+            ypass<R, RPW, +1>(T1, y0, lane, fyc, u);
+        } else {
 #pragma unroll
-            for (int aa = -R; aa <= R; ++aa) s = fmaf(cf[0][aa + R], w[aa], s);
-            T1[i] = s;
+            for (int k = 0; k < RPW; ++k) u[k] = 0.f;
         }
-        __syncthreads();
-        float *Uz = U + ring_slot(zi, G::KZ) * (TY * TX);
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
-            const int yo = warp * RPW + k, xo = lane;
-            const float *t = T1 + (yo + G::RH) * TX + xo;
-            float s = 0.f;
 #pragma unroll
-            for (int b = -R; b <= R; ++b) s = fmaf(cf[1][b + R], t[b * TX], s);
-            Uz[yo * TX + xo] = s;          // read back only by this thread
+            for (int j = 0; j < G::KZ - 1; ++j) uring[k][j] = uring[k][j + 1];
+            uring[k][G::KZ - 1] = u[k];
         }
         if (emit) {
+            // q(zo) = sum_c fz_{zo+c}[c+RZ] u(zo+c), u(zo+c) in uring[.][c+RZ]
+            float fzc[G::KZ];
+#pragma unroll
+            for (int t = 0; t < G::KZ; ++t) fzc[t] = CF[(zo + t - RZ - zbeg) * G::CFS + 2 * G::KXYP + t];
+            const float *xm = full ? px.at(zo - 1) : nullptr;
+            const float *x0p = full ? px.at(zo) : nullptr;
+            const float *xp1 = full ? px.at(zo + 1) : nullptr;
 #pragma unroll
             for (int k = 0; k < RPW; ++k) {
-                const int yo = warp * RPW + k, xo = lane;
-                float q = 0.f;
+                float q0 = 0.f, q1 = 0.f;
 #pragma unroll
-                for (int c = -RZ; c <= RZ; ++c) {
-                    const int zs = zo + c;
-                    if (zs >= 0 && zs < v.nz)
-                        q = fmaf(__ldg(v.fz + (long long)zs * v.kz + c + RZ), U[ring_slot(zs, G::KZ) * (TY * TX) + yo * TX + xo], q);
-                }
-                const int gx = it.tx0 + xo, gy = it.ty0 + yo;
-                if (gx < v.nx && gy < v.ny) {
-                    const long long n = (long long)zo * v.plane + (long long)gy * v.nx + gx;
+                for (int t = 0; t < G::KZ; t += 2) q0 = fmaf(fzc[t], uring[k][t], q0);
+#pragma unroll
+                for (int t = 1; t < G::KZ; t += 2) q1 = fmaf(fzc[t], uring[k][t], q1);
+                const float q = q0 + q1;
+                const int yo = y0 + k, gy = it.ty0 + yo;
+                if (colin && gy < ny) {
+                    const long long n = (long long)zo * plane + (long long)gy * pitch + gx;
                     float gval = q;
                     if (full) {
-                        const int ci = (yo + 1) * XW + xo + 1;
-                        const float *x0 = XS + ring_slot(zo, 3) * XSZ + ci;
+                        const int ci = (yo + 1) * BX1 + lane + XH1;
+                        const float *x0 = x0p + ci;
                         const float xc = x0[0];
                         float pen = 0.f;
-                        if (gx >= 1) { const float t = xc - x0[-1]; pen += t * rsqrtf(fmaf(t, t, v.delta2)); }
-                        if (gx < v.nx - 1) { const float t = x0[1] - xc; pen -= t * rsqrtf(fmaf(t, t, v.delta2)); }
-                        if (gy >= 1) { const float t = xc - x0[-XW]; pen += t * rsqrtf(fmaf(t, t, v.delta2)); }
-                        if (gy < v.ny - 1) { const float t = x0[XW] - xc; pen -= t * rsqrtf(fmaf(t, t, v.delta2)); }
-                        if (zo >= 1) {
-                            const float t = xc - XS[ring_slot(zo - 1, 3) * XSZ + ci];
-                            pen += t * rsqrtf(fmaf(t, t, v.delta2));
-                        }
-                        if (zo < v.nz - 1) {
-                            const float t = XS[ring_slot(zo + 1, 3) * XSZ + ci] - xc;
-                            pen -= t * rsqrtf(fmaf(t, t, v.delta2));
-                        }
-                        const float dist = xc - fminf(fmaxf(xc, v.xmin), v.xmax);
-                        gval = fmaf(v.lam, pen, fmaf(v.eta2, dist, q));
+                        if (gx >= 1) { const float t = xc - x0[-1]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
+                        if (gx < nx - 1) { const float t = x0[1] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
+                        if (gy >= 1) { const float t = xc - x0[-BX1]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
+                        if (gy < ny - 1) { const float t = x0[BX1] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
+                        if (zo >= 1) { const float t = xc - xm[ci]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
+                        if (zo < nz - 1) { const float t = xp1[ci] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
+                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+                        gval = fmaf(lam, pen, fmaf(eta2, dist, q));
                     }
-                    v.g[n] = gval;
+                    gp[n] = gval;
                 }
             }
         }
@@ -404,121 +725,132 @@ __global__ void __launch_bounds__(NT) k_gradient(KArgs a) {
 // the last CTA, the per-slab 2x2 solve.
 //   acc: 0 g.g  1 g.d  2 d.d  3 Hg.Hg  4 Hg.Hd  5 Hd.Hd
 //        6 sum w (Vg)^2  7 sum w Vg Vd  8 sum w (Vd)^2
-// g_S, d_S are g, d masked to the slab's slices [z0, z1).
+// g_S, d_S are g, d masked to the slab's slices [z0, z1) (zero-filled slots).
 // ---------------------------------------------------------------------------
 template <int R, int RZ>
-__global__ void __launch_bounds__(NT) k_curvature(KArgs a) {
-    using G = Geo<R, RZ>;
-    extern __shared__ __align__(16) float smem[];
-    float *ringG = smem;
-    float *ringD = ringG + G::NRING * G::HC;
-    float *Wg = ringD + G::NRING * G::HC;
-    float *Wd = Wg + G::HC;
-    float *T1g = Wd + G::HC;
-    float *T1d = T1g + G::HH * TX;
-    float *XS = T1d + G::HH * TX;               // [2][XSZ]
-    __shared__ float cf[3][G::KXY > G::KZ ? G::KXY : G::KZ];
+__global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
+    using G = Geo<R, RZ, TY_C>;
+    constexpr int RPW = G::RPW;
+    extern __shared__ __align__(128) float smem[];
+    float *sgs = smem;                                   // NSF * SLOT (g)
+    float *sds = sgs + G::NSF * G::SLOT;                 // NSF * SLOT (d)
+    float *xs = sds + G::NSF * G::SLOT;                  // NSX * SLOT1 (x)
+    float *Wg = xs + NSX * G::SLOT1;
+    float *Wd = Wg + G::BY * G::BX;
+    float *T1g = Wd + G::BY * G::BX;
+    float *T1d = T1g + G::BY * TX;
+    float *CF = T1d + G::BY * TX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
     const SegDev sg = a.segs[it.seg];
-    const VolDev v = a.vols[sg.vol];
+    const VolDev &V = a.vols[sg.vol];
+    const int nx = V.nx, ny = V.ny, nz = V.nz;
+    const float delta2 = V.delta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
+
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    if (!init_bars(bar, 2 * G::NSF + NSX, smem, a.sh->status)) return;
+    const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
+    const uint32_t nb = (uint32_t)(G::BX * G::BY * sizeof(float));
+    Pipe<G::NSF, G::SLOT> pg, pd;
+    pg.init(sgs, bar, &a.maps[sg.vol].m[TM_G_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
+    pd.init(sds, bar + G::NSF, &a.maps[sg.vol].m[TM_D_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
+    // x slices for the penalty at outputs zo in [max(zo0, pen_lo), min(zo1, pen_hi)): x(zo), x(zo+1)
+    const int xfirst = max(it.zo0, pen_lo);
+    const int xlo = max(0, xfirst), xhi = min(nz, min(it.zo1, pen_hi) + 1);
+    Pipe<NSX, G::SLOT1> px;
+    px.init(xs, bar + 2 * G::NSF, &a.maps[sg.vol].m[TM_X_1C], it.tx0 - XH1, it.ty0 - 1, xlo, xhi,
+            (uint32_t)(BX1 * G::BY1 * sizeof(float)), xfirst);
+    pg.issue_upto(zbeg + PREF - 1);
+    pd.issue_upto(zbeg + PREF - 1);
+    px.issue_upto(zbeg - RZ + PREF);
+    __syncthreads();
+
     float acc[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) acc[p] = 0.f;
-    bool primed = false;
+    const int y0 = warp * RPW;
+    const int gx = it.tx0 + lane;
+    const bool colin = gx < nx;
 
-    for (int zi = it.zo0 - RZ; zi <= it.zo1 - 1 + G::L; ++zi) {
-        stage_slice<G::HW, G::HH>(ringG + ring_slot(zi, G::NRING) * G::HC, v.g, v, it.tx0, it.ty0, G::RH, zi, sg.z0, sg.z1);
-        stage_slice<G::HW, G::HH>(ringD + ring_slot(zi, G::NRING) * G::HC, v.d, v, it.tx0, it.ty0, G::RH, zi, sg.z0, sg.z1);
-        const int zo = zi - G::L;
-        if (zo < it.zo0) continue;
+    for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
+        const int zo = zi - RZ;
+        const bool emit = zo >= it.zo0;
         const bool pen = zo >= pen_lo && zo < pen_hi;
-        if (pen) {
-            if (!primed)
-                stage_slice<XW, TY + 2>(XS + (zo & 1) * XSZ, v.x, v, it.tx0, it.ty0, 1, zo, 0, v.nz);
-            stage_slice<XW, TY + 2>(XS + ((zo + 1) & 1) * XSZ, v.x, v, it.tx0, it.ty0, 1, zo + 1, 0, v.nz);
-            primed = true;
-        }
-        if (tid < G::KXY) {
-            cf[0][tid] = v.fx[(long long)zo * v.kxy + tid];
-            cf[1][tid] = v.fy[(long long)zo * v.kxy + tid];
-        }
-        if (tid < G::KZ) cf[2][tid] = v.fz[(long long)zo * v.kz + tid];
-        __syncthreads();
-        for (int i = tid; i < G::HC; i += NT) {
-            float sg_ = 0.f, sd = 0.f;
-#pragma unroll
-            for (int c = -RZ; c <= RZ; ++c) {
-                const int o = ring_slot(zo - c, G::NRING) * G::HC + i;
-                sg_ = fmaf(cf[2][c + RZ], ringG[o], sg_);
-                sd = fmaf(cf[2][c + RZ], ringD[o], sd);
+        bool ok = pg.wait_upto(zi);
+        ok = pd.wait_upto(zi) && ok;
+        ok = px.wait_upto(zo + 1) && ok;
+        const float *cfr = CF + (zo - zbeg) * G::CFS;
+        if (emit) {
+            float fzc[G::KZ];
+            row_coeffs(fzc, cfr + 2 * G::KXYP);
+            for (int u = tid; u < 2 * G::ZUNITS; u += NT) {
+                if (u < G::ZUNITS) zcomb_unit<G>(pg, s, u, fzc, Wg);
+                else zcomb_unit<G>(pd, s, u - G::ZUNITS, fzc, Wd);
             }
-            Wg[i] = sg_;
-            Wd[i] = sd;
         }
-        __syncthreads();
-        for (int i = tid; i < G::HH * TX; i += NT) {
-            const int hy = i / TX, xo = i - hy * TX;
-            const int o = hy * G::HW + xo + G::RH;
-            float sg_ = 0.f, sd = 0.f;
-#pragma unroll
-            for (int aa = -R; aa <= R; ++aa) {
-                sg_ = fmaf(cf[0][aa + R], Wg[o - aa], sg_);
-                sd = fmaf(cf[0][aa + R], Wd[o - aa], sd);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) { pg.drain(); pd.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
+            return;
+        }
+        pg.issue_upto(zi + PREF);
+        pd.issue_upto(zi + PREF);
+        px.issue_upto(zo + 1 + PREF);
+        if (!emit) continue;
+        {
+            float fxc[G::KXY];
+            row_coeffs(fxc, cfr);
+            for (int u = tid; u < 2 * G::XUNITS; u += NT) {
+                if (u < G::XUNITS) xpass_unit<G, R, -1>(Wg, T1g, u, fxc);
+                else xpass_unit<G, R, -1>(Wd, T1d, u - G::XUNITS, fxc);
             }
-            T1g[i] = sg_;
-            T1d[i] = sd;
         }
         __syncthreads();
+        float fyc[G::KXY];
+        row_coeffs(fyc, cfr + G::KXYP);
+        float hg[RPW], hd[RPW];
+        ypass<R, RPW, -1>(T1g, y0, lane, fyc, hg);
+        ypass<R, RPW, -1>(T1d, y0, lane, fyc, hd);
+        const int s0 = Pipe<G::NSF, G::SLOT>::back_slot(s, RZ), s1 = Pipe<G::NSF, G::SLOT>::back_slot(s, RZ - 1);
+        const float *gz0 = pg.buf + s0 * G::SLOT, *gz1 = pg.buf + s1 * G::SLOT;   // slices zo, zo+1
+        const float *dz0 = pd.buf + s0 * G::SLOT, *dz1 = pd.buf + s1 * G::SLOT;
+        const float *xz0 = pen ? px.at(zo) : xs, *xz1 = pen ? px.at(zo + 1) : xs;
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
-            const int yo = warp * RPW + k, xo = lane;
-            const int o = (yo + G::RH) * TX + xo;
-            float hg = 0.f, hd = 0.f;
-#pragma unroll
-            for (int b = -R; b <= R; ++b) {
-                hg = fmaf(cf[1][b + R], T1g[o - b * TX], hg);
-                hd = fmaf(cf[1][b + R], T1d[o - b * TX], hd);
-            }
-            const int gx = it.tx0 + xo, gy = it.ty0 + yo;
-            if (gx < v.nx && gy < v.ny) {
-                acc[3] = fmaf(hg, hg, acc[3]);
-                acc[4] = fmaf(hg, hd, acc[4]);
-                acc[5] = fmaf(hd, hd, acc[5]);
+            const int yo = y0 + k, gy = it.ty0 + yo;
+            if (colin && gy < ny) {
+                acc[3] = fmaf(hg[k], hg[k], acc[3]);
+                acc[4] = fmaf(hg[k], hd[k], acc[4]);
+                acc[5] = fmaf(hd[k], hd[k], acc[5]);
                 if (pen) {
-                    const int ci = (yo + G::RH) * G::HW + xo + G::RH;
-                    const float *g0 = ringG + ring_slot(zo, G::NRING) * G::HC + ci;
-                    const float *d0 = ringD + ring_slot(zo, G::NRING) * G::HC + ci;
-                    const float *g1 = ringG + ring_slot(zo + 1, G::NRING) * G::HC + ci;
-                    const float *d1 = ringD + ring_slot(zo + 1, G::NRING) * G::HC + ci;
-                    const int xi = (yo + 1) * XW + xo + 1;
-                    const float *x0 = XS + (zo & 1) * XSZ + xi;
-                    const float *x1 = XS + ((zo + 1) & 1) * XSZ + xi;
-                    const float gc = g0[0], dc = d0[0], xc = x0[0];
+                    const int ci = (yo + R) * G::BX + lane + G::XH;
+                    const int xi = (yo + 1) * BX1 + lane + XH1;
+                    const float gc = gz0[ci], dc = dz0[ci], xc = xz0[xi];
                     if (zo >= sg.z0) {
                         acc[0] = fmaf(gc, gc, acc[0]);
                         acc[1] = fmaf(gc, dc, acc[1]);
                         acc[2] = fmaf(dc, dc, acc[2]);
                     }
-                    if (gx < v.nx - 1) {
-                        const float t = x0[1] - xc, w = rsqrtf(fmaf(t, t, v.delta2));
-                        const float vg = g0[1] - gc, vd = d0[1] - dc;
+                    if (gx < nx - 1) {
+                        const float t = xz0[xi + 1] - xc, w = rsqrtf(fmaf(t, t, delta2));
+                        const float vg = gz0[ci + 1] - gc, vd = dz0[ci + 1] - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);
                     }
-                    if (gy < v.ny - 1) {
-                        const float t = x0[XW] - xc, w = rsqrtf(fmaf(t, t, v.delta2));
-                        const float vg = g0[G::HW] - gc, vd = d0[G::HW] - dc;
+                    if (gy < ny - 1) {
+                        const float t = xz0[xi + BX1] - xc, w = rsqrtf(fmaf(t, t, delta2));
+                        const float vg = gz0[ci + G::BX] - gc, vd = dz0[ci + G::BX] - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);
                     }
-                    if (zo < v.nz - 1) {
-                        const float t = x1[0] - xc, w = rsqrtf(fmaf(t, t, v.delta2));
-                        const float vg = g1[0] - gc, vd = d1[0] - dc;
+                    if (zo < nz - 1) {
+                        const float t = xz1[xi] - xc, w = rsqrtf(fmaf(t, t, delta2));
+                        const float vg = gz1[ci] - gc, vd = dz1[ci] - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);
@@ -526,16 +858,15 @@ __global__ void __launch_bounds__(NT) k_curvature(KArgs a) {
                 }
             }
         }
-        __syncthreads();
     }
     if (!publish_partials<9>(acc, a.partials, a.ticket, a.nitems)) return;
     __shared__ double tot[9];
-    for (int s = 0; s < a.nslots; ++s) {
-        sum_slot<9>(a.partials, a.slot_beg[s], a.slot_beg[s + 1], tot);
+    for (int sl = 0; sl < a.nslots; ++sl) {
+        sum_slot<9>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
         if (tid == 0) {
-            const int slot = a.slot_id[s];
-            const SegDev ss = a.segs[a.items[a.slot_beg[s]].seg];
-            const VolDev vv = a.vols[ss.vol];
+            const int slot = a.slot_id[sl];
+            const SegDev ss = a.segs[a.items[a.slot_beg[sl]].seg];
+            const VolDev &vv = a.vols[ss.vol];
             const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
             const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
             const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);

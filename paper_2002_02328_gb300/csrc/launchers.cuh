@@ -7,32 +7,45 @@ namespace bd3mg {
 
 template <int R, int RZ>
 void launch_residual(const KArgs &a, cudaStream_t s) {
-    k_residual<R, RZ><<<a.nitems, NT, Geo<R, RZ>::smem_residual, s>>>(a);
+    k_residual<R, RZ><<<a.nitems, NT, Smem<R, RZ>::residual, s>>>(a);
 }
 template <int R, int RZ>
 void launch_gradient(const KArgs &a, cudaStream_t s) {
-    k_gradient<R, RZ><<<a.nitems, NT, Geo<R, RZ>::smem_gradient, s>>>(a);
+    k_gradient<R, RZ><<<a.nitems, NT, Smem<R, RZ>::gradient, s>>>(a);
 }
 template <int R, int RZ>
 void launch_curvature(const KArgs &a, cudaStream_t s) {
-    k_curvature<R, RZ><<<a.nitems, NT, Geo<R, RZ>::smem_curvature, s>>>(a);
+    k_curvature<R, RZ><<<a.nitems, NT, Smem<R, RZ>::curvature, s>>>(a);
 }
 template <int R, int RZ>
 cudaError_t prepare_set() {
     cudaError_t e = cudaFuncSetAttribute(k_residual<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Geo<R, RZ>::smem_residual);
+                                         (int)Smem<R, RZ>::residual);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gradient<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Geo<R, RZ>::smem_gradient);
+                                 (int)Smem<R, RZ>::gradient);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curvature<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)Geo<R, RZ>::smem_curvature);
+                                 (int)Smem<R, RZ>::curvature);
     return e;
+}
+
+template <int R, int RZ>
+int occupancy_of(int kind) {
+    int n = 0;
+    cudaError_t e;
+    if (kind == 0)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual<R, RZ>, NT, Smem<R, RZ>::residual);
+    else if (kind == 1)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ>, NT, Smem<R, RZ>::gradient);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ>, NT, Smem<R, RZ>::curvature);
+    return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace bd3mg
 
 #define BD3MG_KERNEL_SET(R, RZ)                                                                        \
     {R, RZ, &bd3mg::launch_residual<R, RZ>, &bd3mg::launch_gradient<R, RZ>, &bd3mg::launch_curvature<R, RZ>, \
-     &bd3mg::prepare_set<R, RZ>, bd3mg::Geo<R, RZ>::smem_residual, bd3mg::Geo<R, RZ>::smem_gradient,       \
-     bd3mg::Geo<R, RZ>::smem_curvature}
+     &bd3mg::prepare_set<R, RZ>, bd3mg::Smem<R, RZ>::residual, bd3mg::Smem<R, RZ>::gradient,       \
+     bd3mg::Smem<R, RZ>::curvature, &bd3mg::occupancy_of<R, RZ>}
