@@ -18,6 +18,7 @@
 #include "../../include/bd3mg.h"
 #include "kernel_sets.h"
 #include "kernels.cuh"
+#include "plan.h"
 
 using namespace bd3mg;
 
@@ -129,33 +130,6 @@ bd3mg_status dalloc_n(bd3mg_ctx *c, T **p, size_t count) {
     return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-// 3D tile map over a pitched float32 volume: dims (nx, ny, nz), box (bx, by, 1),
-// zero fill outside the volume.
-bool encode_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int pitch, int bx, int by) {
-    auto fn = encode_fn();
-    if (!fn) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-    cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * (cuuint64_t)ny};
-    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 // Staged-tile extents of a kernel set (must match Geo<R,RZ> in kernels.cuh).
 int set_xh(const KernelSet *k) { return k->R <= 4 ? 4 : 8; }
 
@@ -174,71 +148,6 @@ bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const float *x, const floa
     if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
     if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
     return ok;
-}
-
-// Rank-1 factoring of each depth's PSF in FP64: with m_x(a) = sum_{b,c} h,
-// m_y, m_z the marginals and S = sum h, a rank-1 tensor satisfies
-// h = m_x m_y m_z / S^2.  Factors: fx = m_x / S, fy = m_y / S, fz = m_z.
-bool factor_psf(const bd3mg_params &p, int R, int RZ, std::vector<float> &fx, std::vector<float> &fy,
-                std::vector<float> &fz, double *worst) {
-    const int rx = (p.px - 1) / 2, ry = (p.py - 1) / 2, rz = (p.pz - 1) / 2;
-    const int kxy = 2 * R + 1, kz = 2 * RZ + 1;
-    fx.assign((size_t)p.nz * kxy, 0.f);
-    fy.assign((size_t)p.nz * kxy, 0.f);
-    fz.assign((size_t)p.nz * kz, 0.f);
-    *worst = 0.0;
-    std::vector<double> mx(p.px), my(p.py), mz(p.pz);
-    for (int z = 0; z < p.nz; ++z) {
-        const float *h = p.psf + (size_t)z * p.pz * p.py * p.px;
-        std::fill(mx.begin(), mx.end(), 0.0);
-        std::fill(my.begin(), my.end(), 0.0);
-        std::fill(mz.begin(), mz.end(), 0.0);
-        double S = 0.0, hmax = 0.0;
-        for (int c = 0; c < p.pz; ++c)
-            for (int b = 0; b < p.py; ++b)
-                for (int a = 0; a < p.px; ++a) {
-                    const double v = h[((size_t)c * p.py + b) * p.px + a];
-                    mx[a] += v;
-                    my[b] += v;
-                    mz[c] += v;
-                    S += v;
-                    hmax = std::max(hmax, std::fabs(v));
-                }
-        if (hmax == 0.0) continue;              // all-zero PSF: zero factors
-        if (S == 0.0) return false;
-        double res = 0.0;
-        for (int c = 0; c < p.pz; ++c)
-            for (int b = 0; b < p.py; ++b)
-                for (int a = 0; a < p.px; ++a) {
-                    const double v = h[((size_t)c * p.py + b) * p.px + a];
-                    res = std::max(res, std::fabs(v - mx[a] * my[b] * mz[c] / (S * S)));
-                }
-        *worst = std::max(*worst, res / hmax);
-        if (res > 1e-6 * hmax) return false;
-        for (int a = 0; a < p.px; ++a) fx[(size_t)z * kxy + (a - rx) + R] = (float)(mx[a] / S);
-        for (int b = 0; b < p.py; ++b) fy[(size_t)z * kxy + (b - ry) + R] = (float)(my[b] / S);
-        for (int c = 0; c < p.pz; ++c) fz[(size_t)z * kz + (c - rz) + RZ] = (float)mz[c];
-    }
-    return true;
-}
-
-// Greedy colouring in increasing z: a slab takes the first colour whose slabs
-// all end at least `gap` slices before it starts.  Slabs of one colour then
-// read and write disjoint data, so updating them together equals updating them
-// one after the other.
-int colour_slabs(const std::vector<int> &bounds, int gap, std::vector<int> &colour) {
-    const int ns = (int)bounds.size() - 1;
-    colour.assign(ns, 0);
-    std::vector<int> last_end;                  // per colour: end slice of its last slab
-    for (int s = 0; s < ns; ++s) {
-        int c = 0;
-        for (; c < (int)last_end.size(); ++c)
-            if (bounds[s] - last_end[c] >= gap) break;
-        if (c == (int)last_end.size()) last_end.push_back(0);
-        colour[s] = c;
-        last_end[c] = bounds[s + 1];
-    }
-    return (int)last_end.size();
 }
 
 int ntiles(const bd3mg_ctx *c, int ty) { return ((c->p.nx + TX - 1) / TX) * ((c->p.ny + ty - 1) / ty); }
@@ -262,27 +171,8 @@ void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi, int zc, int ty) {
 // z halo), the makespan of equal-cost items; ties go to longer chunks.
 int choose_zchunk(const bd3mg_ctx *c, const std::vector<std::pair<int, int>> &ranges, int kind) {
     if (c->p.zchunk > 0) return std::min(c->p.zchunk, ZC_MAX);
-    const long long slots = (long long)c->sms * std::max(1, c->occ[kind]);
-    const int halo = 2 * c->ks->RZ;
-    long long best_cost = -1;
-    int best = 4;
-    for (int zc = 4; zc <= ZC_MAX; ++zc) {
-        long long items = 0;
-        int longest = 0;
-        for (auto &r : ranges) {
-            const int len = r.second - r.first;
-            if (len <= 0) continue;
-            const int nch = (len + zc - 1) / zc;
-            items += (long long)nch * ntiles(c, tile_y(kind));
-            longest = std::max(longest, (len + nch - 1) / nch);
-        }
-        const long long cost = ((items + slots - 1) / slots) * (longest + halo);
-        if (best_cost < 0 || cost <= best_cost) {
-            best_cost = cost;
-            best = zc;
-        }
-    }
-    return best;
+    return bd3mg::choose_zchunk((long long)c->sms * std::max(1, c->occ[kind]), ntiles(c, tile_y(kind)),
+                                2 * c->ks->RZ, ranges);
 }
 
 // Build one launch over the given segments, each with output range f(seg).

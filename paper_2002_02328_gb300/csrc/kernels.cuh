@@ -245,6 +245,11 @@ struct Pipe {
         par = 0u;
         next_issue = next_wait = first_slice;
         issue_slot = wait_slot = 0;
+        // The descriptor sits in global memory and may have been rewritten since
+        // an earlier launch: order the tensormap proxy after those writes.
+        if (threadIdx.x == 0)
+            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
+                         : "memory");
     }
     __device__ __forceinline__ bool loaded(int z) const { return z >= zlo && z < zhi; }
     __device__ __forceinline__ int slot(int z) const { return (z - first) % NS; }

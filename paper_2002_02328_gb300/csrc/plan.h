@@ -1,0 +1,34 @@
+// plan.h -- host-side planning helpers shared by the context API and the
+// static-scratch entry point (internal; not part of the C ABI).
+#pragma once
+#include <cuda.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/bd3mg.h"
+
+namespace bd3mg {
+
+// 3D tile map over a pitched float32 volume: dims (nx, ny, nz), row pitch in
+// floats (multiple of 4), box (bx, by, 1), zero fill outside the volume.
+bool encode_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int pitch, int bx, int by);
+
+constexpr int kMaxPsfExtent = 11;        // largest PSF extent the compiled kernels cover
+
+// Rank-1 factoring of each depth's PSF (FP64), factors zero-padded to radii
+// (R, RZ); false if some depth's relative residual exceeds 1e-6.  The _into
+// form writes caller arrays (nz*(2R+1), nz*(2R+1), nz*(2RZ+1)) and uses no heap.
+bool factor_psf_into(const bd3mg_params &p, int R, int RZ, float *fx, float *fy, float *fz, double *worst);
+bool factor_psf(const bd3mg_params &p, int R, int RZ, std::vector<float> &fx, std::vector<float> &fy,
+                std::vector<float> &fz, double *worst);
+
+// Greedy slab colouring (see bd3mg_plan_slab_colours); returns the colour count.
+int colour_slabs(const std::vector<int> &bounds, int gap, std::vector<int> &colour);
+
+// z-chunk minimising (waves of `slots` resident CTAs) x (longest chunk + halo)
+// over the output ranges, each crossed with `ntiles` xy tiles.
+int choose_zchunk(long long slots, int ntiles, int halo, const std::vector<std::pair<int, int>> &ranges);
+int choose_zchunk(long long slots, int ntiles, int halo, const std::pair<int, int> *ranges, int nranges);
+
+}  // namespace bd3mg
