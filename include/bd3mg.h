@@ -172,6 +172,43 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
 /* Number of kernel launches one iteration enqueues. */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
+/* Size of the device array behind bd3mg_objective_noalloc (bytes). */
+#define BD3MG_STATIC_SCRATCH_BYTES (1u << 20)
+
+/* Objective f(x) without allocating device memory (the paper has no
+ * counterpart; this is a deployment variant of bd3mg_objective).
+ *
+ * For callers that cannot allocate where they need the objective: plug-ins
+ * inside a host framework that owns all device memory and forbids private
+ * allocations, and latency-critical loops that must not take the allocator's
+ * locks or pay the device-wide synchronisation that cudaFree implies.  The
+ * call allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine): its device state lives in one file-scope device array of
+ * BD3MG_STATIC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.
+ *
+ * p: problem as for bd3mg_create (nslabs, precision and pinv_rtol are
+ *    ignored; psf is a host pointer, read during the call).
+ * x, y: DEVICE volumes [nz][ny][nx], read in place; nx must be a multiple of 4
+ *    and both pointers 16-byte aligned.
+ * f_out: DEVICE pointer to 4 doubles, written in stream order with
+ *    {f, data term, box term, penalty term}; a non-finite input shows as a
+ *    non-finite f.
+ * stream: cudaStream_t as void*; the call enqueues one host-to-device copy and
+ *    one kernel and does not synchronise.
+ * err, err_len: optional buffer that receives a one-line message.
+ *
+ * The first call on each device performs that device's set-up (it looks up
+ * the array's device address with that device current); make that first call
+ * before any stream capture.  All calls share the array and each overwrites
+ * it (the completion ticket and status words are cleared at every call), so
+ * calls that overlap on the GPU race: order them on one stream.  Returns
+ * BD3MG_EINVAL, with a message, when the volume's work list and PSF factor rows
+ * do not fit the array (roughly: more than ~20 000 tiles of 32x32 voxels times
+ * z-chunks, or more than a few thousand depth slices). */
+bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const float *x, const float *y, double *f_out,
+                                     void *stream, char *err, size_t err_len);
+
 const char *bd3mg_error_string(bd3mg_ctx *ctx);
 const char *bd3mg_status_string(bd3mg_status s);
 

@@ -30,7 +30,7 @@ FP32, BF16_DIRECTIONS = 0, 1
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
             "bd3mg_gradient", "bd3mg_get_x", "bd3mg_get_d", "bd3mg_set_x", "bd3mg_last_step", "bd3mg_apply_H",
             "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
-            "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_error_string",
+            "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
             "bd3mg_factor_psf": (ip, [ip, ip, ip, ip, vp, vp, vp, vp, vp]),
             "bd3mg_launches_per_iteration": (ip, [vp]),
             "bd3mg_profile_iteration": (ip, [vp, vp, vp]),
+            "bd3mg_objective_noalloc": (ip, [P, vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
             "bd3mg_destroy": (None, [vp]),
@@ -180,6 +181,21 @@ def bd3mg_factor_psf(psf: np.ndarray):
     if st != 0:
         raise Bd3mgError(st, f"PSF not separable (residual {res.value:.3g})")
     return fx, fy, fz, res.value
+
+
+def bd3mg_objective_noalloc(params: Params, x, y, f_out, stream=None):
+    """f(x) into the 4-double device tensor f_out without any device allocation.
+
+    x, y: contiguous float32 CUDA tensors [nz][ny][nx] (nx a multiple of 4).
+    Raises Bd3mgError with the library's message on failure.
+    """
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    err = ctypes.create_string_buffer(256)
+    st = load().bd3mg_objective_noalloc(ctypes.byref(params), ctypes.c_void_p(_ptr(x)), ctypes.c_void_p(_ptr(y)),
+                                        ctypes.c_void_p(_ptr(f_out)), ctypes.c_void_p(int(s)), err, 256)
+    if st != 0:
+        raise Bd3mgError(st, err.value.decode())
 
 
 def _ptr(t) -> int:
