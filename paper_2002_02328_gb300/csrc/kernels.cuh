@@ -405,22 +405,43 @@ __device__ __forceinline__ void stage_coeffs(float *CF, const VolDev &V, int z0,
     }
 }
 
+// N coefficients from a 16-byte aligned shared row padded to a multiple of 4.
 template <int N>
 __device__ __forceinline__ void row_coeffs(float (&c)[N], const float *p) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
 #pragma unroll
-    for (int i = 0; i < N; ++i) c[i] = p[i];
+    for (int i = 0; i < (N + 3) / 4; ++i) {
+        const float4 v = q[i];
+        if (4 * i + 0 < N) c[4 * i + 0] = v.x;
+        if (4 * i + 1 < N) c[4 * i + 1] = v.y;
+        if (4 * i + 2 < N) c[4 * i + 2] = v.z;
+        if (4 * i + 3 < N) c[4 * i + 3] = v.w;
+    }
 }
 
-// Forward z-combine of one unit (4 staged columns of one row) for the output
-// whose newest input slice sits in slot s:  W = sum_t fz[t] * v(zi - t).
-template <class G, int NS, int SLOTF>
-__device__ __forceinline__ void zcomb_unit(const Pipe<NS, SLOTF> &p, int s, int u, const float (&fzc)[G::KZ],
-                                           float *W) {
-    const int off = u * 4;                     // units tile the staged rows exactly (BX % 4 == 0)
+// Per-thread work assignment of the z-combine and x-pass phases, fixed for an
+// item: unit j of this thread is u = tid + j*NT (valid while u < units).
+template <int UNITS>
+struct Units {
+    static constexpr int PER = (UNITS + NT - 1) / NT;
+};
+
+// Window of the forward z-combine: the KZ staged slices zi, zi-1, ..., zi-2RZ
+// (slot s holds zi).
+template <int KZ, int NS, int SLOTF>
+__device__ __forceinline__ void window(const Pipe<NS, SLOTF> &p, int s, const float *(&w)[KZ]) {
+#pragma unroll
+    for (int t = 0; t < KZ; ++t) w[t] = p.buf + Pipe<NS, SLOTF>::back_slot(s, t) * SLOTF;
+}
+
+// Forward z-combine of one unit (4 staged columns at float offset off):
+// W = sum_t fz[t] * v(zi - t) = sum_c fz_zo(c) v(zo - c).
+template <int KZ>
+__device__ __forceinline__ void zcomb_unit(const float *const (&w)[KZ], int off, const float (&fzc)[KZ], float *W) {
     float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
 #pragma unroll
-    for (int t = 0; t < G::KZ; ++t) {
-        const float4 v = *reinterpret_cast<const float4 *>(p.buf + Pipe<NS, SLOTF>::back_slot(s, t) * SLOTF + off);
+    for (int t = 0; t < KZ; ++t) {
+        const float4 v = *reinterpret_cast<const float4 *>(w[t] + off);
         float4 &a = (t & 1) ? acc1 : acc0;
         a.x = fmaf(fzc[t], v.x, a.x);
         a.y = fmaf(fzc[t], v.y, a.y);
@@ -432,11 +453,12 @@ __device__ __forceinline__ void zcomb_unit(const Pipe<NS, SLOTF> &p, int s, int 
 }
 
 // x-pass over staged rows: T1[row][x] = sum_a fx[a+R] * S[row][x + XH + SGN*a]
-// (SGN = -1: convolution for H; SGN = +1: correlation for H^T), 4 outputs per unit.
+// (SGN = -1: convolution for H; SGN = +1: correlation for H^T), 4 outputs per
+// unit; src = float offset of the unit's XNV-float4 window in S, dst = float
+// offset of its 4 outputs in T1.
 template <class G, int R, int SGN>
-__device__ __forceinline__ void xpass_unit(const float *S, float *T1, int u, const float (&fxc)[2 * R + 1]) {
-    const int row = u / (TX / 4), x0 = (u - row * (TX / 4)) * 4;
-    const float4 *sp = reinterpret_cast<const float4 *>(S + row * G::BX + x0 + G::XA0);
+__device__ __forceinline__ void xpass_unit(const float *S, float *T1, int src, int dst, const float (&fxc)[2 * R + 1]) {
+    const float4 *sp = reinterpret_cast<const float4 *>(S + src);
     float w[4 * G::XNV];
 #pragma unroll
     for (int v = 0; v < G::XNV; ++v) {
@@ -456,7 +478,14 @@ __device__ __forceinline__ void xpass_unit(const float *S, float *T1, int u, con
         for (int a = -R + 1; a <= R; a += 2) s1 = fmaf(fxc[a + R], w[i + SGN * a + G::XH - G::XA0], s1);
         o[i] = s0 + s1;
     }
-    *reinterpret_cast<float4 *>(T1 + row * TX + x0) = make_float4(o[0], o[1], o[2], o[3]);
+    *reinterpret_cast<float4 *>(T1 + dst) = make_float4(o[0], o[1], o[2], o[3]);
+}
+
+template <class G>
+__device__ __forceinline__ void xpass_offsets(int u, int &src, int &dst) {
+    const int row = u / (TX / 4), x0 = (u - row * (TX / 4)) * 4;
+    src = row * G::BX + x0 + G::XA0;
+    dst = row * TX + x0;
 }
 
 // y-pass for this thread's RPW outputs (column lane, rows y0..y0+RPW-1):
@@ -517,6 +546,19 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     const int y0 = warp * RPW;
     const int gx = it.tx0 + lane;
     const bool colin = gx < nx;
+    // fixed per-thread offsets of this item
+    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
+    int goff[RPW];
+    unsigned vmask = 0u;
+#pragma unroll
+    for (int k = 0; k < RPW; ++k) {
+        const int gy = it.ty0 + y0 + k;
+        goff[k] = gy * pitch + gx;
+        if (colin && gy < ny) vmask |= 1u << k;
+    }
 
     for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
         const bool ok = px.wait_upto(zi);
@@ -526,14 +568,16 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         float yv[RPW];
         if (emit) {
             // observation values of this thread's outputs, fetched early to hide latency
+            const float *yrow = yp ? yp + (long long)zo * plane : nullptr;
 #pragma unroll
-            for (int k = 0; k < RPW; ++k) {
-                const int gy = it.ty0 + y0 + k;
-                yv[k] = (yp && colin && gy < ny) ? __ldg(yp + (long long)zo * plane + (long long)gy * pitch + gx) : 0.f;
-            }
+            for (int k = 0; k < RPW; ++k) yv[k] = (yrow && ((vmask >> k) & 1u)) ? __ldg(yrow + goff[k]) : 0.f;
             float fzc[G::KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
-            for (int u = tid; u < G::ZUNITS; u += NT) zcomb_unit<G>(px, s, u, fzc, W);
+            const float *w[G::KZ];
+            window(px, s, w);
+#pragma unroll
+            for (int j = 0; j < ZP; ++j)
+                if (tid + j * NT < G::ZUNITS) zcomb_unit(w, 4 * (tid + j * NT), fzc, W);
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) { px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
@@ -544,7 +588,9 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);
-            for (int u = tid; u < G::XUNITS; u += NT) xpass_unit<G, R, -1>(W, T1, u, fxc);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(W, T1, xsrc[j], xdst[j], fxc);
         }
         __syncthreads();
         float fyc[G::KXY];
@@ -553,13 +599,13 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         ypass<R, RPW, -1>(T1, y0, lane, fyc, hx);
         const float *xz = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ) * G::SLOT;       // slice zo
         const float *xz1 = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ - 1) * G::SLOT;  // slice zo+1
+        float *rrow = rp + (long long)zo * plane;
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
             const int yo = y0 + k, gy = it.ty0 + yo;
-            if (colin && gy < ny) {
-                const long long n = (long long)zo * plane + (long long)gy * pitch + gx;
+            if ((vmask >> k) & 1u) {
                 const float rr = hx[k] - yv[k];
-                if (store_r) rp[n] = rr;
+                if (store_r) rrow[goff[k]] = rr;
                 if (obj) {
                     const int ci = (yo + R) * G::BX + lane + G::XH;
                     const float xc = xz[ci];
@@ -569,7 +615,9 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
                     const float tx = gx < nx - 1 ? xz[ci + 1] - xc : 0.f;
                     const float ty = gy < ny - 1 ? xz[ci + G::BX] - xc : 0.f;
                     const float tz = zo < nz - 1 ? xz1[ci] - xc : 0.f;
-                    acc[2] += sqrtf(fmaf(tx, tx, delta2)) + sqrtf(fmaf(ty, ty, delta2)) + sqrtf(fmaf(tz, tz, delta2));
+                    // sqrt(v) = v * rsqrt(v), v >= delta^2 > 0
+                    const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
+                    acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
                 }
             }
         }
@@ -648,6 +696,10 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     const int y0 = warp * RPW;
     const int gx = it.tx0 + lane;
     const bool colin = gx < nx;
+    constexpr int XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
 
     for (int zi = zbeg; zi < zend; ++zi) {
         const int zo = zi - RZ;
@@ -660,7 +712,9 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
             float fxc[G::KXY];
             row_coeffs(fxc, cfi);
             const float *src = pr.at(zi);
-            for (int u = tid; u < G::XUNITS; u += NT) xpass_unit<G, R, +1>(src, T1, u, fxc);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, +1>(src, T1, xsrc[j], xdst[j], fxc);
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) { pr.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
@@ -688,6 +742,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
             float fzc[G::KZ];
 #pragma unroll
             for (int t = 0; t < G::KZ; ++t) fzc[t] = CF[(zo + t - RZ - zbeg) * G::CFS + 2 * G::KXYP + t];
+            float *grow = gp + (long long)zo * plane;
             const float *xm = full ? px.at(zo - 1) : nullptr;
             const float *x0p = full ? px.at(zo) : nullptr;
             const float *xp1 = full ? px.at(zo + 1) : nullptr;
@@ -701,7 +756,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                 const float q = q0 + q1;
                 const int yo = y0 + k, gy = it.ty0 + yo;
                 if (colin && gy < ny) {
-                    const long long n = (long long)zo * plane + (long long)gy * pitch + gx;
+                    const int n = gy * pitch + gx;
                     float gval = q;
                     if (full) {
                         const int ci = (yo + 1) * BX1 + lane + XH1;
@@ -717,7 +772,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                         const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
                         gval = fmaf(lam, pen, fmaf(eta2, dist, q));
                     }
-                    gp[n] = gval;
+                    grow[n] = gval;
                 }
             }
         }
@@ -780,6 +835,10 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     const int y0 = warp * RPW;
     const int gx = it.tx0 + lane;
     const bool colin = gx < nx;
+    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
 
     for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
         const int zo = zi - RZ;
@@ -792,10 +851,15 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
         if (emit) {
             float fzc[G::KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
-            for (int u = tid; u < 2 * G::ZUNITS; u += NT) {
-                if (u < G::ZUNITS) zcomb_unit<G>(pg, s, u, fzc, Wg);
-                else zcomb_unit<G>(pd, s, u - G::ZUNITS, fzc, Wd);
-            }
+            const float *wg[G::KZ], *wd[G::KZ];
+            window(pg, s, wg);
+            window(pd, s, wd);
+#pragma unroll
+            for (int j = 0; j < ZP; ++j)
+                if (tid + j * NT < G::ZUNITS) zcomb_unit(wg, 4 * (tid + j * NT), fzc, Wg);
+#pragma unroll
+            for (int j = 0; j < ZP; ++j)
+                if (tid + j * NT < G::ZUNITS) zcomb_unit(wd, 4 * (tid + j * NT), fzc, Wd);
         }
         if (__syncthreads_or(!ok)) {
             if (tid == 0) { pg.drain(); pd.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
@@ -808,10 +872,12 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
         {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);
-            for (int u = tid; u < 2 * G::XUNITS; u += NT) {
-                if (u < G::XUNITS) xpass_unit<G, R, -1>(Wg, T1g, u, fxc);
-                else xpass_unit<G, R, -1>(Wd, T1d, u - G::XUNITS, fxc);
-            }
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(Wg, T1g, xsrc[j], xdst[j], fxc);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(Wd, T1d, xsrc[j], xdst[j], fxc);
         }
         __syncthreads();
         float fyc[G::KXY];
