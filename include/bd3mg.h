@@ -95,9 +95,25 @@ void bd3mg_params_default(bd3mg_params *p);
 bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
                           void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);
 
-/* Run n >= 0 iterations (one iteration = one sweep over all slabs).  If
- * f_trace is not NULL it receives n+1 host doubles: f(x^k) before each sweep
- * and f after the last.  Synchronises the stream. */
+/* Create a context over nvol >= 1 independent volumes that iterate in lockstep
+ * (one sweep of every volume per iteration, all volumes in the same kernel
+ * launches).  p[v], y[v] and x0[v] (x0 may be NULL, or hold NULL entries, for
+ * x0 = y) describe volume v exactly as for bd3mg_create; sizes, PSFs,
+ * lambda, delta, eta and the box may differ between volumes.  The kernels are
+ * chosen for the largest PSF radii (smaller PSFs are zero padded); pinv_rtol
+ * and zchunk are taken from p[0].  Per-volume results: bd3mg_objectives,
+ * bd3mg_get_volume, and the nvol traces of bd3mg_iterate.  Functions without a
+ * volume index act on volume 0. */
+bd3mg_status bd3mg_batch_create(int nvol, const bd3mg_params *p, const float *const *y, const float *const *x0,
+                                int data_on_device, void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);
+
+/* Number of volumes of the context (0 for NULL). */
+int bd3mg_volume_count(bd3mg_ctx *ctx);
+
+/* Run n >= 0 iterations (one iteration = one sweep over all slabs of every
+ * volume).  If f_trace is not NULL it receives nvol*(n+1) host doubles,
+ * volume-major: f(x^k) of each volume before each sweep and after the last.
+ * Synchronises the stream. */
 bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
 
 /* Enqueue n iterations without synchronising and without reading anything back
@@ -108,6 +124,15 @@ bd3mg_status bd3mg_iterate_async(bd3mg_ctx *ctx, int n);
 /* Objective at the current iterate; parts (optional, 3 doubles) = data term,
  * box term, penalty term.  Synchronises. */
 bd3mg_status bd3mg_objective(bd3mg_ctx *ctx, double *f, double *parts);
+
+/* Objective of every volume at the current iterates: f receives nvol host
+ * doubles.  Synchronises. */
+bd3mg_status bd3mg_objectives(bd3mg_ctx *ctx, double *f);
+
+/* Copy volume vol's iterate (which = 0), memory direction d (1) or last
+ * gradient g (2) to dst (nx*ny*nz floats of that volume; device pointer if
+ * on_device else host).  Synchronises. */
+bd3mg_status bd3mg_get_volume(bd3mg_ctx *ctx, int vol, int which, float *dst, int on_device);
 
 /* Gradient of f at the current iterate (full volume) written to g (nx*ny*nz
  * floats; device pointer if on_device else host); f (optional) receives f.
@@ -120,10 +145,10 @@ bd3mg_status bd3mg_get_x(bd3mg_ctx *ctx, float *x, int on_device);
 bd3mg_status bd3mg_get_d(bd3mg_ctx *ctx, float *d, int on_device);
 bd3mg_status bd3mg_set_x(bd3mg_ctx *ctx, const float *x, int on_device);
 
-/* Diagnostics of the most recent block steps: for each slab s (in slab order),
- * 8 doubles {B00, B01, B11, c0, c1, u0, u1, rank} of the 2x2 system of its
- * last update (B = D^T A D, c = D^T grad f, u = -B^+ c).  info must hold
- * 8*max(nslabs,1) doubles.  Synchronises. */
+/* Diagnostics of the most recent block steps: for each slab s of each volume
+ * (volume-major, slab order), 8 doubles {B00, B01, B11, c0, c1, u0, u1, rank}
+ * of the 2x2 system of its last update (B = D^T A D, c = D^T grad f,
+ * u = -B^+ c).  info must hold 8 * (total slabs) doubles.  Synchronises. */
 bd3mg_status bd3mg_last_step(bd3mg_ctx *ctx, double *info);
 
 /* Apply the blur H or its adjoint H^T of this context to a device volume
@@ -132,9 +157,10 @@ bd3mg_status bd3mg_last_step(bd3mg_ctx *ctx, double *info);
 bd3mg_status bd3mg_apply_H(bd3mg_ctx *ctx, const float *in, float *out);
 bd3mg_status bd3mg_apply_HT(bd3mg_ctx *ctx, const float *in, float *out);
 
-/* Slab colouring chosen at creation: colour[s] for each slab (nslabs ints,
- * host) and the number of colours.  Slabs of one colour are at least
- * max(pz-1, 1) slices apart, so their steps do not interact. */
+/* Slab colouring chosen at creation: colour[s] for each slab of each volume
+ * (volume-major; total-slab ints, host) and the number of colours.  Slabs of
+ * one colour are at least max(pz-1, 1) slices apart, so their steps do not
+ * interact. */
 bd3mg_status bd3mg_slab_colours(bd3mg_ctx *ctx, int *colour, int *ncolours);
 
 /* Host-only planning helpers (no GPU needed).

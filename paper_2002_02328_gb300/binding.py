@@ -30,7 +30,8 @@ FP32, BF16_DIRECTIONS = 0, 1
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
             "bd3mg_gradient", "bd3mg_get_x", "bd3mg_get_d", "bd3mg_set_x", "bd3mg_last_step", "bd3mg_apply_H",
             "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
-            "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc", "bd3mg_error_string",
+            "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc",
+            "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -87,6 +88,10 @@ def load(path: str = LIB_PATH):
             "bd3mg_factor_psf": (ip, [ip, ip, ip, ip, vp, vp, vp, vp, vp]),
             "bd3mg_launches_per_iteration": (ip, [vp]),
             "bd3mg_profile_iteration": (ip, [vp, vp, vp]),
+            "bd3mg_batch_create": (ip, [ip, P, vp, vp, ip, vp, ctypes.POINTER(Allocator), ctypes.POINTER(vp)]),
+            "bd3mg_volume_count": (ip, [vp]),
+            "bd3mg_objectives": (ip, [vp, vp]),
+            "bd3mg_get_volume": (ip, [vp, ip, ip, vp, ip]),
             "bd3mg_objective_noalloc": (ip, [P, vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
@@ -360,3 +365,97 @@ class Solver:
         sl = prob.slabs if slabs == "auto" else slabs
         return cls(prob.shape, prob.psf, y, x0, lam=prob.lam, delta=prob.delta, eta=prob.eta, xmin=prob.xmin,
                    xmax=prob.xmax, slabs=sl, **kw)
+
+
+class BatchSolver:
+    """Many independent volumes iterated in lockstep by one context (plain 3MG each)."""
+
+    def __init__(self, problems, x0s=None, device="cuda", zchunk: int = 0, stream=None,
+                 use_torch_allocator: bool = True):
+        torch = _torch()
+        lib = load()
+        self.shapes = [tuple(int(s) for s in p.shape) for p in problems]
+        self.nvol = len(problems)
+        arr = (Params * self.nvol)()
+        keep = []
+        ys, xs = [], []
+        for v, p in enumerate(problems):
+            prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, None, FP32, 1e-12, zchunk)
+            arr[v] = prm
+            keep.append(k)
+            yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)
+            ys.append(yt)
+            if x0s is not None and x0s[v] is not None:
+                xs.append(torch.from_numpy(np.ascontiguousarray(x0s[v], np.float32)).to(device))
+            else:
+                xs.append(None)
+        on_dev = bool(ys[0].is_cuda)
+        yptr = (ctypes.c_void_p * self.nvol)(*[_ptr(t) for t in ys])
+        xptr = (ctypes.c_void_p * self.nvol)(*[(_ptr(t) if t is not None else None) for t in xs])
+        s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        alloc_p = None
+        if use_torch_allocator:
+            al, cbs = _torch_allocator()
+            keep += [al, cbs]
+            alloc_p = ctypes.byref(al)
+        ctx = ctypes.c_void_p()
+        st = lib.bd3mg_batch_create(self.nvol, arr, yptr, xptr, int(on_dev), ctypes.c_void_p(int(s)), alloc_p,
+                                    ctypes.byref(ctx))
+        if st != 0:
+            msg = lib.bd3mg_error_string(ctx).decode() if ctx.value else lib.bd3mg_status_string(st).decode()
+            if ctx.value:
+                lib.bd3mg_destroy(ctx)
+            raise Bd3mgError(st, msg)
+        self._ctx, self._keep, self._lib = ctx, [arr, keep, ys, xs], lib
+
+    def close(self):
+        if getattr(self, "_ctx", None) is not None and self._ctx.value:
+            self._lib.bd3mg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _c(self, st):
+        _check(self._ctx, st)
+
+    def iterate(self, n: int, trace: bool = True):
+        """n lockstep iterations; returns the (nvol, n+1) objective traces or None."""
+        buf = np.zeros((self.nvol, n + 1)) if trace else None
+        self._c(self._lib.bd3mg_iterate(self._ctx, int(n), buf.ctypes.data if trace else None))
+        return buf
+
+    def iterate_async(self, n: int):
+        self._c(self._lib.bd3mg_iterate_async(self._ctx, int(n)))
+
+    def objectives(self):
+        f = np.zeros(self.nvol)
+        self._c(self._lib.bd3mg_objectives(self._ctx, f.ctypes.data))
+        return f
+
+    def get(self, vol: int, which: int = 0, out=None):
+        """Volume vol's x (which=0), d (1) or g (2) as a CUDA tensor."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.shapes[vol], dtype=torch.float32, device="cuda")
+        self._c(self._lib.bd3mg_get_volume(self._ctx, int(vol), int(which), ctypes.c_void_p(_ptr(out)),
+                                           int(out.is_cuda)))
+        return out
+
+    def profile_iteration(self):
+        ms = np.zeros(5)
+        cnt = np.zeros(5, np.int32)
+        self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(Solver.KERNEL_CLASSES)}
+
+    def launches_per_iteration(self) -> int:
+        return int(self._lib.bd3mg_launches_per_iteration(self._ctx))

@@ -1,13 +1,20 @@
 // api.cu -- host runtime behind the C ABI of include/bd3mg.h.
 //
-// Planning (PSF factoring, slab colouring, work lists), device state, CUDA
-// graph capture of one iteration, and the entry points.  No device arithmetic
-// lives here; every step of the iteration runs in the kernels of kernels.cuh.
+// A context holds one or more volumes (a batch), each split into one or more
+// depth slabs.  Planning (PSF factoring, slab colouring, work lists), device
+// state, CUDA graph capture of one iteration, and the entry points live here;
+// every step of the iteration runs in the kernels of kernels.cuh / update.cu.
+//
+// Work lists: a segment is one slab of one volume (its own 2x2 system and
+// reduction slot).  Every kernel launch covers a list of segments of possibly
+// different volumes; items are (segment, xy tile, z-chunk).  Volumes are
+// independent, so colour c of every volume is processed in the same launch.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -24,16 +31,27 @@ using namespace bd3mg;
 
 namespace {
 
-struct Launch {                 // one tile-kernel launch over a contiguous item range
+struct Launch {                     // one tile-kernel launch over a contiguous item range
     int item_off = 0, nitems = 0;
     int beg_off = 0;                // into slot_beg_h (nslots+1 entries, item offsets within the launch)
     int slot_off = 0, nslots = 0;   // into slot_id_h (nslots entries)
 };
 
+struct VolState {
+    bd3mg_params p{};               // host copy (psf and slab_bounds cleared)
+    int pitch = 0;                  // row stride in floats (multiple of 4)
+    size_t np = 0;                  // pitch*ny*nz
+    float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
+    float *fx = nullptr, *fy = nullptr, *fz = nullptr;
+    VolDev dev{};                   // host copy of the device descriptor
+    std::vector<int> bounds;        // slab bounds
+    std::vector<int> colour;        // per slab
+    int seg0 = 0;                   // index of its first slab segment
+};
+
 }  // namespace
 
 struct bd3mg_ctx {
-    bd3mg_params p{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     bd3mg_allocator alloc{};
@@ -43,25 +61,22 @@ struct bd3mg_ctx {
     bd3mg_status sticky = BD3MG_OK;
 
     const KernelSet *ks = nullptr;
-    int rz = 0;                   // PSF z radius (before padding)
-    int nslabs = 1;
-    std::vector<int> bounds;      // nslabs+1
-    std::vector<int> colour;      // per slab
+    std::vector<VolState> V;
+    int nvol = 0;
+    bool any_slabs = false;         // some volume has more than one slab
     int ncolours = 1;
-    long long n = 0;
+    int nslab_segs = 0;             // segments [0, nslab_segs) are slabs; then one full segment per volume
+    int zchunk = 0;                 // user override (0 = automatic)
+    double pinv_rtol = 1e-12;
 
-    // device state (volumes pitched: rows of `pitch` floats, pitch % 4 == 0)
-    int pitch = 0;
-    size_t np = 0;                // pitch*ny*nz
-    float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
-    float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch (lazy)
-    float *fx = nullptr, *fy = nullptr, *fz = nullptr;
-    VolDev *vols = nullptr;       // [0] = problem, [1] = scratch for operator calls
-    VolMaps *maps = nullptr;      // TMA descriptors, same indexing as vols
-    SegDev *segs = nullptr;       // [0..nslabs-1] slabs, [nslabs] full volume
+    // device state
+    float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch for volume 0 (lazy)
+    VolDev *vols = nullptr;         // [0, nvol) volumes, [nvol] scratch for operator calls
+    VolMaps *maps = nullptr;        // TMA descriptors, same indexing as vols
+    SegDev *segs = nullptr;
     Item *items = nullptr;
     int *slot_beg = nullptr, *slot_id = nullptr;
-    int *seg_lists = nullptr;     // per colour: slab indices (k_update)
+    int *seg_lists = nullptr;       // per colour: slab segments (k_update)
     double *partials = nullptr;
     unsigned int *ticket = nullptr;
     double *u = nullptr, *info = nullptr, *fout = nullptr;
@@ -70,14 +85,14 @@ struct bd3mg_ctx {
     int trace_cap = 0;
     int *counter = nullptr, *status = nullptr;
 
-    VolDev vol_h{};
+    std::vector<SegDev> segs_h;
     std::vector<Item> items_h;
     std::vector<int> slot_beg_h, slot_id_h, seg_lists_h, seg_list_off;
     Launch L_obj, L_res_full, L_grad_full;
     std::vector<Launch> L_res, L_grad, L_curv;
     int max_items = 0;
-    int sms = 152;                // SM count of the device
-    int occ[3] = {1, 1, 1};       // resident CTAs per SM: residual, gradient, curvature
+    int sms = 152;                  // SM count of the device
+    int occ[3] = {1, 1, 1};         // resident CTAs per SM: residual, gradient, curvature
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -130,33 +145,35 @@ bd3mg_status dalloc_n(bd3mg_ctx *c, T **p, size_t count) {
     return dalloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
 }
 
-// Staged-tile extents of a kernel set (must match Geo<R,RZ> in kernels.cuh).
+// Staged-tile x halo of a kernel set (must match Geo<R,RZ,TY>::XH in kernels.cuh).
 int set_xh(const KernelSet *k) { return k->R <= 4 ? 4 : 8; }
 
 // Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
 int tile_y(int kind) { return kind == 2 ? TY_C : TY_A; }
 
-bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const float *x, const float *r, const float *g, const float *d) {
-    const bd3mg_params &p = c->p;
+bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const float *x, const float *r,
+                     const float *g, const float *d) {
+    const bd3mg_params &p = v.p;
     const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks);
     std::memset(vm, 0, sizeof(*vm));
     bool ok = true;
-    if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, p.nx, p.ny, p.nz, c->pitch, bx, TY_A + 2 * R);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, p.nx, p.ny, p.nz, c->pitch, BX1, TY_A + 2);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, p.nx, p.ny, p.nz, c->pitch, BX1, TY_C + 2);
-    if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, p.nx, p.ny, p.nz, c->pitch, bx, TY_A + 2 * R);
-    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
-    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, p.nx, p.ny, p.nz, c->pitch, bx, TY_C + 2 * R);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, p.nx, p.ny, p.nz, v.pitch, BX1, TY_A + 2);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, p.nx, p.ny, p.nz, v.pitch, BX1, TY_C + 2);
+    if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, p.nx, p.ny, p.nz, v.pitch, bx, TY_C + 2 * R);
+    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, p.nx, p.ny, p.nz, v.pitch, bx, TY_C + 2 * R);
     return ok;
 }
 
-int ntiles(const bd3mg_ctx *c, int ty) { return ((c->p.nx + TX - 1) / TX) * ((c->p.ny + ty - 1) / ty); }
+int ntiles_of(const VolState &v, int ty) { return ((v.p.nx + TX - 1) / TX) * ((v.p.ny + ty - 1) / ty); }
 
 // Items of one segment: its output range split into nch balanced z-chunks,
 // each chunk crossed with every xy tile (chunk-major, so concurrently running
 // CTAs share halo slices in L2).
 void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi, int zc, int ty) {
-    const int ntx = (c->p.nx + TX - 1) / TX, nty = (c->p.ny + ty - 1) / ty;
+    const VolState &v = c->V[c->segs_h[seg].vol];
+    const int ntx = (v.p.nx + TX - 1) / TX, nty = (v.p.ny + ty - 1) / ty;
     const int len = zhi - zlo;
     if (len <= 0) return;
     const int nch = (len + zc - 1) / zc;
@@ -169,54 +186,66 @@ void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi, int zc, int ty) {
 
 // z-chunk for a launch: minimise (waves of resident CTAs) x (longest chunk +
 // z halo), the makespan of equal-cost items; ties go to longer chunks.
-int choose_zchunk(const bd3mg_ctx *c, const std::vector<std::pair<int, int>> &ranges, int kind) {
-    if (c->p.zchunk > 0) return std::min(c->p.zchunk, ZC_MAX);
-    return bd3mg::choose_zchunk((long long)c->sms * std::max(1, c->occ[kind]), ntiles(c, tile_y(kind)),
-                                2 * c->ks->RZ, ranges);
+int choose_zc(const bd3mg_ctx *c, const std::vector<std::array<int, 3>> &ranges /* lo, hi, ntiles */, int kind) {
+    if (c->zchunk > 0) return std::min(c->zchunk, ZC_MAX);
+    const long long slots = (long long)c->sms * std::max(1, c->occ[kind]);
+    const int halo = 2 * c->ks->RZ;
+    long long best_cost = -1;
+    int best = 4;
+    for (int zc = 4; zc <= ZC_MAX; ++zc) {
+        long long items = 0;
+        int longest = 0;
+        for (auto &r : ranges) {
+            const int len = r[1] - r[0];
+            if (len <= 0) continue;
+            const int nch = (len + zc - 1) / zc;
+            items += (long long)nch * r[2];
+            longest = std::max(longest, (len + nch - 1) / nch);
+        }
+        const long long cost = ((items + slots - 1) / slots) * (longest + halo);
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
 }
 
-// Build one launch over the given segments, each with output range f(seg).
+enum SlotMode { SLOTS_NONE, SLOTS_PER_VOLUME, SLOTS_PER_SEGMENT };
+
+// One launch over the given segments, each with output range range(seg).
+// Segments must be grouped by volume when slots are per volume.
 template <typename F>
-Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, bool slots, int slot_of_vol, int kind) {
-    std::vector<std::pair<int, int>> ranges;
+Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode slots, int kind) {
+    std::vector<std::array<int, 3>> ranges;
     for (int s : segs) {
         int lo, hi;
         range(s, &lo, &hi);
-        ranges.emplace_back(lo, hi);
+        ranges.push_back({lo, hi, ntiles_of(c->V[c->segs_h[s].vol], tile_y(kind))});
     }
-    const int zc = choose_zchunk(c, ranges, kind);
+    const int zc = choose_zc(c, ranges, kind);
     Launch L;
     L.item_off = (int)c->items_h.size();
     L.beg_off = (int)c->slot_beg_h.size();
     L.slot_off = (int)c->slot_id_h.size();
-    int base = L.item_off;
-    if (slot_of_vol >= 0) {
-        for (int s : segs) {
-            int lo, hi;
-            range(s, &lo, &hi);
-            add_items(c, s, lo, hi, zc, tile_y(kind));
+    const int base = L.item_off;
+    int last_vol = -1;
+    for (size_t i = 0; i < segs.size(); ++i) {
+        const int s = segs[i];
+        const int beg = (int)c->items_h.size() - base;
+        if (slots == SLOTS_PER_SEGMENT) {
+            c->slot_beg_h.push_back(beg);
+            c->slot_id_h.push_back(s);
+        } else if (slots == SLOTS_PER_VOLUME && c->segs_h[s].vol != last_vol) {
+            c->slot_beg_h.push_back(beg);
+            c->slot_id_h.push_back(c->segs_h[s].vol);
+            last_vol = c->segs_h[s].vol;
         }
-        if (slots) {
-            c->slot_beg_h.push_back(0);
-            c->slot_beg_h.push_back((int)c->items_h.size() - base);
-            c->slot_id_h.push_back(slot_of_vol);
-            L.nslots = 1;
-        }
-    } else {
-        for (int s : segs) {
-            int lo, hi;
-            range(s, &lo, &hi);
-            const int beg = (int)c->items_h.size() - base;
-            add_items(c, s, lo, hi, zc, tile_y(kind));
-            if (slots) {
-                c->slot_beg_h.push_back(beg);
-                c->slot_id_h.push_back(s);
-            }
-        }
-        if (slots) {
-            c->slot_beg_h.push_back((int)c->items_h.size() - base);
-            L.nslots = (int)segs.size();
-        }
+        add_items(c, s, ranges[i][0], ranges[i][1], zc, tile_y(kind));
+    }
+    if (slots != SLOTS_NONE) {
+        L.nslots = (int)c->slot_id_h.size() - L.slot_off;
+        c->slot_beg_h.push_back((int)c->items_h.size() - base);
     }
     L.nitems = (int)c->items_h.size() - L.item_off;
     c->max_items = std::max(c->max_items, L.nitems);
@@ -240,11 +269,9 @@ KArgs make_args(bd3mg_ctx *c, const Launch &L, int mode, const VolDev *vols) {
     a.info = c->info;
     a.fout = c->fout;
     a.sh = c->sh;
-    a.pinv_rtol = c->p.pinv_rtol;
+    a.pinv_rtol = c->pinv_rtol;
     return a;
 }
-
-bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s);
 
 bd3mg_status check_launch(bd3mg_ctx *c) {
     cudaError_t e = cudaGetLastError();
@@ -252,22 +279,8 @@ bd3mg_status check_launch(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
-}  // namespace
-
-static bd3mg_status upload_plan(bd3mg_ctx *c) {
-    CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaMemcpyAsync(c->slot_beg, c->slot_beg_h.data(), sizeof(int) * c->slot_beg_h.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->slot_id, c->slot_id_h.data(), sizeof(int) * std::max<size_t>(1, c->slot_id_h.size()),
-                       cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->seg_lists, c->seg_lists_h.data(), sizeof(int) * c->seg_lists_h.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-    return BD3MG_OK;
-}
-
 // Event bracket of one launch while profiling (never inside a graph capture).
-static bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
+bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
     if (!c->prof_on) return BD3MG_OK;
     cudaEvent_t e;
     CK(cudaEventCreate(&e));
@@ -277,7 +290,7 @@ static bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
     return BD3MG_OK;
 }
 
-static bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
+bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
     KArgs a = make_args(c, L, mode, vols);
     bd3mg_status st = prof_mark(c, s, (mode & M_STORE_R) ? BD3MG_K_RESIDUAL : BD3MG_K_OBJECTIVE);
     if (st) return st;
@@ -285,7 +298,7 @@ static bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, 
     return check_launch(c);
 }
 
-static bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
+bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
     KArgs a = make_args(c, L, mode, vols);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
     if (st) return st;
@@ -293,7 +306,7 @@ static bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, 
     return check_launch(c);
 }
 
-static bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
+bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     KArgs a = make_args(c, L, 0, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
@@ -301,12 +314,14 @@ static bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L)
     return check_launch(c);
 }
 
-static bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
+bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     const int off = c->seg_list_off[colour], cnt = c->seg_list_off[colour + 1] - off;
+    if (cnt == 0) return BD3MG_OK;
     long long maxlen = 0;
     for (int k = 0; k < cnt; ++k) {
-        const int sidx = c->seg_lists_h[off + k];
-        maxlen = std::max<long long>(maxlen, (long long)(c->bounds[sidx + 1] - c->bounds[sidx]) * c->pitch * c->p.ny);
+        const SegDev &sg = c->segs_h[c->seg_lists_h[off + k]];
+        const VolState &v = c->V[sg.vol];
+        maxlen = std::max<long long>(maxlen, (long long)(sg.z1 - sg.z0) * v.pitch * v.p.ny);
     }
     long long blocks = (maxlen / 4 + NT - 1) / NT;
     blocks = std::max<long long>(1, std::min<long long>(blocks, 2048));
@@ -317,29 +332,28 @@ static bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     return check_launch(c);
 }
 
-namespace {
+// One iteration = one sweep over every volume's slabs, colour by colour.
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
-    if (c->nslabs == 1) {
+    if (!c->any_slabs) {
         if ((st = run_residual(c, s, c->L_res[0], M_STORE_R | M_OBJ | M_TRACE | M_ADVANCE))) return st;
     } else {
         if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
-        if (c->nslabs > 1 && (st = run_residual(c, s, c->L_res[col], M_STORE_R))) return st;
+        if (c->any_slabs && (st = run_residual(c, s, c->L_res[col], M_STORE_R))) return st;
         if ((st = run_gradient(c, s, c->L_grad[col], 0))) return st;
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
         if ((st = run_update(c, s, col))) return st;
     }
     return BD3MG_OK;
 }
-}  // namespace
 
-static bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
+bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
     if (need <= c->trace_cap) return BD3MG_OK;
-    int cap = std::max(need, 1024);
+    const int cap = std::max(need, 1024);
     double *t = nullptr;
-    bd3mg_status st = dalloc_n(c, &t, (size_t)cap);
+    bd3mg_status st = dalloc_n(c, &t, (size_t)cap * c->nvol);
     if (st) return st;
     Shared sh{t, cap, 0, c->counter, c->status};
     CK(cudaMemcpyAsync(c->sh, &sh, sizeof(Shared), cudaMemcpyHostToDevice, c->stream));
@@ -349,7 +363,7 @@ static bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
     return BD3MG_OK;
 }
 
-static bd3mg_status check_status(bd3mg_ctx *c) {
+bd3mg_status check_status(bd3mg_ctx *c) {
     int st = 0;
     CK(cudaMemcpyAsync(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -357,6 +371,272 @@ static bd3mg_status check_status(bd3mg_ctx *c) {
     if (st & ST_NONFINITE) return fail(c, BD3MG_ENONFINITE, "non-finite value in a subspace matrix or objective");
     return BD3MG_OK;
 }
+
+// Validate one volume's parameters (and its slab bounds) into v.
+bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolState &v) {
+    if (p.nx < 1 || p.ny < 1 || p.nz < 1)
+        return fail(c, BD3MG_EINVAL, "volume %d: extents must be >= 1", vi);
+    if (p.px < 1 || p.py < 1 || p.pz < 1 || !(p.px & 1) || !(p.py & 1) || !(p.pz & 1))
+        return fail(c, BD3MG_EINVAL, "volume %d: PSF extents must be odd and >= 1 (got %d x %d x %d)", vi, p.px, p.py,
+                    p.pz);
+    if (!p.psf) return fail(c, BD3MG_EINVAL, "volume %d: psf is NULL", vi);
+    if (!(p.lambda > 0) || !(p.delta > 0) || !(p.eta >= 0) || !(p.xmin <= p.xmax))
+        return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
+    if (p.precision != BD3MG_FP32)
+        return fail(c, BD3MG_EUNSUPPORTED, "precision mode %d is not available in this build", p.precision);
+    if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return fail(c, BD3MG_EINVAL, "volume %d too large", vi);
+    v.p = p;
+    const int ns = p.nslabs <= 1 ? 1 : p.nslabs;
+    v.bounds.clear();
+    if (ns == 1) {
+        v.bounds = {0, p.nz};
+    } else {
+        if (!p.slab_bounds) return fail(c, BD3MG_EINVAL, "volume %d: slab_bounds is NULL with nslabs = %d", vi, ns);
+        for (int s = 0; s <= ns; ++s) v.bounds.push_back(p.slab_bounds[s]);
+        if (v.bounds.front() != 0 || v.bounds.back() != p.nz)
+            return fail(c, BD3MG_EINVAL, "volume %d: slab bounds must run from 0 to nz", vi);
+        for (int s = 0; s < ns; ++s)
+            if (v.bounds[s + 1] <= v.bounds[s]) return fail(c, BD3MG_EINVAL, "volume %d: slab bounds must increase", vi);
+    }
+    v.p.slab_bounds = nullptr;
+    return BD3MG_OK;
+}
+
+// Shared body of bd3mg_create and bd3mg_batch_create.
+bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const float *const *ys,
+                         const float *const *x0s, int data_on_device) {
+    if (nvol < 1) return fail(c, BD3MG_EINVAL, "need at least one volume");
+    c->nvol = nvol;
+    c->V.resize(nvol);
+    bd3mg_status st;
+    int R = 1, RZ = 1;
+    for (int v = 0; v < nvol; ++v) {
+        if (!ys || !ys[v]) return fail(c, BD3MG_EINVAL, "y of volume %d is NULL", v);
+        if ((st = validate_volume(c, pp[v], v, c->V[v]))) return st;
+        R = std::max(R, std::max((pp[v].px - 1) / 2, (pp[v].py - 1) / 2));
+        RZ = std::max(RZ, (pp[v].pz - 1) / 2);
+    }
+    c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
+    c->zchunk = pp[0].zchunk;
+
+    // kernels for the PSF radii (all volumes share one compiled set; smaller PSFs are zero padded)
+    c->ks = find_kernel_set(R, RZ);
+    if (!c->ks) return fail(c, BD3MG_EUNSUPPORTED, "no kernels for PSF radii (%d, %d); max 5", R, RZ);
+    std::vector<std::vector<float>> FX(nvol), FY(nvol), FZ(nvol);
+    for (int v = 0; v < nvol; ++v) {
+        double worst = 0.0;
+        if (!factor_psf(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v], &worst))
+            return fail(c, BD3MG_EUNSUPPORTED,
+                        "volume %d: PSF is not separable per depth (relative rank-1 residual %.3g > 1e-6); "
+                        "only separable PSFs are implemented", v, worst);
+        c->V[v].p.psf = nullptr;
+    }
+
+    // segments and colouring: slabs of one volume and colour are >= max(pz-1, 1) slices apart
+    c->ncolours = 1;
+    for (int v = 0; v < nvol; ++v) {
+        VolState &vs = c->V[v];
+        const int rz = (vs.p.pz - 1) / 2;
+        c->ncolours = std::max(c->ncolours, colour_slabs(vs.bounds, std::max(2 * rz, 1), vs.colour));
+        vs.seg0 = (int)c->segs_h.size();
+        for (size_t s = 0; s + 1 < vs.bounds.size(); ++s)
+            c->segs_h.push_back(SegDev{v, vs.bounds[s], vs.bounds[s + 1], (int)c->segs_h.size()});
+        if (vs.bounds.size() > 2) c->any_slabs = true;
+    }
+    c->nslab_segs = (int)c->segs_h.size();
+    for (int v = 0; v < nvol; ++v)
+        c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size()});
+
+    // occupancy of the chosen kernels (drives the z-chunk choice)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = c->ks->prepare();
+        if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e));
+        for (int k = 0; k < 3; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+    }
+
+    // work lists
+    const int RZk = c->ks->RZ;          // kernel z radius (padded), governs halos
+    const int Lk = std::max(RZk, 1);
+    std::vector<int> full;
+    for (int v = 0; v < nvol; ++v) full.push_back(c->nslab_segs + v);
+    auto whole = [&](int s, int *lo, int *hi) { *lo = 0; *hi = c->segs_h[s].z1; };
+    c->L_obj = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
+    c->L_res_full = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
+    c->L_grad_full = make_launch(c, full, whole, SLOTS_NONE, 1);
+    c->seg_list_off.push_back(0);
+    for (int col = 0; col < c->ncolours; ++col) {
+        std::vector<int> segs;
+        for (int v = 0; v < nvol; ++v)
+            for (size_t s = 0; s < c->V[v].colour.size(); ++s)
+                if (c->V[v].colour[s] == col) segs.push_back(c->V[v].seg0 + (int)s);
+        auto nzof = [&](int s) { return c->V[c->segs_h[s].vol].p.nz; };
+        if (!c->any_slabs)
+            c->L_res.push_back(make_launch(c, segs, whole, SLOTS_PER_VOLUME, 0));
+        else
+            c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+                *lo = std::max(0, c->segs_h[s].z0 - RZk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
+                SLOTS_NONE, 0));
+        c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1));
+        c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+            *lo = std::max(0, c->segs_h[s].z0 - Lk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
+            SLOTS_PER_SEGMENT, 2));
+        for (int s : segs) c->seg_lists_h.push_back(s);
+        c->seg_list_off.push_back((int)c->seg_lists_h.size());
+    }
+
+    cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return fail(c, BD3MG_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(ce));
+
+    // device allocations
+    const size_t nseg = c->segs_h.size();
+#define AL(ptr, cnt) if ((st = dalloc_n(c, &(ptr), (cnt)))) return st
+    for (int v = 0; v < nvol; ++v) {
+        VolState &vs = c->V[v];
+        vs.pitch = (vs.p.nx + 3) & ~3;
+        vs.np = (size_t)vs.pitch * vs.p.ny * vs.p.nz;
+        AL(vs.x, vs.np); AL(vs.d, vs.np); AL(vs.g, vs.np); AL(vs.r, vs.np); AL(vs.y, vs.np);
+        AL(vs.fx, FX[v].size()); AL(vs.fy, FY[v].size()); AL(vs.fz, FZ[v].size());
+    }
+    AL(c->vols, nvol + 1); AL(c->maps, nvol + 1); AL(c->segs, nseg);
+    AL(c->items, c->items_h.size());
+    AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
+    AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
+    AL(c->partials, (size_t)c->max_items * 9);
+    AL(c->ticket, 1); AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
+    AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1);
+#undef AL
+
+    // data and descriptors
+    const cudaMemcpyKind kin = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    std::vector<VolDev> vd(nvol + 1);
+    std::vector<VolMaps> vm(nvol + 1);
+    for (int v = 0; v < nvol; ++v) {
+        VolState &vs = c->V[v];
+        const bd3mg_params &p = vs.p;
+        const size_t wb = (size_t)p.nx * 4, pb = (size_t)vs.pitch * 4, rows = (size_t)p.ny * p.nz;
+        CK(cudaMemsetAsync(vs.y, 0, vs.np * 4, c->stream));
+        CK(cudaMemsetAsync(vs.x, 0, vs.np * 4, c->stream));
+        CK(cudaMemcpy2DAsync(vs.y, pb, ys[v], wb, wb, rows, kin, c->stream));
+        const float *x0 = (x0s && x0s[v]) ? x0s[v] : ys[v];
+        CK(cudaMemcpy2DAsync(vs.x, pb, x0, wb, wb, rows, kin, c->stream));
+        CK(cudaMemsetAsync(vs.d, 0, vs.np * 4, c->stream));
+        CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
+        CK(cudaMemsetAsync(vs.r, 0, vs.np * 4, c->stream));
+        CK(cudaMemcpyAsync(vs.fx, FX[v].data(), FX[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(vs.fz, FZ[v].data(), FZ[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
+        VolDev d{};
+        d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.pitch = vs.pitch;
+        d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
+        d.plane = (long long)vs.pitch * p.ny;
+        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y;
+        d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
+        d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
+        d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
+        d.lam_d = p.lambda; d.eta_d = p.eta;
+        vs.dev = d;
+        vd[v] = d;
+        if (!encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d))
+            return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
+    }
+    vd[nvol] = vd[0];
+    vm[nvol] = vm[0];
+    CK(cudaMemcpyAsync(c->vols, vd.data(), sizeof(VolDev) * vd.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->maps, vm.data(), sizeof(VolMaps) * vm.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->segs, c->segs_h.data(), sizeof(SegDev) * nseg, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->slot_beg, c->slot_beg_h.data(), sizeof(int) * c->slot_beg_h.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    if (!c->slot_id_h.empty())
+        CK(cudaMemcpyAsync(c->slot_id, c->slot_id_h.data(), sizeof(int) * c->slot_id_h.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    if (!c->seg_lists_h.empty())
+        CK(cudaMemcpyAsync(c->seg_lists, c->seg_lists_h.data(), sizeof(int) * c->seg_lists_h.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->ticket, 0, 4, c->stream));
+    CK(cudaMemsetAsync(c->u, 0, 16 * nseg, c->stream));
+    CK(cudaMemsetAsync(c->info, 0, 64 * nseg, c->stream));
+    CK(cudaMemsetAsync(c->counter, 0, 4, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, 4, c->stream));
+    // the host copies above read pageable and stack memory: finish them before returning
+    CK(cudaStreamSynchronize(c->stream));
+    if ((st = ensure_trace(c, 1024))) return st;
+
+    // capture one iteration as a graph
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+    bd3mg_status es = enqueue_iteration(c, c->cap_stream);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &gr);
+    if (es) {
+        if (gr) cudaGraphDestroy(gr);
+        return es;
+    }
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "end capture: %s", cudaGetErrorString(e));
+    c->graph = gr;
+    e = cudaGraphInstantiate(&c->exec, gr, 0);
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return BD3MG_OK;
+}
+
+// Copy between a caller volume (rows of nx floats) and a library volume (rows of pitch floats).
+bd3mg_status copy_vol(bd3mg_ctx *c, const VolState &v, float *dst, const float *src, int on_device, bool to_lib) {
+    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_lib ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
+    const size_t wb = (size_t)v.p.nx * 4, pb = (size_t)v.pitch * 4, rows = (size_t)v.p.ny * v.p.nz;
+    if (to_lib) CK(cudaMemcpy2DAsync(dst, pb, src, wb, wb, rows, k, c->stream));
+    else CK(cudaMemcpy2DAsync(dst, wb, src, pb, wb, rows, k, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return BD3MG_OK;
+}
+
+// H or H^T of volume 0's operator applied to a caller device volume.
+bd3mg_status apply_op(bd3mg_ctx *c, const float *in, float *out, bool adjoint) {
+    if (!in || !out || in == out) return fail(c, BD3MG_EINVAL, "apply: in/out NULL or aliased");
+    const VolState &v0 = c->V[0];
+    bd3mg_status st;
+    if (!c->scr_in) {
+        if ((st = dalloc_n(c, &c->scr_in, v0.np)) || (st = dalloc_n(c, &c->scr_out, v0.np))) return st;
+        CK(cudaMemsetAsync(c->scr_in, 0, v0.np * 4, c->stream));
+        CK(cudaMemsetAsync(c->scr_out, 0, v0.np * 4, c->stream));
+    }
+    if ((st = copy_vol(c, v0, c->scr_in, in, 1, true))) return st;
+    VolDev v = v0.dev;
+    v.y = nullptr;
+    VolMaps vm;
+    bool ok;
+    if (adjoint) {
+        v.r = c->scr_in;
+        v.g = c->scr_out;
+        ok = encode_vol_maps(&vm, c, v0, nullptr, c->scr_in, nullptr, nullptr);
+    } else {
+        v.x = c->scr_in;
+        v.r = c->scr_out;
+        ok = encode_vol_maps(&vm, c, v0, c->scr_in, nullptr, nullptr, nullptr);
+    }
+    if (!ok) return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed");
+    const int sv = c->nvol;                        // scratch descriptor slot
+    CK(cudaMemcpyAsync(c->vols + sv, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->maps + sv, &vm, sizeof(vm), cudaMemcpyHostToDevice, c->stream));
+    // Volume 0's items come first in the full-volume launches: run just those,
+    // with the descriptor table shifted so that volume index 0 reads the scratch.
+    Launch L = adjoint ? c->L_grad_full : c->L_res_full;
+    int n0 = 0;
+    while (n0 < L.nitems && c->segs_h[c->items_h[L.item_off + n0].seg].vol == 0) ++n0;
+    L.nitems = n0;
+    L.nslots = 0;
+    st = adjoint ? run_gradient(c, c->stream, L, M_HT_ONLY, c->vols + sv)
+                 : run_residual(c, c->stream, L, M_STORE_R, c->vols + sv);
+    if (st) return st;
+    if ((st = copy_vol(c, v0, out, c->scr_out, 1, false))) return st;
+    return check_status(c);
+}
+
+}  // namespace
 
 #define GUARD(c)                                                                        \
     do {                                                                                \
@@ -412,200 +692,35 @@ void bd3mg_destroy(bd3mg_ctx *c) {
     delete c;
 }
 
-bd3mg_status bd3mg_create(const bd3mg_params *pp, const float *y, const float *x0, int data_on_device,
-                          void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out) {
-    if (!out) return BD3MG_EINVAL;
-    *out = nullptr;
+static bd3mg_ctx *new_ctx(void *stream, const bd3mg_allocator *alloc) {
     bd3mg_ctx *c = new bd3mg_ctx();
     c->stream = (cudaStream_t)stream;
-    auto bail = [&](bd3mg_status s) {
-        // keep the context so the caller can read the message, but poisoned
-        *out = c;
-        return s;
-    };
-    if (!pp) return bail(fail(c, BD3MG_EINVAL, "params is NULL"));
-    if (!y) return bail(fail(c, BD3MG_EINVAL, "y is NULL"));
-    c->p = *pp;
-    bd3mg_params &p = c->p;
-    if (p.nx < 1 || p.ny < 1 || p.nz < 1) return bail(fail(c, BD3MG_EINVAL, "volume extents must be >= 1"));
-    if (p.px < 1 || p.py < 1 || p.pz < 1 || !(p.px & 1) || !(p.py & 1) || !(p.pz & 1))
-        return bail(fail(c, BD3MG_EINVAL, "PSF extents must be odd and >= 1 (got %d x %d x %d)", p.px, p.py, p.pz));
-    if (!p.psf) return bail(fail(c, BD3MG_EINVAL, "psf is NULL"));
-    if (!(p.lambda > 0) || !(p.delta > 0) || !(p.eta >= 0) || !(p.xmin <= p.xmax))
-        return bail(fail(c, BD3MG_EINVAL, "need lambda > 0, delta > 0, eta >= 0, xmin <= xmax"));
-    if (p.precision != BD3MG_FP32)
-        return bail(fail(c, BD3MG_EUNSUPPORTED, "precision mode %d is not available in this build", p.precision));
-    if (p.pinv_rtol <= 0) p.pinv_rtol = 1e-12;
-    if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return bail(fail(c, BD3MG_EINVAL, "volume too large"));
-    c->n = (long long)p.nx * p.ny * p.nz;
-
-    // slabs
-    c->nslabs = p.nslabs <= 1 ? 1 : p.nslabs;
-    c->bounds.clear();
-    if (c->nslabs == 1) {
-        c->bounds = {0, p.nz};
-    } else {
-        if (!p.slab_bounds) return bail(fail(c, BD3MG_EINVAL, "slab_bounds is NULL with nslabs = %d", p.nslabs));
-        for (int s = 0; s <= c->nslabs; ++s) c->bounds.push_back(p.slab_bounds[s]);
-        if (c->bounds.front() != 0 || c->bounds.back() != p.nz)
-            return bail(fail(c, BD3MG_EINVAL, "slab bounds must run from 0 to nz"));
-        for (int s = 0; s < c->nslabs; ++s)
-            if (c->bounds[s + 1] <= c->bounds[s]) return bail(fail(c, BD3MG_EINVAL, "slab bounds must increase"));
-    }
-    p.slab_bounds = nullptr;
-
-    // kernels for the PSF radii
-    const int R = std::max(std::max((p.px - 1) / 2, (p.py - 1) / 2), 1);
-    c->rz = (p.pz - 1) / 2;
-    c->ks = find_kernel_set(R, std::max(c->rz, 1));
-    if (!c->ks)
-        return bail(fail(c, BD3MG_EUNSUPPORTED, "no kernels for PSF radii (%d, %d); max 5", R, c->rz));
-    std::vector<float> fx, fy, fz;
-    double worst = 0.0;
-    if (!factor_psf(p, c->ks->R, c->ks->RZ, fx, fy, fz, &worst))
-        return bail(fail(c, BD3MG_EUNSUPPORTED,
-                         "PSF is not separable per depth (relative rank-1 residual %.3g > 1e-6); "
-                         "only separable PSFs are implemented", worst));
-    p.psf = nullptr;
-
-    // colouring: slabs of one colour at least max(2*rz, 1) slices apart
-    c->ncolours = colour_slabs(c->bounds, std::max(2 * c->rz, 1), c->colour);
-
-    // occupancy of the chosen kernels (drives the z-chunk choice)
-    {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = c->ks->prepare();
-        if (e != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e)));
-        for (int k = 0; k < 3; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
-    }
-
-    // work lists
-    const int RZk = c->ks->RZ;          // kernel z radius (padded), governs halos
-    const int Lk = std::max(RZk, 1);
-    const int nz = p.nz;
-    std::vector<int> all_slabs;
-    for (int s = 0; s < c->nslabs; ++s) all_slabs.push_back(s);
-    const int FULL = c->nslabs;          // full-volume segment index
-    c->L_obj = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0);
-    c->L_res_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0);
-    c->L_grad_full = make_launch(c, {FULL}, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, false, 0, 1);
-    c->seg_list_off.push_back(0);
-    for (int col = 0; col < c->ncolours; ++col) {
-        std::vector<int> segs;
-        for (int s = 0; s < c->nslabs; ++s)
-            if (c->colour[s] == col) segs.push_back(s);
-        auto &B = c->bounds;
-        if (c->nslabs == 1)
-            c->L_res.push_back(make_launch(c, segs, [&](int, int *lo, int *hi) { *lo = 0; *hi = nz; }, true, 0, 0));
-        else
-            c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-                *lo = std::max(0, B[s] - RZk); *hi = std::min(nz, B[s + 1] + RZk); }, false, -1, 0));
-        c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) { *lo = B[s]; *hi = B[s + 1]; },
-                                        false, -1, 1));
-        c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = std::max(0, B[s] - Lk); *hi = std::min(nz, B[s + 1] + RZk); }, true, -1, 2));
-        for (int s : segs) c->seg_lists_h.push_back(s);
-        c->seg_list_off.push_back((int)c->seg_lists_h.size());
-    }
-
-    cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
-    if (ce != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(ce)));
     if (alloc && alloc->alloc && alloc->free) {
         c->alloc = *alloc;
         c->has_alloc = true;
     }
-
-    // device allocations
-    c->pitch = (p.nx + 3) & ~3;
-    c->np = (size_t)c->pitch * p.ny * p.nz;
-    const size_t N = c->np;
-    bd3mg_status st = BD3MG_OK;
-#define AL(ptr, cnt) if ((st = dalloc_n(c, &(ptr), (cnt)))) return bail(st)
-    AL(c->x, N); AL(c->d, N); AL(c->g, N); AL(c->r, N); AL(c->y, N);
-    AL(c->fx, fx.size()); AL(c->fy, fy.size()); AL(c->fz, fz.size());
-    AL(c->vols, 2); AL(c->maps, 2); AL(c->segs, c->nslabs + 1);
-    AL(c->items, c->items_h.size());
-    AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
-    AL(c->seg_lists, c->seg_lists_h.size());
-    AL(c->partials, (size_t)c->max_items * 9);
-    AL(c->ticket, 1); AL(c->u, 2 * (c->nslabs + 1)); AL(c->info, 8 * (c->nslabs + 1)); AL(c->fout, 8);
-    AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1);
-#undef AL
-    const cudaMemcpyKind kin = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    {
-        bd3mg_ctx *cc = c;
-        auto ck = [&](cudaError_t e, const char *what) -> bool {
-            if (e == cudaSuccess) return true;
-            fail(cc, BD3MG_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-            return false;
-        };
-        const size_t wb = (size_t)p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)p.ny * p.nz;
-        if (!ck(cudaMemsetAsync(c->y, 0, N * 4, c->stream), "zero y") ||
-            !ck(cudaMemsetAsync(c->x, 0, N * 4, c->stream), "zero x"))
-            return bail(c->sticky);
-        if (!ck(cudaMemcpy2DAsync(c->y, pb, y, wb, wb, rows, kin, c->stream), "copy y")) return bail(c->sticky);
-        if (!ck(cudaMemcpy2DAsync(c->x, pb, x0 ? x0 : y, wb, wb, rows, kin, c->stream), "copy x0"))
-            return bail(c->sticky);
-        if (!ck(cudaMemsetAsync(c->d, 0, N * 4, c->stream), "zero d")) return bail(c->sticky);
-        if (!ck(cudaMemsetAsync(c->g, 0, N * 4, c->stream), "zero g")) return bail(c->sticky);
-        if (!ck(cudaMemsetAsync(c->r, 0, N * 4, c->stream), "zero r")) return bail(c->sticky);
-        if (!ck(cudaMemcpyAsync(c->fx, fx.data(), fx.size() * 4, cudaMemcpyHostToDevice, c->stream), "copy fx") ||
-            !ck(cudaMemcpyAsync(c->fy, fy.data(), fy.size() * 4, cudaMemcpyHostToDevice, c->stream), "copy fy") ||
-            !ck(cudaMemcpyAsync(c->fz, fz.data(), fz.size() * 4, cudaMemcpyHostToDevice, c->stream), "copy fz"))
-            return bail(c->sticky);
-        VolDev v{};
-        v.nx = p.nx; v.ny = p.ny; v.nz = p.nz; v.pitch = c->pitch;
-        v.kxy = 2 * c->ks->R + 1; v.kz = 2 * c->ks->RZ + 1;
-        v.plane = (long long)c->pitch * p.ny;
-        v.x = c->x; v.d = c->d; v.g = c->g; v.r = c->r; v.y = c->y;
-        v.fx = c->fx; v.fy = c->fy; v.fz = c->fz;
-        v.lam = (float)p.lambda; v.delta2 = (float)(p.delta * p.delta); v.eta2 = (float)(2.0 * p.eta);
-        v.xmin = (float)p.xmin; v.xmax = (float)p.xmax;
-        v.lam_d = p.lambda; v.eta_d = p.eta;
-        c->vol_h = v;
-        VolDev vv[2] = {v, v};
-        std::vector<SegDev> sg;
-        for (int s = 0; s < c->nslabs; ++s) sg.push_back(SegDev{0, c->bounds[s], c->bounds[s + 1], s});
-        sg.push_back(SegDev{0, 0, nz, c->nslabs});
-        VolMaps vm[2];
-        if (!encode_vol_maps(&vm[0], c, c->x, c->r, c->g, c->d))
-            return bail(fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)"));
-        vm[1] = vm[0];
-        if (!ck(cudaMemcpyAsync(c->maps, vm, sizeof(vm), cudaMemcpyHostToDevice, c->stream), "copy maps") ||
-            !ck(cudaMemcpyAsync(c->vols, vv, sizeof(vv), cudaMemcpyHostToDevice, c->stream), "copy vols") ||
-            !ck(cudaMemcpyAsync(c->segs, sg.data(), sizeof(SegDev) * sg.size(), cudaMemcpyHostToDevice, c->stream),
-                "copy segs"))
-            return bail(c->sticky);
-        if ((st = upload_plan(c))) return bail(st);
-        if (!ck(cudaMemsetAsync(c->ticket, 0, 4, c->stream), "zero ticket") ||
-            !ck(cudaMemsetAsync(c->u, 0, 16 * (c->nslabs + 1), c->stream), "zero u") ||
-            !ck(cudaMemsetAsync(c->info, 0, 64 * (c->nslabs + 1), c->stream), "zero info") ||
-            !ck(cudaMemsetAsync(c->counter, 0, 4, c->stream), "zero counter") ||
-            !ck(cudaMemsetAsync(c->status, 0, 4, c->stream), "zero status"))
-            return bail(c->sticky);
-        // host copies above read pageable/stack memory: finish them before returning
-        if (!ck(cudaStreamSynchronize(c->stream), "sync")) return bail(c->sticky);
-    }
-    if ((st = ensure_trace(c, 1024))) return bail(st);
-
-    // capture one iteration as a graph
-    {
-        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e)));
-        bd3mg_status es = enqueue_iteration(c, c->cap_stream);
-        cudaGraph_t gr = nullptr;
-        e = cudaStreamEndCapture(c->cap_stream, &gr);
-        if (es) { if (gr) cudaGraphDestroy(gr); return bail(es); }
-        if (e != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "end capture: %s", cudaGetErrorString(e)));
-        c->graph = gr;
-        e = cudaGraphInstantiate(&c->exec, gr, 0);
-        if (e != cudaSuccess) return bail(fail(c, BD3MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)));
-    }
-    *out = c;
-    return BD3MG_OK;
+    return c;
 }
+
+bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
+                          void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out) {
+    if (!out) return BD3MG_EINVAL;
+    bd3mg_ctx *c = new_ctx(stream, alloc);
+    *out = c;                     // returned even on failure so the caller can read the message
+    if (!p) return fail(c, BD3MG_EINVAL, "params is NULL");
+    return create_impl(c, 1, p, &y, &x0, data_on_device);
+}
+
+bd3mg_status bd3mg_batch_create(int nvol, const bd3mg_params *p, const float *const *y, const float *const *x0,
+                                int data_on_device, void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out) {
+    if (!out) return BD3MG_EINVAL;
+    bd3mg_ctx *c = new_ctx(stream, alloc);
+    *out = c;
+    if (!p || !y) return fail(c, BD3MG_EINVAL, "params or y is NULL");
+    return create_impl(c, nvol, p, y, x0, data_on_device);
+}
+
+int bd3mg_volume_count(bd3mg_ctx *c) { return c ? c->nvol : 0; }
 
 bd3mg_status bd3mg_iterate_async(bd3mg_ctx *c, int n) {
     GUARD(c);
@@ -624,7 +739,9 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
     c->iterations += n;
     if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ | M_TRACE))) return st;
-    if (f_trace) CK(cudaMemcpyAsync(f_trace, c->trace, sizeof(double) * (n + 1), cudaMemcpyDeviceToHost, c->stream));
+    if (f_trace)
+        CK(cudaMemcpy2DAsync(f_trace, sizeof(double) * (n + 1), c->trace, sizeof(double) * c->trace_cap,
+                             sizeof(double) * (n + 1), c->nvol, cudaMemcpyDeviceToHost, c->stream));
     return check_status(c);
 }
 
@@ -640,14 +757,27 @@ bd3mg_status bd3mg_objective(bd3mg_ctx *c, double *f, double *parts) {
     return BD3MG_OK;
 }
 
+bd3mg_status bd3mg_objectives(bd3mg_ctx *c, double *f) {
+    GUARD(c);
+    if (!f) return fail(c, BD3MG_EINVAL, "f is NULL");
+    bd3mg_status st;
+    if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ))) return st;
+    std::vector<double> h(4 * (size_t)c->nvol);
+    CK(cudaMemcpyAsync(h.data(), c->fout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    if ((st = check_status(c))) return st;
+    for (int v = 0; v < c->nvol; ++v) f[v] = h[4 * v];
+    return BD3MG_OK;
+}
+
 bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     GUARD(c);
     bd3mg_status st;
     if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R | M_OBJ))) return st;
     if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
     if (g) {
-        const size_t wb = (size_t)c->p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)c->p.ny * c->p.nz;
-        CK(cudaMemcpy2DAsync(g, wb, c->g, pb, wb, rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+        const VolState &v = c->V[0];
+        const size_t wb = (size_t)v.p.nx * 4, pb = (size_t)v.pitch * 4, rows = (size_t)v.p.ny * v.p.nz;
+        CK(cudaMemcpy2DAsync(g, wb, v.g, pb, wb, rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
     }
     double h[4];
@@ -657,75 +787,50 @@ bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     return BD3MG_OK;
 }
 
-// Copy between a caller volume (rows of nx floats) and a library volume (rows of pitch floats).
-static bd3mg_status copy_vol(bd3mg_ctx *c, float *dst, const float *src, int on_device, bool to_lib) {
-    cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : (to_lib ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost);
-    const size_t wb = (size_t)c->p.nx * 4, pb = (size_t)c->pitch * 4, rows = (size_t)c->p.ny * c->p.nz;
-    if (to_lib) CK(cudaMemcpy2DAsync(dst, pb, src, wb, wb, rows, k, c->stream));
-    else CK(cudaMemcpy2DAsync(dst, wb, src, pb, wb, rows, k, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    return BD3MG_OK;
+bd3mg_status bd3mg_get_volume(bd3mg_ctx *c, int vol, int which, float *dst, int on_device) {
+    GUARD(c);
+    if (!dst || vol < 0 || vol >= c->nvol || which < 0 || which > 2)
+        return fail(c, BD3MG_EINVAL, "get_volume: bad volume index, selector or NULL destination");
+    const VolState &v = c->V[vol];
+    const float *src = which == 0 ? v.x : which == 1 ? v.d : v.g;
+    return copy_vol(c, v, dst, src, on_device, false);
 }
 
-bd3mg_status bd3mg_get_x(bd3mg_ctx *c, float *x, int on_device) {
-    GUARD(c);
-    if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
-    return copy_vol(c, x, c->x, on_device, false);
-}
-
-bd3mg_status bd3mg_get_d(bd3mg_ctx *c, float *d, int on_device) {
-    GUARD(c);
-    if (!d) return fail(c, BD3MG_EINVAL, "d is NULL");
-    return copy_vol(c, d, c->d, on_device, false);
-}
+bd3mg_status bd3mg_get_x(bd3mg_ctx *c, float *x, int on_device) { return bd3mg_get_volume(c, 0, 0, x, on_device); }
+bd3mg_status bd3mg_get_d(bd3mg_ctx *c, float *d, int on_device) { return bd3mg_get_volume(c, 0, 1, d, on_device); }
 
 bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     GUARD(c);
     if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
-    CK(cudaMemsetAsync(c->d, 0, c->np * 4, c->stream));
-    return copy_vol(c, c->x, x, on_device, true);
+    const VolState &v = c->V[0];
+    CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
+    return copy_vol(c, v, v.x, x, on_device, true);
 }
 
 bd3mg_status bd3mg_last_step(bd3mg_ctx *c, double *info) {
     GUARD(c);
     if (!info) return fail(c, BD3MG_EINVAL, "info is NULL");
-    CK(cudaMemcpyAsync(info, c->info, sizeof(double) * 8 * c->nslabs, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(info, c->info, sizeof(double) * 8 * c->nslab_segs, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     return BD3MG_OK;
 }
 
-static bd3mg_status apply_op(bd3mg_ctx *c, const float *in, float *out, bool adjoint) {
+bd3mg_status bd3mg_apply_H(bd3mg_ctx *c, const float *in, float *out) {
     GUARD(c);
-    if (!in || !out || in == out) return fail(c, BD3MG_EINVAL, "apply: in/out NULL or aliased");
-    bd3mg_status st;
-    if (!c->scr_in) {
-        if ((st = dalloc_n(c, &c->scr_in, c->np)) || (st = dalloc_n(c, &c->scr_out, c->np))) return st;
-        CK(cudaMemsetAsync(c->scr_in, 0, c->np * 4, c->stream));
-        CK(cudaMemsetAsync(c->scr_out, 0, c->np * 4, c->stream));
-    }
-    if ((st = copy_vol(c, c->scr_in, in, 1, true))) return st;
-    VolDev v = c->vol_h;
-    v.y = nullptr;
-    VolMaps vm;
-    bool ok;
-    if (adjoint) { v.r = c->scr_in; v.g = c->scr_out; ok = encode_vol_maps(&vm, c, nullptr, c->scr_in, nullptr, nullptr); }
-    else { v.x = c->scr_in; v.r = c->scr_out; ok = encode_vol_maps(&vm, c, c->scr_in, nullptr, nullptr, nullptr); }
-    if (!ok) return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed");
-    CK(cudaMemcpyAsync(c->vols + 1, &v, sizeof(v), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->maps + 1, &vm, sizeof(vm), cudaMemcpyHostToDevice, c->stream));
-    st = adjoint ? run_gradient(c, c->stream, c->L_grad_full, M_HT_ONLY, c->vols + 1)
-                 : run_residual(c, c->stream, c->L_res_full, M_STORE_R, c->vols + 1);
-    if (st) return st;
-    if ((st = copy_vol(c, out, c->scr_out, 1, false))) return st;
-    return check_status(c);
+    return apply_op(c, in, out, false);
 }
-
-bd3mg_status bd3mg_apply_H(bd3mg_ctx *c, const float *in, float *out) { return apply_op(c, in, out, false); }
-bd3mg_status bd3mg_apply_HT(bd3mg_ctx *c, const float *in, float *out) { return apply_op(c, in, out, true); }
+bd3mg_status bd3mg_apply_HT(bd3mg_ctx *c, const float *in, float *out) {
+    GUARD(c);
+    return apply_op(c, in, out, true);
+}
 
 bd3mg_status bd3mg_slab_colours(bd3mg_ctx *c, int *colour, int *ncolours) {
     GUARD(c);
-    if (colour) for (int s = 0; s < c->nslabs; ++s) colour[s] = c->colour[s];
+    if (colour) {
+        int k = 0;
+        for (const VolState &v : c->V)
+            for (int col : v.colour) colour[k++] = col;
+    }
     if (ncolours) *ncolours = c->ncolours;
     return BD3MG_OK;
 }
@@ -794,7 +899,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
     if (!c) return 0;
-    return c->nslabs == 1 ? 4 : 1 + 4 * c->ncolours;
+    return c->any_slabs ? 1 + 4 * c->ncolours : 4 * c->ncolours;
 }
 
 }  // extern "C"
