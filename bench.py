@@ -298,18 +298,18 @@ def fstar_of(prob, iters):
     return f, settle
 
 
-def time_to_gap(prob, slabs, fstar, max_iters, stream):
+def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0):
     """Iterations to gap <= 1e-4 (from the trace), then the device time of exactly that many."""
     import torch
     from paper_2002_02328_gb300 import binding
-    with binding.Solver.from_problem(prob, slabs=slabs) as s:
+    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision) as s:
         tr = s.iterate(max_iters)
     gap = (tr - fstar) / abs(fstar)
     hit = np.nonzero(gap <= GAP)[0]
     if hit.size == 0:
         return None, None, float(gap[-1])
     k = int(hit[0])
-    with binding.Solver.from_problem(prob, slabs=slabs) as s:
+    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision) as s:
         s.iterate(2)                         # warm the graph, then restart from y
         s.set_x(torch.from_numpy(prob.y).cuda())
         torch.cuda.synchronize()
@@ -321,6 +321,50 @@ def time_to_gap(prob, slabs, fstar, max_iters, stream):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
     return k, ms / 1e3, float(gap[k])
+
+
+def batch_extra(iters, stream):
+    """16 uneven volumes (96..384)^2 x (32..96), PSF 7x7x7, per-volume ramps and lambda:
+    one lockstep context against the same volumes solved one after the other with
+    single-volume contexts (plain FP32 3MG each)."""
+    import torch
+    from paper_2002_02328_gb300 import binding, synth
+    probs = synth.workload_batch(16, seed=0)
+    nvox = int(sum(p.n for p in probs))
+
+    def timed(fn, reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps / 1e3
+
+    with binding.BatchSolver(probs) as bs:
+        bs.iterate_async(3)
+        t_batch = timed(lambda: bs.iterate_async(1), 20)
+        with binding.BatchSolver(probs) as b2:
+            tr = b2.iterate(iters)
+    fstar = tr[:, -1]
+    settle = float(np.max((tr[:, int(0.9 * iters)] - tr[:, -1]) / np.abs(fstar)))
+    gap = (tr - fstar[:, None]) / np.abs(fstar[:, None])
+    k = [int(np.nonzero(gap[v] <= GAP)[0][0]) if np.any(gap[v] <= GAP) else None for v in range(len(probs))]
+    t_seq = []
+    for p in probs:
+        with binding.Solver.from_problem(p, slabs=None) as s:
+            s.iterate_async(3)
+            t_seq.append(timed(lambda: s.iterate_async(1), 10))
+    ok = all(v is not None for v in k)
+    return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
+            "lockstep_iterations_per_s": 1.0 / t_batch,
+            "sequential_iterations_per_s": 1.0 / sum(t_seq),
+            "fstar_iters": iters, "fstar_settle_rel": settle,
+            "iters_to_gap": k,
+            "time_to_gap_s": {"batched": (max(k) * t_batch) if ok else None,
+                              "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None}}
 
 
 def e2e_run(prob, n_iter, stream):
@@ -401,6 +445,21 @@ def ours(args):
             for k, (ms, cnt) in sp.profile_iteration().items():
                 prof_plain[k][0] += ms
                 prof_plain[k][1] += cnt
+    # block form with BF16 memory directions, same volume
+    with binding.Solver.from_problem(prob, precision=binding.BF16_DIRECTIONS) as sm:
+        for _ in range(args.warmup):
+            flush.fill_(1.0)
+            sm.iterate_async(1)
+        barrier()
+        n_mixed = max(10, args.steps // 2)
+        ms_mixed = time_steps(sm, n_mixed, flush, stream, sampler)
+        barrier()
+        prof_mixed = {k: [0.0, 0] for k in binding.Solver.KERNEL_CLASSES}
+        for _ in range(args.profile_iters):
+            flush.fill_(2.0)
+            for k, (ms, cnt) in sm.profile_iteration().items():
+                prof_mixed[k][0] += ms
+                prof_mixed[k][1] += cnt
     clocks = sampler.stop() if sampler is not None else None
 
     ms_per_step = ms_total / args.steps
@@ -441,17 +500,25 @@ def ours(args):
     extra = {"sweep_vs_28B_lower_bound": sweep_lb_ms / ms_per_step,
              "plain_fp32": {"iterations_per_s": plain_rate, "launches_per_iteration": lpi_plain,
                             "kernel_ms_per_iteration": per_it_plain,
-                            "alg_bytes_per_iteration": sum(alg_plain.values())}}
+                            "alg_bytes_per_iteration": sum(alg_plain.values())},
+             "block_bf16_directions": {"iterations_per_s": 1e3 * n_mixed / ms_mixed,
+                                       "kernel_ms_per_iteration": {k: v[0] / args.profile_iters
+                                                                   for k, v in prof_mixed.items()}}}
 
     cpu = None
     if not args.quick:
         fstar, settle = fstar_of(prob, args.fstar_iters)
         k_b, t_b, g_b = time_to_gap(prob, prob.slabs, fstar, 3000, stream)
         k_p, t_p, g_p = time_to_gap(prob, None, fstar, 3000, stream)
+        k_m, t_m, g_m = time_to_gap(prob, prob.slabs, fstar, 3000, stream, binding.BF16_DIRECTIONS)
+        k_mp, t_mp, g_mp = time_to_gap(prob, None, fstar, 3000, stream, binding.BF16_DIRECTIONS)
         extra["time_to_gap"] = {"gap": GAP, "fstar": fstar, "fstar_iters": args.fstar_iters,
                                 "fstar_settle_rel": settle,
                                 "block": {"iterations": k_b, "seconds": t_b},
-                                "plain_fp32": {"iterations": k_p, "seconds": t_p}}
+                                "plain_fp32": {"iterations": k_p, "seconds": t_p},
+                                "block_bf16_directions": {"iterations": k_m, "seconds": t_m},
+                                "plain_bf16_directions": {"iterations": k_mp, "seconds": t_mp}}
+        extra["batched"] = batch_extra(min(args.fstar_iters, 3000), stream)
         e2e_rate, h2d, d2h, e2e_s = e2e_run(prob, 500, stream)
         e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}

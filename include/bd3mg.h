@@ -65,6 +65,15 @@ typedef struct {
     void *user;
 } bd3mg_allocator;
 
+/* Storage precision of the memory directions (Section 3.2 subspace D = [-g, d]).
+ * BD3MG_FP32: g and d stored in FP32.
+ * BD3MG_BF16_DIRECTIONS: g and d stored in BF16 (round to nearest even), halving
+ *   their traffic; x, y and the residual stay FP32, all arithmetic is FP32 and
+ *   every reduction and the 2x2 solve FP64.  The subspace is then spanned by the
+ *   rounded directions: B = D^T A D and D^T grad f are formed from them (the
+ *   gradient term as -||g_bf16||^2), and x moves by the FP32 step -u0 g + u1 d.
+ *   bd3mg_gradient and bd3mg_get_volume return the BF16 values widened to FP32.
+ *   Every volume of a batch must use the same mode. */
 enum { BD3MG_FP32 = 0, BD3MG_BF16_DIRECTIONS = 1 };
 
 typedef struct {

@@ -371,7 +371,7 @@ class BatchSolver:
     """Many independent volumes iterated in lockstep by one context (plain 3MG each)."""
 
     def __init__(self, problems, x0s=None, device="cuda", zchunk: int = 0, stream=None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, precision: int = FP32):
         torch = _torch()
         lib = load()
         self.shapes = [tuple(int(s) for s in p.shape) for p in problems]
@@ -379,8 +379,10 @@ class BatchSolver:
         arr = (Params * self.nvol)()
         keep = []
         ys, xs = [], []
+        precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * self.nvol
         for v, p in enumerate(problems):
-            prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, None, FP32, 1e-12, zchunk)
+            prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, None, precs[v], 1e-12,
+                                 zchunk)
             arr[v] = prm
             keep.append(k)
             yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)

@@ -39,9 +39,10 @@ struct Launch {                     // one tile-kernel launch over a contiguous 
 
 struct VolState {
     bd3mg_params p{};               // host copy (psf and slab_bounds cleared)
-    int pitch = 0;                  // row stride in floats (multiple of 4)
+    int pitch = 0;                  // row stride in elements (multiple of 8)
     size_t np = 0;                  // pitch*ny*nz
     float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
+    __nv_bfloat16 *dh = nullptr, *gh = nullptr;     // BF16 directions (instead of d, g)
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev dev{};                   // host copy of the device descriptor
     std::vector<int> bounds;        // slab bounds
@@ -68,9 +69,11 @@ struct bd3mg_ctx {
     int nslab_segs = 0;             // segments [0, nslab_segs) are slabs; then one full segment per volume
     int zchunk = 0;                 // user override (0 = automatic)
     double pinv_rtol = 1e-12;
+    bool bf = false;                // directions g, d stored as BF16
 
     // device state
     float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch for volume 0 (lazy)
+    float *scr_dir = nullptr;                        // FP32 copy-out of BF16 directions (lazy)
     VolDev *vols = nullptr;         // [0, nvol) volumes, [nvol] scratch for operator calls
     VolMaps *maps = nullptr;        // TMA descriptors, same indexing as vols
     SegDev *segs = nullptr;
@@ -92,7 +95,7 @@ struct bd3mg_ctx {
     std::vector<Launch> L_res, L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
-    int occ[3] = {1, 1, 1};         // resident CTAs per SM: residual, gradient, curvature
+    int occ[5] = {1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -146,25 +149,29 @@ bd3mg_status dalloc_n(bd3mg_ctx *c, T **p, size_t count) {
 }
 
 // Staged-tile x halo of a kernel set (must match Geo<R,RZ,TY>::XH in kernels.cuh).
-int set_xh(const KernelSet *k) { return k->R <= 4 ? 4 : 8; }
+int set_xh(const KernelSet *k, int esize = 4) { return (esize == 4 && k->R <= 4) ? 4 : 8; }
 
 // Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
 int tile_y(int kind) { return kind == 2 ? TY_C : TY_A; }
 
+// g, d: FP32 or (dir_esize 2) BF16 direction arrays.
 bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const float *x, const float *r,
-                     const float *g, const float *d) {
+                     const void *g, const void *d, int dir_esize = 4) {
     const bd3mg_params &p = v.p;
-    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks);
+    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks), bxd = TX + 2 * set_xh(c->ks, dir_esize);
     std::memset(vm, 0, sizeof(*vm));
     bool ok = true;
-    if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, p.nx, p.ny, p.nz, v.pitch, BX1, TY_A + 2);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, p.nx, p.ny, p.nz, v.pitch, BX1, TY_C + 2);
-    if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, p.nx, p.ny, p.nz, v.pitch, bx, TY_C + 2 * R);
-    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, p.nx, p.ny, p.nz, v.pitch, bx, TY_C + 2 * R);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, 4, p.nx, p.ny, p.nz, v.pitch, BX1, TY_A + 2);
+    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, 4, p.nx, p.ny, p.nz, v.pitch, BX1, TY_C + 2);
+    if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, dir_esize, p.nx, p.ny, p.nz, v.pitch, bxd, TY_C + 2 * R);
+    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, dir_esize, p.nx, p.ny, p.nz, v.pitch, bxd, TY_C + 2 * R);
     return ok;
 }
+
+// Kernel kind used for occupancy: BF16-direction gradient/curvature have their own.
+int occ_kind(const bd3mg_ctx *c, int kind) { return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind; }
 
 int ntiles_of(const VolState &v, int ty) { return ((v.p.nx + TX - 1) / TX) * ((v.p.ny + ty - 1) / ty); }
 
@@ -188,7 +195,7 @@ void add_items(bd3mg_ctx *c, int seg, int zlo, int zhi, int zc, int ty) {
 // z halo), the makespan of equal-cost items; ties go to longer chunks.
 int choose_zc(const bd3mg_ctx *c, const std::vector<std::array<int, 3>> &ranges /* lo, hi, ntiles */, int kind) {
     if (c->zchunk > 0) return std::min(c->zchunk, ZC_MAX);
-    const long long slots = (long long)c->sms * std::max(1, c->occ[kind]);
+    const long long slots = (long long)c->sms * std::max(1, c->occ[occ_kind(c, kind)]);
     const int halo = 2 * c->ks->RZ;
     long long best_cost = -1;
     int best = 4;
@@ -302,7 +309,8 @@ bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
     KArgs a = make_args(c, L, mode, vols);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
     if (st) return st;
-    c->ks->gradient(a, s);
+    // H^T-only operator calls write an FP32 scratch volume in either precision mode.
+    (c->bf && !(mode & M_HT_ONLY) ? c->ks->gradient_bf : c->ks->gradient)(a, s);
     return check_launch(c);
 }
 
@@ -310,7 +318,7 @@ bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     KArgs a = make_args(c, L, 0, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
-    c->ks->curvature(a, s);
+    (c->bf ? c->ks->curvature_bf : c->ks->curvature)(a, s);
     return check_launch(c);
 }
 
@@ -328,7 +336,7 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     dim3 grid((unsigned)blocks, (unsigned)cnt);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_UPDATE);
     if (st) return st;
-    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, grid, s);
+    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, grid, s, c->bf);
     return check_launch(c);
 }
 
@@ -382,8 +390,8 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
     if (!p.psf) return fail(c, BD3MG_EINVAL, "volume %d: psf is NULL", vi);
     if (!(p.lambda > 0) || !(p.delta > 0) || !(p.eta >= 0) || !(p.xmin <= p.xmax))
         return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
-    if (p.precision != BD3MG_FP32)
-        return fail(c, BD3MG_EUNSUPPORTED, "precision mode %d is not available in this build", p.precision);
+    if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_DIRECTIONS)
+        return fail(c, BD3MG_EINVAL, "volume %d: unknown precision mode %d", vi, p.precision);
     if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return fail(c, BD3MG_EINVAL, "volume %d too large", vi);
     v.p = p;
     const int ns = p.nslabs <= 1 ? 1 : p.nslabs;
@@ -418,6 +426,9 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
     c->zchunk = pp[0].zchunk;
+    c->bf = pp[0].precision == BD3MG_BF16_DIRECTIONS;
+    for (int v = 1; v < nvol; ++v)
+        if (pp[v].precision != pp[0].precision) return fail(c, BD3MG_EINVAL, "volumes must share one precision mode");
 
     // kernels for the PSF radii (all volumes share one compiled set; smaller PSFs are zero padded)
     c->ks = find_kernel_set(R, RZ);
@@ -454,7 +465,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = c->ks->prepare();
         if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e));
-        for (int k = 0; k < 3; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+        for (int k = 0; k < 5; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
     }
 
     // work lists
@@ -496,9 +507,11 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
 #define AL(ptr, cnt) if ((st = dalloc_n(c, &(ptr), (cnt)))) return st
     for (int v = 0; v < nvol; ++v) {
         VolState &vs = c->V[v];
-        vs.pitch = (vs.p.nx + 3) & ~3;
+        vs.pitch = (vs.p.nx + 7) & ~7;            // 16-byte rows for both FP32 and BF16 arrays
         vs.np = (size_t)vs.pitch * vs.p.ny * vs.p.nz;
-        AL(vs.x, vs.np); AL(vs.d, vs.np); AL(vs.g, vs.np); AL(vs.r, vs.np); AL(vs.y, vs.np);
+        AL(vs.x, vs.np); AL(vs.r, vs.np); AL(vs.y, vs.np);
+        if (c->bf) { AL(vs.dh, vs.np); AL(vs.gh, vs.np); }
+        else { AL(vs.d, vs.np); AL(vs.g, vs.np); }
         AL(vs.fx, FX[v].size()); AL(vs.fy, FY[v].size()); AL(vs.fz, FZ[v].size());
     }
     AL(c->vols, nvol + 1); AL(c->maps, nvol + 1); AL(c->segs, nseg);
@@ -523,8 +536,13 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpy2DAsync(vs.y, pb, ys[v], wb, wb, rows, kin, c->stream));
         const float *x0 = (x0s && x0s[v]) ? x0s[v] : ys[v];
         CK(cudaMemcpy2DAsync(vs.x, pb, x0, wb, wb, rows, kin, c->stream));
-        CK(cudaMemsetAsync(vs.d, 0, vs.np * 4, c->stream));
-        CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
+        if (c->bf) {
+            CK(cudaMemsetAsync(vs.dh, 0, vs.np * 2, c->stream));
+            CK(cudaMemsetAsync(vs.gh, 0, vs.np * 2, c->stream));
+        } else {
+            CK(cudaMemsetAsync(vs.d, 0, vs.np * 4, c->stream));
+            CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
+        }
         CK(cudaMemsetAsync(vs.r, 0, vs.np * 4, c->stream));
         CK(cudaMemcpyAsync(vs.fx, FX[v].data(), FX[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
@@ -533,14 +551,16 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.pitch = vs.pitch;
         d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
         d.plane = (long long)vs.pitch * p.ny;
-        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y;
+        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.dh = vs.dh; d.gh = vs.gh;
         d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
         d.lam_d = p.lambda; d.eta_d = p.eta;
         vs.dev = d;
         vd[v] = d;
-        if (!encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d))
+        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.dh, 2)
+                              : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
+        if (!ok)
             return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     }
     vd[nvol] = vd[0];
@@ -591,6 +611,22 @@ bd3mg_status copy_vol(bd3mg_ctx *c, const VolState &v, float *dst, const float *
     if (to_lib) CK(cudaMemcpy2DAsync(dst, pb, src, wb, wb, rows, k, c->stream));
     else CK(cudaMemcpy2DAsync(dst, wb, src, pb, wb, rows, k, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return BD3MG_OK;
+}
+
+// FP32 copy of a BF16 direction array of volume v in a scratch buffer (sized
+// for the largest volume, allocated on first use).
+bd3mg_status dir_as_float(bd3mg_ctx *c, const VolState &v, const __nv_bfloat16 *src, const float **out) {
+    size_t need = 0;
+    for (const VolState &w : c->V) need = std::max(need, w.np);
+    if (!c->scr_dir) {
+        bd3mg_status st = dalloc_n(c, &c->scr_dir, need);
+        if (st) return st;
+    }
+    launch_dir_to_float(src, c->scr_dir, (long long)v.np, c->stream);
+    bd3mg_status st = check_launch(c);
+    if (st) return st;
+    *out = c->scr_dir;
     return BD3MG_OK;
 }
 
@@ -776,8 +812,12 @@ bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
     if (g) {
         const VolState &v = c->V[0];
+        const float *src = v.g;
+        if (c->bf) {
+            if ((st = dir_as_float(c, v, v.gh, &src))) return st;
+        }
         const size_t wb = (size_t)v.p.nx * 4, pb = (size_t)v.pitch * 4, rows = (size_t)v.p.ny * v.p.nz;
-        CK(cudaMemcpy2DAsync(g, wb, v.g, pb, wb, rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+        CK(cudaMemcpy2DAsync(g, wb, src, pb, wb, rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
     }
     double h[4];
@@ -793,6 +833,10 @@ bd3mg_status bd3mg_get_volume(bd3mg_ctx *c, int vol, int which, float *dst, int 
         return fail(c, BD3MG_EINVAL, "get_volume: bad volume index, selector or NULL destination");
     const VolState &v = c->V[vol];
     const float *src = which == 0 ? v.x : which == 1 ? v.d : v.g;
+    if (c->bf && which > 0) {
+        bd3mg_status st = dir_as_float(c, v, which == 1 ? v.dh : v.gh, &src);
+        if (st) return st;
+    }
     return copy_vol(c, v, dst, src, on_device, false);
 }
 
@@ -803,7 +847,8 @@ bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     GUARD(c);
     if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
     const VolState &v = c->V[0];
-    CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
+    if (c->bf) CK(cudaMemsetAsync(v.dh, 0, v.np * 2, c->stream));
+    else CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
     return copy_vol(c, v, v.x, x, on_device, true);
 }
 

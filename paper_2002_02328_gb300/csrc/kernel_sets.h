@@ -15,10 +15,12 @@ typedef cudaError_t (*prep_fn)();
 
 struct KernelSet {
     int R, RZ;
-    launch_fn residual, gradient, curvature;
-    prep_fn prepare;               // raises the dynamic shared-memory limit
-    size_t smem_residual, smem_gradient, smem_curvature;
-    int (*occupancy)(int kind);    // resident CTAs per SM of kernel kind (0 residual, 1 gradient, 2 curvature)
+    launch_fn residual, gradient, curvature;        // FP32 directions
+    launch_fn gradient_bf, curvature_bf;            // BF16 directions
+    prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
+    // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
+    // 3 gradient (BF16 directions), 4 curvature (BF16 directions)
+    int (*occupancy)(int kind);
 };
 
 // Smallest compiled set with R' >= R and RZ' >= RZ (fewest padded taps), or null.
@@ -26,7 +28,9 @@ const KernelSet *find_kernel_set(int R, int RZ);
 
 // Block update over the slabs listed in seg_list (grid.y = number of slabs).
 void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, dim3 grid,
-                   cudaStream_t s);
+                   cudaStream_t s, bool bf16);
+// dst[i] = float(src[i]) for n BF16 elements.
+void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
 
 int kernel_sets_r1(const KernelSet **out);
 int kernel_sets_r2(const KernelSet **out);

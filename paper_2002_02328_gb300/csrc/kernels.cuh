@@ -43,8 +43,11 @@
 // deterministic run to run).
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace bd3mg {
 
@@ -73,10 +76,11 @@ constexpr int ST_NONFINITE = 1;
 constexpr int ST_TIMEOUT = 2;
 
 struct VolDev {
-    int nx, ny, nz, pitch;        // pitch: row stride in floats (multiple of 4)
+    int nx, ny, nz, pitch;        // pitch: row stride in elements (multiple of 8)
     int kxy, kz;                  // factor row lengths 2R+1, 2RZ+1 (zero padded)
     long long plane;              // pitch*ny
-    float *x, *d, *g, *r;
+    float *x, *d, *g, *r;         // d, g: FP32 directions (null in the BF16-direction form)
+    __nv_bfloat16 *dh, *gh;       // d, g: BF16 directions (null in the FP32 form)
     const float *y;               // null -> 0
     const float *fx, *fy, *fz;    // [nz][kxy], [nz][kxy], [nz][kz]
     float lam, delta2, eta2, xmin, xmax;
@@ -120,13 +124,16 @@ struct KArgs {
     double pinv_rtol;
 };
 
-template <int R, int RZ, int TY>
+template <int R, int RZ, int TY, int EB = 4>
 struct Geo {
     static constexpr int RPW = TY / NWARP;            // y-pass outputs per thread
-    static constexpr int XH = R <= 4 ? 4 : 8;         // staged x halo (>= R, multiple of 4)
+    // staged x halo: >= R and a multiple of 16 bytes of EB-byte elements (TMA x alignment)
+    static constexpr int XH = (EB == 4 && R <= 4) ? 4 : 8;
     static constexpr int BX = TX + 2 * XH;            // staged tile width (TMA box x)
     static constexpr int BY = TY + 2 * R;             // staged tile height (TMA box y)
-    static constexpr int SLOT = ((BX * BY + 31) / 32) * 32;
+    // slot length: a multiple of 128 bytes, so that every slot (a TMA destination) stays 128-byte aligned
+    static constexpr int SLOT_Q = 128 / EB;
+    static constexpr int SLOT = ((BX * BY + SLOT_Q - 1) / SLOT_Q) * SLOT_Q;
     static constexpr int BY1 = TY + 2;                // 1-halo x tile height
     static constexpr int SLOT1 = ((BX1 * BY1 + 31) / 32) * 32;
     static constexpr int ZUNITS = BY * (BX / 4);      // z-combine units of 4 staged columns
@@ -150,8 +157,13 @@ struct Geo {
 
 template <int R, int RZ>
 struct Smem {
+    static_assert(Geo<R, RZ, TY_A>::SLOT * 4 % 128 == 0 && Geo<R, RZ, TY_C>::SLOT * 4 % 128 == 0 &&
+                      Geo<R, RZ, TY_C, 2>::SLOT * 2 % 128 == 0 && Geo<R, RZ, TY_A>::SLOT1 * 4 % 128 == 0 &&
+                      Geo<R, RZ, TY_C>::SLOT1 * 4 % 128 == 0,
+                  "TMA slots must be multiples of 128 bytes");
     using A = Geo<R, RZ, TY_A>;
     using C = Geo<R, RZ, TY_C>;
+    using CB = Geo<R, RZ, TY_C, 2>;
     static constexpr size_t residual =
         sizeof(float) * (A::NSF * A::SLOT + A::BY * A::BX + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::NSF);
     static constexpr size_t gradient =
@@ -160,7 +172,15 @@ struct Smem {
     static constexpr size_t curvature =
         sizeof(float) * (2 * C::NSF * C::SLOT + NSX * C::SLOT1 + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
         C::bars_bytes(2 * C::NSF + NSX);
+    // BF16 directions: g, d slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
+    static constexpr size_t curvature_bf =
+        2 * (2 * CB::NSF * CB::SLOT) +
+        sizeof(float) * (NSX * CB::SLOT1 + 2 * CB::BY * CB::BX + 2 * CB::BY * TX + CB::CF_FLOATS) +
+        CB::bars_bytes(2 * CB::NSF + NSX);
 };
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 // ---------------------------------------------------------------------------
 // mbarrier / TMA primitives (inline PTX)
@@ -217,20 +237,20 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
 // CTA; thread 0 issues the copies.  Slices outside [zlo, zhi) are zero-filled
 // by all threads when issued; with PREF >= 2 a CTA barrier always separates
 // that fill from the first read of the slot.
-template <int NS, int SLOTF>
+template <int NS, int SLOTF, class T = float>
 struct Pipe {
-    float *buf;
+    T *buf;                       // NS slots of SLOTF elements
     uint64_t *bar;
     const CUtensorMap *map;
     int x0, y0;                   // box origin (x0 is a multiple of 4)
     int zlo, zhi;                 // slices [zlo, zhi) are copied; others are zero-filled
     int first;                    // slice in slot 0
     uint32_t bytes;               // bytes per copy (box size)
-    int fill;                     // floats to zero-fill per slot
+    int fill;                     // 16-byte chunks to zero-fill per slot
     uint32_t par;
     int next_issue, next_wait, issue_slot, wait_slot;
 
-    __device__ void init(float *b, uint64_t *br, const CUtensorMap *m, int bx0, int by0, int lo, int hi,
+    __device__ void init(T *b, uint64_t *br, const CUtensorMap *m, int bx0, int by0, int lo, int hi,
                          uint32_t nbytes, int first_slice) {
         buf = b;
         bar = br;
@@ -241,7 +261,7 @@ struct Pipe {
         zhi = hi;
         first = first_slice;
         bytes = nbytes;
-        fill = (int)(nbytes / 4);
+        fill = (int)((nbytes + 15) / 16);
         par = 0u;
         next_issue = next_wait = first_slice;
         issue_slot = wait_slot = 0;
@@ -253,7 +273,7 @@ struct Pipe {
     }
     __device__ __forceinline__ bool loaded(int z) const { return z >= zlo && z < zhi; }
     __device__ __forceinline__ int slot(int z) const { return (z - first) % NS; }
-    __device__ __forceinline__ const float *at(int z) const { return buf + slot(z) * SLOTF; }
+    __device__ __forceinline__ const T *at(int z) const { return buf + slot(z) * SLOTF; }
     // slot of slice z - back when s is the slot of z (0 <= back < NS)
     __device__ __forceinline__ static int back_slot(int s, int back) {
         const int t = s - back;
@@ -272,7 +292,7 @@ struct Pipe {
                 }
             } else {
                 float4 *d = reinterpret_cast<float4 *>(buf + s * SLOTF);
-                for (int i = threadIdx.x; i < fill / 4; i += NT) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = threadIdx.x; i < fill; i += NT) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
     }
@@ -428,20 +448,28 @@ struct Units {
 
 // Window of the forward z-combine: the KZ staged slices zi, zi-1, ..., zi-2RZ
 // (slot s holds zi).
-template <int KZ, int NS, int SLOTF>
-__device__ __forceinline__ void window(const Pipe<NS, SLOTF> &p, int s, const float *(&w)[KZ]) {
+template <int KZ, int NS, int SLOTF, class T>
+__device__ __forceinline__ void window(const Pipe<NS, SLOTF, T> &p, int s, const T *(&w)[KZ]) {
 #pragma unroll
-    for (int t = 0; t < KZ; ++t) w[t] = p.buf + Pipe<NS, SLOTF>::back_slot(s, t) * SLOTF;
+    for (int t = 0; t < KZ; ++t) w[t] = p.buf + Pipe<NS, SLOTF, T>::back_slot(s, t) * SLOTF;
+}
+
+__device__ __forceinline__ float4 load4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) {
+    const uint2 q = *reinterpret_cast<const uint2 *>(p);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
+    return make_float4(a.x, a.y, b.x, b.y);
 }
 
 // Forward z-combine of one unit (4 staged columns at float offset off):
 // W = sum_t fz[t] * v(zi - t) = sum_c fz_zo(c) v(zo - c).
-template <int KZ>
-__device__ __forceinline__ void zcomb_unit(const float *const (&w)[KZ], int off, const float (&fzc)[KZ], float *W) {
+template <int KZ, class T>
+__device__ __forceinline__ void zcomb_unit(const T *const (&w)[KZ], int off, const float (&fzc)[KZ], float *W) {
     float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
 #pragma unroll
     for (int t = 0; t < KZ; ++t) {
-        const float4 v = *reinterpret_cast<const float4 *>(w[t] + off);
+        const float4 v = load4(w[t] + off);
         float4 &a = (t & 1) ? acc1 : acc0;
         a.x = fmaf(fzc[t], v.x, a.x);
         a.y = fmaf(fzc[t], v.y, a.y);
@@ -653,7 +681,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
 // k_gradient: g = H^T r (+ box and penalty gradient unless M_HT_ONLY) on the
 // slabs' own slices.
 // ---------------------------------------------------------------------------
-template <int R, int RZ>
+template <int R, int RZ, bool BF>
 __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     using G = Geo<R, RZ, TY_A>;
     constexpr int RPW = G::RPW;
@@ -670,6 +698,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
     float *gp = V.g;
+    __nv_bfloat16 *gph = V.gh;
     const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool full = (a.mode & M_HT_ONLY) == 0;
@@ -742,7 +771,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
             float fzc[G::KZ];
 #pragma unroll
             for (int t = 0; t < G::KZ; ++t) fzc[t] = CF[(zo + t - RZ - zbeg) * G::CFS + 2 * G::KXYP + t];
-            float *grow = gp + (long long)zo * plane;
+            const long long zoff = (long long)zo * plane;
             const float *xm = full ? px.at(zo - 1) : nullptr;
             const float *x0p = full ? px.at(zo) : nullptr;
             const float *xp1 = full ? px.at(zo + 1) : nullptr;
@@ -772,7 +801,8 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                         const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
                         gval = fmaf(lam, pen, fmaf(eta2, dist, q));
                     }
-                    grow[n] = gval;
+                    if constexpr (BF) gph[zoff + n] = __float2bfloat16_rn(gval);
+                    else gp[zoff + n] = gval;
                 }
             }
         }
@@ -787,14 +817,15 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
 //        6 sum w (Vg)^2  7 sum w Vg Vd  8 sum w (Vd)^2
 // g_S, d_S are g, d masked to the slab's slices [z0, z1) (zero-filled slots).
 // ---------------------------------------------------------------------------
-template <int R, int RZ>
+template <int R, int RZ, bool BF>
 __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
-    using G = Geo<R, RZ, TY_C>;
+    using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // direction storage
+    using G = Geo<R, RZ, TY_C, sizeof(T)>;
     constexpr int RPW = G::RPW;
     extern __shared__ __align__(128) float smem[];
-    float *sgs = smem;                                   // NSF * SLOT (g)
-    float *sds = sgs + G::NSF * G::SLOT;                 // NSF * SLOT (d)
-    float *xs = sds + G::NSF * G::SLOT;                  // NSX * SLOT1 (x)
+    T *sgs = reinterpret_cast<T *>(smem);                // NSF * SLOT (g)
+    T *sds = sgs + G::NSF * G::SLOT;                     // NSF * SLOT (d)
+    float *xs = reinterpret_cast<float *>(sds + G::NSF * G::SLOT);   // NSX * SLOT1 (x)
     float *Wg = xs + NSX * G::SLOT1;
     float *Wd = Wg + G::BY * G::BX;
     float *T1g = Wd + G::BY * G::BX;
@@ -814,8 +845,8 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, 2 * G::NSF + NSX, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
-    const uint32_t nb = (uint32_t)(G::BX * G::BY * sizeof(float));
-    Pipe<G::NSF, G::SLOT> pg, pd;
+    const uint32_t nb = (uint32_t)(G::BX * G::BY * sizeof(T));
+    Pipe<G::NSF, G::SLOT, T> pg, pd;
     pg.init(sgs, bar, &a.maps[sg.vol].m[TM_G_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
     pd.init(sds, bar + G::NSF, &a.maps[sg.vol].m[TM_D_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
     // x slices for the penalty at outputs zo in [max(zo0, pen_lo), min(zo1, pen_hi)): x(zo), x(zo+1)
@@ -851,7 +882,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
         if (emit) {
             float fzc[G::KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
-            const float *wg[G::KZ], *wd[G::KZ];
+            const T *wg[G::KZ], *wd[G::KZ];
             window(pg, s, wg);
             window(pd, s, wd);
 #pragma unroll
@@ -885,9 +916,9 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
         float hg[RPW], hd[RPW];
         ypass<R, RPW, -1>(T1g, y0, lane, fyc, hg);
         ypass<R, RPW, -1>(T1d, y0, lane, fyc, hd);
-        const int s0 = Pipe<G::NSF, G::SLOT>::back_slot(s, RZ), s1 = Pipe<G::NSF, G::SLOT>::back_slot(s, RZ - 1);
-        const float *gz0 = pg.buf + s0 * G::SLOT, *gz1 = pg.buf + s1 * G::SLOT;   // slices zo, zo+1
-        const float *dz0 = pd.buf + s0 * G::SLOT, *dz1 = pd.buf + s1 * G::SLOT;
+        const int s0 = Pipe<G::NSF, G::SLOT, T>::back_slot(s, RZ), s1 = Pipe<G::NSF, G::SLOT, T>::back_slot(s, RZ - 1);
+        const T *gz0 = pg.buf + s0 * G::SLOT, *gz1 = pg.buf + s1 * G::SLOT;   // slices zo, zo+1
+        const T *dz0 = pd.buf + s0 * G::SLOT, *dz1 = pd.buf + s1 * G::SLOT;
         const float *xz0 = pen ? px.at(zo) : xs, *xz1 = pen ? px.at(zo + 1) : xs;
 #pragma unroll
         for (int k = 0; k < RPW; ++k) {
@@ -899,7 +930,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
                 if (pen) {
                     const int ci = (yo + R) * G::BX + lane + G::XH;
                     const int xi = (yo + 1) * BX1 + lane + XH1;
-                    const float gc = gz0[ci], dc = dz0[ci], xc = xz0[xi];
+                    const float gc = to_f(gz0[ci]), dc = to_f(dz0[ci]), xc = xz0[xi];
                     if (zo >= sg.z0) {
                         acc[0] = fmaf(gc, gc, acc[0]);
                         acc[1] = fmaf(gc, dc, acc[1]);
@@ -907,21 +938,21 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
                     }
                     if (gx < nx - 1) {
                         const float t = xz0[xi + 1] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = gz0[ci + 1] - gc, vd = dz0[ci + 1] - dc;
+                        const float vg = to_f(gz0[ci + 1]) - gc, vd = to_f(dz0[ci + 1]) - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);
                     }
                     if (gy < ny - 1) {
                         const float t = xz0[xi + BX1] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = gz0[ci + G::BX] - gc, vd = dz0[ci + G::BX] - dc;
+                        const float vg = to_f(gz0[ci + G::BX]) - gc, vd = to_f(dz0[ci + G::BX]) - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);
                     }
                     if (zo < nz - 1) {
                         const float t = xz1[xi] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = gz1[ci] - gc, vd = dz1[ci] - dc;
+                        const float vg = to_f(gz1[ci]) - gc, vd = to_f(dz1[ci]) - dc;
                         acc[6] = fmaf(w * vg, vg, acc[6]);
                         acc[7] = fmaf(w * vg, vd, acc[7]);
                         acc[8] = fmaf(w * vd, vd, acc[8]);

@@ -9,24 +9,30 @@ template <int R, int RZ>
 void launch_residual(const KArgs &a, cudaStream_t s) {
     k_residual<R, RZ><<<a.nitems, NT, Smem<R, RZ>::residual, s>>>(a);
 }
-template <int R, int RZ>
+template <int R, int RZ, bool BF>
 void launch_gradient(const KArgs &a, cudaStream_t s) {
-    k_gradient<R, RZ><<<a.nitems, NT, Smem<R, RZ>::gradient, s>>>(a);
+    k_gradient<R, RZ, BF><<<a.nitems, NT, Smem<R, RZ>::gradient, s>>>(a);
 }
-template <int R, int RZ>
+template <int R, int RZ, bool BF>
 void launch_curvature(const KArgs &a, cudaStream_t s) {
-    k_curvature<R, RZ><<<a.nitems, NT, Smem<R, RZ>::curvature, s>>>(a);
+    k_curvature<R, RZ, BF><<<a.nitems, NT, BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature, s>>>(a);
 }
 template <int R, int RZ>
 cudaError_t prepare_set() {
     cudaError_t e = cudaFuncSetAttribute(k_residual<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Smem<R, RZ>::residual);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_gradient<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gradient<R, RZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::gradient);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_curvature<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gradient<R, RZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem<R, RZ>::gradient);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curvature<R, RZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::curvature);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curvature<R, RZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem<R, RZ>::curvature_bf);
     return e;
 }
 
@@ -34,18 +40,19 @@ template <int R, int RZ>
 int occupancy_of(int kind) {
     int n = 0;
     cudaError_t e;
-    if (kind == 0)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual<R, RZ>, NT, Smem<R, RZ>::residual);
-    else if (kind == 1)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ>, NT, Smem<R, RZ>::gradient);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ>, NT, Smem<R, RZ>::curvature);
+    switch (kind) {
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual<R, RZ>, NT, Smem<R, RZ>::residual); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, false>, NT, Smem<R, RZ>::gradient); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, true>, NT, Smem<R, RZ>::gradient); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, true>, NT, Smem<R, RZ>::curvature_bf); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false>, NT, Smem<R, RZ>::curvature); break;
+    }
     return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace bd3mg
 
-#define BD3MG_KERNEL_SET(R, RZ)                                                                        \
-    {R, RZ, &bd3mg::launch_residual<R, RZ>, &bd3mg::launch_gradient<R, RZ>, &bd3mg::launch_curvature<R, RZ>, \
-     &bd3mg::prepare_set<R, RZ>, bd3mg::Smem<R, RZ>::residual, bd3mg::Smem<R, RZ>::gradient,       \
-     bd3mg::Smem<R, RZ>::curvature, &bd3mg::occupancy_of<R, RZ>}
+#define BD3MG_KERNEL_SET(R, RZ)                                                                          \
+    {R, RZ, &bd3mg::launch_residual<R, RZ>, &bd3mg::launch_gradient<R, RZ, false>,                        \
+     &bd3mg::launch_curvature<R, RZ, false>, &bd3mg::launch_gradient<R, RZ, true>,                        \
+     &bd3mg::launch_curvature<R, RZ, true>, &bd3mg::prepare_set<R, RZ>, &bd3mg::occupancy_of<R, RZ>}

@@ -10,9 +10,10 @@
 
 namespace bd3mg {
 
-// 3D tile map over a pitched float32 volume: dims (nx, ny, nz), row pitch in
-// floats (multiple of 4), box (bx, by, 1), zero fill outside the volume.
-bool encode_map(CUtensorMap *m, const float *base, int nx, int ny, int nz, int pitch, int bx, int by);
+// 3D tile map over a pitched volume of float32 (esize 4) or bfloat16 (esize 2)
+// elements: dims (nx, ny, nz), row pitch in elements (pitch*esize a multiple
+// of 16), box (bx, by, 1), zero fill outside the volume.
+bool encode_map(CUtensorMap *m, const void *base, int esize, int nx, int ny, int nz, int pitch, int bx, int by);
 
 constexpr int kMaxPsfExtent = 11;        // largest PSF extent the compiled kernels cover
 

@@ -144,7 +144,7 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     VolMaps vm;
     std::memset(&vm, 0, sizeof(vm));
     const int bx = TX + 2 * (ks->R <= 4 ? 4 : 8);
-    if (!encode_map(&vm.m[TM_X_R], x, p->nx, p->ny, p->nz, p->nx, bx, TY_A + 2 * ks->R))
+    if (!encode_map(&vm.m[TM_X_R], x, 4, p->nx, p->ny, p->nz, p->nx, bx, TY_A + 2 * ks->R))
         return fail(BD3MG_ECUDA, "cuTensorMapEncodeTiled failed");
     std::memcpy(g_host + o_maps, &vm, sizeof(vm));
     const SegDev sg{0, 0, p->nz, 0};
