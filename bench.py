@@ -358,13 +358,23 @@ def batch_extra(iters, stream):
             s.iterate_async(3)
             t_seq.append(timed(lambda: s.iterate_async(1), 10))
     ok = all(v is not None for v in k)
+    # lockstep with per-volume stopping at f <= f* + gap |f*|: a volume that
+    # reaches its target drops out of every later launch
+    t_stop, k_stop = None, None
+    if ok:
+        with binding.BatchSolver(probs) as bs:
+            bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
+            t_stop = timed(lambda: bs.iterate_async(max(k) + 1), 1)
+            k_stop = [int(v) for v in bs.stopped()]
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,
             "sequential_iterations_per_s": 1.0 / sum(t_seq),
             "fstar_iters": iters, "fstar_settle_rel": settle,
             "iters_to_gap": k,
-            "time_to_gap_s": {"batched": (max(k) * t_batch) if ok else None,
-                              "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None}}
+            "time_to_gap_s": {"batched_with_stopping": t_stop,
+                              "batched_lockstep": (max(k) * t_batch) if ok else None,
+                              "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None},
+            "stopped_after": k_stop}
 
 
 def e2e_run(prob, n_iter, stream):

@@ -130,6 +130,26 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
  * synchronising call. */
 bd3mg_status bd3mg_iterate_async(bd3mg_ctx *ctx, int n);
 
+/* Per-volume stopping.  Before each sweep k >= 1 the device tests every
+ * running volume with the rule of the paper's scaling experiment (Section 4.2),
+ *     ||x^k - x^{k-1}|| <= tol * ||x^{k-1}||,
+ * where the step length is summed over the slab steps of sweep k-1 from the
+ * FP64 subspace sums (||-u0 g + u1 d||^2 = u0^2 g.g - 2 u0 u1 g.d + u1^2 d.d)
+ * and ||x^{k-1}||^2 is summed over the same slab steps (each slab is read
+ * before its own update); it also stops a volume
+ * once f(x^k) <= f_target[v].  A stopped volume keeps x^k: the work items of
+ * its later sweeps exit at once and its trace repeats f(x^k).
+ * tol: >= 0 (0 disables the step rule).  f_target: HOST array of nvol doubles,
+ * or NULL for no targets (-INFINITY disables one volume's target).
+ * Clears every volume's stopped state.  Default: tol 0, no targets.
+ * Synchronises the stream.  EINVAL for a negative or non-finite tol or a NaN target. */
+bd3mg_status bd3mg_set_stopping(bd3mg_ctx *ctx, double tol, const double *f_target);
+
+/* sweeps: HOST array of nvol ints; receives, per volume, the number of sweeps
+ * k after which it stopped (x^k is its result), or -1 while it runs.
+ * Synchronises the stream. */
+bd3mg_status bd3mg_stopped(bd3mg_ctx *ctx, int *sweeps);
+
 /* Objective at the current iterate; parts (optional, 3 doubles) = data term,
  * box term, penalty term.  Synchronises. */
 bd3mg_status bd3mg_objective(bd3mg_ctx *ctx, double *f, double *parts);

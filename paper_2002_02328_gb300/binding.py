@@ -31,7 +31,8 @@ EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iter
             "bd3mg_gradient", "bd3mg_get_x", "bd3mg_get_d", "bd3mg_set_x", "bd3mg_last_step", "bd3mg_apply_H",
             "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
             "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc",
-            "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_error_string",
+            "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_set_stopping",
+            "bd3mg_stopped", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
             "bd3mg_volume_count": (ip, [vp]),
             "bd3mg_objectives": (ip, [vp, vp]),
             "bd3mg_get_volume": (ip, [vp, ip, ip, vp, ip]),
+            "bd3mg_set_stopping": (ip, [vp, dp, vp]),
+            "bd3mg_stopped": (ip, [vp, vp]),
             "bd3mg_objective_noalloc": (ip, [P, vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
@@ -324,6 +327,17 @@ class Solver:
         x = x.contiguous()
         self._c(self._lib.bd3mg_set_x(self._ctx, ctypes.c_void_p(_ptr(x)), int(x.is_cuda)))
 
+    def set_stopping(self, tol: float = 0.0, f_target=None):
+        """Stop once ||x^k - x^{k-1}|| <= tol ||x^{k-1}|| or f(x^k) <= f_target (None: no target)."""
+        t = None if f_target is None else np.array([float(f_target)], np.float64)
+        self._c(self._lib.bd3mg_set_stopping(self._ctx, float(tol), None if t is None else t.ctypes.data))
+
+    def stopped(self) -> int:
+        """Sweeps after which the solve stopped, or -1 while it runs."""
+        k = np.zeros(1, np.int32)
+        self._c(self._lib.bd3mg_stopped(self._ctx, k.ctypes.data))
+        return int(k[0])
+
     def last_step(self) -> np.ndarray:
         """Per slab: [B00, B01, B11, c0, c1, u0, u1, rank] of its latest update."""
         buf = np.zeros((self.nslabs, 8))
@@ -438,6 +452,20 @@ class BatchSolver:
 
     def iterate_async(self, n: int):
         self._c(self._lib.bd3mg_iterate_async(self._ctx, int(n)))
+
+    def set_stopping(self, tol: float = 0.0, f_target=None):
+        """Per volume: stop once ||x^k - x^{k-1}|| <= tol ||x^{k-1}|| or f(x^k) <= f_target[v]."""
+        t = None if f_target is None else np.ascontiguousarray(f_target, np.float64)
+        if t is not None and t.shape != (self.nvol,):
+            raise ValueError("f_target needs one value per volume")
+        self._c(self._lib.bd3mg_set_stopping(self._ctx, float(tol), None if t is None else t.ctypes.data))
+        self._keep_t = t
+
+    def stopped(self) -> np.ndarray:
+        """Per volume: sweeps after which it stopped, or -1 while it runs."""
+        k = np.zeros(self.nvol, np.int32)
+        self._c(self._lib.bd3mg_stopped(self._ctx, k.ctypes.data))
+        return k
 
     def objectives(self):
         f = np.zeros(self.nvol)

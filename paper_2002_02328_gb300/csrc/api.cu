@@ -86,6 +86,9 @@ struct bd3mg_ctx {
     Shared *sh = nullptr;
     double *trace = nullptr;
     int trace_cap = 0;
+    VolRun *run = nullptr;          // per-volume stopping state
+    double tol2 = 0.0;              // squared step tolerance (0: off)
+    std::vector<double> f_target;   // per volume (-inf: none)
     int *counter = nullptr, *status = nullptr;
 
     std::vector<SegDev> segs_h;
@@ -315,7 +318,7 @@ bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
 }
 
 bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
-    KArgs a = make_args(c, L, 0, nullptr);
+    KArgs a = make_args(c, L, M_ITER, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
     (c->bf ? c->ks->curvature_bf : c->ks->curvature)(a, s);
@@ -336,7 +339,7 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     dim3 grid((unsigned)blocks, (unsigned)cnt);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_UPDATE);
     if (st) return st;
-    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, grid, s, c->bf);
+    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, c->run, grid, s, c->bf);
     return check_launch(c);
 }
 
@@ -344,16 +347,23 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
     if (!c->any_slabs) {
-        if ((st = run_residual(c, s, c->L_res[0], M_STORE_R | M_OBJ | M_TRACE | M_ADVANCE))) return st;
+        if ((st = run_residual(c, s, c->L_res[0], M_STORE_R | M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     } else {
-        if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE))) return st;
+        if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
-        if (c->any_slabs && (st = run_residual(c, s, c->L_res[col], M_STORE_R))) return st;
-        if ((st = run_gradient(c, s, c->L_grad[col], 0))) return st;
+        if (c->any_slabs && (st = run_residual(c, s, c->L_res[col], M_STORE_R | M_ITER))) return st;
+        if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
         if ((st = run_update(c, s, col))) return st;
     }
+    return BD3MG_OK;
+}
+
+bd3mg_status upload_shared(bd3mg_ctx *c) {
+    Shared sh{c->trace, c->trace_cap, 0, c->counter, c->status, c->run, c->tol2};
+    CK(cudaMemcpyAsync(c->sh, &sh, sizeof(Shared), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));      // keep `sh` alive until copied
     return BD3MG_OK;
 }
 
@@ -363,11 +373,18 @@ bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
     double *t = nullptr;
     bd3mg_status st = dalloc_n(c, &t, (size_t)cap * c->nvol);
     if (st) return st;
-    Shared sh{t, cap, 0, c->counter, c->status};
-    CK(cudaMemcpyAsync(c->sh, &sh, sizeof(Shared), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));      // keep `sh` alive until copied
     c->trace = t;
     c->trace_cap = cap;
+    return upload_shared(c);
+}
+
+// Clear the stopping state of volume vol (all volumes when vol < 0), keeping the targets.
+bd3mg_status reset_run(bd3mg_ctx *c, int vol) {
+    std::vector<VolRun> h(c->nvol);
+    for (int v = 0; v < c->nvol; ++v) h[v] = VolRun{0.0, 0.0, c->f_target[v], 0, 0};
+    const int v0 = vol < 0 ? 0 : vol, cnt = vol < 0 ? c->nvol : 1;
+    CK(cudaMemcpyAsync(c->run + v0, h.data() + v0, sizeof(VolRun) * cnt, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return BD3MG_OK;
 }
 
@@ -518,9 +535,9 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     AL(c->items, c->items_h.size());
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
-    AL(c->partials, (size_t)c->max_items * 9);
+    AL(c->partials, (size_t)c->max_items * 10);    // up to 10 partial sums per item
     AL(c->ticket, 1); AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
-    AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1);
+    AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1); AL(c->run, nvol);
 #undef AL
 
     // data and descriptors
@@ -585,6 +602,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     CK(cudaMemsetAsync(c->status, 0, 4, c->stream));
     // the host copies above read pageable and stack memory: finish them before returning
     CK(cudaStreamSynchronize(c->stream));
+    c->f_target.assign(nvol, -INFINITY);
+    if ((st = reset_run(c, -1))) return st;
     if ((st = ensure_trace(c, 1024))) return st;
 
     // capture one iteration as a graph
@@ -781,6 +800,31 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     return check_status(c);
 }
 
+bd3mg_status bd3mg_set_stopping(bd3mg_ctx *c, double tol, const double *f_target) {
+    GUARD(c);
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, BD3MG_EINVAL, "tol must be finite and >= 0");
+    for (int v = 0; v < c->nvol; ++v) {
+        const double t = f_target ? f_target[v] : -INFINITY;
+        if (std::isnan(t)) return fail(c, BD3MG_EINVAL, "f_target[%d] is NaN", v);
+        c->f_target[v] = t;
+    }
+    c->tol2 = tol * tol;
+    bd3mg_status st;
+    if ((st = upload_shared(c))) return st;
+    return reset_run(c, -1);
+}
+
+bd3mg_status bd3mg_stopped(bd3mg_ctx *c, int *sweeps) {
+    GUARD(c);
+    if (!sweeps) return fail(c, BD3MG_EINVAL, "sweeps is NULL");
+    std::vector<VolRun> h(c->nvol);
+    CK(cudaMemcpyAsync(h.data(), c->run, sizeof(VolRun) * c->nvol, cudaMemcpyDeviceToHost, c->stream));
+    bd3mg_status st;
+    if ((st = check_status(c))) return st;
+    for (int v = 0; v < c->nvol; ++v) sweeps[v] = h[v].stopped ? h[v].sweeps : -1;
+    return BD3MG_OK;
+}
+
 bd3mg_status bd3mg_objective(bd3mg_ctx *c, double *f, double *parts) {
     GUARD(c);
     bd3mg_status st;
@@ -849,6 +893,8 @@ bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     const VolState &v = c->V[0];
     if (c->bf) CK(cudaMemsetAsync(v.dh, 0, v.np * 2, c->stream));
     else CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
+    bd3mg_status st = reset_run(c, 0);
+    if (st) return st;
     return copy_vol(c, v, v.x, x, on_device, true);
 }
 

@@ -10,6 +10,7 @@ namespace bd3mg {
 struct KArgs;
 struct VolDev;
 struct SegDev;
+struct VolRun;
 typedef void (*launch_fn)(const KArgs &, cudaStream_t);
 typedef cudaError_t (*prep_fn)();
 
@@ -26,9 +27,10 @@ struct KernelSet {
 // Smallest compiled set with R' >= R and RZ' >= RZ (fewest padded taps), or null.
 const KernelSet *find_kernel_set(int R, int RZ);
 
-// Block update over the slabs listed in seg_list (grid.y = number of slabs).
-void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, dim3 grid,
-                   cudaStream_t s, bool bf16);
+// Block update over the slabs listed in seg_list (grid.y = number of slabs);
+// run (nullable) marks stopped volumes.
+void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
+                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16);
 // dst[i] = float(src[i]) for n BF16 elements.
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
 

@@ -70,6 +70,7 @@ constexpr int M_OBJ = 2;          // k_residual: reduce the objective
 constexpr int M_TRACE = 4;        // k_residual: append f to the trace
 constexpr int M_ADVANCE = 8;      // k_residual: advance the trace counter
 constexpr int M_HT_ONLY = 16;     // k_gradient: output H^T r only
+constexpr int M_ITER = 32;        // launch belongs to an iteration: items of stopped volumes exit at once
 
 // Status bits (device word)
 constexpr int ST_NONFINITE = 1;
@@ -97,13 +98,29 @@ struct VolMaps { CUtensorMap m[TM_COUNT]; };
 struct SegDev { int vol, z0, z1, slot; };
 struct Item { int seg, tx0, ty0, zo0, zo1; };
 
+// Per-volume stopping state (device).  The objective launch that opens a
+// sweep tests the volume: it stops once the last sweep moved x by at most
+// tol * ||x|| (||x^{k+1} - x^k|| <= tol ||x^k||, the rule of the paper's
+// scaling experiment, Section 4.2) or once f(x^k) <= f_target.
+struct VolRun {
+    double xx_prev;               // ||x^k||^2 of the sweep's start iterate, summed over its slab steps
+    double dx2;                   // ||x^{k+1} - x^k||^2 summed over the sweep's slab steps
+    double f_target;              // -inf: no objective target
+    int stopped;                  // 1: every later iteration launch skips this volume
+    int sweeps;                   // sweeps completed (x^sweeps is the result once stopped)
+};
+
 struct Shared {                   // device-resident context words (graph-stable)
     double *trace;
     int trace_cap;
     int pad;
     int *counter;
     int *status;
+    VolRun *run;                  // [volume] or null (no stopping)
+    double tol2;                  // tol^2 of the step rule (0: off)
 };
+
+
 
 struct KArgs {
     const VolDev *vols;
@@ -374,6 +391,16 @@ __device__ void sum_slot(const double *partials, int ib, int ie, double *out) {
     __syncthreads();
 }
 
+// True when this launch is part of an iteration and the volume has stopped.
+// The flag changes only in the last CTA of an objective launch, after every
+// CTA of that launch has read it, so the read-only path is coherent here (and
+// keeps the tile loops' registers at their count without the test).
+__device__ __forceinline__ bool vol_stopped(const KArgs &a, int vol) {
+    int v = 0;
+    if ((a.mode & M_ITER) && a.sh->run) v = __ldg(&a.sh->run[vol].stopped);
+    return v != 0;
+}
+
 // u = -B^+ c for the symmetric 2x2 B = [[b00, b01], [b01, b11]] (Moore-Penrose
 // pseudo-inverse): full inverse when the small eigenvalue exceeds rtol times the
 // large one, projection on the dominant eigenvector when only that one does,
@@ -535,6 +562,52 @@ __device__ __forceinline__ void ypass(const float *T1, int y0, int lane, const f
     }
 }
 
+// Last CTA of an objective launch: per volume slot, f and its parts, the trace
+// entry, and (M_ADVANCE, the launch that opens a sweep) the stopping test.
+// A volume skipped as stopped keeps its last f.
+static __device__ __forceinline__ void objective_finish(const KArgs &a) {
+    __shared__ double tot[3];
+    const int tid = threadIdx.x;
+    const int k = *a.sh->counter;
+    const bool trace = (a.mode & M_TRACE) && k < a.sh->trace_cap;
+    for (int sl = 0; sl < a.nslots; ++sl) {
+        const int vid = a.slot_id[sl];
+        if (vol_stopped(a, vid)) {
+            if (tid == 0 && trace) a.sh->trace[(size_t)vid * a.sh->trace_cap + k] = a.fout[vid * 4];
+            continue;
+        }
+        sum_slot<3>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
+        if (tid == 0) {
+            const VolDev &vv = a.vols[vid];
+            const double f1 = tot[0], f2 = vv.eta_d * tot[1], f3 = vv.lam_d * tot[2];
+            const double f = f1 + f2 + f3;
+            a.fout[vid * 4 + 0] = f;
+            a.fout[vid * 4 + 1] = f1;
+            a.fout[vid * 4 + 2] = f2;
+            a.fout[vid * 4 + 3] = f3;
+            if (!isfinite(f)) atomicOr(a.sh->status, ST_NONFINITE);
+            if (trace) a.sh->trace[(size_t)vid * a.sh->trace_cap + k] = f;
+            VolRun *run = a.sh->run;
+            if (run && (a.mode & M_ADVANCE) && (a.mode & M_ITER)) {
+                VolRun &rv = run[vid];
+                const bool small_step = rv.sweeps > 0 && a.sh->tol2 > 0.0 && rv.dx2 <= a.sh->tol2 * rv.xx_prev;
+                if (small_step || f <= rv.f_target) {
+                    rv.stopped = 1;
+                } else {
+                    rv.sweeps += 1;
+                    rv.xx_prev = 0.0;
+                    rv.dx2 = 0.0;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (a.mode & M_ADVANCE) *a.sh->counter = k + 1;
+        *a.ticket = 0u;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ).
 // ---------------------------------------------------------------------------
@@ -560,8 +633,11 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool store_r = (a.mode & M_STORE_R) != 0;
     const bool obj = (a.mode & M_OBJ) != 0;
+    // A stopped volume's item gets an empty range: no copies, no loop, zero
+    // partials, but it still takes its ticket.
+    const bool stopped = vol_stopped(a, sg.vol);
 
-    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, G::NSF, smem, a.sh->status)) return;
     Pipe<G::NSF, G::SLOT> px;
@@ -570,7 +646,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     px.issue_upto(zbeg + PREF - 1);
     __syncthreads();
 
-    float acc[3] = {0.f, 0.f, 0.f};
+    float acc[3] = {0.f, 0.f, 0.f};           // data, box, penalty
     const int y0 = warp * RPW;
     const int gx = it.tx0 + lane;
     const bool colin = gx < nx;
@@ -651,30 +727,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         }
     }
     if (!obj) return;
-    if (!publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) return;
-    // Last CTA: objective per volume slot, trace, counter.
-    __shared__ double tot[3];
-    const int k = *a.sh->counter;
-    for (int sl = 0; sl < a.nslots; ++sl) {
-        sum_slot<3>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
-        if (tid == 0) {
-            const int vid = a.slot_id[sl];
-            const VolDev &vv = a.vols[vid];
-            const double f1 = tot[0], f2 = vv.eta_d * tot[1], f3 = vv.lam_d * tot[2];
-            const double f = f1 + f2 + f3;
-            a.fout[vid * 4 + 0] = f;
-            a.fout[vid * 4 + 1] = f1;
-            a.fout[vid * 4 + 2] = f2;
-            a.fout[vid * 4 + 3] = f3;
-            if (!isfinite(f)) atomicOr(a.sh->status, ST_NONFINITE);
-            if ((a.mode & M_TRACE) && k < a.sh->trace_cap) a.sh->trace[(size_t)vid * a.sh->trace_cap + k] = f;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        if (a.mode & M_ADVANCE) *a.sh->counter = k + 1;
-        *a.ticket = 0u;
-    }
+    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -702,6 +755,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool full = (a.mode & M_HT_ONLY) == 0;
+    if (vol_stopped(a, sg.vol)) return;
 
     const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
@@ -810,6 +864,55 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     }
 }
 
+// Last CTA of a curvature launch: per slab slot, B = D^T A D and c = D^T grad f
+// (D = [-g, d]) from the FP64 sums, u = -B^+ c, and the squared length of the
+// step D u added to the volume's sweep total.  Slots of stopped volumes get u = 0.
+static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
+    __shared__ double tot[10];
+    const int tid = threadIdx.x;
+    for (int sl = 0; sl < a.nslots; ++sl) {
+        const int slot = a.slot_id[sl];
+        const SegDev ss = a.segs[a.items[a.slot_beg[sl]].seg];
+        if (vol_stopped(a, ss.vol)) {
+            if (tid == 0) {
+                a.u[2 * slot] = 0.0;
+                a.u[2 * slot + 1] = 0.0;
+            }
+            continue;
+        }
+        sum_slot<10>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
+        if (tid == 0) {
+            const VolDev &vv = a.vols[ss.vol];
+            const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
+            const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
+            const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
+            const double b11 = tot[5] + e2 * tot[2] + lam * tot[8];
+            const double c0 = -tot[0], c1 = tot[1];
+            double u0 = 0.0, u1 = 0.0;
+            int rank = 0;
+            if (isfinite(b00) && isfinite(b01) && isfinite(b11) && isfinite(c0) && isfinite(c1)) {
+                rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
+            } else {
+                atomicOr(a.sh->status, ST_NONFINITE);
+            }
+            a.u[2 * slot] = u0;
+            a.u[2 * slot + 1] = u1;
+            double *inf = a.info + 8 * slot;
+            inf[0] = b00; inf[1] = b01; inf[2] = b11; inf[3] = c0; inf[4] = c1;
+            inf[5] = u0; inf[6] = u1; inf[7] = (double)rank;
+            // Slab S of the sweep from x^k: x_S still holds x^k_S (only its own
+            // update writes it), and the step is ||-u0 g + u1 d||^2 over S.
+            if (a.sh->run) {
+                VolRun &rv = a.sh->run[ss.vol];
+                rv.dx2 += u0 * u0 * tot[0] - 2.0 * u0 * u1 * tot[1] + u1 * u1 * tot[2];
+                rv.xx_prev += tot[9];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *a.ticket = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // k_curvature: nine inner products of the restricted subspace system and, in
 // the last CTA, the per-slab 2x2 solve.
@@ -840,8 +943,11 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     const float delta2 = V.delta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
+    // A stopped volume's item gets empty ranges: no copies, no loop, zero
+    // partials, but it still takes its ticket.
+    const bool stopped = vol_stopped(a, sg.vol);
 
-    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, 2 * G::NSF + NSX, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
@@ -851,7 +957,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     pd.init(sds, bar + G::NSF, &a.maps[sg.vol].m[TM_D_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
     // x slices for the penalty at outputs zo in [max(zo0, pen_lo), min(zo1, pen_hi)): x(zo), x(zo+1)
     const int xfirst = max(it.zo0, pen_lo);
-    const int xlo = max(0, xfirst), xhi = min(nz, min(it.zo1, pen_hi) + 1);
+    const int xlo = max(0, xfirst), xhi = stopped ? xlo : min(nz, min(it.zo1, pen_hi) + 1);
     Pipe<NSX, G::SLOT1> px;
     px.init(xs, bar + 2 * G::NSF, &a.maps[sg.vol].m[TM_X_1C], it.tx0 - XH1, it.ty0 - 1, xlo, xhi,
             (uint32_t)(BX1 * G::BY1 * sizeof(float)), xfirst);
@@ -860,9 +966,9 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     px.issue_upto(zbeg - RZ + PREF);
     __syncthreads();
 
-    float acc[9];
+    float acc[10];                            // 9 subspace sums, ||x_S||^2
 #pragma unroll
-    for (int p = 0; p < 9; ++p) acc[p] = 0.f;
+    for (int p = 0; p < 10; ++p) acc[p] = 0.f;
     const int y0 = warp * RPW;
     const int gx = it.tx0 + lane;
     const bool colin = gx < nx;
@@ -935,6 +1041,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
                         acc[0] = fmaf(gc, gc, acc[0]);
                         acc[1] = fmaf(gc, dc, acc[1]);
                         acc[2] = fmaf(dc, dc, acc[2]);
+                        acc[9] = fmaf(xc, xc, acc[9]);
                     }
                     if (gx < nx - 1) {
                         const float t = xz0[xi + 1] - xc, w = rsqrtf(fmaf(t, t, delta2));
@@ -961,35 +1068,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
             }
         }
     }
-    if (!publish_partials<9>(acc, a.partials, a.ticket, a.nitems)) return;
-    __shared__ double tot[9];
-    for (int sl = 0; sl < a.nslots; ++sl) {
-        sum_slot<9>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
-        if (tid == 0) {
-            const int slot = a.slot_id[sl];
-            const SegDev ss = a.segs[a.items[a.slot_beg[sl]].seg];
-            const VolDev &vv = a.vols[ss.vol];
-            const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
-            const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
-            const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
-            const double b11 = tot[5] + e2 * tot[2] + lam * tot[8];
-            const double c0 = -tot[0], c1 = tot[1];
-            double u0 = 0.0, u1 = 0.0;
-            int rank = 0;
-            if (isfinite(b00) && isfinite(b01) && isfinite(b11) && isfinite(c0) && isfinite(c1)) {
-                rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
-            } else {
-                atomicOr(a.sh->status, ST_NONFINITE);
-            }
-            a.u[2 * slot] = u0;
-            a.u[2 * slot + 1] = u1;
-            double *inf = a.info + 8 * slot;
-            inf[0] = b00; inf[1] = b01; inf[2] = b11; inf[3] = c0; inf[4] = c1;
-            inf[5] = u0; inf[6] = u1; inf[7] = (double)rank;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) *a.ticket = 0u;
+    if (publish_partials<10>(acc, a.partials, a.ticket, a.nitems)) curvature_finish(a);
 }
 
 }  // namespace bd3mg

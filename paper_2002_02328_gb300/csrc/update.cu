@@ -9,15 +9,17 @@ namespace bd3mg {
 
 // ---------------------------------------------------------------------------
 // k_update: x_S += -u0 g_S + u1 d_S, d_S = -u0 g_S + u1 d_S over each slab's
-// contiguous slices (blockIdx.y = slab of this launch).  Planes are multiples
-// of 8 elements, so every slab starts on a 16-byte boundary of every array.
+// contiguous slices (blockIdx.y = slab of this launch); slabs of stopped
+// volumes are skipped.  Planes are multiples of 8 elements, so every slab
+// starts on a 16-byte boundary of every array.
 // BF: directions stored as BF16 (the increment is formed in FP32; x gets the
 // FP32 increment, d keeps its BF16 rounding).
 // ---------------------------------------------------------------------------
 template <bool BF>
 __global__ void __launch_bounds__(NT) k_update(const VolDev *vols, const SegDev *segs, const int *seg_list,
-                                               const double *u) {
+                                               const double *u, const VolRun *run) {
     const SegDev sg = segs[seg_list[blockIdx.y]];
+    if (run && run[sg.vol].stopped) return;
     const VolDev &v = vols[sg.vol];
     const float u0 = (float)u[2 * sg.slot], u1 = (float)u[2 * sg.slot + 1];
     const long long beg = (long long)sg.z0 * v.plane, end = (long long)sg.z1 * v.plane;
@@ -64,10 +66,10 @@ __global__ void __launch_bounds__(NT) k_dir_to_float(const __nv_bfloat16 *src, f
         dst[i] = __bfloat162float(src[i]);
 }
 
-void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, dim3 grid,
-                   cudaStream_t s, bool bf16) {
-    if (bf16) k_update<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u);
-    else k_update<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u);
+void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
+                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16) {
+    if (bf16) k_update<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+    else k_update<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
 }
 
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s) {
