@@ -298,13 +298,14 @@ def fstar_of(prob, iters):
     return f, settle
 
 
-def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0):
-    """Iterations to gap <= 1e-4 (from the trace), then the device time of exactly that many."""
+def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0, normalized=False):
+    """Iterations to gap <= 1e-4 (from the trace), then the device time of exactly that many.
+    gap = (f - f*)/|f*|, or (f - f*)/(f0 - f*) when normalized."""
     import torch
     from paper_2002_02328_gb300 import binding
     with binding.Solver.from_problem(prob, slabs=slabs, precision=precision) as s:
         tr = s.iterate(max_iters)
-    gap = (tr - fstar) / abs(fstar)
+    gap = (tr - fstar) / (abs(tr[0] - fstar) if normalized else abs(fstar))
     hit = np.nonzero(gap <= GAP)[0]
     if hit.size == 0:
         return None, None, float(gap[-1])
@@ -375,6 +376,33 @@ def batch_extra(iters, stream):
                               "batched_lockstep": (max(k) * t_batch) if ok else None,
                               "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None},
             "stopped_after": k_stop}
+
+
+def mixed_extra(fstar_iters, stream, flush, steps):
+    """512x512x128 volume, 800 ellipsoids + texture, PSF 9x9x7 (sigma_xy 0.5->3.0), noise 0.01:
+    plain 3MG with FP32 directions against BF16 directions (iterations/s with the L2 flushed
+    before every step, and device time to gap 1e-4; f* from a long FP32 run)."""
+    from paper_2002_02328_gb300 import binding, synth
+    prob = synth.workload_mixed(seed=0)
+    out = {"workload": "plain 3MG 512x512x128, PSF 9x9x7 depth-variant Gaussian, 800 ellipsoids + texture",
+           "voxels": prob.n}
+    for name, prec in (("fp32", binding.FP32), ("bf16_directions", binding.BF16_DIRECTIONS)):
+        with binding.Solver.from_problem(prob, slabs=None, precision=prec) as s:
+            for _ in range(3):
+                flush.fill_(1.0)
+                s.iterate_async(1)
+            ms = time_steps(s, steps, flush, stream)
+            prof = s.profile_iteration()
+        out[name] = {"iterations_per_s": 1e3 * steps / ms,
+                     "kernel_ms_per_iteration": {k: v[0] for k, v in prof.items()}}
+    fstar, settle = fstar_of(prob, fstar_iters)
+    out.update({"fstar": fstar, "fstar_iters": fstar_iters, "fstar_settle_rel": settle})
+    for name, prec in (("fp32", binding.FP32), ("bf16_directions", binding.BF16_DIRECTIONS)):
+        k, t, g = time_to_gap(prob, None, fstar, 3000, stream, prec)
+        kn, tn, gn = time_to_gap(prob, None, fstar, 3000, stream, prec, normalized=True)
+        out[name]["time_to_gap"] = {"iterations": k, "seconds": t, "gap_reached": g}
+        out[name]["time_to_normalized_gap"] = {"iterations": kn, "seconds": tn, "gap_reached": gn}
+    return out
 
 
 def e2e_run(prob, n_iter, stream):
@@ -522,13 +550,19 @@ def ours(args):
         k_p, t_p, g_p = time_to_gap(prob, None, fstar, 3000, stream)
         k_m, t_m, g_m = time_to_gap(prob, prob.slabs, fstar, 3000, stream, binding.BF16_DIRECTIONS)
         k_mp, t_mp, g_mp = time_to_gap(prob, None, fstar, 3000, stream, binding.BF16_DIRECTIONS)
+        k_bn, t_bn, _ = time_to_gap(prob, prob.slabs, fstar, 3000, stream, normalized=True)
+        k_pn, t_pn, _ = time_to_gap(prob, None, fstar, 3000, stream, normalized=True)
         extra["time_to_gap"] = {"gap": GAP, "fstar": fstar, "fstar_iters": args.fstar_iters,
                                 "fstar_settle_rel": settle,
                                 "block": {"iterations": k_b, "seconds": t_b},
                                 "plain_fp32": {"iterations": k_p, "seconds": t_p},
                                 "block_bf16_directions": {"iterations": k_m, "seconds": t_m},
-                                "plain_bf16_directions": {"iterations": k_mp, "seconds": t_mp}}
+                                "plain_bf16_directions": {"iterations": k_mp, "seconds": t_mp},
+                                "normalized_gap": {"definition": "(f - f*) / (f0 - f*) <= 1e-4",
+                                                   "block": {"iterations": k_bn, "seconds": t_bn},
+                                                   "plain_fp32": {"iterations": k_pn, "seconds": t_pn}}}
         extra["batched"] = batch_extra(min(args.fstar_iters, 3000), stream)
+        extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
         e2e_rate, h2d, d2h, e2e_s = e2e_run(prob, 500, stream)
         e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}

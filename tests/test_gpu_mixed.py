@@ -80,3 +80,31 @@ def test_mixed_batch_precisions_rejected(cuda_lib):
     probs = [synth.tiny_problem(shape=(8, 16, 16), psf_shape=(3, 3, 3), seed=27)] * 2
     with pytest.raises(cuda_lib.Bd3mgError, match="precision"):
         cuda_lib.BatchSolver(probs, precision=[cuda_lib.FP32, cuda_lib.BF16_DIRECTIONS])
+
+
+def test_crop_errors_against_oracle(cuda_lib):
+    """Errors of both precisions against the FP64 oracle on the 128x128x32 crop
+    of the 512x512x128 recipe (PSF 9x9x7): f and g at x0 = y, and f and x after
+    10 sweeps.  BF16 directions leave f(x0) unchanged (it does not involve them),
+    round g to 8 significand bits, and perturb the later steps."""
+    p = synth.workload_mixed(seed=0, crop=True)
+    oracle.set_threads(oracle.max_threads())
+    op = oracle.OracleProblem.from_synth(p)
+    f0 = oracle.objective(op, p.y, p.y)
+    g0 = oracle.gradient(op, p.y, p.y)
+    n = 10
+    xr, _, fr = oracle.run(op, p.y, p.y, n)
+    errs = {}
+    for prec in (cuda_lib.FP32, cuda_lib.BF16_DIRECTIONS):
+        with cuda_lib.Solver.from_problem(p, slabs=None, precision=prec) as s:
+            g, f = s.gradient()
+            tr = s.iterate(n)
+            x = s.get_x().cpu().numpy()
+        errs[prec] = dict(f0=abs(f - f0) / abs(f0), g0=_rel(g.cpu().numpy(), g0),
+                          f10=abs(tr[-1] - fr[-1]) / abs(fr[-1]), x10=_rel(x, xr))
+    print("crop errors vs oracle:", errs)
+    e32, ebf = errs[cuda_lib.FP32], errs[cuda_lib.BF16_DIRECTIONS]
+    assert e32["f0"] <= 1e-5 and e32["g0"] <= 1e-5 and e32["f10"] <= 1e-5 and e32["x10"] <= 1e-4
+    assert ebf["f0"] <= 1e-5
+    assert ebf["g0"] <= 2.0 ** -8                     # per-element rounding bound, in norm
+    assert ebf["f10"] <= 1e-4 and ebf["x10"] <= 1e-2
