@@ -1,0 +1,529 @@
+// unet_kernels.cuh -- device kernels of the learned warm start (a 3D U-Net),
+// BF16 activations in channels-last layout [B][D][H][W][C], FP32 accumulation.
+//
+// Dense contractions run on the tcgen05 tensor cores as implicit GEMMs:
+//   k_gemm   rows (M = 128 output voxels per CTA) x output channels (N), the
+//            reduction K = taps x input channels.  A is gathered row by row
+//            from the activation tensor (zero outside the volume) with 16-byte
+//            cp.async copies into K-major shared tiles, B is the tap's weight
+//            slab [N][K]; one thread issues the MMAs, the accumulator lives in
+//            TMEM and the epilogue (bias, ReLU, gradient mask, BF16 rounding,
+//            strided or scattered store) reads it back with tcgen05.ld.
+//            Gather maps: CONV3 (3x3x3, same grid: the forward convolution,
+//            and its input gradient with flipped, transposed weights), UPFWD
+//            (2x2x2 stride-2 transposed convolution, one tap per grid row,
+//            scattered to the fine grid) and UPBWD (its input gradient:
+//            8 taps gathered from the fine grid).
+//   k_wgrad  weight gradients: rows = output channels (padded to 128), columns
+//            = input channels, K = voxels; both operands are transposed while
+//            they are staged (channels-last -> K-major), per-split FP32
+//            partials are summed in a fixed order by k_split_sum.
+// Everything else (pooling, head, loss, bias sums, Adam, weight packing) is
+// plain CUDA-core code.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+#include "umma.cuh"
+
+namespace bd3mg {
+namespace unet {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int GT = 128;          // threads of the GEMM kernels (4 warps: one per 32 TMEM lanes)
+constexpr int GM = 128;          // rows (M) per CTA
+constexpr int STAGES = 3;        // shared-memory pipeline depth of k_gemm
+constexpr int KV = 64;           // voxels (K) per k_wgrad block
+
+enum GatherMode { G_CONV3 = 0, G_UPFWD = 1, G_UPBWD = 2 };
+
+constexpr int ST_MMA_TIMEOUT = 4;
+
+struct GemmArgs {
+    int mode;
+    int B, D, H, W;              // grid of the output rows (CONV3, UPBWD) or of the coarse rows (UPFWD)
+    long long M;                 // number of rows = B*D*H*W
+    const bf16 *A;               // source activations, rows of lda elements
+    int lda;
+    int K;                       // channels per tap (multiple of 16)
+    int KC;                      // channels per K block (16, 32 or 64; divides K)
+    const bf16 *Wt;              // [T][N][K]
+    int N;                       // output channels (multiple of 16, <= 256)
+    int T;                       // taps reduced in this launch (CONV3 27, UPBWD 8, UPFWD 1)
+    const float *bias;           // [N] or null
+    int relu;
+    const bf16 *mask;            // out *= (mask > 0) per element, rows of ldm; or null
+    int ldm;
+    bf16 *out;                   // rows of ldo elements (UPFWD: fine grid rows)
+    int ldo;
+    int *status;
+};
+
+// Source row of output row (b, z, y, x) for tap t, or -1 (zero fill).
+__device__ __forceinline__ long long gather_src(const GemmArgs &a, long long v, int b, int z, int y, int x, int t) {
+    if (a.mode == G_CONV3) {
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        const int zz = z + dz, yy = y + dy, xx = x + dx;
+        if (zz < 0 || zz >= a.D || yy < 0 || yy >= a.H || xx < 0 || xx >= a.W) return -1;
+        return v + ((long long)dz * a.H + dy) * a.W + dx;
+    }
+    if (a.mode == G_UPBWD) {
+        const int az = t >> 2, ay = (t >> 1) & 1, ax = t & 1;
+        const long long FH = 2LL * a.H, FW = 2LL * a.W;
+        return (((long long)b * 2 * a.D + 2 * z + az) * FH + 2 * y + ay) * FW + 2 * x + ax;
+    }
+    return v;   // UPFWD reads the coarse row itself
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+// ---------------------------------------------------------------------------
+// k_gemm: implicit-GEMM convolution on tcgen05 (see the file comment).
+// Dynamic shared memory: STAGES x (A tile 128 x KC | B tile N x KC) + barriers.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int KC = a.KC, N = a.N;
+    const uint32_t a_bytes = GM * KC * 2, b_bytes = (uint32_t)N * KC * 2;
+    const uint32_t stage_bytes = a_bytes + b_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + STAGES * stage_bytes);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + STAGES);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tap_y = blockIdx.y;                  // UPFWD: the tap of this launch row
+    const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(bar + s, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, ncols);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // this thread's A row
+    const long long m0 = (long long)blockIdx.x * GM;
+    const long long v = m0 + tid;
+    const bool row_ok = v < a.M;
+    int xb = 0, yb = 0, zb = 0, bb = 0;
+    if (row_ok) {
+        long long t1 = v / a.W;
+        xb = (int)(v - t1 * a.W);
+        long long t2 = t1 / a.H;
+        yb = (int)(t1 - t2 * a.H);
+        bb = (int)(t2 / a.D);
+        zb = (int)(t2 - (long long)bb * a.D);
+    }
+    const int kpt = a.K / KC;                      // K blocks per tap
+    const int nk = a.T * kpt;
+    const int cpr = KC / 8;                        // 16-byte chunks per row of a block
+
+    auto load_block = [&](int kb, int slot) {
+        uint8_t *As = sm + slot * stage_bytes;
+        uint8_t *Bs = As + a_bytes;
+        const int t = kb / kpt, c0 = (kb - t * kpt) * KC;
+        const int tw = a.mode == G_UPFWD ? tap_y : t;
+        long long src = row_ok ? gather_src(a, v, bb, zb, yb, xb, t) : -1;
+        const bf16 *ap = src >= 0 ? a.A + src * a.lda + c0 : a.A;
+        const uint32_t nb = src >= 0 ? 16u : 0u;
+        for (int kg = 0; kg < cpr; ++kg) umma::cp_async16(As + kg * (GM * 16) + tid * 16, ap + (src >= 0 ? kg * 8 : 0), nb);
+        const bf16 *wp = a.Wt + (long long)tw * N * a.K + c0;
+        for (int q = tid; q < N * cpr; q += GT) {
+            const int n = q / cpr, kg = q - n * cpr;
+            umma::cp_async16(Bs + kg * (N * 16) + n * 16, wp + (long long)n * a.K + kg * 8, 16u);
+        }
+    };
+
+    const uint32_t idesc = umma::idesc_bf16(GM, N);
+    bool ok = true;
+#pragma unroll 1
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < nk) load_block(s, s);
+        umma::cp_async_commit();
+    }
+#pragma unroll 1
+    for (int kb = 0; kb < nk; ++kb) {
+        const int slot = kb % STAGES;
+        umma::cp_async_wait<STAGES - 2>();
+        umma::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t as = umma::smem_addr(sm + slot * stage_bytes), bs = as + a_bytes;
+            for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint64_t ad = umma::desc(as + kk * 2 * (GM * 16), GM * 16, 128);
+                const uint64_t bd = umma::desc(bs + kk * 2 * (N * 16), N * 16, 128);
+                umma::mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma::commit(bar + slot);
+        }
+        const int nxt = kb + STAGES - 1;
+        if (nxt < nk) {
+            const int ns = nxt % STAGES;
+            if (nxt >= STAGES) ok = mbar_wait(bar + ns, (uint32_t)((nxt / STAGES - 1) & 1)) && ok;
+            load_block(nxt, ns);
+        }
+        umma::cp_async_commit();
+    }
+    umma::cp_async_wait<0>();
+    ok = mbar_wait(bar + (nk - 1) % STAGES, (uint32_t)(((nk - 1) / STAGES) & 1)) && ok;
+    if (!ok && lane == 0) atomicOr(a.status, ST_MMA_TIMEOUT);
+    umma::fence_after_sync();
+
+    // epilogue: row m = 32*warp + lane of the TMEM accumulator
+    bf16 *orow = nullptr;
+    const bf16 *mrow = nullptr;
+    if (row_ok) {
+        long long o = v;
+        if (a.mode == G_UPFWD) {
+            const int az = tap_y >> 2, ay = (tap_y >> 1) & 1, ax = tap_y & 1;
+            o = (((long long)bb * 2 * a.D + 2 * zb + az) * (2LL * a.H) + 2 * yb + ay) * (2LL * a.W) + 2 * xb + ax;
+        }
+        orow = a.out + o * a.ldo;
+        if (a.mask) mrow = a.mask + o * a.ldm;
+    }
+    for (int c = 0; c < N; c += 16) {
+        float acc[16];
+        umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, acc);
+        if (!row_ok) continue;
+        if (a.bias) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
+        }
+        if (a.relu) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = fmaxf(acc[i], 0.f);
+        }
+        if (mrow) {
+            const uint4 m0v = *reinterpret_cast<const uint4 *>(mrow + c);
+            const uint4 m1v = *reinterpret_cast<const uint4 *>(mrow + c + 8);
+            const bf16 *mh0 = reinterpret_cast<const bf16 *>(&m0v), *mh1 = reinterpret_cast<const bf16 *>(&m1v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (!(__bfloat162float(mh0[i]) > 0.f)) acc[i] = 0.f;
+                if (!(__bfloat162float(mh1[i]) > 0.f)) acc[8 + i] = 0.f;
+            }
+        }
+        uint4 o0, o1;
+        o0.x = pack2(acc[0], acc[1]);   o0.y = pack2(acc[2], acc[3]);
+        o0.z = pack2(acc[4], acc[5]);   o0.w = pack2(acc[6], acc[7]);
+        o1.x = pack2(acc[8], acc[9]);   o1.y = pack2(acc[10], acc[11]);
+        o1.z = pack2(acc[12], acc[13]); o1.w = pack2(acc[14], acc[15]);
+        *reinterpret_cast<uint4 *>(orow + c) = o0;
+        *reinterpret_cast<uint4 *>(orow + c + 8) = o1;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
+// k_wgrad: dW[t][co][ci] = sum_v dZ[v][co] * X[src(v, t)][ci] over this CTA's
+// voxel range (blockIdx.x = split, blockIdx.y = tap), FP32 partial out.
+//   CONV3: v over the conv's grid, src = v shifted by tap t (zero outside).
+//   UPW:   v over the coarse grid, dZ read at the fine voxel of tap t, X at v.
+// ---------------------------------------------------------------------------
+enum WgradMode { W_CONV3 = 0, W_UP = 1 };
+
+struct WgradArgs {
+    int mode;
+    int B, D, H, W;              // grid of v
+    long long V;                 // number of v
+    const bf16 *dz;              // rows of lddz (CONV3: grid of v; UP: fine grid)
+    int lddz, Cout;              // Cout multiple of 16, <= 128
+    const bf16 *x;               // rows of ldx (grid of v)
+    int ldx, Cin;                // Cin multiple of 16, <= 256
+    int splits;
+    long long per_split;         // voxels per split (multiple of KV)
+    float *part;                 // [splits][T][Cout][Cin]
+    int T;
+    int *status;
+};
+
+__global__ void __launch_bounds__(GT, 1) k_wgrad(WgradArgs a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int Cin = a.Cin, Cout = a.Cout;
+    const uint32_t a_bytes = GM * KV * 2, b_bytes = (uint32_t)Cin * KV * 2, stage = a_bytes + b_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * stage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t = blockIdx.y, split = blockIdx.x;
+    const uint32_t ncols = Cin <= 32 ? 32u : (Cin <= 64 ? 64u : (Cin <= 128 ? 128u : 256u));
+
+    // rows >= Cout of both A stages stay zero for the whole kernel
+    for (int i = tid; i < (int)(2 * stage / 16); i += GT) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init(bar + 1, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, ncols);
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    const long long vb = (long long)split * a.per_split;
+    const long long ve = min(a.V, vb + a.per_split);
+    const int nk = ve > vb ? (int)((ve - vb + KV - 1) / KV) : 0;
+    const int az = t >> 2, ay = (t >> 1) & 1, ax = t & 1;
+    const int dz3 = t / 9 - 1, dy3 = (t / 3) % 3 - 1, dx3 = t % 3 - 1;
+    const uint32_t idesc = umma::idesc_bf16(GM, Cin);
+    bool ok = true;
+
+#pragma unroll 1
+    for (int kb = 0; kb < nk; ++kb) {
+        const int slot = kb & 1;
+        uint8_t *As = sm + slot * stage, *Bs = As + a_bytes;
+        if (kb >= 2) ok = mbar_wait(bar + slot, (uint32_t)((kb / 2 - 1) & 1)) && ok;
+        // stage: voxel k of the block, 8-channel chunk cg; element (row, k) at
+        // (k/8)*LBO + (row/8)*128 + (row%8)*16 + (k%8)*2
+        const int cga = Cout / 8, cgb = Cin / 8;
+        for (int q = tid; q < KV * (cga + cgb); q += GT) {
+            const int k = q % KV, cg = q / KV;
+            const long long v = vb + (long long)kb * KV + k;
+            uint4 val = make_uint4(0, 0, 0, 0);
+            uint8_t *base;
+            uint32_t lbo;
+            int row0;
+            if (v < ve) {
+                long long t1 = v / a.W;
+                const int x = (int)(v - t1 * a.W);
+                long long t2 = t1 / a.H;
+                const int y = (int)(t1 - t2 * a.H);
+                const int b = (int)(t2 / a.D);
+                const int z = (int)(t2 - (long long)b * a.D);
+                if (cg < cga) {
+                    long long r = v;
+                    if (a.mode == W_UP)
+                        r = (((long long)b * 2 * a.D + 2 * z + az) * (2LL * a.H) + 2 * y + ay) * (2LL * a.W) + 2 * x + ax;
+                    val = *reinterpret_cast<const uint4 *>(a.dz + r * a.lddz + cg * 8);
+                } else {
+                    long long r = v;
+                    bool in = true;
+                    if (a.mode == W_CONV3) {
+                        const int zz = z + dz3, yy = y + dy3, xx = x + dx3;
+                        in = zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                        r = v + ((long long)dz3 * a.H + dy3) * a.W + dx3;
+                    }
+                    if (in) val = *reinterpret_cast<const uint4 *>(a.x + r * a.ldx + (cg - cga) * 8);
+                }
+            }
+            if (cg < cga) { base = As; lbo = GM * 16; row0 = cg * 8; }
+            else { base = Bs; lbo = (uint32_t)Cin * 16; row0 = (cg - cga) * 8; }
+            const uint16_t *h = reinterpret_cast<const uint16_t *>(&val);
+            uint8_t *p = base + (k >> 3) * lbo + (row0 >> 3) * 128 + (k & 7) * 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint16_t *>(p + j * 16) = h[j];
+        }
+        umma::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t as = umma::smem_addr(As), bs = umma::smem_addr(Bs);
+            for (int kk = 0; kk < KV / 16; ++kk) {
+                const uint64_t ad = umma::desc(as + kk * 2 * (GM * 16), GM * 16, 128);
+                const uint64_t bd = umma::desc(bs + kk * 2 * (Cin * 16), Cin * 16, 128);
+                umma::mma_bf16(tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+            }
+            umma::commit(bar + slot);
+        }
+    }
+    if (nk > 0) ok = mbar_wait(bar + ((nk - 1) & 1), (uint32_t)(((nk - 1) / 2) & 1)) && ok;
+    if (!ok && lane == 0) atomicOr(a.status, ST_MMA_TIMEOUT);
+    umma::fence_after_sync();
+    const int co = warp * 32 + lane;
+    float *prow = a.part + (((long long)split * a.T + t) * Cout + co) * Cin;
+    for (int c = 0; c < Cin; c += 16) {
+        float acc[16];
+        umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, acc);
+        if (co >= Cout) continue;
+        if (nk == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[i] = 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4 *>(prow + c + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+}
+
+// Fixed-order sum of per-split partials: for row r < rows and column c < co,
+// out[r * co + c] = sum_k part[k * stride + r * cp + c] (cp >= co: columns
+// beyond co are dropped).
+__global__ void k_split_sum(const float *part, int splits, long long stride, long long rows, int cp, int co,
+                            float *out) {
+    const long long n = rows * co;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / co;
+        const int c = (int)(i - r * co);
+        float s = 0.f;
+        for (int k = 0; k < splits; ++k) s += part[(long long)k * stride + r * cp + c];
+        out[i] = s;
+    }
+}
+
+// Column sums: part[blk][c] = sum over this block's rows of x[row][c] (rows of
+// ld), C <= 256 channels; blockDim.x = 256, thread = channel (c < C).
+__global__ void k_colsum(const bf16 *x, int ld, int C, long long rows, long long rows_per_blk, float *part) {
+    const int c = threadIdx.x;
+    const long long r0 = (long long)blockIdx.x * rows_per_blk, r1 = min(rows, r0 + rows_per_blk);
+    if (c >= C) return;
+    float s = 0.f;
+    for (long long r = r0; r < r1; ++r) s += __bfloat162float(x[r * ld + c]);
+    part[(long long)blockIdx.x * C + c] = s;
+}
+
+// 2x2x2 max pooling of a [B][2D][2H][2W][C] tensor (rows of ld) into
+// out [B][D][H][W][C] and the tap (0..7) of the first maximum.
+__global__ void k_maxpool(const bf16 *in, int ld, int C, int B, int D, int H, int W, bf16 *out, uint8_t *arg) {
+    const long long n = (long long)B * D * H * W * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        long long v = i / C;
+        const int x = (int)(v % W); v /= W;
+        const int y = (int)(v % H); v /= H;
+        const int z = (int)(v % D);
+        const int b = (int)(v / D);
+        float best = -INFINITY;
+        int bi = 0;
+        for (int a = 0; a < 8; ++a) {
+            const int az = a >> 2, ay = (a >> 1) & 1, ax = a & 1;
+            const long long u = (((long long)b * 2 * D + 2 * z + az) * (2LL * H) + 2 * y + ay) * (2LL * W) + 2 * x + ax;
+            const float val = __bfloat162float(in[u * ld + c]);
+            if (val > best) { best = val; bi = a; }
+        }
+        out[i] = __float2bfloat16_rn(best);
+        arg[i] = (uint8_t)bi;
+    }
+}
+
+// Gradient at the output of a ReLU layer whose activation act (rows of lda)
+// feeds both a skip path (gradient dskip, rows of lds, may be null) and a 2x2x2
+// max pooling (gradient dpool on the coarse grid, argmax arg; may be null):
+// dz[u][c] = (dskip + [u is the window's argmax] dpool) * (act > 0), fine grid
+// [B][2D][2H][2W] (D, H, W: coarse extents).
+__global__ void k_pool_bwd(const bf16 *dskip, int lds, const bf16 *dpool, const uint8_t *arg, const bf16 *act,
+                           int lda, int C, int B, int D, int H, int W, bf16 *dz) {
+    const long long n = (long long)B * 8 * D * H * W * C;
+    const long long FW = 2LL * W, FH = 2LL * H, FD = 2LL * D;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long u = i / C;
+        long long r = u;
+        const int x = (int)(r % FW); r /= FW;
+        const int y = (int)(r % FH); r /= FH;
+        const int z = (int)(r % FD);
+        const int b = (int)(r / FD);
+        float g = dskip ? __bfloat162float(dskip[u * lds + c]) : 0.f;
+        if (dpool) {
+            const long long vc = (((long long)b * D + (z >> 1)) * H + (y >> 1)) * W + (x >> 1);
+            const int tap = ((z & 1) << 2) | ((y & 1) << 1) | (x & 1);
+            if (arg[vc * C + c] == tap) g += __bfloat162float(dpool[vc * C + c]);
+        }
+        if (!(__bfloat162float(act[u * lda + c]) > 0.f)) g = 0.f;
+        dz[u * C + c] = __float2bfloat16_rn(g);
+    }
+}
+
+// Network input [V][cin] FP32 -> BF16 rows of 16 channels (zero padded).
+__global__ void k_pack_input(const float *inp, int cin, long long V, bf16 *out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i & 15);
+        const long long v = i >> 4;
+        out[i] = __float2bfloat16_rn(c < cin ? inp[v * cin + c] : 0.f);
+    }
+}
+
+// Head: pred[v] = base[v] + b + sum_c w[c] h[v][c] (1x1x1 convolution, residual output).
+__global__ void k_head_fwd(const bf16 *h, int C, long long V, const float *w, const float *b, const float *base,
+                           float *pred) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < C; ++c) s = fmaf(w[c], __bfloat162float(h[v * C + c]), s);
+        pred[v] = (base ? base[v] : 0.f) + b[0] + s;
+    }
+}
+
+// MSE loss mean((pred - target)^2) and the backward pass through the head:
+// dout = 2 (pred - target) / V; dz[v][c] = dout w[c] (h > 0) (ReLU of the last
+// decoder layer); per-block partials: loss (FP64), sum_v dout h[v][c] and
+// sum_v dout (FP32, C + 1 per block).  blockDim.x = 256.
+__global__ void k_head_bwd(const float *pred, const float *target, const bf16 *h, int C, long long V,
+                           const float *w, bf16 *dz, double *loss_part, float *wpart) {
+    __shared__ double sl[256];
+    __shared__ float sw[256][17];
+    const int tid = threadIdx.x;
+    double l = 0.0;
+    float acc[17];
+    for (int c = 0; c <= 16; ++c) acc[c] = 0.f;
+    const float inv = 2.f / (float)V;
+    for (long long v = (long long)blockIdx.x * blockDim.x + tid; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const float diff = pred[v] - target[v];
+        l += (double)diff * (double)diff;
+        const float g = inv * diff;
+        for (int c = 0; c < C; ++c) {
+            const float hv = __bfloat162float(h[v * C + c]);
+            acc[c] = fmaf(g, hv, acc[c]);
+            dz[v * C + c] = __float2bfloat16_rn(hv > 0.f ? g * w[c] : 0.f);
+        }
+        acc[16] += g;
+    }
+    sl[tid] = l;
+    for (int c = 0; c <= 16; ++c) sw[tid][c] = acc[c];
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 256; ++i) s += sl[i];
+        loss_part[blockIdx.x] = s;
+    }
+    if (tid <= 16) {
+        float s = 0.f;
+        for (int i = 0; i < 256; ++i) s += sw[i][tid];
+        wpart[blockIdx.x * 17 + tid] = s;
+    }
+}
+
+// Pack FP32 master weights [T][Cout][Cin] into the BF16 forward layout
+// [T][Cout][Cinp] (zero padded) and, when wt != null, the input-gradient
+// layout [T][Cinp][Cout] with taps reversed for 3x3x3 kernels (flip = 1).
+__global__ void k_pack_weights(const float *w, int T, int Cout, int Cin, int Cinp, int flip, bf16 *wf, bf16 *wt) {
+    const long long n = (long long)T * Cout * Cinp;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int ci = (int)(i % Cinp);
+        const int co = (int)((i / Cinp) % Cout);
+        const int t = (int)(i / ((long long)Cinp * Cout));
+        const float val = ci < Cin ? w[((long long)t * Cout + co) * Cin + ci] : 0.f;
+        wf[i] = __float2bfloat16_rn(val);
+        if (wt) {
+            const int tt = flip ? T - 1 - t : t;
+            wt[((long long)tt * Cinp + ci) * Cout + co] = __float2bfloat16_rn(val);
+        }
+    }
+}
+
+// Adam with bias-corrected moments on FP32 masters (step t >= 1).
+__global__ void k_adam(float *w, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+}  // namespace unet
+}  // namespace bd3mg
