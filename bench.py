@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip f*, time-to-gap and e2e (for profiling runs)")
+    ap.add_argument("--ws-crops", type=int, default=2000, help="warm start: training crops (90%% train)")
+    ap.add_argument("--ws-target-iters", type=int, default=200, help="warm start: 3MG iterations per target")
+    ap.add_argument("--ws-epochs", type=int, default=1)
+    ap.add_argument("--ws-train-seconds", type=float, default=60.0, help="warm start: training time budget")
+    ap.add_argument("--no-warm-start", action="store_true")
     return ap.parse_args()
 
 
@@ -405,6 +410,96 @@ def mixed_extra(fstar_iters, stream, flush, steps):
     return out
 
 
+def _timed_iterations(prob, x0, k, stream):
+    """Device time (s) of exactly k plain FP32 iterations from x0 (graph warmed first)."""
+    import torch
+    from paper_2002_02328_gb300 import binding
+    with binding.Solver.from_problem(prob, slabs=None) as s:
+        s.iterate(2, trace=False)
+        s.set_x(x0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        if k > 0:
+            s.iterate(k, trace=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+
+def warm_start_extra(args, stream, fstar):
+    """Learned warm start on the 512x512x128 recipe: training pairs (y, x_3mg) of 128x128x48
+    crops made by plain 3MG, the U-Net (4 levels, 16/32/64/128 channels) trained with the
+    library's tensor-core kernels, inference on the full volume, then 3MG from the predicted
+    start (objective-checked, y as fallback) against 3MG from y."""
+    import torch
+    from paper_2002_02328_gb300 import binding, synth, unet_binding as ub, warmstart as ws
+    widths, shape = (16, 32, 64, 128), (48, 128, 128)
+    out = {"workload": "U-Net warm start: crops 128x128x48 of the 512x512x128 recipe (PSF 9x9x7), "
+                       "inference on the 512x512x128 volume", "crops": args.ws_crops,
+           "target_iterations": args.ws_target_iters, "widths": list(widths)}
+    t0 = time.perf_counter()
+    ys, ramps = ws.make_crops(args.ws_crops, shape, seed=0)
+    t1 = time.perf_counter()
+    targets = ws.solve_targets(ys, ramps, iters=args.ws_target_iters)
+    t2 = time.perf_counter()
+    ntr = int(round(0.9 * args.ws_crops))
+    with ub.UNet(widths, 2, lr=1e-3) as net:
+        net.set_params(ub.he_init(widths, 2, 0))
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        losses = ws.train(net, ys, ramps, targets, range(ntr), epochs=args.ws_epochs, batch=4,
+                          time_budget_s=args.ws_train_seconds)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        mse_y, mse_x = [], []
+        for k in range(ntr, args.ws_crops):
+            xh = ws.predict(net, ys[k], ramps[k])
+            mse_y.append(float(torch.mean((ys[k] - targets[k]) ** 2)))
+            mse_x.append(float(torch.mean((xh - targets[k]) ** 2)))
+        out.update({"seconds": {"crops": t1 - t0, "targets": t2 - t1, "training": t4 - t3},
+                    "train_steps": len(losses), "batch": 4, "ms_per_train_step": 1e3 * (t4 - t3) / max(1, len(losses)),
+                    "loss_first": losses[0], "loss_last20": float(np.mean(losses[-20:])),
+                    "heldout_mse": {"x_hat": float(np.mean(mse_x)), "y": float(np.mean(mse_y))}})
+        prob = synth.workload_mixed(seed=0)
+        y = torch.from_numpy(prob.y).cuda()
+        ws.predict(net, y, ws.C2_SXY)                 # warm-up (buffers)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xh = ws.predict(net, y, ws.C2_SXY).clone()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_inf = a.elapsed_time(b) / 1e3
+    tc = time.perf_counter()
+    start, fx, fy = ws.choose_start(prob, xh)
+    torch.cuda.synchronize()
+    t_check = time.perf_counter() - tc
+    n = 400
+    with binding.Solver.from_problem(prob, slabs=None) as s:
+        tr_y = s.iterate(n)
+    with binding.Solver.from_problem(prob, slabs=None) as s:
+        s.set_x(start)
+        tr_x = s.iterate(n)
+    res = {}
+    for name, gap, norm in (("rel_1e-4", 1e-4, False), ("normalized_1e-4", 1e-4, True),
+                            ("rel_1e-7", 1e-7, False), ("normalized_1e-6", 1e-6, True)):
+        den = (tr_y[0] - fstar) if norm else abs(fstar)
+        ky = np.nonzero((tr_y - fstar) / den <= gap)[0]
+        kx = np.nonzero((tr_x - fstar) / den <= gap)[0]
+        ky = int(ky[0]) if ky.size else None
+        kx = int(kx[0]) if kx.size else None
+        ty = _timed_iterations(prob, y, ky, stream) if ky is not None else None
+        tx = _timed_iterations(prob, start, kx, stream) + t_inf + t_check if kx is not None else None
+        res[name] = {"from_y": {"iterations": ky, "seconds": ty},
+                     "warm_start": {"iterations": kx, "seconds_incl_inference": tx}}
+    out.update({"inference_512x512x128_s": t_inf, "objective_check_s": t_check, "f_y": fy, "f_x_hat": fx,
+                "start_used": "x_hat" if fx < fy else "y (fallback)", "fstar": fstar, "time_to_gap": res})
+    return out
+
+
 def e2e_run(prob, n_iter, stream):
     """Whole solve through the public API with host buffers: H2D of y from pinned memory,
     context creation, n_iter sweeps with the f trace read back, D2H of x to pinned memory."""
@@ -563,6 +658,8 @@ def ours(args):
                                                    "plain_fp32": {"iterations": k_pn, "seconds": t_pn}}}
         extra["batched"] = batch_extra(min(args.fstar_iters, 3000), stream)
         extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
+        if not args.no_warm_start:
+            extra["warm_start_512x512x128"] = warm_start_extra(args, stream, extra["mixed_512x512x128"]["fstar"])
         e2e_rate, h2d, d2h, e2e_s = e2e_run(prob, 500, stream)
         e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}
