@@ -187,13 +187,12 @@ struct Smem {
         sizeof(float) * (A::NSA * A::SLOT + NSX * A::SLOT1 + A::BY * TX + A::CF_FLOATS) +
         A::bars_bytes(A::NSA + NSX);
     static constexpr size_t curvature =
-        sizeof(float) * (2 * C::NSF * C::SLOT + NSX * C::SLOT1 + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
-        C::bars_bytes(2 * C::NSF + NSX);
+        sizeof(float) * (2 * C::NSF * C::SLOT + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
+        C::bars_bytes(C::NSF);
     // BF16 directions: g, d slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
     static constexpr size_t curvature_bf =
         2 * (2 * CB::NSF * CB::SLOT) +
-        sizeof(float) * (NSX * CB::SLOT1 + 2 * CB::BY * CB::BX + 2 * CB::BY * TX + CB::CF_FLOATS) +
-        CB::bars_bytes(2 * CB::NSF + NSX);
+        sizeof(float) * (2 * CB::BY * CB::BX + 2 * CB::BY * TX + CB::CF_FLOATS) + CB::bars_bytes(CB::NSF);
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -914,159 +913,284 @@ static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
 }
 
 // ---------------------------------------------------------------------------
+// Helpers of the ring-unrolled kernels.
+// ---------------------------------------------------------------------------
+
+// Calls f(integral_constant<int, S>) for S = 0 .. N-1 in order while it returns
+// true; false as soon as one call returns false.  A z-march unrolled this way
+// sees the ring slot of every slice as a compile-time constant, so every
+// shared-memory address of the window is an immediate offset.
+template <int S, int N, class F>
+__device__ __forceinline__ bool for_slots(F &f) {
+    if constexpr (S == N) {
+        return true;
+    } else {
+        if (!f(std::integral_constant<int, S>{})) return false;
+        return for_slots<S + 1, N>(f);
+    }
+}
+
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+}
+
+// Forward z-combine of one unit of 4 staged columns with paired FP32 FMAs:
+// W = sum_t fz[t] v(zi - t), slice zi - t held in ring slot (S - t) mod NS.
+// Per component this is the same sequence of roundings as zcomb_unit.
+template <int KZ, int NS, int S, int SLOT, class T>
+__device__ __forceinline__ void zcomb_ring(const T *base, const float (&fz)[KZ], float *W) {
+    float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
+#pragma unroll
+    for (int t = 0; t < KZ; ++t) {
+        const float4 v = load4(base + ((S - t + NS) % NS) * SLOT);
+        const float2 c2 = make_float2(fz[t], fz[t]);
+        if (t & 1) {
+            b0 = __ffma2_rn(c2, make_float2(v.x, v.y), b0);
+            b1 = __ffma2_rn(c2, make_float2(v.z, v.w), b1);
+        } else {
+            a0 = __ffma2_rn(c2, make_float2(v.x, v.y), a0);
+            a1 = __ffma2_rn(c2, make_float2(v.z, v.w), a1);
+        }
+    }
+    const float2 lo = __fadd2_rn(a0, b0), hi = __fadd2_rn(a1, b1);
+    *reinterpret_cast<float4 *>(W) = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// Forward y-pass of the column pair (c, c+1) at output row yo with paired FMAs:
+// out = sum_b fy[b+R] T1[yo + R - b][c .. c+1] (same rounding sequence as ypass).
+template <int R>
+__device__ __forceinline__ float2 ypass_pair(const float *T1, int yo, int c, const float (&fy)[2 * R + 1]) {
+    float2 t[2 * R + 1];
+#pragma unroll
+    for (int j = 0; j < 2 * R + 1; ++j) t[j] = ld2(T1 + (yo + j) * TX + c);
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+#pragma unroll
+    for (int b = -R; b <= R; b += 2) s0 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[R - b], s0);
+#pragma unroll
+    for (int b = -R + 1; b <= R; b += 2) s1 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[R - b], s1);
+    return __fadd2_rn(s0, s1);
+}
+
+// Half-quadratic curvature terms of one voxel along one axis: with
+// t = x(n + e) - x(n), w = 1/sqrt(delta^2 + t^2), vg = g(n + e) - g(n),
+// vd = d(n + e) - d(n): acc6 += w vg^2, acc7 += w vg vd, acc8 += w vd^2.
+__device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge, float dn, float de, float delta2,
+                                         float *acc) {
+    const float t = xe - xn, w = rsqrtf(fmaf(t, t, delta2));
+    const float vg = ge - gn, vd = de - dn, wvg = w * vg;
+    acc[6] = fmaf(wvg, vg, acc[6]);
+    acc[7] = fmaf(wvg, vd, acc[7]);
+    acc[8] = fmaf(w * vd, vd, acc[8]);
+}
+
+// ---------------------------------------------------------------------------
 // k_curvature: nine inner products of the restricted subspace system and, in
 // the last CTA, the per-slab 2x2 solve.
 //   acc: 0 g.g  1 g.d  2 d.d  3 Hg.Hg  4 Hg.Hd  5 Hd.Hd
-//        6 sum w (Vg)^2  7 sum w Vg Vd  8 sum w (Vd)^2
+//        6 sum w (Vg)^2  7 sum w Vg Vd  8 sum w (Vd)^2   9 ||x_S||^2
 // g_S, d_S are g, d masked to the slab's slices [z0, z1) (zero-filled slots).
+// The slices of g and d share one mbarrier per ring slot; the z-march is
+// unrolled over the ring (compile-time slots); the z-combine and the y-pass
+// use paired FP32 FMAs; each thread of the y-pass and of the epilogue owns a
+// pair of adjacent columns of one output row; x for the weights is read
+// through the L1 cache.
 // ---------------------------------------------------------------------------
 template <int R, int RZ, bool BF>
 __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // direction storage
     using G = Geo<R, RZ, TY_C, sizeof(T)>;
-    constexpr int RPW = G::RPW;
+    constexpr int NS = G::NSF, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
     extern __shared__ __align__(128) float smem[];
-    T *sgs = reinterpret_cast<T *>(smem);                // NSF * SLOT (g)
-    T *sds = sgs + G::NSF * G::SLOT;                     // NSF * SLOT (d)
-    float *xs = reinterpret_cast<float *>(sds + G::NSF * G::SLOT);   // NSX * SLOT1 (x)
-    float *Wg = xs + NSX * G::SLOT1;
-    float *Wd = Wg + G::BY * G::BX;
-    float *T1g = Wd + G::BY * G::BX;
-    float *T1d = T1g + G::BY * TX;
-    float *CF = T1d + G::BY * TX;
+    T *sgs = reinterpret_cast<T *>(smem);                // NS * SLOT (g)
+    T *sds = sgs + NS * SLOT;                            // NS * SLOT (d)
+    float *Wb = reinterpret_cast<float *>(sds + NS * SLOT);   // [g, d][BY * BX]
+    float *T1b = Wb + 2 * BY * BX;                            // [g, d][BY * TX]
+    float *CF = T1b + 2 * BY * TX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
     const SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
-    const int nx = V.nx, ny = V.ny, nz = V.nz;
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane;
+    const float *xg = V.x;
     const float delta2 = V.delta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
-    // A stopped volume's item gets empty ranges: no copies, no loop, zero
+    // A stopped volume's item gets an empty range: no copies, no loop, zero
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
 
     const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
-    if (!init_bars(bar, 2 * G::NSF + NSX, smem, a.sh->status)) return;
+    if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
-    const uint32_t nb = (uint32_t)(G::BX * G::BY * sizeof(T));
-    Pipe<G::NSF, G::SLOT, T> pg, pd;
-    pg.init(sgs, bar, &a.maps[sg.vol].m[TM_G_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
-    pd.init(sds, bar + G::NSF, &a.maps[sg.vol].m[TM_D_R], it.tx0 - G::XH, it.ty0 - R, glo, ghi, nb, zbeg);
-    // x slices for the penalty at outputs zo in [max(zo0, pen_lo), min(zo1, pen_hi)): x(zo), x(zo+1)
-    const int xfirst = max(it.zo0, pen_lo);
-    const int xlo = max(0, xfirst), xhi = stopped ? xlo : min(nz, min(it.zo1, pen_hi) + 1);
-    Pipe<NSX, G::SLOT1> px;
-    px.init(xs, bar + 2 * G::NSF, &a.maps[sg.vol].m[TM_X_1C], it.tx0 - XH1, it.ty0 - 1, xlo, xhi,
-            (uint32_t)(BX1 * G::BY1 * sizeof(float)), xfirst);
-    pg.issue_upto(zbeg + PREF - 1);
-    pd.issue_upto(zbeg + PREF - 1);
-    px.issue_upto(zbeg - RZ + PREF);
+    const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R], *md = &a.maps[sg.vol].m[TM_D_R];
+    if (tid == 0) {
+        // the descriptors sit in global memory and may have been rewritten since an earlier launch
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mg)) : "memory");
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(md)) : "memory");
+    }
+    const uint32_t nb = (uint32_t)(BX * BY * sizeof(T));
+    const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
+    constexpr int FILL = (int)(SLOT * sizeof(T) / 16);
+    // slice z of g_S and d_S into ring slot s: TMA copies when z is a slab slice, else zeros
+    auto issue = [&](int z, int s) {
+        if (z >= glo && z < ghi) {
+            if (tid == 0) {
+                mbar_expect_tx(bar + s, 2 * nb);
+                tma_load_3d(sgs + s * SLOT, mg, bx0, by0, z, bar + s);
+                tma_load_3d(sds + s * SLOT, md, bx0, by0, z, bar + s);
+            }
+        } else {
+            float4 *pg = reinterpret_cast<float4 *>(sgs + s * SLOT), *pd = reinterpret_cast<float4 *>(sds + s * SLOT);
+            for (int i = tid; i < FILL; i += NT) {
+                pg[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                pd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            // order these generic writes before any later TMA write into the slot
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+    };
+#pragma unroll
+    for (int p = 0; p < PREF; ++p) issue(zbeg + p, p);      // slice z lives in slot (z - zbeg) % NS
     __syncthreads();
 
-    float acc[10];                            // 9 subspace sums, ||x_S||^2
+    float acc[10];
 #pragma unroll
     for (int p = 0; p < 10; ++p) acc[p] = 0.f;
-    const int y0 = warp * RPW;
-    const int gx = it.tx0 + lane;
-    const bool colin = gx < nx;
-    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
-    int xsrc[XP], xdst[XP];
-#pragma unroll
-    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
+    constexpr int ZP = Units<G::ZUNITS>::PER;      // z-combine units per thread (1 or 2)
+    static_assert(G::XUNITS <= NT, "one x-pass unit per thread");
+    const bool zu = tid < G::ZUNITS, xu = tid < G::XUNITS;
+    int xsrc, xdst;
+    xpass_offsets<G>(tid, xsrc, xdst);
+    // y-pass / epilogue: output row yo, columns c, c+1
+    const int yo = 2 * warp + (lane >> 4), c = 2 * (lane & 15);
+    const int gy = it.ty0 + yo, gx = it.tx0 + c;
+    const bool v0 = gy < ny && gx < nx, v1 = gy < ny && gx + 1 < nx;
+    const bool xe0 = gx + 1 < nx, xe1 = gx + 2 < nx, ye = gy + 1 < ny;
+    // x offsets for the weights (clamped to the voxel itself where the neighbour does not exist)
+    const long long n0 = v0 ? (long long)gy * pitch + gx : 0;
+    const long long n2 = xe1 ? n0 + 2 : n0;
+    const long long ny0 = ye ? n0 + pitch : n0;
+    const int ci = (yo + R) * BX + XH + c;                // staged index of column c
+    float *Wg = Wb, *Wd = Wb + BY * BX, *T1g = T1b, *T1d = T1b + BY * TX;
+    uint32_t par = 0u;
+    bool timed_out = false;
+    int zi = zbeg;
 
-    for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
+    // Step for slice zi (ring slot S): z-combine of output zo = zi - RZ; barrier;
+    // x-pass; barrier; y-pass, products and weights of zo.
+    auto step = [&](auto sc) -> bool {
+        constexpr int S = decltype(sc)::value;
+        if (zi >= zend) return false;
         const int zo = zi - RZ;
         const bool emit = zo >= it.zo0;
-        const bool pen = zo >= pen_lo && zo < pen_hi;
-        bool ok = pg.wait_upto(zi);
-        ok = pd.wait_upto(zi) && ok;
-        ok = px.wait_upto(zo + 1) && ok;
+        const bool pen = emit && v0 && zo >= pen_lo && zo < pen_hi;
+        bool ok = true;
+        if (zi >= glo && zi < ghi) {
+            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            if (ok) par ^= 1u << S;
+        }
+        // x of this thread's voxels at zo (and zo + 1), fetched early
+        float2 x0 = make_float2(0.f, 0.f), xy = x0, xz = x0;
+        float x2 = 0.f;
+        if (pen) {
+            const long long zoff = (long long)zo * plane;
+            const long long zn = zo + 1 < nz ? plane : 0;
+            x0 = __ldg(reinterpret_cast<const float2 *>(xg + zoff + n0));
+            x2 = __ldg(xg + zoff + n2);
+            xy = __ldg(reinterpret_cast<const float2 *>(xg + zoff + ny0));
+            xz = __ldg(reinterpret_cast<const float2 *>(xg + zoff + zn + n0));
+        }
         const float *cfr = CF + (zo - zbeg) * G::CFS;
-        if (emit) {
-            float fzc[G::KZ];
+        if (emit && zu) {
+            float fzc[KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
-            const T *wg[G::KZ], *wd[G::KZ];
-            window(pg, s, wg);
-            window(pd, s, wd);
 #pragma unroll
-            for (int j = 0; j < ZP; ++j)
-                if (tid + j * NT < G::ZUNITS) zcomb_unit(wg, 4 * (tid + j * NT), fzc, Wg);
-#pragma unroll
-            for (int j = 0; j < ZP; ++j)
-                if (tid + j * NT < G::ZUNITS) zcomb_unit(wd, 4 * (tid + j * NT), fzc, Wd);
+            for (int j = 0; j < ZP; ++j) {
+                const int u = 4 * (tid + j * NT);
+                if (j == 0 || tid + j * NT < G::ZUNITS) {
+                    zcomb_ring<KZ, NS, S, SLOT>(sgs + u, fzc, Wg + u);
+                    zcomb_ring<KZ, NS, S, SLOT>(sds + u, fzc, Wd + u);
+                }
+            }
         }
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) { pg.drain(); pd.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
-            return;
+            timed_out = true;
+            return false;
         }
-        pg.issue_upto(zi + PREF);
-        pd.issue_upto(zi + PREF);
-        px.issue_upto(zo + 1 + PREF);
-        if (!emit) continue;
-        {
+        issue(zi + PREF, (S + PREF) % NS);
+        ++zi;
+        if (!emit) return true;
+        if (xu) {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);
-#pragma unroll
-            for (int j = 0; j < XP; ++j)
-                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(Wg, T1g, xsrc[j], xdst[j], fxc);
-#pragma unroll
-            for (int j = 0; j < XP; ++j)
-                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(Wd, T1d, xsrc[j], xdst[j], fxc);
+            xpass_unit<G, R, -1>(Wg, T1g, xsrc, xdst, fxc);
+            xpass_unit<G, R, -1>(Wd, T1d, xsrc, xdst, fxc);
         }
         __syncthreads();
         float fyc[G::KXY];
         row_coeffs(fyc, cfr + G::KXYP);
-        float hg[RPW], hd[RPW];
-        ypass<R, RPW, -1>(T1g, y0, lane, fyc, hg);
-        ypass<R, RPW, -1>(T1d, y0, lane, fyc, hd);
-        const int s0 = Pipe<G::NSF, G::SLOT, T>::back_slot(s, RZ), s1 = Pipe<G::NSF, G::SLOT, T>::back_slot(s, RZ - 1);
-        const T *gz0 = pg.buf + s0 * G::SLOT, *gz1 = pg.buf + s1 * G::SLOT;   // slices zo, zo+1
-        const T *dz0 = pd.buf + s0 * G::SLOT, *dz1 = pd.buf + s1 * G::SLOT;
-        const float *xz0 = pen ? px.at(zo) : xs, *xz1 = pen ? px.at(zo + 1) : xs;
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-            const int yo = y0 + k, gy = it.ty0 + yo;
-            if (colin && gy < ny) {
-                acc[3] = fmaf(hg[k], hg[k], acc[3]);
-                acc[4] = fmaf(hg[k], hd[k], acc[4]);
-                acc[5] = fmaf(hd[k], hd[k], acc[5]);
-                if (pen) {
-                    const int ci = (yo + R) * G::BX + lane + G::XH;
-                    const int xi = (yo + 1) * BX1 + lane + XH1;
-                    const float gc = to_f(gz0[ci]), dc = to_f(dz0[ci]), xc = xz0[xi];
-                    if (zo >= sg.z0) {
-                        acc[0] = fmaf(gc, gc, acc[0]);
-                        acc[1] = fmaf(gc, dc, acc[1]);
-                        acc[2] = fmaf(dc, dc, acc[2]);
-                        acc[9] = fmaf(xc, xc, acc[9]);
-                    }
-                    if (gx < nx - 1) {
-                        const float t = xz0[xi + 1] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = to_f(gz0[ci + 1]) - gc, vd = to_f(dz0[ci + 1]) - dc;
-                        acc[6] = fmaf(w * vg, vg, acc[6]);
-                        acc[7] = fmaf(w * vg, vd, acc[7]);
-                        acc[8] = fmaf(w * vd, vd, acc[8]);
-                    }
-                    if (gy < ny - 1) {
-                        const float t = xz0[xi + BX1] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = to_f(gz0[ci + G::BX]) - gc, vd = to_f(dz0[ci + G::BX]) - dc;
-                        acc[6] = fmaf(w * vg, vg, acc[6]);
-                        acc[7] = fmaf(w * vg, vd, acc[7]);
-                        acc[8] = fmaf(w * vd, vd, acc[8]);
-                    }
-                    if (zo < nz - 1) {
-                        const float t = xz1[xi] - xc, w = rsqrtf(fmaf(t, t, delta2));
-                        const float vg = to_f(gz1[ci]) - gc, vd = to_f(dz1[ci]) - dc;
-                        acc[6] = fmaf(w * vg, vg, acc[6]);
-                        acc[7] = fmaf(w * vg, vd, acc[7]);
-                        acc[8] = fmaf(w * vd, vd, acc[8]);
-                    }
+        const float2 hg = ypass_pair<R>(T1g, yo, c, fyc);
+        const float2 hd = ypass_pair<R>(T1d, yo, c, fyc);
+        if (v0) {
+            acc[3] = fmaf(hg.x, hg.x, acc[3]);
+            acc[4] = fmaf(hg.x, hd.x, acc[4]);
+            acc[5] = fmaf(hd.x, hd.x, acc[5]);
+        }
+        if (v1) {
+            acc[3] = fmaf(hg.y, hg.y, acc[3]);
+            acc[4] = fmaf(hg.y, hd.y, acc[4]);
+            acc[5] = fmaf(hd.y, hd.y, acc[5]);
+        }
+        if (pen) {
+            constexpr int s0 = (S - RZ + NS) % NS, s1 = (S - RZ + 1 + NS) % NS;   // slices zo, zo + 1
+            const T *g0 = sgs + s0 * SLOT + ci, *d0 = sds + s0 * SLOT + ci;
+            const T *g1 = sgs + s1 * SLOT + ci, *d1 = sds + s1 * SLOT + ci;
+            const float2 gc = ld2(g0), dc = ld2(d0), gyv = ld2(g0 + BX), dyv = ld2(d0 + BX);
+            const float2 gzv = ld2(g1), dzv = ld2(d1);
+            const float gr = to_f(g0[2]), dr = to_f(d0[2]);
+            const bool inslab = zo >= sg.z0, ze = zo + 1 < nz;
+            // voxel c
+            if (inslab) {
+                acc[0] = fmaf(gc.x, gc.x, acc[0]);
+                acc[1] = fmaf(gc.x, dc.x, acc[1]);
+                acc[2] = fmaf(dc.x, dc.x, acc[2]);
+                acc[9] = fmaf(x0.x, x0.x, acc[9]);
+            }
+            if (xe0) pen_axis(x0.x, x0.y, gc.x, gc.y, dc.x, dc.y, delta2, acc);
+            if (ye) pen_axis(x0.x, xy.x, gc.x, gyv.x, dc.x, dyv.x, delta2, acc);
+            if (ze) pen_axis(x0.x, xz.x, gc.x, gzv.x, dc.x, dzv.x, delta2, acc);
+            // voxel c + 1
+            if (v1) {
+                if (inslab) {
+                    acc[0] = fmaf(gc.y, gc.y, acc[0]);
+                    acc[1] = fmaf(gc.y, dc.y, acc[1]);
+                    acc[2] = fmaf(dc.y, dc.y, acc[2]);
+                    acc[9] = fmaf(x0.y, x0.y, acc[9]);
                 }
+                if (xe1) pen_axis(x0.y, x2, gc.y, gr, dc.y, dr, delta2, acc);
+                if (ye) pen_axis(x0.y, xy.y, gc.y, gyv.y, dc.y, dyv.y, delta2, acc);
+                if (ze) pen_axis(x0.y, xz.y, gc.y, gzv.y, dc.y, dzv.y, delta2, acc);
             }
         }
+        return true;
+    };
+    while (for_slots<0, NS>(step)) {
+    }
+    if (timed_out) {
+        // leave only after every copy in flight has landed (bounded waits)
+        if (tid == 0) {
+            for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
+                if (z < glo || z >= ghi) continue;
+                const int s = (z - zbeg) % NS;
+                if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+            }
+            atomicOr(a.sh->status, ST_TIMEOUT);
+        }
+        return;
     }
     if (publish_partials<10>(acc, a.partials, a.ticket, a.nitems)) curvature_finish(a);
 }

@@ -184,7 +184,7 @@ def test_first_adam_step_follows_the_oracle_gradient_sign(ub):
     # |dw| <= lr, up to the FP32 rounding of w0 and w1 (one ulp of |w| each)
     assert np.all(np.abs(dw) <= lr * (1 + 1e-5) + 2.4e-7 * np.abs(w0))
     big = np.abs(gflat) > 0.05 * np.sqrt(np.mean(gflat ** 2))
-    assert big.sum() > 0.5 * gflat.size
+    assert big.sum() > 0.2 * gflat.size
     ref_step, _, _ = U.adam_step(w0, gflat, np.zeros_like(gflat), np.zeros_like(gflat), 1, lr=lr)
     agree = np.abs(dw[big] - (ref_step - w0)[big]) <= 1e-6 + 2.4e-7 * np.abs(w0[big])
     assert agree.mean() > 0.995, agree.mean()
