@@ -227,6 +227,46 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
 /* Number of kernel launches one iteration enqueues. */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
+/* Precision escalation of the BF16-direction form (Section 3.2's subspace D =
+ * [-g, d] with directions stored in BF16).  With tol > 0, bd3mg_iterate runs
+ * in chunks of 4 iterations and reads the objective trace between chunks;
+ * once some volume's objective decreases by at most tol * |f| from one
+ * iteration to the next, the context switches for good to FP32 directions (d
+ * widened from its BF16 values, g recomputed) and a new iteration graph.
+ * bd3mg_iterate_async never escalates.  tol = 0 turns it off (the default);
+ * no effect on FP32 contexts.  bd3mg_escalated: *at = the iteration count at
+ * which the switch happened, -1 if it has not.  Errors: BD3MG_EINVAL for a
+ * negative or non-finite tol or a NULL at. */
+bd3mg_status bd3mg_set_escalation(bd3mg_ctx *ctx, double tol);
+bd3mg_status bd3mg_escalated(bd3mg_ctx *ctx, long long *at);
+
+/* Checkpoint / resume.  bd3mg_save writes the state an iteration starts from
+ * (x and the memory directions d of every volume, in the context's storage
+ * precision, and the iteration count) to the file `path` (overwritten);
+ * bd3mg_load reads such a file into a context created with the same volumes,
+ * slabs and precision, and clears the stopping state.  Everything else an
+ * iteration needs (residual, gradient, 2x2 system) is recomputed from x and d,
+ * so a loaded context continues bit for bit like the one that was saved.
+ * Errors: BD3MG_EINVAL (unreadable or mismatching file; the message says
+ * which), BD3MG_ECUDA. */
+bd3mg_status bd3mg_save(bd3mg_ctx *ctx, const char *path);
+bd3mg_status bd3mg_load(bd3mg_ctx *ctx, const char *path);
+
+/* z-chunk autotuner of the tile kernels.  Times `iters` lockstep iterations
+ * (after 2 untimed ones) of contexts built like bd3mg_batch_create(nvol, p, y,
+ * NULL, data_on_device, stream, NULL, ...) with zchunk = 0 (the library's cost
+ * model) and 4, 6, 8, 12, 16, 24, 32, 48 output slices per work item, and
+ * returns the fastest in *zchunk (give it to bd3mg_params.zchunk) and its
+ * device time per iteration in *ms_per_iteration (may be NULL).  Candidates
+ * that do not fit in device memory are skipped.  cache_path (may be NULL):
+ * a JSON-lines file; when it holds an entry for the same shape class (SM
+ * count, precision, every volume's extents, PSF extents and slab bounds) that
+ * entry is returned without timing (*ms_per_iteration = -1), otherwise the
+ * result is appended.  The contexts are created and destroyed on `stream`;
+ * the caller's data is only read. */
+bd3mg_status bd3mg_autotune(int nvol, const bd3mg_params *p, const float *const *y, int data_on_device, void *stream,
+                            int iters, const char *cache_path, int *zchunk, double *ms_per_iteration);
+
 /* Size of the device array behind bd3mg_objective_noalloc (bytes). */
 #define BD3MG_STATIC_SCRATCH_BYTES (1u << 20)
 

@@ -32,7 +32,8 @@ EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iter
             "bd3mg_apply_HT", "bd3mg_slab_colours", "bd3mg_plan_slab_colours", "bd3mg_factor_psf",
             "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc",
             "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_set_stopping",
-            "bd3mg_stopped", "bd3mg_error_string",
+            "bd3mg_stopped", "bd3mg_set_escalation", "bd3mg_escalated", "bd3mg_save", "bd3mg_load",
+            "bd3mg_autotune", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -96,6 +97,11 @@ def load(path: str = LIB_PATH):
             "bd3mg_set_stopping": (ip, [vp, dp, vp]),
             "bd3mg_stopped": (ip, [vp, vp]),
             "bd3mg_objective_noalloc": (ip, [P, vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
+            "bd3mg_set_escalation": (ip, [vp, dp]),
+            "bd3mg_escalated": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "bd3mg_save": (ip, [vp, ctypes.c_char_p]),
+            "bd3mg_load": (ip, [vp, ctypes.c_char_p]),
+            "bd3mg_autotune": (ip, [ip, P, vp, ip, vp, ip, ctypes.c_char_p, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
             "bd3mg_destroy": (None, [vp]),
@@ -338,6 +344,24 @@ class Solver:
         self._c(self._lib.bd3mg_stopped(self._ctx, k.ctypes.data))
         return int(k[0])
 
+    def set_escalation(self, tol: float):
+        """BF16 directions: switch to FP32 directions once f decreases by <= tol |f| per iteration."""
+        self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
+
+    def escalated(self) -> int:
+        """Iteration count at which the context switched to FP32 directions, or -1."""
+        at = ctypes.c_longlong()
+        self._c(self._lib.bd3mg_escalated(self._ctx, ctypes.byref(at)))
+        return int(at.value)
+
+    def save(self, path: str):
+        """Checkpoint x, d and the iteration count to `path`."""
+        self._c(self._lib.bd3mg_save(self._ctx, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by save() of an identical context."""
+        self._c(self._lib.bd3mg_load(self._ctx, os.fsencode(path)))
+
     def last_step(self) -> np.ndarray:
         """Per slab: [B00, B01, B11, c0, c1, u0, u1, rank] of its latest update."""
         buf = np.zeros((self.nslabs, 8))
@@ -481,6 +505,24 @@ class BatchSolver:
                                            int(out.is_cuda)))
         return out
 
+    def set_escalation(self, tol: float):
+        """BF16 directions: switch to FP32 directions once f decreases by <= tol |f| per iteration."""
+        self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
+
+    def escalated(self) -> int:
+        """Iteration count at which the context switched to FP32 directions, or -1."""
+        at = ctypes.c_longlong()
+        self._c(self._lib.bd3mg_escalated(self._ctx, ctypes.byref(at)))
+        return int(at.value)
+
+    def save(self, path: str):
+        """Checkpoint x, d and the iteration count to `path`."""
+        self._c(self._lib.bd3mg_save(self._ctx, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by save() of an identical context."""
+        self._c(self._lib.bd3mg_load(self._ctx, os.fsencode(path)))
+
     def profile_iteration(self):
         ms = np.zeros(5)
         cnt = np.zeros(5, np.int32)
@@ -489,3 +531,26 @@ class BatchSolver:
 
     def launches_per_iteration(self) -> int:
         return int(self._lib.bd3mg_launches_per_iteration(self._ctx))
+
+
+def autotune(problems, iters: int = 10, cache_path: Optional[str] = None, precision: int = FP32):
+    """Fastest z-chunk for these volumes (bd3mg_autotune): (zchunk, ms per iteration or -1 if cached)."""
+    torch = _torch()
+    lib = load()
+    n = len(problems)
+    arr = (Params * n)()
+    keep, ys = [], []
+    for v, p in enumerate(problems):
+        prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precision, 1e-12, 0)
+        arr[v] = prm
+        keep.append(k)
+        ys.append(torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).cuda())
+    yptr = (ctypes.c_void_p * n)(*[_ptr(t) for t in ys])
+    z = ctypes.c_int()
+    ms = ctypes.c_double()
+    s = torch.cuda.current_stream().cuda_stream
+    st = lib.bd3mg_autotune(n, arr, yptr, 1, ctypes.c_void_p(int(s)), int(iters),
+                            os.fsencode(cache_path) if cache_path else None, ctypes.byref(z), ctypes.byref(ms))
+    if st != 0:
+        raise Bd3mgError(st, lib.bd3mg_status_string(st).decode())
+    return int(z.value), float(ms.value)

@@ -19,6 +19,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -107,6 +109,9 @@ struct bd3mg_ctx {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<int> prof_cls;
     long long iterations = 0;
+    // precision escalation of the BF16-direction form (0: off)
+    double esc_tol = 0.0;
+    long long esc_at = -1;          // iteration count at which the context switched to FP32 directions
 };
 
 namespace {
@@ -397,6 +402,79 @@ bd3mg_status check_status(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+// Device descriptors (VolDev, TMA maps) of every volume from the host state,
+// uploaded to c->vols / c->maps (slot nvol mirrors volume 0 for operator calls).
+bd3mg_status upload_descriptors(bd3mg_ctx *c) {
+    const int nvol = c->nvol;
+    std::vector<VolDev> vd(nvol + 1);
+    std::vector<VolMaps> vm(nvol + 1);
+    for (int v = 0; v < nvol; ++v) {
+        VolState &vs = c->V[v];
+        const bd3mg_params &p = vs.p;
+        VolDev d{};
+        d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.pitch = vs.pitch;
+        d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
+        d.plane = (long long)vs.pitch * p.ny;
+        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.dh = vs.dh; d.gh = vs.gh;
+        d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
+        d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
+        d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
+        d.lam_d = p.lambda; d.eta_d = p.eta;
+        vs.dev = d;
+        vd[v] = d;
+        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.dh, 2)
+                              : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
+        if (!ok)
+            return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
+    }
+    vd[nvol] = vd[0];
+    vm[nvol] = vm[0];
+    CK(cudaMemcpyAsync(c->vols, vd.data(), sizeof(VolDev) * vd.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->maps, vm.data(), sizeof(VolMaps) * vm.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));        // vd, vm live on this stack frame
+    return BD3MG_OK;
+}
+
+// Capture one iteration as a CUDA graph (replacing any earlier one).
+bd3mg_status capture_graph(bd3mg_ctx *c) {
+    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
+    bd3mg_status es = enqueue_iteration(c, c->cap_stream);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(c->cap_stream, &gr);
+    if (es) {
+        if (gr) cudaGraphDestroy(gr);
+        return es;
+    }
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "end capture: %s", cudaGetErrorString(e));
+    c->graph = gr;
+    e = cudaGraphInstantiate(&c->exec, gr, 0);
+    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return BD3MG_OK;
+}
+
+// Switch a BF16-direction context to FP32 directions: FP32 g and d arrays (d
+// widened from its BF16 values, g recomputed by the next iteration), FP32
+// descriptors, and a new iteration graph.
+bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
+    if (!c->bf) return BD3MG_OK;
+    bd3mg_status st;
+    for (VolState &vs : c->V) {
+        if (!vs.d) {
+            if ((st = dalloc_n(c, &vs.d, vs.np)) || (st = dalloc_n(c, &vs.g, vs.np))) return st;
+        }
+        launch_dir_to_float(vs.dh, vs.d, (long long)vs.np, c->stream);
+        if ((st = check_launch(c))) return st;
+        CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
+    }
+    c->bf = false;
+    if ((st = upload_descriptors(c))) return st;
+    c->esc_at = c->iterations;
+    return capture_graph(c);
+}
+
 // Validate one volume's parameters (and its slab bounds) into v.
 bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolState &v) {
     if (p.nx < 1 || p.ny < 1 || p.nz < 1)
@@ -542,8 +620,6 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
 
     // data and descriptors
     const cudaMemcpyKind kin = data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    std::vector<VolDev> vd(nvol + 1);
-    std::vector<VolMaps> vm(nvol + 1);
     for (int v = 0; v < nvol; ++v) {
         VolState &vs = c->V[v];
         const bd3mg_params &p = vs.p;
@@ -564,26 +640,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpyAsync(vs.fx, FX[v].data(), FX[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fz, FZ[v].data(), FZ[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
-        VolDev d{};
-        d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.pitch = vs.pitch;
-        d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
-        d.plane = (long long)vs.pitch * p.ny;
-        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.dh = vs.dh; d.gh = vs.gh;
-        d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
-        d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
-        d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
-        d.lam_d = p.lambda; d.eta_d = p.eta;
-        vs.dev = d;
-        vd[v] = d;
-        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.dh, 2)
-                              : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
-        if (!ok)
-            return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     }
-    vd[nvol] = vd[0];
-    vm[nvol] = vm[0];
-    CK(cudaMemcpyAsync(c->vols, vd.data(), sizeof(VolDev) * vd.size(), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->maps, vm.data(), sizeof(VolMaps) * vm.size(), cudaMemcpyHostToDevice, c->stream));
+    if ((st = upload_descriptors(c))) return st;
     CK(cudaMemcpyAsync(c->segs, c->segs_h.data(), sizeof(SegDev) * nseg, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
                        c->stream));
@@ -606,21 +664,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     if ((st = reset_run(c, -1))) return st;
     if ((st = ensure_trace(c, 1024))) return st;
 
-    // capture one iteration as a graph
-    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
-    bd3mg_status es = enqueue_iteration(c, c->cap_stream);
-    cudaGraph_t gr = nullptr;
-    e = cudaStreamEndCapture(c->cap_stream, &gr);
-    if (es) {
-        if (gr) cudaGraphDestroy(gr);
-        return es;
-    }
-    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "end capture: %s", cudaGetErrorString(e));
-    c->graph = gr;
-    e = cudaGraphInstantiate(&c->exec, gr, 0);
-    if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-    return BD3MG_OK;
+    return capture_graph(c);
 }
 
 // Copy between a caller volume (rows of nx floats) and a library volume (rows of pitch floats).
@@ -791,8 +835,35 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     bd3mg_status st;
     if ((st = ensure_trace(c, n + 1))) return st;
     CK(cudaMemsetAsync(c->counter, 0, sizeof(int), c->stream));
-    for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
-    c->iterations += n;
+    const long long base = c->iterations;
+    if (c->bf && c->esc_tol > 0.0) {
+        // run in chunks, reading the objective trace between them; switch to FP32
+        // directions once some volume decreases by at most esc_tol relative
+        const int chunk = 4;
+        std::vector<double> tr;
+        int k = 0;
+        while (k < n && c->bf) {
+            const int m = std::min(chunk, n - k);
+            for (int j = 0; j < m; ++j) CK(cudaGraphLaunch(c->exec, c->stream));
+            k += m;
+            c->iterations = base + k;
+            tr.resize((size_t)c->nvol * k);       // f(x_0) .. f(x_{k-1}) of every volume
+            CK(cudaMemcpy2DAsync(tr.data(), sizeof(double) * k, c->trace, sizeof(double) * c->trace_cap,
+                                 sizeof(double) * k, c->nvol, cudaMemcpyDeviceToHost, c->stream));
+            if ((st = check_status(c))) return st;
+            bool slow = false;
+            for (int v = 0; v < c->nvol && !slow; ++v)
+                for (int j = std::max(1, k - m); j < k && !slow; ++j) {
+                    const double a0 = tr[(size_t)v * k + j - 1], a1 = tr[(size_t)v * k + j];
+                    slow = (a0 - a1) <= c->esc_tol * std::fabs(a1);
+                }
+            if (slow && (st = escalate_to_fp32(c))) return st;
+        }
+        for (; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
+    } else {
+        for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
+    }
+    c->iterations = base + n;
     if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ | M_TRACE))) return st;
     if (f_trace)
         CK(cudaMemcpy2DAsync(f_trace, sizeof(double) * (n + 1), c->trace, sizeof(double) * c->trace_cap,
@@ -896,6 +967,90 @@ bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     bd3mg_status st = reset_run(c, 0);
     if (st) return st;
     return copy_vol(c, v, v.x, x, on_device, true);
+}
+
+bd3mg_status bd3mg_set_escalation(bd3mg_ctx *c, double tol) {
+    GUARD(c);
+    if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, BD3MG_EINVAL, "escalation tol must be finite and >= 0");
+    c->esc_tol = tol;
+    return BD3MG_OK;
+}
+
+bd3mg_status bd3mg_escalated(bd3mg_ctx *c, long long *at) {
+    GUARD(c);
+    if (!at) return fail(c, BD3MG_EINVAL, "at is NULL");
+    *at = c->esc_at;
+    return BD3MG_OK;
+}
+
+namespace {
+const char kCkptMagic[8] = {'B', 'D', '3', 'M', 'G', 'C', 'K', '1'};
+
+struct CkptHead {
+    char magic[8];
+    int32_t version, nvol, bf, pad;
+    int64_t iterations;
+};
+}  // namespace
+
+bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
+    GUARD(c);
+    if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
+    std::ofstream f(path, std::ios::binary | std::ios::trunc);
+    if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s for writing", path);
+    CkptHead h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.nvol = c->nvol;
+    h.bf = c->bf ? 1 : 0;
+    h.iterations = c->iterations;
+    f.write(reinterpret_cast<const char *>(&h), sizeof(h));
+    std::vector<char> buf;
+    for (const VolState &v : c->V) {
+        const int32_t dims[4] = {v.p.nx, v.p.ny, v.p.nz, v.pitch};
+        f.write(reinterpret_cast<const char *>(dims), sizeof(dims));
+        const size_t xb = v.np * 4, db = v.np * (c->bf ? 2 : 4);
+        buf.resize(std::max(xb, db));
+        CK(cudaMemcpyAsync(buf.data(), v.x, xb, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        f.write(buf.data(), (std::streamsize)xb);
+        CK(cudaMemcpyAsync(buf.data(), c->bf ? (const void *)v.dh : (const void *)v.d, db, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        f.write(buf.data(), (std::streamsize)db);
+    }
+    if (!f) return fail(c, BD3MG_EINVAL, "write to %s failed", path);
+    return BD3MG_OK;
+}
+
+bd3mg_status bd3mg_load(bd3mg_ctx *c, const char *path) {
+    GUARD(c);
+    if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
+    std::ifstream f(path, std::ios::binary);
+    if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s", path);
+    CkptHead h{};
+    f.read(reinterpret_cast<char *>(&h), sizeof(h));
+    if (!f || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return fail(c, BD3MG_EINVAL, "%s is not a checkpoint of this library", path);
+    if (h.nvol != c->nvol || h.bf != (c->bf ? 1 : 0))
+        return fail(c, BD3MG_EINVAL, "checkpoint has %d volume(s), precision %d; the context has %d, %d", h.nvol, h.bf,
+                    c->nvol, c->bf ? 1 : 0);
+    std::vector<char> buf;
+    for (VolState &v : c->V) {
+        int32_t dims[4];
+        f.read(reinterpret_cast<char *>(dims), sizeof(dims));
+        if (!f || dims[0] != v.p.nx || dims[1] != v.p.ny || dims[2] != v.p.nz || dims[3] != v.pitch)
+            return fail(c, BD3MG_EINVAL, "checkpoint volume shape does not match the context");
+        const size_t xb = v.np * 4, db = v.np * (c->bf ? 2 : 4);
+        buf.resize(xb + db);
+        f.read(buf.data(), (std::streamsize)(xb + db));
+        if (!f) return fail(c, BD3MG_EINVAL, "checkpoint %s is truncated", path);
+        CK(cudaMemcpyAsync(v.x, buf.data(), xb, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->bf ? (void *)v.dh : (void *)v.d, buf.data() + xb, db, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    c->iterations = h.iterations;
+    return reset_run(c, -1);
 }
 
 bd3mg_status bd3mg_last_step(bd3mg_ctx *c, double *info) {
