@@ -184,8 +184,7 @@ struct Smem {
     static constexpr size_t residual =
         sizeof(float) * (A::NSF * A::SLOT + A::BY * A::BX + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::NSF);
     static constexpr size_t gradient =
-        sizeof(float) * (A::NSA * A::SLOT + NSX * A::SLOT1 + A::BY * TX + A::CF_FLOATS) +
-        A::bars_bytes(A::NSA + NSX);
+        sizeof(float) * (A::KZ * A::SLOT + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::KZ);
     static constexpr size_t curvature =
         sizeof(float) * (2 * C::NSF * C::SLOT + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
         C::bars_bytes(C::NSF);
@@ -608,311 +607,6 @@ static __device__ __forceinline__ void objective_finish(const KArgs &a) {
 }
 
 // ---------------------------------------------------------------------------
-// k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ).
-// ---------------------------------------------------------------------------
-template <int R, int RZ>
-__global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
-    using G = Geo<R, RZ, TY_A>;
-    constexpr int RPW = G::RPW;
-    extern __shared__ __align__(128) float smem[];
-    float *stg = smem;
-    float *W = stg + G::NSF * G::SLOT;
-    float *T1 = W + G::BY * G::BX;
-    float *CF = T1 + G::BY * TX;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
-
-    const Item it = a.items[blockIdx.x];
-    const SegDev sg = a.segs[it.seg];
-    const VolDev &V = a.vols[sg.vol];
-    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
-    const long long plane = V.plane;
-    const float *yp = V.y;
-    float *rp = V.r;
-    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool store_r = (a.mode & M_STORE_R) != 0;
-    const bool obj = (a.mode & M_OBJ) != 0;
-    // A stopped volume's item gets an empty range: no copies, no loop, zero
-    // partials, but it still takes its ticket.
-    const bool stopped = vol_stopped(a, sg.vol);
-
-    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
-    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
-    if (!init_bars(bar, G::NSF, smem, a.sh->status)) return;
-    Pipe<G::NSF, G::SLOT> px;
-    px.init(stg, bar, &a.maps[sg.vol].m[TM_X_R], it.tx0 - G::XH, it.ty0 - R, max(0, zbeg), min(nz, zend),
-            (uint32_t)(G::BX * G::BY * sizeof(float)), zbeg);
-    px.issue_upto(zbeg + PREF - 1);
-    __syncthreads();
-
-    float acc[3] = {0.f, 0.f, 0.f};           // data, box, penalty
-    const int y0 = warp * RPW;
-    const int gx = it.tx0 + lane;
-    const bool colin = gx < nx;
-    // fixed per-thread offsets of this item
-    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
-    int xsrc[XP], xdst[XP];
-#pragma unroll
-    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
-    int goff[RPW];
-    unsigned vmask = 0u;
-#pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-        const int gy = it.ty0 + y0 + k;
-        goff[k] = gy * pitch + gx;
-        if (colin && gy < ny) vmask |= 1u << k;
-    }
-
-    for (int zi = zbeg, s = 0; zi < zend; ++zi, s = (s + 1 == G::NSF) ? 0 : s + 1) {
-        const bool ok = px.wait_upto(zi);
-        const int zo = zi - RZ;
-        const bool emit = zo >= it.zo0;
-        const float *cfr = CF + (zo - zbeg) * G::CFS;
-        float yv[RPW];
-        if (emit) {
-            // observation values of this thread's outputs, fetched early to hide latency
-            const float *yrow = yp ? yp + (long long)zo * plane : nullptr;
-#pragma unroll
-            for (int k = 0; k < RPW; ++k) yv[k] = (yrow && ((vmask >> k) & 1u)) ? __ldg(yrow + goff[k]) : 0.f;
-            float fzc[G::KZ];
-            row_coeffs(fzc, cfr + 2 * G::KXYP);
-            const float *w[G::KZ];
-            window(px, s, w);
-#pragma unroll
-            for (int j = 0; j < ZP; ++j)
-                if (tid + j * NT < G::ZUNITS) zcomb_unit(w, 4 * (tid + j * NT), fzc, W);
-        }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) { px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
-            return;
-        }
-        px.issue_upto(zi + PREF);
-        if (!emit) continue;
-        {
-            float fxc[G::KXY];
-            row_coeffs(fxc, cfr);
-#pragma unroll
-            for (int j = 0; j < XP; ++j)
-                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(W, T1, xsrc[j], xdst[j], fxc);
-        }
-        __syncthreads();
-        float fyc[G::KXY];
-        row_coeffs(fyc, cfr + G::KXYP);
-        float hx[RPW];
-        ypass<R, RPW, -1>(T1, y0, lane, fyc, hx);
-        const float *xz = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ) * G::SLOT;       // slice zo
-        const float *xz1 = px.buf + Pipe<G::NSF, G::SLOT>::back_slot(s, RZ - 1) * G::SLOT;  // slice zo+1
-        float *rrow = rp + (long long)zo * plane;
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-            const int yo = y0 + k, gy = it.ty0 + yo;
-            if ((vmask >> k) & 1u) {
-                const float rr = hx[k] - yv[k];
-                if (store_r) rrow[goff[k]] = rr;
-                if (obj) {
-                    const int ci = (yo + R) * G::BX + lane + G::XH;
-                    const float xc = xz[ci];
-                    acc[0] = fmaf(0.5f * rr, rr, acc[0]);
-                    const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                    acc[1] = fmaf(dist, dist, acc[1]);
-                    const float tx = gx < nx - 1 ? xz[ci + 1] - xc : 0.f;
-                    const float ty = gy < ny - 1 ? xz[ci + G::BX] - xc : 0.f;
-                    const float tz = zo < nz - 1 ? xz1[ci] - xc : 0.f;
-                    // sqrt(v) = v * rsqrt(v), v >= delta^2 > 0
-                    const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
-                    acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
-                }
-            }
-        }
-    }
-    if (!obj) return;
-    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
-}
-
-// ---------------------------------------------------------------------------
-// k_gradient: g = H^T r (+ box and penalty gradient unless M_HT_ONLY) on the
-// slabs' own slices.
-// ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF>
-__global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
-    using G = Geo<R, RZ, TY_A>;
-    constexpr int RPW = G::RPW;
-    extern __shared__ __align__(128) float smem[];
-    float *stg = smem;                                   // NSA * SLOT (r)
-    float *xs = stg + G::NSA * G::SLOT;                  // NSX * SLOT1 (x, 1-voxel halo)
-    float *T1 = xs + NSX * G::SLOT1;
-    float *CF = T1 + G::BY * TX;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
-
-    const Item it = a.items[blockIdx.x];
-    const SegDev sg = a.segs[it.seg];
-    const VolDev &V = a.vols[sg.vol];
-    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
-    const long long plane = V.plane;
-    float *gp = V.g;
-    __nv_bfloat16 *gph = V.gh;
-    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool full = (a.mode & M_HT_ONLY) == 0;
-    if (vol_stopped(a, sg.vol)) return;
-
-    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
-    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
-    if (!init_bars(bar, G::NSA + NSX, smem, a.sh->status)) return;
-    Pipe<G::NSA, G::SLOT> pr;
-    pr.init(stg, bar, &a.maps[sg.vol].m[TM_R_R], it.tx0 - G::XH, it.ty0 - R, max(0, zbeg), min(nz, zend),
-            (uint32_t)(G::BX * G::BY * sizeof(float)), zbeg);
-    Pipe<NSX, G::SLOT1> px;
-    px.init(xs, bar + G::NSA, &a.maps[sg.vol].m[TM_X_1A], it.tx0 - XH1, it.ty0 - 1, max(0, it.zo0 - 1),
-            min(nz, it.zo1 + 1), (uint32_t)(BX1 * G::BY1 * sizeof(float)), it.zo0 - 1);
-    pr.issue_upto(zbeg + PREF - 1);
-    if (full) px.issue_upto(zbeg - RZ + PREF);
-    __syncthreads();
-
-    // uring[k][j]: u of slice zi - (KZ-1) + j for this thread's outputs (j = KZ-1 newest)
-    float uring[RPW][G::KZ];
-#pragma unroll
-    for (int k = 0; k < RPW; ++k)
-#pragma unroll
-        for (int j = 0; j < G::KZ; ++j) uring[k][j] = 0.f;
-    const int y0 = warp * RPW;
-    const int gx = it.tx0 + lane;
-    const bool colin = gx < nx;
-    constexpr int XP = Units<G::XUNITS>::PER;
-    int xsrc[XP], xdst[XP];
-#pragma unroll
-    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
-
-    for (int zi = zbeg; zi < zend; ++zi) {
-        const int zo = zi - RZ;
-        const bool emit = zo >= it.zo0;
-        bool ok = pr.wait_upto(zi);
-        if (full) ok = px.wait_upto(zo + 1) && ok;
-        const bool ld = pr.loaded(zi);
-        const float *cfi = CF + (zi - zbeg) * G::CFS;
-        if (ld) {
-            float fxc[G::KXY];
-            row_coeffs(fxc, cfi);
-            const float *src = pr.at(zi);
-#pragma unroll
-            for (int j = 0; j < XP; ++j)
-                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, +1>(src, T1, xsrc[j], xdst[j], fxc);
-        }
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) { pr.drain(); px.drain(); atomicOr(a.sh->status, ST_TIMEOUT); }
-            return;
-        }
-        pr.issue_upto(zi + PREF);
-        if (full) px.issue_upto(zo + 1 + PREF);
-        float u[RPW];
-        if (ld) {
-            float fyc[G::KXY];
-            row_coeffs(fyc, cfi + G::KXYP);
-            ypass<R, RPW, +1>(T1, y0, lane, fyc, u);
-        } else {
-#pragma unroll
-            for (int k = 0; k < RPW; ++k) u[k] = 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < RPW; ++k) {
-#pragma unroll
-            for (int j = 0; j < G::KZ - 1; ++j) uring[k][j] = uring[k][j + 1];
-            uring[k][G::KZ - 1] = u[k];
-        }
-        if (emit) {
-            // q(zo) = sum_c fz_{zo+c}[c+RZ] u(zo+c), u(zo+c) in uring[.][c+RZ]
-            float fzc[G::KZ];
-#pragma unroll
-            for (int t = 0; t < G::KZ; ++t) fzc[t] = CF[(zo + t - RZ - zbeg) * G::CFS + 2 * G::KXYP + t];
-            const long long zoff = (long long)zo * plane;
-            const float *xm = full ? px.at(zo - 1) : nullptr;
-            const float *x0p = full ? px.at(zo) : nullptr;
-            const float *xp1 = full ? px.at(zo + 1) : nullptr;
-#pragma unroll
-            for (int k = 0; k < RPW; ++k) {
-                float q0 = 0.f, q1 = 0.f;
-#pragma unroll
-                for (int t = 0; t < G::KZ; t += 2) q0 = fmaf(fzc[t], uring[k][t], q0);
-#pragma unroll
-                for (int t = 1; t < G::KZ; t += 2) q1 = fmaf(fzc[t], uring[k][t], q1);
-                const float q = q0 + q1;
-                const int yo = y0 + k, gy = it.ty0 + yo;
-                if (colin && gy < ny) {
-                    const int n = gy * pitch + gx;
-                    float gval = q;
-                    if (full) {
-                        const int ci = (yo + 1) * BX1 + lane + XH1;
-                        const float *x0 = x0p + ci;
-                        const float xc = x0[0];
-                        float pen = 0.f;
-                        if (gx >= 1) { const float t = xc - x0[-1]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
-                        if (gx < nx - 1) { const float t = x0[1] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
-                        if (gy >= 1) { const float t = xc - x0[-BX1]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
-                        if (gy < ny - 1) { const float t = x0[BX1] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
-                        if (zo >= 1) { const float t = xc - xm[ci]; pen += t * rsqrtf(fmaf(t, t, delta2)); }
-                        if (zo < nz - 1) { const float t = xp1[ci] - xc; pen -= t * rsqrtf(fmaf(t, t, delta2)); }
-                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                        gval = fmaf(lam, pen, fmaf(eta2, dist, q));
-                    }
-                    if constexpr (BF) gph[zoff + n] = __float2bfloat16_rn(gval);
-                    else gp[zoff + n] = gval;
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Last CTA of a curvature launch: per slab slot, B = D^T A D and c = D^T grad f
-// (D = [-g, d]) from the FP64 sums, u = -B^+ c, and the squared length of the
-// step D u added to the volume's sweep total.  Slots of stopped volumes get u = 0.
-static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
-    __shared__ double tot[10];
-    const int tid = threadIdx.x;
-    for (int sl = 0; sl < a.nslots; ++sl) {
-        const int slot = a.slot_id[sl];
-        const SegDev ss = a.segs[a.items[a.slot_beg[sl]].seg];
-        if (vol_stopped(a, ss.vol)) {
-            if (tid == 0) {
-                a.u[2 * slot] = 0.0;
-                a.u[2 * slot + 1] = 0.0;
-            }
-            continue;
-        }
-        sum_slot<10>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
-        if (tid == 0) {
-            const VolDev &vv = a.vols[ss.vol];
-            const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
-            const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
-            const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
-            const double b11 = tot[5] + e2 * tot[2] + lam * tot[8];
-            const double c0 = -tot[0], c1 = tot[1];
-            double u0 = 0.0, u1 = 0.0;
-            int rank = 0;
-            if (isfinite(b00) && isfinite(b01) && isfinite(b11) && isfinite(c0) && isfinite(c1)) {
-                rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
-            } else {
-                atomicOr(a.sh->status, ST_NONFINITE);
-            }
-            a.u[2 * slot] = u0;
-            a.u[2 * slot + 1] = u1;
-            double *inf = a.info + 8 * slot;
-            inf[0] = b00; inf[1] = b01; inf[2] = b11; inf[3] = c0; inf[4] = c1;
-            inf[5] = u0; inf[6] = u1; inf[7] = (double)rank;
-            // Slab S of the sweep from x^k: x_S still holds x^k_S (only its own
-            // update writes it), and the step is ||-u0 g + u1 d||^2 over S.
-            if (a.sh->run) {
-                VolRun &rv = a.sh->run[ss.vol];
-                rv.dx2 += u0 * u0 * tot[0] - 2.0 * u0 * u1 * tot[1] + u1 * u1 * tot[2];
-                rv.xx_prev += tot[9];
-            }
-        }
-        __syncthreads();
-    }
-    if (tid == 0) *a.ticket = 0u;
-}
-
-// ---------------------------------------------------------------------------
 // Helpers of the ring-unrolled kernels.
 // ---------------------------------------------------------------------------
 
@@ -970,6 +664,496 @@ __device__ __forceinline__ float2 ypass_pair(const float *T1, int yo, int c, con
 #pragma unroll
     for (int b = -R + 1; b <= R; b += 2) s1 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[R - b], s1);
     return __fadd2_rn(s0, s1);
+}
+
+// Forward y-pass of the column pair (c, c+1) at output rows yo and yo+1 (one
+// load of the 2R+2 staged rows they share): out_k = sum_b fy[b+R] T1[yo+k+R-b].
+template <int R>
+__device__ __forceinline__ void ypass_pair2(const float *T1, int yo, int c, const float (&fy)[2 * R + 1],
+                                            float2 &o0, float2 &o1) {
+    float2 t[2 * R + 2];
+#pragma unroll
+    for (int j = 0; j < 2 * R + 2; ++j) t[j] = ld2(T1 + (yo + j) * TX + c);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+#pragma unroll
+        for (int b = -R; b <= R; b += 2) s0 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[k + R - b], s0);
+#pragma unroll
+        for (int b = -R + 1; b <= R; b += 2) s1 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[k + R - b], s1);
+        (k == 0 ? o0 : o1) = __fadd2_rn(s0, s1);
+    }
+}
+
+// Objective terms of one voxel with centre value xc and forward differences
+// tx, ty, tz (0 where the neighbour does not exist): acc0 += r^2/2,
+// acc1 += dist(xc, [xmin, xmax])^2, acc2 += sum_a sqrt(delta^2 + t_a^2).
+__device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty, float tz, float delta2, float xmin,
+                                          float xmax, float (&acc)[3]) {
+    acc[0] = fmaf(0.5f * rr, rr, acc[0]);
+    const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+    acc[1] = fmaf(dist, dist, acc[1]);
+    // sqrt(v) = v * rsqrt(v), v >= delta^2 > 0
+    const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
+    acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
+}
+
+// ---------------------------------------------------------------------------
+// k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ).
+// z-march unrolled over the ring (compile-time slots); z-combine and y-pass
+// with paired FP32 FMAs; each thread of the y-pass and of the epilogue owns
+// a 2 x 2 block of outputs (rows yo, yo+1; columns c, c+1).
+// ---------------------------------------------------------------------------
+template <int R, int RZ>
+__global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
+    using G = Geo<R, RZ, TY_A>;
+    constexpr int NS = G::NSF, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
+    extern __shared__ __align__(128) float smem[];
+    float *stg = smem;
+    float *W = stg + NS * SLOT;
+    float *T1 = W + BY * BX;
+    float *CF = T1 + BY * TX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
+
+    const Item it = a.items[blockIdx.x];
+    const SegDev sg = a.segs[it.seg];
+    const VolDev &V = a.vols[sg.vol];
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane;
+    const float *yp = V.y;
+    float *rp = V.r;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool store_r = (a.mode & M_STORE_R) != 0;
+    const bool obj = (a.mode & M_OBJ) != 0;
+    // A stopped volume's item gets an empty range: no copies, no loop, zero
+    // partials, but it still takes its ticket.
+    const bool stopped = vol_stopped(a, sg.vol);
+
+    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    if (!init_bars(bar, NS, smem, a.sh->status)) return;
+    const int xlo = max(0, zbeg), xhi = min(nz, zend);
+    const CUtensorMap *mx = &a.maps[sg.vol].m[TM_X_R];
+    if (tid == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mx)) : "memory");
+    const uint32_t nb = (uint32_t)(BX * BY * sizeof(float));
+    const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
+    constexpr int FILL = SLOT / 4;
+    auto issue = [&](int z, int s) {
+        if (z >= xlo && z < xhi) {
+            if (tid == 0) {
+                mbar_expect_tx(bar + s, nb);
+                tma_load_3d(stg + s * SLOT, mx, bx0, by0, z, bar + s);
+            }
+        } else {
+            float4 *p4 = reinterpret_cast<float4 *>(stg + s * SLOT);
+            for (int i = tid; i < FILL; i += NT) p4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+    };
+#pragma unroll
+    for (int p = 0; p < PREF; ++p) issue(zbeg + p, p);
+    __syncthreads();
+
+    float acc[3] = {0.f, 0.f, 0.f};           // data, box, penalty
+    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
+    // 2 x 2 outputs: rows yo, yo+1; columns c, c+1
+    const int yo = 4 * warp + 2 * (lane >> 4), c = 2 * (lane & 15);
+    const int gx = it.tx0 + c, gy = it.ty0 + yo;
+    const bool c0ok = gx < nx, c1ok = gx + 1 < nx;
+    const bool r0ok = gy < ny, r1ok = gy + 1 < ny;
+    const bool xe0 = gx + 1 < nx, xe1 = gx + 2 < nx;       // x neighbour exists
+    const bool ye0 = gy + 1 < ny, ye1 = gy + 2 < ny;       // y neighbour exists
+    const long long o0 = (long long)gy * pitch + gx, o1 = o0 + pitch;
+    const int ci = (yo + R) * BX + XH + c;                // staged index of (yo, c)
+    uint32_t par = 0u;
+    bool timed_out = false;
+    int zi = zbeg;
+
+    auto step = [&](auto sc) -> bool {
+        constexpr int S = decltype(sc)::value;
+        if (zi >= zend) return false;
+        const int zo = zi - RZ;
+        const bool emit = zo >= it.zo0;
+        bool ok = true;
+        if (zi >= xlo && zi < xhi) {
+            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            if (ok) par ^= 1u << S;
+        }
+        const float *cfr = CF + (zo - zbeg) * G::CFS;
+        float2 y0v = make_float2(0.f, 0.f), y1v = y0v;
+        if (emit) {
+            // observation values of this thread's outputs, fetched early to hide latency
+            if (yp) {
+                const float *yrow = yp + (long long)zo * plane;
+                if (r0ok && c0ok) y0v = __ldg(reinterpret_cast<const float2 *>(yrow + o0));
+                if (r1ok && c0ok) y1v = __ldg(reinterpret_cast<const float2 *>(yrow + o1));
+            }
+            float fzc[KZ];
+            row_coeffs(fzc, cfr + 2 * G::KXYP);
+#pragma unroll
+            for (int j = 0; j < ZP; ++j) {
+                const int u = 4 * (tid + j * NT);
+                if (tid + j * NT < G::ZUNITS) zcomb_ring<KZ, NS, S, SLOT>(stg + u, fzc, W + u);
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            return false;
+        }
+        issue(zi + PREF, (S + PREF) % NS);
+        ++zi;
+        if (!emit) return true;
+        {
+            float fxc[G::KXY];
+            row_coeffs(fxc, cfr);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(W, T1, xsrc[j], xdst[j], fxc);
+        }
+        __syncthreads();
+        float fyc[G::KXY];
+        row_coeffs(fyc, cfr + G::KXYP);
+        float2 h0, h1;
+        ypass_pair2<R>(T1, yo, c, fyc, h0, h1);
+        const float2 r0 = make_float2(h0.x - y0v.x, h0.y - y0v.y), r1 = make_float2(h1.x - y1v.x, h1.y - y1v.y);
+        if (store_r) {
+            float *rrow = rp + (long long)zo * plane;
+            if (r0ok && c0ok) {
+                if (c1ok) *reinterpret_cast<float2 *>(rrow + o0) = r0;
+                else rrow[o0] = r0.x;
+            }
+            if (r1ok && c0ok) {
+                if (c1ok) *reinterpret_cast<float2 *>(rrow + o1) = r1;
+                else rrow[o1] = r1.x;
+            }
+        }
+        if (obj && r0ok && c0ok) {
+            constexpr int s0 = (S - RZ + NS) % NS, s1 = (S - RZ + 1 + NS) % NS;   // slices zo, zo + 1
+            const float *xa = stg + s0 * SLOT + ci, *xb = stg + s1 * SLOT + ci;
+            const float2 a0 = ld2(xa), a1 = ld2(xa + BX), a2 = ld2(xa + 2 * BX);
+            const float e0 = xa[2], e1 = xa[BX + 2];
+            const float2 z0 = ld2(xb), z1 = ld2(xb + BX);
+            const bool ze = zo + 1 < nz;
+            obj_terms(r0.x, a0.x, xe0 ? a0.y - a0.x : 0.f, ye0 ? a1.x - a0.x : 0.f, ze ? z0.x - a0.x : 0.f, delta2,
+                      xmin, xmax, acc);
+            if (c1ok)
+                obj_terms(r0.y, a0.y, xe1 ? e0 - a0.y : 0.f, ye0 ? a1.y - a0.y : 0.f, ze ? z0.y - a0.y : 0.f, delta2,
+                          xmin, xmax, acc);
+            if (r1ok) {
+                obj_terms(r1.x, a1.x, xe0 ? a1.y - a1.x : 0.f, ye1 ? a2.x - a1.x : 0.f, ze ? z1.x - a1.x : 0.f,
+                          delta2, xmin, xmax, acc);
+                if (c1ok)
+                    obj_terms(r1.y, a1.y, xe1 ? e1 - a1.y : 0.f, ye1 ? a2.y - a1.y : 0.f, ze ? z1.y - a1.y : 0.f,
+                              delta2, xmin, xmax, acc);
+            }
+        }
+        return true;
+    };
+    while (for_slots<0, NS>(step)) {
+    }
+    if (timed_out) {
+        if (tid == 0) {
+            for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
+                if (z < xlo || z >= xhi) continue;
+                const int s = (z - zbeg) % NS;
+                if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+            }
+            atomicOr(a.sh->status, ST_TIMEOUT);
+        }
+        return;
+    }
+    if (!obj) return;
+    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
+}
+
+// Adjoint y-pass (correlation) of the column pair (c, c+1) at rows yo, yo+1:
+// out_k = sum_b fy[b+R] T1[yo+k+R+b].
+template <int R>
+__device__ __forceinline__ void ypassT_pair2(const float *T1, int yo, int c, const float (&fy)[2 * R + 1],
+                                             float2 &o0, float2 &o1) {
+    float2 t[2 * R + 2];
+#pragma unroll
+    for (int j = 0; j < 2 * R + 2; ++j) t[j] = ld2(T1 + (yo + j) * TX + c);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float2 s0 = make_float2(0.f, 0.f), s1 = s0;
+#pragma unroll
+        for (int b = -R; b <= R; b += 2) s0 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[k + R + b], s0);
+#pragma unroll
+        for (int b = -R + 1; b <= R; b += 2) s1 = __ffma2_rn(make_float2(fy[b + R], fy[b + R]), t[k + R + b], s1);
+        (k == 0 ? o0 : o1) = __fadd2_rn(s0, s1);
+    }
+}
+
+// psi'(t) = t / sqrt(delta^2 + t^2) of the hyperbolic penalty.
+__device__ __forceinline__ float dpsi(float t, float delta2) { return t * rsqrtf(fmaf(t, t, delta2)); }
+
+// ---------------------------------------------------------------------------
+// k_gradient: g = H^T r (+ box and penalty gradient unless M_HT_ONLY) on the
+// slabs' own slices.  Adjoint order: each input slice of r is correlated in x
+// and y with its own depth's factors, and the z-combine runs in registers over
+// a ring of KZ per-thread slices.  The r ring has KZ slots, so ring slot and
+// register-ring index are the same compile-time constant in the unrolled
+// z-march.  Each thread owns a 2 x 2 block of outputs; the forward
+// differences of x it needs are shared between its four voxels; x is read
+// through the L1 cache.
+// ---------------------------------------------------------------------------
+template <int R, int RZ, bool BF>
+__global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
+    using G = Geo<R, RZ, TY_A>;
+    constexpr int KZ = G::KZ, NS = KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
+    static_assert(NS >= PREF + 1, "ring too short for the prefetch distance");
+    extern __shared__ __align__(128) float smem[];
+    float *stg = smem;                                   // NS * SLOT (r)
+    float *T1 = stg + NS * SLOT;
+    float *CF = T1 + BY * TX;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
+
+    const Item it = a.items[blockIdx.x];
+    const SegDev sg = a.segs[it.seg];
+    const VolDev &V = a.vols[sg.vol];
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane;
+    float *gp = V.g;
+    __nv_bfloat16 *gph = V.gh;
+    const float *xg = V.x;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool full = (a.mode & M_HT_ONLY) == 0;
+    if (vol_stopped(a, sg.vol)) return;
+
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    if (!init_bars(bar, NS, smem, a.sh->status)) return;
+    const int rlo = max(0, zbeg), rhi = min(nz, zend);
+    const CUtensorMap *mr = &a.maps[sg.vol].m[TM_R_R];
+    if (tid == 0)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mr)) : "memory");
+    const uint32_t nb = (uint32_t)(BX * BY * sizeof(float));
+    const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
+    auto issue = [&](int z, int s) {
+        if (tid == 0 && z >= rlo && z < rhi) {
+            mbar_expect_tx(bar + s, nb);
+            tma_load_3d(stg + s * SLOT, mr, bx0, by0, z, bar + s);
+        }
+    };
+#pragma unroll
+    for (int p = 0; p < PREF; ++p) issue(zbeg + p, p);
+    __syncthreads();
+
+    constexpr int XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
+    const int yo = 4 * warp + 2 * (lane >> 4), c = 2 * (lane & 15);
+    const int gx = it.tx0 + c, gy = it.ty0 + yo;
+    const bool c0ok = gx < nx, c1ok = gx + 1 < nx, r0ok = gy < ny, r1ok = gy + 1 < ny;
+    const long long o0 = (long long)gy * pitch + gx, o1 = o0 + pitch;
+    // uring[t]: H_xy^T r of the rows (yo, yo+1) x columns (c, c+1) for slice zi - ((S - t) mod KZ)
+    float2 ur0[KZ], ur1[KZ];
+#pragma unroll
+    for (int t = 0; t < KZ; ++t) ur0[t] = ur1[t] = make_float2(0.f, 0.f);
+    uint32_t par = 0u;
+    bool timed_out = false;
+    int zi = zbeg;
+
+    auto step = [&](auto sc) -> bool {
+        constexpr int S = decltype(sc)::value;
+        if (zi >= zend) return false;
+        const int zo = zi - RZ;
+        const bool emit = zo >= it.zo0;
+        const bool ld = zi >= rlo && zi < rhi;
+        bool ok = true;
+        if (ld) {
+            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            if (ok) par ^= 1u << S;
+        }
+        const float *cfi = CF + (zi - zbeg) * G::CFS;
+        if (ld) {
+            float fxc[G::KXY];
+            row_coeffs(fxc, cfi);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, +1>(stg + S * SLOT, T1, xsrc[j], xdst[j], fxc);
+        }
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            return false;
+        }
+        issue(zi + PREF, (S + PREF) % NS);
+        if (ld) {
+            float fyc[G::KXY];
+            row_coeffs(fyc, cfi + G::KXYP);
+            ypassT_pair2<R>(T1, yo, c, fyc, ur0[S], ur1[S]);
+        } else {
+            ur0[S] = ur1[S] = make_float2(0.f, 0.f);
+        }
+        if (emit) {
+            // q(zo) = sum_t fz_{zo+t-RZ}[t] u(zo + t - RZ); u of slice zi - 2RZ + t in ring index (S + 1 + t) mod KZ
+            float2 qa0 = make_float2(0.f, 0.f), qb0 = qa0, qa1 = qa0, qb1 = qa0;
+#pragma unroll
+            for (int t = 0; t < KZ; ++t) {
+                const float f = CF[(zo + t - RZ - zbeg) * G::CFS + 2 * G::KXYP + t];
+                const float2 f2 = make_float2(f, f);
+                const int ri = (S + 1 + t) % KZ;
+                if (t & 1) {
+                    qb0 = __ffma2_rn(f2, ur0[ri], qb0);
+                    qb1 = __ffma2_rn(f2, ur1[ri], qb1);
+                } else {
+                    qa0 = __ffma2_rn(f2, ur0[ri], qa0);
+                    qa1 = __ffma2_rn(f2, ur1[ri], qa1);
+                }
+            }
+            float2 q0 = __fadd2_rn(qa0, qb0), q1 = __fadd2_rn(qa1, qb1);
+            if (full && r0ok && c0ok) {
+                const long long zoff = (long long)zo * plane;
+                const float *xr = xg + zoff + o0;                  // (yo, c) at slice zo
+                const bool xl = gx >= 1, xr1 = gx + 2 < nx;
+                const bool yu = gy >= 1, yd2 = gy + 2 < ny;
+                const bool zl = zo >= 1, zr = zo + 1 < nz;
+                // row yo: columns c-1 .. c+2; row yo+1 likewise
+                const float2 p0 = __ldg(reinterpret_cast<const float2 *>(xr));
+                const float m0 = xl ? __ldg(xr - 1) : p0.x, e0 = xr1 ? __ldg(xr + 2) : p0.y;
+                float2 p1 = p0;
+                float m1 = m0, e1 = e0;
+                if (r1ok) {
+                    p1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch));
+                    m1 = xl ? __ldg(xr + pitch - 1) : p1.x;
+                    e1 = xr1 ? __ldg(xr + pitch + 2) : p1.y;
+                }
+                const float2 pu = yu ? __ldg(reinterpret_cast<const float2 *>(xr - pitch)) : p0;
+                const float2 pd = yd2 ? __ldg(reinterpret_cast<const float2 *>(xr + 2 * pitch)) : p1;
+                const float2 zl0 = zl ? __ldg(reinterpret_cast<const float2 *>(xr - plane)) : p0;
+                const float2 zr0 = zr ? __ldg(reinterpret_cast<const float2 *>(xr + plane)) : p0;
+                float2 zl1 = p1, zr1 = p1;
+                if (r1ok) {
+                    if (zl) zl1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch - plane));
+                    if (zr) zr1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch + plane));
+                }
+                // x differences (each shared by its two voxels): row k: (c-1,c), (c,c+1), (c+1,c+2)
+                const bool hx0 = c1ok;                               // (c, c+1) is a difference of the volume
+                const float ax0 = xl ? dpsi(p0.x - m0, delta2) : 0.f;
+                const float bx0 = hx0 ? dpsi(p0.y - p0.x, delta2) : 0.f;
+                const float cx0 = xr1 ? dpsi(e0 - p0.y, delta2) : 0.f;
+                const float ax1 = xl ? dpsi(p1.x - m1, delta2) : 0.f;
+                const float bx1 = hx0 ? dpsi(p1.y - p1.x, delta2) : 0.f;
+                const float cx1 = xr1 ? dpsi(e1 - p1.y, delta2) : 0.f;
+                // y differences per column: (yo-1,yo), (yo,yo+1), (yo+1,yo+2)
+                const float2 ay = yu ? make_float2(dpsi(p0.x - pu.x, delta2), dpsi(p0.y - pu.y, delta2))
+                                     : make_float2(0.f, 0.f);
+                const float2 by = r1ok ? make_float2(dpsi(p1.x - p0.x, delta2), dpsi(p1.y - p0.y, delta2))
+                                       : make_float2(0.f, 0.f);
+                const float2 cy = yd2 ? make_float2(dpsi(pd.x - p1.x, delta2), dpsi(pd.y - p1.y, delta2))
+                                      : make_float2(0.f, 0.f);
+                // z differences per voxel
+                auto zterm = [&](float xc, float xlz, float xrz) {
+                    return (zl ? dpsi(xc - xlz, delta2) : 0.f) - (zr ? dpsi(xrz - xc, delta2) : 0.f);
+                };
+                const float pen00 = ax0 - bx0 + ay.x - by.x + zterm(p0.x, zl0.x, zr0.x);
+                const float pen01 = bx0 - cx0 + ay.y - by.y + zterm(p0.y, zl0.y, zr0.y);
+                const float pen10 = ax1 - bx1 + by.x - cy.x + zterm(p1.x, zl1.x, zr1.x);
+                const float pen11 = bx1 - cx1 + by.y - cy.y + zterm(p1.y, zl1.y, zr1.y);
+                auto gval = [&](float q, float xc, float pen) {
+                    const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+                    return fmaf(lam, pen, fmaf(eta2, dist, q));
+                };
+                q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
+                q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
+            }
+            if (c0ok) {
+                const long long zoff = (long long)zo * plane;
+                if constexpr (BF) {
+                    if (full) {
+                        if (r0ok) {
+                            if (c1ok) *reinterpret_cast<__nv_bfloat162 *>(gph + zoff + o0) = __floats2bfloat162_rn(q0.x, q0.y);
+                            else gph[zoff + o0] = __float2bfloat16_rn(q0.x);
+                        }
+                        if (r1ok) {
+                            if (c1ok) *reinterpret_cast<__nv_bfloat162 *>(gph + zoff + o1) = __floats2bfloat162_rn(q1.x, q1.y);
+                            else gph[zoff + o1] = __float2bfloat16_rn(q1.x);
+                        }
+                    }
+                }
+                if (!BF || !full) {
+                    if (r0ok) {
+                        if (c1ok) *reinterpret_cast<float2 *>(gp + zoff + o0) = q0;
+                        else gp[zoff + o0] = q0.x;
+                    }
+                    if (r1ok) {
+                        if (c1ok) *reinterpret_cast<float2 *>(gp + zoff + o1) = q1;
+                        else gp[zoff + o1] = q1.x;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        ++zi;
+        return true;
+    };
+    while (for_slots<0, NS>(step)) {
+    }
+    if (timed_out && tid == 0) {
+        for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
+            if (z < rlo || z >= rhi) continue;
+            const int s = (z - zbeg) % NS;
+            if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+        }
+        atomicOr(a.sh->status, ST_TIMEOUT);
+    }
+}
+
+// Last CTA of a curvature launch: per slab slot, B = D^T A D and c = D^T grad f
+// (D = [-g, d]) from the FP64 sums, u = -B^+ c, and the squared length of the
+// step D u added to the volume's sweep total.  Slots of stopped volumes get u = 0.
+static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
+    __shared__ double tot[10];
+    const int tid = threadIdx.x;
+    for (int sl = 0; sl < a.nslots; ++sl) {
+        const int slot = a.slot_id[sl];
+        const SegDev ss = a.segs[a.items[a.slot_beg[sl]].seg];
+        if (vol_stopped(a, ss.vol)) {
+            if (tid == 0) {
+                a.u[2 * slot] = 0.0;
+                a.u[2 * slot + 1] = 0.0;
+            }
+            continue;
+        }
+        sum_slot<10>(a.partials, a.slot_beg[sl], a.slot_beg[sl + 1], tot);
+        if (tid == 0) {
+            const VolDev &vv = a.vols[ss.vol];
+            const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
+            const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
+            const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
+            const double b11 = tot[5] + e2 * tot[2] + lam * tot[8];
+            const double c0 = -tot[0], c1 = tot[1];
+            double u0 = 0.0, u1 = 0.0;
+            int rank = 0;
+            if (isfinite(b00) && isfinite(b01) && isfinite(b11) && isfinite(c0) && isfinite(c1)) {
+                rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
+            } else {
+                atomicOr(a.sh->status, ST_NONFINITE);
+            }
+            a.u[2 * slot] = u0;
+            a.u[2 * slot + 1] = u1;
+            double *inf = a.info + 8 * slot;
+            inf[0] = b00; inf[1] = b01; inf[2] = b11; inf[3] = c0; inf[4] = c1;
+            inf[5] = u0; inf[6] = u1; inf[7] = (double)rank;
+            // Slab S of the sweep from x^k: x_S still holds x^k_S (only its own
+            // update writes it), and the step is ||-u0 g + u1 d||^2 over S.
+            if (a.sh->run) {
+                VolRun &rv = a.sh->run[ss.vol];
+                rv.dx2 += u0 * u0 * tot[0] - 2.0 * u0 * u1 * tot[1] + u1 * u1 * tot[2];
+                rv.xx_prev += tot[9];
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *a.ticket = 0u;
 }
 
 // Half-quadratic curvature terms of one voxel along one axis: with
