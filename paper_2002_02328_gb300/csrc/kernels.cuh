@@ -169,7 +169,22 @@ struct Geo {
     static constexpr int CFS = 2 * KXYP + KZP;
     static constexpr int CF_ROWS = ZC_MAX + 2 * RZ;
     static constexpr int CF_FLOATS = ((CF_ROWS * CFS + 31) / 32) * 32;
+    static constexpr int CF_OUT_FLOATS = ((ZC_MAX * CFS + 31) / 32) * 32;   // rows of output slices only
     static constexpr size_t bars_bytes(int n) { return ((n * 8 + 127) / 128) * 128; }
+};
+
+// Ring of k_curvature: KZ + PF slots per direction array.  One slice in flight
+// (PF = 1) when that lets three CTAs share an SM, otherwise two.
+template <int R, int RZ, int EB>
+struct CurvRing {
+    using C = Geo<R, RZ, TY_C, EB>;
+    static constexpr size_t bytes(int pf) {
+        return (size_t)EB * (2 * (C::KZ + pf) * C::SLOT) +
+               sizeof(float) * (2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_OUT_FLOATS) + C::bars_bytes(C::KZ + pf);
+    }
+    static constexpr int PF = bytes(1) <= 74 * 1024 ? 1 : 2;
+    static constexpr int NS = C::KZ + PF;
+    static constexpr size_t SMEM = bytes(PF);
 };
 
 template <int R, int RZ>
@@ -185,13 +200,9 @@ struct Smem {
         sizeof(float) * (A::NSF * A::SLOT + A::BY * A::BX + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::NSF);
     static constexpr size_t gradient =
         sizeof(float) * (A::KZ * A::SLOT + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::KZ);
-    static constexpr size_t curvature =
-        sizeof(float) * (2 * C::NSF * C::SLOT + 2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_FLOATS) +
-        C::bars_bytes(C::NSF);
+    static constexpr size_t curvature = CurvRing<R, RZ, 4>::SMEM;
     // BF16 directions: g, d slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
-    static constexpr size_t curvature_bf =
-        2 * (2 * CB::NSF * CB::SLOT) +
-        sizeof(float) * (2 * CB::BY * CB::BX + 2 * CB::BY * TX + CB::CF_FLOATS) + CB::bars_bytes(CB::NSF);
+    static constexpr size_t curvature_bf = CurvRing<R, RZ, 2>::SMEM;
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -1181,17 +1192,18 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
 // through the L1 cache.
 // ---------------------------------------------------------------------------
 template <int R, int RZ, bool BF>
-__global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
+__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::PF == 1 ? 3 : 2) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // direction storage
     using G = Geo<R, RZ, TY_C, sizeof(T)>;
-    constexpr int NS = G::NSF, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
+    constexpr int PF = CurvRing<R, RZ, sizeof(T)>::PF;    // slices in flight ahead of the consumer
+    constexpr int NS = CurvRing<R, RZ, sizeof(T)>::NS, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
     extern __shared__ __align__(128) float smem[];
     T *sgs = reinterpret_cast<T *>(smem);                // NS * SLOT (g)
     T *sds = sgs + NS * SLOT;                            // NS * SLOT (d)
     float *Wb = reinterpret_cast<float *>(sds + NS * SLOT);   // [g, d][BY * BX]
     float *T1b = Wb + 2 * BY * BX;                            // [g, d][BY * TX]
     float *CF = T1b + 2 * BY * TX;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_OUT_FLOATS);
 
     const Item it = a.items[blockIdx.x];
     const SegDev sg = a.segs[it.seg];
@@ -1207,7 +1219,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     const bool stopped = vol_stopped(a, sg.vol);
 
     const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
-    stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
+    stage_coeffs<G>(CF, V, it.zo0, stopped ? 0 : it.zo1 - it.zo0);   // rows of the output slices only
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
     const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R], *md = &a.maps[sg.vol].m[TM_D_R];
@@ -1238,7 +1250,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
         }
     };
 #pragma unroll
-    for (int p = 0; p < PREF; ++p) issue(zbeg + p, p);      // slice z lives in slot (z - zbeg) % NS
+    for (int p = 0; p < PF; ++p) issue(zbeg + p, p);        // slice z lives in slot (z - zbeg) % NS
     __syncthreads();
 
     float acc[10];
@@ -1288,7 +1300,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
             xy = __ldg(reinterpret_cast<const float2 *>(xg + zoff + ny0));
             xz = __ldg(reinterpret_cast<const float2 *>(xg + zoff + zn + n0));
         }
-        const float *cfr = CF + (zo - zbeg) * G::CFS;
+        const float *cfr = CF + (zo - it.zo0) * G::CFS;
         if (emit && zu) {
             float fzc[KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
@@ -1305,7 +1317,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
             timed_out = true;
             return false;
         }
-        issue(zi + PREF, (S + PREF) % NS);
+        issue(zi + PF, (S + PF) % NS);
         ++zi;
         if (!emit) return true;
         if (xu) {
@@ -1367,7 +1379,7 @@ __global__ void __launch_bounds__(NT, 2) k_curvature(KArgs a) {
     if (timed_out) {
         // leave only after every copy in flight has landed (bounded waits)
         if (tid == 0) {
-            for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
+            for (int z = zi; z < min(zi + PF, zend + PF); ++z) {
                 if (z < glo || z >= ghi) continue;
                 const int s = (z - zbeg) % NS;
                 if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
