@@ -349,10 +349,15 @@ def batch_extra(iters, stream):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps / 1e3
 
+    # z-chunk from the library's autotuner (timed on this GPU for these volumes)
+    zc, zc_ms = binding.autotune(probs, iters=10)
     with binding.BatchSolver(probs) as bs:
         bs.iterate_async(3)
+        t_default = timed(lambda: bs.iterate_async(1), 20)
+    with binding.BatchSolver(probs, zchunk=zc) as bs:
+        bs.iterate_async(3)
         t_batch = timed(lambda: bs.iterate_async(1), 20)
-        with binding.BatchSolver(probs) as b2:
+        with binding.BatchSolver(probs, zchunk=zc) as b2:
             tr = b2.iterate(iters)
     fstar = tr[:, -1]
     settle = float(np.max((tr[:, int(0.9 * iters)] - tr[:, -1]) / np.abs(fstar)))
@@ -368,12 +373,13 @@ def batch_extra(iters, stream):
     # reaches its target drops out of every later launch
     t_stop, k_stop = None, None
     if ok:
-        with binding.BatchSolver(probs) as bs:
+        with binding.BatchSolver(probs, zchunk=zc) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
             t_stop = timed(lambda: bs.iterate_async(max(k) + 1), 1)
             k_stop = [int(v) for v in bs.stopped()]
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,
+            "autotuned_zchunk": zc, "lockstep_iterations_per_s_default_zchunk": 1.0 / t_default,
             "sequential_iterations_per_s": 1.0 / sum(t_seq),
             "fstar_iters": iters, "fstar_settle_rel": settle,
             "iters_to_gap": k,
@@ -402,6 +408,18 @@ def mixed_extra(fstar_iters, stream, flush, steps):
                      "kernel_ms_per_iteration": {k: v[0] for k, v in prof.items()}}
     fstar, settle = fstar_of(prob, fstar_iters)
     out.update({"fstar": fstar, "fstar_iters": fstar_iters, "fstar_settle_rel": settle})
+    # BF16 directions with precision escalation (switch to FP32 directions once f decreases by
+    # <= 1e-9 |f| per iteration): iterations of the escalating run to each gap level
+    with binding.Solver.from_problem(prob, slabs=None, precision=binding.BF16_DIRECTIONS) as s:
+        s.set_escalation(1e-9)
+        tr = s.iterate(400)
+        at = s.escalated()
+    esc = {"tol": 1e-9, "escalated_at_iteration": at}
+    for name, den in (("rel_1e-7", abs(fstar)), ("normalized_1e-6", tr[0] - fstar)):
+        lvl = 1e-7 if name.startswith("rel") else 1e-6
+        hit = np.nonzero((tr - fstar) / den <= lvl)[0]
+        esc[name + "_iterations"] = int(hit[0]) if hit.size else None
+    out["bf16_escalating"] = esc
     for name, prec in (("fp32", binding.FP32), ("bf16_directions", binding.BF16_DIRECTIONS)):
         k, t, g = time_to_gap(prob, None, fstar, 3000, stream, prec)
         kn, tn, gn = time_to_gap(prob, None, fstar, 3000, stream, prec, normalized=True)

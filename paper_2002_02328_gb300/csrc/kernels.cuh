@@ -1319,7 +1319,13 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::PF == 1 ? 3 :
         }
         issue(zi + PF, (S + PF) % NS);
         ++zi;
-        if (!emit) return true;
+        if (!emit) {
+            // a zero-filled slot is plain shared-memory stores: with one slice of
+            // prefetch the next step may read it, so order the fill by a barrier
+            // (TMA-filled slots are ordered by their mbarrier)
+            if (PF < 2 && (zi + PF - 1 < glo || zi + PF - 1 >= ghi)) __syncthreads();
+            return true;
+        }
         if (xu) {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);

@@ -148,3 +148,27 @@ def test_full_size_slab_sweeps_descend(cuda_lib, full_slabs):
     assert nc == 3
     assert np.all(np.diff(tr) <= 1e-6 * np.abs(tr[1:]))
     assert tr[-1] < 0.9 * tr[0]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("zchunk", [4, 5])
+def test_slab_form_with_short_chunks_matches_oracle(cuda_lib, prec, zchunk):
+    """Short z-chunks make work items start and end at every slab edge, where
+    slices outside the slab are zero-filled in the curvature ring."""
+    bounds = [0, 4, 11, 13, 20]
+    p = synth.tiny_problem(shape=(20, 36, 40), psf_shape=(7, 7, 7), seed=9, n_ellipsoids=8, sxy=(0.5, 2.0), sz=1.0,
+                           slabs=bounds)
+    op = oracle.OracleProblem.from_synth(p)
+    _, order = _colour_major(bounds, 7)
+    oracle.set_threads(oracle.max_threads())
+    xr, _, fr = oracle.run(op, p.y, p.y, 8, bounds=bounds, order=order)
+    with cuda_lib.Solver.from_problem(p, precision=prec, zchunk=zchunk) as s:
+        tr = s.iterate(8)
+        x = s.get_x().cpu().numpy()
+    assert np.all(np.isfinite(tr)) and np.all(np.isfinite(x))
+    if prec == 0:
+        assert _rel(x, xr) <= 2e-5
+        assert np.max(np.abs(tr - fr) / np.abs(fr)) <= 1e-5
+    else:                                  # BF16 directions: descent and closeness to the FP32 oracle path
+        assert np.all(np.diff(tr) <= 1e-6 * np.abs(tr[1:]))
+        assert np.max(np.abs(tr - fr) / np.abs(fr)) <= 1e-3
