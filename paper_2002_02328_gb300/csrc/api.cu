@@ -57,6 +57,10 @@ struct VolState {
 struct bd3mg_ctx {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;  // second capture stream: the objective branch of a block-form sweep
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    double *partials_obj = nullptr;     // reduction slots and ticket of the objective branch
+    unsigned int *ticket_obj = nullptr;
     bd3mg_allocator alloc{};
     bool has_alloc = false;
     std::vector<std::pair<void *, size_t>> owned;
@@ -307,6 +311,10 @@ bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
 
 bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
     KArgs a = make_args(c, L, mode, vols);
+    if (s == c->aux_stream) {             // the objective branch reduces into its own slots
+        a.partials = c->partials_obj;
+        a.ticket = c->ticket_obj;
+    }
     bd3mg_status st = prof_mark(c, s, (mode & M_STORE_R) ? BD3MG_K_RESIDUAL : BD3MG_K_OBJECTIVE);
     if (st) return st;
     c->ks->residual(a, s);
@@ -349,17 +357,43 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
 }
 
 // One iteration = one sweep over every volume's slabs, colour by colour.
+// True when some volume can stop (a step tolerance or an objective target is set).
+bool stopping_enabled(const bd3mg_ctx *c) {
+    if (c->tol2 > 0.0) return true;
+    for (double t : c->f_target)
+        if (t != -INFINITY) return true;
+    return false;
+}
+
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
     if (!c->any_slabs) {
         if ((st = run_residual(c, s, c->L_res[0], M_STORE_R | M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
+        for (int col = 0; col < c->ncolours; ++col) {
+            if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
+            if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
+            if ((st = run_update(c, s, col))) return st;
+        }
+        return BD3MG_OK;
+    }
+    // Block form.  The objective pass that opens the sweep reads x and y and
+    // only has to finish before the first update writes x; without stopping
+    // (whose flag it sets for the later launches) it runs as a parallel branch
+    // of the graph beside colour 0's residual, gradient and curvature.
+    const bool branch = !c->prof_on && s == c->cap_stream && !stopping_enabled(c);
+    if (branch) {
+        CK(cudaEventRecord(c->ev_fork, s));
+        CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+        if ((st = run_residual(c, c->aux_stream, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
+        CK(cudaEventRecord(c->ev_join, c->aux_stream));
     } else {
         if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
-        if (c->any_slabs && (st = run_residual(c, s, c->L_res[col], M_STORE_R | M_ITER))) return st;
+        if ((st = run_residual(c, s, c->L_res[col], M_STORE_R | M_ITER))) return st;
         if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
+        if (branch && col == 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
         if ((st = run_update(c, s, col))) return st;
     }
     return BD3MG_OK;
@@ -595,6 +629,9 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
 
     cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (ce != cudaSuccess) return fail(c, BD3MG_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(ce));
 
     // device allocations
@@ -614,7 +651,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
     AL(c->partials, (size_t)c->max_items * 10);    // up to 10 partial sums per item
-    AL(c->ticket, 1); AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
+    AL(c->ticket, 1); AL(c->ticket_obj, 1); AL(c->partials_obj, (size_t)std::max(1, c->L_obj.nitems) * 3);
+    AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
     AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1); AL(c->run, nvol);
 #undef AL
 
@@ -654,6 +692,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpyAsync(c->seg_lists, c->seg_lists_h.data(), sizeof(int) * c->seg_lists_h.size(),
                            cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->ticket, 0, 4, c->stream));
+    CK(cudaMemsetAsync(c->ticket_obj, 0, 4, c->stream));
     CK(cudaMemsetAsync(c->u, 0, 16 * nseg, c->stream));
     CK(cudaMemsetAsync(c->info, 0, 64 * nseg, c->stream));
     CK(cudaMemsetAsync(c->counter, 0, 4, c->stream));
@@ -788,6 +827,9 @@ void bd3mg_destroy(bd3mg_ctx *c) {
     }
     cudaStreamSynchronize(c->stream);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -882,7 +924,9 @@ bd3mg_status bd3mg_set_stopping(bd3mg_ctx *c, double tol, const double *f_target
     c->tol2 = tol * tol;
     bd3mg_status st;
     if ((st = upload_shared(c))) return st;
-    return reset_run(c, -1);
+    if ((st = reset_run(c, -1))) return st;
+    // the block-form graph runs the objective as a parallel branch only without stopping
+    return c->any_slabs ? capture_graph(c) : BD3MG_OK;
 }
 
 bd3mg_status bd3mg_stopped(bd3mg_ctx *c, int *sweeps) {
