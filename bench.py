@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=1)
     ap.add_argument("--ws-train-seconds", type=float, default=60.0, help="warm start: training time budget")
     ap.add_argument("--no-warm-start", action="store_true")
+    ap.add_argument("--profile-case", choices=["plain512", "unet-train"], default=None,
+                    help="run a small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
 
@@ -703,8 +705,45 @@ def ours(args):
     return 0
 
 
+def profile_case(name):
+    """Small fixed workloads for ncu captures (no timing contract).
+    plain512: plain FP32 context on a 512x512x128 volume (uniform random y, PSF 9x9x7 with the
+      0.5 -> 3.0 ramp), 3 iterations, 20 more, then one per-launch profiled iteration.
+    unet-train: the U-Net (16/32/64/128) on 8 crops of 128x128x48, 3 training steps of batch 4."""
+    import torch
+    from paper_2002_02328_gb300 import binding, synth
+    torch.cuda.set_device(0)
+    if name == "plain512":
+        shape = (128, 512, 512)
+        fx, fy, fz = synth.gaussian_factors(shape[0], 9, 9, 7, 0.5, 3.0, 1.0)
+        y = torch.from_numpy(np.random.default_rng(0).uniform(0, 1, size=shape).astype(np.float32)).cuda()
+        with binding.Solver(shape, synth.dense_psf(fx, fy, fz), y) as s:
+            s.iterate(3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.iterate(20)
+            torch.cuda.synchronize()
+            print("iterations/s", 20 / (time.perf_counter() - t0))
+            print(s.profile_iteration())
+    else:
+        from paper_2002_02328_gb300 import unet_binding as ub, warmstart as ws
+        widths = (16, 32, 64, 128)
+        ys, ramps = ws.make_crops(8, (48, 128, 128), seed=0, source_shape=None)
+        with ub.UNet(widths, 2) as net:
+            net.set_params(ub.he_init(widths, 2, 0))
+            for _ in range(3):
+                sel = [0, 1, 2, 3]
+                inp = torch.stack([ws.net_input(ys[i], ramps[i]) for i in sel])
+                net.train_step(inp, ys[sel], ys[sel].clone())
+            torch.cuda.synchronize()
+        print("ok")
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return reference_arm(args)
     return ours(args)
