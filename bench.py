@@ -540,6 +540,23 @@ def e2e_run(prob, n_iter, stream):
     return n_iter / dt, h2d / n_iter, d2h / n_iter, dt
 
 
+def max_over_ranks(ms_per_step: float, world: int, device) -> float:
+    """The slowest rank's step time (all-reduce MAX over the process group); unchanged on one rank."""
+    if world <= 1:
+        return ms_per_step
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_per_step], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, ms_per_step: float) -> float:
+    """Whole-job sweeps per second: every rank solves its own replica (weak scaling, no
+    collective on the data path), all ranks' sweeps divided by the slowest rank's time."""
+    return world * 1e3 / ms_per_step
+
+
 def ours(args):
     import torch
     args.profile_iters = max(1, args.profile_iters)
@@ -615,12 +632,7 @@ def ours(args):
                 prof_mixed[k][1] += cnt
     clocks = sampler.stop() if sampler is not None else None
 
-    ms_per_step = ms_total / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_per_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_per_step = max_over_ranks(ms_total / args.steps, world, "cuda")
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -628,7 +640,7 @@ def ours(args):
             dist.destroy_process_group()
         return 0
 
-    value = world * 1e3 / ms_per_step
+    value = job_rate(world, ms_per_step)
     plain_rate = 1e3 / (ms_plain / max(10, args.steps // 2))
 
     # roofline of the dominant kernel (largest device time per sweep)
