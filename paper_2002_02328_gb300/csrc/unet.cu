@@ -109,7 +109,9 @@ cudaError_t prepare_kernels() {
     return res;
 }
 
-int kc_of(int K) { return K >= 64 ? 64 : K; }
+// K elements per block: 64 (a part of one tap) when K >= 64, else as many whole
+// taps of K channels as fit in 64 (never more than T taps)
+int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
 // Launch one implicit GEMM (see GemmArgs).  UPFWD launches 8 grid rows (taps).
 cudaError_t gemm(cudaStream_t s, int mode, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt,
@@ -121,7 +123,7 @@ cudaError_t gemm(cudaStream_t s, int mode, int B, int D, int H, int W, const bf1
     a.mode = mode;
     a.B = B; a.D = D; a.H = H; a.W = W;
     a.M = (long long)B * D * H * W;
-    a.A = A; a.lda = lda; a.K = K; a.KC = kc_of(K);
+    a.A = A; a.lda = lda; a.K = K; a.KC = kc_of(K, T);
     a.Wt = Wt; a.N = N; a.T = T;
     a.bias = bias; a.relu = relu; a.mask = mask; a.ldm = ldm;
     a.out = out; a.ldo = ldo; a.status = status;

@@ -49,7 +49,7 @@ struct GemmArgs {
     const bf16 *A;               // source activations, rows of lda elements
     int lda;
     int K;                       // channels per tap (multiple of 16)
-    int KC;                      // channels per K block (16, 32 or 64; divides K)
+    int KC;                      // K elements per block: 64 when K >= 64 (divides K), else a multiple of K
     const bf16 *Wt;              // [T][N][K]
     int N;                       // output channels (multiple of 16, <= 256)
     int T;                       // taps reduced in this launch (CONV3 27, UPBWD 8, UPFWD 1)
@@ -121,23 +121,36 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
         bb = (int)(t2 / a.D);
         zb = (int)(t2 - (long long)bb * a.D);
     }
-    const int kpt = a.K / KC;                      // K blocks per tap
-    const int nk = a.T * kpt;
-    const int cpr = KC / 8;                        // 16-byte chunks per row of a block
+    // K runs over (tap, channel) pairs flattened as k = t * K + c.  With K >= KC a
+    // block is part of one tap (K / KC blocks per tap); with K < KC a block spans
+    // KC / K whole taps (layers with 16 or 32 input channels); chunks past the
+    // last tap are zero.
+    const int tpb = KC > a.K ? KC / a.K : 1;       // taps per block
+    const int kpt = KC > a.K ? 1 : a.K / KC;       // blocks per tap
+    const int nk = KC > a.K ? (a.T + tpb - 1) / tpb : a.T * kpt;
+    const int cpt = (KC > a.K ? a.K : KC) / 8;     // 16-byte chunks per tap within a block
 
     auto load_block = [&](int kb, int slot) {
         uint8_t *As = sm + slot * stage_bytes;
         uint8_t *Bs = As + a_bytes;
-        const int t = kb / kpt, c0 = (kb - t * kpt) * KC;
-        const int tw = a.mode == G_UPFWD ? tap_y : t;
-        long long src = row_ok ? gather_src(a, v, bb, zb, yb, xb, t) : -1;
-        const bf16 *ap = src >= 0 ? a.A + src * a.lda + c0 : a.A;
-        const uint32_t nb = src >= 0 ? 16u : 0u;
-        for (int kg = 0; kg < cpr; ++kg) umma::cp_async16(As + kg * (GM * 16) + tid * 16, ap + (src >= 0 ? kg * 8 : 0), nb);
-        const bf16 *wp = a.Wt + (long long)tw * N * a.K + c0;
-        for (int q = tid; q < N * cpr; q += GT) {
-            const int n = q / cpr, kg = q - n * cpr;
-            umma::cp_async16(Bs + kg * (N * 16) + n * 16, wp + (long long)n * a.K + kg * 8, 16u);
+        const int t0 = KC > a.K ? kb * tpb : kb / kpt;
+        const int c0 = KC > a.K ? 0 : (kb - t0 * kpt) * KC;
+        for (int j = 0; j < tpb; ++j) {
+            const int t = t0 + j;
+            const bool tv = t < a.T;
+            const long long src = (row_ok && tv) ? gather_src(a, v, bb, zb, yb, xb, t) : -1;
+            const bf16 *ap = src >= 0 ? a.A + src * a.lda + c0 : a.A;
+            const uint32_t nb = src >= 0 ? 16u : 0u;
+            for (int kg = 0; kg < cpt; ++kg)
+                umma::cp_async16(As + (j * cpt + kg) * (GM * 16) + tid * 16, ap + (src >= 0 ? kg * 8 : 0), nb);
+        }
+        for (int q = tid; q < N * tpb * cpt; q += GT) {
+            const int n = q / (tpb * cpt), kq = q - n * (tpb * cpt);
+            const int j = kq / cpt, kg = kq - j * cpt, t = t0 + j;
+            const int tw = a.mode == G_UPFWD ? tap_y : t;
+            const bool tv = t < a.T;
+            const bf16 *wp = tv ? a.Wt + ((long long)tw * N + n) * a.K + c0 + kg * 8 : a.Wt;
+            umma::cp_async16(Bs + kq * (N * 16) + n * 16, wp, tv ? 16u : 0u);
         }
     };
 
