@@ -45,6 +45,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
 
+// The same with both operands MN-major (A stored M-contiguous, B N-contiguous):
+// element (r, k) of an R x K tile at (r / 8) * SBO + (k / 8) * LBO + (k % 8) * 16
+// + (r % 8) * 2, i.e. each 16-byte row of a core matrix holds 8 consecutive
+// rows of the operand for one k.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 15) | (1u << 16);
+}
+
 // D[tmem] (+)= A[desc] * B[desc]^T, issued by one thread.
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {

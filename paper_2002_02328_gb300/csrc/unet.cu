@@ -96,7 +96,7 @@ int L_dec(const bd3mg_unet *n, int l, int b) { return L_up(n, l) + 1 + b; }
 int L_head(const bd3mg_unet *n) { return (int)n->layers.size() - 1; }
 
 size_t gemm_smem(int KC, int N) { return (size_t)STAGES * (GM * KC * 2 + (size_t)N * KC * 2) + STAGES * 8 + 16; }
-size_t wgrad_smem(int Cin) { return 2 * ((size_t)GM * KV * 2 + (size_t)Cin * KV * 2) + 2 * 8 + 16; }
+size_t wgrad_smem(int Cin) { return WSTAGES * ((size_t)GM * KV * 2 + (size_t)Cin * KV * 2) + WSTAGES * 8 + 16; }
 
 cudaError_t prepare_kernels() {
     static bool done = false;

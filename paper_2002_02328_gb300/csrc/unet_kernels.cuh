@@ -15,9 +15,10 @@
 //            scattered to the fine grid) and UPBWD (its input gradient:
 //            8 taps gathered from the fine grid).
 //   k_wgrad  weight gradients: rows = output channels (padded to 128), columns
-//            = input channels, K = voxels; both operands are transposed while
-//            they are staged (channels-last -> K-major), per-split FP32
-//            partials are summed in a fixed order by k_split_sum.
+//            = input channels, K = voxels; both operands are read MN-major
+//            (channels contiguous, as stored), so 16-byte cp.async copies fill
+//            the tiles without a transpose; per-split FP32 partials are summed
+//            in a fixed order by k_split_sum.
 // Everything else (pooling, head, loss, bias sums, Adam, weight packing) is
 // plain CUDA-core code.
 #pragma once
@@ -37,6 +38,7 @@ constexpr int GT = 128;          // threads of the GEMM kernels (4 warps: one pe
 constexpr int GM = 128;          // rows (M) per CTA
 constexpr int STAGES = 3;        // shared-memory pipeline depth of k_gemm
 constexpr int KV = 64;           // voxels (K) per k_wgrad block
+constexpr int WSTAGES = 3;       // shared-memory pipeline depth of k_wgrad
 
 enum GatherMode { G_CONV3 = 0, G_UPFWD = 1, G_UPBWD = 2 };
 
@@ -263,18 +265,19 @@ struct WgradArgs {
 __global__ void __launch_bounds__(GT, 1) k_wgrad(WgradArgs a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int Cin = a.Cin, Cout = a.Cout;
+    // operand tiles MN-major: the 16-byte chunk (8 channels) of voxel k lands at
+    // (channel / 8) * 128 + (k / 8) * LBO + (k % 8) * 16, with LBO = rows * 16
     const uint32_t a_bytes = GM * KV * 2, b_bytes = (uint32_t)Cin * KV * 2, stage = a_bytes + b_bytes;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * stage);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 2);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + WSTAGES * stage);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + WSTAGES);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.y, split = blockIdx.x;
     const uint32_t ncols = Cin <= 32 ? 32u : (Cin <= 64 ? 64u : (Cin <= 128 ? 128u : 256u));
 
-    // rows >= Cout of both A stages stay zero for the whole kernel
-    for (int i = tid; i < (int)(2 * stage / 16); i += GT) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    // rows >= Cout of every A stage stay zero for the whole kernel
+    for (int i = tid; i < (int)(WSTAGES * stage / 16); i += GT) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+        for (int s = 0; s < WSTAGES; ++s) mbar_init(bar + s, 1);
         fence_barrier_init();
     }
     if (warp == 0) umma::tmem_alloc(tslot, ncols);
@@ -288,59 +291,65 @@ __global__ void __launch_bounds__(GT, 1) k_wgrad(WgradArgs a) {
     const int nk = ve > vb ? (int)((ve - vb + KV - 1) / KV) : 0;
     const int az = t >> 2, ay = (t >> 1) & 1, ax = t & 1;
     const int dz3 = t / 9 - 1, dy3 = (t / 3) % 3 - 1, dx3 = t % 3 - 1;
-    const uint32_t idesc = umma::idesc_bf16(GM, Cin);
-    bool ok = true;
+    const uint32_t idesc = umma::idesc_bf16_mn(GM, Cin);
+    const int cga = Cout / 8, cgb = Cin / 8;
 
+    // thread -> voxel k = tid % KV of the block and every (GT / KV)-th channel chunk:
+    // the voxel's source rows are found once per block
+    static_assert(GT % KV == 0, "whole voxel columns per thread group");
+    const int kv = tid % KV, cg0 = tid / KV;
+    auto load_block = [&](int kb, int slot) {
+        uint8_t *As = sm + slot * stage, *Bs = As + a_bytes;
+        const long long v = vb + (long long)kb * KV + kv;
+        const bf16 *ra = a.dz, *rb = a.x;
+        bool va = false, vbx = false;
+        if (v < ve) {
+            long long t1 = v / a.W;
+            const int x = (int)(v - t1 * a.W);
+            long long t2 = t1 / a.H;
+            const int y = (int)(t1 - t2 * a.H);
+            const int b = (int)(t2 / a.D);
+            const int z = (int)(t2 - (long long)b * a.D);
+            long long r = v;
+            if (a.mode == W_UP)
+                r = (((long long)b * 2 * a.D + 2 * z + az) * (2LL * a.H) + 2 * y + ay) * (2LL * a.W) + 2 * x + ax;
+            ra = a.dz + r * a.lddz;
+            va = true;
+            long long rx = v;
+            bool in = true;
+            if (a.mode == W_CONV3) {
+                const int zz = z + dz3, yy = y + dy3, xx = x + dx3;
+                in = zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+                rx = v + ((long long)dz3 * a.H + dy3) * a.W + dx3;
+            }
+            if (in) {
+                rb = a.x + rx * a.ldx;
+                vbx = true;
+            }
+        }
+        uint8_t *da = As + (kv >> 3) * (GM * 16) + (kv & 7) * 16;
+        uint8_t *db = Bs + (kv >> 3) * (Cin * 16) + (kv & 7) * 16;
+        for (int cg = cg0; cg < cga + cgb; cg += GT / KV) {
+            if (cg < cga) umma::cp_async16(da + cg * 128, va ? ra + cg * 8 : a.dz, va ? 16u : 0u);
+            else umma::cp_async16(db + (cg - cga) * 128, vbx ? rb + (cg - cga) * 8 : a.x, vbx ? 16u : 0u);
+        }
+    };
+
+    bool ok = true;
+#pragma unroll 1
+    for (int s = 0; s < WSTAGES - 1; ++s) {
+        if (s < nk) load_block(s, s);
+        umma::cp_async_commit();
+    }
 #pragma unroll 1
     for (int kb = 0; kb < nk; ++kb) {
-        const int slot = kb & 1;
-        uint8_t *As = sm + slot * stage, *Bs = As + a_bytes;
-        if (kb >= 2) ok = mbar_wait(bar + slot, (uint32_t)((kb / 2 - 1) & 1)) && ok;
-        // stage: voxel k of the block, 8-channel chunk cg; element (row, k) at
-        // (k/8)*LBO + (row/8)*128 + (row%8)*16 + (k%8)*2
-        const int cga = Cout / 8, cgb = Cin / 8;
-        for (int q = tid; q < KV * (cga + cgb); q += GT) {
-            const int k = q % KV, cg = q / KV;
-            const long long v = vb + (long long)kb * KV + k;
-            uint4 val = make_uint4(0, 0, 0, 0);
-            uint8_t *base;
-            uint32_t lbo;
-            int row0;
-            if (v < ve) {
-                long long t1 = v / a.W;
-                const int x = (int)(v - t1 * a.W);
-                long long t2 = t1 / a.H;
-                const int y = (int)(t1 - t2 * a.H);
-                const int b = (int)(t2 / a.D);
-                const int z = (int)(t2 - (long long)b * a.D);
-                if (cg < cga) {
-                    long long r = v;
-                    if (a.mode == W_UP)
-                        r = (((long long)b * 2 * a.D + 2 * z + az) * (2LL * a.H) + 2 * y + ay) * (2LL * a.W) + 2 * x + ax;
-                    val = *reinterpret_cast<const uint4 *>(a.dz + r * a.lddz + cg * 8);
-                } else {
-                    long long r = v;
-                    bool in = true;
-                    if (a.mode == W_CONV3) {
-                        const int zz = z + dz3, yy = y + dy3, xx = x + dx3;
-                        in = zz >= 0 && zz < a.D && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-                        r = v + ((long long)dz3 * a.H + dy3) * a.W + dx3;
-                    }
-                    if (in) val = *reinterpret_cast<const uint4 *>(a.x + r * a.ldx + (cg - cga) * 8);
-                }
-            }
-            if (cg < cga) { base = As; lbo = GM * 16; row0 = cg * 8; }
-            else { base = Bs; lbo = (uint32_t)Cin * 16; row0 = (cg - cga) * 8; }
-            const uint16_t *h = reinterpret_cast<const uint16_t *>(&val);
-            uint8_t *p = base + (k >> 3) * lbo + (row0 >> 3) * 128 + (k & 7) * 2;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) *reinterpret_cast<uint16_t *>(p + j * 16) = h[j];
-        }
+        const int slot = kb % WSTAGES;
+        umma::cp_async_wait<WSTAGES - 2>();
         umma::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
             umma::fence_after_sync();
-            const uint32_t as = umma::smem_addr(As), bs = umma::smem_addr(Bs);
+            const uint32_t as = umma::smem_addr(sm + slot * stage), bs = as + a_bytes;
             for (int kk = 0; kk < KV / 16; ++kk) {
                 const uint64_t ad = umma::desc(as + kk * 2 * (GM * 16), GM * 16, 128);
                 const uint64_t bd = umma::desc(bs + kk * 2 * (Cin * 16), Cin * 16, 128);
@@ -348,8 +357,16 @@ __global__ void __launch_bounds__(GT, 1) k_wgrad(WgradArgs a) {
             }
             umma::commit(bar + slot);
         }
+        const int nxt = kb + WSTAGES - 1;
+        if (nxt < nk) {
+            const int ns = nxt % WSTAGES;
+            if (nxt >= WSTAGES) ok = mbar_wait(bar + ns, (uint32_t)((nxt / WSTAGES - 1) & 1)) && ok;
+            load_block(nxt, ns);
+        }
+        umma::cp_async_commit();
     }
-    if (nk > 0) ok = mbar_wait(bar + ((nk - 1) & 1), (uint32_t)(((nk - 1) / 2) & 1)) && ok;
+    umma::cp_async_wait<0>();
+    if (nk > 0) ok = mbar_wait(bar + (nk - 1) % WSTAGES, (uint32_t)(((nk - 1) / WSTAGES) & 1)) && ok;
     if (!ok && lane == 0) atomicOr(a.status, ST_MMA_TIMEOUT);
     umma::fence_after_sync();
     const int co = warp * 32 + lane;
