@@ -377,7 +377,8 @@ def batch_extra(iters, stream):
     if ok:
         with binding.BatchSolver(probs, zchunk=zc) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
-            t_stop = timed(lambda: bs.iterate_async(max(k) + 1), 1)
+            # the synchronous call drops stopped volumes from the work lists between chunks
+            t_stop = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
             k_stop = [int(v) for v in bs.stopped()]
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,

@@ -419,7 +419,7 @@ class BatchSolver:
         ys, xs = [], []
         precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * self.nvol
         for v, p in enumerate(problems):
-            prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, None, precs[v], 1e-12,
+            prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precs[v], 1e-12,
                                  zchunk)
             arr[v] = prm
             keep.append(k)

@@ -59,6 +59,9 @@ struct bd3mg_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaStream_t aux_stream = nullptr;  // second capture stream: the objective branch of a block-form sweep
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    std::vector<char> plan_active;      // volumes the per-colour work lists cover (stopped ones are dropped)
+    std::vector<int> colour_zc;         // z-chunk of each per-colour launch, fixed at creation
+    size_t base_items = 0, base_beg = 0, base_slot = 0;   // sizes of the lists before the per-colour launches
     double *partials_obj = nullptr;     // reduction slots and ticket of the objective branch
     unsigned int *ticket_obj = nullptr;
     bd3mg_allocator alloc{};
@@ -235,14 +238,16 @@ enum SlotMode { SLOTS_NONE, SLOTS_PER_VOLUME, SLOTS_PER_SEGMENT };
 // One launch over the given segments, each with output range range(seg).
 // Segments must be grouped by volume when slots are per volume.
 template <typename F>
-Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode slots, int kind) {
+Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode slots, int kind, int *zc_io = nullptr) {
     std::vector<std::array<int, 3>> ranges;
     for (int s : segs) {
         int lo, hi;
         range(s, &lo, &hi);
         ranges.push_back({lo, hi, ntiles_of(c->V[c->segs_h[s].vol], tile_y(kind))});
     }
-    const int zc = choose_zc(c, ranges, kind);
+    // zc_io > 0: reuse that chunk (a re-plan keeps every item, and so every sum, as it was)
+    const int zc = (zc_io && *zc_io > 0) ? *zc_io : choose_zc(c, ranges, kind);
+    if (zc_io) *zc_io = zc;
     Launch L;
     L.item_off = (int)c->items_h.size();
     L.beg_off = (int)c->slot_beg_h.size();
@@ -310,6 +315,7 @@ bd3mg_status prof_mark(bd3mg_ctx *c, cudaStream_t s, int cls) {
 }
 
 bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
+    if (L.nitems == 0) return BD3MG_OK;
     KArgs a = make_args(c, L, mode, vols);
     if (s == c->aux_stream) {             // the objective branch reduces into its own slots
         a.partials = c->partials_obj;
@@ -322,6 +328,7 @@ bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
 }
 
 bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode, const VolDev *vols = nullptr) {
+    if (L.nitems == 0) return BD3MG_OK;
     KArgs a = make_args(c, L, mode, vols);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
     if (st) return st;
@@ -331,6 +338,7 @@ bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
 }
 
 bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
+    if (L.nitems == 0) return BD3MG_OK;
     KArgs a = make_args(c, L, M_ITER, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
@@ -418,12 +426,20 @@ bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
 }
 
 // Clear the stopping state of volume vol (all volumes when vol < 0), keeping the targets.
+bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active);
+
 bd3mg_status reset_run(bd3mg_ctx *c, int vol) {
     std::vector<VolRun> h(c->nvol);
     for (int v = 0; v < c->nvol; ++v) h[v] = VolRun{0.0, 0.0, c->f_target[v], 0, 0};
     const int v0 = vol < 0 ? 0 : vol, cnt = vol < 0 ? c->nvol : 1;
     CK(cudaMemcpyAsync(c->run + v0, h.data() + v0, sizeof(VolRun) * cnt, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    // volumes that run again must be back in the work lists
+    if (!c->plan_active.empty() && c->exec) {
+        std::vector<char> act = c->plan_active;
+        for (int v = v0; v < v0 + cnt; ++v) act[v] = 1;
+        return replan(c, act);
+    }
     return BD3MG_OK;
 }
 
@@ -506,6 +522,74 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     c->bf = false;
     if ((st = upload_descriptors(c))) return st;
     c->esc_at = c->iterations;
+    return capture_graph(c);
+}
+
+// Per-colour launches (residual of the slab form, gradient, curvature, update
+// lists) over the volumes marked active; the plain form's residual launch, which
+// also evaluates the objective and writes the trace, always covers every volume.
+void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
+    c->items_h.resize(c->base_items);
+    c->slot_beg_h.resize(c->base_beg);
+    c->slot_id_h.resize(c->base_slot);
+    c->seg_lists_h.clear();
+    c->seg_list_off.assign(1, 0);
+    c->L_res.clear();
+    c->L_grad.clear();
+    c->L_curv.clear();
+    const int RZk = c->ks->RZ;
+    const int Lk = std::max(RZk, 1);
+    auto whole = [&](int s, int *lo, int *hi) { *lo = 0; *hi = c->segs_h[s].z1; };
+    auto nzof = [&](int s) { return c->V[c->segs_h[s].vol].p.nz; };
+    if (c->colour_zc.empty()) c->colour_zc.assign(3 * (size_t)c->ncolours, 0);
+    for (int col = 0; col < c->ncolours; ++col) {
+        std::vector<int> segs, all;
+        for (int v = 0; v < c->nvol; ++v)
+            for (size_t s = 0; s < c->V[v].colour.size(); ++s)
+                if (c->V[v].colour[s] == col) {
+                    all.push_back(c->V[v].seg0 + (int)s);
+                    if (active[v]) segs.push_back(c->V[v].seg0 + (int)s);
+                }
+        int *zc = c->colour_zc.data() + 3 * col;
+        if (!c->any_slabs)
+            c->L_res.push_back(make_launch(c, all, whole, SLOTS_PER_VOLUME, 0, zc));
+        else
+            c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+                *lo = std::max(0, c->segs_h[s].z0 - RZk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
+                SLOTS_NONE, 0, zc));
+        c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1, zc + 1));
+        c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+            *lo = std::max(0, c->segs_h[s].z0 - Lk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
+            SLOTS_PER_SEGMENT, 2, zc + 2));
+        for (int s : segs) c->seg_lists_h.push_back(s);
+        c->seg_list_off.push_back((int)c->seg_lists_h.size());
+    }
+    c->plan_active = active;
+}
+
+// Copy the work lists to the device (the device arrays were sized for every volume).
+bd3mg_status upload_work_lists(bd3mg_ctx *c) {
+    CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->slot_beg, c->slot_beg_h.data(), sizeof(int) * c->slot_beg_h.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    if (!c->slot_id_h.empty())
+        CK(cudaMemcpyAsync(c->slot_id, c->slot_id_h.data(), sizeof(int) * c->slot_id_h.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    if (!c->seg_lists_h.empty())
+        CK(cudaMemcpyAsync(c->seg_lists, c->seg_lists_h.data(), sizeof(int) * c->seg_lists_h.size(),
+                           cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));        // the host vectors may change before the next copy
+    return BD3MG_OK;
+}
+
+// Re-plan the per-colour launches for the given active set and re-capture the graph.
+bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active) {
+    if (active == c->plan_active) return BD3MG_OK;
+    build_colour_launches(c, active);
+    bd3mg_status st = upload_work_lists(c);
+    if (st) return st;
     return capture_graph(c);
 }
 
@@ -606,27 +690,10 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     c->L_obj = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
     c->L_res_full = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
     c->L_grad_full = make_launch(c, full, whole, SLOTS_NONE, 1);
-    c->seg_list_off.push_back(0);
-    for (int col = 0; col < c->ncolours; ++col) {
-        std::vector<int> segs;
-        for (int v = 0; v < nvol; ++v)
-            for (size_t s = 0; s < c->V[v].colour.size(); ++s)
-                if (c->V[v].colour[s] == col) segs.push_back(c->V[v].seg0 + (int)s);
-        auto nzof = [&](int s) { return c->V[c->segs_h[s].vol].p.nz; };
-        if (!c->any_slabs)
-            c->L_res.push_back(make_launch(c, segs, whole, SLOTS_PER_VOLUME, 0));
-        else
-            c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-                *lo = std::max(0, c->segs_h[s].z0 - RZk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
-                SLOTS_NONE, 0));
-        c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1));
-        c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = std::max(0, c->segs_h[s].z0 - Lk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
-            SLOTS_PER_SEGMENT, 2));
-        for (int s : segs) c->seg_lists_h.push_back(s);
-        c->seg_list_off.push_back((int)c->seg_lists_h.size());
-    }
+    c->base_items = c->items_h.size();
+    c->base_beg = c->slot_beg_h.size();
+    c->base_slot = c->slot_id_h.size();
+    build_colour_launches(c, std::vector<char>(nvol, 1));
 
     cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
@@ -878,30 +945,44 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     if ((st = ensure_trace(c, n + 1))) return st;
     CK(cudaMemsetAsync(c->counter, 0, sizeof(int), c->stream));
     const long long base = c->iterations;
-    if (c->bf && c->esc_tol > 0.0) {
-        // run in chunks, reading the objective trace between them; switch to FP32
-        // directions once some volume decreases by at most esc_tol relative
-        const int chunk = 4;
+    const bool compact = c->nvol > 1 && stopping_enabled(c);
+    if ((c->bf && c->esc_tol > 0.0) || compact) {
+        // run in chunks of 4 iterations, reading state between them:
+        //  - escalation: switch to FP32 directions once some volume decreases by
+        //    at most esc_tol relative;
+        //  - per-volume stopping in a batch: drop stopped volumes from the
+        //    gradient, curvature and update work lists (the objective pass keeps
+        //    every volume, so every trace stays complete)
+        const int chunk = (c->bf && c->esc_tol > 0.0) ? 4 : 8;
         std::vector<double> tr;
+        std::vector<VolRun> rh(c->nvol);
         int k = 0;
-        while (k < n && c->bf) {
+        while (k < n) {
             const int m = std::min(chunk, n - k);
             for (int j = 0; j < m; ++j) CK(cudaGraphLaunch(c->exec, c->stream));
             k += m;
             c->iterations = base + k;
-            tr.resize((size_t)c->nvol * k);       // f(x_0) .. f(x_{k-1}) of every volume
-            CK(cudaMemcpy2DAsync(tr.data(), sizeof(double) * k, c->trace, sizeof(double) * c->trace_cap,
-                                 sizeof(double) * k, c->nvol, cudaMemcpyDeviceToHost, c->stream));
-            if ((st = check_status(c))) return st;
-            bool slow = false;
-            for (int v = 0; v < c->nvol && !slow; ++v)
-                for (int j = std::max(1, k - m); j < k && !slow; ++j) {
-                    const double a0 = tr[(size_t)v * k + j - 1], a1 = tr[(size_t)v * k + j];
-                    slow = (a0 - a1) <= c->esc_tol * std::fabs(a1);
-                }
-            if (slow && (st = escalate_to_fp32(c))) return st;
+            if (c->bf && c->esc_tol > 0.0) {
+                tr.resize((size_t)c->nvol * k);       // f(x_0) .. f(x_{k-1}) of every volume
+                CK(cudaMemcpy2DAsync(tr.data(), sizeof(double) * k, c->trace, sizeof(double) * c->trace_cap,
+                                     sizeof(double) * k, c->nvol, cudaMemcpyDeviceToHost, c->stream));
+                if ((st = check_status(c))) return st;
+                bool slow = false;
+                for (int v = 0; v < c->nvol && !slow; ++v)
+                    for (int j = std::max(1, k - m); j < k && !slow; ++j) {
+                        const double a0 = tr[(size_t)v * k + j - 1], a1 = tr[(size_t)v * k + j];
+                        slow = (a0 - a1) <= c->esc_tol * std::fabs(a1);
+                    }
+                if (slow && (st = escalate_to_fp32(c))) return st;
+            }
+            if (compact && k < n) {
+                CK(cudaMemcpyAsync(rh.data(), c->run, sizeof(VolRun) * c->nvol, cudaMemcpyDeviceToHost, c->stream));
+                if ((st = check_status(c))) return st;
+                std::vector<char> act(c->nvol);
+                for (int v = 0; v < c->nvol; ++v) act[v] = rh[v].stopped ? 0 : 1;
+                if (act != c->plan_active && (st = replan(c, act))) return st;
+            }
         }
-        for (; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
     } else {
         for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
     }

@@ -386,6 +386,20 @@ __device__ bool publish_partials(const float (&acc)[NP], double *partials, unsig
     return is_last != 0;
 }
 
+// Item of a stopped volume: zero partials and the ticket only (all threads
+// call; true in the last CTA to finish).
+template <int NP>
+__device__ bool publish_zero(double *partials, unsigned int *ticket, int nitems) {
+    __shared__ int last_z;
+    if (threadIdx.x < NP) partials[(size_t)blockIdx.x * NP + threadIdx.x] = 0.0;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_z = atomicAdd(ticket, 1u) == (unsigned int)(nitems - 1);
+    __syncthreads();
+    if (last_z) __threadfence();
+    return last_z != 0;
+}
+
 // Fixed-order sum of the partials of items [ib, ie) into out[NP] (shared).
 template <int NP>
 __device__ void sum_slot(const double *partials, int ib, int ie, double *out) {
@@ -740,8 +754,12 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     // A stopped volume's item gets an empty range: no copies, no loop, zero
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
+    if (stopped) {
+        if (obj && publish_zero<3>(a.partials, a.ticket, a.nitems)) objective_finish(a);
+        return;
+    }
 
-    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int xlo = max(0, zbeg), xhi = min(nz, zend);
@@ -1217,9 +1235,13 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::PF == 1 ? 3 :
     // A stopped volume's item gets an empty range: no copies, no loop, zero
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
+    if (stopped) {
+        if (publish_zero<10>(a.partials, a.ticket, a.nitems)) curvature_finish(a);
+        return;
+    }
 
-    const int zbeg = it.zo0 - RZ, zend = stopped ? zbeg : it.zo1 + RZ;
-    stage_coeffs<G>(CF, V, it.zo0, stopped ? 0 : it.zo1 - it.zo0);   // rows of the output slices only
+    const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
+    stage_coeffs<G>(CF, V, it.zo0, it.zo1 - it.zo0);   // rows of the output slices only
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
     const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R], *md = &a.maps[sg.vol].m[TM_D_R];

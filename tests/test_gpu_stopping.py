@@ -110,3 +110,29 @@ def test_stopping_rejects_bad_arguments(cuda_lib):
     with pytest.raises(cuda_lib.Bd3mgError, match="NaN"):
         with cuda_lib.Solver.from_problem(prob, slabs=None) as s:
             s.set_stopping(0.0, float("nan"))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dropping_stopped_volumes_from_the_work_lists_changes_nothing(cuda_lib, precision):
+    """The synchronous iterate re-plans the gradient, curvature and update launches
+    without the volumes that stopped; the asynchronous one keeps launching their
+    (empty) items.  Both must leave every volume bit-identical."""
+    probs = _batch()
+    probs[2].slabs = synth.slab_bounds([5, 6, 5])       # one volume in the slab form
+    n = 24
+    with cuda_lib.BatchSolver(probs, precision=precision) as b:
+        free = b.iterate(n)
+    targets = np.array([free[0][5], free[1][11], free[2][17]])   # every volume stops, at different sweeps
+    runs = []
+    for sync in (True, False):
+        with cuda_lib.BatchSolver(probs, precision=precision) as b:
+            b.set_stopping(0.0, targets)
+            if sync:
+                b.iterate(n, trace=False)
+            else:
+                b.iterate_async(n)
+            runs.append(([b.get(v).cpu().numpy() for v in range(3)], b.stopped()))
+    np.testing.assert_array_equal(runs[0][1], [5, 11, 17])
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
+    for v in range(3):
+        np.testing.assert_array_equal(runs[0][0][v], runs[1][0][v])
