@@ -185,6 +185,9 @@ struct CurvRing {
     static constexpr int PF = bytes(1) <= 74 * 1024 ? 1 : 2;
     static constexpr int NS = C::KZ + PF;
     static constexpr size_t SMEM = bytes(PF);
+    // CTAs per SM the launch bounds ask registers for: four where the shared
+    // memory allows it, three with one slice in flight, else two
+    static constexpr int CTAS = SMEM <= 55 * 1024 ? 4 : (PF == 1 ? 3 : 2);
 };
 
 template <int R, int RZ>
@@ -1210,7 +1213,7 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
 // through the L1 cache.
 // ---------------------------------------------------------------------------
 template <int R, int RZ, bool BF>
-__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::PF == 1 ? 3 : 2) k_curvature(KArgs a) {
+__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // direction storage
     using G = Geo<R, RZ, TY_C, sizeof(T)>;
     constexpr int PF = CurvRing<R, RZ, sizeof(T)>::PF;    // slices in flight ahead of the consumer
