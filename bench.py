@@ -7,8 +7,9 @@ lambda = delta = 1e-2, eta = 1, box [0, 1], 8 depth slabs of 4,14,6,10,5,12,7,6
 slices (3 colours).  Synthetic data stands in for the paper's microscopy volumes.
 
 One step = one sweep of block 3MG over all slabs (objective pass + for each
-colour: residual, gradient, curvature + 2x2 solve, update), launched as one
-CUDA graph.  `value` is sweeps per second over all ranks (each rank solves its
+colour: gradient, curvature + 2x2 solve, update; the residual and the images
+H d_S follow the update and are recomputed exactly every 256 sweeps), launched
+as one CUDA graph.  `value` is sweeps per second over all ranks (each rank solves its
 own replica: weak scaling, no collective on the data path).  L2 is flushed
 (256 MiB write) before every timed step; each step is bracketed by CUDA events
 on the library's stream.
@@ -263,19 +264,28 @@ def kernel_traffic(name: str):
         return None
 
 
-def algorithmic_bytes(prob, slabs, rz):
-    """Per-class algorithmic bytes of one sweep (FP32 words per voxel, halos excluded):
-    objective 2 (x, y), residual 3 per output voxel (x, y in; r out), gradient 3 (r, x in; g out),
-    curvature 3 (g, d, x in), update 5 (x, g, d in; x, d out)."""
+def algorithmic_bytes(prob, slabs, rz, g_bytes=4):
+    """Per-class algorithmic bytes of one sweep (halos excluded; n voxels, each
+    slab's zone = the slab widened by rz slices each way, at least one below):
+    objective 8 per voxel (x, y in); gradient 8 + g_bytes (r, x in; g out);
+    curvature g_bytes + 8 per voxel (g, d, x in) + 8 per zone voxel (H d_S in,
+    H g_S out); update 12 + g_bytes per voxel (x, g, d in; x, d out) + 20 per
+    zone voxel (H g_S, H d_S, r in; H d_S, r out).  The exact refreshes of r and
+    H d_S (every 256 sweeps) are not counted."""
     nz, ny, nx = prob.shape
     plane = nx * ny
     n = prob.n
-    if slabs is None or len(slabs) <= 2:
-        return {"objective": 0.0, "residual": 12.0 * n, "gradient": 12.0 * n, "curvature": 12.0 * n,
-                "update": 20.0 * n}
-    res = sum(min(nz, slabs[s + 1] + rz) - max(0, slabs[s] - rz) for s in range(len(slabs) - 1)) * plane
-    return {"objective": 8.0 * n, "residual": 12.0 * res, "gradient": 12.0 * n, "curvature": 12.0 * n,
-            "update": 20.0 * n}
+    b = list(slabs) if slabs is not None and len(slabs) > 2 else [0, nz]
+    zone = sum(min(nz, b[s + 1] + rz) - max(0, b[s] - max(rz, 1)) for s in range(len(b) - 1)) * plane
+    return {"objective": 8.0 * n, "residual": 0.0, "gradient": (8.0 + g_bytes) * n,
+            "curvature": (g_bytes + 8.0) * n + 8.0 * zone, "update": (12.0 + g_bytes) * n + 20.0 * zone}
+
+
+def refresh_launches(first: int, count: int, every: int = 256) -> int:
+    """Launches of the exact refreshes of r and H d_S (two per refresh) before
+    iterations first .. first + count - 1 of a context (one before iteration 0,
+    then every `every` iterations)."""
+    return 2 * sum(1 for i in range(first, first + count) if i % every == 0)
 
 
 def time_steps(solver, steps, flush, stream, sampler=None):
@@ -394,13 +404,13 @@ def batch_extra(iters, stream):
 
 def mixed_extra(fstar_iters, stream, flush, steps):
     """512x512x128 volume, 800 ellipsoids + texture, PSF 9x9x7 (sigma_xy 0.5->3.0), noise 0.01:
-    plain 3MG with FP32 directions against BF16 directions (iterations/s with the L2 flushed
+    plain 3MG with an FP32 gradient against a BF16 gradient (iterations/s with the L2 flushed
     before every step, and device time to gap 1e-4; f* from a long FP32 run)."""
     from paper_2002_02328_gb300 import binding, synth
     prob = synth.workload_mixed(seed=0)
     out = {"workload": "plain 3MG 512x512x128, PSF 9x9x7 depth-variant Gaussian, 800 ellipsoids + texture",
            "voxels": prob.n}
-    for name, prec in (("fp32", binding.FP32), ("bf16_directions", binding.BF16_DIRECTIONS)):
+    for name, prec in (("fp32", binding.FP32), ("bf16_gradient", binding.BF16_GRADIENT)):
         with binding.Solver.from_problem(prob, slabs=None, precision=prec) as s:
             for _ in range(3):
                 flush.fill_(1.0)
@@ -411,9 +421,9 @@ def mixed_extra(fstar_iters, stream, flush, steps):
                      "kernel_ms_per_iteration": {k: v[0] for k, v in prof.items()}}
     fstar, settle = fstar_of(prob, fstar_iters)
     out.update({"fstar": fstar, "fstar_iters": fstar_iters, "fstar_settle_rel": settle})
-    # BF16 directions with precision escalation (switch to FP32 directions once f decreases by
+    # BF16 gradient with precision escalation (switch to an FP32 gradient once f decreases by
     # <= 1e-9 |f| per iteration): iterations of the escalating run to each gap level
-    with binding.Solver.from_problem(prob, slabs=None, precision=binding.BF16_DIRECTIONS) as s:
+    with binding.Solver.from_problem(prob, slabs=None, precision=binding.BF16_GRADIENT) as s:
         s.set_escalation(1e-9)
         tr = s.iterate(400)
         at = s.escalated()
@@ -423,7 +433,7 @@ def mixed_extra(fstar_iters, stream, flush, steps):
         hit = np.nonzero((tr - fstar) / den <= lvl)[0]
         esc[name + "_iterations"] = int(hit[0]) if hit.size else None
     out["bf16_escalating"] = esc
-    for name, prec in (("fp32", binding.FP32), ("bf16_directions", binding.BF16_DIRECTIONS)):
+    for name, prec in (("fp32", binding.FP32), ("bf16_gradient", binding.BF16_GRADIENT)):
         k, t, g = time_to_gap(prob, None, fstar, 3000, stream, prec)
         kn, tn, gn = time_to_gap(prob, None, fstar, 3000, stream, prec, normalized=True)
         out[name]["time_to_gap"] = {"iterations": k, "seconds": t, "gap_reached": g}
@@ -616,8 +626,8 @@ def ours(args):
             for k, (ms, cnt) in sp.profile_iteration().items():
                 prof_plain[k][0] += ms
                 prof_plain[k][1] += cnt
-    # block form with BF16 memory directions, same volume
-    with binding.Solver.from_problem(prob, precision=binding.BF16_DIRECTIONS) as sm:
+    # block form with a BF16 gradient, same volume
+    with binding.Solver.from_problem(prob, precision=binding.BF16_GRADIENT) as sm:
         for _ in range(args.warmup):
             flush.fill_(1.0)
             sm.iterate_async(1)
@@ -667,7 +677,7 @@ def ours(args):
              "plain_fp32": {"iterations_per_s": plain_rate, "launches_per_iteration": lpi_plain,
                             "kernel_ms_per_iteration": per_it_plain,
                             "alg_bytes_per_iteration": sum(alg_plain.values())},
-             "block_bf16_directions": {"iterations_per_s": 1e3 * n_mixed / ms_mixed,
+             "block_bf16_gradient": {"iterations_per_s": 1e3 * n_mixed / ms_mixed,
                                        "kernel_ms_per_iteration": {k: v[0] / args.profile_iters
                                                                    for k, v in prof_mixed.items()}}}
 
@@ -676,16 +686,16 @@ def ours(args):
         fstar, settle = fstar_of(prob, args.fstar_iters)
         k_b, t_b, g_b = time_to_gap(prob, prob.slabs, fstar, 3000, stream)
         k_p, t_p, g_p = time_to_gap(prob, None, fstar, 3000, stream)
-        k_m, t_m, g_m = time_to_gap(prob, prob.slabs, fstar, 3000, stream, binding.BF16_DIRECTIONS)
-        k_mp, t_mp, g_mp = time_to_gap(prob, None, fstar, 3000, stream, binding.BF16_DIRECTIONS)
+        k_m, t_m, g_m = time_to_gap(prob, prob.slabs, fstar, 3000, stream, binding.BF16_GRADIENT)
+        k_mp, t_mp, g_mp = time_to_gap(prob, None, fstar, 3000, stream, binding.BF16_GRADIENT)
         k_bn, t_bn, _ = time_to_gap(prob, prob.slabs, fstar, 3000, stream, normalized=True)
         k_pn, t_pn, _ = time_to_gap(prob, None, fstar, 3000, stream, normalized=True)
         extra["time_to_gap"] = {"gap": GAP, "fstar": fstar, "fstar_iters": args.fstar_iters,
                                 "fstar_settle_rel": settle,
                                 "block": {"iterations": k_b, "seconds": t_b},
                                 "plain_fp32": {"iterations": k_p, "seconds": t_p},
-                                "block_bf16_directions": {"iterations": k_m, "seconds": t_m},
-                                "plain_bf16_directions": {"iterations": k_mp, "seconds": t_mp},
+                                "block_bf16_gradient": {"iterations": k_m, "seconds": t_m},
+                                "plain_bf16_gradient": {"iterations": k_mp, "seconds": t_mp},
                                 "normalized_gap": {"definition": "(f - f*) / (f0 - f*) <= 1e-4",
                                                    "block": {"iterations": k_bn, "seconds": t_bn},
                                                    "plain_fp32": {"iterations": k_pn, "seconds": t_pn}}}
@@ -709,7 +719,8 @@ def ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(prob, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": args.steps * lpi + 0, "clocks": clocks, "extra": extra}
+            "gpu_launches": args.steps * lpi + refresh_launches(args.warmup, args.steps), "clocks": clocks,
+            "extra": extra}
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -65,16 +65,18 @@ typedef struct {
     void *user;
 } bd3mg_allocator;
 
-/* Storage precision of the memory directions (Section 3.2 subspace D = [-g, d]).
- * BD3MG_FP32: g and d stored in FP32.
- * BD3MG_BF16_DIRECTIONS: g and d stored in BF16 (round to nearest even), halving
- *   their traffic; x, y and the residual stay FP32, all arithmetic is FP32 and
- *   every reduction and the 2x2 solve FP64.  The subspace is then spanned by the
- *   rounded directions: B = D^T A D and D^T grad f are formed from them (the
- *   gradient term as -||g_bf16||^2), and x moves by the FP32 step -u0 g + u1 d.
- *   bd3mg_gradient and bd3mg_get_volume return the BF16 values widened to FP32.
+/* Storage precision of the gradient direction (Section 3.2 subspace D = [-g, d]).
+ * BD3MG_FP32: g stored in FP32.
+ * BD3MG_BF16_GRADIENT: g stored in BF16 (round to nearest even), halving its
+ *   traffic and the curvature pass's shared-memory ring; x, y, d, the residual
+ *   and the images H d_S stay FP32 (they are carried from one iteration to the
+ *   next, g is recomputed every time), all arithmetic is FP32 and every
+ *   reduction and the 2x2 solve FP64.  The subspace is then spanned by
+ *   [-g_bf16, d]: B = D^T A D and D^T grad f are formed from it (the gradient
+ *   term as -||g_bf16||^2), and x moves by the FP32 step -u0 g_bf16 + u1 d.
+ *   bd3mg_gradient and bd3mg_get_volume return g widened to FP32.
  *   Every volume of a batch must use the same mode. */
-enum { BD3MG_FP32 = 0, BD3MG_BF16_DIRECTIONS = 1 };
+enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1 };
 
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
@@ -84,7 +86,7 @@ typedef struct {
     double delta;             /* > 0 hyperbolic smoothing */
     double eta;               /* >= 0 box weight */
     double xmin, xmax;        /* box bounds, xmin <= xmax */
-    int precision;            /* BD3MG_FP32 or BD3MG_BF16_DIRECTIONS */
+    int precision;            /* BD3MG_FP32 or BD3MG_BF16_GRADIENT */
     int nslabs;               /* number of depth blocks; 0 or 1 = plain 3MG on the whole volume */
     const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
     double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
@@ -99,7 +101,12 @@ void bd3mg_params_default(bd3mg_params *p);
  * needs h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c) to FP64 relative residual <=
  * 1e-6; otherwise BD3MG_EUNSUPPORTED), plans the slab colouring, copies y and
  * x0 (NULL -> x0 = y) into library memory, sets d = 0 and captures the
- * per-iteration CUDA graph.  data_on_device: y and x0 are device pointers
+ * per-iteration CUDA graph.  An iteration blurs twice (H^T r and H g_S per
+ * slab): the residual r = H x - y and the images H d_S of the slabs' memory
+ * directions follow the iterate through the update (H d_S(new) = -u0 H g_S +
+ * u1 H d_S, r += H d_S(new)), and are recomputed exactly before the first
+ * iteration after creation, bd3mg_set_x or bd3mg_load, and every 256
+ * iterations.  data_on_device: y and x0 are device pointers
  * (else host).  stream: cudaStream_t as void*.  alloc may be NULL. */
 bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
                           void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);
@@ -209,11 +216,11 @@ bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, 
 
 /* Kernel classes reported by bd3mg_profile_iteration. */
 enum {
-    BD3MG_K_OBJECTIVE = 0,   /* objective pass of the block form (one per sweep) */
-    BD3MG_K_RESIDUAL = 1,    /* r = H x - y (plain form: fused with the objective) */
+    BD3MG_K_OBJECTIVE = 0,   /* objective pass (one per sweep) */
+    BD3MG_K_RESIDUAL = 1,    /* exact r = H x - y and H d_S (refreshes only: not part of an iteration) */
     BD3MG_K_GRADIENT = 2,    /* g = H^T r + box + penalty gradient */
-    BD3MG_K_CURVATURE = 3,   /* H g_S, H d_S, weights, inner products, 2x2 solve */
-    BD3MG_K_UPDATE = 4,      /* x_S += D u, d_S = D u */
+    BD3MG_K_CURVATURE = 3,   /* H g_S, weights, inner products, 2x2 solve */
+    BD3MG_K_UPDATE = 4,      /* x_S += D u, d_S = D u; H d_S and r on the slab's zone */
     BD3MG_K_CLASSES = 5
 };
 
@@ -227,12 +234,12 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
 /* Number of kernel launches one iteration enqueues. */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
-/* Precision escalation of the BF16-direction form (Section 3.2's subspace D =
- * [-g, d] with directions stored in BF16).  With tol > 0, bd3mg_iterate runs
+/* Precision escalation of the BF16-gradient form (Section 3.2's subspace D =
+ * [-g, d] with g stored in BF16).  With tol > 0, bd3mg_iterate runs
  * in chunks of 4 iterations and reads the objective trace between chunks;
  * once some volume's objective decreases by at most tol * |f| from one
- * iteration to the next, the context switches for good to FP32 directions (d
- * widened from its BF16 values, g recomputed) and a new iteration graph.
+ * iteration to the next, the context switches for good to an FP32 gradient
+ * (g recomputed by the next iteration) and a new iteration graph.
  * bd3mg_iterate_async never escalates.  tol = 0 turns it off (the default);
  * no effect on FP32 contexts.  bd3mg_escalated: *at = the iteration count at
  * which the switch happened, -1 if it has not.  Errors: BD3MG_EINVAL for a
@@ -241,12 +248,13 @@ bd3mg_status bd3mg_set_escalation(bd3mg_ctx *ctx, double tol);
 bd3mg_status bd3mg_escalated(bd3mg_ctx *ctx, long long *at);
 
 /* Checkpoint / resume.  bd3mg_save writes the state an iteration starts from
- * (x and the memory directions d of every volume, in the context's storage
- * precision, and the iteration count) to the file `path` (overwritten);
- * bd3mg_load reads such a file into a context created with the same volumes,
- * slabs and precision, and clears the stopping state.  Everything else an
- * iteration needs (residual, gradient, 2x2 system) is recomputed from x and d,
- * so a loaded context continues bit for bit like the one that was saved.
+ * (x, the memory direction d and the residual r of every volume, the images
+ * H d_S of every slab, the iteration count and the refresh schedule) to the
+ * file `path` (overwritten); bd3mg_load reads such a file into a context
+ * created with the same volumes, slabs and precision, and clears the stopping
+ * state.  Everything else an iteration needs (gradient, 2x2 system) is
+ * recomputed, so a loaded context continues bit for bit like the one that was
+ * saved.
  * Errors: BD3MG_EINVAL (unreadable or mismatching file; the message says
  * which), BD3MG_ECUDA. */
 bd3mg_status bd3mg_save(bd3mg_ctx *ctx, const char *path);

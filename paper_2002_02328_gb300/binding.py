@@ -24,7 +24,7 @@ _lib = None
 
 STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA", 4: "BD3MG_ETIMEOUT",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
-FP32, BF16_DIRECTIONS = 0, 1
+FP32, BF16_GRADIENT = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
@@ -345,7 +345,7 @@ class Solver:
         return int(k[0])
 
     def set_escalation(self, tol: float):
-        """BF16 directions: switch to FP32 directions once f decreases by <= tol |f| per iteration."""
+        """BF16 gradient: switch to an FP32 gradient once f decreases by <= tol |f| per iteration."""
         self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
 
     def escalated(self) -> int:
@@ -506,7 +506,7 @@ class BatchSolver:
         return out
 
     def set_escalation(self, tol: float):
-        """BF16 directions: switch to FP32 directions once f decreases by <= tol |f| per iteration."""
+        """BF16 gradient: switch to an FP32 gradient once f decreases by <= tol |f| per iteration."""
         self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
 
     def escalated(self) -> int:

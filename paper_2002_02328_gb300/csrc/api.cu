@@ -9,6 +9,11 @@
 // reduction slot).  Every kernel launch covers a list of segments of possibly
 // different volumes; items are (segment, xy tile, z-chunk).  Volumes are
 // independent, so colour c of every volume is processed in the same launch.
+//
+// The residual r = H x - y and the images H d_S of the slabs' memory
+// directions (in per-slab zone buffers) follow the iterate through the update
+// (kernels.cuh); they are recomputed exactly before the first iteration after
+// x or d was set from outside, and every kRefreshEvery iterations.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -44,7 +49,7 @@ struct VolState {
     int pitch = 0;                  // row stride in elements (multiple of 8)
     size_t np = 0;                  // pitch*ny*nz
     float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
-    __nv_bfloat16 *dh = nullptr, *gh = nullptr;     // BF16 directions (instead of d, g)
+    __nv_bfloat16 *gh = nullptr;    // BF16 gradient (instead of g)
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev dev{};                   // host copy of the device descriptor
     std::vector<int> bounds;        // slab bounds
@@ -78,7 +83,11 @@ struct bd3mg_ctx {
     int nslab_segs = 0;             // segments [0, nslab_segs) are slabs; then one full segment per volume
     int zchunk = 0;                 // user override (0 = automatic)
     double pinv_rtol = 1e-12;
-    bool bf = false;                // directions g, d stored as BF16
+    bool bf = false;                // gradient g stored as BF16
+    float *zone_hg = nullptr, *zone_hd = nullptr;   // H g_S, H d_S of every slab over its zone
+    size_t zone_elems = 0;
+    bool stale = true;              // r and H d_S must be recomputed before the next iteration
+    long long since_refresh = 0;    // iterations since they were last recomputed
 
     // device state
     float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch for volume 0 (lazy)
@@ -103,8 +112,8 @@ struct bd3mg_ctx {
     std::vector<SegDev> segs_h;
     std::vector<Item> items_h;
     std::vector<int> slot_beg_h, slot_id_h, seg_lists_h, seg_list_off;
-    Launch L_obj, L_res_full, L_grad_full;
-    std::vector<Launch> L_res, L_grad, L_curv;
+    Launch L_obj, L_res_full, L_grad_full, L_hd;
+    std::vector<Launch> L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
     int occ[5] = {1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
@@ -169,19 +178,17 @@ int set_xh(const KernelSet *k, int esize = 4) { return (esize == 4 && k->R <= 4)
 // Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
 int tile_y(int kind) { return kind == 2 ? TY_C : TY_A; }
 
-// g, d: FP32 or (dir_esize 2) BF16 direction arrays.
+// g: FP32 or (g_esize 2) BF16 gradient; d: FP32 memory direction.
 bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const float *x, const float *r,
-                     const void *g, const void *d, int dir_esize = 4) {
+                     const void *g, const float *d, int g_esize = 4) {
     const bd3mg_params &p = v.p;
-    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks), bxd = TX + 2 * set_xh(c->ks, dir_esize);
+    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks), bxg = TX + 2 * set_xh(c->ks, g_esize);
     std::memset(vm, 0, sizeof(*vm));
     bool ok = true;
     if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1A], x, 4, p.nx, p.ny, p.nz, v.pitch, BX1, TY_A + 2);
-    if (x) ok = ok && encode_map(&vm->m[TM_X_1C], x, 4, p.nx, p.ny, p.nz, v.pitch, BX1, TY_C + 2);
     if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, dir_esize, p.nx, p.ny, p.nz, v.pitch, bxd, TY_C + 2 * R);
-    if (d) ok = ok && encode_map(&vm->m[TM_D_R], d, dir_esize, p.nx, p.ny, p.nz, v.pitch, bxd, TY_C + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, g_esize, p.nx, p.ny, p.nz, v.pitch, bxg, TY_C + 2 * R);
+    if (d) ok = ok && encode_map(&vm->m[TM_D_X], d, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
     return ok;
 }
 
@@ -353,7 +360,8 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     for (int k = 0; k < cnt; ++k) {
         const SegDev &sg = c->segs_h[c->seg_lists_h[off + k]];
         const VolState &v = c->V[sg.vol];
-        maxlen = std::max<long long>(maxlen, (long long)(sg.z1 - sg.z0) * v.pitch * v.p.ny);
+        const int planes = std::max(sg.z1 - sg.z0, sg.hz1 - sg.hz0);
+        maxlen = std::max<long long>(maxlen, (long long)planes * v.pitch * v.p.ny);
     }
     long long blocks = (maxlen / 4 + NT - 1) / NT;
     blocks = std::max<long long>(1, std::min<long long>(blocks, 2048));
@@ -375,19 +383,10 @@ bool stopping_enabled(const bd3mg_ctx *c) {
 
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
-    if (!c->any_slabs) {
-        if ((st = run_residual(c, s, c->L_res[0], M_STORE_R | M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
-        for (int col = 0; col < c->ncolours; ++col) {
-            if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
-            if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
-            if ((st = run_update(c, s, col))) return st;
-        }
-        return BD3MG_OK;
-    }
-    // Block form.  The objective pass that opens the sweep reads x and y and
-    // only has to finish before the first update writes x; without stopping
-    // (whose flag it sets for the later launches) it runs as a parallel branch
-    // of the graph beside colour 0's residual, gradient and curvature.
+    // The objective pass that opens the sweep reads x and y and only has to
+    // finish before the first update writes x; without stopping (whose flag it
+    // sets for the later launches) it runs as a parallel branch of the graph
+    // beside colour 0's gradient and curvature.
     const bool branch = !c->prof_on && s == c->cap_stream && !stopping_enabled(c);
     if (branch) {
         CK(cudaEventRecord(c->ev_fork, s));
@@ -398,11 +397,35 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
         if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
-        if ((st = run_residual(c, s, c->L_res[col], M_STORE_R | M_ITER))) return st;
         if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
         if (branch && col == 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
         if ((st = run_update(c, s, col))) return st;
+    }
+    return BD3MG_OK;
+}
+
+// Exact r = H x - y of every volume and H d_S of every slab (d masked to the
+// slab) into its zone buffer, on the context stream.
+constexpr long long kRefreshEvery = 256;
+bd3mg_status refresh_products(bd3mg_ctx *c) {
+    bd3mg_status st;
+    if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
+    if ((st = run_residual(c, c->stream, c->L_hd, M_STORE_R | M_ZONE))) return st;
+    c->stale = false;
+    c->since_refresh = 0;
+    return BD3MG_OK;
+}
+
+// n graph launches of one iteration each, with the refreshes they are due.
+bd3mg_status launch_iterations(bd3mg_ctx *c, int n) {
+    for (int k = 0; k < n; ++k) {
+        if (c->stale || c->since_refresh >= kRefreshEvery) {
+            bd3mg_status st = refresh_products(c);
+            if (st) return st;
+        }
+        CK(cudaGraphLaunch(c->exec, c->stream));
+        ++c->since_refresh;
     }
     return BD3MG_OK;
 }
@@ -465,14 +488,14 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         d.nx = p.nx; d.ny = p.ny; d.nz = p.nz; d.pitch = vs.pitch;
         d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
         d.plane = (long long)vs.pitch * p.ny;
-        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.dh = vs.dh; d.gh = vs.gh;
+        d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.gh = vs.gh;
         d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
         d.lam_d = p.lambda; d.eta_d = p.eta;
         vs.dev = d;
         vd[v] = d;
-        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.dh, 2)
+        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
                               : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
         if (!ok)
             return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
@@ -505,18 +528,14 @@ bd3mg_status capture_graph(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
-// Switch a BF16-direction context to FP32 directions: FP32 g and d arrays (d
-// widened from its BF16 values, g recomputed by the next iteration), FP32
-// descriptors, and a new iteration graph.
+// Switch a BF16-gradient context to an FP32 gradient: FP32 g arrays (g is
+// recomputed by the next iteration; d, r and the zone buffers are FP32 in both
+// forms), FP32 descriptors, and a new iteration graph.
 bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     if (!c->bf) return BD3MG_OK;
     bd3mg_status st;
     for (VolState &vs : c->V) {
-        if (!vs.d) {
-            if ((st = dalloc_n(c, &vs.d, vs.np)) || (st = dalloc_n(c, &vs.g, vs.np))) return st;
-        }
-        launch_dir_to_float(vs.dh, vs.d, (long long)vs.np, c->stream);
-        if ((st = check_launch(c))) return st;
+        if (!vs.g && (st = dalloc_n(c, &vs.g, vs.np))) return st;
         CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
     }
     c->bf = false;
@@ -525,43 +544,27 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     return capture_graph(c);
 }
 
-// Per-colour launches (residual of the slab form, gradient, curvature, update
-// lists) over the volumes marked active; the plain form's residual launch, which
-// also evaluates the objective and writes the trace, always covers every volume.
+// Per-colour launches (gradient, curvature, update lists) over the volumes
+// marked active.  A curvature item range is its slab's zone.
 void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
     c->items_h.resize(c->base_items);
     c->slot_beg_h.resize(c->base_beg);
     c->slot_id_h.resize(c->base_slot);
     c->seg_lists_h.clear();
     c->seg_list_off.assign(1, 0);
-    c->L_res.clear();
     c->L_grad.clear();
     c->L_curv.clear();
-    const int RZk = c->ks->RZ;
-    const int Lk = std::max(RZk, 1);
-    auto whole = [&](int s, int *lo, int *hi) { *lo = 0; *hi = c->segs_h[s].z1; };
-    auto nzof = [&](int s) { return c->V[c->segs_h[s].vol].p.nz; };
-    if (c->colour_zc.empty()) c->colour_zc.assign(3 * (size_t)c->ncolours, 0);
+    if (c->colour_zc.empty()) c->colour_zc.assign(2 * (size_t)c->ncolours, 0);
     for (int col = 0; col < c->ncolours; ++col) {
-        std::vector<int> segs, all;
+        std::vector<int> segs;
         for (int v = 0; v < c->nvol; ++v)
             for (size_t s = 0; s < c->V[v].colour.size(); ++s)
-                if (c->V[v].colour[s] == col) {
-                    all.push_back(c->V[v].seg0 + (int)s);
-                    if (active[v]) segs.push_back(c->V[v].seg0 + (int)s);
-                }
-        int *zc = c->colour_zc.data() + 3 * col;
-        if (!c->any_slabs)
-            c->L_res.push_back(make_launch(c, all, whole, SLOTS_PER_VOLUME, 0, zc));
-        else
-            c->L_res.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-                *lo = std::max(0, c->segs_h[s].z0 - RZk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
-                SLOTS_NONE, 0, zc));
+                if (c->V[v].colour[s] == col && active[v]) segs.push_back(c->V[v].seg0 + (int)s);
+        int *zc = c->colour_zc.data() + 2 * col;
         c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1, zc + 1));
+            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1, zc));
         c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = std::max(0, c->segs_h[s].z0 - Lk); *hi = std::min(nzof(s), c->segs_h[s].z1 + RZk); },
-            SLOTS_PER_SEGMENT, 2, zc + 2));
+            *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_PER_SEGMENT, 2, zc + 1));
         for (int s : segs) c->seg_lists_h.push_back(s);
         c->seg_list_off.push_back((int)c->seg_lists_h.size());
     }
@@ -603,7 +606,7 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
     if (!p.psf) return fail(c, BD3MG_EINVAL, "volume %d: psf is NULL", vi);
     if (!(p.lambda > 0) || !(p.delta > 0) || !(p.eta >= 0) || !(p.xmin <= p.xmax))
         return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
-    if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_DIRECTIONS)
+    if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_GRADIENT)
         return fail(c, BD3MG_EINVAL, "volume %d: unknown precision mode %d", vi, p.precision);
     if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return fail(c, BD3MG_EINVAL, "volume %d too large", vi);
     v.p = p;
@@ -639,7 +642,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
     c->zchunk = pp[0].zchunk;
-    c->bf = pp[0].precision == BD3MG_BF16_DIRECTIONS;
+    c->bf = pp[0].precision == BD3MG_BF16_GRADIENT;
     for (int v = 1; v < nvol; ++v)
         if (pp[v].precision != pp[0].precision) return fail(c, BD3MG_EINVAL, "volumes must share one precision mode");
 
@@ -656,20 +659,25 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         c->V[v].p.psf = nullptr;
     }
 
-    // segments and colouring: slabs of one volume and colour are >= max(pz-1, 1) slices apart
+    // segments and colouring: slabs of one volume and colour are >= max(pz-1, 1)
+    // slices apart, so their zones [z0 - max(rz, 1), z1 + rz) (the slab widened
+    // by the volume's own PSF z radius rz) are disjoint
     c->ncolours = 1;
     for (int v = 0; v < nvol; ++v) {
         VolState &vs = c->V[v];
-        const int rz = (vs.p.pz - 1) / 2;
+        const int rz = (vs.p.pz - 1) / 2, nz = vs.p.nz;
         c->ncolours = std::max(c->ncolours, colour_slabs(vs.bounds, std::max(2 * rz, 1), vs.colour));
         vs.seg0 = (int)c->segs_h.size();
-        for (size_t s = 0; s + 1 < vs.bounds.size(); ++s)
-            c->segs_h.push_back(SegDev{v, vs.bounds[s], vs.bounds[s + 1], (int)c->segs_h.size()});
+        for (size_t s = 0; s + 1 < vs.bounds.size(); ++s) {
+            const int z0 = vs.bounds[s], z1 = vs.bounds[s + 1];
+            c->segs_h.push_back(SegDev{v, z0, z1, (int)c->segs_h.size(), std::max(0, z0 - std::max(rz, 1)),
+                                       std::min(nz, z1 + rz), nullptr, nullptr});
+        }
         if (vs.bounds.size() > 2) c->any_slabs = true;
     }
     c->nslab_segs = (int)c->segs_h.size();
     for (int v = 0; v < nvol; ++v)
-        c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size()});
+        c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size(), 0, 0, nullptr, nullptr});
 
     // occupancy of the chosen kernels (drives the z-chunk choice)
     {
@@ -682,14 +690,15 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
 
     // work lists
-    const int RZk = c->ks->RZ;          // kernel z radius (padded), governs halos
-    const int Lk = std::max(RZk, 1);
-    std::vector<int> full;
+    std::vector<int> full, slabs;
     for (int v = 0; v < nvol; ++v) full.push_back(c->nslab_segs + v);
+    for (int s = 0; s < c->nslab_segs; ++s) slabs.push_back(s);
     auto whole = [&](int s, int *lo, int *hi) { *lo = 0; *hi = c->segs_h[s].z1; };
     c->L_obj = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
     c->L_res_full = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
     c->L_grad_full = make_launch(c, full, whole, SLOTS_NONE, 1);
+    c->L_hd = make_launch(c, slabs, [&](int s, int *lo, int *hi) { *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; },
+                          SLOTS_NONE, 0);
     c->base_items = c->items_h.size();
     c->base_beg = c->slot_beg_h.size();
     c->base_slot = c->slot_id_h.size();
@@ -703,15 +712,35 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
 
     // device allocations
     const size_t nseg = c->segs_h.size();
-#define AL(ptr, cnt) if ((st = dalloc_n(c, &(ptr), (cnt)))) return st
+#define AL(ptr, cnt) do { if ((st = dalloc_n(c, &(ptr), (cnt)))) return st; } while (0)
     for (int v = 0; v < nvol; ++v) {
         VolState &vs = c->V[v];
         vs.pitch = (vs.p.nx + 7) & ~7;            // 16-byte rows for both FP32 and BF16 arrays
         vs.np = (size_t)vs.pitch * vs.p.ny * vs.p.nz;
-        AL(vs.x, vs.np); AL(vs.r, vs.np); AL(vs.y, vs.np);
-        if (c->bf) { AL(vs.dh, vs.np); AL(vs.gh, vs.np); }
-        else { AL(vs.d, vs.np); AL(vs.g, vs.np); }
+        AL(vs.x, vs.np); AL(vs.r, vs.np); AL(vs.y, vs.np); AL(vs.d, vs.np);
+        if (c->bf) {
+            AL(vs.gh, vs.np);
+        } else {
+            AL(vs.g, vs.np);
+        }
         AL(vs.fx, FX[v].size()); AL(vs.fy, FY[v].size()); AL(vs.fz, FZ[v].size());
+    }
+    // zone buffers of the slabs, one after another (every zone a whole number of planes)
+    c->zone_elems = 0;
+    for (int s = 0; s < c->nslab_segs; ++s) {
+        const SegDev &sg = c->segs_h[s];
+        c->zone_elems += (size_t)(sg.hz1 - sg.hz0) * c->V[sg.vol].pitch * c->V[sg.vol].p.ny;
+    }
+    AL(c->zone_hg, std::max<size_t>(c->zone_elems, 4));
+    AL(c->zone_hd, std::max<size_t>(c->zone_elems, 4));
+    {
+        size_t off = 0;
+        for (int s = 0; s < c->nslab_segs; ++s) {
+            SegDev &sg = c->segs_h[s];
+            sg.hg = c->zone_hg + off;
+            sg.hd = c->zone_hd + off;
+            off += (size_t)(sg.hz1 - sg.hz0) * c->V[sg.vol].pitch * c->V[sg.vol].p.ny;
+        }
     }
     AL(c->vols, nvol + 1); AL(c->maps, nvol + 1); AL(c->segs, nseg);
     AL(c->items, c->items_h.size());
@@ -734,11 +763,10 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpy2DAsync(vs.y, pb, ys[v], wb, wb, rows, kin, c->stream));
         const float *x0 = (x0s && x0s[v]) ? x0s[v] : ys[v];
         CK(cudaMemcpy2DAsync(vs.x, pb, x0, wb, wb, rows, kin, c->stream));
+        CK(cudaMemsetAsync(vs.d, 0, vs.np * 4, c->stream));
         if (c->bf) {
-            CK(cudaMemsetAsync(vs.dh, 0, vs.np * 2, c->stream));
             CK(cudaMemsetAsync(vs.gh, 0, vs.np * 2, c->stream));
         } else {
-            CK(cudaMemsetAsync(vs.d, 0, vs.np * 4, c->stream));
             CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
         }
         CK(cudaMemsetAsync(vs.r, 0, vs.np * 4, c->stream));
@@ -746,6 +774,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fz, FZ[v].data(), FZ[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
     }
+    CK(cudaMemsetAsync(c->zone_hg, 0, c->zone_elems * 4, c->stream));
+    CK(cudaMemsetAsync(c->zone_hd, 0, c->zone_elems * 4, c->stream));
     if ((st = upload_descriptors(c))) return st;
     CK(cudaMemcpyAsync(c->segs, c->segs_h.data(), sizeof(SegDev) * nseg, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
@@ -769,6 +799,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     c->f_target.assign(nvol, -INFINITY);
     if ((st = reset_run(c, -1))) return st;
     if ((st = ensure_trace(c, 1024))) return st;
+    c->stale = true;
 
     return capture_graph(c);
 }
@@ -933,7 +964,8 @@ int bd3mg_volume_count(bd3mg_ctx *c) { return c ? c->nvol : 0; }
 bd3mg_status bd3mg_iterate_async(bd3mg_ctx *c, int n) {
     GUARD(c);
     if (n < 0) return fail(c, BD3MG_EINVAL, "n < 0");
-    for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
+    bd3mg_status st = launch_iterations(c, n);
+    if (st) return st;
     c->iterations += n;
     return BD3MG_OK;
 }
@@ -948,7 +980,7 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     const bool compact = c->nvol > 1 && stopping_enabled(c);
     if ((c->bf && c->esc_tol > 0.0) || compact) {
         // run in chunks of 4 iterations, reading state between them:
-        //  - escalation: switch to FP32 directions once some volume decreases by
+        //  - escalation: switch to an FP32 gradient once some volume decreases by
         //    at most esc_tol relative;
         //  - per-volume stopping in a batch: drop stopped volumes from the
         //    gradient, curvature and update work lists (the objective pass keeps
@@ -959,7 +991,7 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
         int k = 0;
         while (k < n) {
             const int m = std::min(chunk, n - k);
-            for (int j = 0; j < m; ++j) CK(cudaGraphLaunch(c->exec, c->stream));
+            if ((st = launch_iterations(c, m))) return st;
             k += m;
             c->iterations = base + k;
             if (c->bf && c->esc_tol > 0.0) {
@@ -984,7 +1016,7 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
             }
         }
     } else {
-        for (int k = 0; k < n; ++k) CK(cudaGraphLaunch(c->exec, c->stream));
+        if ((st = launch_iterations(c, n))) return st;
     }
     c->iterations = base + n;
     if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ | M_TRACE))) return st;
@@ -1006,8 +1038,8 @@ bd3mg_status bd3mg_set_stopping(bd3mg_ctx *c, double tol, const double *f_target
     bd3mg_status st;
     if ((st = upload_shared(c))) return st;
     if ((st = reset_run(c, -1))) return st;
-    // the block-form graph runs the objective as a parallel branch only without stopping
-    return c->any_slabs ? capture_graph(c) : BD3MG_OK;
+    // the graph runs the objective as a parallel branch only without stopping
+    return capture_graph(c);
 }
 
 bd3mg_status bd3mg_stopped(bd3mg_ctx *c, int *sweeps) {
@@ -1073,8 +1105,8 @@ bd3mg_status bd3mg_get_volume(bd3mg_ctx *c, int vol, int which, float *dst, int 
         return fail(c, BD3MG_EINVAL, "get_volume: bad volume index, selector or NULL destination");
     const VolState &v = c->V[vol];
     const float *src = which == 0 ? v.x : which == 1 ? v.d : v.g;
-    if (c->bf && which > 0) {
-        bd3mg_status st = dir_as_float(c, v, which == 1 ? v.dh : v.gh, &src);
+    if (c->bf && which == 2) {
+        bd3mg_status st = dir_as_float(c, v, v.gh, &src);
         if (st) return st;
     }
     return copy_vol(c, v, dst, src, on_device, false);
@@ -1087,8 +1119,8 @@ bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     GUARD(c);
     if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
     const VolState &v = c->V[0];
-    if (c->bf) CK(cudaMemsetAsync(v.dh, 0, v.np * 2, c->stream));
-    else CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
+    CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
+    c->stale = true;                // r and H d_S of the new x (d = 0) before the next iteration
     bd3mg_status st = reset_run(c, 0);
     if (st) return st;
     return copy_vol(c, v, v.x, x, on_device, true);
@@ -1113,68 +1145,84 @@ const char kCkptMagic[8] = {'B', 'D', '3', 'M', 'G', 'C', 'K', '1'};
 
 struct CkptHead {
     char magic[8];
-    int32_t version, nvol, bf, pad;
-    int64_t iterations;
+    int32_t version, nvol, bf, stale;
+    int64_t iterations, since_refresh, zone_elems;
 };
+
+// Device -> file (write) or file -> device (read) of n bytes through a host buffer.
+bool ckpt_io(bd3mg_ctx *c, std::fstream &f, void *dev, size_t n, bool write, std::vector<char> &buf) {
+    buf.resize(n);
+    if (write) {
+        if (cudaMemcpyAsync(buf.data(), dev, n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return false;
+        f.write(buf.data(), (std::streamsize)n);
+    } else {
+        f.read(buf.data(), (std::streamsize)n);
+        if (!f) return false;
+        if (cudaMemcpyAsync(dev, buf.data(), n, cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return false;
+    }
+    return (bool)f;
+}
 }  // namespace
 
 bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
-    std::ofstream f(path, std::ios::binary | std::ios::trunc);
+    std::fstream f(path, std::ios::out | std::ios::binary | std::ios::trunc);
     if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s for writing", path);
     CkptHead h{};
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = 2;
     h.nvol = c->nvol;
     h.bf = c->bf ? 1 : 0;
+    h.stale = c->stale ? 1 : 0;
     h.iterations = c->iterations;
+    h.since_refresh = c->since_refresh;
+    h.zone_elems = (int64_t)c->zone_elems;
     f.write(reinterpret_cast<const char *>(&h), sizeof(h));
     std::vector<char> buf;
     for (const VolState &v : c->V) {
         const int32_t dims[4] = {v.p.nx, v.p.ny, v.p.nz, v.pitch};
         f.write(reinterpret_cast<const char *>(dims), sizeof(dims));
-        const size_t xb = v.np * 4, db = v.np * (c->bf ? 2 : 4);
-        buf.resize(std::max(xb, db));
-        CK(cudaMemcpyAsync(buf.data(), v.x, xb, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        f.write(buf.data(), (std::streamsize)xb);
-        CK(cudaMemcpyAsync(buf.data(), c->bf ? (const void *)v.dh : (const void *)v.d, db, cudaMemcpyDeviceToHost,
-                           c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        f.write(buf.data(), (std::streamsize)db);
+        if (!ckpt_io(c, f, v.x, v.np * 4, true, buf) || !ckpt_io(c, f, v.d, v.np * 4, true, buf) ||
+            !ckpt_io(c, f, v.r, v.np * 4, true, buf))
+            return fail(c, BD3MG_EINVAL, "write to %s failed", path);
     }
-    if (!f) return fail(c, BD3MG_EINVAL, "write to %s failed", path);
+    if (!ckpt_io(c, f, c->zone_hd, c->zone_elems * 4, true, buf))
+        return fail(c, BD3MG_EINVAL, "write to %s failed", path);
     return BD3MG_OK;
 }
 
 bd3mg_status bd3mg_load(bd3mg_ctx *c, const char *path) {
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
-    std::ifstream f(path, std::ios::binary);
+    std::fstream f(path, std::ios::in | std::ios::binary);
     if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s", path);
     CkptHead h{};
     f.read(reinterpret_cast<char *>(&h), sizeof(h));
-    if (!f || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    if (!f || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2)
         return fail(c, BD3MG_EINVAL, "%s is not a checkpoint of this library", path);
-    if (h.nvol != c->nvol || h.bf != (c->bf ? 1 : 0))
-        return fail(c, BD3MG_EINVAL, "checkpoint has %d volume(s), precision %d; the context has %d, %d", h.nvol, h.bf,
-                    c->nvol, c->bf ? 1 : 0);
+    if (h.nvol != c->nvol || h.bf != (c->bf ? 1 : 0) || h.zone_elems != (int64_t)c->zone_elems)
+        return fail(c, BD3MG_EINVAL, "checkpoint has %d volume(s), precision %d; the context has %d, %d (or other slabs)",
+                    h.nvol, h.bf, c->nvol, c->bf ? 1 : 0);
     std::vector<char> buf;
     for (VolState &v : c->V) {
         int32_t dims[4];
         f.read(reinterpret_cast<char *>(dims), sizeof(dims));
         if (!f || dims[0] != v.p.nx || dims[1] != v.p.ny || dims[2] != v.p.nz || dims[3] != v.pitch)
             return fail(c, BD3MG_EINVAL, "checkpoint volume shape does not match the context");
-        const size_t xb = v.np * 4, db = v.np * (c->bf ? 2 : 4);
-        buf.resize(xb + db);
-        f.read(buf.data(), (std::streamsize)(xb + db));
-        if (!f) return fail(c, BD3MG_EINVAL, "checkpoint %s is truncated", path);
-        CK(cudaMemcpyAsync(v.x, buf.data(), xb, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaMemcpyAsync(c->bf ? (void *)v.dh : (void *)v.d, buf.data() + xb, db, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+        if (!ckpt_io(c, f, v.x, v.np * 4, false, buf) || !ckpt_io(c, f, v.d, v.np * 4, false, buf) ||
+            !ckpt_io(c, f, v.r, v.np * 4, false, buf))
+            return fail(c, BD3MG_EINVAL, "checkpoint %s is truncated", path);
     }
+    if (!ckpt_io(c, f, c->zone_hd, c->zone_elems * 4, false, buf))
+        return fail(c, BD3MG_EINVAL, "checkpoint %s is truncated", path);
     c->iterations = h.iterations;
+    c->since_refresh = h.since_refresh;
+    c->stale = h.stale != 0;
     return reset_run(c, -1);
 }
 
@@ -1241,6 +1289,10 @@ bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, 
 
 bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
     GUARD(c);
+    if (c->stale || c->since_refresh >= kRefreshEvery) {
+        bd3mg_status sr = refresh_products(c);
+        if (sr) return sr;
+    }
     c->prof_on = true;
     c->prof_ev.clear();
     c->prof_cls.clear();
@@ -1249,6 +1301,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
     c->prof_on = false;
     if (st) return st;
     c->iterations += 1;
+    c->since_refresh += 1;
     CK(cudaStreamSynchronize(c->stream));
     double tot[BD3MG_K_CLASSES] = {0};
     int cnt[BD3MG_K_CLASSES] = {0};
@@ -1270,7 +1323,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
     if (!c) return 0;
-    return c->any_slabs ? 1 + 4 * c->ncolours : 4 * c->ncolours;
+    return 1 + 3 * c->ncolours;
 }
 
 }  // extern "C"

@@ -1,19 +1,28 @@
 // kernels.cuh -- device kernels of the block 3MG iteration (sm_103a).
 //
-// One iteration (one sweep) of block 3MG over a set of depth slabs is four
-// passes, each a z-marching tile kernel over a work list of (slab, xy tile,
-// output z-chunk) items:
+// One iteration (one sweep) of block 3MG over a set of depth slabs is an
+// objective pass and, per colour of slabs, three passes, each a z-marching
+// tile kernel over a work list of (slab, xy tile, output z-chunk) items:
 //
-//   k_residual  r = H x - y on the slabs' dependence zone, and/or the objective
-//               f(x) (Section 3.1, Eq. "crit") with a fixed-order FP64 reduction
+//   k_residual  f(x) (Section 3.1, Eq. "crit") with a fixed-order FP64
+//               reduction; outside the iteration also r = H x - y, and the
+//               images H d_S of the memory directions (exact refresh)
 //   k_gradient  g = H^T r + 2 eta (x - P(x)) + lambda sum_a V^aT psi'(V^a x) on
 //               the slabs (the gradient the Worker box needs in step (3))
-//   k_curvature H g_S and H d_S on the fly, the half-quadratic weights
-//               w_a = 1/sqrt(delta^2 + (V^a x)^2) and the nine inner products of
-//               D^T A D and D^T grad f (Eq. "maj", D = [-g_S | d_S]); the last
-//               CTA to finish sums the per-CTA partials per slab in a fixed
-//               order and solves the 2x2 system u = -B^+ c (Eq. "minimizer")
-//   k_update    x_S += D u, d_S = D u (Master box step (2)), in update.cu
+//   k_curvature H g_S on the fly (written to the slab's zone buffer), the
+//               half-quadratic weights w_a = 1/sqrt(delta^2 + (V^a x)^2) and the
+//               inner products of D^T A D and D^T grad f (Eq. "maj", D = [-g_S | d_S]),
+//               with H d_S read from the zone buffer; the last CTA to finish sums
+//               the per-CTA partials per slab in a fixed order and solves the 2x2
+//               system u = -B^+ c (Eq. "minimizer")
+//   k_update    x_S += D u, d_S = D u (Master box step (2)), and, since
+//               H d_S(new) = H D u = -u0 H g_S + u1 H d_S, the zone buffer
+//               H d_S and the residual r += H d_S(new) on the slab's zone, in update.cu
+//
+// So every iteration blurs twice (H^T r and H g_S) instead of four times: the
+// residual and H d_S follow the iterate through the linear update.  Both are
+// recomputed exactly (k_residual) when x or d is set from outside and every
+// few hundred iterations, which bounds the FP32 drift of the recurrences.
 //
 // The blur H is depth-variant with a separable PSF per OUTPUT depth z:
 // h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c).  Forward: z-combine the input slices
@@ -30,12 +39,11 @@
 // read every tap unconditionally.  The forward z-combine reads the 2*RZ+1
 // resident slices of its window with float4 shared loads (4 halo columns per
 // unit), the x-pass is register-blocked by 4 outputs (float4 shared loads),
-// the y-pass by TY/8 outputs; two CTA barriers per slice.  The PSF factor rows
-// of an item's depth range are staged once in shared memory.  Residual and
-// gradient use 32x32 tiles; the curvature kernel, which stages two arrays,
-// uses 32x16 tiles.
+// the y-pass by pairs of columns; two CTA barriers per slice.  The PSF factor
+// rows of an item's depth range are staged once in shared memory.  Residual and
+// gradient use 32x32 tiles, the curvature kernel 32x16 tiles.
 //
-// Volumes are stored with a row pitch that is a multiple of 4 floats (16-byte
+// Volumes are stored with a row pitch that is a multiple of 8 floats (16-byte
 // TMA strides); padding columns stay zero and are never outputs.
 //
 // Per-voxel arithmetic is FP32; per-thread partial sums are FP32 over at most
@@ -58,9 +66,6 @@ constexpr int NT = 256;           // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int PREF = 2;           // slices in flight ahead of the consumer (>= 2, see Pipe)
 constexpr int ZC_MAX = 48;        // max output slices per work item
-constexpr int XH1 = 4;            // x halo of the 1-voxel-halo x tiles (rounded to 4 floats)
-constexpr int BX1 = TX + 2 * XH1;
-constexpr int NSX = PREF + 3;     // slots of the 1-halo x pipeline
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier wait (2 s)
 
@@ -71,6 +76,7 @@ constexpr int M_TRACE = 4;        // k_residual: append f to the trace
 constexpr int M_ADVANCE = 8;      // k_residual: advance the trace counter
 constexpr int M_HT_ONLY = 16;     // k_gradient: output H^T r only
 constexpr int M_ITER = 32;        // launch belongs to an iteration: items of stopped volumes exit at once
+constexpr int M_ZONE = 64;        // k_residual: H d_S of each slab (d masked to the slab) into its zone buffer
 
 // Status bits (device word)
 constexpr int ST_NONFINITE = 1;
@@ -80,8 +86,8 @@ struct VolDev {
     int nx, ny, nz, pitch;        // pitch: row stride in elements (multiple of 8)
     int kxy, kz;                  // factor row lengths 2R+1, 2RZ+1 (zero padded)
     long long plane;              // pitch*ny
-    float *x, *d, *g, *r;         // d, g: FP32 directions (null in the BF16-direction form)
-    __nv_bfloat16 *dh, *gh;       // d, g: BF16 directions (null in the FP32 form)
+    float *x, *d, *g, *r;         // d: FP32 memory direction; g: FP32 gradient (null in the BF16 form)
+    __nv_bfloat16 *gh;            // g stored as BF16 (null in the FP32 form)
     const float *y;               // null -> 0
     const float *fx, *fy, *fz;    // [nz][kxy], [nz][kxy], [nz][kz]
     float lam, delta2, eta2, xmin, xmax;
@@ -90,12 +96,19 @@ struct VolDev {
 
 // TMA descriptors of one volume (global memory, 64-byte aligned).
 //   X_R: x, halo R, 32-row tiles (k_residual)    R_R: r, halo R, 32-row tiles (k_gradient)
-//   X_1A: x, halo 1, 32-row tiles (k_gradient)   G_R, D_R: g, d, halo R, 16-row tiles (k_curvature)
-//   X_1C: x, halo 1, 16-row tiles (k_curvature)
-enum { TM_X_R = 0, TM_R_R = 1, TM_X_1A = 2, TM_G_R = 3, TM_D_R = 4, TM_X_1C = 5, TM_COUNT = 6 };
+//   G_R: g, halo R, 16-row tiles (k_curvature)   D_X: d, halo R, 32-row tiles (k_residual, M_ZONE)
+enum { TM_X_R = 0, TM_R_R = 1, TM_G_R = 2, TM_D_X = 3, TM_COUNT = 4 };
 struct VolMaps { CUtensorMap m[TM_COUNT]; };
 
-struct SegDev { int vol, z0, z1, slot; };
+// A segment is one slab [z0, z1) of a volume.  Its zone [hz0, hz1) is the
+// output range of its curvature items (the slab widened by the PSF's z radius,
+// and by at least one slice below for the z differences); hg and hd hold H g_S
+// and H d_S there, slice z at (z - hz0) * plane (null for whole-volume segments).
+struct SegDev {
+    int vol, z0, z1, slot;
+    int hz0, hz1;
+    float *hg, *hd;
+};
 struct Item { int seg, tx0, ty0, zo0, zo1; };
 
 // Per-volume stopping state (device).  The objective launch that opens a
@@ -151,8 +164,6 @@ struct Geo {
     // slot length: a multiple of 128 bytes, so that every slot (a TMA destination) stays 128-byte aligned
     static constexpr int SLOT_Q = 128 / EB;
     static constexpr int SLOT = ((BX * BY + SLOT_Q - 1) / SLOT_Q) * SLOT_Q;
-    static constexpr int BY1 = TY + 2;                // 1-halo x tile height
-    static constexpr int SLOT1 = ((BX1 * BY1 + 31) / 32) * 32;
     static constexpr int ZUNITS = BY * (BX / 4);      // z-combine units of 4 staged columns
     static constexpr int KXY = 2 * R + 1;
     static constexpr int KZ = 2 * RZ + 1;
@@ -173,28 +184,26 @@ struct Geo {
     static constexpr size_t bars_bytes(int n) { return ((n * 8 + 127) / 128) * 128; }
 };
 
-// Ring of k_curvature: KZ + PF slots per direction array.  One slice in flight
-// (PF = 1) when that lets three CTAs share an SM, otherwise two.
+// Ring of k_curvature: KZ + PF slots of g.  Two slices in flight when four
+// CTAs still share an SM, otherwise one; the launch bounds ask registers for
+// four CTAs per SM where the shared memory allows it, else three (or two).
 template <int R, int RZ, int EB>
 struct CurvRing {
     using C = Geo<R, RZ, TY_C, EB>;
     static constexpr size_t bytes(int pf) {
-        return (size_t)EB * (2 * (C::KZ + pf) * C::SLOT) +
-               sizeof(float) * (2 * C::BY * C::BX + 2 * C::BY * TX + C::CF_OUT_FLOATS) + C::bars_bytes(C::KZ + pf);
+        return (size_t)EB * ((C::KZ + pf) * C::SLOT) + sizeof(float) * (C::BY * C::BX + C::BY * TX + C::CF_OUT_FLOATS) +
+               C::bars_bytes(C::KZ + pf);
     }
-    static constexpr int PF = bytes(1) <= 74 * 1024 ? 1 : 2;
+    static constexpr int PF = bytes(2) <= 55 * 1024 ? 2 : 1;
     static constexpr int NS = C::KZ + PF;
     static constexpr size_t SMEM = bytes(PF);
-    // CTAs per SM the launch bounds ask registers for: four where the shared
-    // memory allows it, three with one slice in flight, else two
-    static constexpr int CTAS = SMEM <= 55 * 1024 ? 4 : (PF == 1 ? 3 : 2);
+    static constexpr int CTAS = SMEM <= 55 * 1024 ? 4 : (SMEM <= 74 * 1024 ? 3 : 2);
 };
 
 template <int R, int RZ>
 struct Smem {
     static_assert(Geo<R, RZ, TY_A>::SLOT * 4 % 128 == 0 && Geo<R, RZ, TY_C>::SLOT * 4 % 128 == 0 &&
-                      Geo<R, RZ, TY_C, 2>::SLOT * 2 % 128 == 0 && Geo<R, RZ, TY_A>::SLOT1 * 4 % 128 == 0 &&
-                      Geo<R, RZ, TY_C>::SLOT1 * 4 % 128 == 0,
+                      Geo<R, RZ, TY_C, 2>::SLOT * 2 % 128 == 0,
                   "TMA slots must be multiples of 128 bytes");
     using A = Geo<R, RZ, TY_A>;
     using C = Geo<R, RZ, TY_C>;
@@ -204,7 +213,7 @@ struct Smem {
     static constexpr size_t gradient =
         sizeof(float) * (A::KZ * A::SLOT + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::KZ);
     static constexpr size_t curvature = CurvRing<R, RZ, 4>::SMEM;
-    // BF16 directions: g, d slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
+    // BF16 gradient: g slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
     static constexpr size_t curvature_bf = CurvRing<R, RZ, 2>::SMEM;
 };
 
@@ -727,7 +736,8 @@ __device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty
 }
 
 // ---------------------------------------------------------------------------
-// k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ).
+// k_residual: r = Hx - y (M_STORE_R) and/or the objective (M_OBJ); with
+// M_ZONE | M_STORE_R, H d_S of each slab item into the slab's zone buffer.
 // z-march unrolled over the ring (compile-time slots); z-combine and y-pass
 // with paired FP32 FMAs; each thread of the y-pass and of the epilogue owns
 // a 2 x 2 block of outputs (rows yo, yo+1; columns c, c+1).
@@ -748,12 +758,15 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
-    const float *yp = V.y;
+    // M_ZONE: the input is d masked to the slab, the output H d_S goes to the
+    // slab's zone buffer, and there is no observation term
+    const bool zone = (a.mode & M_ZONE) != 0;
+    const float *yp = zone ? nullptr : V.y;
     float *rp = V.r;
     const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool store_r = (a.mode & M_STORE_R) != 0;
-    const bool obj = (a.mode & M_OBJ) != 0;
+    const bool obj = (a.mode & M_OBJ) != 0 && !zone;
     // A stopped volume's item gets an empty range: no copies, no loop, zero
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
@@ -765,8 +778,8 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
-    const int xlo = max(0, zbeg), xhi = min(nz, zend);
-    const CUtensorMap *mx = &a.maps[sg.vol].m[TM_X_R];
+    const int xlo = max(zone ? sg.z0 : 0, zbeg), xhi = min(zone ? sg.z1 : nz, zend);
+    const CUtensorMap *mx = &a.maps[sg.vol].m[zone ? TM_D_X : TM_X_R];
     if (tid == 0)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mx)) : "memory");
     const uint32_t nb = (uint32_t)(BX * BY * sizeof(float));
@@ -854,7 +867,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         ypass_pair2<R>(T1, yo, c, fyc, h0, h1);
         const float2 r0 = make_float2(h0.x - y0v.x, h0.y - y0v.y), r1 = make_float2(h1.x - y1v.x, h1.y - y1v.y);
         if (store_r) {
-            float *rrow = rp + (long long)zo * plane;
+            float *rrow = zone ? sg.hd + (long long)(zo - sg.hz0) * plane : rp + (long long)zo * plane;
             if (r0ok && c0ok) {
                 if (c1ok) *reinterpret_cast<float2 *>(rrow + o0) = r0;
                 else rrow[o0] = r0.x;
@@ -1201,29 +1214,29 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
 }
 
 // ---------------------------------------------------------------------------
-// k_curvature: nine inner products of the restricted subspace system and, in
+// k_curvature: the inner products of the restricted subspace system and, in
 // the last CTA, the per-slab 2x2 solve.
 //   acc: 0 g.g  1 g.d  2 d.d  3 Hg.Hg  4 Hg.Hd  5 Hd.Hd
 //        6 sum w (Vg)^2  7 sum w Vg Vd  8 sum w (Vd)^2   9 ||x_S||^2
-// g_S, d_S are g, d masked to the slab's slices [z0, z1) (zero-filled slots).
-// The slices of g and d share one mbarrier per ring slot; the z-march is
+// g_S is g masked to the slab's slices [z0, z1) (zero-filled ring slots);
+// d_S is d masked the same way, read through the L1 cache with x.  H g_S is
+// formed on the fly over the slab's zone and written to its zone buffer (the
+// update needs it); H d_S comes from the zone buffer.  The z-march is
 // unrolled over the ring (compile-time slots); the z-combine and the y-pass
 // use paired FP32 FMAs; each thread of the y-pass and of the epilogue owns a
-// pair of adjacent columns of one output row; x for the weights is read
-// through the L1 cache.
+// pair of adjacent columns of one output row.
 // ---------------------------------------------------------------------------
 template <int R, int RZ, bool BF>
 __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curvature(KArgs a) {
-    using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // direction storage
+    using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
     using G = Geo<R, RZ, TY_C, sizeof(T)>;
     constexpr int PF = CurvRing<R, RZ, sizeof(T)>::PF;    // slices in flight ahead of the consumer
     constexpr int NS = CurvRing<R, RZ, sizeof(T)>::NS, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
     extern __shared__ __align__(128) float smem[];
-    T *sgs = reinterpret_cast<T *>(smem);                // NS * SLOT (g)
-    T *sds = sgs + NS * SLOT;                            // NS * SLOT (d)
-    float *Wb = reinterpret_cast<float *>(sds + NS * SLOT);   // [g, d][BY * BX]
-    float *T1b = Wb + 2 * BY * BX;                            // [g, d][BY * TX]
-    float *CF = T1b + 2 * BY * TX;
+    T *sgs = reinterpret_cast<T *>(smem);                     // NS * SLOT (g)
+    float *W = reinterpret_cast<float *>(sgs + NS * SLOT);    // BY * BX
+    float *T1 = W + BY * BX;                                  // BY * TX
+    float *CF = T1 + BY * TX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_OUT_FLOATS);
 
     const Item it = a.items[blockIdx.x];
@@ -1231,7 +1244,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
-    const float *xg = V.x;
+    const float *xg = V.x, *dg = V.d;
     const float delta2 = V.delta2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
@@ -1247,29 +1260,22 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     stage_coeffs<G>(CF, V, it.zo0, it.zo1 - it.zo0);   // rows of the output slices only
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
-    const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R], *md = &a.maps[sg.vol].m[TM_D_R];
-    if (tid == 0) {
-        // the descriptors sit in global memory and may have been rewritten since an earlier launch
+    const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R];
+    if (tid == 0)   // the descriptor sits in global memory and may have been rewritten since an earlier launch
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mg)) : "memory");
-        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(md)) : "memory");
-    }
     const uint32_t nb = (uint32_t)(BX * BY * sizeof(T));
     const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
     constexpr int FILL = (int)(SLOT * sizeof(T) / 16);
-    // slice z of g_S and d_S into ring slot s: TMA copies when z is a slab slice, else zeros
+    // slice z of g_S into ring slot s: a TMA copy when z is a slab slice, else zeros
     auto issue = [&](int z, int s) {
         if (z >= glo && z < ghi) {
             if (tid == 0) {
-                mbar_expect_tx(bar + s, 2 * nb);
+                mbar_expect_tx(bar + s, nb);
                 tma_load_3d(sgs + s * SLOT, mg, bx0, by0, z, bar + s);
-                tma_load_3d(sds + s * SLOT, md, bx0, by0, z, bar + s);
             }
         } else {
-            float4 *pg = reinterpret_cast<float4 *>(sgs + s * SLOT), *pd = reinterpret_cast<float4 *>(sds + s * SLOT);
-            for (int i = tid; i < FILL; i += NT) {
-                pg[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                pd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            float4 *pg = reinterpret_cast<float4 *>(sgs + s * SLOT);
+            for (int i = tid; i < FILL; i += NT) pg[i] = make_float4(0.f, 0.f, 0.f, 0.f);
             // order these generic writes before any later TMA write into the slot
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
@@ -1291,18 +1297,19 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     const int gy = it.ty0 + yo, gx = it.tx0 + c;
     const bool v0 = gy < ny && gx < nx, v1 = gy < ny && gx + 1 < nx;
     const bool xe0 = gx + 1 < nx, xe1 = gx + 2 < nx, ye = gy + 1 < ny;
-    // x offsets for the weights (clamped to the voxel itself where the neighbour does not exist)
+    // offsets of x and d for the weights and differences (clamped to the voxel
+    // itself where the neighbour does not exist); pitch is a multiple of 8, so
+    // the pair (c, c+1) never crosses a row
     const long long n0 = v0 ? (long long)gy * pitch + gx : 0;
     const long long n2 = xe1 ? n0 + 2 : n0;
     const long long ny0 = ye ? n0 + pitch : n0;
     const int ci = (yo + R) * BX + XH + c;                // staged index of column c
-    float *Wg = Wb, *Wd = Wb + BY * BX, *T1g = T1b, *T1d = T1b + BY * TX;
     uint32_t par = 0u;
     bool timed_out = false;
     int zi = zbeg;
 
     // Step for slice zi (ring slot S): z-combine of output zo = zi - RZ; barrier;
-    // x-pass; barrier; y-pass, products and weights of zo.
+    // x-pass; barrier; y-pass, H g_S out, products and weights of zo.
     auto step = [&](auto sc) -> bool {
         constexpr int S = decltype(sc)::value;
         if (zi >= zend) return false;
@@ -1314,9 +1321,11 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
             ok = mbar_wait(bar + S, (par >> S) & 1u);
             if (ok) par ^= 1u << S;
         }
-        // x of this thread's voxels at zo (and zo + 1), fetched early
-        float2 x0 = make_float2(0.f, 0.f), xy = x0, xz = x0;
-        float x2 = 0.f;
+        // H d_S, x and d_S of this thread's voxels at zo (and zo + 1), fetched early
+        float2 hd = make_float2(0.f, 0.f);
+        if (emit && v0) hd = __ldg(reinterpret_cast<const float2 *>(sg.hd + (long long)(zo - sg.hz0) * plane + n0));
+        float2 x0 = make_float2(0.f, 0.f), xy = x0, xz = x0, d0 = x0, dy = x0, dz = x0;
+        float x2 = 0.f, d2 = 0.f;
         if (pen) {
             const long long zoff = (long long)zo * plane;
             const long long zn = zo + 1 < nz ? plane : 0;
@@ -1324,6 +1333,12 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
             x2 = __ldg(xg + zoff + n2);
             xy = __ldg(reinterpret_cast<const float2 *>(xg + zoff + ny0));
             xz = __ldg(reinterpret_cast<const float2 *>(xg + zoff + zn + n0));
+            if (zo >= sg.z0) {            // d_S is zero below the slab
+                d0 = __ldg(reinterpret_cast<const float2 *>(dg + zoff + n0));
+                d2 = __ldg(dg + zoff + n2);
+                dy = __ldg(reinterpret_cast<const float2 *>(dg + zoff + ny0));
+            }
+            if (zo + 1 < sg.z1) dz = __ldg(reinterpret_cast<const float2 *>(dg + zoff + zn + n0));
         }
         const float *cfr = CF + (zo - it.zo0) * G::CFS;
         if (emit && zu) {
@@ -1332,10 +1347,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
 #pragma unroll
             for (int j = 0; j < ZP; ++j) {
                 const int u = 4 * (tid + j * NT);
-                if (j == 0 || tid + j * NT < G::ZUNITS) {
-                    zcomb_ring<KZ, NS, S, SLOT>(sgs + u, fzc, Wg + u);
-                    zcomb_ring<KZ, NS, S, SLOT>(sds + u, fzc, Wd + u);
-                }
+                if (j == 0 || tid + j * NT < G::ZUNITS) zcomb_ring<KZ, NS, S, SLOT>(sgs + u, fzc, W + u);
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -1354,15 +1366,16 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
         if (xu) {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);
-            xpass_unit<G, R, -1>(Wg, T1g, xsrc, xdst, fxc);
-            xpass_unit<G, R, -1>(Wd, T1d, xsrc, xdst, fxc);
+            xpass_unit<G, R, -1>(W, T1, xsrc, xdst, fxc);
         }
         __syncthreads();
         float fyc[G::KXY];
         row_coeffs(fyc, cfr + G::KXYP);
-        const float2 hg = ypass_pair<R>(T1g, yo, c, fyc);
-        const float2 hd = ypass_pair<R>(T1d, yo, c, fyc);
+        const float2 hg = ypass_pair<R>(T1, yo, c, fyc);
         if (v0) {
+            float *hrow = sg.hg + (long long)(zo - sg.hz0) * plane + n0;
+            if (v1) *reinterpret_cast<float2 *>(hrow) = hg;
+            else hrow[0] = hg.x;
             acc[3] = fmaf(hg.x, hg.x, acc[3]);
             acc[4] = fmaf(hg.x, hd.x, acc[4]);
             acc[5] = fmaf(hd.x, hd.x, acc[5]);
@@ -1374,33 +1387,31 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
         }
         if (pen) {
             constexpr int s0 = (S - RZ + NS) % NS, s1 = (S - RZ + 1 + NS) % NS;   // slices zo, zo + 1
-            const T *g0 = sgs + s0 * SLOT + ci, *d0 = sds + s0 * SLOT + ci;
-            const T *g1 = sgs + s1 * SLOT + ci, *d1 = sds + s1 * SLOT + ci;
-            const float2 gc = ld2(g0), dc = ld2(d0), gyv = ld2(g0 + BX), dyv = ld2(d0 + BX);
-            const float2 gzv = ld2(g1), dzv = ld2(d1);
-            const float gr = to_f(g0[2]), dr = to_f(d0[2]);
+            const T *g0 = sgs + s0 * SLOT + ci, *g1 = sgs + s1 * SLOT + ci;
+            const float2 gc = ld2(g0), gyv = ld2(g0 + BX), gzv = ld2(g1);
+            const float gr = to_f(g0[2]);
             const bool inslab = zo >= sg.z0, ze = zo + 1 < nz;
             // voxel c
             if (inslab) {
                 acc[0] = fmaf(gc.x, gc.x, acc[0]);
-                acc[1] = fmaf(gc.x, dc.x, acc[1]);
-                acc[2] = fmaf(dc.x, dc.x, acc[2]);
+                acc[1] = fmaf(gc.x, d0.x, acc[1]);
+                acc[2] = fmaf(d0.x, d0.x, acc[2]);
                 acc[9] = fmaf(x0.x, x0.x, acc[9]);
             }
-            if (xe0) pen_axis(x0.x, x0.y, gc.x, gc.y, dc.x, dc.y, delta2, acc);
-            if (ye) pen_axis(x0.x, xy.x, gc.x, gyv.x, dc.x, dyv.x, delta2, acc);
-            if (ze) pen_axis(x0.x, xz.x, gc.x, gzv.x, dc.x, dzv.x, delta2, acc);
+            if (xe0) pen_axis(x0.x, x0.y, gc.x, gc.y, d0.x, d0.y, delta2, acc);
+            if (ye) pen_axis(x0.x, xy.x, gc.x, gyv.x, d0.x, dy.x, delta2, acc);
+            if (ze) pen_axis(x0.x, xz.x, gc.x, gzv.x, d0.x, dz.x, delta2, acc);
             // voxel c + 1
             if (v1) {
                 if (inslab) {
                     acc[0] = fmaf(gc.y, gc.y, acc[0]);
-                    acc[1] = fmaf(gc.y, dc.y, acc[1]);
-                    acc[2] = fmaf(dc.y, dc.y, acc[2]);
+                    acc[1] = fmaf(gc.y, d0.y, acc[1]);
+                    acc[2] = fmaf(d0.y, d0.y, acc[2]);
                     acc[9] = fmaf(x0.y, x0.y, acc[9]);
                 }
-                if (xe1) pen_axis(x0.y, x2, gc.y, gr, dc.y, dr, delta2, acc);
-                if (ye) pen_axis(x0.y, xy.y, gc.y, gyv.y, dc.y, dyv.y, delta2, acc);
-                if (ze) pen_axis(x0.y, xz.y, gc.y, gzv.y, dc.y, dzv.y, delta2, acc);
+                if (xe1) pen_axis(x0.y, x2, gc.y, gr, d0.y, d2, delta2, acc);
+                if (ye) pen_axis(x0.y, xy.y, gc.y, gyv.y, d0.y, dy.y, delta2, acc);
+                if (ze) pen_axis(x0.y, xz.y, gc.y, gzv.y, d0.y, dz.y, delta2, acc);
             }
         }
         return true;

@@ -147,7 +147,7 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     if (!encode_map(&vm.m[TM_X_R], x, 4, p->nx, p->ny, p->nz, p->nx, bx, TY_A + 2 * ks->R))
         return fail(BD3MG_ECUDA, "cuTensorMapEncodeTiled failed");
     std::memcpy(g_host + o_maps, &vm, sizeof(vm));
-    const SegDev sg{0, 0, p->nz, 0};
+    const SegDev sg{0, 0, p->nz, 0, 0, 0, nullptr, nullptr};
     std::memcpy(g_host + o_seg, &sg, sizeof(sg));
     Item *items = reinterpret_cast<Item *>(g_host + o_items);
     long long k = 0;

@@ -1,5 +1,5 @@
 """GPU tests of the runtime around the iteration: checkpoint / resume, precision
-escalation of the BF16-direction form, and the z-chunk autotuner."""
+escalation of the BF16-gradient form, and the z-chunk autotuner."""
 import json
 
 import numpy as np
@@ -47,11 +47,11 @@ def test_checkpoint_of_another_shape_is_rejected(cuda_lib, tmp_path):
         assert e.value.status == 1
 
 
-def test_escalation_switches_to_fp32_directions_and_keeps_descending(cuda_lib):
+def test_escalation_switches_to_fp32_gradient_and_keeps_descending(cuda_lib):
     p = _prob(seed=2)
     with cuda_lib.Solver.from_problem(p) as s32:
         f32 = s32.iterate(300)[-1]
-    with cuda_lib.Solver.from_problem(p, precision=cuda_lib.BF16_DIRECTIONS) as s:
+    with cuda_lib.Solver.from_problem(p, precision=cuda_lib.BF16_GRADIENT) as s:
         assert s.escalated() == -1
         s.set_escalation(1e-5)
         tr = s.iterate(300)
