@@ -75,6 +75,25 @@ def test_slab_colouring_rules(lib):
         binding.bd3mg_plan_slab_colours([0, 3, 3, 5], 3)
 
 
+def test_same_colour_zones_are_disjoint(lib):
+    """The update adds H D u to r over each slab's zone [z0 - max(rz, 1), z1 + rz)
+    for all slabs of a colour in one launch: the colouring must make those zones
+    disjoint (one writer per voxel of r), for every slab layout and PSF depth."""
+    rng = np.random.default_rng(1)
+    for _ in range(200):
+        t = rng.integers(1, 10, size=rng.integers(2, 14))
+        b = list(np.concatenate([[0], np.cumsum(t)]))
+        nz = b[-1]
+        pz = int(rng.choice([1, 3, 5, 7, 9, 11]))
+        rz = (pz - 1) // 2
+        col, nc = binding.bd3mg_plan_slab_colours(b, pz)
+        for c in range(nc):
+            cover = np.zeros(nz, np.int64)
+            for s in np.nonzero(col == c)[0]:
+                cover[max(0, b[s] - max(rz, 1)):min(nz, b[s + 1] + rz)] += 1
+            assert cover.max() <= 1, (b, pz, col)
+
+
 def test_psf_factoring(lib):
     fx, fy, fz = synth.gaussian_factors(6, 7, 5, 3, 0.5, 3.0, 1.0)
     psf = synth.dense_psf(fx, fy, fz)
