@@ -349,7 +349,7 @@ class Solver:
         self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
 
     def escalated(self) -> int:
-        """Iteration count at which the context switched to FP32 directions, or -1."""
+        """Iteration count at which the context switched to an FP32 gradient, or -1."""
         at = ctypes.c_longlong()
         self._c(self._lib.bd3mg_escalated(self._ctx, ctypes.byref(at)))
         return int(at.value)
@@ -510,7 +510,7 @@ class BatchSolver:
         self._c(self._lib.bd3mg_set_escalation(self._ctx, float(tol)))
 
     def escalated(self) -> int:
-        """Iteration count at which the context switched to FP32 directions, or -1."""
+        """Iteration count at which the context switched to an FP32 gradient, or -1."""
         at = ctypes.c_longlong()
         self._c(self._lib.bd3mg_escalated(self._ctx, ctypes.byref(at)))
         return int(at.value)

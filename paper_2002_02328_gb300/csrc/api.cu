@@ -91,7 +91,7 @@ struct bd3mg_ctx {
 
     // device state
     float *scr_in = nullptr, *scr_out = nullptr;   // operator-call scratch for volume 0 (lazy)
-    float *scr_dir = nullptr;                        // FP32 copy-out of BF16 directions (lazy)
+    float *scr_dir = nullptr;                        // FP32 copy-out of a BF16 gradient (lazy)
     VolDev *vols = nullptr;         // [0, nvol) volumes, [nvol] scratch for operator calls
     VolMaps *maps = nullptr;        // TMA descriptors, same indexing as vols
     SegDev *segs = nullptr;
@@ -127,7 +127,7 @@ struct bd3mg_ctx {
     long long iterations = 0;
     // precision escalation of the BF16-direction form (0: off)
     double esc_tol = 0.0;
-    long long esc_at = -1;          // iteration count at which the context switched to FP32 directions
+    long long esc_at = -1;          // iteration count at which the context switched to an FP32 gradient
 };
 
 namespace {
@@ -814,7 +814,7 @@ bd3mg_status copy_vol(bd3mg_ctx *c, const VolState &v, float *dst, const float *
     return BD3MG_OK;
 }
 
-// FP32 copy of a BF16 direction array of volume v in a scratch buffer (sized
+// FP32 copy of a BF16 gradient array of volume v in a scratch buffer (sized
 // for the largest volume, allocated on first use).
 bd3mg_status dir_as_float(bd3mg_ctx *c, const VolState &v, const __nv_bfloat16 *src, const float **out) {
     size_t need = 0;

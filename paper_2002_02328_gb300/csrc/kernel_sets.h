@@ -16,11 +16,11 @@ typedef cudaError_t (*prep_fn)();
 
 struct KernelSet {
     int R, RZ;
-    launch_fn residual, gradient, curvature;        // FP32 directions
-    launch_fn gradient_bf, curvature_bf;            // BF16 directions
+    launch_fn residual, gradient, curvature;        // FP32 gradient
+    launch_fn gradient_bf, curvature_bf;            // BF16 gradient
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
     // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
-    // 3 gradient (BF16 directions), 4 curvature (BF16 directions)
+    // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient)
     int (*occupancy)(int kind);
 };
 

@@ -169,6 +169,6 @@ def test_slab_form_with_short_chunks_matches_oracle(cuda_lib, prec, zchunk):
     if prec == 0:
         assert _rel(x, xr) <= 2e-5
         assert np.max(np.abs(tr - fr) / np.abs(fr)) <= 1e-5
-    else:                                  # BF16 directions: descent and closeness to the FP32 oracle path
+    else:                                  # BF16 gradient: descent and closeness to the FP32 oracle path
         assert np.all(np.diff(tr) <= 1e-6 * np.abs(tr[1:]))
         assert np.max(np.abs(tr - fr) / np.abs(fr)) <= 1e-3
