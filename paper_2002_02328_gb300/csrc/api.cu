@@ -175,8 +175,9 @@ bd3mg_status dalloc_n(bd3mg_ctx *c, T **p, size_t count) {
 // Staged-tile x halo of a kernel set (must match Geo<R,RZ,TY>::XH in kernels.cuh).
 int set_xh(const KernelSet *k, int esize = 4) { return (esize == 4 && k->R <= 4) ? 4 : 8; }
 
-// Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
-int tile_y(int kind) { return kind == 2 ? TY_C : TY_A; }
+// Tile height of the curvature kernel for a gradient of g_esize bytes (must
+// match CurvRing<R,RZ,EB>::TY in kernels.cuh).
+int curv_ty(int g_esize) { return g_esize == 2 ? 2 * TY_C : TY_C; }
 
 // g: FP32 or (g_esize 2) BF16 gradient; d: FP32 memory direction.
 bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const float *x, const float *r,
@@ -187,13 +188,16 @@ bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const f
     bool ok = true;
     if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
     if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, g_esize, p.nx, p.ny, p.nz, v.pitch, bxg, TY_C + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, g_esize, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(g_esize) + 2 * R);
     if (d) ok = ok && encode_map(&vm->m[TM_D_X], d, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
     return ok;
 }
 
-// Kernel kind used for occupancy: BF16-direction gradient/curvature have their own.
+// Kernel kind used for occupancy: BF16-gradient gradient/curvature have their own.
 int occ_kind(const bd3mg_ctx *c, int kind) { return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind; }
+
+// Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
+int tile_y(const bd3mg_ctx *c, int kind) { return kind == 2 ? curv_ty(c->bf ? 2 : 4) : TY_A; }
 
 int ntiles_of(const VolState &v, int ty) { return ((v.p.nx + TX - 1) / TX) * ((v.p.ny + ty - 1) / ty); }
 
@@ -250,7 +254,7 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode
     for (int s : segs) {
         int lo, hi;
         range(s, &lo, &hi);
-        ranges.push_back({lo, hi, ntiles_of(c->V[c->segs_h[s].vol], tile_y(kind))});
+        ranges.push_back({lo, hi, ntiles_of(c->V[c->segs_h[s].vol], tile_y(c, kind))});
     }
     // zc_io > 0: reuse that chunk (a re-plan keeps every item, and so every sum, as it was)
     const int zc = (zc_io && *zc_io > 0) ? *zc_io : choose_zc(c, ranges, kind);
@@ -272,7 +276,7 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode
             c->slot_id_h.push_back(c->segs_h[s].vol);
             last_vol = c->segs_h[s].vol;
         }
-        add_items(c, s, ranges[i][0], ranges[i][1], zc, tile_y(kind));
+        add_items(c, s, ranges[i][0], ranges[i][1], zc, tile_y(c, kind));
     }
     if (slots != SLOTS_NONE) {
         L.nslots = (int)c->slot_id_h.size() - L.slot_off;
@@ -528,9 +532,13 @@ bd3mg_status capture_graph(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active);
+bd3mg_status upload_work_lists(bd3mg_ctx *c);
+
 // Switch a BF16-gradient context to an FP32 gradient: FP32 g arrays (g is
 // recomputed by the next iteration; d, r and the zone buffers are FP32 in both
-// forms), FP32 descriptors, and a new iteration graph.
+// forms), the FP32 curvature kernel's work lists (lower tiles, same z-chunks),
+// FP32 descriptors, and a new iteration graph.
 bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     if (!c->bf) return BD3MG_OK;
     bd3mg_status st;
@@ -539,6 +547,8 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
         CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
     }
     c->bf = false;
+    build_colour_launches(c, c->plan_active);       // the FP32 kernel's curvature tiles
+    if ((st = upload_work_lists(c))) return st;
     if ((st = upload_descriptors(c))) return st;
     c->esc_at = c->iterations;
     return capture_graph(c);
@@ -703,6 +713,16 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     c->base_beg = c->slot_beg_h.size();
     c->base_slot = c->slot_id_h.size();
     build_colour_launches(c, std::vector<char>(nvol, 1));
+    // A BF16-gradient context may escalate to an FP32 gradient, whose curvature
+    // tiles are lower (more items): size the device work list for both layouts.
+    size_t items_cap = c->items_h.size();
+    if (c->bf) {
+        c->bf = false;
+        build_colour_launches(c, std::vector<char>(nvol, 1));
+        items_cap = std::max(items_cap, c->items_h.size());
+        c->bf = true;
+        build_colour_launches(c, std::vector<char>(nvol, 1));
+    }
 
     cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
@@ -743,7 +763,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         }
     }
     AL(c->vols, nvol + 1); AL(c->maps, nvol + 1); AL(c->segs, nseg);
-    AL(c->items, c->items_h.size());
+    AL(c->items, items_cap);
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
     AL(c->partials, (size_t)c->max_items * 10);    // up to 10 partial sums per item

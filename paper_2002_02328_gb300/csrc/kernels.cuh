@@ -61,7 +61,7 @@ namespace bd3mg {
 
 constexpr int TX = 32;            // tile width  (x, one warp lane per column)
 constexpr int TY_A = 32;          // tile height of k_residual / k_gradient
-constexpr int TY_C = 16;          // tile height of k_curvature
+constexpr int TY_C = 16;          // tile height of k_curvature per output row of a thread (see CurvRing)
 constexpr int NT = 256;           // threads per CTA
 constexpr int NWARP = NT / 32;
 constexpr int PREF = 2;           // slices in flight ahead of the consumer (>= 2, see Pipe)
@@ -184,30 +184,37 @@ struct Geo {
     static constexpr size_t bars_bytes(int n) { return ((n * 8 + 127) / 128) * 128; }
 };
 
-// Ring of k_curvature: KZ + PF slots of g.  Two slices in flight when four
-// CTAs still share an SM, otherwise one; the launch bounds ask registers for
-// four CTAs per SM where the shared memory allows it, else three (or two).
+// Geometry of k_curvature.  Each thread owns RPT output rows of a pair of
+// columns, so a tile is TY_C * RPT rows high: one row with an FP32 gradient
+// (16-row tiles, whose small ring lets four CTAs share an SM at 64 registers),
+// two with a BF16 gradient (32-row tiles; half the per-step overhead per voxel,
+// three CTAs).  The ring holds KZ + PF slots of g, two slices in flight where
+// that keeps the CTA count, else one.
 template <int R, int RZ, int EB>
 struct CurvRing {
-    using C = Geo<R, RZ, TY_C, EB>;
+    static constexpr int RPT = EB == 2 ? 2 : 1;
+    static constexpr int TY = TY_C * RPT;
+    using C = Geo<R, RZ, TY, EB>;
     static constexpr size_t bytes(int pf) {
         return (size_t)EB * ((C::KZ + pf) * C::SLOT) + sizeof(float) * (C::BY * C::BX + C::BY * TX + C::CF_OUT_FLOATS) +
                C::bars_bytes(C::KZ + pf);
     }
-    static constexpr int PF = bytes(2) <= 55 * 1024 ? 2 : 1;
+    static constexpr size_t KB = 1024;
+    static constexpr int PF = RPT == 1 ? (bytes(2) <= 55 * KB ? 2 : 1) : (bytes(2) <= 74 * KB ? 2 : 1);
     static constexpr int NS = C::KZ + PF;
     static constexpr size_t SMEM = bytes(PF);
-    static constexpr int CTAS = SMEM <= 55 * 1024 ? 4 : (SMEM <= 74 * 1024 ? 3 : 2);
+    // CTAs per SM the launch bounds ask registers for (z kernels longer than 7
+    // taps keep more of the ring window in registers)
+    static constexpr int CTAS = RPT == 1 ? (SMEM <= 55 * KB ? 4 : (SMEM <= 74 * KB ? 3 : 2))
+                                         : (SMEM <= 74 * KB && C::KZ <= 7 ? 3 : 2);
 };
 
 template <int R, int RZ>
 struct Smem {
-    static_assert(Geo<R, RZ, TY_A>::SLOT * 4 % 128 == 0 && Geo<R, RZ, TY_C>::SLOT * 4 % 128 == 0 &&
-                      Geo<R, RZ, TY_C, 2>::SLOT * 2 % 128 == 0,
+    static_assert(Geo<R, RZ, TY_A>::SLOT * 4 % 128 == 0 && CurvRing<R, RZ, 4>::C::SLOT * 4 % 128 == 0 &&
+                      CurvRing<R, RZ, 2>::C::SLOT * 2 % 128 == 0,
                   "TMA slots must be multiples of 128 bytes");
     using A = Geo<R, RZ, TY_A>;
-    using C = Geo<R, RZ, TY_C>;
-    using CB = Geo<R, RZ, TY_C, 2>;
     static constexpr size_t residual =
         sizeof(float) * (A::NSF * A::SLOT + A::BY * A::BX + A::BY * TX + A::CF_FLOATS) + A::bars_bytes(A::NSF);
     static constexpr size_t gradient =
@@ -1223,15 +1230,19 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
 // formed on the fly over the slab's zone and written to its zone buffer (the
 // update needs it); H d_S comes from the zone buffer.  The z-march is
 // unrolled over the ring (compile-time slots); the z-combine and the y-pass
-// use paired FP32 FMAs; each thread of the y-pass and of the epilogue owns a
-// pair of adjacent columns of one output row.
+// use paired FP32 FMAs; each thread of the y-pass and of the epilogue owns RPT
+// rows of a pair of adjacent columns (CurvRing).  With two rows the
+// half-quadratic terms are formed between the two barriers of a step, before
+// the convolution's registers are needed; with one, after the y-pass.
 // ---------------------------------------------------------------------------
 template <int R, int RZ, bool BF>
 __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
-    using G = Geo<R, RZ, TY_C, sizeof(T)>;
-    constexpr int PF = CurvRing<R, RZ, sizeof(T)>::PF;    // slices in flight ahead of the consumer
-    constexpr int NS = CurvRing<R, RZ, sizeof(T)>::NS, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
+    using CR = CurvRing<R, RZ, sizeof(T)>;
+    using G = typename CR::C;
+    constexpr int PF = CR::PF;                        // slices in flight ahead of the consumer
+    constexpr int RPT = CR::RPT;                      // output rows per thread
+    constexpr int NS = CR::NS, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
     extern __shared__ __align__(128) float smem[];
     T *sgs = reinterpret_cast<T *>(smem);                     // NS * SLOT (g)
     float *W = reinterpret_cast<float *>(sgs + NS * SLOT);    // BY * BX
@@ -1287,67 +1298,132 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     float acc[10];
 #pragma unroll
     for (int p = 0; p < 10; ++p) acc[p] = 0.f;
-    constexpr int ZP = Units<G::ZUNITS>::PER;      // z-combine units per thread (1 or 2)
-    static_assert(G::XUNITS <= NT, "one x-pass unit per thread");
-    const bool zu = tid < G::ZUNITS, xu = tid < G::XUNITS;
-    int xsrc, xdst;
-    xpass_offsets<G>(tid, xsrc, xdst);
-    // y-pass / epilogue: output row yo, columns c, c+1
-    const int yo = 2 * warp + (lane >> 4), c = 2 * (lane & 15);
-    const int gy = it.ty0 + yo, gx = it.tx0 + c;
-    const bool v0 = gy < ny && gx < nx, v1 = gy < ny && gx + 1 < nx;
-    const bool xe0 = gx + 1 < nx, xe1 = gx + 2 < nx, ye = gy + 1 < ny;
-    // offsets of x and d for the weights and differences (clamped to the voxel
-    // itself where the neighbour does not exist); pitch is a multiple of 8, so
-    // the pair (c, c+1) never crosses a row
-    const long long n0 = v0 ? (long long)gy * pitch + gx : 0;
-    const long long n2 = xe1 ? n0 + 2 : n0;
-    const long long ny0 = ye ? n0 + pitch : n0;
-    const int ci = (yo + R) * BX + XH + c;                // staged index of column c
+    constexpr int ZP = Units<G::ZUNITS>::PER, XP = Units<G::XUNITS>::PER;
+    int xsrc[XP], xdst[XP];
+#pragma unroll
+    for (int j = 0; j < XP; ++j) xpass_offsets<G>(tid + j * NT, xsrc[j], xdst[j]);
+    // y-pass / epilogue: rows yo .. yo+RPT-1, columns c, c+1
+    const int yo = RPT * (2 * warp + (lane >> 4)), c = 2 * (lane & 15);
+    const int gx = it.tx0 + c, gy = it.ty0 + yo;
+    const bool c0ok = gx < nx, c1ok = gx + 1 < nx;
+    const bool xe0 = gx + 1 < nx, xe1 = gx + 2 < nx;     // x neighbours of columns c, c+1
+    bool rok[RPT], yeo[RPT];                             // row yo+k exists; its y neighbour exists
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+        rok[k] = gy + k < ny;
+        yeo[k] = gy + k + 1 < ny;
+    }
+    const bool v00 = rok[0] && c0ok;                     // voxel (yo, c) exists; the others imply it
+    // offsets of x and d of rows yo .. yo+RPT (row yo+RPT only for the y
+    // differences), clamped to an existing voxel where a row or neighbour does
+    // not exist; pitch is a multiple of 8, so the pair (c, c+1) never crosses a row
+    long long orow[RPT + 1], oe[RPT];
+    orow[0] = v00 ? (long long)gy * pitch + gx : 0;
+#pragma unroll
+    for (int k = 1; k <= RPT; ++k) orow[k] = gy + k < ny ? orow[k - 1] + pitch : orow[k - 1];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) oe[k] = xe1 ? orow[k] + 2 : orow[k];
+    const int ci = (yo + R) * BX + XH + c;                // staged index of (yo, c)
     uint32_t par = 0u;
     bool timed_out = false;
     int zi = zbeg;
 
     // Step for slice zi (ring slot S): z-combine of output zo = zi - RZ; barrier;
-    // x-pass; barrier; y-pass, H g_S out, products and weights of zo.
+    // x-pass; barrier; y-pass, H g_S out, products; the half-quadratic terms of
+    // zo before the x-pass (RPT 2) or after the y-pass (RPT 1).
     auto step = [&](auto sc) -> bool {
         constexpr int S = decltype(sc)::value;
         if (zi >= zend) return false;
         const int zo = zi - RZ;
         const bool emit = zo >= it.zo0;
-        const bool pen = emit && v0 && zo >= pen_lo && zo < pen_hi;
+        const bool pen = emit && v00 && zo >= pen_lo && zo < pen_hi;
         bool ok = true;
         if (zi >= glo && zi < ghi) {
             ok = mbar_wait(bar + S, (par >> S) & 1u);
             if (ok) par ^= 1u << S;
         }
-        // H d_S, x and d_S of this thread's voxels at zo (and zo + 1), fetched early
-        float2 hd = make_float2(0.f, 0.f);
-        if (emit && v0) hd = __ldg(reinterpret_cast<const float2 *>(sg.hd + (long long)(zo - sg.hz0) * plane + n0));
-        float2 x0 = make_float2(0.f, 0.f), xy = x0, xz = x0, d0 = x0, dy = x0, dz = x0;
-        float x2 = 0.f, d2 = 0.f;
-        if (pen) {
-            const long long zoff = (long long)zo * plane;
-            const long long zn = zo + 1 < nz ? plane : 0;
-            x0 = __ldg(reinterpret_cast<const float2 *>(xg + zoff + n0));
-            x2 = __ldg(xg + zoff + n2);
-            xy = __ldg(reinterpret_cast<const float2 *>(xg + zoff + ny0));
-            xz = __ldg(reinterpret_cast<const float2 *>(xg + zoff + zn + n0));
-            if (zo >= sg.z0) {            // d_S is zero below the slab
-                d0 = __ldg(reinterpret_cast<const float2 *>(dg + zoff + n0));
-                d2 = __ldg(dg + zoff + n2);
-                dy = __ldg(reinterpret_cast<const float2 *>(dg + zoff + ny0));
-            }
-            if (zo + 1 < sg.z1) dz = __ldg(reinterpret_cast<const float2 *>(dg + zoff + zn + n0));
+        // x and d_S of the rows and their +x, +y, +z neighbours, and H d_S, fetched early
+        float2 xa[RPT + 1], da[RPT + 1], xz[RPT], dz[RPT], hd[RPT];
+        float xev[RPT], dev[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            xz[k] = dz[k] = hd[k] = make_float2(0.f, 0.f);
+            xev[k] = dev[k] = 0.f;
         }
+#pragma unroll
+        for (int k = 0; k <= RPT; ++k) xa[k] = da[k] = make_float2(0.f, 0.f);
+        if (pen) {
+            const float *xp = xg + (long long)zo * plane, *dp = dg + (long long)zo * plane;
+            const long long zn = zo + 1 < nz ? plane : 0;
+            const bool dlo = zo >= sg.z0, dhi = zo + 1 < sg.z1;     // d_S at zo, at zo + 1
+#pragma unroll
+            for (int k = 0; k <= RPT; ++k) {
+                xa[k] = __ldg(reinterpret_cast<const float2 *>(xp + orow[k]));
+                if (dlo) da[k] = __ldg(reinterpret_cast<const float2 *>(dp + orow[k]));
+            }
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                xev[k] = __ldg(xp + oe[k]);
+                xz[k] = __ldg(reinterpret_cast<const float2 *>(xp + zn + orow[k]));
+                if (dlo) dev[k] = __ldg(dp + oe[k]);
+                if (dhi) dz[k] = __ldg(reinterpret_cast<const float2 *>(dp + zn + orow[k]));
+            }
+        }
+        const long long zz = (long long)(zo - sg.hz0) * plane;       // slice zo in the zone buffers
+        if (emit && v00) {
+#pragma unroll
+            for (int k = 0; k < RPT; ++k)
+                if (rok[k]) hd[k] = __ldg(reinterpret_cast<const float2 *>(sg.hd + zz + orow[k]));
+        }
+        // half-quadratic terms and g, d products of the thread's voxels at zo
+        auto terms = [&]() {
+            constexpr int s0 = (S - RZ + NS) % NS, s1 = (S - RZ + 1 + NS) % NS;   // slices zo, zo + 1
+            const T *g0 = sgs + s0 * SLOT + ci, *g1 = sgs + s1 * SLOT + ci;
+            float2 ga[RPT + 1], gz[RPT];
+            float gev[RPT];
+#pragma unroll
+            for (int k = 0; k <= RPT; ++k) ga[k] = ld2(g0 + k * BX);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                gev[k] = to_f(g0[k * BX + 2]);
+                gz[k] = ld2(g1 + k * BX);
+            }
+            const bool inslab = zo >= sg.z0, ze = zo + 1 < nz;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (!rok[k]) continue;
+                // voxel (yo+k, c)
+                if (inslab) {
+                    acc[0] = fmaf(ga[k].x, ga[k].x, acc[0]);
+                    acc[1] = fmaf(ga[k].x, da[k].x, acc[1]);
+                    acc[2] = fmaf(da[k].x, da[k].x, acc[2]);
+                    acc[9] = fmaf(xa[k].x, xa[k].x, acc[9]);
+                }
+                if (xe0) pen_axis(xa[k].x, xa[k].y, ga[k].x, ga[k].y, da[k].x, da[k].y, delta2, acc);
+                if (yeo[k]) pen_axis(xa[k].x, xa[k + 1].x, ga[k].x, ga[k + 1].x, da[k].x, da[k + 1].x, delta2, acc);
+                if (ze) pen_axis(xa[k].x, xz[k].x, ga[k].x, gz[k].x, da[k].x, dz[k].x, delta2, acc);
+                // voxel (yo+k, c+1)
+                if (c1ok) {
+                    if (inslab) {
+                        acc[0] = fmaf(ga[k].y, ga[k].y, acc[0]);
+                        acc[1] = fmaf(ga[k].y, da[k].y, acc[1]);
+                        acc[2] = fmaf(da[k].y, da[k].y, acc[2]);
+                        acc[9] = fmaf(xa[k].y, xa[k].y, acc[9]);
+                    }
+                    if (xe1) pen_axis(xa[k].y, xev[k], ga[k].y, gev[k], da[k].y, dev[k], delta2, acc);
+                    if (yeo[k]) pen_axis(xa[k].y, xa[k + 1].y, ga[k].y, ga[k + 1].y, da[k].y, da[k + 1].y, delta2, acc);
+                    if (ze) pen_axis(xa[k].y, xz[k].y, ga[k].y, gz[k].y, da[k].y, dz[k].y, delta2, acc);
+                }
+            }
+        };
         const float *cfr = CF + (zo - it.zo0) * G::CFS;
-        if (emit && zu) {
+        if (emit) {
             float fzc[KZ];
             row_coeffs(fzc, cfr + 2 * G::KXYP);
 #pragma unroll
             for (int j = 0; j < ZP; ++j) {
                 const int u = 4 * (tid + j * NT);
-                if (j == 0 || tid + j * NT < G::ZUNITS) zcomb_ring<KZ, NS, S, SLOT>(sgs + u, fzc, W + u);
+                if (tid + j * NT < G::ZUNITS) zcomb_ring<KZ, NS, S, SLOT>(sgs + u, fzc, W + u);
             }
         }
         if (__syncthreads_or(!ok)) {
@@ -1363,56 +1439,41 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
             if (PF < 2 && (zi + PF - 1 < glo || zi + PF - 1 >= ghi)) __syncthreads();
             return true;
         }
-        if (xu) {
+        if constexpr (RPT == 2) {
+            if (pen) terms();
+        }
+        {
             float fxc[G::KXY];
             row_coeffs(fxc, cfr);
-            xpass_unit<G, R, -1>(W, T1, xsrc, xdst, fxc);
+#pragma unroll
+            for (int j = 0; j < XP; ++j)
+                if (tid + j * NT < G::XUNITS) xpass_unit<G, R, -1>(W, T1, xsrc[j], xdst[j], fxc);
         }
         __syncthreads();
         float fyc[G::KXY];
         row_coeffs(fyc, cfr + G::KXYP);
-        const float2 hg = ypass_pair<R>(T1, yo, c, fyc);
-        if (v0) {
-            float *hrow = sg.hg + (long long)(zo - sg.hz0) * plane + n0;
-            if (v1) *reinterpret_cast<float2 *>(hrow) = hg;
-            else hrow[0] = hg.x;
-            acc[3] = fmaf(hg.x, hg.x, acc[3]);
-            acc[4] = fmaf(hg.x, hd.x, acc[4]);
-            acc[5] = fmaf(hd.x, hd.x, acc[5]);
-        }
-        if (v1) {
-            acc[3] = fmaf(hg.y, hg.y, acc[3]);
-            acc[4] = fmaf(hg.y, hd.y, acc[4]);
-            acc[5] = fmaf(hd.y, hd.y, acc[5]);
-        }
-        if (pen) {
-            constexpr int s0 = (S - RZ + NS) % NS, s1 = (S - RZ + 1 + NS) % NS;   // slices zo, zo + 1
-            const T *g0 = sgs + s0 * SLOT + ci, *g1 = sgs + s1 * SLOT + ci;
-            const float2 gc = ld2(g0), gyv = ld2(g0 + BX), gzv = ld2(g1);
-            const float gr = to_f(g0[2]);
-            const bool inslab = zo >= sg.z0, ze = zo + 1 < nz;
-            // voxel c
-            if (inslab) {
-                acc[0] = fmaf(gc.x, gc.x, acc[0]);
-                acc[1] = fmaf(gc.x, d0.x, acc[1]);
-                acc[2] = fmaf(d0.x, d0.x, acc[2]);
-                acc[9] = fmaf(x0.x, x0.x, acc[9]);
-            }
-            if (xe0) pen_axis(x0.x, x0.y, gc.x, gc.y, d0.x, d0.y, delta2, acc);
-            if (ye) pen_axis(x0.x, xy.x, gc.x, gyv.x, d0.x, dy.x, delta2, acc);
-            if (ze) pen_axis(x0.x, xz.x, gc.x, gzv.x, d0.x, dz.x, delta2, acc);
-            // voxel c + 1
-            if (v1) {
-                if (inslab) {
-                    acc[0] = fmaf(gc.y, gc.y, acc[0]);
-                    acc[1] = fmaf(gc.y, d0.y, acc[1]);
-                    acc[2] = fmaf(d0.y, d0.y, acc[2]);
-                    acc[9] = fmaf(x0.y, x0.y, acc[9]);
+        float2 hg[RPT];
+        if constexpr (RPT == 2) ypass_pair2<R>(T1, yo, c, fyc, hg[0], hg[RPT - 1]);
+        else hg[0] = ypass_pair<R>(T1, yo, c, fyc);
+        if (v00) {
+            float *hgz = sg.hg + zz;
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                if (!rok[k]) continue;
+                if (c1ok) *reinterpret_cast<float2 *>(hgz + orow[k]) = hg[k];
+                else hgz[orow[k]] = hg[k].x;
+                acc[3] = fmaf(hg[k].x, hg[k].x, acc[3]);
+                acc[4] = fmaf(hg[k].x, hd[k].x, acc[4]);
+                acc[5] = fmaf(hd[k].x, hd[k].x, acc[5]);
+                if (c1ok) {
+                    acc[3] = fmaf(hg[k].y, hg[k].y, acc[3]);
+                    acc[4] = fmaf(hg[k].y, hd[k].y, acc[4]);
+                    acc[5] = fmaf(hd[k].y, hd[k].y, acc[5]);
                 }
-                if (xe1) pen_axis(x0.y, x2, gc.y, gr, d0.y, d2, delta2, acc);
-                if (ye) pen_axis(x0.y, xy.y, gc.y, gyv.y, d0.y, dy.y, delta2, acc);
-                if (ze) pen_axis(x0.y, xz.y, gc.y, gzv.y, d0.y, dz.y, delta2, acc);
             }
+        }
+        if constexpr (RPT == 1) {
+            if (pen) terms();
         }
         return true;
     };
