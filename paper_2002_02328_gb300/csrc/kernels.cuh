@@ -64,7 +64,8 @@ constexpr int TY_A = 32;          // tile height of k_residual / k_gradient
 constexpr int TY_C = 16;          // tile height of k_curvature per output row of a thread (see CurvRing)
 constexpr int NT = 256;           // threads per CTA
 constexpr int NWARP = NT / 32;
-constexpr int PREF = 2;           // slices in flight ahead of the consumer (>= 2, see Pipe)
+constexpr int PREF = 2;           // slices in flight ahead of the consumer (>= 2: a zero-filled slot is
+                                  // first read after a CTA barrier)
 constexpr int ZC_MAX = 48;        // max output slices per work item
 
 constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded mbarrier wait (2 s)
@@ -156,7 +157,6 @@ struct KArgs {
 
 template <int R, int RZ, int TY, int EB = 4>
 struct Geo {
-    static constexpr int RPW = TY / NWARP;            // y-pass outputs per thread
     // staged x halo: >= R and a multiple of 16 bytes of EB-byte elements (TMA x alignment)
     static constexpr int XH = (EB == 4 && R <= 4) ? 4 : 8;
     static constexpr int BX = TX + 2 * XH;            // staged tile width (TMA box x)
@@ -168,7 +168,6 @@ struct Geo {
     static constexpr int KXY = 2 * R + 1;
     static constexpr int KZ = 2 * RZ + 1;
     static constexpr int NSF = PREF + KZ;             // forward pipelines: the whole z window stays resident
-    static constexpr int NSA = PREF + 1;              // adjoint r pipeline
     // x-pass register blocking: outputs x0..x0+3 read staged columns
     // [x0+XH-R, x0+XH+3+R]; loaded as XNV float4 from x0+XA0.
     static constexpr int XA0 = (XH - R) & ~3;
@@ -276,87 +275,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-
-// A ring of NS shared-memory slots fed by TMA slice copies.  Slice z lives in
-// slot (z - first) mod NS.  Counters and parity bits are uniform across the
-// CTA; thread 0 issues the copies.  Slices outside [zlo, zhi) are zero-filled
-// by all threads when issued; with PREF >= 2 a CTA barrier always separates
-// that fill from the first read of the slot.
-template <int NS, int SLOTF, class T = float>
-struct Pipe {
-    T *buf;                       // NS slots of SLOTF elements
-    uint64_t *bar;
-    const CUtensorMap *map;
-    int x0, y0;                   // box origin (x0 is a multiple of 4)
-    int zlo, zhi;                 // slices [zlo, zhi) are copied; others are zero-filled
-    int first;                    // slice in slot 0
-    uint32_t bytes;               // bytes per copy (box size)
-    int fill;                     // 16-byte chunks to zero-fill per slot
-    uint32_t par;
-    int next_issue, next_wait, issue_slot, wait_slot;
-
-    __device__ void init(T *b, uint64_t *br, const CUtensorMap *m, int bx0, int by0, int lo, int hi,
-                         uint32_t nbytes, int first_slice) {
-        buf = b;
-        bar = br;
-        map = m;
-        x0 = bx0;
-        y0 = by0;
-        zlo = lo;
-        zhi = hi;
-        first = first_slice;
-        bytes = nbytes;
-        fill = (int)((nbytes + 15) / 16);
-        par = 0u;
-        next_issue = next_wait = first_slice;
-        issue_slot = wait_slot = 0;
-        // The descriptor sits in global memory and may have been rewritten since
-        // an earlier launch: order the tensormap proxy after those writes.
-        if (threadIdx.x == 0)
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(m))
-                         : "memory");
-    }
-    __device__ __forceinline__ bool loaded(int z) const { return z >= zlo && z < zhi; }
-    __device__ __forceinline__ int slot(int z) const { return (z - first) % NS; }
-    __device__ __forceinline__ const T *at(int z) const { return buf + slot(z) * SLOTF; }
-    // slot of slice z - back when s is the slot of z (0 <= back < NS)
-    __device__ __forceinline__ static int back_slot(int s, int back) {
-        const int t = s - back;
-        return t < 0 ? t + NS : t;
-    }
-    // All threads call; issues (or zero-fills) every slice in [next_issue, upto].
-    __device__ void issue_upto(int upto) {
-        for (; next_issue <= upto; ++next_issue) {
-            const int s = issue_slot;
-            issue_slot = (s + 1 == NS) ? 0 : s + 1;
-            if (loaded(next_issue)) {
-                if (threadIdx.x == 0) {
-                    uint64_t *b = bar + s;
-                    mbar_expect_tx(b, bytes);
-                    tma_load_3d(buf + s * SLOTF, map, x0, y0, next_issue, b);
-                }
-            } else {
-                float4 *d = reinterpret_cast<float4 *>(buf + s * SLOTF);
-                for (int i = threadIdx.x; i < fill; i += NT) d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-    }
-    // All threads call; waits for every copied slice in [next_wait, upto]; false on timeout.
-    __device__ bool wait_upto(int upto) {
-        bool ok = true;
-        for (; next_wait <= upto; ++next_wait) {
-            const int s = wait_slot;
-            wait_slot = (s + 1 == NS) ? 0 : s + 1;
-            if (loaded(next_wait)) {
-                ok = mbar_wait(bar + s, (par >> s) & 1u) && ok;
-                par ^= 1u << s;
-            }
-        }
-        return ok;
-    }
-    // Bounded wait for every copy issued and not yet consumed (used before leaving early).
-    __device__ void drain() { wait_upto(next_issue - 1); }
-};
 
 // Initialise n mbarriers (count 1).  Returns false (all threads) if the
 // dynamic shared memory is not 128-byte aligned, which TMA destinations need.
@@ -515,38 +433,12 @@ struct Units {
     static constexpr int PER = (UNITS + NT - 1) / NT;
 };
 
-// Window of the forward z-combine: the KZ staged slices zi, zi-1, ..., zi-2RZ
-// (slot s holds zi).
-template <int KZ, int NS, int SLOTF, class T>
-__device__ __forceinline__ void window(const Pipe<NS, SLOTF, T> &p, int s, const T *(&w)[KZ]) {
-#pragma unroll
-    for (int t = 0; t < KZ; ++t) w[t] = p.buf + Pipe<NS, SLOTF, T>::back_slot(s, t) * SLOTF;
-}
-
 __device__ __forceinline__ float4 load4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ float4 load4(const __nv_bfloat16 *p) {
     const uint2 q = *reinterpret_cast<const uint2 *>(p);
     const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
     const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
     return make_float4(a.x, a.y, b.x, b.y);
-}
-
-// Forward z-combine of one unit (4 staged columns at float offset off):
-// W = sum_t fz[t] * v(zi - t) = sum_c fz_zo(c) v(zo - c).
-template <int KZ, class T>
-__device__ __forceinline__ void zcomb_unit(const T *const (&w)[KZ], int off, const float (&fzc)[KZ], float *W) {
-    float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-#pragma unroll
-    for (int t = 0; t < KZ; ++t) {
-        const float4 v = load4(w[t] + off);
-        float4 &a = (t & 1) ? acc1 : acc0;
-        a.x = fmaf(fzc[t], v.x, a.x);
-        a.y = fmaf(fzc[t], v.y, a.y);
-        a.z = fmaf(fzc[t], v.z, a.z);
-        a.w = fmaf(fzc[t], v.w, a.w);
-    }
-    *reinterpret_cast<float4 *>(W + off) =
-        make_float4(acc0.x + acc1.x, acc0.y + acc1.y, acc0.z + acc1.z, acc0.w + acc1.w);
 }
 
 // x-pass over staged rows: T1[row][x] = sum_a fx[a+R] * S[row][x + XH + SGN*a]
@@ -583,25 +475,6 @@ __device__ __forceinline__ void xpass_offsets(int u, int &src, int &dst) {
     const int row = u / (TX / 4), x0 = (u - row * (TX / 4)) * 4;
     src = row * G::BX + x0 + G::XA0;
     dst = row * TX + x0;
-}
-
-// y-pass for this thread's RPW outputs (column lane, rows y0..y0+RPW-1):
-// out[k] = sum_b fy[b+R] * T1[y0 + k + R + SGN*b][lane].
-template <int R, int RPW, int SGN>
-__device__ __forceinline__ void ypass(const float *T1, int y0, int lane, const float (&fyc)[2 * R + 1],
-                                      float (&out)[RPW]) {
-    float t[RPW + 2 * R];
-#pragma unroll
-    for (int j = 0; j < RPW + 2 * R; ++j) t[j] = T1[(y0 + j) * TX + lane];
-#pragma unroll
-    for (int k = 0; k < RPW; ++k) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int b = -R; b <= R; b += 2) s0 = fmaf(fyc[b + R], t[k + R + SGN * b], s0);
-#pragma unroll
-        for (int b = -R + 1; b <= R; b += 2) s1 = fmaf(fyc[b + R], t[k + R + SGN * b], s1);
-        out[k] = s0 + s1;
-    }
 }
 
 // Last CTA of an objective launch: per volume slot, f and its parts, the trace
@@ -675,7 +548,8 @@ __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
 
 // Forward z-combine of one unit of 4 staged columns with paired FP32 FMAs:
 // W = sum_t fz[t] v(zi - t), slice zi - t held in ring slot (S - t) mod NS.
-// Per component this is the same sequence of roundings as zcomb_unit.
+// Per component: two partial sums over the even and the odd taps, each a
+// chain of FMAs, added at the end.
 template <int KZ, int NS, int S, int SLOT, class T>
 __device__ __forceinline__ void zcomb_ring(const T *base, const float (&fz)[KZ], float *W) {
     float2 a0 = make_float2(0.f, 0.f), a1 = a0, b0 = a0, b1 = a0;
@@ -696,7 +570,8 @@ __device__ __forceinline__ void zcomb_ring(const T *base, const float (&fz)[KZ],
 }
 
 // Forward y-pass of the column pair (c, c+1) at output row yo with paired FMAs:
-// out = sum_b fy[b+R] T1[yo + R - b][c .. c+1] (same rounding sequence as ypass).
+// out = sum_b fy[b+R] T1[yo + R - b][c .. c+1] (per component two FMA chains over
+// the even and the odd taps, added at the end).
 template <int R>
 __device__ __forceinline__ float2 ypass_pair(const float *T1, int yo, int c, const float (&fy)[2 * R + 1]) {
     float2 t[2 * R + 1];
