@@ -512,10 +512,11 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
-// Capture one iteration as a CUDA graph (replacing any earlier one).
+// Capture one iteration as a CUDA graph.  An earlier executable graph of the
+// same shape (the same launches with other grid sizes and arguments, as after
+// a re-plan) is updated in place, which costs far less than a new
+// instantiation; otherwise it is replaced.
 bd3mg_status capture_graph(bd3mg_ctx *c) {
-    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-    if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     bd3mg_status es = enqueue_iteration(c, c->cap_stream);
@@ -526,6 +527,18 @@ bd3mg_status capture_graph(bd3mg_ctx *c) {
         return es;
     }
     if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "end capture: %s", cudaGetErrorString(e));
+    if (c->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(c->exec, gr, &info) == cudaSuccess) {
+            if (c->graph) cudaGraphDestroy(c->graph);
+            c->graph = gr;
+            return BD3MG_OK;
+        }
+        (void)cudaGetLastError();   // the refused update is not an error of a later launch
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+    }
+    if (c->graph) cudaGraphDestroy(c->graph);
     c->graph = gr;
     e = cudaGraphInstantiate(&c->exec, gr, 0);
     if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
