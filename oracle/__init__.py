@@ -18,6 +18,12 @@ Parity status per function (what pins it is in the tests named):
   step / run (3MG) .......... pinned (dense least-squares solve when lambda=0 and
                               the box is inactive; per-voxel closed form for H=I;
                               monotone descent; stationarity)  tests/test_oracle_3mg.py
+  penalty mode 1 (joint X-Y hyperbolic + kappa ||V^Z x||^2, as printed in Section 3.1):
+                              pinned (hand-computed fixture case C; closed form
+                              along z with numpy.diff; reduction to the per-axis
+                              mode along x; finite differences; majorisation,
+                              tangency, exact quadratic Z majorant; descent and
+                              stationarity)       tests/test_oracle_objective.py, test_oracle_3mg.py
 Workload-level values of the paper (SNR on FlyBrain/Aneurysm): parity unpinned
 (datasets not available).
 """
@@ -43,7 +49,8 @@ class _Problem(ctypes.Structure):
                 ("px", ctypes.c_int), ("py", ctypes.c_int), ("pz", ctypes.c_int),
                 ("psf", ctypes.c_void_p),
                 ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("eta", ctypes.c_double),
-                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double)]
+                ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("penalty", ctypes.c_int), ("kappa", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -100,7 +107,7 @@ def _ptr(a: np.ndarray):
 class OracleProblem:
     """Holds the problem description (PSF as float32 [nz,pz,py,px], parameters)."""
 
-    def __init__(self, shape, psf, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0):
+    def __init__(self, shape, psf, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0, penalty=0, kappa=0.0):
         self.shape = tuple(int(s) for s in shape)
         nz, ny, nx = self.shape
         self.psf = _f32(psf)
@@ -108,11 +115,13 @@ class OracleProblem:
         pz, py, px = self.psf.shape[1:]
         assert px % 2 == 1 and py % 2 == 1 and pz % 2 == 1
         self.params = (float(lam), float(delta), float(eta), float(xmin), float(xmax))
-        self._c = _Problem(nx, ny, nz, px, py, pz, self.psf.ctypes.data, *self.params)
+        self.penalty, self.kappa = int(penalty), float(kappa)
+        self._c = _Problem(nx, ny, nz, px, py, pz, self.psf.ctypes.data, *self.params, self.penalty, self.kappa)
 
     @classmethod
     def from_synth(cls, prob):
-        return cls(prob.shape, prob.psf, prob.lam, prob.delta, prob.eta, prob.xmin, prob.xmax)
+        return cls(prob.shape, prob.psf, prob.lam, prob.delta, prob.eta, prob.xmin, prob.xmax,
+                   getattr(prob, "penalty", 0), getattr(prob, "kappa", 0.0))
 
     @property
     def ref(self):

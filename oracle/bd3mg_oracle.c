@@ -12,9 +12,10 @@
  *   - objective f = f1 + f2 + f3 (Section 3.1, Eq. "crit"):
  *       f1(x) = 1/2 ||Hx - y||^2
  *       f2(x) = eta * sum_n dist(x_n, [xmin, xmax])^2
- *       f3(x) = lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
- *     (the per-axis hyperbolic penalty; the paper's kappa*||V^Z x||^2 term is
- *      not part of this objective);
+ *       f3 per penalty mode:
+ *         0 (per axis):  lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
+ *         1 (as printed in Section 3.1): lambda * sum_n sqrt(delta^2 + ([V^X x]_n)^2
+ *           + ([V^Y x]_n)^2) + kappa * ||V^Z x||^2;
  *   - H: depth-variant blur, PSF of the OUTPUT depth, convolution orientation,
  *     zero outside the volume (Eq. "model");
  *   - H^T from the transpose definition (H^T r)_m = sum_n H_{n,m} r_n;
@@ -23,7 +24,9 @@
  *   - majorant matrix A(x~) = H^T H + 2 eta I + lambda sum_a V^aT Diag(w_a) V^a,
  *     w_a = 1/sqrt(delta^2 + (V^a x~)^2) (half-quadratic construction the
  *     paper defers to its reference for 3MG, Section 3.1), used in the block
- *     quadratic majorant Q (Section 2.2, Eq. "maj");
+ *     quadratic majorant Q (Section 2.2, Eq. "maj"); in mode 1 the X and Y
+ *     differences share the weight w = 1/sqrt(delta^2 + (V^X x~)^2 + (V^Y x~)^2)
+ *     and the quadratic Z term contributes its exact Hessian 2 kappa V^ZT V^Z;
  *   - memory-gradient subspace D = [-grad f | d] (Section 2.3), subspace
  *     matrix B = D^T A D by explicit products A*D, u = -B^+ D^T grad f via the
  *     symmetric 2x2 eigendecomposition (Eq. "minimizer", Moore-Penrose
@@ -50,6 +53,8 @@ typedef struct {
     int px, py, pz;
     const float *psf;     /* [nz][pz][py][px] */
     double lambda, delta, eta, xmin, xmax;
+    int penalty;          /* 0: per-axis hyperbolic; 1: joint X-Y hyperbolic + kappa ||V^Z x||^2 */
+    double kappa;
 } orc_problem;
 
 static long long nvox(const orc_problem *p) { return (long long)p->nx * p->ny * p->nz; }
@@ -176,9 +181,19 @@ double orc_objective(const orc_problem *p, const float *y, const double *x, doub
         double dist = x[k] - clampd(x[k], p->xmin, p->xmax);
         f2 += p->eta * dist * dist;
     }
-    for (int axis = 0; axis < 3; ++axis) {
-        orc_apply_V(p, axis, x, t);
-        for (long long k = 0; k < n; ++k) f3 += p->lambda * sqrt(p->delta * p->delta + t[k] * t[k]);
+    if (p->penalty == 0) {
+        for (int axis = 0; axis < 3; ++axis) {
+            orc_apply_V(p, axis, x, t);
+            for (long long k = 0; k < n; ++k) f3 += p->lambda * sqrt(p->delta * p->delta + t[k] * t[k]);
+        }
+    } else {
+        double *ty = (double *)malloc(sizeof(double) * n);
+        orc_apply_V(p, 0, x, t);
+        orc_apply_V(p, 1, x, ty);
+        for (long long k = 0; k < n; ++k) f3 += p->lambda * sqrt(p->delta * p->delta + t[k] * t[k] + ty[k] * ty[k]);
+        orc_apply_V(p, 2, x, t);
+        for (long long k = 0; k < n; ++k) f3 += p->kappa * t[k] * t[k];
+        free(ty);
     }
     free(hx);
     free(t);
@@ -186,8 +201,10 @@ double orc_objective(const orc_problem *p, const float *y, const double *x, doub
     return f1 + f2 + f3;
 }
 
-/* grad f(x) = H^T(Hx - y) + 2 eta (x - P(x)) + lambda sum_a V^aT psi'(V^a x),
- * psi'(t) = t / sqrt(delta^2 + t^2). */
+/* grad f(x) = H^T(Hx - y) + 2 eta (x - P(x)) + the penalty's gradient:
+ *   mode 0: lambda sum_a V^aT psi'(V^a x), psi'(t) = t / sqrt(delta^2 + t^2);
+ *   mode 1: lambda (V^XT (w t_X) + V^YT (w t_Y)) + 2 kappa V^ZT V^Z x,
+ *           t_a = V^a x, w = 1/sqrt(delta^2 + t_X^2 + t_Y^2). */
 void orc_gradient(const orc_problem *p, const float *y, const double *x, double *g) {
     long long n = nvox(p);
     double *r = (double *)malloc(sizeof(double) * n);
@@ -197,18 +214,40 @@ void orc_gradient(const orc_problem *p, const float *y, const double *x, double 
     for (long long k = 0; k < n; ++k) r[k] -= (double)y[k];
     orc_apply_HT(p, r, g);
     for (long long k = 0; k < n; ++k) g[k] += 2.0 * p->eta * (x[k] - clampd(x[k], p->xmin, p->xmax));
-    for (int axis = 0; axis < 3; ++axis) {
-        orc_apply_V(p, axis, x, t);
-        for (long long k = 0; k < n; ++k) t[k] = t[k] / sqrt(p->delta * p->delta + t[k] * t[k]);
-        orc_apply_VT(p, axis, t, vt);
+    if (p->penalty == 0) {
+        for (int axis = 0; axis < 3; ++axis) {
+            orc_apply_V(p, axis, x, t);
+            for (long long k = 0; k < n; ++k) t[k] = t[k] / sqrt(p->delta * p->delta + t[k] * t[k]);
+            orc_apply_VT(p, axis, t, vt);
+            for (long long k = 0; k < n; ++k) g[k] += p->lambda * vt[k];
+        }
+    } else {
+        double *ty = (double *)malloc(sizeof(double) * n);
+        orc_apply_V(p, 0, x, t);
+        orc_apply_V(p, 1, x, ty);
+        for (long long k = 0; k < n; ++k) {
+            double w = 1.0 / sqrt(p->delta * p->delta + t[k] * t[k] + ty[k] * ty[k]);
+            t[k] *= w;
+            ty[k] *= w;
+        }
+        orc_apply_VT(p, 0, t, vt);
         for (long long k = 0; k < n; ++k) g[k] += p->lambda * vt[k];
+        orc_apply_VT(p, 1, ty, vt);
+        for (long long k = 0; k < n; ++k) g[k] += p->lambda * vt[k];
+        orc_apply_V(p, 2, x, t);
+        orc_apply_VT(p, 2, t, vt);
+        for (long long k = 0; k < n; ++k) g[k] += 2.0 * p->kappa * vt[k];
+        free(ty);
     }
     free(r);
     free(t);
     free(vt);
 }
 
-/* A(xt) v = H^T H v + 2 eta v + lambda sum_a V^aT (w_a * V^a v), w_a = 1/sqrt(delta^2 + (V^a xt)^2). */
+/* A(xt) v = H^T H v + 2 eta v + the penalty's majorant curvature:
+ *   mode 0: lambda sum_a V^aT (w_a * V^a v), w_a = 1/sqrt(delta^2 + (V^a xt)^2);
+ *   mode 1: lambda (V^XT (w V^X v) + V^YT (w V^Y v)) + 2 kappa V^ZT V^Z v,
+ *           w = 1/sqrt(delta^2 + (V^X xt)^2 + (V^Y xt)^2). */
 void orc_apply_A(const orc_problem *p, const double *xt, const double *v, double *out) {
     long long n = nvox(p);
     double *hv = (double *)malloc(sizeof(double) * n);
@@ -218,12 +257,31 @@ void orc_apply_A(const orc_problem *p, const double *xt, const double *v, double
     orc_apply_H(p, v, hv);
     orc_apply_HT(p, hv, out);
     for (long long k = 0; k < n; ++k) out[k] += 2.0 * p->eta * v[k];
-    for (int axis = 0; axis < 3; ++axis) {
-        orc_apply_V(p, axis, xt, tx);
-        orc_apply_V(p, axis, v, tv);
-        for (long long k = 0; k < n; ++k) tv[k] *= 1.0 / sqrt(p->delta * p->delta + tx[k] * tx[k]);
-        orc_apply_VT(p, axis, tv, vt);
-        for (long long k = 0; k < n; ++k) out[k] += p->lambda * vt[k];
+    if (p->penalty == 0) {
+        for (int axis = 0; axis < 3; ++axis) {
+            orc_apply_V(p, axis, xt, tx);
+            orc_apply_V(p, axis, v, tv);
+            for (long long k = 0; k < n; ++k) tv[k] *= 1.0 / sqrt(p->delta * p->delta + tx[k] * tx[k]);
+            orc_apply_VT(p, axis, tv, vt);
+            for (long long k = 0; k < n; ++k) out[k] += p->lambda * vt[k];
+        }
+    } else {
+        double *ty = (double *)malloc(sizeof(double) * n);
+        double *w = (double *)malloc(sizeof(double) * n);
+        orc_apply_V(p, 0, xt, tx);
+        orc_apply_V(p, 1, xt, ty);
+        for (long long k = 0; k < n; ++k) w[k] = 1.0 / sqrt(p->delta * p->delta + tx[k] * tx[k] + ty[k] * ty[k]);
+        for (int axis = 0; axis < 2; ++axis) {
+            orc_apply_V(p, axis, v, tv);
+            for (long long k = 0; k < n; ++k) tv[k] *= w[k];
+            orc_apply_VT(p, axis, tv, vt);
+            for (long long k = 0; k < n; ++k) out[k] += p->lambda * vt[k];
+        }
+        orc_apply_V(p, 2, v, tv);
+        orc_apply_VT(p, 2, tv, vt);
+        for (long long k = 0; k < n; ++k) out[k] += 2.0 * p->kappa * vt[k];
+        free(ty);
+        free(w);
     }
     free(hv);
     free(tx);
@@ -360,19 +418,38 @@ void orc_gradient_at(const orc_problem *p, const float *y, const double *x, int 
         }
         double xm = x[m];
         s += 2.0 * p->eta * (xm - clampd(xm, p->xmin, p->xmax));
-        /* penalty: lambda * sum_a [psi'(t_a at m - e_a) - psi'(t_a at m)] */
         int pos[3] = {im, jm, zm};
         int len[3] = {p->nx, p->ny, p->nz};
         long long stride[3] = {1, p->nx, (long long)p->nx * p->ny};
-        for (int axis = 0; axis < 3; ++axis) {
-            if (pos[axis] >= 1) {
-                double t = xm - x[m - stride[axis]];
-                s += p->lambda * t / sqrt(p->delta * p->delta + t * t);
+        if (p->penalty == 0) {
+            /* penalty: lambda * sum_a [psi'(t_a at m - e_a) - psi'(t_a at m)] */
+            for (int axis = 0; axis < 3; ++axis) {
+                if (pos[axis] >= 1) {
+                    double t = xm - x[m - stride[axis]];
+                    s += p->lambda * t / sqrt(p->delta * p->delta + t * t);
+                }
+                if (pos[axis] < len[axis] - 1) {
+                    double t = x[m + stride[axis]] - xm;
+                    s -= p->lambda * t / sqrt(p->delta * p->delta + t * t);
+                }
             }
-            if (pos[axis] < len[axis] - 1) {
-                double t = x[m + stride[axis]] - xm;
-                s -= p->lambda * t / sqrt(p->delta * p->delta + t * t);
+        } else {
+            /* joint X-Y term: lambda * [w t_X at m - e_X + w t_Y at m - e_Y - w (t_X + t_Y) at m],
+             * with t_a, w of a voxel from its own forward differences; Z term: 2 kappa V^ZT V^Z x */
+            long long at[3] = {m, im >= 1 ? m - 1 : -1, jm >= 1 ? m - p->nx : -1};
+            for (int e = 0; e < 3; ++e) {
+                long long v = at[e];
+                if (v < 0) continue;
+                int iv = (int)(v % p->nx), jv = (int)((v / p->nx) % p->ny);
+                double tx = iv < p->nx - 1 ? x[v + 1] - x[v] : 0.0;
+                double ty = jv < p->ny - 1 ? x[v + p->nx] - x[v] : 0.0;
+                double w = 1.0 / sqrt(p->delta * p->delta + tx * tx + ty * ty);
+                if (e == 0) s -= p->lambda * w * (tx + ty);
+                else if (e == 1) s += p->lambda * w * tx;
+                else s += p->lambda * w * ty;
             }
+            if (pos[2] >= 1) s += 2.0 * p->kappa * (xm - x[m - stride[2]]);
+            if (pos[2] < len[2] - 1) s -= 2.0 * p->kappa * (x[m + stride[2]] - xm);
         }
         out[q] = s;
     }

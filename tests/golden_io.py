@@ -31,6 +31,8 @@ def load_cases(name: str = "objective_hand.txt"):
             elif key == "params":
                 lam, delta, eta, xmin, xmax = nums
                 cur["params"] = dict(lam=lam, delta=delta, eta=eta, xmin=xmin, xmax=xmax)
+            elif key == "penalty":                                   # mode, kappa
+                cur["params"].update(penalty=int(nums[0]), kappa=nums[1])
             elif key in ("y", "x", "Hx", "grad"):
                 cur[key] = np.array(nums).reshape(cur["shape"])
             else:

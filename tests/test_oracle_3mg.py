@@ -134,3 +134,19 @@ def test_block_form_converges_to_the_same_minimiser(small):
     assert np.all(np.diff(fs) <= 1e-12 * np.abs(fs[1:]))
     assert abs(fs[-1] - fa[-1]) <= 1e-10 * abs(fa[-1])
     assert np.linalg.norm(xs - xa) <= 1e-4 * np.linalg.norm(xa)
+
+
+def test_paper_penalty_descent_stationarity_and_slab_steps():
+    """Penalty mode 1 (joint X-Y hyperbolic + kappa ||V^Z x||^2, Section 3.1):
+    monotone descent to a stationary point in the plain form, and the slab
+    form's sweeps descend to the same objective."""
+    p = synth.tiny_problem(shape=(8, 10, 12), psf_shape=(3, 3, 3), seed=50, n_ellipsoids=4)
+    op = oracle.OracleProblem(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, penalty=1, kappa=0.05)
+    x0 = synth.uniform_start(p.y, seed=5)
+    x, _, ft = oracle.run(op, p.y, x0, 400)
+    assert np.all(np.diff(ft) <= 1e-12 * np.abs(ft[1:]))
+    g0 = oracle.gradient(op, p.y, x0.astype(np.float64))
+    assert np.linalg.norm(oracle.gradient(op, p.y, x)) <= 1e-4 * np.linalg.norm(g0)
+    xs, _, fs = oracle.run(op, p.y, x0, 400, bounds=[0, 3, 5, 8], order=[0, 2, 1])
+    assert np.all(np.diff(fs) <= 1e-12 * np.abs(fs[1:]))
+    assert abs(fs[-1] - ft[-1]) <= 1e-8 * abs(ft[-1])

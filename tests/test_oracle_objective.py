@@ -129,3 +129,106 @@ def test_pinv2_against_numpy():
         c = rng.standard_normal(2)
         u, _ = oracle.pinv2_solve(B, c)
         np.testing.assert_allclose(u, -np.linalg.pinv(B, rcond=1e-12, hermitian=True) @ c, rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Penalty mode 1: the objective as printed in Section 3.1, a joint X-Y
+# hyperbolic term plus kappa ||V^Z x||^2.
+# ---------------------------------------------------------------------------
+
+def test_paper_penalty_hand_case_C():
+    c = load_cases()["C"]
+    op = oracle.OracleProblem(c["shape"], c["psf"], **c["params"])
+    f, parts = oracle.objective(op, c["y"], c["x"], parts=True)
+    np.testing.assert_allclose(parts, [c["f1"], c["f2"], c["f3"]], rtol=1e-14)
+    np.testing.assert_allclose(oracle.gradient(op, c["y"], c["x"]), c["grad"], rtol=1e-14)
+
+
+def test_paper_penalty_along_z_is_the_quadratic_closed_form():
+    # nx = ny = 1: the joint term is delta at every voxel (no X or Y neighbour),
+    # and the Z term is kappa * sum of squared numpy differences along z.
+    shape = (7, 1, 1)
+    op = oracle.OracleProblem(shape, np.zeros((7, 1, 1, 1), np.float32), lam=0.3, delta=0.2, eta=0.0,
+                              penalty=1, kappa=1.7)
+    x = np.random.default_rng(30).standard_normal(shape)
+    _, parts = oracle.objective(op, np.zeros(shape, np.float32), x, parts=True)
+    assert abs(parts[2] - (0.3 * 0.2 * 7 + 1.7 * np.sum(np.diff(x[:, 0, 0]) ** 2))) <= 1e-13
+
+
+def test_paper_penalty_along_x_reduces_to_the_per_axis_penalty():
+    # ny = nz = 1: with no Y or Z neighbour the joint term is the per-axis X term,
+    # and the per-axis mode adds delta for each of the two absent axes.
+    shape = (1, 1, 9)
+    psf = np.full((1, 1, 1, 3), 1.0 / 3.0, np.float32)
+    x = np.random.default_rng(31).uniform(-0.5, 1.5, shape)
+    y = np.random.default_rng(32).uniform(0, 1, shape).astype(np.float32)
+    kw = dict(lam=0.2, delta=0.3, eta=1.5)
+    op0 = oracle.OracleProblem(shape, psf, **kw)
+    op1 = oracle.OracleProblem(shape, psf, **kw, penalty=1, kappa=4.0)
+    f0, p0 = oracle.objective(op0, y, x, parts=True)
+    f1, p1 = oracle.objective(op1, y, x, parts=True)
+    assert abs(p1[2] - (p0[2] - 0.2 * 0.3 * 2 * 9)) <= 1e-13
+    np.testing.assert_allclose(oracle.gradient(op1, y, x), oracle.gradient(op0, y, x), rtol=1e-13, atol=1e-15)
+    v = np.random.default_rng(33).standard_normal(shape)
+    np.testing.assert_allclose(oracle.apply_A(op1, x, v), oracle.apply_A(op0, x, v), rtol=1e-13, atol=1e-15)
+
+
+def _paper(seed, **kw):
+    p = synth.tiny_problem(seed=seed, **kw)
+    return p, oracle.OracleProblem(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, penalty=1, kappa=0.05)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_paper_penalty_gradient_central_differences(seed):
+    p, op = _paper(seed, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(40 + seed)
+    x = p.y.astype(np.float64) + 0.3 * rng.standard_normal(p.shape)
+    g = oracle.gradient(op, p.y, x)
+    h = 1e-6
+    for k in rng.choice(x.size, size=40, replace=False):
+        e = np.zeros(x.size)
+        e[k] = h
+        e = e.reshape(x.shape)
+        fd = (oracle.objective(op, p.y, x + e) - oracle.objective(op, p.y, x - e)) / (2 * h)
+        assert abs(fd - g.ravel()[k]) <= 2e-7 * max(1.0, abs(g.ravel()[k])), (k, fd, g.ravel()[k])
+
+
+def test_paper_penalty_gradient_at_matches_full_gradient():
+    p, op = _paper(3, shape=(5, 7, 8), psf_shape=(5, 3, 3))
+    x = synth.uniform_start(p.y, seed=3).astype(np.float64)
+    g = oracle.gradient(op, p.y, x)
+    idx = np.array([0, 1, 7, 8, 8 * 7 - 1, 100, 123, x.size - 1, x.size // 2])
+    np.testing.assert_allclose(oracle.gradient_at(op, p.y, x, idx), g.ravel()[idx], rtol=1e-12, atol=1e-14)
+
+
+def test_paper_penalty_majorisation_and_tangency():
+    p, op = _paper(7, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(48)
+    for _ in range(200):
+        x = rng.uniform(-0.5, 1.5, p.shape)
+        xp = x + rng.standard_normal(p.shape) * rng.choice([1e-3, 1e-1, 1.0])
+        q = _q(op, p.y, x, xp)
+        assert oracle.objective(op, p.y, xp) <= q + 1e-12 * abs(q)
+    # tangency: Q and f agree to first order at x, so (Q - f) / (f(x + h v) - f(x))
+    # shrinks in proportion to h
+    x = rng.uniform(0, 1, p.shape)
+    v = rng.standard_normal(p.shape)
+    rel = []
+    for h in (1e-3, 1e-4):
+        f0, f1 = oracle.objective(op, p.y, x), oracle.objective(op, p.y, x + h * v)
+        rel.append(abs(_q(op, p.y, x, x + h * v) - f1) / abs(f1 - f0))
+    assert rel[1] <= 0.2 * rel[0] and rel[1] < 1e-2, rel
+
+
+def test_paper_penalty_z_term_majorant_is_exact():
+    # lambda = 0, eta = 0, H = 0: only kappa ||V^Z x||^2 remains, a quadratic whose
+    # Hessian 2 kappa V^ZT V^Z is the majorant's curvature, so Q equals f everywhere.
+    shape = (5, 3, 4)
+    op = oracle.OracleProblem(shape, np.zeros((5, 1, 1, 1), np.float32), lam=0.0, delta=0.1, eta=0.0,
+                              penalty=1, kappa=0.8)
+    y = np.zeros(shape, np.float32)
+    rng = np.random.default_rng(49)
+    for _ in range(5):
+        x, xp = rng.standard_normal(shape), rng.standard_normal(shape)
+        f = oracle.objective(op, y, xp)
+        assert abs(_q(op, y, x, xp) - f) <= 1e-12 * abs(f)
