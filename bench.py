@@ -16,6 +16,8 @@ on the library's stream.
 
 Extra keys: the plain FP32 single-block form on the same volume, iterations and
 device time to relative objective gap 1e-4 for both forms (f* from a long run),
+the same volume under the penalty as Section 3.1 prints it (joint X-Y term plus
+kappa ||V^Z x||^2, kappa = 0.05),
 the per-kernel roofline, e2e through host buffers, and the FP64 CPU oracle
 timed on a bounded sample (`cpu_baseline`).
 
@@ -40,6 +42,9 @@ if ROOT not in sys.path:
 METRIC = "3MG iterations/s and time to rel. objective gap 1e-4 vs plain FP32, at 1 GB300"
 UNIT = "iterations/s"
 GAP = 1e-4
+# kappa of the penalty printed in Section 3.1 (joint X-Y hyperbolic + kappa ||V^Z x||^2); the paper
+# tunes it by hand on its datasets, so the synthetic workload takes a fixed value
+KAPPA_JOINT = 0.05
 
 
 def parse():
@@ -339,6 +344,32 @@ def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0, normalized=F
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
     return k, ms / 1e3, float(gap[k])
+
+
+def joint_penalty_extra(prob, args, flush, stream):
+    """Block and plain forms of the workload under penalty mode 1 (joint X-Y
+    hyperbolic term + kappa ||V^Z x||^2): sweeps/s, and time to the relative
+    gap 1e-4 against this objective's own f*."""
+    import dataclasses
+    from paper_2002_02328_gb300 import binding
+    pj = dataclasses.replace(prob, penalty=binding.PENALTY_JOINT_XY, kappa=KAPPA_JOINT)
+    out = {"penalty": "lambda sum sqrt(delta^2 + (V^X x)^2 + (V^Y x)^2) + kappa ||V^Z x||^2",
+           "kappa": KAPPA_JOINT}
+    n = max(10, args.steps // 4)
+    for key, slabs in (("block", pj.slabs), ("plain", None)):
+        with binding.Solver.from_problem(pj, slabs=slabs) as s:
+            for _ in range(args.warmup):
+                flush.fill_(1.0)
+                s.iterate_async(1)
+            ms = time_steps(s, n, flush, stream)
+        out[key] = {"iterations_per_s": 1e3 * n / ms}
+    if not args.quick:
+        fstar, settle = fstar_of(pj, args.fstar_iters)
+        out["fstar"], out["fstar_settle_rel"] = fstar, settle
+        for key, slabs in (("block", pj.slabs), ("plain", None)):
+            k, t, g = time_to_gap(pj, slabs, fstar, 3000, stream)
+            out[key].update({"iterations_to_gap": k, "seconds_to_gap": t})
+    return out
 
 
 def batch_extra(iters, stream):
@@ -681,6 +712,7 @@ def ours(args):
                                        "kernel_ms_per_iteration": {k: v[0] / args.profile_iters
                                                                    for k, v in prof_mixed.items()}}}
 
+    extra["joint_xy_penalty"] = joint_penalty_extra(prob, args, flush, stream)
     cpu = None
     if not args.quick:
         fstar, settle = fstar_of(prob, args.fstar_iters)

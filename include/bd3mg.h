@@ -9,6 +9,9 @@
  *        + eta * sum_n dist(x_n, [xmin, xmax])^2              (box term)
  *        + lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
  *
+ * (the default, per-axis penalty; the form printed in Section 3.1, a joint
+ * X-Y hyperbolic term plus kappa ||V^Z x||^2, is BD3MG_PENALTY_JOINT_XY)
+ *
  * with the Majorize-Minimize Memory Gradient iteration run block by block
  * (Sections 2.2-2.3): at each step a block S (a slab of depth slices) builds
  * the half-quadratic majorant Q_(S) (Eq. "maj"), the memory-gradient subspace
@@ -78,6 +81,19 @@ typedef struct {
  *   Every volume of a batch must use the same mode. */
 enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1 };
 
+/* Penalty term f3 of the objective (Section 3.1, Eq. "crit"), with forward
+ * differences [V^a x]_n = x_{n+e_a} - x_n, zero on the last plane of axis a.
+ * BD3MG_PENALTY_PER_AXIS (default): f3 = lambda sum_n sum_{a in X,Y,Z}
+ *   sqrt(delta^2 + [V^a x]_n^2); the majorant weights each axis by
+ *   w_a = 1/sqrt(delta^2 + [V^a x]_n^2).
+ * BD3MG_PENALTY_JOINT_XY (the form printed in Section 3.1): f3 = lambda sum_n
+ *   sqrt(delta^2 + [V^X x]_n^2 + [V^Y x]_n^2) + kappa ||V^Z x||^2; the X and Y
+ *   differences share one weight w = 1/sqrt(delta^2 + [V^X x]_n^2 + [V^Y x]_n^2)
+ *   in the majorant and the Z term contributes its exact Hessian
+ *   2 kappa V^ZT V^Z.
+ * Every volume of a batch must use the same penalty mode. */
+enum { BD3MG_PENALTY_PER_AXIS = 0, BD3MG_PENALTY_JOINT_XY = 1 };
+
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
     int px, py, pz;           /* PSF extents, odd, >= 1 */
@@ -91,10 +107,13 @@ typedef struct {
     const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
     double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
     int zchunk;               /* output slices per work item; 0 -> chosen by the library */
+    int penalty;              /* BD3MG_PENALTY_PER_AXIS or BD3MG_PENALTY_JOINT_XY */
+    double kappa;             /* >= 0, finite: weight of kappa ||V^Z x||^2 (BD3MG_PENALTY_JOINT_XY only) */
 } bd3mg_params;
 
-/* Fill *p with defaults (plain FP32, lambda = delta = 1e-2, eta = 1, box [0, 1],
- * no slabs, extents zero: the caller must set nx..pz and psf). */
+/* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,
+ * eta = 1, box [0, 1], no slabs, kappa = 0, extents zero: the caller must set
+ * nx..pz and psf). */
 void bd3mg_params_default(bd3mg_params *p);
 
 /* Create a context: validates *p, factors each depth's PSF (the fast path

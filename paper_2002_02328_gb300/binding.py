@@ -25,6 +25,7 @@ _lib = None
 STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA", 4: "BD3MG_ETIMEOUT",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
 FP32, BF16_GRADIENT = 0, 1
+PENALTY_PER_AXIS, PENALTY_JOINT_XY = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
@@ -50,7 +51,8 @@ class Params(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("eta", ctypes.c_double),
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
                 ("precision", ctypes.c_int), ("nslabs", ctypes.c_int), ("slab_bounds", ctypes.c_void_p),
-                ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int)]
+                ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int),
+                ("penalty", ctypes.c_int), ("kappa", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -149,7 +151,7 @@ def _torch_allocator():
 
 def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
-                zchunk: int = 0):
+                zchunk: int = 0, penalty: int = 0, kappa: float = 0.0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -163,6 +165,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.precision = int(precision)
     p.pinv_rtol = float(pinv_rtol)
     p.zchunk = int(zchunk)
+    p.penalty, p.kappa = int(penalty), float(kappa)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -252,12 +255,13 @@ class Solver:
 
     def __init__(self, shape, psf, y, x0=None, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
-        params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk)
+        params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
+                                   penalty, kappa)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -401,6 +405,8 @@ class Solver:
         if x0 is not None:
             x0 = torch.from_numpy(np.ascontiguousarray(x0, np.float32)).to(device)
         sl = prob.slabs if slabs == "auto" else slabs
+        kw.setdefault("penalty", getattr(prob, "penalty", 0))
+        kw.setdefault("kappa", getattr(prob, "kappa", 0.0))
         return cls(prob.shape, prob.psf, y, x0, lam=prob.lam, delta=prob.delta, eta=prob.eta, xmin=prob.xmin,
                    xmax=prob.xmax, slabs=sl, **kw)
 
@@ -420,7 +426,7 @@ class BatchSolver:
         precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * self.nvol
         for v, p in enumerate(problems):
             prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precs[v], 1e-12,
-                                 zchunk)
+                                 zchunk, getattr(p, "penalty", 0), getattr(p, "kappa", 0.0))
             arr[v] = prm
             keep.append(k)
             yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)

@@ -497,6 +497,11 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
         d.lam_d = p.lambda; d.eta_d = p.eta;
+        if (p.penalty == BD3MG_PENALTY_JOINT_XY) {
+            d.kl = (float)(p.kappa / p.lambda);
+            d.kl2 = (float)(2.0 * p.kappa / p.lambda);
+            d.kap2 = (float)(2.0 * p.kappa);
+        }
         vs.dev = d;
         vd[v] = d;
         const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
@@ -631,6 +636,10 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
         return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
     if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_GRADIENT)
         return fail(c, BD3MG_EINVAL, "volume %d: unknown precision mode %d", vi, p.precision);
+    if (p.penalty != BD3MG_PENALTY_PER_AXIS && p.penalty != BD3MG_PENALTY_JOINT_XY)
+        return fail(c, BD3MG_EINVAL, "volume %d: unknown penalty mode %d", vi, p.penalty);
+    if (!(p.kappa >= 0) || !std::isfinite(p.kappa))
+        return fail(c, BD3MG_EINVAL, "volume %d: kappa must be finite and >= 0", vi);
     if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return fail(c, BD3MG_EINVAL, "volume %d too large", vi);
     v.p = p;
     const int ns = p.nslabs <= 1 ? 1 : p.nslabs;
@@ -668,9 +677,11 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     c->bf = pp[0].precision == BD3MG_BF16_GRADIENT;
     for (int v = 1; v < nvol; ++v)
         if (pp[v].precision != pp[0].precision) return fail(c, BD3MG_EINVAL, "volumes must share one precision mode");
+    for (int v = 1; v < nvol; ++v)
+        if (pp[v].penalty != pp[0].penalty) return fail(c, BD3MG_EINVAL, "volumes must share one penalty mode");
 
     // kernels for the PSF radii (all volumes share one compiled set; smaller PSFs are zero padded)
-    c->ks = find_kernel_set(R, RZ);
+    c->ks = find_kernel_set(R, RZ, pp[0].penalty);
     if (!c->ks) return fail(c, BD3MG_EUNSUPPORTED, "no kernels for PSF radii (%d, %d); max 5", R, RZ);
     std::vector<std::vector<float>> FX(nvol), FY(nvol), FZ(nvol);
     for (int v = 0; v < nvol; ++v) {
@@ -1362,10 +1373,13 @@ int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
 }  // extern "C"
 
 namespace bd3mg {
-const KernelSet *find_kernel_set(int R, int RZ) {
+const KernelSet *find_kernel_set(int R, int RZ, int pm) {
     const KernelSet *best = nullptr;
-    int (*fns[])(const KernelSet **) = {kernel_sets_r1, kernel_sets_r2, kernel_sets_r3, kernel_sets_r4, kernel_sets_r5};
-    for (auto fn : fns) {
+    int (*fns0[])(const KernelSet **) = {kernel_sets_r1, kernel_sets_r2, kernel_sets_r3, kernel_sets_r4, kernel_sets_r5};
+    int (*fns1[])(const KernelSet **) = {kernel_sets_joint_r1, kernel_sets_joint_r2, kernel_sets_joint_r3,
+                                         kernel_sets_joint_r4, kernel_sets_joint_r5};
+    if (pm != 0 && pm != 1) return nullptr;
+    for (auto fn : pm ? fns1 : fns0) {
         const KernelSet *sets;
         int n = fn(&sets);
         for (int i = 0; i < n; ++i) {

@@ -1,10 +1,10 @@
-// inst_r2.cu -- tile kernels instantiated for xy PSF radius 2.
+// inst_r2.cu -- tile kernels instantiated for xy PSF radius 2, per-axis penalty.
 #include "launchers.cuh"
 
 namespace bd3mg {
 static const KernelSet kSets[] = {
-    BD3MG_KERNEL_SET(2,1),
-    BD3MG_KERNEL_SET(2,2),
+    BD3MG_KERNEL_SET(2,1,0),
+    BD3MG_KERNEL_SET(2,2,0),
 };
 int kernel_sets_r2(const KernelSet **out) {
     *out = kSets;

@@ -1,0 +1,14 @@
+// inst_r5_joint.cu -- tile kernels instantiated for xy PSF radius 5, penalty mode 1
+// (joint X-Y hyperbolic term plus kappa ||V^Z x||^2).
+#include "launchers.cuh"
+
+namespace bd3mg {
+static const KernelSet kSets[] = {
+    BD3MG_KERNEL_SET(5,3,1),
+    BD3MG_KERNEL_SET(5,5,1),
+};
+int kernel_sets_joint_r5(const KernelSet **out) {
+    *out = kSets;
+    return (int)(sizeof(kSets) / sizeof(kSets[0]));
+}
+}  // namespace bd3mg

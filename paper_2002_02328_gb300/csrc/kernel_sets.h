@@ -1,6 +1,8 @@
-// kernel_sets.h -- registry of the compiled (R, RZ) instantiations of the tile
-// kernels.  R is the xy PSF radius, RZ the z radius the kernels are built for;
-// a context pads its PSF factors with zero taps up to the chosen set.
+// kernel_sets.h -- registry of the compiled (R, RZ, PM) instantiations of the
+// tile kernels.  R is the xy PSF radius, RZ the z radius the kernels are built
+// for (a context pads its PSF factors with zero taps up to the chosen set), PM
+// the penalty mode (0 per-axis hyperbolic, 1 joint X-Y hyperbolic plus a
+// quadratic Z term).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -15,7 +17,7 @@ typedef void (*launch_fn)(const KArgs &, cudaStream_t);
 typedef cudaError_t (*prep_fn)();
 
 struct KernelSet {
-    int R, RZ;
+    int R, RZ, PM;
     launch_fn residual, gradient, curvature;        // FP32 gradient
     launch_fn gradient_bf, curvature_bf;            // BF16 gradient
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
@@ -24,8 +26,9 @@ struct KernelSet {
     int (*occupancy)(int kind);
 };
 
-// Smallest compiled set with R' >= R and RZ' >= RZ (fewest padded taps), or null.
-const KernelSet *find_kernel_set(int R, int RZ);
+// Smallest compiled set of penalty mode pm with R' >= R and RZ' >= RZ (fewest
+// padded taps), or null.
+const KernelSet *find_kernel_set(int R, int RZ, int pm);
 
 // Block update over the slabs listed in seg_list (grid.y = number of slabs);
 // run (nullable) marks stopped volumes.
@@ -39,5 +42,10 @@ int kernel_sets_r2(const KernelSet **out);
 int kernel_sets_r3(const KernelSet **out);
 int kernel_sets_r4(const KernelSet **out);
 int kernel_sets_r5(const KernelSet **out);
+int kernel_sets_joint_r1(const KernelSet **out);
+int kernel_sets_joint_r2(const KernelSet **out);
+int kernel_sets_joint_r3(const KernelSet **out);
+int kernel_sets_joint_r4(const KernelSet **out);
+int kernel_sets_joint_r5(const KernelSet **out);
 
 }  // namespace bd3mg

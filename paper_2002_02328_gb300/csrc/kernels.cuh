@@ -92,6 +92,9 @@ struct VolDev {
     const float *y;               // null -> 0
     const float *fx, *fy, *fz;    // [nz][kxy], [nz][kxy], [nz][kz]
     float lam, delta2, eta2, xmin, xmax;
+    // penalty mode 1 (joint X-Y hyperbolic + kappa ||V^Z x||^2): kappa/lambda,
+    // 2 kappa/lambda, 2 kappa (zero in mode 0)
+    float kl, kl2, kap2;
     double lam_d, eta_d;
 };
 
@@ -606,15 +609,23 @@ __device__ __forceinline__ void ypass_pair2(const float *T1, int yo, int c, cons
 
 // Objective terms of one voxel with centre value xc and forward differences
 // tx, ty, tz (0 where the neighbour does not exist): acc0 += r^2/2,
-// acc1 += dist(xc, [xmin, xmax])^2, acc2 += sum_a sqrt(delta^2 + t_a^2).
-__device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty, float tz, float delta2, float xmin,
-                                          float xmax, float (&acc)[3]) {
+// acc1 += dist(xc, [xmin, xmax])^2, and the penalty (divided by lambda) into
+// acc2: PM 0: sum_a sqrt(delta^2 + t_a^2); PM 1: sqrt(delta^2 + tx^2 + ty^2)
+// + (kappa/lambda) tz^2.
+template <int PM>
+__device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty, float tz, float delta2, float kl,
+                                          float xmin, float xmax, float (&acc)[3]) {
     acc[0] = fmaf(0.5f * rr, rr, acc[0]);
     const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
     acc[1] = fmaf(dist, dist, acc[1]);
     // sqrt(v) = v * rsqrt(v), v >= delta^2 > 0
-    const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
-    acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
+    if constexpr (PM == 0) {
+        const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
+        acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
+    } else {
+        const float v = fmaf(tx, tx, fmaf(ty, ty, delta2));
+        acc[2] += fmaf(kl * tz, tz, v * rsqrtf(v));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -624,7 +635,7 @@ __device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty
 // with paired FP32 FMAs; each thread of the y-pass and of the epilogue owns
 // a 2 x 2 block of outputs (rows yo, yo+1; columns c, c+1).
 // ---------------------------------------------------------------------------
-template <int R, int RZ>
+template <int R, int RZ, int PM>
 __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     using G = Geo<R, RZ, TY_A>;
     constexpr int NS = G::NSF, KZ = G::KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
@@ -645,7 +656,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     const bool zone = (a.mode & M_ZONE) != 0;
     const float *yp = zone ? nullptr : V.y;
     float *rp = V.r;
-    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, kl = V.kl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool store_r = (a.mode & M_STORE_R) != 0;
     const bool obj = (a.mode & M_OBJ) != 0 && !zone;
@@ -766,17 +777,17 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
             const float e0 = xa[2], e1 = xa[BX + 2];
             const float2 z0 = ld2(xb), z1 = ld2(xb + BX);
             const bool ze = zo + 1 < nz;
-            obj_terms(r0.x, a0.x, xe0 ? a0.y - a0.x : 0.f, ye0 ? a1.x - a0.x : 0.f, ze ? z0.x - a0.x : 0.f, delta2,
-                      xmin, xmax, acc);
+            obj_terms<PM>(r0.x, a0.x, xe0 ? a0.y - a0.x : 0.f, ye0 ? a1.x - a0.x : 0.f, ze ? z0.x - a0.x : 0.f,
+                          delta2, kl, xmin, xmax, acc);
             if (c1ok)
-                obj_terms(r0.y, a0.y, xe1 ? e0 - a0.y : 0.f, ye0 ? a1.y - a0.y : 0.f, ze ? z0.y - a0.y : 0.f, delta2,
-                          xmin, xmax, acc);
+                obj_terms<PM>(r0.y, a0.y, xe1 ? e0 - a0.y : 0.f, ye0 ? a1.y - a0.y : 0.f, ze ? z0.y - a0.y : 0.f,
+                              delta2, kl, xmin, xmax, acc);
             if (r1ok) {
-                obj_terms(r1.x, a1.x, xe0 ? a1.y - a1.x : 0.f, ye1 ? a2.x - a1.x : 0.f, ze ? z1.x - a1.x : 0.f,
-                          delta2, xmin, xmax, acc);
+                obj_terms<PM>(r1.x, a1.x, xe0 ? a1.y - a1.x : 0.f, ye1 ? a2.x - a1.x : 0.f, ze ? z1.x - a1.x : 0.f,
+                              delta2, kl, xmin, xmax, acc);
                 if (c1ok)
-                    obj_terms(r1.y, a1.y, xe1 ? e1 - a1.y : 0.f, ye1 ? a2.y - a1.y : 0.f, ze ? z1.y - a1.y : 0.f,
-                              delta2, xmin, xmax, acc);
+                    obj_terms<PM>(r1.y, a1.y, xe1 ? e1 - a1.y : 0.f, ye1 ? a2.y - a1.y : 0.f,
+                                  ze ? z1.y - a1.y : 0.f, delta2, kl, xmin, xmax, acc);
             }
         }
         return true;
@@ -830,7 +841,7 @@ __device__ __forceinline__ float dpsi(float t, float delta2) { return t * rsqrtf
 // differences of x it needs are shared between its four voxels; x is read
 // through the L1 cache.
 // ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF>
+template <int R, int RZ, bool BF, int PM>
 __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     using G = Geo<R, RZ, TY_A>;
     constexpr int KZ = G::KZ, NS = KZ, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
@@ -849,7 +860,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     float *gp = V.g;
     __nv_bfloat16 *gph = V.gh;
     const float *xg = V.x;
-    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2, kap2 = V.kap2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool full = (a.mode & M_HT_ONLY) == 0;
     if (vol_stopped(a, sg.vol)) return;
@@ -962,35 +973,77 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                     if (zl) zl1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch - plane));
                     if (zr) zr1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch + plane));
                 }
-                // x differences (each shared by its two voxels): row k: (c-1,c), (c,c+1), (c+1,c+2)
-                const bool hx0 = c1ok;                               // (c, c+1) is a difference of the volume
-                const float ax0 = xl ? dpsi(p0.x - m0, delta2) : 0.f;
-                const float bx0 = hx0 ? dpsi(p0.y - p0.x, delta2) : 0.f;
-                const float cx0 = xr1 ? dpsi(e0 - p0.y, delta2) : 0.f;
-                const float ax1 = xl ? dpsi(p1.x - m1, delta2) : 0.f;
-                const float bx1 = hx0 ? dpsi(p1.y - p1.x, delta2) : 0.f;
-                const float cx1 = xr1 ? dpsi(e1 - p1.y, delta2) : 0.f;
-                // y differences per column: (yo-1,yo), (yo,yo+1), (yo+1,yo+2)
-                const float2 ay = yu ? make_float2(dpsi(p0.x - pu.x, delta2), dpsi(p0.y - pu.y, delta2))
-                                     : make_float2(0.f, 0.f);
-                const float2 by = r1ok ? make_float2(dpsi(p1.x - p0.x, delta2), dpsi(p1.y - p0.y, delta2))
-                                       : make_float2(0.f, 0.f);
-                const float2 cy = yd2 ? make_float2(dpsi(pd.x - p1.x, delta2), dpsi(pd.y - p1.y, delta2))
-                                      : make_float2(0.f, 0.f);
-                // z differences per voxel
-                auto zterm = [&](float xc, float xlz, float xrz) {
-                    return (zl ? dpsi(xc - xlz, delta2) : 0.f) - (zr ? dpsi(xrz - xc, delta2) : 0.f);
-                };
-                const float pen00 = ax0 - bx0 + ay.x - by.x + zterm(p0.x, zl0.x, zr0.x);
-                const float pen01 = bx0 - cx0 + ay.y - by.y + zterm(p0.y, zl0.y, zr0.y);
-                const float pen10 = ax1 - bx1 + by.x - cy.x + zterm(p1.x, zl1.x, zr1.x);
-                const float pen11 = bx1 - cx1 + by.y - cy.y + zterm(p1.y, zl1.y, zr1.y);
-                auto gval = [&](float q, float xc, float pen) {
-                    const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                    return fmaf(lam, pen, fmaf(eta2, dist, q));
-                };
-                q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
-                q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
+                if constexpr (PM == 0) {
+                    // x differences (each shared by its two voxels): row k: (c-1,c), (c,c+1), (c+1,c+2)
+                    const bool hx0 = c1ok;                               // (c, c+1) is a difference of the volume
+                    const float ax0 = xl ? dpsi(p0.x - m0, delta2) : 0.f;
+                    const float bx0 = hx0 ? dpsi(p0.y - p0.x, delta2) : 0.f;
+                    const float cx0 = xr1 ? dpsi(e0 - p0.y, delta2) : 0.f;
+                    const float ax1 = xl ? dpsi(p1.x - m1, delta2) : 0.f;
+                    const float bx1 = hx0 ? dpsi(p1.y - p1.x, delta2) : 0.f;
+                    const float cx1 = xr1 ? dpsi(e1 - p1.y, delta2) : 0.f;
+                    // y differences per column: (yo-1,yo), (yo,yo+1), (yo+1,yo+2)
+                    const float2 ay = yu ? make_float2(dpsi(p0.x - pu.x, delta2), dpsi(p0.y - pu.y, delta2))
+                                         : make_float2(0.f, 0.f);
+                    const float2 by = r1ok ? make_float2(dpsi(p1.x - p0.x, delta2), dpsi(p1.y - p0.y, delta2))
+                                           : make_float2(0.f, 0.f);
+                    const float2 cy = yd2 ? make_float2(dpsi(pd.x - p1.x, delta2), dpsi(pd.y - p1.y, delta2))
+                                          : make_float2(0.f, 0.f);
+                    // z differences per voxel
+                    auto zterm = [&](float xc, float xlz, float xrz) {
+                        return (zl ? dpsi(xc - xlz, delta2) : 0.f) - (zr ? dpsi(xrz - xc, delta2) : 0.f);
+                    };
+                    const float pen00 = ax0 - bx0 + ay.x - by.x + zterm(p0.x, zl0.x, zr0.x);
+                    const float pen01 = bx0 - cx0 + ay.y - by.y + zterm(p0.y, zl0.y, zr0.y);
+                    const float pen10 = ax1 - bx1 + by.x - cy.x + zterm(p1.x, zl1.x, zr1.x);
+                    const float pen11 = bx1 - cx1 + by.y - cy.y + zterm(p1.y, zl1.y, zr1.y);
+                    auto gval = [&](float q, float xc, float pen) {
+                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+                        return fmaf(lam, pen, fmaf(eta2, dist, q));
+                    };
+                    q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
+                    q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
+                } else {
+                    // Joint X-Y weight w = 1/sqrt(delta^2 + tX^2 + tY^2) of a voxel, with tX,
+                    // tY its forward differences (0 where the +neighbour does not exist).  The
+                    // gradient needs w at the four voxels and at their -x and -y neighbours;
+                    // these read x on rows yo-1 .. yo+2 and columns c-1 .. c+2, of which
+                    // (yo-1, c+2) and (yo+2, c-1) are not loaded above.
+                    const float q3 = (yu && xr1) ? __ldg(xr - pitch + 2) : 0.f;        // (yo-1, c+2)
+                    const float s2 = (yd2 && xl) ? __ldg(xr + 2 * pitch - 1) : 0.f;   // (yo+2, c-1)
+                    auto w_of = [&](float tx, float ty) { return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, delta2))); };
+                    // (tX, tY) of (yo, c-1), (yo+1, c-1), (yo-1, c), (yo-1, c+1) and the own voxels
+                    const float txl0 = xl ? p0.x - m0 : 0.f, tyl0 = (xl && r1ok) ? m1 - m0 : 0.f;
+                    const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f, tyl1 = (xl && yd2) ? s2 - m1 : 0.f;
+                    const float txu0 = (yu && c1ok) ? pu.y - pu.x : 0.f, tyu0 = yu ? p0.x - pu.x : 0.f;
+                    const float txu1 = (yu && xr1) ? q3 - pu.y : 0.f, tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
+                    const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
+                    const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
+                    const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
+                    const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
+                    const float wl0 = w_of(txl0, tyl0), wl1 = w_of(txl1, tyl1);
+                    const float wu0 = w_of(txu0, tyu0), wu1 = w_of(txu1, tyu1);
+                    const float w00 = w_of(tx00, ty00), w01 = w_of(tx01, ty01);
+                    const float w10 = w_of(tx10, ty10), w11 = w_of(tx11, ty11);
+                    // V^XT (w tX) + V^YT (w tY): inflow from the -x and -y neighbours minus the
+                    // voxel's own outflow
+                    const float pen00 = wl0 * txl0 - w00 * tx00 + wu0 * tyu0 - w00 * ty00;
+                    const float pen01 = w00 * tx00 - w01 * tx01 + wu1 * tyu1 - w01 * ty01;
+                    const float pen10 = wl1 * txl1 - w10 * tx10 + w00 * ty00 - w10 * ty10;
+                    const float pen11 = w10 * tx10 - w11 * tx11 + w01 * ty01 - w11 * ty11;
+                    // V^ZT V^Z x of the quadratic z term
+                    auto zq = [&](float xc, float xlz, float xrz) {
+                        return (zl ? xc - xlz : 0.f) - (zr ? xrz - xc : 0.f);
+                    };
+                    auto gval = [&](float q, float xc, float pen, float zt) {
+                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+                        return fmaf(kap2, zt, fmaf(lam, pen, fmaf(eta2, dist, q)));
+                    };
+                    q0 = make_float2(gval(q0.x, p0.x, pen00, zq(p0.x, zl0.x, zr0.x)),
+                                     gval(q0.y, p0.y, pen01, zq(p0.y, zl0.y, zr0.y)));
+                    q1 = make_float2(gval(q1.x, p1.x, pen10, zq(p1.x, zl1.x, zr1.x)),
+                                     gval(q1.y, p1.y, pen11, zq(p1.y, zl1.y, zr1.y)));
+                }
             }
             if (c0ok) {
                 const long long zoff = (long long)zo * plane;
@@ -1095,6 +1148,28 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
     acc[8] = fmaf(w * vd, vd, acc[8]);
 }
 
+// Penalty mode 1, X and Y: the two differences of a voxel share the weight
+// w = 1/sqrt(delta^2 + tx^2 + ty^2) (tx, ty of x; all differences 0 where the
+// neighbour does not exist): acc6 += w (vgx^2 + vgy^2), acc7 += w (vgx vdx +
+// vgy vdy), acc8 += w (vdx^2 + vdy^2).
+__device__ __forceinline__ void pen_joint(float tx, float ty, float vgx, float vgy, float vdx, float vdy, float delta2,
+                                          float *acc) {
+    const float w = rsqrtf(fmaf(tx, tx, fmaf(ty, ty, delta2)));
+    acc[6] = fmaf(w, fmaf(vgx, vgx, vgy * vgy), acc[6]);
+    acc[7] = fmaf(w, fmaf(vgx, vdx, vgy * vdy), acc[7]);
+    acc[8] = fmaf(w, fmaf(vdx, vdx, vdy * vdy), acc[8]);
+}
+
+// Penalty mode 1, Z: the quadratic term kappa ||V^Z x||^2 is its own majorant;
+// its products enter with weight 2 kappa / lambda (kl2), since the sums are
+// scaled by lambda when the subspace matrix is formed.
+__device__ __forceinline__ void pen_quad(float vg, float vd, float kl2, float *acc) {
+    const float kvg = kl2 * vg;
+    acc[6] = fmaf(kvg, vg, acc[6]);
+    acc[7] = fmaf(kvg, vd, acc[7]);
+    acc[8] = fmaf(kl2 * vd, vd, acc[8]);
+}
+
 // ---------------------------------------------------------------------------
 // k_curvature: the inner products of the restricted subspace system and, in
 // the last CTA, the per-slab 2x2 solve.
@@ -1110,7 +1185,7 @@ __device__ __forceinline__ void pen_axis(float xn, float xe, float gn, float ge,
 // half-quadratic terms are formed between the two barriers of a step, before
 // the convolution's registers are needed; with one, after the y-pass.
 // ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF>
+template <int R, int RZ, bool BF, int PM>
 __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
     using CR = CurvRing<R, RZ, sizeof(T)>;
@@ -1131,7 +1206,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
     const float *xg = V.x, *dg = V.d;
-    const float delta2 = V.delta2;
+    const float delta2 = V.delta2, kl2 = V.kl2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
     // A stopped volume's item gets an empty range: no copies, no loop, zero
@@ -1274,9 +1349,16 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
                     acc[2] = fmaf(da[k].x, da[k].x, acc[2]);
                     acc[9] = fmaf(xa[k].x, xa[k].x, acc[9]);
                 }
-                if (xe0) pen_axis(xa[k].x, xa[k].y, ga[k].x, ga[k].y, da[k].x, da[k].y, delta2, acc);
-                if (yeo[k]) pen_axis(xa[k].x, xa[k + 1].x, ga[k].x, ga[k + 1].x, da[k].x, da[k + 1].x, delta2, acc);
-                if (ze) pen_axis(xa[k].x, xz[k].x, ga[k].x, gz[k].x, da[k].x, dz[k].x, delta2, acc);
+                if constexpr (PM == 0) {
+                    if (xe0) pen_axis(xa[k].x, xa[k].y, ga[k].x, ga[k].y, da[k].x, da[k].y, delta2, acc);
+                    if (yeo[k]) pen_axis(xa[k].x, xa[k + 1].x, ga[k].x, ga[k + 1].x, da[k].x, da[k + 1].x, delta2, acc);
+                    if (ze) pen_axis(xa[k].x, xz[k].x, ga[k].x, gz[k].x, da[k].x, dz[k].x, delta2, acc);
+                } else {
+                    pen_joint(xe0 ? xa[k].y - xa[k].x : 0.f, yeo[k] ? xa[k + 1].x - xa[k].x : 0.f,
+                              xe0 ? ga[k].y - ga[k].x : 0.f, yeo[k] ? ga[k + 1].x - ga[k].x : 0.f,
+                              xe0 ? da[k].y - da[k].x : 0.f, yeo[k] ? da[k + 1].x - da[k].x : 0.f, delta2, acc);
+                    if (ze) pen_quad(gz[k].x - ga[k].x, dz[k].x - da[k].x, kl2, acc);
+                }
                 // voxel (yo+k, c+1)
                 if (c1ok) {
                     if (inslab) {
@@ -1285,9 +1367,17 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
                         acc[2] = fmaf(da[k].y, da[k].y, acc[2]);
                         acc[9] = fmaf(xa[k].y, xa[k].y, acc[9]);
                     }
-                    if (xe1) pen_axis(xa[k].y, xev[k], ga[k].y, gev[k], da[k].y, dev[k], delta2, acc);
-                    if (yeo[k]) pen_axis(xa[k].y, xa[k + 1].y, ga[k].y, ga[k + 1].y, da[k].y, da[k + 1].y, delta2, acc);
-                    if (ze) pen_axis(xa[k].y, xz[k].y, ga[k].y, gz[k].y, da[k].y, dz[k].y, delta2, acc);
+                    if constexpr (PM == 0) {
+                        if (xe1) pen_axis(xa[k].y, xev[k], ga[k].y, gev[k], da[k].y, dev[k], delta2, acc);
+                        if (yeo[k])
+                            pen_axis(xa[k].y, xa[k + 1].y, ga[k].y, ga[k + 1].y, da[k].y, da[k + 1].y, delta2, acc);
+                        if (ze) pen_axis(xa[k].y, xz[k].y, ga[k].y, gz[k].y, da[k].y, dz[k].y, delta2, acc);
+                    } else {
+                        pen_joint(xe1 ? xev[k] - xa[k].y : 0.f, yeo[k] ? xa[k + 1].y - xa[k].y : 0.f,
+                                  xe1 ? gev[k] - ga[k].y : 0.f, yeo[k] ? ga[k + 1].y - ga[k].y : 0.f,
+                                  xe1 ? dev[k] - da[k].y : 0.f, yeo[k] ? da[k + 1].y - da[k].y : 0.f, delta2, acc);
+                        if (ze) pen_quad(gz[k].y - ga[k].y, dz[k].y - da[k].y, kl2, acc);
+                    }
                 }
             }
         };

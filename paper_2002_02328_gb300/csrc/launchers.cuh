@@ -1,58 +1,59 @@
-// launchers.cuh -- host launch wrappers for one (R, RZ) instantiation.
+// launchers.cuh -- host launch wrappers for one (R, RZ, penalty mode) instantiation.
 #pragma once
 #include "kernel_sets.h"
 #include "kernels.cuh"
 
 namespace bd3mg {
 
-template <int R, int RZ>
+template <int R, int RZ, int PM>
 void launch_residual(const KArgs &a, cudaStream_t s) {
-    k_residual<R, RZ><<<a.nitems, NT, Smem<R, RZ>::residual, s>>>(a);
+    k_residual<R, RZ, PM><<<a.nitems, NT, Smem<R, RZ>::residual, s>>>(a);
 }
-template <int R, int RZ, bool BF>
+template <int R, int RZ, bool BF, int PM>
 void launch_gradient(const KArgs &a, cudaStream_t s) {
-    k_gradient<R, RZ, BF><<<a.nitems, NT, Smem<R, RZ>::gradient, s>>>(a);
+    k_gradient<R, RZ, BF, PM><<<a.nitems, NT, Smem<R, RZ>::gradient, s>>>(a);
 }
-template <int R, int RZ, bool BF>
+template <int R, int RZ, bool BF, int PM>
 void launch_curvature(const KArgs &a, cudaStream_t s) {
-    k_curvature<R, RZ, BF><<<a.nitems, NT, BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature, s>>>(a);
+    k_curvature<R, RZ, BF, PM><<<a.nitems, NT, BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature, s>>>(a);
 }
-template <int R, int RZ>
+template <int R, int RZ, int PM>
 cudaError_t prepare_set() {
-    cudaError_t e = cudaFuncSetAttribute(k_residual<R, RZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_residual<R, RZ, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Smem<R, RZ>::residual);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_gradient<R, RZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gradient<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::gradient);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_gradient<R, RZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_gradient<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::gradient);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_curvature<R, RZ, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_curvature<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::curvature);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_curvature<R, RZ, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_curvature<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::curvature_bf);
     return e;
 }
 
-template <int R, int RZ>
+template <int R, int RZ, int PM>
 int occupancy_of(int kind) {
     int n = 0;
     cudaError_t e;
     switch (kind) {
-        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual<R, RZ>, NT, Smem<R, RZ>::residual); break;
-        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, false>, NT, Smem<R, RZ>::gradient); break;
-        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, true>, NT, Smem<R, RZ>::gradient); break;
-        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, true>, NT, Smem<R, RZ>::curvature_bf); break;
-        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false>, NT, Smem<R, RZ>::curvature); break;
+        case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_residual<R, RZ, PM>, NT, Smem<R, RZ>::residual); break;
+        case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, false, PM>, NT, Smem<R, RZ>::gradient); break;
+        case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, true, PM>, NT, Smem<R, RZ>::gradient); break;
+        case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, true, PM>, NT, Smem<R, RZ>::curvature_bf); break;
+        default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM>, NT, Smem<R, RZ>::curvature); break;
     }
     return e == cudaSuccess ? n : 0;
 }
 
 }  // namespace bd3mg
 
-#define BD3MG_KERNEL_SET(R, RZ)                                                                          \
-    {R, RZ, &bd3mg::launch_residual<R, RZ>, &bd3mg::launch_gradient<R, RZ, false>,                        \
-     &bd3mg::launch_curvature<R, RZ, false>, &bd3mg::launch_gradient<R, RZ, true>,                        \
-     &bd3mg::launch_curvature<R, RZ, true>, &bd3mg::prepare_set<R, RZ>, &bd3mg::occupancy_of<R, RZ>}
+#define BD3MG_KERNEL_SET(R, RZ, PM)                                                                      \
+    {R, RZ, PM, &bd3mg::launch_residual<R, RZ, PM>, &bd3mg::launch_gradient<R, RZ, false, PM>,              \
+     &bd3mg::launch_curvature<R, RZ, false, PM>, &bd3mg::launch_gradient<R, RZ, true, PM>,                  \
+     &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::prepare_set<R, RZ, PM>,                             \
+     &bd3mg::occupancy_of<R, RZ, PM>}

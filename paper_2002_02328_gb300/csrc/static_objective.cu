@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -69,13 +70,16 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
         return fail(BD3MG_EINVAL, "volume extents must be >= 1 and PSF extents odd, with a PSF");
     if (!(p->lambda > 0) || !(p->delta > 0) || !(p->eta >= 0) || !(p->xmin <= p->xmax))
         return fail(BD3MG_EINVAL, "need lambda > 0, delta > 0, eta >= 0, xmin <= xmax");
+    if ((p->penalty != BD3MG_PENALTY_PER_AXIS && p->penalty != BD3MG_PENALTY_JOINT_XY) || !(p->kappa >= 0) ||
+        !(p->kappa < HUGE_VAL))
+        return fail(BD3MG_EINVAL, "unknown penalty mode, or kappa not finite and >= 0");
     // The caller's volumes are read in place by TMA: rows must start on 16-byte boundaries.
     if ((p->nx & 3) || (reinterpret_cast<uintptr_t>(x) & 15) || (reinterpret_cast<uintptr_t>(y) & 15) ||
         (reinterpret_cast<uintptr_t>(f_out) & 7))
         return fail(BD3MG_EINVAL, "nx must be a multiple of 4, x and y 16-byte aligned, f_out 8-byte aligned");
     const int R = std::max(std::max((p->px - 1) / 2, (p->py - 1) / 2), 1);
     const int rz = (p->pz - 1) / 2;
-    const KernelSet *ks = find_kernel_set(R, std::max(rz, 1));
+    const KernelSet *ks = find_kernel_set(R, std::max(rz, 1), p->penalty);
     if (!ks) return fail(BD3MG_EUNSUPPORTED, "PSF radii above 5 are not compiled");
     const size_t nfx = (size_t)p->nz * (2 * ks->R + 1), nfz = (size_t)p->nz * (2 * ks->RZ + 1);
     if (sizeof(float) * (2 * nfx + nfz) > kStaticScratchBytes / 2)
@@ -140,6 +144,7 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     v.lam = (float)p->lambda; v.delta2 = (float)(p->delta * p->delta); v.eta2 = (float)(2.0 * p->eta);
     v.xmin = (float)p->xmin; v.xmax = (float)p->xmax;
     v.lam_d = p->lambda; v.eta_d = p->eta;
+    if (p->penalty == BD3MG_PENALTY_JOINT_XY) v.kl = (float)(p->kappa / p->lambda);
     std::memcpy(g_host + o_vol, &v, sizeof(v));
     VolMaps vm;
     std::memset(&vm, 0, sizeof(vm));
