@@ -24,6 +24,12 @@ Parity status per function (what pins it is in the tests named):
                               mode along x; finite differences; majorisation,
                               tangency, exact quadratic Z majorant; descent and
                               stationarity)       tests/test_oracle_objective.py, test_oracle_3mg.py
+  penalty mode 2 (isotropic hyperbolic term over X, Y and Z):
+                              pinned (hand-computed fixture case D; reduction to
+                              the per-axis mode along each single axis; invariance
+                              under axis permutation; finite differences;
+                              majorisation, tangency; descent and stationarity)
+                                                  tests/test_oracle_objective.py, test_oracle_3mg.py
 Workload-level values of the paper (SNR on FlyBrain/Aneurysm): parity unpinned
 (datasets not available).
 """

@@ -16,6 +16,8 @@
  *         0 (per axis):  lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
  *         1 (as printed in Section 3.1): lambda * sum_n sqrt(delta^2 + ([V^X x]_n)^2
  *           + ([V^Y x]_n)^2) + kappa * ||V^Z x||^2;
+ *         2 (isotropic over the three axes): lambda * sum_n sqrt(delta^2
+ *           + ([V^X x]_n)^2 + ([V^Y x]_n)^2 + ([V^Z x]_n)^2);
  *   - H: depth-variant blur, PSF of the OUTPUT depth, convolution orientation,
  *     zero outside the volume (Eq. "model");
  *   - H^T from the transpose definition (H^T r)_m = sum_n H_{n,m} r_n;
@@ -27,6 +29,7 @@
  *     quadratic majorant Q (Section 2.2, Eq. "maj"); in mode 1 the X and Y
  *     differences share the weight w = 1/sqrt(delta^2 + (V^X x~)^2 + (V^Y x~)^2)
  *     and the quadratic Z term contributes its exact Hessian 2 kappa V^ZT V^Z;
+ *     in mode 2 all three differences share w = 1/sqrt(delta^2 + sum_a (V^a x~)^2);
  *   - memory-gradient subspace D = [-grad f | d] (Section 2.3), subspace
  *     matrix B = D^T A D by explicit products A*D, u = -B^+ D^T grad f via the
  *     symmetric 2x2 eigendecomposition (Eq. "minimizer", Moore-Penrose
@@ -53,7 +56,8 @@ typedef struct {
     int px, py, pz;
     const float *psf;     /* [nz][pz][py][px] */
     double lambda, delta, eta, xmin, xmax;
-    int penalty;          /* 0: per-axis hyperbolic; 1: joint X-Y hyperbolic + kappa ||V^Z x||^2 */
+    int penalty;          /* 0: per-axis hyperbolic; 1: joint X-Y hyperbolic + kappa ||V^Z x||^2;
+                             2: isotropic hyperbolic over X, Y, Z */
     double kappa;
 } orc_problem;
 
@@ -186,7 +190,7 @@ double orc_objective(const orc_problem *p, const float *y, const double *x, doub
             orc_apply_V(p, axis, x, t);
             for (long long k = 0; k < n; ++k) f3 += p->lambda * sqrt(p->delta * p->delta + t[k] * t[k]);
         }
-    } else {
+    } else if (p->penalty == 1) {
         double *ty = (double *)malloc(sizeof(double) * n);
         orc_apply_V(p, 0, x, t);
         orc_apply_V(p, 1, x, ty);
@@ -194,6 +198,16 @@ double orc_objective(const orc_problem *p, const float *y, const double *x, doub
         orc_apply_V(p, 2, x, t);
         for (long long k = 0; k < n; ++k) f3 += p->kappa * t[k] * t[k];
         free(ty);
+    } else {
+        double *ty = (double *)malloc(sizeof(double) * n);
+        double *tz = (double *)malloc(sizeof(double) * n);
+        orc_apply_V(p, 0, x, t);
+        orc_apply_V(p, 1, x, ty);
+        orc_apply_V(p, 2, x, tz);
+        for (long long k = 0; k < n; ++k)
+            f3 += p->lambda * sqrt(p->delta * p->delta + t[k] * t[k] + ty[k] * ty[k] + tz[k] * tz[k]);
+        free(ty);
+        free(tz);
     }
     free(hx);
     free(t);
@@ -204,7 +218,8 @@ double orc_objective(const orc_problem *p, const float *y, const double *x, doub
 /* grad f(x) = H^T(Hx - y) + 2 eta (x - P(x)) + the penalty's gradient:
  *   mode 0: lambda sum_a V^aT psi'(V^a x), psi'(t) = t / sqrt(delta^2 + t^2);
  *   mode 1: lambda (V^XT (w t_X) + V^YT (w t_Y)) + 2 kappa V^ZT V^Z x,
- *           t_a = V^a x, w = 1/sqrt(delta^2 + t_X^2 + t_Y^2). */
+ *           t_a = V^a x, w = 1/sqrt(delta^2 + t_X^2 + t_Y^2);
+ *   mode 2: lambda sum_a V^aT (w t_a), w = 1/sqrt(delta^2 + t_X^2 + t_Y^2 + t_Z^2). */
 void orc_gradient(const orc_problem *p, const float *y, const double *x, double *g) {
     long long n = nvox(p);
     double *r = (double *)malloc(sizeof(double) * n);
@@ -221,6 +236,21 @@ void orc_gradient(const orc_problem *p, const float *y, const double *x, double 
             orc_apply_VT(p, axis, t, vt);
             for (long long k = 0; k < n; ++k) g[k] += p->lambda * vt[k];
         }
+    } else if (p->penalty == 2) {
+        double *ta[3], *w = (double *)malloc(sizeof(double) * n);
+        for (int axis = 0; axis < 3; ++axis) {
+            ta[axis] = (double *)malloc(sizeof(double) * n);
+            orc_apply_V(p, axis, x, ta[axis]);
+        }
+        for (long long k = 0; k < n; ++k)
+            w[k] = 1.0 / sqrt(p->delta * p->delta + ta[0][k] * ta[0][k] + ta[1][k] * ta[1][k] + ta[2][k] * ta[2][k]);
+        for (int axis = 0; axis < 3; ++axis) {
+            for (long long k = 0; k < n; ++k) ta[axis][k] *= w[k];
+            orc_apply_VT(p, axis, ta[axis], vt);
+            for (long long k = 0; k < n; ++k) g[k] += p->lambda * vt[k];
+            free(ta[axis]);
+        }
+        free(w);
     } else {
         double *ty = (double *)malloc(sizeof(double) * n);
         orc_apply_V(p, 0, x, t);
@@ -247,7 +277,8 @@ void orc_gradient(const orc_problem *p, const float *y, const double *x, double 
 /* A(xt) v = H^T H v + 2 eta v + the penalty's majorant curvature:
  *   mode 0: lambda sum_a V^aT (w_a * V^a v), w_a = 1/sqrt(delta^2 + (V^a xt)^2);
  *   mode 1: lambda (V^XT (w V^X v) + V^YT (w V^Y v)) + 2 kappa V^ZT V^Z v,
- *           w = 1/sqrt(delta^2 + (V^X xt)^2 + (V^Y xt)^2). */
+ *           w = 1/sqrt(delta^2 + (V^X xt)^2 + (V^Y xt)^2);
+ *   mode 2: lambda sum_a V^aT (w V^a v), w = 1/sqrt(delta^2 + sum_a (V^a xt)^2). */
 void orc_apply_A(const orc_problem *p, const double *xt, const double *v, double *out) {
     long long n = nvox(p);
     double *hv = (double *)malloc(sizeof(double) * n);
@@ -265,6 +296,21 @@ void orc_apply_A(const orc_problem *p, const double *xt, const double *v, double
             orc_apply_VT(p, axis, tv, vt);
             for (long long k = 0; k < n; ++k) out[k] += p->lambda * vt[k];
         }
+    } else if (p->penalty == 2) {
+        double *w = (double *)malloc(sizeof(double) * n);
+        for (long long k = 0; k < n; ++k) w[k] = p->delta * p->delta;
+        for (int axis = 0; axis < 3; ++axis) {
+            orc_apply_V(p, axis, xt, tx);
+            for (long long k = 0; k < n; ++k) w[k] += tx[k] * tx[k];
+        }
+        for (long long k = 0; k < n; ++k) w[k] = 1.0 / sqrt(w[k]);
+        for (int axis = 0; axis < 3; ++axis) {
+            orc_apply_V(p, axis, v, tv);
+            for (long long k = 0; k < n; ++k) tv[k] *= w[k];
+            orc_apply_VT(p, axis, tv, vt);
+            for (long long k = 0; k < n; ++k) out[k] += p->lambda * vt[k];
+        }
+        free(w);
     } else {
         double *ty = (double *)malloc(sizeof(double) * n);
         double *w = (double *)malloc(sizeof(double) * n);
@@ -432,6 +478,22 @@ void orc_gradient_at(const orc_problem *p, const float *y, const double *x, int 
                     double t = x[m + stride[axis]] - xm;
                     s -= p->lambda * t / sqrt(p->delta * p->delta + t * t);
                 }
+            }
+        } else if (p->penalty == 2) {
+            /* isotropic term: lambda * [sum_a w t_a at m - e_a - w (t_X + t_Y + t_Z) at m], with
+             * t_a, w of a voxel from its own forward differences */
+            for (int e = 0; e < 4; ++e) {
+                if (e > 0 && pos[e - 1] < 1) continue;
+                long long v = e == 0 ? m : m - stride[e - 1];
+                int pv[3] = {(int)(v % p->nx), (int)((v / p->nx) % p->ny), (int)(v / stride[2])};
+                double ta[3], ss = p->delta * p->delta;
+                for (int axis = 0; axis < 3; ++axis) {
+                    ta[axis] = pv[axis] < len[axis] - 1 ? x[v + stride[axis]] - x[v] : 0.0;
+                    ss += ta[axis] * ta[axis];
+                }
+                double w = 1.0 / sqrt(ss);
+                if (e == 0) s -= p->lambda * w * (ta[0] + ta[1] + ta[2]);
+                else s += p->lambda * w * ta[e - 1];
             }
         } else {
             /* joint X-Y term: lambda * [w t_X at m - e_X + w t_Y at m - e_Y - w (t_X + t_Y) at m],

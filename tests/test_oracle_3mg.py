@@ -150,3 +150,19 @@ def test_paper_penalty_descent_stationarity_and_slab_steps():
     xs, _, fs = oracle.run(op, p.y, x0, 400, bounds=[0, 3, 5, 8], order=[0, 2, 1])
     assert np.all(np.diff(fs) <= 1e-12 * np.abs(fs[1:]))
     assert abs(fs[-1] - ft[-1]) <= 1e-8 * abs(ft[-1])
+
+
+def test_isotropic_penalty_descent_stationarity_and_slab_steps():
+    """Penalty mode 2 (isotropic hyperbolic term over X, Y, Z): monotone descent to
+    a stationary point in the plain form, and the slab form's sweeps descend to
+    the same objective."""
+    p = synth.tiny_problem(shape=(8, 10, 12), psf_shape=(3, 3, 3), seed=51, n_ellipsoids=4)
+    op = oracle.OracleProblem(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, penalty=2)
+    x0 = synth.uniform_start(p.y, seed=6)
+    x, _, ft = oracle.run(op, p.y, x0, 400)
+    assert np.all(np.diff(ft) <= 1e-12 * np.abs(ft[1:]))
+    g0 = oracle.gradient(op, p.y, x0.astype(np.float64))
+    assert np.linalg.norm(oracle.gradient(op, p.y, x)) <= 1e-4 * np.linalg.norm(g0)
+    xs, _, fs = oracle.run(op, p.y, x0, 400, bounds=[0, 3, 5, 8], order=[0, 2, 1])
+    assert np.all(np.diff(fs) <= 1e-12 * np.abs(fs[1:]))
+    assert abs(fs[-1] - ft[-1]) <= 1e-8 * abs(ft[-1])

@@ -232,3 +232,104 @@ def test_paper_penalty_z_term_majorant_is_exact():
         x, xp = rng.standard_normal(shape), rng.standard_normal(shape)
         f = oracle.objective(op, y, xp)
         assert abs(_q(op, y, x, xp) - f) <= 1e-12 * abs(f)
+
+
+# ---------------------------------------------------------------------------
+# Penalty mode 2: the isotropic hyperbolic term over the three axes,
+# lambda sum_n sqrt(delta^2 + [V^X x]_n^2 + [V^Y x]_n^2 + [V^Z x]_n^2).
+# ---------------------------------------------------------------------------
+
+def test_isotropic_penalty_hand_case_D():
+    c = load_cases()["D"]
+    op = oracle.OracleProblem(c["shape"], c["psf"], **c["params"])
+    f, parts = oracle.objective(op, c["y"], c["x"], parts=True)
+    np.testing.assert_allclose(parts, [c["f1"], c["f2"], c["f3"]], rtol=1e-14)
+    np.testing.assert_allclose(oracle.gradient(op, c["y"], c["x"]), c["grad"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_isotropic_penalty_along_one_axis_reduces_to_the_per_axis_penalty(axis):
+    # A volume that extends along one axis only: the isotropic term is that axis's
+    # per-axis term, and the per-axis mode adds delta for each of the two absent axes.
+    shape = [1, 1, 1]
+    shape[2 - axis] = 9
+    shape = tuple(shape)
+    psf = np.zeros((shape[0], 1, 1, 1), np.float32)
+    psf[...] = 1.0
+    x = np.random.default_rng(60 + axis).uniform(-0.5, 1.5, shape)
+    y = np.random.default_rng(63 + axis).uniform(0, 1, shape).astype(np.float32)
+    kw = dict(lam=0.2, delta=0.3, eta=1.5)
+    op0 = oracle.OracleProblem(shape, psf, **kw)
+    op2 = oracle.OracleProblem(shape, psf, **kw, penalty=2)
+    _, p0 = oracle.objective(op0, y, x, parts=True)
+    _, p2 = oracle.objective(op2, y, x, parts=True)
+    assert abs(p2[2] - (p0[2] - 0.2 * 0.3 * 2 * 9)) <= 1e-13
+    np.testing.assert_allclose(oracle.gradient(op2, y, x), oracle.gradient(op0, y, x), rtol=1e-13, atol=1e-15)
+    v = np.random.default_rng(66 + axis).standard_normal(shape)
+    np.testing.assert_allclose(oracle.apply_A(op2, x, v), oracle.apply_A(op0, x, v), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("perm", [(2, 1, 0), (1, 0, 2), (0, 2, 1)])
+def test_isotropic_penalty_is_invariant_under_axis_permutation(perm):
+    # With H = I and a box term the objective treats the three axes alike in this
+    # mode: permuting the axes of x and y permutes the gradient and the majorant's
+    # action and leaves f unchanged (a dropped or mis-weighted axis breaks this).
+    shape = (4, 5, 6)
+    rng = np.random.default_rng(70)
+    x = rng.uniform(-0.5, 1.5, shape)
+    y = rng.uniform(0, 1, shape).astype(np.float32)
+    v = rng.standard_normal(shape)
+    kw = dict(lam=0.15, delta=0.2, eta=0.7, penalty=2)
+    op = oracle.OracleProblem(shape, np.ones((shape[0], 1, 1, 1), np.float32), **kw)
+    xs, ys, vs = (np.ascontiguousarray(np.transpose(a, perm)) for a in (x, y, v))
+    ops = oracle.OracleProblem(xs.shape, np.ones((xs.shape[0], 1, 1, 1), np.float32), **kw)
+    assert abs(oracle.objective(ops, ys, xs) - oracle.objective(op, y, x)) <= 1e-12 * abs(oracle.objective(op, y, x))
+    np.testing.assert_allclose(oracle.gradient(ops, ys, xs), np.transpose(oracle.gradient(op, y, x), perm),
+                               rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(oracle.apply_A(ops, xs, vs), np.transpose(oracle.apply_A(op, x, v), perm),
+                               rtol=1e-12, atol=1e-14)
+
+
+def _iso(seed, **kw):
+    p = synth.tiny_problem(seed=seed, **kw)
+    return p, oracle.OracleProblem(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, penalty=2)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_isotropic_penalty_gradient_central_differences(seed):
+    p, op = _iso(seed, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(80 + seed)
+    x = p.y.astype(np.float64) + 0.3 * rng.standard_normal(p.shape)
+    g = oracle.gradient(op, p.y, x)
+    h = 1e-6
+    for k in rng.choice(x.size, size=40, replace=False):
+        e = np.zeros(x.size)
+        e[k] = h
+        e = e.reshape(x.shape)
+        fd = (oracle.objective(op, p.y, x + e) - oracle.objective(op, p.y, x - e)) / (2 * h)
+        assert abs(fd - g.ravel()[k]) <= 2e-7 * max(1.0, abs(g.ravel()[k])), (k, fd, g.ravel()[k])
+
+
+def test_isotropic_penalty_gradient_at_matches_full_gradient():
+    p, op = _iso(3, shape=(5, 7, 8), psf_shape=(5, 3, 3))
+    x = synth.uniform_start(p.y, seed=3).astype(np.float64)
+    g = oracle.gradient(op, p.y, x)
+    idx = np.array([0, 1, 7, 8, 8 * 7 - 1, 8 * 7, 100, 123, x.size - 1, x.size // 2])
+    np.testing.assert_allclose(oracle.gradient_at(op, p.y, x, idx), g.ravel()[idx], rtol=1e-12, atol=1e-14)
+
+
+def test_isotropic_penalty_majorisation_and_tangency():
+    p, op = _iso(7, shape=(4, 6, 7), psf_shape=(3, 3, 3))
+    rng = np.random.default_rng(88)
+    for _ in range(200):
+        x = rng.uniform(-0.5, 1.5, p.shape)
+        xp = x + rng.standard_normal(p.shape) * rng.choice([1e-3, 1e-1, 1.0])
+        q = _q(op, p.y, x, xp)
+        assert oracle.objective(op, p.y, xp) <= q + 1e-12 * abs(q)
+    x = rng.uniform(0, 1, p.shape)
+    v = rng.standard_normal(p.shape)
+    rel = []
+    for h in (1e-3, 1e-4):
+        f0, f1 = oracle.objective(op, p.y, x), oracle.objective(op, p.y, x + h * v)
+        rel.append(abs(_q(op, p.y, x, x + h * v) - f1) / abs(f1 - f0))
+    assert rel[1] <= 0.2 * rel[0] and rel[1] < 1e-2, rel
