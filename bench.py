@@ -17,7 +17,7 @@ on the library's stream.
 Extra keys: the plain FP32 single-block form on the same volume, iterations and
 device time to relative objective gap 1e-4 for both forms (f* from a long run),
 the same volume under the penalty as Section 3.1 prints it (joint X-Y term plus
-kappa ||V^Z x||^2, kappa = 0.05),
+kappa ||V^Z x||^2, kappa = 0.05) and under the isotropic penalty over X, Y, Z,
 the per-kernel roofline, e2e through host buffers, and the FP64 CPU oracle
 timed on a bounded sample (`cpu_baseline`).
 
@@ -346,15 +346,19 @@ def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0, normalized=F
     return k, ms / 1e3, float(gap[k])
 
 
-def joint_penalty_extra(prob, args, flush, stream):
+def penalty_mode_extra(prob, args, flush, stream, mode):
     """Block and plain forms of the workload under penalty mode 1 (joint X-Y
-    hyperbolic term + kappa ||V^Z x||^2): sweeps/s, and time to the relative
-    gap 1e-4 against this objective's own f*."""
+    hyperbolic term + kappa ||V^Z x||^2) or 2 (isotropic over X, Y, Z):
+    sweeps/s, and time to the relative gap 1e-4 against this objective's own f*."""
     import dataclasses
     from paper_2002_02328_gb300 import binding
-    pj = dataclasses.replace(prob, penalty=binding.PENALTY_JOINT_XY, kappa=KAPPA_JOINT)
-    out = {"penalty": "lambda sum sqrt(delta^2 + (V^X x)^2 + (V^Y x)^2) + kappa ||V^Z x||^2",
-           "kappa": KAPPA_JOINT}
+    if mode == binding.PENALTY_JOINT_XY:
+        pj = dataclasses.replace(prob, penalty=mode, kappa=KAPPA_JOINT)
+        out = {"penalty": "lambda sum sqrt(delta^2 + (V^X x)^2 + (V^Y x)^2) + kappa ||V^Z x||^2",
+               "kappa": KAPPA_JOINT}
+    else:
+        pj = dataclasses.replace(prob, penalty=mode, kappa=0.0)
+        out = {"penalty": "lambda sum sqrt(delta^2 + (V^X x)^2 + (V^Y x)^2 + (V^Z x)^2)"}
     n = max(10, args.steps // 4)
     for key, slabs in (("block", pj.slabs), ("plain", None)):
         with binding.Solver.from_problem(pj, slabs=slabs) as s:
@@ -712,7 +716,8 @@ def ours(args):
                                        "kernel_ms_per_iteration": {k: v[0] / args.profile_iters
                                                                    for k, v in prof_mixed.items()}}}
 
-    extra["joint_xy_penalty"] = joint_penalty_extra(prob, args, flush, stream)
+    extra["joint_xy_penalty"] = penalty_mode_extra(prob, args, flush, stream, binding.PENALTY_JOINT_XY)
+    extra["isotropic_penalty"] = penalty_mode_extra(prob, args, flush, stream, binding.PENALTY_ISOTROPIC)
     cpu = None
     if not args.quick:
         fstar, settle = fstar_of(prob, args.fstar_iters)

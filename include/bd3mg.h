@@ -10,7 +10,8 @@
  *        + lambda * sum_n sum_{a in X,Y,Z} sqrt(delta^2 + ([V^a x]_n)^2)
  *
  * (the default, per-axis penalty; the form printed in Section 3.1, a joint
- * X-Y hyperbolic term plus kappa ||V^Z x||^2, is BD3MG_PENALTY_JOINT_XY)
+ * X-Y hyperbolic term plus kappa ||V^Z x||^2, is BD3MG_PENALTY_JOINT_XY, and an
+ * isotropic term over the three axes is BD3MG_PENALTY_ISOTROPIC)
  *
  * with the Majorize-Minimize Memory Gradient iteration run block by block
  * (Sections 2.2-2.3): at each step a block S (a slab of depth slices) builds
@@ -91,8 +92,12 @@ enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1 };
  *   differences share one weight w = 1/sqrt(delta^2 + [V^X x]_n^2 + [V^Y x]_n^2)
  *   in the majorant and the Z term contributes its exact Hessian
  *   2 kappa V^ZT V^Z.
+ * BD3MG_PENALTY_ISOTROPIC: f3 = lambda sum_n sqrt(delta^2 + [V^X x]_n^2
+ *   + [V^Y x]_n^2 + [V^Z x]_n^2); the three differences of a voxel share one
+ *   weight w = 1/sqrt(delta^2 + sum_a [V^a x]_n^2) in the majorant (kappa is
+ *   not used).
  * Every volume of a batch must use the same penalty mode. */
-enum { BD3MG_PENALTY_PER_AXIS = 0, BD3MG_PENALTY_JOINT_XY = 1 };
+enum { BD3MG_PENALTY_PER_AXIS = 0, BD3MG_PENALTY_JOINT_XY = 1, BD3MG_PENALTY_ISOTROPIC = 2 };
 
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
@@ -107,7 +112,7 @@ typedef struct {
     const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
     double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
     int zchunk;               /* output slices per work item; 0 -> chosen by the library */
-    int penalty;              /* BD3MG_PENALTY_PER_AXIS or BD3MG_PENALTY_JOINT_XY */
+    int penalty;              /* BD3MG_PENALTY_PER_AXIS, BD3MG_PENALTY_JOINT_XY or BD3MG_PENALTY_ISOTROPIC */
     double kappa;             /* >= 0, finite: weight of kappa ||V^Z x||^2 (BD3MG_PENALTY_JOINT_XY only) */
 } bd3mg_params;
 

@@ -25,7 +25,7 @@ _lib = None
 STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA", 4: "BD3MG_ETIMEOUT",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
 FP32, BF16_GRADIENT = 0, 1
-PENALTY_PER_AXIS, PENALTY_JOINT_XY = 0, 1
+PENALTY_PER_AXIS, PENALTY_JOINT_XY, PENALTY_ISOTROPIC = 0, 1, 2
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",

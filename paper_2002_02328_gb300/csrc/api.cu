@@ -636,7 +636,8 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
         return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
     if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_GRADIENT)
         return fail(c, BD3MG_EINVAL, "volume %d: unknown precision mode %d", vi, p.precision);
-    if (p.penalty != BD3MG_PENALTY_PER_AXIS && p.penalty != BD3MG_PENALTY_JOINT_XY)
+    if (p.penalty != BD3MG_PENALTY_PER_AXIS && p.penalty != BD3MG_PENALTY_JOINT_XY &&
+        p.penalty != BD3MG_PENALTY_ISOTROPIC)
         return fail(c, BD3MG_EINVAL, "volume %d: unknown penalty mode %d", vi, p.penalty);
     if (!(p.kappa >= 0) || !std::isfinite(p.kappa))
         return fail(c, BD3MG_EINVAL, "volume %d: kappa must be finite and >= 0", vi);
@@ -1378,8 +1379,10 @@ const KernelSet *find_kernel_set(int R, int RZ, int pm) {
     int (*fns0[])(const KernelSet **) = {kernel_sets_r1, kernel_sets_r2, kernel_sets_r3, kernel_sets_r4, kernel_sets_r5};
     int (*fns1[])(const KernelSet **) = {kernel_sets_joint_r1, kernel_sets_joint_r2, kernel_sets_joint_r3,
                                          kernel_sets_joint_r4, kernel_sets_joint_r5};
-    if (pm != 0 && pm != 1) return nullptr;
-    for (auto fn : pm ? fns1 : fns0) {
+    int (*fns2[])(const KernelSet **) = {kernel_sets_iso_r1, kernel_sets_iso_r2, kernel_sets_iso_r3,
+                                         kernel_sets_iso_r4, kernel_sets_iso_r5};
+    if (pm < 0 || pm > 2) return nullptr;
+    for (auto fn : pm == 0 ? fns0 : pm == 1 ? fns1 : fns2) {
         const KernelSet *sets;
         int n = fn(&sets);
         for (int i = 0; i < n; ++i) {

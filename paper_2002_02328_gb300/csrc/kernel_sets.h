@@ -2,7 +2,7 @@
 // tile kernels.  R is the xy PSF radius, RZ the z radius the kernels are built
 // for (a context pads its PSF factors with zero taps up to the chosen set), PM
 // the penalty mode (0 per-axis hyperbolic, 1 joint X-Y hyperbolic plus a
-// quadratic Z term).
+// quadratic Z term, 2 isotropic hyperbolic over X, Y, Z).
 #pragma once
 #include <cuda_runtime.h>
 #include <stddef.h>
@@ -47,5 +47,10 @@ int kernel_sets_joint_r2(const KernelSet **out);
 int kernel_sets_joint_r3(const KernelSet **out);
 int kernel_sets_joint_r4(const KernelSet **out);
 int kernel_sets_joint_r5(const KernelSet **out);
+int kernel_sets_iso_r1(const KernelSet **out);
+int kernel_sets_iso_r2(const KernelSet **out);
+int kernel_sets_iso_r3(const KernelSet **out);
+int kernel_sets_iso_r4(const KernelSet **out);
+int kernel_sets_iso_r5(const KernelSet **out);
 
 }  // namespace bd3mg

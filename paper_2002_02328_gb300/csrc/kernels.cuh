@@ -611,7 +611,7 @@ __device__ __forceinline__ void ypass_pair2(const float *T1, int yo, int c, cons
 // tx, ty, tz (0 where the neighbour does not exist): acc0 += r^2/2,
 // acc1 += dist(xc, [xmin, xmax])^2, and the penalty (divided by lambda) into
 // acc2: PM 0: sum_a sqrt(delta^2 + t_a^2); PM 1: sqrt(delta^2 + tx^2 + ty^2)
-// + (kappa/lambda) tz^2.
+// + (kappa/lambda) tz^2; PM 2: sqrt(delta^2 + tx^2 + ty^2 + tz^2).
 template <int PM>
 __device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty, float tz, float delta2, float kl,
                                           float xmin, float xmax, float (&acc)[3]) {
@@ -622,9 +622,12 @@ __device__ __forceinline__ void obj_terms(float rr, float xc, float tx, float ty
     if constexpr (PM == 0) {
         const float vx = fmaf(tx, tx, delta2), vy = fmaf(ty, ty, delta2), vz = fmaf(tz, tz, delta2);
         acc[2] += vx * rsqrtf(vx) + vy * rsqrtf(vy) + vz * rsqrtf(vz);
-    } else {
+    } else if constexpr (PM == 1) {
         const float v = fmaf(tx, tx, fmaf(ty, ty, delta2));
         acc[2] += fmaf(kl * tz, tz, v * rsqrtf(v));
+    } else {
+        const float v = fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2)));
+        acc[2] += v * rsqrtf(v);
     }
 }
 
@@ -1003,7 +1006,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                     };
                     q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
                     q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
-                } else {
+                } else if constexpr (PM == 1) {
                     // Joint X-Y weight w = 1/sqrt(delta^2 + tX^2 + tY^2) of a voxel, with tX,
                     // tY its forward differences (0 where the +neighbour does not exist).  The
                     // gradient needs w at the four voxels and at their -x and -y neighbours;
@@ -1043,6 +1046,71 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
                                      gval(q0.y, p0.y, pen01, zq(p0.y, zl0.y, zr0.y)));
                     q1 = make_float2(gval(q1.x, p1.x, pen10, zq(p1.x, zl1.x, zr1.x)),
                                      gval(q1.y, p1.y, pen11, zq(p1.y, zl1.y, zr1.y)));
+                } else {
+                    // Isotropic weight w = 1/sqrt(delta^2 + tX^2 + tY^2 + tZ^2) of a voxel (its
+                    // forward differences, 0 where the +neighbour does not exist), needed at
+                    // the four voxels and at their -x, -y and -z neighbours.  Besides the
+                    // values loaded above this reads, on slice zo, (yo-1, c+2) and
+                    // (yo+2, c-1); on zo+1, column c-1 of rows yo, yo+1 and row yo-1 of
+                    // columns c, c+1; on zo-1, column c+2 of rows yo, yo+1 and row yo+2 of
+                    // columns c, c+1.
+                    const float q3 = (yu && xr1) ? __ldg(xr - pitch + 2) : 0.f;                 // (zo, yo-1, c+2)
+                    const float s2 = (yd2 && xl) ? __ldg(xr + 2 * pitch - 1) : 0.f;            // (zo, yo+2, c-1)
+                    const float zrm0 = (zr && xl) ? __ldg(xr + plane - 1) : 0.f;               // (zo+1, yo, c-1)
+                    const float zrm1 = (zr && xl && r1ok) ? __ldg(xr + plane + pitch - 1) : 0.f;
+                    const float2 zru = (zr && yu) ? __ldg(reinterpret_cast<const float2 *>(xr + plane - pitch))
+                                                  : make_float2(0.f, 0.f);                    // (zo+1, yo-1, c..c+1)
+                    const float zle0 = (zl && xr1) ? __ldg(xr - plane + 2) : 0.f;              // (zo-1, yo, c+2)
+                    const float zle1 = (zl && xr1 && r1ok) ? __ldg(xr - plane + pitch + 2) : 0.f;
+                    const float2 zld = (zl && yd2) ? __ldg(reinterpret_cast<const float2 *>(xr - plane + 2 * pitch))
+                                                   : make_float2(0.f, 0.f);                   // (zo-1, yo+2, c..c+1)
+                    auto w_of = [&](float tx, float ty, float tz) {
+                        return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2))));
+                    };
+                    // own voxels
+                    const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
+                    const float tz00 = zr ? zr0.x - p0.x : 0.f;
+                    const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
+                    const float tz01 = (zr && c1ok) ? zr0.y - p0.y : 0.f;
+                    const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
+                    const float tz10 = (zr && r1ok) ? zr1.x - p1.x : 0.f;
+                    const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
+                    const float tz11 = (zr && r1ok && c1ok) ? zr1.y - p1.y : 0.f;
+                    // -x neighbours (yo, c-1), (yo+1, c-1): only tX enters their outflow to us
+                    const float txl0 = xl ? p0.x - m0 : 0.f;
+                    const float wl0 = w_of(txl0, (xl && r1ok) ? m1 - m0 : 0.f, (xl && zr) ? zrm0 - m0 : 0.f);
+                    const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f;
+                    const float wl1 = w_of(txl1, (xl && yd2) ? s2 - m1 : 0.f, (xl && zr && r1ok) ? zrm1 - m1 : 0.f);
+                    // -y neighbours (yo-1, c), (yo-1, c+1)
+                    const float tyu0 = yu ? p0.x - pu.x : 0.f;
+                    const float wu0 = w_of((yu && c1ok) ? pu.y - pu.x : 0.f, tyu0, (yu && zr) ? zru.x - pu.x : 0.f);
+                    const float tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
+                    const float wu1 = w_of((yu && xr1) ? q3 - pu.y : 0.f, tyu1, (yu && zr && c1ok) ? zru.y - pu.y : 0.f);
+                    // -z neighbours (slice zo-1) of the four voxels
+                    const float tzb00 = zl ? p0.x - zl0.x : 0.f;
+                    const float wb00 = w_of((zl && c1ok) ? zl0.y - zl0.x : 0.f, (zl && r1ok) ? zl1.x - zl0.x : 0.f, tzb00);
+                    const float tzb01 = (zl && c1ok) ? p0.y - zl0.y : 0.f;
+                    const float wb01 = w_of((zl && xr1) ? zle0 - zl0.y : 0.f, (zl && r1ok && c1ok) ? zl1.y - zl0.y : 0.f,
+                                            tzb01);
+                    const float tzb10 = (zl && r1ok) ? p1.x - zl1.x : 0.f;
+                    const float wb10 = w_of((zl && r1ok && c1ok) ? zl1.y - zl1.x : 0.f, (zl && yd2) ? zld.x - zl1.x : 0.f,
+                                            tzb10);
+                    const float tzb11 = (zl && r1ok && c1ok) ? p1.y - zl1.y : 0.f;
+                    const float wb11 = w_of((zl && r1ok && xr1) ? zle1 - zl1.y : 0.f,
+                                            (zl && yd2 && c1ok) ? zld.y - zl1.y : 0.f, tzb11);
+                    const float w00 = w_of(tx00, ty00, tz00), w01 = w_of(tx01, ty01, tz01);
+                    const float w10 = w_of(tx10, ty10, tz10), w11 = w_of(tx11, ty11, tz11);
+                    // sum_a V^aT (w t_a): inflow from the -x, -y, -z neighbours minus own outflow
+                    const float pen00 = wl0 * txl0 + wu0 * tyu0 + wb00 * tzb00 - w00 * (tx00 + ty00 + tz00);
+                    const float pen01 = w00 * tx00 + wu1 * tyu1 + wb01 * tzb01 - w01 * (tx01 + ty01 + tz01);
+                    const float pen10 = wl1 * txl1 + w00 * ty00 + wb10 * tzb10 - w10 * (tx10 + ty10 + tz10);
+                    const float pen11 = w10 * tx10 + w01 * ty01 + wb11 * tzb11 - w11 * (tx11 + ty11 + tz11);
+                    auto gval = [&](float q, float xc, float pen) {
+                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+                        return fmaf(lam, pen, fmaf(eta2, dist, q));
+                    };
+                    q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
+                    q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
                 }
             }
             if (c0ok) {
@@ -1158,6 +1226,17 @@ __device__ __forceinline__ void pen_joint(float tx, float ty, float vgx, float v
     acc[6] = fmaf(w, fmaf(vgx, vgx, vgy * vgy), acc[6]);
     acc[7] = fmaf(w, fmaf(vgx, vdx, vgy * vdy), acc[7]);
     acc[8] = fmaf(w, fmaf(vdx, vdx, vdy * vdy), acc[8]);
+}
+
+// Penalty mode 2: the three differences of a voxel share the weight
+// w = 1/sqrt(delta^2 + tx^2 + ty^2 + tz^2) (all differences 0 where the
+// neighbour does not exist).
+__device__ __forceinline__ void pen_iso(float tx, float ty, float tz, float vgx, float vgy, float vgz, float vdx,
+                                        float vdy, float vdz, float delta2, float *acc) {
+    const float w = rsqrtf(fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2))));
+    acc[6] = fmaf(w, fmaf(vgx, vgx, fmaf(vgy, vgy, vgz * vgz)), acc[6]);
+    acc[7] = fmaf(w, fmaf(vgx, vdx, fmaf(vgy, vdy, vgz * vdz)), acc[7]);
+    acc[8] = fmaf(w, fmaf(vdx, vdx, fmaf(vdy, vdy, vdz * vdz)), acc[8]);
 }
 
 // Penalty mode 1, Z: the quadratic term kappa ||V^Z x||^2 is its own majorant;
@@ -1353,11 +1432,17 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
                     if (xe0) pen_axis(xa[k].x, xa[k].y, ga[k].x, ga[k].y, da[k].x, da[k].y, delta2, acc);
                     if (yeo[k]) pen_axis(xa[k].x, xa[k + 1].x, ga[k].x, ga[k + 1].x, da[k].x, da[k + 1].x, delta2, acc);
                     if (ze) pen_axis(xa[k].x, xz[k].x, ga[k].x, gz[k].x, da[k].x, dz[k].x, delta2, acc);
-                } else {
+                } else if constexpr (PM == 1) {
                     pen_joint(xe0 ? xa[k].y - xa[k].x : 0.f, yeo[k] ? xa[k + 1].x - xa[k].x : 0.f,
                               xe0 ? ga[k].y - ga[k].x : 0.f, yeo[k] ? ga[k + 1].x - ga[k].x : 0.f,
                               xe0 ? da[k].y - da[k].x : 0.f, yeo[k] ? da[k + 1].x - da[k].x : 0.f, delta2, acc);
                     if (ze) pen_quad(gz[k].x - ga[k].x, dz[k].x - da[k].x, kl2, acc);
+                } else {
+                    pen_iso(xe0 ? xa[k].y - xa[k].x : 0.f, yeo[k] ? xa[k + 1].x - xa[k].x : 0.f,
+                            ze ? xz[k].x - xa[k].x : 0.f, xe0 ? ga[k].y - ga[k].x : 0.f,
+                            yeo[k] ? ga[k + 1].x - ga[k].x : 0.f, ze ? gz[k].x - ga[k].x : 0.f,
+                            xe0 ? da[k].y - da[k].x : 0.f, yeo[k] ? da[k + 1].x - da[k].x : 0.f,
+                            ze ? dz[k].x - da[k].x : 0.f, delta2, acc);
                 }
                 // voxel (yo+k, c+1)
                 if (c1ok) {
@@ -1372,11 +1457,17 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
                         if (yeo[k])
                             pen_axis(xa[k].y, xa[k + 1].y, ga[k].y, ga[k + 1].y, da[k].y, da[k + 1].y, delta2, acc);
                         if (ze) pen_axis(xa[k].y, xz[k].y, ga[k].y, gz[k].y, da[k].y, dz[k].y, delta2, acc);
-                    } else {
+                    } else if constexpr (PM == 1) {
                         pen_joint(xe1 ? xev[k] - xa[k].y : 0.f, yeo[k] ? xa[k + 1].y - xa[k].y : 0.f,
                                   xe1 ? gev[k] - ga[k].y : 0.f, yeo[k] ? ga[k + 1].y - ga[k].y : 0.f,
                                   xe1 ? dev[k] - da[k].y : 0.f, yeo[k] ? da[k + 1].y - da[k].y : 0.f, delta2, acc);
                         if (ze) pen_quad(gz[k].y - ga[k].y, dz[k].y - da[k].y, kl2, acc);
+                    } else {
+                        pen_iso(xe1 ? xev[k] - xa[k].y : 0.f, yeo[k] ? xa[k + 1].y - xa[k].y : 0.f,
+                                ze ? xz[k].y - xa[k].y : 0.f, xe1 ? gev[k] - ga[k].y : 0.f,
+                                yeo[k] ? ga[k + 1].y - ga[k].y : 0.f, ze ? gz[k].y - ga[k].y : 0.f,
+                                xe1 ? dev[k] - da[k].y : 0.f, yeo[k] ? da[k + 1].y - da[k].y : 0.f,
+                                ze ? dz[k].y - da[k].y : 0.f, delta2, acc);
                     }
                 }
             }

@@ -70,7 +70,8 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
         return fail(BD3MG_EINVAL, "volume extents must be >= 1 and PSF extents odd, with a PSF");
     if (!(p->lambda > 0) || !(p->delta > 0) || !(p->eta >= 0) || !(p->xmin <= p->xmax))
         return fail(BD3MG_EINVAL, "need lambda > 0, delta > 0, eta >= 0, xmin <= xmax");
-    if ((p->penalty != BD3MG_PENALTY_PER_AXIS && p->penalty != BD3MG_PENALTY_JOINT_XY) || !(p->kappa >= 0) ||
+    if ((p->penalty != BD3MG_PENALTY_PER_AXIS && p->penalty != BD3MG_PENALTY_JOINT_XY &&
+         p->penalty != BD3MG_PENALTY_ISOTROPIC) || !(p->kappa >= 0) ||
         !(p->kappa < HUGE_VAL))
         return fail(BD3MG_EINVAL, "unknown penalty mode, or kappa not finite and >= 0");
     // The caller's volumes are read in place by TMA: rows must start on 16-byte boundaries.

@@ -41,7 +41,7 @@ class Problem:
     xmax: float = 1.0
     slabs: Optional[List[int]] = None    # slab boundaries z_0=0 < ... < z_S=nz
     meta: dict = field(default_factory=dict)
-    penalty: int = 0                     # 0 per-axis hyperbolic; 1 joint X-Y hyperbolic + kappa ||V^Z x||^2
+    penalty: int = 0                     # 0 per-axis; 1 joint X-Y + kappa ||V^Z x||^2; 2 isotropic X, Y, Z
     kappa: float = 0.0
 
     @property
