@@ -153,7 +153,10 @@ int bd3mg_volume_count(bd3mg_ctx *ctx);
 /* Run n >= 0 iterations (one iteration = one sweep over all slabs of every
  * volume).  If f_trace is not NULL it receives nvol*(n+1) host doubles,
  * volume-major: f(x^k) of each volume before each sweep and after the last.
- * Synchronises the stream. */
+ * Every entry takes its data term 1/2 ||r||^2 from the carried residual r
+ * (bd3mg_objective applies H to x afresh; the two agree to ~1e-8 relative, the
+ * FP32 evaluation accuracy), so a run split across calls reports the same
+ * trace.  Synchronises the stream. */
 bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
 
 /* Enqueue n iterations without synchronising and without reading anything back

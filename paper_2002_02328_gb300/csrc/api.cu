@@ -113,6 +113,7 @@ struct bd3mg_ctx {
     std::vector<Item> items_h;
     std::vector<int> slot_beg_h, slot_id_h, seg_lists_h, seg_list_off;
     Launch L_obj, L_res_full, L_grad_full, L_hd;
+    Launch L_objc;                      // k_objective (carried residual): CTA ranges per volume, no items
     std::vector<Launch> L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
@@ -287,6 +288,30 @@ Launch make_launch(bd3mg_ctx *c, const std::vector<int> &segs, F range, SlotMode
     return L;
 }
 
+// Launch of k_objective: no items; volume v owns a contiguous range of CTAs in
+// proportion to its voxels, one wave of ctas_per_wave in total.
+Launch make_objective_launch(bd3mg_ctx *c, int ctas_per_wave) {
+    Launch L;
+    L.item_off = (int)c->items_h.size();
+    L.beg_off = (int)c->slot_beg_h.size();
+    L.slot_off = (int)c->slot_id_h.size();
+    long long total = 0;
+    for (const VolState &v : c->V) total += (long long)v.p.nx * v.p.ny * v.p.nz;
+    const long long target = std::max(1, ctas_per_wave);
+    int beg = 0;
+    for (int v = 0; v < c->nvol; ++v) {
+        const long long n = (long long)c->V[v].p.nx * c->V[v].p.ny * c->V[v].p.nz;
+        c->slot_beg_h.push_back(beg);
+        c->slot_id_h.push_back(v);
+        beg += (int)std::max(1LL, (target * n + total - 1) / total);
+    }
+    c->slot_beg_h.push_back(beg);
+    L.nslots = c->nvol;
+    L.nitems = beg;
+    c->max_items = std::max(c->max_items, L.nitems);
+    return L;
+}
+
 KArgs make_args(bd3mg_ctx *c, const Launch &L, int mode, const VolDev *vols) {
     KArgs a{};
     a.vols = vols ? vols : c->vols;
@@ -335,6 +360,21 @@ bd3mg_status run_residual(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
     bd3mg_status st = prof_mark(c, s, (mode & M_STORE_R) ? BD3MG_K_RESIDUAL : BD3MG_K_OBJECTIVE);
     if (st) return st;
     c->ks->residual(a, s);
+    return check_launch(c);
+}
+
+// Objective pass from the carried residual (r must be current: the pass that
+// opens a sweep); same slots, partials and finish as run_residual's objective.
+bd3mg_status run_objective(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode) {
+    if (L.nitems == 0) return BD3MG_OK;
+    KArgs a = make_args(c, L, mode, nullptr);
+    if (s == c->aux_stream) {
+        a.partials = c->partials_obj;
+        a.ticket = c->ticket_obj;
+    }
+    bd3mg_status st = prof_mark(c, s, BD3MG_K_OBJECTIVE);
+    if (st) return st;
+    launch_objective(a, s, c->ks->PM);
     return check_launch(c);
 }
 
@@ -387,18 +427,19 @@ bool stopping_enabled(const bd3mg_ctx *c) {
 
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
-    // The objective pass that opens the sweep reads x and y and only has to
-    // finish before the first update writes x; without stopping (whose flag it
-    // sets for the later launches) it runs as a parallel branch of the graph
-    // beside colour 0's gradient and curvature.
+    // The objective pass that opens the sweep reads x and the carried residual
+    // r (current here: exact after a refresh, carried by every update since)
+    // and only has to finish before the first update writes x and r; without
+    // stopping (whose flag it sets for the later launches) it runs as a
+    // parallel branch of the graph beside colour 0's gradient and curvature.
     const bool branch = !c->prof_on && s == c->cap_stream && !stopping_enabled(c);
     if (branch) {
         CK(cudaEventRecord(c->ev_fork, s));
         CK(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
-        if ((st = run_residual(c, c->aux_stream, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
+        if ((st = run_objective(c, c->aux_stream, c->L_objc, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
         CK(cudaEventRecord(c->ev_join, c->aux_stream));
     } else {
-        if ((st = run_residual(c, s, c->L_obj, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
+        if ((st = run_objective(c, s, c->L_objc, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
         if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
@@ -730,6 +771,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     for (int s = 0; s < c->nslab_segs; ++s) slabs.push_back(s);
     auto whole = [&](int s, int *lo, int *hi) { *lo = 0; *hi = c->segs_h[s].z1; };
     c->L_obj = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
+    c->L_objc = make_objective_launch(c, c->sms * std::max(1, objective_occupancy(c->ks->PM)));
     c->L_res_full = make_launch(c, full, whole, SLOTS_PER_VOLUME, 0);
     c->L_grad_full = make_launch(c, full, whole, SLOTS_NONE, 1);
     c->L_hd = make_launch(c, slabs, [&](int s, int *lo, int *hi) { *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; },
@@ -792,7 +834,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
     AL(c->partials, (size_t)c->max_items * 10);    // up to 10 partial sums per item
-    AL(c->ticket, 1); AL(c->ticket_obj, 1); AL(c->partials_obj, (size_t)std::max(1, c->L_obj.nitems) * 3);
+    AL(c->ticket, 1); AL(c->ticket_obj, 1); AL(c->partials_obj, (size_t)std::max(1, std::max(c->L_obj.nitems, c->L_objc.nitems)) * 3);
     AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
     AL(c->sh, 1); AL(c->counter, 1); AL(c->status, 1); AL(c->run, nvol);
 #undef AL
@@ -1064,7 +1106,13 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
         if ((st = launch_iterations(c, n))) return st;
     }
     c->iterations = base + n;
-    if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ | M_TRACE))) return st;
+    // f(x^n) from the carried residual, like every sweep's entry, so a run split
+    // across calls gives the same trace; r is brought to the state the next
+    // sweep would see (the refresh it is due, if any) first
+    if (c->stale || c->since_refresh >= kRefreshEvery) {
+        if ((st = refresh_products(c))) return st;
+    }
+    if ((st = run_objective(c, c->stream, c->L_objc, M_OBJ | M_TRACE))) return st;
     if (f_trace)
         CK(cudaMemcpy2DAsync(f_trace, sizeof(double) * (n + 1), c->trace, sizeof(double) * c->trace_cap,
                              sizeof(double) * (n + 1), c->nvol, cudaMemcpyDeviceToHost, c->stream));

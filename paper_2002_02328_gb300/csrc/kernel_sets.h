@@ -34,6 +34,12 @@ const KernelSet *find_kernel_set(int R, int RZ, int pm);
 // run (nullable) marks stopped volumes.
 void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
                    const VolRun *run, dim3 grid, cudaStream_t s, bool bf16);
+// Objective of every volume from the carried residual (no convolution),
+// penalty mode pm: a.nitems CTAs, volume slot sl owning CTAs
+// [slot_beg[sl], slot_beg[sl+1]); same reduction and finish as k_residual's
+// objective mode.  objective_occupancy: resident CTAs per SM of that kernel.
+void launch_objective(const KArgs &a, cudaStream_t s, int pm);
+int objective_occupancy(int pm);
 // dst[i] = float(src[i]) for n BF16 elements.
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
 

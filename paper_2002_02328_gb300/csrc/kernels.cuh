@@ -20,9 +20,11 @@
 //               H d_S and the residual r += H d_S(new) on the slab's zone, in update.cu
 //
 // So every iteration blurs twice (H^T r and H g_S) instead of four times: the
-// residual and H d_S follow the iterate through the linear update.  Both are
-// recomputed exactly (k_residual) when x or d is set from outside and every
-// few hundred iterations, which bounds the FP32 drift of the recurrences.
+// residual and H d_S follow the iterate through the linear update, and the
+// objective pass that opens a sweep (k_objective, update.cu) reads the carried
+// residual instead of blurring x.  Both are recomputed exactly (k_residual)
+// when x or d is set from outside and every few hundred iterations, which
+// bounds the FP32 drift of the recurrences.
 //
 // The blur H is depth-variant with a separable PSF per OUTPUT depth z:
 // h_z(a,b,c) = fx_z(a) fy_z(b) fz_z(c).  Forward: z-combine the input slices

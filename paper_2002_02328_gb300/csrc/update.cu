@@ -1,6 +1,6 @@
 // update.cu -- the block update x_S += D u, d_S = D u (Master box step (2))
-// with the images of the update under H, and the BF16-to-FP32 copy-out of a
-// BF16 gradient.
+// with the images of the update under H, the objective of each sweep from the
+// carried residual, and the BF16-to-FP32 copy-out of a BF16 gradient.
 #include <algorithm>
 
 #include "kernel_sets.h"
@@ -73,6 +73,64 @@ __global__ void __launch_bounds__(NT) k_update(const VolDev *vols, const SegDev 
     }
 }
 
+// ---------------------------------------------------------------------------
+// k_objective: f(x) (Section 3.1, Eq. "crit") of every volume from the
+// carried residual r = H x - y, without a convolution: per voxel 1/2 r^2, the
+// box distance and the penalty of penalty mode PM (the per-voxel terms of
+// k_residual's objective mode), FP32 per thread, FP64 per CTA and across CTAs
+// in a fixed order; the last CTA forms f per volume, the trace entry and the
+// stopping test (objective_finish).  It opens each sweep, where r is current:
+// exact after a refresh and carried by every update since.
+// Volume slot sl owns CTAs [slot_beg[sl], slot_beg[sl+1]) (in proportion to
+// its voxels, one wave in all: the CTAs stride over the rows, so occupancy,
+// not the grid, keeps the loads in flight); each warp takes whole rows (y, z) in turn and its lanes read
+// four voxels of x and r per float4, with the +y and +z neighbours' float4
+// (L1/L2 hits) and the next voxel in x, so HBM sees x and r once.
+// ---------------------------------------------------------------------------
+template <int PM>
+__global__ void __launch_bounds__(NT, 6) k_objective(KArgs a) {
+    int sl = 0;
+    while (sl + 1 < a.nslots && a.slot_beg[sl + 1] <= (int)blockIdx.x) ++sl;
+    const int vid = a.slot_id[sl];
+    if (vol_stopped(a, vid)) {
+        if (publish_zero<3>(a.partials, a.ticket, a.nitems)) objective_finish(a);
+        return;
+    }
+    const int bx = (int)blockIdx.x - a.slot_beg[sl], gx = a.slot_beg[sl + 1] - a.slot_beg[sl];
+    const VolDev &V = a.vols[vid];
+    const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
+    const long long plane = V.plane, rows = (long long)ny * nz;
+    const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, kl = V.kl;
+    const int lane = threadIdx.x & 31, nq = (nx + 3) >> 2;    // float4 columns holding voxels
+    float acc[3] = {0.f, 0.f, 0.f};                            // data, box, penalty / lambda
+    for (long long row = (long long)bx * NWARP + (threadIdx.x >> 5); row < rows; row += (long long)gx * NWARP) {
+        const int z = (int)(row / ny), y = (int)(row - (long long)z * ny);
+        const bool yok = y + 1 < ny, zok = z + 1 < nz;
+        // rows start on 32-byte boundaries (pitch is a multiple of 8 elements)
+        const float *xr = V.x + (long long)z * plane + (long long)y * pitch;
+        const float4 *x4 = reinterpret_cast<const float4 *>(xr);
+        const float4 *r4 = reinterpret_cast<const float4 *>(V.r + (long long)z * plane + (long long)y * pitch);
+        for (int q = lane; q < nq; q += 32) {
+            const int x0 = 4 * q;
+            const float4 xv = __ldg(x4 + q), rv = __ldg(r4 + q);
+            const float4 xy = yok ? __ldg(reinterpret_cast<const float4 *>(xr + pitch) + q) : xv;
+            const float4 xz = zok ? __ldg(reinterpret_cast<const float4 *>(xr + plane) + q) : xv;
+            const float xe = x0 + 4 < nx ? __ldg(xr + x0 + 4) : 0.f;
+            const float xs[5] = {xv.x, xv.y, xv.z, xv.w, xe};
+            const float ys[4] = {xy.x, xy.y, xy.z, xy.w}, zs[4] = {xz.x, xz.y, xz.z, xz.w};
+            const float rs[4] = {rv.x, rv.y, rv.z, rv.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (x0 + k < nx)
+                    obj_terms<PM>(rs[k], xs[k], x0 + k + 1 < nx ? xs[k + 1] - xs[k] : 0.f,
+                                  yok ? ys[k] - xs[k] : 0.f, zok ? zs[k] - xs[k] : 0.f, delta2, kl, xmin, xmax,
+                                  acc);
+            }
+        }
+    }
+    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
+}
+
 __global__ void __launch_bounds__(NT) k_dir_to_float(const __nv_bfloat16 *src, float *dst, long long n) {
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
         dst[i] = __bfloat162float(src[i]);
@@ -82,6 +140,20 @@ void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, 
                    const VolRun *run, dim3 grid, cudaStream_t s, bool bf16) {
     if (bf16) k_update<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
     else k_update<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+}
+
+void launch_objective(const KArgs &a, cudaStream_t s, int pm) {
+    if (pm == 1) k_objective<1><<<a.nitems, NT, 0, s>>>(a);
+    else if (pm == 2) k_objective<2><<<a.nitems, NT, 0, s>>>(a);
+    else k_objective<0><<<a.nitems, NT, 0, s>>>(a);
+}
+
+int objective_occupancy(int pm) {
+    int n = 0;
+    cudaError_t e = pm == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_objective<1>, NT, 0)
+                  : pm == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_objective<2>, NT, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_objective<0>, NT, 0);
+    return e == cudaSuccess ? n : 0;
 }
 
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s) {

@@ -67,3 +67,25 @@ def test_set_x_continues_like_a_new_context(cuda_lib, bounds):
         xb = b.get_x().cpu().numpy()
     assert np.array_equal(tr_a, tr_b)
     assert np.array_equal(xa, xb)
+
+
+@pytest.mark.parametrize("bounds,precision", [(None, 0), ([0, 3, 7, 12], 0), (None, 1)])
+def test_sweep_objective_from_the_carried_residual(cuda_lib, bounds, precision):
+    """Every trace entry takes its data term from the carried residual;
+    bd3mg_objective applies H to x afresh.  At the same iterate -- after 5
+    iterations, and after 252, shortly before the exact refresh at 256, when the
+    carried r has drifted most -- both are within 1e-6 of the FP64 oracle's
+    objective at that iterate and of each other: the two differ only in the
+    residual entering 1/2 r^2, each an FP32 evaluation (the spec trace bound
+    against the oracle is 1e-5).  The end of a call and the start of the next
+    report the same value, bit for bit."""
+    p = synth.tiny_problem(shape=(12, 32, 40), psf_shape=(5, 5, 5), seed=43, n_ellipsoids=6, slabs=bounds)
+    op = oracle.OracleProblem.from_synth(p)
+    with cuda_lib.Solver.from_problem(p, precision=precision) as s:
+        for n in (5, 246):
+            carried = s.iterate(n)[-1]              # f(x^k) at the end of the call
+            exact = s.objective()                   # H x afresh
+            ref = oracle.objective(op, p.y, s.get_x().cpu().numpy())
+            assert abs(carried - ref) <= 1e-6 * abs(ref), (n, carried, ref)
+            assert abs(exact - ref) <= 1e-6 * abs(ref), (n, exact, ref)
+            assert s.iterate(1)[0] == carried       # the pass that opens the next sweep
