@@ -114,11 +114,15 @@ typedef struct {
     int zchunk;               /* output slices per work item; 0 -> chosen by the library */
     int penalty;              /* BD3MG_PENALTY_PER_AXIS, BD3MG_PENALTY_JOINT_XY or BD3MG_PENALTY_ISOTROPIC */
     double kappa;             /* >= 0, finite: weight of kappa ||V^Z x||^2 (BD3MG_PENALTY_JOINT_XY only) */
+    int refresh_every;        /* >= 0: iterations between exact recomputations of r and H d_S; 0 -> 256 */
+    int barrier_timeout_ms;   /* 0..600000: limit of every bounded device wait (TMA slice copies);
+                                 0 -> 2000.  A wait that runs out makes the call return BD3MG_ETIMEOUT */
 } bd3mg_params;
 
 /* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,
- * eta = 1, box [0, 1], no slabs, kappa = 0, extents zero: the caller must set
- * nx..pz and psf). */
+ * eta = 1, box [0, 1], no slabs, kappa = 0, refresh every 256 iterations,
+ * 2 s device wait limit, extents zero: the caller must set nx..pz and psf).
+ * refresh_every and barrier_timeout_ms of a batch are taken from p[0]. */
 void bd3mg_params_default(bd3mg_params *p);
 
 /* Create a context: validates *p, factors each depth's PSF (the fast path
@@ -273,6 +277,17 @@ int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
  * negative or non-finite tol or a NULL at. */
 bd3mg_status bd3mg_set_escalation(bd3mg_ctx *ctx, double tol);
 bd3mg_status bd3mg_escalated(bd3mg_ctx *ctx, long long *at);
+
+/* Fault injection for testing failure detection (no counterpart in the paper).
+ * BD3MG_FAULT_SKIP_COPY: from the next iteration on, the first CTA of every
+ * curvature launch leaves the copy of one input slice out, so nothing
+ * completes the shared-memory barrier it then waits on; that bounded wait runs
+ * out after barrier_timeout_ms, the CTA waits (again bounded) for its other
+ * copies and returns, and the call reports BD3MG_ETIMEOUT (the context is then
+ * poisoned; the CUDA context stays usable).  Nothing traps, faults or hangs.
+ * BD3MG_FAULT_NONE turns it off.  Takes effect at the next launch. */
+enum { BD3MG_FAULT_NONE = 0, BD3MG_FAULT_SKIP_COPY = 1 };
+bd3mg_status bd3mg_inject_fault(bd3mg_ctx *ctx, int kind);
 
 /* Checkpoint / resume.  bd3mg_save writes the state an iteration starts from
  * (x, the memory direction d and the residual r of every volume, the images

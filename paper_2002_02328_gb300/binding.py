@@ -26,6 +26,7 @@ STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
 FP32, BF16_GRADIENT = 0, 1
 PENALTY_PER_AXIS, PENALTY_JOINT_XY, PENALTY_ISOTROPIC = 0, 1, 2
+FAULT_NONE, FAULT_SKIP_COPY = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
@@ -34,7 +35,7 @@ EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iter
             "bd3mg_launches_per_iteration", "bd3mg_profile_iteration", "bd3mg_objective_noalloc",
             "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_set_stopping",
             "bd3mg_stopped", "bd3mg_set_escalation", "bd3mg_escalated", "bd3mg_save", "bd3mg_load",
-            "bd3mg_autotune", "bd3mg_error_string",
+            "bd3mg_autotune", "bd3mg_inject_fault", "bd3mg_error_string",
             "bd3mg_status_string", "bd3mg_destroy"]
 
 
@@ -52,7 +53,8 @@ class Params(ctypes.Structure):
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
                 ("precision", ctypes.c_int), ("nslabs", ctypes.c_int), ("slab_bounds", ctypes.c_void_p),
                 ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int),
-                ("penalty", ctypes.c_int), ("kappa", ctypes.c_double)]
+                ("penalty", ctypes.c_int), ("kappa", ctypes.c_double),
+                ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -101,6 +103,7 @@ def load(path: str = LIB_PATH):
             "bd3mg_objective_noalloc": (ip, [P, vp, vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]),
             "bd3mg_set_escalation": (ip, [vp, dp]),
             "bd3mg_escalated": (ip, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+            "bd3mg_inject_fault": (ip, [vp, ip]),
             "bd3mg_save": (ip, [vp, ctypes.c_char_p]),
             "bd3mg_load": (ip, [vp, ctypes.c_char_p]),
             "bd3mg_autotune": (ip, [ip, P, vp, ip, vp, ip, ctypes.c_char_p, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
@@ -151,7 +154,8 @@ def _torch_allocator():
 
 def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
-                zchunk: int = 0, penalty: int = 0, kappa: float = 0.0):
+                zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
+                barrier_timeout_ms: int = 0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -166,6 +170,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.pinv_rtol = float(pinv_rtol)
     p.zchunk = int(zchunk)
     p.penalty, p.kappa = int(penalty), float(kappa)
+    p.refresh_every, p.barrier_timeout_ms = int(refresh_every), int(barrier_timeout_ms)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -255,13 +260,14 @@ class Solver:
 
     def __init__(self, shape, psf, y, x0=None, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
-                 use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0):
+                 use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
+                 barrier_timeout_ms: int = 0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
-                                   penalty, kappa)
+                                   penalty, kappa, refresh_every, barrier_timeout_ms)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -357,6 +363,10 @@ class Solver:
         at = ctypes.c_longlong()
         self._c(self._lib.bd3mg_escalated(self._ctx, ctypes.byref(at)))
         return int(at.value)
+
+    def inject_fault(self, kind: int = FAULT_SKIP_COPY):
+        """Test hook: make the next iterations' bounded device waits run out (bd3mg_inject_fault)."""
+        self._c(self._lib.bd3mg_inject_fault(self._ctx, int(kind)))
 
     def save(self, path: str):
         """Checkpoint x, d and the iteration count to `path`."""

@@ -13,7 +13,8 @@
 // The residual r = H x - y and the images H d_S of the slabs' memory
 // directions (in per-slab zone buffers) follow the iterate through the update
 // (kernels.cuh); they are recomputed exactly before the first iteration after
-// x or d was set from outside, and every kRefreshEvery iterations.
+// x or d was set from outside, and every refresh_every iterations (256 unless
+// the parameters say otherwise).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -106,6 +107,9 @@ struct bd3mg_ctx {
     int trace_cap = 0;
     VolRun *run = nullptr;          // per-volume stopping state
     double tol2 = 0.0;              // squared step tolerance (0: off)
+    long long refresh_every = 256;  // iterations between exact refreshes of r and H d_S
+    unsigned long long wait_ns = WAIT_NS;   // device wait limit of the tile kernels
+    int fault = 0;                  // host-set fault injection (FAULT_SKIP_COPY)
     std::vector<double> f_target;   // per volume (-inf: none)
     int *counter = nullptr, *status = nullptr;
 
@@ -452,7 +456,6 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
 
 // Exact r = H x - y of every volume and H d_S of every slab (d masked to the
 // slab) into its zone buffer, on the context stream.
-constexpr long long kRefreshEvery = 256;
 bd3mg_status refresh_products(bd3mg_ctx *c) {
     bd3mg_status st;
     if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
@@ -465,7 +468,7 @@ bd3mg_status refresh_products(bd3mg_ctx *c) {
 // n graph launches of one iteration each, with the refreshes they are due.
 bd3mg_status launch_iterations(bd3mg_ctx *c, int n) {
     for (int k = 0; k < n; ++k) {
-        if (c->stale || c->since_refresh >= kRefreshEvery) {
+        if (c->stale || c->since_refresh >= c->refresh_every) {
             bd3mg_status st = refresh_products(c);
             if (st) return st;
         }
@@ -476,7 +479,7 @@ bd3mg_status launch_iterations(bd3mg_ctx *c, int n) {
 }
 
 bd3mg_status upload_shared(bd3mg_ctx *c) {
-    Shared sh{c->trace, c->trace_cap, 0, c->counter, c->status, c->run, c->tol2};
+    Shared sh{c->trace, c->trace_cap, 0, c->counter, c->status, c->run, c->tol2, c->wait_ns, c->fault};
     CK(cudaMemcpyAsync(c->sh, &sh, sizeof(Shared), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));      // keep `sh` alive until copied
     return BD3MG_OK;
@@ -715,6 +718,11 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         RZ = std::max(RZ, (pp[v].pz - 1) / 2);
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
+    if (pp[0].refresh_every < 0) return fail(c, BD3MG_EINVAL, "refresh_every must be >= 0 (0: every 256 iterations)");
+    if (pp[0].barrier_timeout_ms < 0 || pp[0].barrier_timeout_ms > 600000)
+        return fail(c, BD3MG_EINVAL, "barrier_timeout_ms must be in [0, 600000] (0: 2000)");
+    c->refresh_every = pp[0].refresh_every > 0 ? pp[0].refresh_every : 256;
+    if (pp[0].barrier_timeout_ms > 0) c->wait_ns = 1000000ull * (unsigned long long)pp[0].barrier_timeout_ms;
     c->zchunk = pp[0].zchunk;
     c->bf = pp[0].precision == BD3MG_BF16_GRADIENT;
     for (int v = 1; v < nvol; ++v)
@@ -1109,7 +1117,7 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     // f(x^n) from the carried residual, like every sweep's entry, so a run split
     // across calls gives the same trace; r is brought to the state the next
     // sweep would see (the refresh it is due, if any) first
-    if (c->stale || c->since_refresh >= kRefreshEvery) {
+    if (c->stale || c->since_refresh >= c->refresh_every) {
         if ((st = refresh_products(c))) return st;
     }
     if ((st = run_objective(c, c->stream, c->L_objc, M_OBJ | M_TRACE))) return st;
@@ -1224,6 +1232,14 @@ bd3mg_status bd3mg_set_escalation(bd3mg_ctx *c, double tol) {
     if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(c, BD3MG_EINVAL, "escalation tol must be finite and >= 0");
     c->esc_tol = tol;
     return BD3MG_OK;
+}
+
+bd3mg_status bd3mg_inject_fault(bd3mg_ctx *c, int kind) {
+    GUARD(c);
+    if (kind != BD3MG_FAULT_NONE && kind != BD3MG_FAULT_SKIP_COPY)
+        return fail(c, BD3MG_EINVAL, "unknown fault kind %d", kind);
+    c->fault = kind == BD3MG_FAULT_SKIP_COPY ? FAULT_SKIP_COPY : 0;
+    return upload_shared(c);
 }
 
 bd3mg_status bd3mg_escalated(bd3mg_ctx *c, long long *at) {
@@ -1382,7 +1398,7 @@ bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, 
 
 bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
     GUARD(c);
-    if (c->stale || c->since_refresh >= kRefreshEvery) {
+    if (c->stale || c->since_refresh >= c->refresh_every) {
         bd3mg_status sr = refresh_products(c);
         if (sr) return sr;
     }

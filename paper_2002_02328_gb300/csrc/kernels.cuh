@@ -137,7 +137,15 @@ struct Shared {                   // device-resident context words (graph-stable
     int *status;
     VolRun *run;                  // [volume] or null (no stopping)
     double tol2;                  // tol^2 of the step rule (0: off)
+    unsigned long long wait_ns;   // limit of every bounded mbarrier wait of the tile kernels
+    int fault;                    // FAULT_SKIP_COPY: CTA 0 of each curvature launch skips one slice copy
 };
+
+// Host-set fault injection (Shared::fault).  FAULT_SKIP_COPY makes CTA 0 of
+// every k_curvature launch skip the TMA copy of its first slab slice: nothing
+// ever completes that slot's mbarrier phase, so the CTA's bounded wait runs
+// out, it drains its other copies and returns, and the host reads ST_TIMEOUT.
+constexpr int FAULT_SKIP_COPY = 1;
 
 
 
@@ -263,16 +271,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait for the phase with the given parity; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the phase with the given parity; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - t0 > WAIT_NS) return false;
+        if (global_ns() - t0 > limit_ns) return false;
         __nanosleep(64);
     }
     return true;
 }
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) { return mbar_wait(bar, parity, WAIT_NS); }
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
@@ -652,6 +661,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
+    const unsigned long long wait_ns = a.sh->wait_ns;
     const SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
@@ -724,7 +734,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
         const bool emit = zo >= it.zo0;
         bool ok = true;
         if (zi >= xlo && zi < xhi) {
-            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            ok = mbar_wait(bar + S, (par >> S) & 1u, wait_ns);
             if (ok) par ^= 1u << S;
         }
         const float *cfr = CF + (zo - zbeg) * G::CFS;
@@ -804,7 +814,7 @@ __global__ void __launch_bounds__(NT, 3) k_residual(KArgs a) {
             for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
                 if (z < xlo || z >= xhi) continue;
                 const int s = (z - zbeg) % NS;
-                if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+                if (mbar_wait(bar + s, (par >> s) & 1u, wait_ns)) par ^= 1u << s;
             }
             atomicOr(a.sh->status, ST_TIMEOUT);
         }
@@ -858,6 +868,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
     const Item it = a.items[blockIdx.x];
+    const unsigned long long wait_ns = a.sh->wait_ns;
     const SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
@@ -913,7 +924,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
         const bool ld = zi >= rlo && zi < rhi;
         bool ok = true;
         if (ld) {
-            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            ok = mbar_wait(bar + S, (par >> S) & 1u, wait_ns);
             if (ok) par ^= 1u << S;
         }
         const float *cfi = CF + (zi - zbeg) * G::CFS;
@@ -1151,7 +1162,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
         for (int z = zi; z < min(zi + PREF, zend + PREF); ++z) {
             if (z < rlo || z >= rhi) continue;
             const int s = (z - zbeg) % NS;
-            if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+            if (mbar_wait(bar + s, (par >> s) & 1u, wait_ns)) par ^= 1u << s;
         }
         atomicOr(a.sh->status, ST_TIMEOUT);
     }
@@ -1282,6 +1293,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_OUT_FLOATS);
 
     const Item it = a.items[blockIdx.x];
+    const unsigned long long wait_ns = a.sh->wait_ns;
     const SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
@@ -1309,9 +1321,11 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
     constexpr int FILL = (int)(SLOT * sizeof(T) / 16);
     // slice z of g_S into ring slot s: a TMA copy when z is a slab slice, else zeros
+    // (FAULT_SKIP_COPY: CTA 0 leaves the copy of its first slab slice out)
+    const bool skip_first = a.sh->fault == FAULT_SKIP_COPY && blockIdx.x == 0;
     auto issue = [&](int z, int s) {
         if (z >= glo && z < ghi) {
-            if (tid == 0) {
+            if (tid == 0 && !(skip_first && z == glo)) {
                 mbar_expect_tx(bar + s, nb);
                 tma_load_3d(sgs + s * SLOT, mg, bx0, by0, z, bar + s);
             }
@@ -1370,7 +1384,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
         const bool pen = emit && v00 && zo >= pen_lo && zo < pen_hi;
         bool ok = true;
         if (zi >= glo && zi < ghi) {
-            ok = mbar_wait(bar + S, (par >> S) & 1u);
+            ok = mbar_wait(bar + S, (par >> S) & 1u, wait_ns);
             if (ok) par ^= 1u << S;
         }
         // x and d_S of the rows and their +x, +y, +z neighbours, and H d_S, fetched early
@@ -1543,7 +1557,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
             for (int z = zi; z < min(zi + PF, zend + PF); ++z) {
                 if (z < glo || z >= ghi) continue;
                 const int s = (z - zbeg) % NS;
-                if (mbar_wait(bar + s, (par >> s) & 1u)) par ^= 1u << s;
+                if (mbar_wait(bar + s, (par >> s) & 1u, wait_ns)) par ^= 1u << s;
             }
             atomicOr(a.sh->status, ST_TIMEOUT);
         }

@@ -167,7 +167,8 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     slots[1] = (int)nitems;
     slots[2] = 0;                 // slot_id = {0}
     unsigned int *words = reinterpret_cast<unsigned int *>(base + o_word);
-    Shared sh{nullptr, 0, 0, reinterpret_cast<int *>(words + 1), reinterpret_cast<int *>(words + 2), nullptr, 0.0};
+    Shared sh{nullptr, 0, 0, reinterpret_cast<int *>(words + 1), reinterpret_cast<int *>(words + 2), nullptr, 0.0,
+              WAIT_NS, 0};
     std::memcpy(g_host + o_sh, &sh, sizeof(sh));
     double worst = 0.0;
     if (!factor_psf_into(*p, ks->R, ks->RZ, reinterpret_cast<float *>(g_host + o_fx),

@@ -43,10 +43,11 @@ def test_status_strings(lib):
 
 def test_params_default(lib):
     p = binding.Params()
-    p.penalty, p.kappa = 7, 3.5            # the library's defaults must reach the struct's last fields
+    p.penalty, p.kappa, p.barrier_timeout_ms = 7, 3.5, 9   # the defaults must reach the struct's last fields
     lib.bd3mg_params_default(ctypes.byref(p))
     assert p.lambda_ == 1e-2 and p.delta == 1e-2 and p.eta == 1.0 and p.xmax == 1.0 and p.nslabs == 1
     assert p.penalty == binding.PENALTY_PER_AXIS and p.kappa == 0.0
+    assert p.refresh_every == 0 and p.barrier_timeout_ms == 0      # library defaults: 256 iterations, 2 s
 
 
 def test_slab_colouring_of_the_8_slab_workload(lib):
