@@ -418,13 +418,18 @@ def batch_extra(iters, stream):
     ok = all(v is not None for v in k)
     # lockstep with per-volume stopping at f <= f* + gap |f*|: a volume that
     # reaches its target drops out of every later launch
-    t_stop, k_stop = None, None
+    t_stop, k_stop, t_stop_model = None, None, None
     if ok:
         with binding.BatchSolver(probs, zchunk=zc) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
             # the synchronous call drops stopped volumes from the work lists between chunks
             t_stop = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
             k_stop = [int(v) for v in bs.stopped()]
+        # the same with the cost model's z-chunks, which the library re-chooses for
+        # the volumes still running each time some stop
+        with binding.BatchSolver(probs) as bs:
+            bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
+            t_stop_model = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,
             "autotuned_zchunk": zc, "lockstep_iterations_per_s_default_zchunk": 1.0 / t_default,
@@ -432,6 +437,7 @@ def batch_extra(iters, stream):
             "fstar_iters": iters, "fstar_settle_rel": settle,
             "iters_to_gap": k,
             "time_to_gap_s": {"batched_with_stopping": t_stop,
+                              "batched_with_stopping_model_zchunk": t_stop_model,
                               "batched_lockstep": (max(k) * t_batch) if ok else None,
                               "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None},
             "stopped_after": k_stop}
@@ -583,7 +589,15 @@ def e2e_run(prob, n_iter, stream):
     dt = time.perf_counter() - t0
     h2d = prob.y.nbytes + prob.psf.nbytes
     d2h = x_host.numel() * 4 + tr.nbytes
-    return n_iter / dt, h2d / n_iter, d2h / n_iter, dt
+    return n_iter / dt, h2d / n_iter, d2h / n_iter, dt, x_host.numpy()
+
+
+def snr_db(a, ref):
+    """Signal-to-noise ratio 10 log10(||ref||^2 / ||a - ref||^2) in dB, the restoration
+    quality measure the paper reports (Section 4)."""
+    a = np.asarray(a, np.float64)
+    ref = np.asarray(ref, np.float64)
+    return float(10.0 * np.log10(np.sum(ref * ref) / np.sum((a - ref) ** 2)))
 
 
 def max_over_ranks(ms_per_step: float, world: int, device) -> float:
@@ -740,9 +754,16 @@ def ours(args):
         extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
         if not args.no_warm_start:
             extra["warm_start_512x512x128"] = warm_start_extra(args, stream, extra["mixed_512x512x128"]["fstar"])
-        e2e_rate, h2d, d2h, e2e_s = e2e_run(prob, 500, stream)
+        e2e_rate, h2d, d2h, e2e_s, x500 = e2e_run(prob, 500, stream)
         e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}
+        # the workload's box [xmin, xmax] clips the phantom's overlapping ellipsoids
+        # (which reach several times xmax), so the SNR is given against the phantom
+        # and against the phantom clipped to the box
+        xt_box = np.clip(prob.x_true, prob.xmin, prob.xmax)
+        extra["snr_db"] = {"observation_y": {"phantom": snr_db(prob.y, prob.x_true), "phantom_in_box": snr_db(prob.y, xt_box)},
+                           "after_500_sweeps": {"phantom": snr_db(x500, prob.x_true),
+                                                "phantom_in_box": snr_db(x500, xt_box)}}
     else:
         e2e = None
     if not args.no_cpu_baseline and world == 1:

@@ -66,7 +66,10 @@ struct bd3mg_ctx {
     cudaStream_t aux_stream = nullptr;  // second capture stream: the objective branch of a block-form sweep
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<char> plan_active;      // volumes the per-colour work lists cover (stopped ones are dropped)
-    std::vector<int> colour_zc;         // z-chunk of each per-colour launch, fixed at creation
+    std::vector<int> colour_zc;         // z-chunk of each per-colour launch (0: choose on the next build)
+    std::vector<int> colour_zc0;        // the chunks chosen at creation for every volume
+    size_t items_cap = 0;               // device work-list capacity (items)
+    int items_per_launch_cap = 0;       // largest launch the partial-sum buffer holds
     size_t base_items = 0, base_beg = 0, base_slot = 0;   // sizes of the lists before the per-colour launches
     double *partials_obj = nullptr;     // reduction slots and ticket of the objective branch
     unsigned int *ticket_obj = nullptr;
@@ -457,6 +460,7 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
 // Exact r = H x - y of every volume and H d_S of every slab (d masked to the
 // slab) into its zone buffer, on the context stream.
 bd3mg_status refresh_products(bd3mg_ctx *c) {
+    NvtxRange nvtx_("bd3mg refresh r, H d_S");
     bd3mg_status st;
     if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
     if ((st = run_residual(c, c->stream, c->L_hd, M_STORE_R | M_ZONE))) return st;
@@ -498,6 +502,7 @@ bd3mg_status ensure_trace(bd3mg_ctx *c, int need) {
 
 // Clear the stopping state of volume vol (all volumes when vol < 0), keeping the targets.
 bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active);
+bool work_lists_fit(const bd3mg_ctx *c);
 
 bd3mg_status reset_run(bd3mg_ctx *c, int vol) {
     std::vector<VolRun> h(c->nvol);
@@ -566,6 +571,7 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
 // a re-plan) is updated in place, which costs far less than a new
 // instantiation; otherwise it is replaced.
 bd3mg_status capture_graph(bd3mg_ctx *c) {
+    NvtxRange nvtx_("bd3mg capture iteration graph");
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "begin capture: %s", cudaGetErrorString(e));
     bd3mg_status es = enqueue_iteration(c, c->cap_stream);
@@ -602,6 +608,7 @@ bd3mg_status upload_work_lists(bd3mg_ctx *c);
 // forms), the FP32 curvature kernel's work lists (lower tiles, same z-chunks),
 // FP32 descriptors, and a new iteration graph.
 bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
+    NvtxRange nvtx_("bd3mg escalate to FP32 gradient");
     if (!c->bf) return BD3MG_OK;
     bd3mg_status st;
     for (VolState &vs : c->V) {
@@ -610,6 +617,10 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     }
     c->bf = false;
     build_colour_launches(c, c->plan_active);       // the FP32 kernel's curvature tiles
+    if (!work_lists_fit(c)) {                       // re-planned chunks: back to the creation-time ones
+        c->colour_zc = c->colour_zc0;
+        build_colour_launches(c, c->plan_active);
+    }
     if ((st = upload_work_lists(c))) return st;
     if ((st = upload_descriptors(c))) return st;
     c->esc_at = c->iterations;
@@ -659,10 +670,33 @@ bd3mg_status upload_work_lists(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+// Whether the per-colour work lists fit the device buffers sized at creation.
+bool work_lists_fit(const bd3mg_ctx *c) {
+    if (c->items_h.size() > c->items_cap) return false;
+    for (const Launch &L : c->L_grad)
+        if (L.nitems > c->items_per_launch_cap) return false;
+    for (const Launch &L : c->L_curv)
+        if (L.nitems > c->items_per_launch_cap) return false;
+    return true;
+}
+
 // Re-plan the per-colour launches for the given active set and re-capture the graph.
 bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active) {
+    NvtxRange nvtx_("bd3mg re-plan work lists");
     if (active == c->plan_active) return BD3MG_OK;
-    build_colour_launches(c, active);
+    if (c->zchunk > 0) {
+        build_colour_launches(c, active);   // the caller's chunk: every running volume keeps its items and sums
+    } else {
+        // chunks chosen by the cost model for the volumes still running (the
+        // last few volumes then get enough CTAs); their partial sums regroup, so
+        // the iterates match an uncompacted run to rounding, not bit for bit
+        c->colour_zc.clear();
+        build_colour_launches(c, active);
+        if (!work_lists_fit(c)) {
+            c->colour_zc = c->colour_zc0;
+            build_colour_launches(c, active);
+        }
+    }
     bd3mg_status st = upload_work_lists(c);
     if (st) return st;
     return capture_graph(c);
@@ -706,6 +740,7 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
 // Shared body of bd3mg_create and bd3mg_batch_create.
 bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const float *const *ys,
                          const float *const *x0s, int data_on_device) {
+    NvtxRange nvtx_("bd3mg create");
     if (nvol < 1) return fail(c, BD3MG_EINVAL, "need at least one volume");
     c->nvol = nvol;
     c->V.resize(nvol);
@@ -798,6 +833,9 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         c->bf = true;
         build_colour_launches(c, std::vector<char>(nvol, 1));
     }
+    c->colour_zc0 = c->colour_zc;
+    c->items_cap = items_cap;
+    c->items_per_launch_cap = c->max_items;
 
     cudaError_t ce = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking);
@@ -1057,6 +1095,7 @@ bd3mg_status bd3mg_batch_create(int nvol, const bd3mg_params *p, const float *co
 int bd3mg_volume_count(bd3mg_ctx *c) { return c ? c->nvol : 0; }
 
 bd3mg_status bd3mg_iterate_async(bd3mg_ctx *c, int n) {
+    NvtxRange nvtx_("bd3mg iterate async");
     GUARD(c);
     if (n < 0) return fail(c, BD3MG_EINVAL, "n < 0");
     bd3mg_status st = launch_iterations(c, n);
@@ -1066,6 +1105,7 @@ bd3mg_status bd3mg_iterate_async(bd3mg_ctx *c, int n) {
 }
 
 bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
+    NvtxRange nvtx_("bd3mg iterate");
     GUARD(c);
     if (n < 0) return fail(c, BD3MG_EINVAL, "n < 0");
     bd3mg_status st;
@@ -1278,6 +1318,7 @@ bool ckpt_io(bd3mg_ctx *c, std::fstream &f, void *dev, size_t n, bool write, std
 }  // namespace
 
 bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
+    NvtxRange nvtx_("bd3mg save");
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
     std::fstream f(path, std::ios::out | std::ios::binary | std::ios::trunc);
@@ -1306,6 +1347,7 @@ bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
 }
 
 bd3mg_status bd3mg_load(bd3mg_ctx *c, const char *path) {
+    NvtxRange nvtx_("bd3mg load");
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
     std::fstream f(path, std::ios::in | std::ios::binary);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/bd3mg.h"
+#include "plan.h"
 
 namespace {
 
@@ -54,6 +55,7 @@ int cache_lookup(const char *path, const std::string &key) {
 extern "C" bd3mg_status bd3mg_autotune(int nvol, const bd3mg_params *p, const float *const *y, int data_on_device,
                                        void *stream, int iters, const char *cache_path, int *zchunk,
                                        double *ms_per_iteration) {
+    bd3mg::NvtxRange nvtx_("bd3mg autotune");
     if (nvol < 1 || !p || !y || !zchunk || iters < 1) return BD3MG_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

@@ -3,12 +3,24 @@
 #pragma once
 #include <cuda.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <utility>
 #include <vector>
 
 #include "../../include/bd3mg.h"
 
 namespace bd3mg {
+
+// Named NVTX range over a host scope (create, iterate, refresh, capture,
+// re-plan, checkpoint I/O, autotune), shown by profilers that record NVTX;
+// without one attached the calls return at once.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // 3D tile map over a pitched volume of float32 (esize 4) or bfloat16 (esize 2)
 // elements: dims (nx, ny, nz), row pitch in elements (pitch*esize a multiple
