@@ -18,6 +18,9 @@ Extra keys: the plain FP32 single-block form on the same volume, iterations and
 device time to relative objective gap 1e-4 for both forms (f* from a long run),
 the same volume under the penalty as Section 3.1 prints it (joint X-Y term plus
 kappa ||V^Z x||^2, kappa = 0.05) and under the isotropic penalty over X, Y, Z,
+the 16-volume batch (lockstep rate, time to gap with per-volume stopping under
+the autotuned and the cost model's z-chunks, against sequential single-volume
+contexts), the SNR of y and of a 500-sweep solve against the phantom,
 the per-kernel roofline, e2e through host buffers, and the FP64 CPU oracle
 timed on a bounded sample (`cpu_baseline`).
 

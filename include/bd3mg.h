@@ -133,8 +133,9 @@ void bd3mg_params_default(bd3mg_params *p);
  * slab): the residual r = H x - y and the images H d_S of the slabs' memory
  * directions follow the iterate through the update (H d_S(new) = -u0 H g_S +
  * u1 H d_S, r += H d_S(new)), and are recomputed exactly before the first
- * iteration after creation, bd3mg_set_x or bd3mg_load, and every 256
- * iterations.  data_on_device: y and x0 are device pointers
+ * iteration after creation or bd3mg_set_x, and every refresh_every (256)
+ * iterations; bd3mg_load restores them with the refresh schedule.  Each
+ * sweep's objective takes its data term from the carried r.  data_on_device: y and x0 are device pointers
  * (else host).  stream: cudaStream_t as void*.  alloc may be NULL. */
 bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
                           void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);

@@ -1,7 +1,7 @@
 """GPU checks of the state the update carries from one iteration to the next:
 the residual r = H x - y and the images H d_S of the slabs' memory directions
 (H d_S(new) = -u0 H g_S + u1 H d_S, r += H d_S(new)), recomputed exactly
-before the first iteration after creation, set_x or load, and every 256
+before the first iteration after creation or set_x, and every 256
 iterations.  Runs longer than a refresh period must keep the oracle parity of
 the 200-iteration test, and a context whose iterate was set from outside
 must continue exactly like one created at that iterate."""
