@@ -111,7 +111,11 @@ typedef struct {
     int nslabs;               /* number of depth blocks; 0 or 1 = plain 3MG on the whole volume */
     const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
     double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
-    int zchunk;               /* output slices per work item; 0 -> chosen by the library */
+    int zchunk;               /* output slices per work item; 0 -> chosen by the library's cost model,
+                                 and chosen again for the volumes still running when some volumes
+                                 of a batch stop (their sums regroup: iterates equal to rounding);
+                                 > 0 -> kept for every launch (stopping then leaves every running
+                                 volume bit-identical to an uncompacted run) */
     int penalty;              /* BD3MG_PENALTY_PER_AXIS, BD3MG_PENALTY_JOINT_XY or BD3MG_PENALTY_ISOTROPIC */
     double kappa;             /* >= 0, finite: weight of kappa ||V^Z x||^2 (BD3MG_PENALTY_JOINT_XY only) */
     int refresh_every;        /* >= 0: iterations between exact recomputations of r and H d_S; 0 -> 256 */
@@ -135,8 +139,9 @@ void bd3mg_params_default(bd3mg_params *p);
  * u1 H d_S, r += H d_S(new)), and are recomputed exactly before the first
  * iteration after creation or bd3mg_set_x, and every refresh_every (256)
  * iterations; bd3mg_load restores them with the refresh schedule.  Each
- * sweep's objective takes its data term from the carried r.  data_on_device: y and x0 are device pointers
- * (else host).  stream: cudaStream_t as void*.  alloc may be NULL. */
+ * sweep's objective takes its data term from the carried r.
+ * data_on_device: y and x0 are device pointers (else host).  stream:
+ * cudaStream_t as void*.  alloc may be NULL. */
 bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,
                           void *stream, const bd3mg_allocator *alloc, bd3mg_ctx **out);
 
@@ -145,8 +150,9 @@ bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0
  * launches).  p[v], y[v] and x0[v] (x0 may be NULL, or hold NULL entries, for
  * x0 = y) describe volume v exactly as for bd3mg_create; sizes, PSFs,
  * lambda, delta, eta and the box may differ between volumes.  The kernels are
- * chosen for the largest PSF radii (smaller PSFs are zero padded); pinv_rtol
- * and zchunk are taken from p[0].  Per-volume results: bd3mg_objectives,
+ * chosen for the largest PSF radii (smaller PSFs are zero padded); pinv_rtol,
+ * zchunk, refresh_every and barrier_timeout_ms are taken from p[0], and every
+ * volume must share p[0]'s precision and penalty mode.  Per-volume results: bd3mg_objectives,
  * bd3mg_get_volume, and the nvol traces of bd3mg_iterate.  Functions without a
  * volume index act on volume 0. */
 bd3mg_status bd3mg_batch_create(int nvol, const bd3mg_params *p, const float *const *y, const float *const *x0,
@@ -189,8 +195,9 @@ bd3mg_status bd3mg_set_stopping(bd3mg_ctx *ctx, double tol, const double *f_targ
  * Synchronises the stream. */
 bd3mg_status bd3mg_stopped(bd3mg_ctx *ctx, int *sweeps);
 
-/* Objective at the current iterate; parts (optional, 3 doubles) = data term,
- * box term, penalty term.  Synchronises. */
+/* Objective at the current iterate, with H applied to x afresh (valid at any
+ * point, e.g. right after bd3mg_set_x); parts (optional, 3 doubles) = data
+ * term, box term, penalty term.  Synchronises. */
 bd3mg_status bd3mg_objective(bd3mg_ctx *ctx, double *f, double *parts);
 
 /* Objective of every volume at the current iterates: f receives nvol host
