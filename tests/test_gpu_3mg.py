@@ -1,6 +1,6 @@
 """GPU parity of the block 3MG iteration against the FP64 oracle, through the C ABI.
 
-Bounds (spec parity targets): objective and gradient within relative 1e-5
+Parity bounds: objective and gradient within relative 1e-5
 after one iteration; iterate within relative 1e-4 (L2) after 200 iterations on
 the 64x64x24 workload (PSF 5x5x5).  The slab form is compared with the oracle
 visiting the slabs one after the other in colour-major order.  At the full

@@ -76,7 +76,7 @@ def test_sweep_objective_from_the_carried_residual(cuda_lib, bounds, precision):
     iterations, and after 252, shortly before the exact refresh at 256, when the
     carried r has drifted most -- both are within 1e-6 of the FP64 oracle's
     objective at that iterate and of each other: the two differ only in the
-    residual entering 1/2 r^2, each an FP32 evaluation (the spec trace bound
+    residual entering 1/2 r^2, each an FP32 evaluation (the trace's parity bound
     against the oracle is 1e-5).  The end of a call and the start of the next
     report the same value, bit for bit."""
     p = synth.tiny_problem(shape=(12, 32, 40), psf_shape=(5, 5, 5), seed=43, n_ellipsoids=6, slabs=bounds)

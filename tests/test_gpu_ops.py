@@ -2,8 +2,8 @@
 
 Every call goes through the C ABI (libbd3mg.so via the ctypes binding).
 Tolerances: FP32 arithmetic against FP64 -- relative L2 error 2e-6 for single
-operator applications, 1e-5 for the objective and gradient (the bound the
-spec parity target states for one iteration).
+operator applications, 1e-5 for the objective and gradient (the parity bound
+for one iteration).
 """
 import numpy as np
 import pytest
