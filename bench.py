@@ -275,9 +275,9 @@ def kernel_traffic(name: str):
 def algorithmic_bytes(prob, slabs, rz, g_bytes=4):
     """Per-class algorithmic bytes of one sweep (halos excluded; n voxels, each
     slab's zone = the slab widened by rz slices each way, at least one below):
-    objective 8 per voxel (x, y in); gradient 8 + g_bytes (r, x in; g out);
+    objective 8 per voxel (x and the carried r in); gradient 8 + g_bytes (r, x in; g out);
     curvature g_bytes + 8 per voxel (g, d, x in) + 8 per zone voxel (H d_S in,
-    H g_S out); update 12 + g_bytes per voxel (x, g, d in; x, d out) + 20 per
+    H g_S out); update 16 + g_bytes per voxel (x, g, d in; x, d out) + 20 per
     zone voxel (H g_S, H d_S, r in; H d_S, r out).  The exact refreshes of r and
     H d_S (every 256 sweeps) are not counted."""
     nz, ny, nx = prob.shape
@@ -286,7 +286,7 @@ def algorithmic_bytes(prob, slabs, rz, g_bytes=4):
     b = list(slabs) if slabs is not None and len(slabs) > 2 else [0, nz]
     zone = sum(min(nz, b[s + 1] + rz) - max(0, b[s] - max(rz, 1)) for s in range(len(b) - 1)) * plane
     return {"objective": 8.0 * n, "residual": 0.0, "gradient": (8.0 + g_bytes) * n,
-            "curvature": (g_bytes + 8.0) * n + 8.0 * zone, "update": (12.0 + g_bytes) * n + 20.0 * zone}
+            "curvature": (g_bytes + 8.0) * n + 8.0 * zone, "update": (16.0 + g_bytes) * n + 20.0 * zone}
 
 
 def refresh_launches(first: int, count: int, every: int = 256) -> int:
