@@ -597,7 +597,7 @@ def e2e_run(prob, n_iter, stream):
 
 def snr_db(a, ref):
     """Signal-to-noise ratio 10 log10(||ref||^2 / ||a - ref||^2) in dB, the restoration
-    quality measure the paper reports (Section 4)."""
+    quality measure the paper reports (Sections 3.2 and 3.3)."""
     a = np.asarray(a, np.float64)
     ref = np.asarray(ref, np.float64)
     return float(10.0 * np.log10(np.sum(ref * ref) / np.sum((a - ref) ** 2)))

@@ -69,7 +69,7 @@ typedef struct {
     void *user;
 } bd3mg_allocator;
 
-/* Storage precision of the gradient direction (Section 3.2 subspace D = [-g, d]).
+/* Storage precision of the gradient direction (Section 2.3 subspace D = [-g, d]).
  * BD3MG_FP32: g stored in FP32.
  * BD3MG_BF16_GRADIENT: g stored in BF16 (round to nearest even), halving its
  *   traffic and the curvature pass's shared-memory ring; x, y, d, the residual
@@ -176,7 +176,7 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
 bd3mg_status bd3mg_iterate_async(bd3mg_ctx *ctx, int n);
 
 /* Per-volume stopping.  Before each sweep k >= 1 the device tests every
- * running volume with the rule of the paper's scaling experiment (Section 4.2),
+ * running volume with the rule of the paper's scaling experiment (Section 3.3),
  *     ||x^k - x^{k-1}|| <= tol * ||x^{k-1}||,
  * where the step length is summed over the slab steps of sweep k-1 from the
  * FP64 subspace sums (||-u0 g + u1 d||^2 = u0^2 g.g - 2 u0 u1 g.d + u1^2 d.d)
@@ -273,7 +273,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
 /* Number of kernel launches one iteration enqueues. */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
-/* Precision escalation of the BF16-gradient form (Section 3.2's subspace D =
+/* Precision escalation of the BF16-gradient form (Section 2.3's subspace D =
  * [-g, d] with g stored in BF16).  With tol > 0, bd3mg_iterate runs
  * in chunks of 4 iterations and reads the objective trace between chunks;
  * once some volume's objective decreases by at most tol * |f| from one
@@ -344,11 +344,16 @@ bd3mg_status bd3mg_autotune(int nvol, const bd3mg_params *p, const float *const 
  *    ignored; psf is a host pointer, read during the call).
  * x, y: DEVICE volumes [nz][ny][nx], read in place; nx must be a multiple of 4
  *    and both pointers 16-byte aligned.
- * f_out: DEVICE pointer to 4 doubles, written in stream order with
- *    {f, data term, box term, penalty term}; a non-finite input shows as a
- *    non-finite f.
- * stream: cudaStream_t as void*; the call enqueues one host-to-device copy and
- *    one kernel and does not synchronise.
+ * f_out: DEVICE pointer to 4 doubles, written with {f, data term, box term,
+ *    penalty term}.  The call first fills them with NaN, so a NaN f means the
+ *    kernel did not finish (a timed-out wait) or the input was not finite;
+ *    the status returned says which.
+ * stream: cudaStream_t as void*; the call enqueues one host-to-device copy of
+ *    its plan (from pageable host memory, so the call may wait while the
+ *    driver stages it), a fill of f_out and one kernel, then synchronises the
+ *    stream to read the kernel's status word back.  Returns BD3MG_ETIMEOUT
+ *    when a wait of the kernel ran out and BD3MG_ENONFINITE for a non-finite
+ *    objective; f_out is NaN or non-finite then.
  * err, err_len: optional buffer that receives a one-line message.
  *
  * The first call on each device performs that device's set-up (it looks up

@@ -10,7 +10,7 @@ Parity status per function (what pins it is in the tests named):
   apply_H / apply_HT ........ pinned (scipy.ndimage.convolve per depth; adjoint
                               identity; delta PSF)            tests/test_oracle_ops.py
   apply_V / apply_VT ........ pinned (numpy.diff; adjoint)    tests/test_oracle_ops.py
-  objective ................. pinned (hand-computed fixture tests/golden/objective_2x1x1.txt;
+  objective ................. pinned (hand-computed fixture tests/golden/objective_hand.txt;
                               closed forms)                   tests/test_oracle_objective.py
   gradient / gradient_at .... pinned (central finite differences of objective)
   apply_A ................... pinned (majorisation inequality, tangency)

@@ -120,7 +120,7 @@ struct Item { int seg, tx0, ty0, zo0, zo1; };
 // Per-volume stopping state (device).  The objective launch that opens a
 // sweep tests the volume: it stops once the last sweep moved x by at most
 // tol * ||x|| (||x^{k+1} - x^k|| <= tol ||x^k||, the rule of the paper's
-// scaling experiment, Section 4.2) or once f(x^k) <= f_target.
+// scaling experiment, Section 3.3) or once f(x^k) <= f_target.
 struct VolRun {
     double xx_prev;               // ||x^k||^2 of the sweep's start iterate, summed over its slab steps
     double dx2;                   // ||x^{k+1} - x^k||^2 summed over the sweep's slab steps

@@ -174,8 +174,13 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     if (!factor_psf_into(*p, ks->R, ks->RZ, reinterpret_cast<float *>(g_host + o_fx),
                          reinterpret_cast<float *>(g_host + o_fy), reinterpret_cast<float *>(g_host + o_fz), &worst))
         return fail(BD3MG_EUNSUPPORTED, "PSF is not separable per depth");
+    // g_host is pageable: the driver stages the copy and the call may wait for that.
     if (cudaMemcpyAsync(base, g_host, L.off, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return fail(BD3MG_ECUDA, "copy of the call's plan into the static scratch failed");
+    // f_out starts as NaN (all bits set), so a launch that never reaches its
+    // finish leaves NaN rather than the previous call's value.
+    if (cudaMemsetAsync(f_out, 0xFF, 4 * sizeof(double), s) != cudaSuccess)
+        return fail(BD3MG_ECUDA, "clearing f_out failed");
 
     KArgs a{};
     a.vols = reinterpret_cast<const VolDev *>(base + o_vol);
@@ -194,5 +199,13 @@ extern "C" bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const flo
     a.pinv_rtol = 1e-12;
     ks->residual(a, s);
     if (cudaGetLastError() != cudaSuccess) return fail(BD3MG_ECUDA, "kernel launch failed");
+    // The status word the kernel sets on a timed-out wait or a non-finite sum:
+    // read back once the stream reaches it, so the call reports what happened.
+    int status = 0;
+    if (cudaMemcpyAsync(&status, words + 2, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return fail(BD3MG_ECUDA, "reading the status word back failed");
+    if (status & ST_TIMEOUT) return fail(BD3MG_ETIMEOUT, "a TMA slice copy did not complete within the wait limit");
+    if (status & ST_NONFINITE) return fail(BD3MG_ENONFINITE, "non-finite objective");
     return fail(BD3MG_OK, "ok");
 }

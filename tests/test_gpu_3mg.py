@@ -6,6 +6,10 @@ the 64x64x24 workload (PSF 5x5x5).  The slab form is compared with the oracle
 visiting the slabs one after the other in colour-major order.  At the full
 256x256x64 size the gradient is compared at sampled voxels and the objective in
 full; the iteration is checked through properties (descent, determinism).
+Beside the L2 bounds, element-wise bounds (max|a - b| over max|b|) catch errors
+confined to a few voxels: 2e-5 for g, x and d after one iteration, 1e-3 for
+the iterate after 200 iterations and for slab sweeps (a local error the L2 norm
+would dilute by the square root of the voxel count is far above these).
 """
 import numpy as np
 import pytest
@@ -20,6 +24,13 @@ def _rel(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _maxrel(a, b):
+    """Largest element-wise error, relative to the largest reference magnitude."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def _colour_major(bounds, pz):
@@ -61,9 +72,13 @@ def test_one_iteration_parity(cuda_lib, plain_small):
     assert abs(tr[0] - f0_ref) <= 1e-5 * abs(f0_ref)
     assert abs(tr[1] - f1_ref) <= 1e-5 * abs(f1_ref)
     assert abs(f1 - f1_ref) <= 1e-5 * abs(f1_ref)
-    assert _rel(g1.cpu().numpy(), oracle.gradient(op, p.y, x1_ref)) <= 1e-5
+    g1_ref = oracle.gradient(op, p.y, x1_ref)
+    assert _rel(g1.cpu().numpy(), g1_ref) <= 1e-5
     assert _rel(x1, x1_ref) <= 1e-5
     assert _rel(d1, d1_ref) <= 1e-5
+    assert _maxrel(g1.cpu().numpy(), g1_ref) <= 2e-5
+    assert _maxrel(x1, x1_ref) <= 2e-5
+    assert _maxrel(d1, d1_ref) <= 2e-5
     B = info["B"]
     np.testing.assert_allclose([st[0], st[1], st[2]], [B[0, 0], B[0, 1], B[1, 1]], rtol=1e-5, atol=1e-12)
     np.testing.assert_allclose(st[3:5], info["c"], rtol=1e-5, atol=1e-12)
@@ -76,6 +91,7 @@ def test_200_iterations_parity(cuda_lib, plain_small):
         tr = s.iterate(200)
         x = s.get_x().cpu().numpy()
     assert _rel(x, x200) <= 1e-4
+    assert _maxrel(x, x200) <= 1e-3
     assert np.max(np.abs(tr - ft) / np.abs(ft)) <= 1e-5
 
 
@@ -111,6 +127,7 @@ def test_slab_form_matches_sequential_oracle(cuda_lib, shape, psf_shape, bounds)
     np.testing.assert_array_equal(col, col_ref)
     assert _rel(x, xr) <= 2e-5
     assert _rel(d, dr) <= 1e-4
+    assert _maxrel(x, xr) <= 1e-3
     assert np.max(np.abs(tr - fr) / np.abs(fr)) <= 1e-5
     assert np.all(np.diff(tr) <= 1e-6 * np.abs(tr[1:]))
 

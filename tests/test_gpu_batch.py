@@ -64,6 +64,24 @@ def test_batch_volumes_follow_their_own_solves(cuda_lib):
         assert abs(fb[v] - ts[-1]) <= 1e-6 * abs(ts[-1])
 
 
+def test_full_size_batch_members_match_oracle(cuda_lib):
+    """The 16-volume recipe at full size, 3 lockstep sweeps: its two smallest
+    volumes against the oracle run on each alone (iterate and trace as the tiny
+    batch above)."""
+    probs = synth.workload_batch(count=16, seed=0)
+    order = np.argsort([p.n for p in probs])[:2]
+    oracle.set_threads(oracle.max_threads())
+    with cuda_lib.BatchSolver(probs) as b:
+        tr = b.iterate(3)
+        xs = {int(v): b.get(int(v)).cpu().numpy() for v in order}
+    for v in order:
+        p = probs[int(v)]
+        op = oracle.OracleProblem.from_synth(p)
+        xr, _, fr = oracle.run(op, p.y, p.y, 3)
+        assert _rel(xs[int(v)], xr) <= 2e-5, v
+        assert np.max(np.abs(tr[v] - fr) / np.abs(fr)) <= 1e-5, v
+
+
 def test_uneven_batch_recipe_descends(cuda_lib):
     probs = synth.workload_batch(count=16, seed=0, scale=0.5)
     with cuda_lib.BatchSolver(probs) as b:

@@ -3,7 +3,13 @@
 Every call goes through the C ABI (libbd3mg.so via the ctypes binding).
 Tolerances: FP32 arithmetic against FP64 -- relative L2 error 2e-6 for single
 operator applications, 1e-5 for the objective and gradient (the parity bound
-for one iteration).
+for one iteration).  Beside each L2 bound an element-wise bound, max|a - b|
+over max|b|, catches errors confined to a few voxels (a boundary row, a tile
+seam) that the volume norm would dilute: 1e-5 for an operator (a separable
+pass of at most 11 + 11 + 11 FP32 taps of a sum-1 PSF rounds each output by at
+most ~33 ulp of max|x|, 2e-6 of it, and max|Hx| is not below a fifth of max|x|
+here), 2e-5 for the gradient (the residual entering H^T carries the same
+rounding).
 """
 import numpy as np
 import pytest
@@ -34,6 +40,13 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
 
 
+def _maxrel(a, b):
+    """Largest element-wise error, relative to the largest reference magnitude."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
 @pytest.mark.parametrize("shape,psf_shape", SHAPES)
 def test_H_and_HT_match_oracle(cuda_lib, shape, psf_shape):
     import torch
@@ -45,8 +58,11 @@ def test_H_and_HT_match_oracle(cuda_lib, shape, psf_shape):
         xt = torch.from_numpy(x).cuda()
         hx = s.apply_H(xt).cpu().numpy()
         htx = s.apply_H(xt, adjoint=True).cpu().numpy()
-    assert _rel(hx, oracle.apply_H(op, x)) <= 2e-6
-    assert _rel(htx, oracle.apply_HT(op, x)) <= 2e-6
+    hx_ref, htx_ref = oracle.apply_H(op, x), oracle.apply_HT(op, x)
+    assert _rel(hx, hx_ref) <= 2e-6
+    assert _rel(htx, htx_ref) <= 2e-6
+    assert _maxrel(hx, hx_ref) <= 1e-5
+    assert _maxrel(htx, htx_ref) <= 1e-5
 
 
 def test_gpu_adjoint_identity(cuda_lib):
@@ -77,6 +93,7 @@ def test_objective_and_gradient_match_oracle(cuda_lib, shape, psf_shape):
     assert abs(fg - f_ref) <= 1e-5 * abs(f_ref)
     np.testing.assert_allclose(parts, parts_ref, rtol=1e-5, atol=1e-9 * abs(f_ref))
     assert _rel(g, g_ref) <= 1e-5
+    assert _maxrel(g, g_ref) <= 2e-5
 
 
 def test_non_separable_psf_is_rejected(cuda_lib):

@@ -1,5 +1,5 @@
 """GPU checks of per-volume stopping.  The rule of the paper's scaling
-experiment (Section 4.2), ||x^k - x^{k-1}|| <= tol ||x^{k-1}||, and an
+experiment (Section 3.3), ||x^k - x^{k-1}|| <= tol ||x^{k-1}||, and an
 objective target are tested on the device before every sweep; a stopped volume
 keeps its iterate while the other volumes of the batch run on unchanged."""
 import numpy as np
