@@ -121,6 +121,10 @@ typedef struct {
     int refresh_every;        /* >= 0: iterations between exact recomputations of r and H d_S; 0 -> 256 */
     int barrier_timeout_ms;   /* 0..600000: limit of every bounded device wait (TMA slice copies);
                                  0 -> 2000.  A wait that runs out makes the call return BD3MG_ETIMEOUT */
+    int separate_update;      /* 0 (default): a context whose volumes are not split into slabs applies
+                                 each iteration's update inside the next gradient pass (two passes
+                                 per iteration, see bd3mg_create); 1: separate objective and update
+                                 passes, as the slab form always runs.  Taken from p[0] of a batch */
 } bd3mg_params;
 
 /* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,
@@ -140,6 +144,15 @@ void bd3mg_params_default(bd3mg_params *p);
  * iteration after creation or bd3mg_set_x, and every refresh_every (256)
  * iterations; bd3mg_load restores them with the refresh schedule.  Each
  * sweep's objective takes its data term from the carried r.
+ * Without slabs (and separate_update = 0) an iteration is two kernel passes:
+ * the gradient pass first applies the previous iteration's update (x, d, r
+ * and H d) as it reads them, forms g and the objective of the new iterate,
+ * and writes the new state into a second buffer set; the curvature pass then
+ * builds and solves the 2x2 system.  The last update of bd3mg_iterate_async
+ * stays pending until a call that reads the state (bd3mg_iterate's end,
+ * bd3mg_objective, bd3mg_gradient, bd3mg_get_*, bd3mg_set_x, bd3mg_save,
+ * bd3mg_set_stopping) applies it.  The iterates are the same bits as with
+ * the separate update pass; the objective's summation order differs.
  * data_on_device: y and x0 are device pointers (else host).  stream:
  * cudaStream_t as void*.  alloc may be NULL. */
 bd3mg_status bd3mg_create(const bd3mg_params *p, const float *y, const float *x0, int data_on_device,

@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("nslabs", ctypes.c_int), ("slab_bounds", ctypes.c_void_p),
                 ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int),
                 ("penalty", ctypes.c_int), ("kappa", ctypes.c_double),
-                ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int)]
+                ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
+                ("separate_update", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -155,7 +156,7 @@ def _torch_allocator():
 def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
                 zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
-                barrier_timeout_ms: int = 0):
+                barrier_timeout_ms: int = 0, separate_update: int = 0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -171,6 +172,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.zchunk = int(zchunk)
     p.penalty, p.kappa = int(penalty), float(kappa)
     p.refresh_every, p.barrier_timeout_ms = int(refresh_every), int(barrier_timeout_ms)
+    p.separate_update = int(separate_update)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -261,13 +263,13 @@ class Solver:
     def __init__(self, shape, psf, y, x0=None, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
                  use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
-                 barrier_timeout_ms: int = 0):
+                 barrier_timeout_ms: int = 0, separate_update: int = 0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
-                                   penalty, kappa, refresh_every, barrier_timeout_ms)
+                                   penalty, kappa, refresh_every, barrier_timeout_ms, separate_update)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -425,7 +427,7 @@ class BatchSolver:
     """Many independent volumes iterated in lockstep by one context (plain 3MG each)."""
 
     def __init__(self, problems, x0s=None, device="cuda", zchunk: int = 0, stream=None,
-                 use_torch_allocator: bool = True, precision: int = FP32):
+                 use_torch_allocator: bool = True, precision: int = FP32, separate_update: int = 0):
         torch = _torch()
         lib = load()
         self.shapes = [tuple(int(s) for s in p.shape) for p in problems]
@@ -436,7 +438,8 @@ class BatchSolver:
         precs = list(precision) if isinstance(precision, (list, tuple)) else [precision] * self.nvol
         for v, p in enumerate(problems):
             prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precs[v], 1e-12,
-                                 zchunk, getattr(p, "penalty", 0), getattr(p, "kappa", 0.0))
+                                 zchunk, getattr(p, "penalty", 0), getattr(p, "kappa", 0.0),
+                                 separate_update=separate_update)
             arr[v] = prm
             keep.append(k)
             yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)

@@ -51,6 +51,9 @@ struct VolState {
     size_t np = 0;                  // pitch*ny*nz
     float *x = nullptr, *d = nullptr, *g = nullptr, *r = nullptr, *y = nullptr;
     __nv_bfloat16 *gh = nullptr;    // BF16 gradient (instead of g)
+    // second buffer set of the fused-update iteration (contexts without slabs)
+    float *x1 = nullptr, *d1 = nullptr, *g1 = nullptr, *r1 = nullptr;
+    __nv_bfloat16 *gh1 = nullptr;
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev dev{};                   // host copy of the device descriptor
     std::vector<int> bounds;        // slab bounds
@@ -90,6 +93,12 @@ struct bd3mg_ctx {
     bool bf = false;                // gradient g stored as BF16
     float *zone_hg = nullptr, *zone_hd = nullptr;   // H g_S, H d_S of every slab over its zone
     size_t zone_elems = 0;
+    // fused-update iteration (no slabs): the gradient pass applies the previous
+    // update; a second buffer set (x1.., zone_hg1, zone_hd1) takes what it writes
+    bool lazy = false;
+    bool pending = false;           // some graph launch may have left an update or set 1 state behind
+    float *zone_hg1 = nullptr, *zone_hd1 = nullptr;
+    int *flush_list = nullptr;      // every slab segment (one per volume), for k_flush
     bool stale = true;              // r and H d_S must be recomputed before the next iteration
     long long since_refresh = 0;    // iterations since they were last recomputed
 
@@ -124,7 +133,7 @@ struct bd3mg_ctx {
     std::vector<Launch> L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
-    int occ[5] = {1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
+    int occ[7] = {1, 1, 1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -201,8 +210,27 @@ bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const f
     return ok;
 }
 
+// Maps of the fused-update iteration: H g and H d of the volume's (whole-volume)
+// zone in both buffer sets, and r and g of the second set.
+bool encode_lazy_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v) {
+    const bd3mg_params &p = v.p;
+    const SegDev &sg = c->segs_h[v.seg0];
+    const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks), ge = c->bf ? 2 : 4, bxg = TX + 2 * set_xh(c->ks, ge);
+    const int by = TY_A + 2 * R;
+    const void *g1 = c->bf ? static_cast<const void *>(v.gh1) : static_cast<const void *>(v.g1);
+    return encode_map(&vm->m[TM_HG_R], sg.hg, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
+           encode_map(&vm->m[TM_HD_R], sg.hd, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
+           encode_map(&vm->m[TM_R1_R], v.r1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
+           encode_map(&vm->m[TM_G1_R], g1, ge, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(ge) + 2 * R) &&
+           encode_map(&vm->m[TM_HG1_R], sg.hg1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
+           encode_map(&vm->m[TM_HD1_R], sg.hd1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by);
+}
+
 // Kernel kind used for occupancy: BF16-gradient gradient/curvature have their own.
-int occ_kind(const bd3mg_ctx *c, int kind) { return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind; }
+int occ_kind(const bd3mg_ctx *c, int kind) {
+    if (c->lazy && kind == 1) return c->bf ? 6 : 5;
+    return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind;
+}
 
 // Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
 int tile_y(const bd3mg_ctx *c, int kind) { return kind == 2 ? curv_ty(c->bf ? 2 : 4) : TY_A; }
@@ -395,9 +423,20 @@ bd3mg_status run_gradient(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
     return check_launch(c);
 }
 
+// Fused-update gradient pass (contexts without slabs): applies each volume's
+// pending update, forms g and the objective (trace, stopping test with M_ITER).
+bd3mg_status run_gradlazy(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mode) {
+    if (L.nitems == 0) return BD3MG_OK;
+    KArgs a = make_args(c, L, mode | M_OBJ | M_LAZY, nullptr);
+    bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
+    if (st) return st;
+    (c->bf ? c->ks->gradlazy_bf : c->ks->gradlazy)(a, s);
+    return check_launch(c);
+}
+
 bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     if (L.nitems == 0) return BD3MG_OK;
-    KArgs a = make_args(c, L, M_ITER, nullptr);
+    KArgs a = make_args(c, L, c->lazy ? (M_ITER | M_PAR) : M_ITER, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
     (c->bf ? c->ks->curvature_bf : c->ks->curvature)(a, s);
@@ -434,6 +473,11 @@ bool stopping_enabled(const bd3mg_ctx *c) {
 
 bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     bd3mg_status st;
+    if (c->lazy) {
+        // two passes: update + gradient + objective, then curvature + solve
+        if ((st = run_gradlazy(c, s, c->L_grad[0], M_TRACE | M_ADVANCE | M_ITER))) return st;
+        return run_curvature(c, s, c->L_curv[0]);
+    }
     // The objective pass that opens the sweep reads x and the carried residual
     // r (current here: exact after a refresh, carried by every update since)
     // and only has to finish before the first update writes x and r; without
@@ -469,14 +513,37 @@ bd3mg_status refresh_products(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+// Fused-update iteration: apply every pending update and bring each volume's
+// state back to buffer set 0, where everything outside the iteration reads it.
+bd3mg_status settle(bd3mg_ctx *c) {
+    if (!c->lazy || !c->pending) return BD3MG_OK;
+    NvtxRange nvtx_("bd3mg apply pending update");
+    long long maxlen = 0;
+    for (const VolState &v : c->V) maxlen = std::max<long long>(maxlen, (long long)v.np);
+    long long blocks = (maxlen / 4 + NT - 1) / NT;
+    blocks = std::max<long long>(1, std::min<long long>(blocks, 2048));
+    launch_flush(c->vols, c->segs, c->flush_list, c->u, c->run, dim3((unsigned)blocks, (unsigned)c->nslab_segs),
+                 c->stream, c->bf);
+    bd3mg_status st = check_launch(c);
+    if (!st) {
+        launch_clear_pending(c->run, c->nvol, c->stream);
+        st = check_launch(c);
+    }
+    if (st) return st;
+    c->pending = false;
+    return BD3MG_OK;
+}
+
 // n graph launches of one iteration each, with the refreshes they are due.
 bd3mg_status launch_iterations(bd3mg_ctx *c, int n) {
     for (int k = 0; k < n; ++k) {
         if (c->stale || c->since_refresh >= c->refresh_every) {
-            bd3mg_status st = refresh_products(c);
+            bd3mg_status st = settle(c);
+            if (!st) st = refresh_products(c);
             if (st) return st;
         }
         CK(cudaGraphLaunch(c->exec, c->stream));
+        if (c->lazy) c->pending = true;
         ++c->since_refresh;
     }
     return BD3MG_OK;
@@ -505,6 +572,8 @@ bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active);
 bool work_lists_fit(const bd3mg_ctx *c);
 
 bd3mg_status reset_run(bd3mg_ctx *c, int vol) {
+    bd3mg_status sst = settle(c);          // the record below clears the pending-update words
+    if (sst) return sst;
     std::vector<VolRun> h(c->nvol);
     for (int v = 0; v < c->nvol; ++v) h[v] = VolRun{0.0, 0.0, c->f_target[v], 0, 0};
     const int v0 = vol < 0 ? 0 : vol, cnt = vol < 0 ? c->nvol : 1;
@@ -542,6 +611,7 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         d.kxy = 2 * c->ks->R + 1; d.kz = 2 * c->ks->RZ + 1;
         d.plane = (long long)vs.pitch * p.ny;
         d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.gh = vs.gh;
+        d.x1 = vs.x1; d.d1 = vs.d1; d.g1 = vs.g1; d.r1 = vs.r1; d.gh1 = vs.gh1;
         d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
@@ -553,8 +623,9 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         }
         vs.dev = d;
         vd[v] = d;
-        const bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
+        bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
                               : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
+        if (ok && c->lazy) ok = encode_lazy_maps(&vm[v], c, vs);
         if (!ok)
             return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     }
@@ -611,9 +682,14 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     NvtxRange nvtx_("bd3mg escalate to FP32 gradient");
     if (!c->bf) return BD3MG_OK;
     bd3mg_status st;
+    if ((st = settle(c))) return st;
     for (VolState &vs : c->V) {
         if (!vs.g && (st = dalloc_n(c, &vs.g, vs.np))) return st;
         CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
+        if (c->lazy) {
+            if (!vs.g1 && (st = dalloc_n(c, &vs.g1, vs.np))) return st;
+            CK(cudaMemsetAsync(vs.g1, 0, vs.np * 4, c->stream));
+        }
     }
     c->bf = false;
     build_colour_launches(c, c->plan_active);       // the FP32 kernel's curvature tiles
@@ -639,13 +715,19 @@ void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
     c->L_curv.clear();
     if (c->colour_zc.empty()) c->colour_zc.assign(2 * (size_t)c->ncolours, 0);
     for (int col = 0; col < c->ncolours; ++col) {
-        std::vector<int> segs;
+        std::vector<int> segs, gsegs;
         for (int v = 0; v < c->nvol; ++v)
             for (size_t s = 0; s < c->V[v].colour.size(); ++s)
-                if (c->V[v].colour[s] == col && active[v]) segs.push_back(c->V[v].seg0 + (int)s);
+                if (c->V[v].colour[s] == col) {
+                    if (active[v]) segs.push_back(c->V[v].seg0 + (int)s);
+                    if (active[v] || c->lazy) gsegs.push_back(c->V[v].seg0 + (int)s);
+                }
         int *zc = c->colour_zc.data() + 2 * col;
-        c->L_grad.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, SLOTS_NONE, 1, zc));
+        // The fused-update gradient pass also reduces each volume's objective and
+        // writes its trace entry, so it keeps stopped volumes (their items only
+        // take their reduction ticket) and every trace stays complete.
+        c->L_grad.push_back(make_launch(c, c->lazy ? gsegs : segs, [&](int s, int *lo, int *hi) {
+            *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; }, c->lazy ? SLOTS_PER_VOLUME : SLOTS_NONE, 1, zc));
         c->L_curv.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
             *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_PER_SEGMENT, 2, zc + 1));
         for (int s : segs) c->seg_lists_h.push_back(s);
@@ -684,6 +766,8 @@ bool work_lists_fit(const bd3mg_ctx *c) {
 bd3mg_status replan(bd3mg_ctx *c, const std::vector<char> &active) {
     NvtxRange nvtx_("bd3mg re-plan work lists");
     if (active == c->plan_active) return BD3MG_OK;
+    bd3mg_status sst = settle(c);
+    if (sst) return sst;
     if (c->zchunk > 0) {
         build_colour_launches(c, active);   // the caller's chunk: every running volume keeps its items and sums
     } else {
@@ -754,6 +838,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
     if (pp[0].refresh_every < 0) return fail(c, BD3MG_EINVAL, "refresh_every must be >= 0 (0: every 256 iterations)");
+    if (pp[0].separate_update != 0 && pp[0].separate_update != 1)
+        return fail(c, BD3MG_EINVAL, "separate_update must be 0 or 1");
     if (pp[0].barrier_timeout_ms < 0 || pp[0].barrier_timeout_ms > 600000)
         return fail(c, BD3MG_EINVAL, "barrier_timeout_ms must be in [0, 600000] (0: 2000)");
     c->refresh_every = pp[0].refresh_every > 0 ? pp[0].refresh_every : 256;
@@ -795,6 +881,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         if (vs.bounds.size() > 2) c->any_slabs = true;
     }
     c->nslab_segs = (int)c->segs_h.size();
+    // without slabs, each update is applied inside the next gradient pass
+    c->lazy = !c->any_slabs && pp[0].separate_update == 0;
     for (int v = 0; v < nvol; ++v)
         c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size(), 0, 0, nullptr, nullptr});
 
@@ -805,7 +893,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = c->ks->prepare();
         if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e));
-        for (int k = 0; k < 5; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+        for (int k = 0; k < 7; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
     }
 
     // work lists
@@ -856,6 +944,14 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         } else {
             AL(vs.g, vs.np);
         }
+        if (c->lazy) {
+            AL(vs.x1, vs.np); AL(vs.r1, vs.np); AL(vs.d1, vs.np);
+            if (c->bf) {
+                AL(vs.gh1, vs.np);
+            } else {
+                AL(vs.g1, vs.np);
+            }
+        }
         AL(vs.fx, FX[v].size()); AL(vs.fy, FY[v].size()); AL(vs.fz, FZ[v].size());
     }
     // zone buffers of the slabs, one after another (every zone a whole number of planes)
@@ -866,12 +962,20 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     AL(c->zone_hg, std::max<size_t>(c->zone_elems, 4));
     AL(c->zone_hd, std::max<size_t>(c->zone_elems, 4));
+    if (c->lazy) {
+        AL(c->zone_hg1, std::max<size_t>(c->zone_elems, 4));
+        AL(c->zone_hd1, std::max<size_t>(c->zone_elems, 4));
+    }
     {
         size_t off = 0;
         for (int s = 0; s < c->nslab_segs; ++s) {
             SegDev &sg = c->segs_h[s];
             sg.hg = c->zone_hg + off;
             sg.hd = c->zone_hd + off;
+            if (c->lazy) {
+                sg.hg1 = c->zone_hg1 + off;
+                sg.hd1 = c->zone_hd1 + off;
+            }
             off += (size_t)(sg.hz1 - sg.hz0) * c->V[sg.vol].pitch * c->V[sg.vol].p.ny;
         }
     }
@@ -879,6 +983,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     AL(c->items, items_cap);
     AL(c->slot_beg, c->slot_beg_h.size()); AL(c->slot_id, std::max<size_t>(1, c->slot_id_h.size()));
     AL(c->seg_lists, std::max<size_t>(1, c->seg_lists_h.size()));
+    AL(c->flush_list, std::max(1, c->nslab_segs));
     AL(c->partials, (size_t)c->max_items * 10);    // up to 10 partial sums per item
     AL(c->ticket, 1); AL(c->ticket_obj, 1); AL(c->partials_obj, (size_t)std::max(1, std::max(c->L_obj.nitems, c->L_objc.nitems)) * 3);
     AL(c->u, 2 * nseg); AL(c->info, 8 * nseg); AL(c->fout, 4 * (size_t)nvol);
@@ -903,12 +1008,32 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
             CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
         }
         CK(cudaMemsetAsync(vs.r, 0, vs.np * 4, c->stream));
+        if (c->lazy) {
+            CK(cudaMemsetAsync(vs.x1, 0, vs.np * 4, c->stream));
+            CK(cudaMemsetAsync(vs.r1, 0, vs.np * 4, c->stream));
+            CK(cudaMemsetAsync(vs.d1, 0, vs.np * 4, c->stream));
+            if (c->bf) {
+                CK(cudaMemsetAsync(vs.gh1, 0, vs.np * 2, c->stream));
+            } else {
+                CK(cudaMemsetAsync(vs.g1, 0, vs.np * 4, c->stream));
+            }
+        }
         CK(cudaMemcpyAsync(vs.fx, FX[v].data(), FX[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fz, FZ[v].data(), FZ[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
     }
     CK(cudaMemsetAsync(c->zone_hg, 0, c->zone_elems * 4, c->stream));
     CK(cudaMemsetAsync(c->zone_hd, 0, c->zone_elems * 4, c->stream));
+    if (c->lazy) {
+        CK(cudaMemsetAsync(c->zone_hg1, 0, c->zone_elems * 4, c->stream));
+        CK(cudaMemsetAsync(c->zone_hd1, 0, c->zone_elems * 4, c->stream));
+    }
+    {
+        std::vector<int> fl(std::max(1, c->nslab_segs), 0);
+        for (int s = 0; s < c->nslab_segs; ++s) fl[s] = s;
+        CK(cudaMemcpyAsync(c->flush_list, fl.data(), sizeof(int) * fl.size(), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
     if ((st = upload_descriptors(c))) return st;
     CK(cudaMemcpyAsync(c->segs, c->segs_h.data(), sizeof(SegDev) * nseg, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->items, c->items_h.data(), sizeof(Item) * c->items_h.size(), cudaMemcpyHostToDevice,
@@ -1156,11 +1281,18 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     c->iterations = base + n;
     // f(x^n) from the carried residual, like every sweep's entry, so a run split
     // across calls gives the same trace; r is brought to the state the next
-    // sweep would see (the refresh it is due, if any) first
+    // sweep would see (the refresh it is due, if any) first.  The fused-update
+    // form applies the last update and evaluates f with its own gradient pass
+    // (the reduction order of its trace entries; it also leaves g of x^n).
+    if ((st = settle(c))) return st;
     if (c->stale || c->since_refresh >= c->refresh_every) {
         if ((st = refresh_products(c))) return st;
     }
-    if ((st = run_objective(c, c->stream, c->L_objc, M_OBJ | M_TRACE))) return st;
+    if (c->lazy) {
+        if ((st = run_gradlazy(c, c->stream, c->L_grad[0], M_TRACE))) return st;
+    } else {
+        if ((st = run_objective(c, c->stream, c->L_objc, M_OBJ | M_TRACE))) return st;
+    }
     if (f_trace)
         CK(cudaMemcpy2DAsync(f_trace, sizeof(double) * (n + 1), c->trace, sizeof(double) * c->trace_cap,
                              sizeof(double) * (n + 1), c->nvol, cudaMemcpyDeviceToHost, c->stream));
@@ -1197,6 +1329,7 @@ bd3mg_status bd3mg_stopped(bd3mg_ctx *c, int *sweeps) {
 bd3mg_status bd3mg_objective(bd3mg_ctx *c, double *f, double *parts) {
     GUARD(c);
     bd3mg_status st;
+    if ((st = settle(c))) return st;
     if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ))) return st;
     double h[4];
     CK(cudaMemcpyAsync(h, c->fout, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
@@ -1210,6 +1343,7 @@ bd3mg_status bd3mg_objectives(bd3mg_ctx *c, double *f) {
     GUARD(c);
     if (!f) return fail(c, BD3MG_EINVAL, "f is NULL");
     bd3mg_status st;
+    if ((st = settle(c))) return st;
     if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ))) return st;
     std::vector<double> h(4 * (size_t)c->nvol);
     CK(cudaMemcpyAsync(h.data(), c->fout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
@@ -1221,6 +1355,7 @@ bd3mg_status bd3mg_objectives(bd3mg_ctx *c, double *f) {
 bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     GUARD(c);
     bd3mg_status st;
+    if ((st = settle(c))) return st;
     if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R | M_OBJ))) return st;
     if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
     if (g) {
@@ -1244,6 +1379,8 @@ bd3mg_status bd3mg_get_volume(bd3mg_ctx *c, int vol, int which, float *dst, int 
     GUARD(c);
     if (!dst || vol < 0 || vol >= c->nvol || which < 0 || which > 2)
         return fail(c, BD3MG_EINVAL, "get_volume: bad volume index, selector or NULL destination");
+    bd3mg_status sst = settle(c);
+    if (sst) return sst;
     const VolState &v = c->V[vol];
     const float *src = which == 0 ? v.x : which == 1 ? v.d : v.g;
     if (c->bf && which == 2) {
@@ -1259,6 +1396,8 @@ bd3mg_status bd3mg_get_d(bd3mg_ctx *c, float *d, int on_device) { return bd3mg_g
 bd3mg_status bd3mg_set_x(bd3mg_ctx *c, const float *x, int on_device) {
     GUARD(c);
     if (!x) return fail(c, BD3MG_EINVAL, "x is NULL");
+    bd3mg_status sst = settle(c);
+    if (sst) return sst;
     const VolState &v = c->V[0];
     CK(cudaMemsetAsync(v.d, 0, v.np * 4, c->stream));
     c->stale = true;                // r and H d_S of the new x (d = 0) before the next iteration
@@ -1321,6 +1460,8 @@ bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
     NvtxRange nvtx_("bd3mg save");
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
+    bd3mg_status sst = settle(c);
+    if (sst) return sst;
     std::fstream f(path, std::ios::out | std::ios::binary | std::ios::trunc);
     if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s for writing", path);
     CkptHead h{};
@@ -1350,6 +1491,8 @@ bd3mg_status bd3mg_load(bd3mg_ctx *c, const char *path) {
     NvtxRange nvtx_("bd3mg load");
     GUARD(c);
     if (!path) return fail(c, BD3MG_EINVAL, "path is NULL");
+    bd3mg_status sst = settle(c);
+    if (sst) return sst;
     std::fstream f(path, std::ios::in | std::ios::binary);
     if (!f) return fail(c, BD3MG_EINVAL, "cannot open %s", path);
     CkptHead h{};
@@ -1441,8 +1584,16 @@ bd3mg_status bd3mg_factor_psf(int nz, int px, int py, int pz, const float *psf, 
 bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
     GUARD(c);
     if (c->stale || c->since_refresh >= c->refresh_every) {
-        bd3mg_status sr = refresh_products(c);
+        bd3mg_status sr = settle(c);
+        if (!sr) sr = refresh_products(c);
         if (sr) return sr;
+    }
+    if (c->lazy && !c->pending) {
+        // the steady state of the fused-update form applies an update in every
+        // gradient pass: run one iteration first so that the profiled one does
+        bd3mg_status sr = launch_iterations(c, 1);
+        if (sr) return sr;
+        c->iterations += 1;
     }
     c->prof_on = true;
     c->prof_ev.clear();
@@ -1453,6 +1604,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
     if (st) return st;
     c->iterations += 1;
     c->since_refresh += 1;
+    if (c->lazy) c->pending = true;
     CK(cudaStreamSynchronize(c->stream));
     double tot[BD3MG_K_CLASSES] = {0};
     int cnt[BD3MG_K_CLASSES] = {0};
@@ -1474,7 +1626,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
     if (!c) return 0;
-    return 1 + 3 * c->ncolours;
+    return c->lazy ? 2 : 1 + 3 * c->ncolours;
 }
 
 }  // extern "C"

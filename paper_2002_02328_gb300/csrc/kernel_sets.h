@@ -20,9 +20,11 @@ struct KernelSet {
     int R, RZ, PM;
     launch_fn residual, gradient, curvature;        // FP32 gradient
     launch_fn gradient_bf, curvature_bf;            // BF16 gradient
+    launch_fn gradlazy, gradlazy_bf;                // fused-update gradient pass (FP32 / BF16 gradient)
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
     // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
-    // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient)
+    // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient), 5 fused-update
+    // gradient, 6 fused-update gradient (BF16 gradient)
     int (*occupancy)(int kind);
 };
 
@@ -40,6 +42,12 @@ void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, 
 // objective mode.  objective_occupancy: resident CTAs per SM of that kernel.
 void launch_objective(const KArgs &a, cudaStream_t s, int pm);
 int objective_occupancy(int pm);
+// Fused-update iteration: apply each listed plain volume's pending update and
+// bring its state to buffer set 0 (grid.y = number of volumes), then clear
+// every volume's set index and pending flag.
+void launch_flush(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, const VolRun *run,
+                  dim3 grid, cudaStream_t s, bool bf16);
+void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s);
 // dst[i] = float(src[i]) for n BF16 elements.
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
 

@@ -80,6 +80,10 @@ constexpr int M_ADVANCE = 8;      // k_residual: advance the trace counter
 constexpr int M_HT_ONLY = 16;     // k_gradient: output H^T r only
 constexpr int M_ITER = 32;        // launch belongs to an iteration: items of stopped volumes exit at once
 constexpr int M_ZONE = 64;        // k_residual: H d_S of each slab (d masked to the slab) into its zone buffer
+constexpr int M_LAZY = 128;       // objective finish of k_gradlazy: a volume whose pending update was applied
+                                  // now lives in its other buffer set (VolRun::par flips)
+constexpr int M_PAR = 256;        // k_curvature: read the volume's current buffer set (VolRun::par) and mark
+                                  // the new update pending (VolRun::pending)
 
 // Status bits (device word)
 constexpr int ST_NONFINITE = 1;
@@ -91,6 +95,10 @@ struct VolDev {
     long long plane;              // pitch*ny
     float *x, *d, *g, *r;         // d: FP32 memory direction; g: FP32 gradient (null in the BF16 form)
     __nv_bfloat16 *gh;            // g stored as BF16 (null in the FP32 form)
+    // second buffer set of the fused-update iteration (k_gradlazy reads one set
+    // and writes the other; null when the context does not use it)
+    float *x1, *d1, *g1, *r1;
+    __nv_bfloat16 *gh1;
     const float *y;               // null -> 0
     const float *fx, *fy, *fz;    // [nz][kxy], [nz][kxy], [nz][kz]
     float lam, delta2, eta2, xmin, xmax;
@@ -103,7 +111,12 @@ struct VolDev {
 // TMA descriptors of one volume (global memory, 64-byte aligned).
 //   X_R: x, halo R, 32-row tiles (k_residual)    R_R: r, halo R, 32-row tiles (k_gradient)
 //   G_R: g, halo R, 16-row tiles (k_curvature)   D_X: d, halo R, 32-row tiles (k_residual, M_ZONE)
-enum { TM_X_R = 0, TM_R_R = 1, TM_G_R = 2, TM_D_X = 3, TM_COUNT = 4 };
+//   HG_R, HD_R: H g and H d of a whole-volume zone, halo R, 32-row tiles (k_gradlazy)
+//   *1_*: the same maps over the second buffer set (fused-update iteration)
+enum {
+    TM_X_R = 0, TM_R_R = 1, TM_G_R = 2, TM_D_X = 3, TM_HG_R = 4, TM_HD_R = 5,
+    TM_R1_R = 6, TM_G1_R = 7, TM_HG1_R = 8, TM_HD1_R = 9, TM_COUNT = 10
+};
 struct VolMaps { CUtensorMap m[TM_COUNT]; };
 
 // A segment is one slab [z0, z1) of a volume.  Its zone [hz0, hz1) is the
@@ -114,6 +127,7 @@ struct SegDev {
     int vol, z0, z1, slot;
     int hz0, hz1;
     float *hg, *hd;
+    float *hg1, *hd1;             // zone buffers of the second buffer set (fused-update iteration), or null
 };
 struct Item { int seg, tx0, ty0, zo0, zo1; };
 
@@ -127,6 +141,11 @@ struct VolRun {
     double f_target;              // -inf: no objective target
     int stopped;                  // 1: every later iteration launch skips this volume
     int sweeps;                   // sweeps completed (x^sweeps is the result once stopped)
+    // fused-update iteration: buffer set holding the current state (0 or 1), and
+    // whether the last solve's update u is still to be applied (by the next
+    // gradient pass or by the flush); both 0 between library calls
+    int par;
+    int pending;
 };
 
 struct Shared {                   // device-resident context words (graph-stable)
@@ -517,6 +536,9 @@ static __device__ __forceinline__ void objective_finish(const KArgs &a) {
             if (!isfinite(f)) atomicOr(a.sh->status, ST_NONFINITE);
             if (trace) a.sh->trace[(size_t)vid * a.sh->trace_cap + k] = f;
             VolRun *run = a.sh->run;
+            // every CTA of this k_gradlazy launch has read par and pending: a
+            // volume whose update was applied now lives in the other buffer set
+            if (run && (a.mode & M_LAZY) && run[vid].pending) run[vid].par ^= 1;
             if (run && (a.mode & M_ADVANCE) && (a.mode & M_ITER)) {
                 VolRun &rv = run[vid];
                 const bool small_step = rv.sweeps > 0 && a.sh->tol2 > 0.0 && rv.dx2 <= a.sh->tol2 * rv.xx_prev;
@@ -846,6 +868,227 @@ __device__ __forceinline__ void ypassT_pair2(const float *T1, int yo, int c, con
 // psi'(t) = t / sqrt(delta^2 + t^2) of the hyperbolic penalty.
 __device__ __forceinline__ float dpsi(float t, float delta2) { return t * rsqrtf(fmaf(t, t, delta2)); }
 
+// psi'(t) as dpsi, and psi(t) = sqrt(delta^2 + t^2) from the same reciprocal root.
+__device__ __forceinline__ float dpsi_psi(float t, float delta2, float &psi) {
+    const float v = fmaf(t, t, delta2), w = rsqrtf(v);
+    psi = v * w;
+    return t * w;
+}
+
+// Where a thread's 2 x 2 block of voxels (rows yo, yo+1; columns c, c+1) sits in
+// the volume at depth zo, and the penalty parameters.
+struct PenCtx {
+    bool c1ok, r1ok;              // column c+1, row yo+1 exist
+    bool xl, xr1, yu, yd2, zl, zr;   // column c-1, column c+2, row yo-1, row yo+2, slice zo-1, slice zo+1 exist
+    float delta2, lam, eta2, kap2, kl, xmin, xmax;
+};
+
+// Box and penalty gradient of the block, added to q0 (row yo) and q1 (row yo+1),
+// which hold (H^T r) there: g = H^T r + 2 eta (x - P(x)) + lambda sum_a V^aT psi'(V^a x)
+// (per penalty mode PM; the quadratic Z term of mode 1 adds 2 kappa V^ZT V^Z x).
+// p0, p1: the iterate on rows yo and yo+1 (row yo+1 repeats row yo where it does
+// not exist); X1(dz, dy, dx) / X2(dz, dy, dx): the iterate at voxel
+// (zo + dz, yo + dy, c + dx), one value or the pair at columns (c + dx,
+// c + dx + 1), called with literal offsets, dz in [-1, 1], dy and dx in
+// [-1, 2], and only where the voxel exists.  The forward
+// differences are shared between the block's voxels.  With OBJ, the box term
+// dist(x, [xmin, xmax])^2 of the block's voxels that exist is added to ob[0]
+// and their penalty term, divided by lambda, to ob[1] (per voxel: PM 0,
+// sum_a sqrt(delta^2 + t_a^2); PM 1, sqrt(delta^2 + tX^2 + tY^2) + (kappa /
+// lambda) tZ^2; PM 2, sqrt(delta^2 + tX^2 + tY^2 + tZ^2); t_a the voxel's
+// forward differences, 0 on the last plane).
+template <int PM, bool OBJ, class F1, class F2>
+__device__ __forceinline__ void pen_block(const F1 &X1, const F2 &X2, const PenCtx &k, float2 p0, float2 p1,
+                                          float2 &q0, float2 &q1, float *ob) {
+    const bool c1ok = k.c1ok, r1ok = k.r1ok, xl = k.xl, xr1 = k.xr1, yu = k.yu, yd2 = k.yd2, zl = k.zl, zr = k.zr;
+    const float delta2 = k.delta2, lam = k.lam, eta2 = k.eta2, kap2 = k.kap2, xmin = k.xmin, xmax = k.xmax;
+    // row yo: columns c-1 .. c+2; row yo+1 likewise
+    const float m0 = xl ? X1(0, 0, -1) : p0.x, e0 = xr1 ? X1(0, 0, 2) : p0.y;
+    float m1 = m0, e1 = e0;
+    if (r1ok) {
+        m1 = xl ? X1(0, 1, -1) : p1.x;
+        e1 = xr1 ? X1(0, 1, 2) : p1.y;
+    }
+    const float2 pu = yu ? X2(0, -1, 0) : p0;
+    const float2 pd = yd2 ? X2(0, 2, 0) : p1;
+    const float2 zl0 = zl ? X2(-1, 0, 0) : p0;
+    const float2 zr0 = zr ? X2(1, 0, 0) : p0;
+    float2 zl1 = p1, zr1 = p1;
+    if (r1ok) {
+        if (zl) zl1 = X2(-1, 1, 0);
+        if (zr) zr1 = X2(1, 1, 0);
+    }
+    // existence of the block's voxels (the caller guarantees (yo, c))
+    const bool v01 = c1ok, v10 = r1ok, v11 = r1ok && c1ok;
+    auto boxd = [&](float xc, bool ex) {
+        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
+        if constexpr (OBJ) {
+            if (ex) ob[0] = fmaf(dist, dist, ob[0]);
+        }
+        return dist;
+    };
+    if constexpr (PM == 0) {
+        // psi(0) = delta: the penalty of a difference on a last plane
+        const float psi0 = delta2 * rsqrtf(delta2);
+        // x differences (each shared by its two voxels): row k: (c-1,c), (c,c+1), (c+1,c+2)
+        const bool hx0 = c1ok;                               // (c, c+1) is a difference of the volume
+        float sbx0 = psi0, scx0 = psi0, sbx1 = psi0, scx1 = psi0;
+        const float ax0 = xl ? dpsi(p0.x - m0, delta2) : 0.f;
+        const float bx0 = hx0 ? dpsi_psi(p0.y - p0.x, delta2, sbx0) : 0.f;
+        const float cx0 = xr1 ? dpsi_psi(e0 - p0.y, delta2, scx0) : 0.f;
+        const float ax1 = xl ? dpsi(p1.x - m1, delta2) : 0.f;
+        const float bx1 = hx0 ? dpsi_psi(p1.y - p1.x, delta2, sbx1) : 0.f;
+        const float cx1 = xr1 ? dpsi_psi(e1 - p1.y, delta2, scx1) : 0.f;
+        // y differences per column: (yo-1,yo), (yo,yo+1), (yo+1,yo+2)
+        float2 sby = make_float2(psi0, psi0), scy = sby;
+        const float2 ay = yu ? make_float2(dpsi(p0.x - pu.x, delta2), dpsi(p0.y - pu.y, delta2))
+                             : make_float2(0.f, 0.f);
+        const float2 by = r1ok ? make_float2(dpsi_psi(p1.x - p0.x, delta2, sby.x), dpsi_psi(p1.y - p0.y, delta2, sby.y))
+                               : make_float2(0.f, 0.f);
+        const float2 cy = yd2 ? make_float2(dpsi_psi(pd.x - p1.x, delta2, scy.x), dpsi_psi(pd.y - p1.y, delta2, scy.y))
+                              : make_float2(0.f, 0.f);
+        // z differences per voxel: inflow from zo-1 minus outflow to zo+1 (psi of the latter)
+        auto zterm = [&](float xc, float xlz, float xrz, float &sz) {
+            sz = psi0;
+            return (zl ? dpsi(xc - xlz, delta2) : 0.f) - (zr ? dpsi_psi(xrz - xc, delta2, sz) : 0.f);
+        };
+        float sz00, sz01, sz10, sz11;
+        const float pen00 = ax0 - bx0 + ay.x - by.x + zterm(p0.x, zl0.x, zr0.x, sz00);
+        const float pen01 = bx0 - cx0 + ay.y - by.y + zterm(p0.y, zl0.y, zr0.y, sz01);
+        const float pen10 = ax1 - bx1 + by.x - cy.x + zterm(p1.x, zl1.x, zr1.x, sz10);
+        const float pen11 = bx1 - cx1 + by.y - cy.y + zterm(p1.y, zl1.y, zr1.y, sz11);
+        auto gval = [&](float q, float xc, float pen, bool ex) { return fmaf(lam, pen, fmaf(eta2, boxd(xc, ex), q)); };
+        q0 = make_float2(gval(q0.x, p0.x, pen00, true), gval(q0.y, p0.y, pen01, v01));
+        q1 = make_float2(gval(q1.x, p1.x, pen10, v10), gval(q1.y, p1.y, pen11, v11));
+        if constexpr (OBJ) {
+            float s = (sbx0 + sby.x) + sz00;
+            if (v01) s += (scx0 + sby.y) + sz01;
+            if (v10) s += (sbx1 + scy.x) + sz10;
+            if (v11) s += (scx1 + scy.y) + sz11;
+            ob[1] += s;
+        }
+    } else if constexpr (PM == 1) {
+        // Joint X-Y weight w = 1/sqrt(delta^2 + tX^2 + tY^2) of a voxel, with tX,
+        // tY its forward differences (0 where the +neighbour does not exist).  The
+        // gradient needs w at the four voxels and at their -x and -y neighbours;
+        // these read x on rows yo-1 .. yo+2 and columns c-1 .. c+2, of which
+        // (yo-1, c+2) and (yo+2, c-1) are not loaded above.
+        const float q3 = (yu && xr1) ? X1(0, -1, 2) : 0.f;        // (yo-1, c+2)
+        const float s2 = (yd2 && xl) ? X1(0, 2, -1) : 0.f;    // (yo+2, c-1)
+        auto w_of = [&](float tx, float ty) { return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, delta2))); };
+        // (tX, tY) of (yo, c-1), (yo+1, c-1), (yo-1, c), (yo-1, c+1) and the own voxels
+        const float txl0 = xl ? p0.x - m0 : 0.f, tyl0 = (xl && r1ok) ? m1 - m0 : 0.f;
+        const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f, tyl1 = (xl && yd2) ? s2 - m1 : 0.f;
+        const float txu0 = (yu && c1ok) ? pu.y - pu.x : 0.f, tyu0 = yu ? p0.x - pu.x : 0.f;
+        const float txu1 = (yu && xr1) ? q3 - pu.y : 0.f, tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
+        const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
+        const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
+        const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
+        const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
+        const float wl0 = w_of(txl0, tyl0), wl1 = w_of(txl1, tyl1);
+        const float wu0 = w_of(txu0, tyu0), wu1 = w_of(txu1, tyu1);
+        const float w00 = w_of(tx00, ty00), w01 = w_of(tx01, ty01);
+        const float w10 = w_of(tx10, ty10), w11 = w_of(tx11, ty11);
+        // V^XT (w tX) + V^YT (w tY): inflow from the -x and -y neighbours minus the
+        // voxel's own outflow
+        const float pen00 = wl0 * txl0 - w00 * tx00 + wu0 * tyu0 - w00 * ty00;
+        const float pen01 = w00 * tx00 - w01 * tx01 + wu1 * tyu1 - w01 * ty01;
+        const float pen10 = wl1 * txl1 - w10 * tx10 + w00 * ty00 - w10 * ty10;
+        const float pen11 = w10 * tx10 - w11 * tx11 + w01 * ty01 - w11 * ty11;
+        // V^ZT V^Z x of the quadratic z term
+        auto zq = [&](float xc, float xlz, float xrz) {
+            return (zl ? xc - xlz : 0.f) - (zr ? xrz - xc : 0.f);
+        };
+        auto gval = [&](float q, float xc, float pen, float zt, bool ex) {
+            return fmaf(kap2, zt, fmaf(lam, pen, fmaf(eta2, boxd(xc, ex), q)));
+        };
+        q0 = make_float2(gval(q0.x, p0.x, pen00, zq(p0.x, zl0.x, zr0.x), true),
+                         gval(q0.y, p0.y, pen01, zq(p0.y, zl0.y, zr0.y), v01));
+        q1 = make_float2(gval(q1.x, p1.x, pen10, zq(p1.x, zl1.x, zr1.x), v10),
+                         gval(q1.y, p1.y, pen11, zq(p1.y, zl1.y, zr1.y), v11));
+        if constexpr (OBJ) {
+            auto psi = [&](float tx, float ty, float w, float tz) {
+                return fmaf(k.kl * tz, tz, fmaf(tx, tx, fmaf(ty, ty, delta2)) * w);
+            };
+            float s = psi(tx00, ty00, w00, zr ? zr0.x - p0.x : 0.f);
+            if (v01) s += psi(tx01, ty01, w01, zr ? zr0.y - p0.y : 0.f);
+            if (v10) s += psi(tx10, ty10, w10, zr ? zr1.x - p1.x : 0.f);
+            if (v11) s += psi(tx11, ty11, w11, zr ? zr1.y - p1.y : 0.f);
+            ob[1] += s;
+        }
+    } else {
+        // Isotropic weight w = 1/sqrt(delta^2 + tX^2 + tY^2 + tZ^2) of a voxel (its
+        // forward differences, 0 where the +neighbour does not exist), needed at
+        // the four voxels and at their -x, -y and -z neighbours.  Besides the
+        // values loaded above this reads, on slice zo, (yo-1, c+2) and
+        // (yo+2, c-1); on zo+1, column c-1 of rows yo, yo+1 and row yo-1 of
+        // columns c, c+1; on zo-1, column c+2 of rows yo, yo+1 and row yo+2 of
+        // columns c, c+1.
+        const float q3 = (yu && xr1) ? X1(0, -1, 2) : 0.f;                 // (zo, yo-1, c+2)
+        const float s2 = (yd2 && xl) ? X1(0, 2, -1) : 0.f;             // (zo, yo+2, c-1)
+        const float zrm0 = (zr && xl) ? X1(1, 0, -1) : 0.f;                // (zo+1, yo, c-1)
+        const float zrm1 = (zr && xl && r1ok) ? X1(1, 1, -1) : 0.f;
+        const float2 zru = (zr && yu) ? X2(1, -1, 0) : make_float2(0.f, 0.f);           // (zo+1, yo-1, c..c+1)
+        const float zle0 = (zl && xr1) ? X1(-1, 0, 2) : 0.f;              // (zo-1, yo, c+2)
+        const float zle1 = (zl && xr1 && r1ok) ? X1(-1, 1, 2) : 0.f;
+        const float2 zld = (zl && yd2) ? X2(-1, 2, 0) : make_float2(0.f, 0.f);     // (zo-1, yo+2, c..c+1)
+        auto w_of = [&](float tx, float ty, float tz) {
+            return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2))));
+        };
+        // own voxels
+        const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
+        const float tz00 = zr ? zr0.x - p0.x : 0.f;
+        const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
+        const float tz01 = (zr && c1ok) ? zr0.y - p0.y : 0.f;
+        const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
+        const float tz10 = (zr && r1ok) ? zr1.x - p1.x : 0.f;
+        const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
+        const float tz11 = (zr && r1ok && c1ok) ? zr1.y - p1.y : 0.f;
+        // -x neighbours (yo, c-1), (yo+1, c-1): only tX enters their outflow to us
+        const float txl0 = xl ? p0.x - m0 : 0.f;
+        const float wl0 = w_of(txl0, (xl && r1ok) ? m1 - m0 : 0.f, (xl && zr) ? zrm0 - m0 : 0.f);
+        const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f;
+        const float wl1 = w_of(txl1, (xl && yd2) ? s2 - m1 : 0.f, (xl && zr && r1ok) ? zrm1 - m1 : 0.f);
+        // -y neighbours (yo-1, c), (yo-1, c+1)
+        const float tyu0 = yu ? p0.x - pu.x : 0.f;
+        const float wu0 = w_of((yu && c1ok) ? pu.y - pu.x : 0.f, tyu0, (yu && zr) ? zru.x - pu.x : 0.f);
+        const float tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
+        const float wu1 = w_of((yu && xr1) ? q3 - pu.y : 0.f, tyu1, (yu && zr && c1ok) ? zru.y - pu.y : 0.f);
+        // -z neighbours (slice zo-1) of the four voxels
+        const float tzb00 = zl ? p0.x - zl0.x : 0.f;
+        const float wb00 = w_of((zl && c1ok) ? zl0.y - zl0.x : 0.f, (zl && r1ok) ? zl1.x - zl0.x : 0.f, tzb00);
+        const float tzb01 = (zl && c1ok) ? p0.y - zl0.y : 0.f;
+        const float wb01 = w_of((zl && xr1) ? zle0 - zl0.y : 0.f, (zl && r1ok && c1ok) ? zl1.y - zl0.y : 0.f,
+                                tzb01);
+        const float tzb10 = (zl && r1ok) ? p1.x - zl1.x : 0.f;
+        const float wb10 = w_of((zl && r1ok && c1ok) ? zl1.y - zl1.x : 0.f, (zl && yd2) ? zld.x - zl1.x : 0.f,
+                                tzb10);
+        const float tzb11 = (zl && r1ok && c1ok) ? p1.y - zl1.y : 0.f;
+        const float wb11 = w_of((zl && r1ok && xr1) ? zle1 - zl1.y : 0.f,
+                                (zl && yd2 && c1ok) ? zld.y - zl1.y : 0.f, tzb11);
+        const float w00 = w_of(tx00, ty00, tz00), w01 = w_of(tx01, ty01, tz01);
+        const float w10 = w_of(tx10, ty10, tz10), w11 = w_of(tx11, ty11, tz11);
+        // sum_a V^aT (w t_a): inflow from the -x, -y, -z neighbours minus own outflow
+        const float pen00 = wl0 * txl0 + wu0 * tyu0 + wb00 * tzb00 - w00 * (tx00 + ty00 + tz00);
+        const float pen01 = w00 * tx00 + wu1 * tyu1 + wb01 * tzb01 - w01 * (tx01 + ty01 + tz01);
+        const float pen10 = wl1 * txl1 + w00 * ty00 + wb10 * tzb10 - w10 * (tx10 + ty10 + tz10);
+        const float pen11 = w10 * tx10 + w01 * ty01 + wb11 * tzb11 - w11 * (tx11 + ty11 + tz11);
+        auto gval = [&](float q, float xc, float pen, bool ex) { return fmaf(lam, pen, fmaf(eta2, boxd(xc, ex), q)); };
+        q0 = make_float2(gval(q0.x, p0.x, pen00, true), gval(q0.y, p0.y, pen01, v01));
+        q1 = make_float2(gval(q1.x, p1.x, pen10, v10), gval(q1.y, p1.y, pen11, v11));
+        if constexpr (OBJ) {
+            auto psi = [&](float tx, float ty, float tz, float w) {
+                return fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2))) * w;
+            };
+            float s = psi(tx00, ty00, tz00, w00);
+            if (v01) s += psi(tx01, ty01, tz01, w01);
+            if (v10) s += psi(tx10, ty10, tz10, w10);
+            if (v11) s += psi(tx11, ty11, tz11, w11);
+            ob[1] += s;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_gradient: g = H^T r (+ box and penalty gradient unless M_HT_ONLY) on the
 // slabs' own slices.  Adjoint order: each input slice of r is correlated in x
@@ -965,166 +1208,16 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
             }
             float2 q0 = __fadd2_rn(qa0, qb0), q1 = __fadd2_rn(qa1, qb1);
             if (full && r0ok && c0ok) {
-                const long long zoff = (long long)zo * plane;
-                const float *xr = xg + zoff + o0;                  // (yo, c) at slice zo
-                const bool xl = gx >= 1, xr1 = gx + 2 < nx;
-                const bool yu = gy >= 1, yd2 = gy + 2 < ny;
-                const bool zl = zo >= 1, zr = zo + 1 < nz;
-                // row yo: columns c-1 .. c+2; row yo+1 likewise
-                const float2 p0 = __ldg(reinterpret_cast<const float2 *>(xr));
-                const float m0 = xl ? __ldg(xr - 1) : p0.x, e0 = xr1 ? __ldg(xr + 2) : p0.y;
-                float2 p1 = p0;
-                float m1 = m0, e1 = e0;
-                if (r1ok) {
-                    p1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch));
-                    m1 = xl ? __ldg(xr + pitch - 1) : p1.x;
-                    e1 = xr1 ? __ldg(xr + pitch + 2) : p1.y;
-                }
-                const float2 pu = yu ? __ldg(reinterpret_cast<const float2 *>(xr - pitch)) : p0;
-                const float2 pd = yd2 ? __ldg(reinterpret_cast<const float2 *>(xr + 2 * pitch)) : p1;
-                const float2 zl0 = zl ? __ldg(reinterpret_cast<const float2 *>(xr - plane)) : p0;
-                const float2 zr0 = zr ? __ldg(reinterpret_cast<const float2 *>(xr + plane)) : p0;
-                float2 zl1 = p1, zr1 = p1;
-                if (r1ok) {
-                    if (zl) zl1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch - plane));
-                    if (zr) zr1 = __ldg(reinterpret_cast<const float2 *>(xr + pitch + plane));
-                }
-                if constexpr (PM == 0) {
-                    // x differences (each shared by its two voxels): row k: (c-1,c), (c,c+1), (c+1,c+2)
-                    const bool hx0 = c1ok;                               // (c, c+1) is a difference of the volume
-                    const float ax0 = xl ? dpsi(p0.x - m0, delta2) : 0.f;
-                    const float bx0 = hx0 ? dpsi(p0.y - p0.x, delta2) : 0.f;
-                    const float cx0 = xr1 ? dpsi(e0 - p0.y, delta2) : 0.f;
-                    const float ax1 = xl ? dpsi(p1.x - m1, delta2) : 0.f;
-                    const float bx1 = hx0 ? dpsi(p1.y - p1.x, delta2) : 0.f;
-                    const float cx1 = xr1 ? dpsi(e1 - p1.y, delta2) : 0.f;
-                    // y differences per column: (yo-1,yo), (yo,yo+1), (yo+1,yo+2)
-                    const float2 ay = yu ? make_float2(dpsi(p0.x - pu.x, delta2), dpsi(p0.y - pu.y, delta2))
-                                         : make_float2(0.f, 0.f);
-                    const float2 by = r1ok ? make_float2(dpsi(p1.x - p0.x, delta2), dpsi(p1.y - p0.y, delta2))
-                                           : make_float2(0.f, 0.f);
-                    const float2 cy = yd2 ? make_float2(dpsi(pd.x - p1.x, delta2), dpsi(pd.y - p1.y, delta2))
-                                          : make_float2(0.f, 0.f);
-                    // z differences per voxel
-                    auto zterm = [&](float xc, float xlz, float xrz) {
-                        return (zl ? dpsi(xc - xlz, delta2) : 0.f) - (zr ? dpsi(xrz - xc, delta2) : 0.f);
-                    };
-                    const float pen00 = ax0 - bx0 + ay.x - by.x + zterm(p0.x, zl0.x, zr0.x);
-                    const float pen01 = bx0 - cx0 + ay.y - by.y + zterm(p0.y, zl0.y, zr0.y);
-                    const float pen10 = ax1 - bx1 + by.x - cy.x + zterm(p1.x, zl1.x, zr1.x);
-                    const float pen11 = bx1 - cx1 + by.y - cy.y + zterm(p1.y, zl1.y, zr1.y);
-                    auto gval = [&](float q, float xc, float pen) {
-                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                        return fmaf(lam, pen, fmaf(eta2, dist, q));
-                    };
-                    q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
-                    q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
-                } else if constexpr (PM == 1) {
-                    // Joint X-Y weight w = 1/sqrt(delta^2 + tX^2 + tY^2) of a voxel, with tX,
-                    // tY its forward differences (0 where the +neighbour does not exist).  The
-                    // gradient needs w at the four voxels and at their -x and -y neighbours;
-                    // these read x on rows yo-1 .. yo+2 and columns c-1 .. c+2, of which
-                    // (yo-1, c+2) and (yo+2, c-1) are not loaded above.
-                    const float q3 = (yu && xr1) ? __ldg(xr - pitch + 2) : 0.f;        // (yo-1, c+2)
-                    const float s2 = (yd2 && xl) ? __ldg(xr + 2 * pitch - 1) : 0.f;   // (yo+2, c-1)
-                    auto w_of = [&](float tx, float ty) { return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, delta2))); };
-                    // (tX, tY) of (yo, c-1), (yo+1, c-1), (yo-1, c), (yo-1, c+1) and the own voxels
-                    const float txl0 = xl ? p0.x - m0 : 0.f, tyl0 = (xl && r1ok) ? m1 - m0 : 0.f;
-                    const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f, tyl1 = (xl && yd2) ? s2 - m1 : 0.f;
-                    const float txu0 = (yu && c1ok) ? pu.y - pu.x : 0.f, tyu0 = yu ? p0.x - pu.x : 0.f;
-                    const float txu1 = (yu && xr1) ? q3 - pu.y : 0.f, tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
-                    const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
-                    const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
-                    const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
-                    const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
-                    const float wl0 = w_of(txl0, tyl0), wl1 = w_of(txl1, tyl1);
-                    const float wu0 = w_of(txu0, tyu0), wu1 = w_of(txu1, tyu1);
-                    const float w00 = w_of(tx00, ty00), w01 = w_of(tx01, ty01);
-                    const float w10 = w_of(tx10, ty10), w11 = w_of(tx11, ty11);
-                    // V^XT (w tX) + V^YT (w tY): inflow from the -x and -y neighbours minus the
-                    // voxel's own outflow
-                    const float pen00 = wl0 * txl0 - w00 * tx00 + wu0 * tyu0 - w00 * ty00;
-                    const float pen01 = w00 * tx00 - w01 * tx01 + wu1 * tyu1 - w01 * ty01;
-                    const float pen10 = wl1 * txl1 - w10 * tx10 + w00 * ty00 - w10 * ty10;
-                    const float pen11 = w10 * tx10 - w11 * tx11 + w01 * ty01 - w11 * ty11;
-                    // V^ZT V^Z x of the quadratic z term
-                    auto zq = [&](float xc, float xlz, float xrz) {
-                        return (zl ? xc - xlz : 0.f) - (zr ? xrz - xc : 0.f);
-                    };
-                    auto gval = [&](float q, float xc, float pen, float zt) {
-                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                        return fmaf(kap2, zt, fmaf(lam, pen, fmaf(eta2, dist, q)));
-                    };
-                    q0 = make_float2(gval(q0.x, p0.x, pen00, zq(p0.x, zl0.x, zr0.x)),
-                                     gval(q0.y, p0.y, pen01, zq(p0.y, zl0.y, zr0.y)));
-                    q1 = make_float2(gval(q1.x, p1.x, pen10, zq(p1.x, zl1.x, zr1.x)),
-                                     gval(q1.y, p1.y, pen11, zq(p1.y, zl1.y, zr1.y)));
-                } else {
-                    // Isotropic weight w = 1/sqrt(delta^2 + tX^2 + tY^2 + tZ^2) of a voxel (its
-                    // forward differences, 0 where the +neighbour does not exist), needed at
-                    // the four voxels and at their -x, -y and -z neighbours.  Besides the
-                    // values loaded above this reads, on slice zo, (yo-1, c+2) and
-                    // (yo+2, c-1); on zo+1, column c-1 of rows yo, yo+1 and row yo-1 of
-                    // columns c, c+1; on zo-1, column c+2 of rows yo, yo+1 and row yo+2 of
-                    // columns c, c+1.
-                    const float q3 = (yu && xr1) ? __ldg(xr - pitch + 2) : 0.f;                 // (zo, yo-1, c+2)
-                    const float s2 = (yd2 && xl) ? __ldg(xr + 2 * pitch - 1) : 0.f;            // (zo, yo+2, c-1)
-                    const float zrm0 = (zr && xl) ? __ldg(xr + plane - 1) : 0.f;               // (zo+1, yo, c-1)
-                    const float zrm1 = (zr && xl && r1ok) ? __ldg(xr + plane + pitch - 1) : 0.f;
-                    const float2 zru = (zr && yu) ? __ldg(reinterpret_cast<const float2 *>(xr + plane - pitch))
-                                                  : make_float2(0.f, 0.f);                    // (zo+1, yo-1, c..c+1)
-                    const float zle0 = (zl && xr1) ? __ldg(xr - plane + 2) : 0.f;              // (zo-1, yo, c+2)
-                    const float zle1 = (zl && xr1 && r1ok) ? __ldg(xr - plane + pitch + 2) : 0.f;
-                    const float2 zld = (zl && yd2) ? __ldg(reinterpret_cast<const float2 *>(xr - plane + 2 * pitch))
-                                                   : make_float2(0.f, 0.f);                   // (zo-1, yo+2, c..c+1)
-                    auto w_of = [&](float tx, float ty, float tz) {
-                        return rsqrtf(fmaf(tx, tx, fmaf(ty, ty, fmaf(tz, tz, delta2))));
-                    };
-                    // own voxels
-                    const float tx00 = c1ok ? p0.y - p0.x : 0.f, ty00 = r1ok ? p1.x - p0.x : 0.f;
-                    const float tz00 = zr ? zr0.x - p0.x : 0.f;
-                    const float tx01 = xr1 ? e0 - p0.y : 0.f, ty01 = (r1ok && c1ok) ? p1.y - p0.y : 0.f;
-                    const float tz01 = (zr && c1ok) ? zr0.y - p0.y : 0.f;
-                    const float tx10 = (r1ok && c1ok) ? p1.y - p1.x : 0.f, ty10 = yd2 ? pd.x - p1.x : 0.f;
-                    const float tz10 = (zr && r1ok) ? zr1.x - p1.x : 0.f;
-                    const float tx11 = (r1ok && xr1) ? e1 - p1.y : 0.f, ty11 = (yd2 && c1ok) ? pd.y - p1.y : 0.f;
-                    const float tz11 = (zr && r1ok && c1ok) ? zr1.y - p1.y : 0.f;
-                    // -x neighbours (yo, c-1), (yo+1, c-1): only tX enters their outflow to us
-                    const float txl0 = xl ? p0.x - m0 : 0.f;
-                    const float wl0 = w_of(txl0, (xl && r1ok) ? m1 - m0 : 0.f, (xl && zr) ? zrm0 - m0 : 0.f);
-                    const float txl1 = (xl && r1ok) ? p1.x - m1 : 0.f;
-                    const float wl1 = w_of(txl1, (xl && yd2) ? s2 - m1 : 0.f, (xl && zr && r1ok) ? zrm1 - m1 : 0.f);
-                    // -y neighbours (yo-1, c), (yo-1, c+1)
-                    const float tyu0 = yu ? p0.x - pu.x : 0.f;
-                    const float wu0 = w_of((yu && c1ok) ? pu.y - pu.x : 0.f, tyu0, (yu && zr) ? zru.x - pu.x : 0.f);
-                    const float tyu1 = (yu && c1ok) ? p0.y - pu.y : 0.f;
-                    const float wu1 = w_of((yu && xr1) ? q3 - pu.y : 0.f, tyu1, (yu && zr && c1ok) ? zru.y - pu.y : 0.f);
-                    // -z neighbours (slice zo-1) of the four voxels
-                    const float tzb00 = zl ? p0.x - zl0.x : 0.f;
-                    const float wb00 = w_of((zl && c1ok) ? zl0.y - zl0.x : 0.f, (zl && r1ok) ? zl1.x - zl0.x : 0.f, tzb00);
-                    const float tzb01 = (zl && c1ok) ? p0.y - zl0.y : 0.f;
-                    const float wb01 = w_of((zl && xr1) ? zle0 - zl0.y : 0.f, (zl && r1ok && c1ok) ? zl1.y - zl0.y : 0.f,
-                                            tzb01);
-                    const float tzb10 = (zl && r1ok) ? p1.x - zl1.x : 0.f;
-                    const float wb10 = w_of((zl && r1ok && c1ok) ? zl1.y - zl1.x : 0.f, (zl && yd2) ? zld.x - zl1.x : 0.f,
-                                            tzb10);
-                    const float tzb11 = (zl && r1ok && c1ok) ? p1.y - zl1.y : 0.f;
-                    const float wb11 = w_of((zl && r1ok && xr1) ? zle1 - zl1.y : 0.f,
-                                            (zl && yd2 && c1ok) ? zld.y - zl1.y : 0.f, tzb11);
-                    const float w00 = w_of(tx00, ty00, tz00), w01 = w_of(tx01, ty01, tz01);
-                    const float w10 = w_of(tx10, ty10, tz10), w11 = w_of(tx11, ty11, tz11);
-                    // sum_a V^aT (w t_a): inflow from the -x, -y, -z neighbours minus own outflow
-                    const float pen00 = wl0 * txl0 + wu0 * tyu0 + wb00 * tzb00 - w00 * (tx00 + ty00 + tz00);
-                    const float pen01 = w00 * tx00 + wu1 * tyu1 + wb01 * tzb01 - w01 * (tx01 + ty01 + tz01);
-                    const float pen10 = wl1 * txl1 + w00 * ty00 + wb10 * tzb10 - w10 * (tx10 + ty10 + tz10);
-                    const float pen11 = w10 * tx10 + w01 * ty01 + wb11 * tzb11 - w11 * (tx11 + ty11 + tz11);
-                    auto gval = [&](float q, float xc, float pen) {
-                        const float dist = xc - fminf(fmaxf(xc, xmin), xmax);
-                        return fmaf(lam, pen, fmaf(eta2, dist, q));
-                    };
-                    q0 = make_float2(gval(q0.x, p0.x, pen00), gval(q0.y, p0.y, pen01));
-                    q1 = make_float2(gval(q1.x, p1.x, pen10), gval(q1.y, p1.y, pen11));
-                }
+                const float *xr = xg + (long long)zo * plane + o0;            // (yo, c) at slice zo
+                const PenCtx pk{c1ok, r1ok, gx >= 1, gx + 2 < nx, gy >= 1, gy + 2 < ny, zo >= 1, zo + 1 < nz,
+                                delta2, lam, eta2, kap2, 0.f, xmin, xmax};
+                auto X1 = [&](int dz, int dy, int dx) { return __ldg(xr + dz * plane + dy * pitch + dx); };
+                auto X2 = [&](int dz, int dy, int dx) {
+                    return __ldg(reinterpret_cast<const float2 *>(xr + dz * plane + dy * pitch + dx));
+                };
+                const float2 p0 = X2(0, 0, 0);
+                const float2 p1 = r1ok ? X2(0, 1, 0) : p0;
+                pen_block<PM, false>(X1, X2, pk, p0, p1, q0, q1, nullptr);
             }
             if (c0ok) {
                 const long long zoff = (long long)zo * plane;
@@ -1181,6 +1274,7 @@ static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
             if (tid == 0) {
                 a.u[2 * slot] = 0.0;
                 a.u[2 * slot + 1] = 0.0;
+                if ((a.mode & M_PAR) && a.sh->run) a.sh->run[ss.vol].pending = 0;
             }
             continue;
         }
@@ -1210,6 +1304,7 @@ static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
                 VolRun &rv = a.sh->run[ss.vol];
                 rv.dx2 += u0 * u0 * tot[0] - 2.0 * u0 * u1 * tot[1] + u1 * u1 * tot[2];
                 rv.xx_prev += tot[9];
+                if (a.mode & M_PAR) rv.pending = 1;     // the next gradient pass (or the flush) applies u
             }
         }
         __syncthreads();
@@ -1294,11 +1389,19 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
 
     const Item it = a.items[blockIdx.x];
     const unsigned long long wait_ns = a.sh->wait_ns;
-    const SegDev sg = a.segs[it.seg];
+    SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
     const float *xg = V.x, *dg = V.d;
+    // fused-update iteration: the volume's state may live in its second buffer set
+    const bool set1 = (a.mode & M_PAR) && a.sh->run && __ldg(&a.sh->run[sg.vol].par) != 0;
+    if (set1) {
+        xg = V.x1;
+        dg = V.d1;
+        sg.hg = sg.hg1;
+        sg.hd = sg.hd1;
+    }
     const float delta2 = V.delta2, kl2 = V.kl2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
@@ -1314,7 +1417,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     stage_coeffs<G>(CF, V, it.zo0, it.zo1 - it.zo0);   // rows of the output slices only
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
-    const CUtensorMap *mg = &a.maps[sg.vol].m[TM_G_R];
+    const CUtensorMap *mg = &a.maps[sg.vol].m[set1 ? TM_G1_R : TM_G_R];
     if (tid == 0)   // the descriptor sits in global memory and may have been rewritten since an earlier launch
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mg)) : "memory");
     const uint32_t nb = (uint32_t)(BX * BY * sizeof(T));

@@ -2,6 +2,7 @@
 #pragma once
 #include "kernel_sets.h"
 #include "kernels.cuh"
+#include "lazy.cuh"
 
 namespace bd3mg {
 
@@ -16,6 +17,10 @@ void launch_gradient(const KArgs &a, cudaStream_t s) {
 template <int R, int RZ, bool BF, int PM>
 void launch_curvature(const KArgs &a, cudaStream_t s) {
     k_curvature<R, RZ, BF, PM><<<a.nitems, NT, BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature, s>>>(a);
+}
+template <int R, int RZ, bool BF, int PM>
+void launch_gradlazy(const KArgs &a, cudaStream_t s) {
+    k_gradlazy<R, RZ, BF, PM><<<a.nitems, NT, LazyGeo<R, RZ>::SMEM, s>>>(a);
 }
 template <int R, int RZ, int PM>
 cudaError_t prepare_set() {
@@ -33,6 +38,12 @@ cudaError_t prepare_set() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curvature<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::curvature_bf);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gradlazy<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)LazyGeo<R, RZ>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_gradlazy<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)LazyGeo<R, RZ>::SMEM);
     return e;
 }
 
@@ -45,6 +56,8 @@ int occupancy_of(int kind) {
         case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, false, PM>, NT, Smem<R, RZ>::gradient); break;
         case 3: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradient<R, RZ, true, PM>, NT, Smem<R, RZ>::gradient); break;
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, true, PM>, NT, Smem<R, RZ>::curvature_bf); break;
+        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, false, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, true, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM>, NT, Smem<R, RZ>::curvature); break;
     }
     return e == cudaSuccess ? n : 0;
@@ -55,5 +68,5 @@ int occupancy_of(int kind) {
 #define BD3MG_KERNEL_SET(R, RZ, PM)                                                                      \
     {R, RZ, PM, &bd3mg::launch_residual<R, RZ, PM>, &bd3mg::launch_gradient<R, RZ, false, PM>,              \
      &bd3mg::launch_curvature<R, RZ, false, PM>, &bd3mg::launch_gradient<R, RZ, true, PM>,                  \
-     &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::prepare_set<R, RZ, PM>,                             \
-     &bd3mg::occupancy_of<R, RZ, PM>}
+     &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::launch_gradlazy<R, RZ, false, PM>,                  \
+     &bd3mg::launch_gradlazy<R, RZ, true, PM>, &bd3mg::prepare_set<R, RZ, PM>, &bd3mg::occupancy_of<R, RZ, PM>}

@@ -131,6 +131,79 @@ __global__ void __launch_bounds__(NT, 6) k_objective(KArgs a) {
     if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
 }
 
+// ---------------------------------------------------------------------------
+// k_flush over plain volumes (blockIdx.y = volume's segment): a pending update
+// is applied with k_update's arithmetic, and the state moves from the volume's
+// current buffer set to set 0 (x, d, r, H d; g too when it was in set 1).
+// k_clear_pending then marks every volume settled.
+// ---------------------------------------------------------------------------
+template <bool BF>
+__global__ void __launch_bounds__(NT) k_flush(const VolDev *vols, const SegDev *segs, const int *seg_list,
+                                              const double *u, const VolRun *run) {
+    const SegDev sg = segs[seg_list[blockIdx.y]];
+    const bool set1 = run[sg.vol].par != 0, apply = run[sg.vol].pending != 0;
+    if (!set1 && !apply) return;
+    const VolDev &v = vols[sg.vol];
+    const float u0 = apply ? (float)u[2 * sg.slot] : 0.f, u1 = apply ? (float)u[2 * sg.slot + 1] : 0.f;
+    const long long n4 = ((long long)v.nz * v.plane) >> 2, stride = (long long)gridDim.x * NT;
+    const float4 *xs = reinterpret_cast<const float4 *>(set1 ? v.x1 : v.x);
+    const float4 *ds = reinterpret_cast<const float4 *>(set1 ? v.d1 : v.d);
+    const float4 *rs = reinterpret_cast<const float4 *>(set1 ? v.r1 : v.r);
+    const float4 *hgs = reinterpret_cast<const float4 *>(set1 ? sg.hg1 : sg.hg);
+    const float4 *hds = reinterpret_cast<const float4 *>(set1 ? sg.hd1 : sg.hd);
+    float4 *xd = reinterpret_cast<float4 *>(v.x), *dd = reinterpret_cast<float4 *>(v.d);
+    float4 *rd = reinterpret_cast<float4 *>(v.r), *hdd = reinterpret_cast<float4 *>(sg.hd);
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
+        float4 g;
+        if constexpr (BF) {
+            const uint2 gq = reinterpret_cast<const uint2 *>(set1 ? v.gh1 : v.gh)[i];
+            if (set1) reinterpret_cast<uint2 *>(v.gh)[i] = gq;
+            const float2 g0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&gq.x));
+            const float2 g1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&gq.y));
+            g = make_float4(g0.x, g0.y, g1.x, g1.y);
+        } else {
+            g = reinterpret_cast<const float4 *>(set1 ? v.g1 : v.g)[i];
+            if (set1) reinterpret_cast<float4 *>(v.g)[i] = g;
+        }
+        float4 x = xs[i], d = ds[i], r = rs[i], hd = hds[i];
+        if (apply) {
+            const float4 hg = hgs[i];
+            float4 nd, nh;
+            nd.x = fmaf(-u0, g.x, u1 * d.x);
+            nd.y = fmaf(-u0, g.y, u1 * d.y);
+            nd.z = fmaf(-u0, g.z, u1 * d.z);
+            nd.w = fmaf(-u0, g.w, u1 * d.w);
+            x.x += nd.x; x.y += nd.y; x.z += nd.z; x.w += nd.w;
+            d = nd;
+            nh.x = fmaf(-u0, hg.x, u1 * hd.x);
+            nh.y = fmaf(-u0, hg.y, u1 * hd.y);
+            nh.z = fmaf(-u0, hg.z, u1 * hd.z);
+            nh.w = fmaf(-u0, hg.w, u1 * hd.w);
+            r.x += nh.x; r.y += nh.y; r.z += nh.z; r.w += nh.w;
+            hd = nh;
+        }
+        xd[i] = x;
+        dd[i] = d;
+        rd[i] = r;
+        hdd[i] = hd;
+    }
+}
+
+__global__ void k_clear_pending(VolRun *run, int nvol) {
+    for (int v = threadIdx.x; v < nvol; v += blockDim.x) {
+        run[v].par = 0;
+        run[v].pending = 0;
+    }
+}
+
+void launch_flush(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, const VolRun *run,
+                  dim3 grid, cudaStream_t s, bool bf16) {
+    if (bf16) k_flush<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+    else k_flush<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+}
+
+void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s) { k_clear_pending<<<1, 128, 0, s>>>(run, nvol); }
+
 __global__ void __launch_bounds__(NT) k_dir_to_float(const __nv_bfloat16 *src, float *dst, long long n) {
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
         dst[i] = __bfloat162float(src[i]);
