@@ -22,9 +22,14 @@ the 16-volume batch (lockstep rate, time to gap with per-volume stopping under
 the autotuned and the cost model's z-chunks, against sequential single-volume
 contexts), the SNR of y and of a 500-sweep solve against the phantom,
 the per-kernel roofline, e2e through host buffers, and the FP64 CPU oracle
-timed on a bounded sample (`cpu_baseline`).
+timed on whole sweeps of the workload (`cpu_baseline`, all host threads; the
+64x64x24 plain workload in whole iterations with one thread and with all).
+`roofline_plain_512` is the plain FP32 iteration on the 512x512x128 recipe,
+where the HBM roofline target is set: its dominant kernel, and the iteration
+against the 28 B/voxel one-pass bound and against its own byte count.
 
-`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only), one whole
+sweep per step, as many steps as fit about 150 s (reported as run).
 """
 from __future__ import annotations
 
@@ -91,65 +96,67 @@ def workload_config(prob, extra=None):
 
 
 # ---------------------------------------------------------------------------
-# oracle sample (CPU baseline and the reference arm)
+# the FP64 oracle timed on whole workloads (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def _tap_work(shape, psf_shape):
-    """Inner-loop iterations of one plain dense convolution over `shape` (valid taps only)."""
-    tot = 1.0
-    for n, p in zip(shape, psf_shape):
-        r = (p - 1) // 2
-        i = np.arange(n)[:, None] - np.arange(-r, r + 1)[None, :]
-        tot *= float(np.count_nonzero((i >= 0) & (i < n)))
-    return tot
+def sweep_order(prob):
+    """Colour-major slab order of the workload (the order the library's sweep equals)."""
+    from paper_2002_02328_gb300 import binding
+    b = list(prob.slabs) if prob.slabs is not None and len(prob.slabs) > 2 else [0, prob.shape[0]]
+    if len(b) <= 2:
+        return b, [0]
+    col, nc = binding.bd3mg_plan_slab_colours(b, prob.psf.shape[1])
+    return b, [s for c in range(nc) for s in range(len(col)) if col[s] == c]
 
 
-class OracleSample:
-    """The FP64 oracle timed on an x/y crop (all depth slices) of the workload.
-
-    One sample = one oracle slab step (gradient + two majorant products + the
-    2x2 solve, all full-crop plain convolutions) plus one oracle objective.  A
-    sweep of the workload is 8 slab steps + 1 objective over the full volume
-    (each oracle step works on the whole volume), so the sweep time is the
-    sample time scaled by the ratio of valid PSF taps (full / crop)."""
-
-    def __init__(self, prob, budget_s: float, threads: int):
-        import oracle
-        oracle.set_threads(threads)
-        self.prob = prob
-        self.threads = threads
-        nz, ny, nx = prob.shape
-        t16 = self._run(16)[2]
-        c = int(16 * np.sqrt(max(budget_s, 1e-3) / max(t16, 1e-6)))
-        self.c = int(max(8, min(min(nx, ny), c)))
-
-    def _run(self, c):
-        import oracle
-        p = self.prob
-        y = np.ascontiguousarray(p.y[:, :c, :c])
-        op = oracle.OracleProblem(y.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax)
-        x = y.astype(np.float64)
+def oracle_sweeps(prob, threads: int, budget_s: float, max_sweeps: int, warmup: int = 0):
+    """Whole FP64 oracle sweeps of `prob` (each: the objective of the sweep's start
+    iterate, then every slab step in colour-major order over the full volume),
+    one after the other from x0 = y, while the elapsed time stays within budget_s
+    (at least one timed sweep).  Returns (timed sweep seconds, warm-up sweeps run)."""
+    import oracle
+    oracle.set_threads(threads)
+    op = oracle.OracleProblem.from_synth(prob)
+    bounds, order = sweep_order(prob)
+    x = prob.y.astype(np.float64)
+    d = np.zeros_like(x)
+    times, done_w, t_start = [], 0, time.perf_counter()
+    while len(times) < max_sweeps:
         t0 = time.perf_counter()
-        oracle.step(op, y, x, np.zeros_like(x))
-        t1 = time.perf_counter()
-        oracle.objective(op, y, x)
-        t2 = time.perf_counter()
-        return t1 - t0, t2 - t1, t2 - t0
+        oracle.objective(op, prob.y, x)
+        x, d, _ = oracle.run(op, prob.y, x, 1, bounds=bounds, order=order, d0=d, trace=False)
+        dt = time.perf_counter() - t0
+        if done_w < warmup:
+            done_w += 1
+        else:
+            times.append(dt)
+        if time.perf_counter() - t_start + dt > budget_s and times:
+            break
+    return times, done_w
 
-    def measure(self):
-        """Returns (sweeps/s estimate, sample seconds)."""
-        ts, to, tt = self._run(self.c)
-        p = self.prob
-        pz, py, px = p.psf.shape[1:]
-        scale = _tap_work(p.shape, (pz, py, px)) / _tap_work((p.shape[0], self.c, self.c), (pz, py, px))
-        return 1.0 / (scale * (8 * ts + to)), tt
 
-    def text(self, secs):
-        nz = self.prob.shape[0]
-        return (f"FP64 oracle slab step + objective on a {self.c}x{self.c}x{nz} x/y crop ({secs:.2f} s per sample), "
-                f"scaled to one 8-slab sweep of the full volume by the count of valid PSF taps")
+def cpu_baseline(prob, budget_s: float):
+    """The oracle as it stands, timed on the host cores: whole sweeps of the
+    workload with all threads (the value), and the 64x64x24 plain workload in
+    whole iterations with one thread and with all threads."""
+    from paper_2002_02328_gb300 import synth
+    threads = len(os.sched_getaffinity(0))
+    times, _ = oracle_sweeps(prob, threads, budget_s, 1000)
+    small = synth.workload_plain_small()
+    t1, _ = oracle_sweeps(small, 1, 0.3 * budget_s, 200)
+    tn, _ = oracle_sweeps(small, threads, 0.3 * budget_s, 200)
+    return {"value": 1.0 / float(np.mean(times)), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{len(times)} whole FP64 oracle sweep(s) of the 256x256x64 block workload (objective + 8 "
+                      f"slab steps over the full volume each, colour-major order, from x0 = y), {threads} threads, "
+                      f"{float(np.mean(times)):.2f} s per sweep; measured, not scaled",
+            "plain_64x64x24": {"iterations_per_s_1_thread": 1.0 / float(np.mean(t1)), "iterations_1_thread": len(t1),
+                               "iterations_per_s_all_threads": 1.0 / float(np.mean(tn)),
+                               "iterations_all_threads": len(tn)}}
 
 
 def reference_arm(args):
+    """The FP64 oracle on the bench's workload: each step one whole oracle sweep
+    (all host threads), as many of the requested steps as fit in about two and a
+    half minutes; `steps` and `warmup` report the sweeps actually run."""
     rank, world, _ = env_rank()
     if rank != 0:
         return 0
@@ -157,21 +164,17 @@ def reference_arm(args):
     oracle.build()
     prob = workload()
     threads = len(os.sched_getaffinity(0))
-    budget = max(0.02, 120.0 / max(1, args.steps + args.warmup))
-    smp = OracleSample(prob, budget, threads)
-    rates, secs = [], []
-    for k in range(args.warmup + args.steps):
-        r, t = smp.measure()
-        if k >= args.warmup:
-            rates.append(r)
-            secs.append(t)
-    v = float(np.mean(rates))
+    times, warm = oracle_sweeps(prob, threads, 150.0, max(1, args.steps), warmup=min(1, args.warmup))
+    ms = 1e3 * float(np.mean(times))
+    v = 1e3 / ms
+    sample = (f"{len(times)} whole FP64 oracle sweep(s) of the workload after {warm} warm-up sweep(s), "
+              f"{threads} threads, {ms / 1e3:.2f} s per sweep (requested {args.steps} steps, {args.warmup} warm-up; "
+              f"the count that fits about 150 s)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+            "steps": len(times), "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(prob, {"precision": "fp64 (CPU oracle)"}),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": smp.text(float(np.mean(secs)))},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -251,11 +254,18 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def kernel_sources_sha256() -> str:
+    """Hash of the tile kernels' sources (kernels.cuh, then lazy.cuh)."""
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "lazy.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2002_02328_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def kernel_traffic(name: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel source (else None)."""
+    current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", f"traffic_{name}.txt")
-    src = os.path.join(ROOT, "paper_2002_02328_gb300", "csrc", "kernels.cuh")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -263,8 +273,7 @@ def kernel_traffic(name: str):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if kv.get("kernels_cuh_sha256") != sha:
+    if kv.get("kernel_sources_sha256") != kernel_sources_sha256():
         return None
     try:
         return float(kv["dram_bytes_per_launch_full_size"])
@@ -272,17 +281,23 @@ def kernel_traffic(name: str):
         return None
 
 
-def algorithmic_bytes(prob, slabs, rz, g_bytes=4):
+def algorithmic_bytes(prob, slabs, rz, g_bytes=4, fused=False):
     """Per-class algorithmic bytes of one sweep (halos excluded; n voxels, each
     slab's zone = the slab widened by rz slices each way, at least one below):
     objective 8 per voxel (x and the carried r in); gradient 8 + g_bytes (r, x in; g out);
     curvature g_bytes + 8 per voxel (g, d, x in) + 8 per zone voxel (H d_S in,
     H g_S out); update 16 + g_bytes per voxel (x, g, d in; x, d out) + 20 per
-    zone voxel (H g_S, H d_S, r in; H d_S, r out).  The exact refreshes of r and
-    H d_S (every 256 sweeps) are not counted."""
+    zone voxel (H g_S, H d_S, r in; H d_S, r out).  The fused-update iteration
+    of a volume without slabs (fused=True) has no objective or update pass: its
+    gradient pass reads x, g, d, r, H g, H d and writes x, d, r, H d, g
+    (36 + 2 g_bytes per voxel), its curvature pass g_bytes + 16.  The exact
+    refreshes of r and H d_S (every 256 sweeps) are not counted."""
     nz, ny, nx = prob.shape
     plane = nx * ny
     n = prob.n
+    if fused:
+        return {"objective": 0.0, "residual": 0.0, "gradient": (36.0 + 2 * g_bytes) * n,
+                "curvature": (g_bytes + 16.0) * n, "update": 0.0}
     b = list(slabs) if slabs is not None and len(slabs) > 2 else [0, nz]
     zone = sum(min(nz, b[s + 1] + rz) - max(0, b[s] - max(rz, 1)) for s in range(len(b) - 1)) * plane
     return {"objective": 8.0 * n, "residual": 0.0, "gradient": (8.0 + g_bytes) * n,
@@ -444,6 +459,53 @@ def batch_extra(iters, stream):
                               "batched_lockstep": (max(k) * t_batch) if ok else None,
                               "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None},
             "stopped_after": k_stop}
+
+
+def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
+    """The plain FP32 iteration on the 512x512x128 recipe (PSF 9x9x7), where the
+    HBM roofline target is set: iterations/s of the fused-update form (two
+    passes) and of the separate-update form (four), L2 flushed before every
+    step (every array is 128 MiB, larger than L2), the dominant kernel's
+    roofline, and the iteration against the 28 B/voxel one-pass bound and
+    against the form's own byte count."""
+    from paper_2002_02328_gb300 import binding, synth
+    prob = synth.workload_mixed(seed=0)
+    rates, profs = {}, {}
+    for name, sep in (("fused", 0), ("separate", 1)):
+        with binding.Solver.from_problem(prob, slabs=None, separate_update=sep) as s:
+            for _ in range(3):
+                flush.fill_(1.0)
+                s.iterate_async(1)
+            ms = time_steps(s, steps, flush, stream)
+            prof = {k: [0.0, 0] for k in binding.Solver.KERNEL_CLASSES}
+            for _ in range(profile_iters):
+                flush.fill_(2.0)
+                for k, (t, cnt) in s.profile_iteration().items():
+                    prof[k][0] += t
+                    prof[k][1] += cnt
+        rates[name] = (ms / steps, 1e3 * steps / ms)
+        profs[name] = {k: v[0] / profile_iters for k, v in prof.items()}
+        if name == "fused":
+            prof_f = prof
+    alg = algorithmic_bytes(prob, None, 4, fused=True)
+    per_it = profs["fused"]
+    dom = max(per_it, key=per_it.get)
+    launches = prof_f[dom][1] / profile_iters
+    avg_ms = per_it[dom] / launches
+    achieved = (alg[dom] / launches) / (avg_ms * 1e-3) / 1e9
+    name = "k_gradlazy" if dom == "gradient" else f"k_{dom}"
+    ms_it = rates["fused"][0]
+    own = sum(alg.values())
+    return {"workload": "plain 3MG 512x512x128, PSF 9x9x7 depth-variant Gaussian, 800 ellipsoids + texture, FP32",
+            "bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": kernel_traffic(name), "peak_kind": f"{peak_kind} hbm_gbs",
+            "alg_bytes_per_launch": alg[dom] / launches, "avg_launch_ms": avg_ms,
+            "iterations_per_s": rates["fused"][1], "ms_per_iteration": ms_it,
+            "iterations_per_s_separate_update": rates["separate"][1],
+            "kernel_ms_per_iteration": per_it, "kernel_ms_per_iteration_separate_update": profs["separate"],
+            "iteration_vs_28B_bound": 28.0 * prob.n / (ms_it * 1e-3) / 1e9 / peak,
+            "own_bytes_per_voxel": own / prob.n,
+            "iteration_vs_own_bytes": own / (ms_it * 1e-3) / 1e9 / peak}
 
 
 def mixed_extra(fstar_iters, stream, flush, steps):
@@ -722,7 +784,7 @@ def ours(args):
                 "kernel_ms_per_sweep": per_it}
     # whole sweep against the 7-word (28 B/voxel) lower bound of one fused pass
     sweep_lb_ms = 28.0 * prob.n / (peak * 1e9) * 1e3
-    alg_plain = algorithmic_bytes(prob, None, 3)
+    alg_plain = algorithmic_bytes(prob, None, 3, fused=True)
     per_it_plain = {k: v[0] / args.profile_iters for k, v in prof_plain.items()}
 
     extra = {"sweep_vs_28B_lower_bound": sweep_lb_ms / ms_per_step,
@@ -733,6 +795,7 @@ def ours(args):
                                        "kernel_ms_per_iteration": {k: v[0] / args.profile_iters
                                                                    for k, v in prof_mixed.items()}}}
 
+    roof512 = plain512_roofline(stream, flush, max(10, args.steps), args.profile_iters, peak, peak_kind)
     extra["joint_xy_penalty"] = penalty_mode_extra(prob, args, flush, stream, binding.PENALTY_JOINT_XY)
     extra["isotropic_penalty"] = penalty_mode_extra(prob, args, flush, stream, binding.PENALTY_ISOTROPIC)
     cpu = None
@@ -770,16 +833,13 @@ def ours(args):
     else:
         e2e = None
     if not args.no_cpu_baseline and world == 1:
-        threads = len(os.sched_getaffinity(0))
-        smp = OracleSample(prob, args.cpu_seconds, threads)
-        r, secs = smp.measure()
-        cpu = {"value": r, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": smp.text(secs)}
+        cpu = cpu_baseline(prob, args.cpu_seconds)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(prob, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "roofline_plain_512": roof512, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * lpi + refresh_launches(args.warmup, args.steps), "clocks": clocks,
             "extra": extra}
     print(json.dumps(line), flush=True)

@@ -36,6 +36,17 @@ def test_plain_iteration_moves_80_bytes_per_voxel():
     assert bf["gradient"] / p.n == 10.0 and bf["curvature"] / p.n == 18.0 and bf["update"] / p.n == 38.0
 
 
+def test_fused_iteration_moves_64_bytes_per_voxel():
+    """Two passes: gradient reads x, g, d, r, H g, H d and writes x, d, r, H d, g;
+    curvature reads g, d, x, H d and writes H g."""
+    p = _prob((128, 512, 512))
+    b = bench.algorithmic_bytes(p, None, 4, fused=True)
+    per_voxel = {k: v / p.n for k, v in b.items()}
+    assert per_voxel == {"objective": 0.0, "residual": 0.0, "gradient": 44.0, "curvature": 20.0, "update": 0.0}
+    bf = bench.algorithmic_bytes(p, None, 4, g_bytes=2, fused=True)
+    assert bf["gradient"] / p.n == 40.0 and bf["curvature"] / p.n == 18.0
+
+
 def test_block_workload_zones_and_curvature_bytes():
     p = _prob((64, 256, 256))
     bounds = [0, 4, 18, 24, 34, 39, 51, 58, 64]
