@@ -30,6 +30,12 @@ Parity status per function (what pins it is in the tests named):
                               under axis permutation; finite differences;
                               majorisation, tangency; descent and stationarity)
                                                   tests/test_oracle_objective.py, test_oracle_3mg.py
+  ablation variants (run_variant; Section 3.2, Table 1): A = L I with the
+  Lipschitz bound, D = -g, the Fletcher-Reeves conjugate direction with the
+  majorant's closed-form step, the Jacobi block schedule with curvature
+  inflation: pinned (Hessian eigenvalues below the bound; dense gradient
+  descent; scipy CG on least squares; Jacobi = sequential for decoupled slabs;
+  monotone descent)                   tests/test_oracle_variants.py
 Workload-level values of the paper (SNR on FlyBrain/Aneurysm): parity unpinned
 (datasets not available).
 """
@@ -57,6 +63,11 @@ class _Problem(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("eta", ctypes.c_double),
                 ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
                 ("penalty", ctypes.c_int), ("kappa", ctypes.c_double)]
+
+
+class _Variant(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_int), ("lipschitz", ctypes.c_double), ("direction", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -92,6 +103,11 @@ def _load():
             lib.orc_3mg_step.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]
             lib.orc_3mg.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, dp]
             lib.orc_gradient_at.argtypes = [P, dp, dp, ctypes.c_int, dp, dp]
+            V = ctypes.POINTER(_Variant)
+            lib.orc_lipschitz_bound.argtypes = [P]
+            lib.orc_lipschitz_bound.restype = ctypes.c_double
+            lib.orc_3mg_step_v.argtypes = [P, V, dp, dp, dp, dp, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp, dp]
+            lib.orc_3mg_v.argtypes = [P, V, dp, dp, dp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double, dp, dp]
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -247,3 +263,41 @@ def run(op: OracleProblem, y, x0, n_sweeps: int, bounds: Optional[Sequence[int]]
     _load().orc_3mg(op.ref, _ptr(y), _ptr(x), _ptr(d), int(n_sweeps), int(ns), _ptr(b), _ptr(o),
                     float(rtol), _ptr(ft) if trace else None)
     return x, d, (ft if trace else None)
+
+
+# ---------------------------------------------------------------------------
+# Ablation variants (Section 3.2, Table 1) and block schedules
+# ---------------------------------------------------------------------------
+METRIC_MAJORANT, METRIC_LIPSCHITZ = 0, 1
+DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2
+SCHEDULE_SEQUENTIAL, SCHEDULE_JACOBI = 0, 1
+
+
+def lipschitz_bound(op: OracleProblem) -> float:
+    """Upper bound on the Lipschitz constant of grad f (||H||_1 ||H||_inf + 2 eta
+    + the penalty's Hessian bound)."""
+    return float(_load().orc_lipschitz_bound(op.ref))
+
+
+def _variant(metric=0, lipschitz=0.0, direction=0, schedule=0, inflation=1.0):
+    return _Variant(int(metric), float(lipschitz), int(direction), int(schedule), float(inflation))
+
+
+def run_variant(op: OracleProblem, y, x0, n_sweeps: int, bounds: Optional[Sequence[int]] = None,
+                order: Optional[Sequence[int]] = None, rtol: float = 1e-12, **variant):
+    """n_sweeps sweeps of an ablation variant (keywords: metric, lipschitz,
+    direction, schedule, inflation).  Returns (x, d, f_trace)."""
+    y = _f32(y)
+    x = op._vol(x0).copy()
+    d = np.zeros_like(x)
+    if bounds is None:
+        bounds = [0, op.shape[0]]
+    b = np.ascontiguousarray(bounds, dtype=np.int32)
+    ns = len(bounds) - 1
+    o = np.ascontiguousarray(order if order is not None else range(ns), dtype=np.int32)
+    state = np.zeros(2 * ns)
+    ft = np.zeros(n_sweeps + 1)
+    v = _variant(**variant)
+    _load().orc_3mg_v(op.ref, ctypes.byref(v), _ptr(y), _ptr(x), _ptr(d), int(n_sweeps), int(ns), _ptr(b), _ptr(o),
+                      float(rtol), _ptr(state), _ptr(ft))
+    return x, d, ft

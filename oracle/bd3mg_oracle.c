@@ -516,3 +516,147 @@ void orc_gradient_at(const orc_problem *p, const float *y, const double *x, int 
         out[q] = s;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Ablation variants of Section 3.2 (Table 1) and the block schedules.
+ *
+ *   metric 0: the half-quadratic majorant A(x) above (3MG, BD3MG, BP3MG);
+ *   metric 1: A = L I, L a bound on the Lipschitz constant of grad f
+ *             (Async-GD, Async-CG);
+ *   direction 0: D = [-g | d] (memory gradient, 2x2 solve);
+ *   direction 1: D = -g (gradient only, 1x1 solve; Async-GD);
+ *   direction 2: conjugate direction p = -g + beta p_prev with the
+ *             Fletcher-Reeves beta = ||g||^2 / ||g_prev||^2 of the block, and
+ *             the step minimising the block majorant along p (the closed-form
+ *             stepsize of memory-gradient / CG methods), restarted with
+ *             p = -g when p is not a descent direction (Async-CG);
+ *   schedule 0: blocks one after the other in the given order (delta = 0);
+ *   schedule 1: Jacobi -- every block's step computed from the same iterate
+ *             x^k and all of them added (the parallel block update of BP3MG);
+ *   inflation: the block majorant's curvature scaled by this factor >= 1
+ *             (Assumption C asks the block curvature to exceed the delayed
+ *             one; m blocks updated at once from the same iterate majorise f
+ *             when it is at least m, by (sum_S v_S)^T A (sum_S v_S) <=
+ *             m sum_S v_S^T A v_S for positive semidefinite A).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int metric;
+    double lipschitz;
+    int direction;
+    int schedule;
+    double inflation;
+} orc_variant;
+
+/* Upper bound on the Lipschitz constant of grad f: ||H||_2^2 <= ||H||_1 ||H||_inf
+ * (largest absolute column sum times largest absolute row sum of H), the box
+ * term's 2 eta, and the penalty's Hessian bound (its curvature in t is at most
+ * lambda / delta, ||V^a||_2 <= 2): mode 0 and mode 2, 12 lambda / delta;
+ * mode 1, 8 lambda / delta + 8 kappa. */
+double orc_lipschitz_bound(const orc_problem *p) {
+    int rx = (p->px - 1) / 2, ry = (p->py - 1) / 2, rz = (p->pz - 1) / 2;
+    double rowmax = 0.0, colmax = 0.0;
+    for (int z = 0; z < p->nz; ++z) {
+        double s = 0.0;
+        for (int c = -rz; c <= rz; ++c)
+            for (int b = -ry; b <= ry; ++b)
+                for (int a = -rx; a <= rx; ++a) s += fabs(tap(p, z, a, b, c));
+        if (s > rowmax) rowmax = s;
+    }
+    /* column of input depth zi: every output depth z = zi + c that reads it */
+    for (int zi = 0; zi < p->nz; ++zi) {
+        double s = 0.0;
+        for (int c = -rz; c <= rz; ++c) {
+            int z = zi + c;
+            if (z < 0 || z >= p->nz) continue;
+            for (int b = -ry; b <= ry; ++b)
+                for (int a = -rx; a <= rx; ++a) s += fabs(tap(p, z, a, b, c));
+        }
+        if (s > colmax) colmax = s;
+    }
+    double pen = p->penalty == 1 ? 8.0 * p->lambda / p->delta + 8.0 * p->kappa : 12.0 * p->lambda / p->delta;
+    return rowmax * colmax + 2.0 * p->eta + pen;
+}
+
+/* One block step of a variant on the slab [z0, z1): g and the metric are taken
+ * at xe (the sweep's iterate for the Jacobi schedule, x itself otherwise); the
+ * increment D u is added to x and stored in d.  state[2] carries the block's
+ * previous ||g_S||^2 and step length for direction 2 (zero at the start).
+ * info (optional, 8): B[4], c[2], u[2]. */
+void orc_3mg_step_v(const orc_problem *p, const orc_variant *v, const float *y, const double *xe, double *x,
+                    double *d, int z0, int z1, double pinv_rtol, double *state, double *info) {
+    long long n = nvox(p);
+    long long plane = (long long)p->nx * p->ny;
+    long long k0 = (long long)z0 * plane, k1 = (long long)z1 * plane;
+    double *g = (double *)calloc(n, sizeof(double));
+    double *D0 = (double *)calloc(n, sizeof(double));
+    double *D1 = (double *)calloc(n, sizeof(double));
+    double *A0 = (double *)malloc(sizeof(double) * n);
+    double *A1 = (double *)malloc(sizeof(double) * n);
+    orc_gradient(p, y, xe, g);
+    for (long long k = k0; k < k1; ++k) { D0[k] = -g[k]; D1[k] = v->direction == 1 ? 0.0 : d[k]; }
+    if (v->metric == 1) {
+        for (long long k = 0; k < n; ++k) { A0[k] = v->lipschitz * D0[k]; A1[k] = v->lipschitz * D1[k]; }
+    } else {
+        orc_apply_A(p, xe, D0, A0);
+        orc_apply_A(p, xe, D1, A1);
+    }
+    double B[4] = {dot(D0, A0, n), dot(D0, A1, n), dot(D1, A0, n), dot(D1, A1, n)};
+    for (int i = 0; i < 4; ++i) B[i] *= v->inflation;
+    double gS[2] = {0, 0};
+    for (long long k = k0; k < k1; ++k) { gS[0] += D0[k] * g[k]; gS[1] += D1[k] * g[k]; }
+    double u[2] = {0.0, 0.0};
+    if (v->direction == 0) {
+        orc_pinv2_solve(B, gS, u, pinv_rtol);
+    } else if (v->direction == 1) {
+        if (B[0] > 0.0) u[0] = -gS[0] / B[0];
+    } else {
+        /* p = -g + beta p_prev, p_prev = d / (previous step): p = D [1, beta'] */
+        double gg = -gS[0], bp = 0.0;
+        if (state[0] > 0.0 && state[1] > 0.0) bp = (gg / state[0]) / state[1];
+        double slope = gS[0] + bp * gS[1];
+        double curv = B[0] + bp * (B[1] + B[2]) + bp * bp * B[3];
+        if (!(slope < 0.0) || !(curv > 0.0)) {             /* restart along -g */
+            bp = 0.0;
+            slope = gS[0];
+            curv = B[0];
+        }
+        if (curv > 0.0) {
+            double a = -slope / curv;
+            u[0] = a;
+            u[1] = a * bp;
+        }
+        state[0] = gg;
+        state[1] = u[0];
+    }
+    for (long long k = k0; k < k1; ++k) {
+        double inc = u[0] * D0[k] + u[1] * D1[k];
+        x[k] += inc;
+        d[k] = inc;
+    }
+    if (info) {
+        info[0] = B[0]; info[1] = B[1]; info[2] = B[2]; info[3] = B[3];
+        info[4] = gS[0]; info[5] = gS[1]; info[6] = u[0]; info[7] = u[1];
+    }
+    free(g); free(D0); free(D1); free(A0); free(A1);
+}
+
+/* n_sweeps sweeps of a variant: schedule 0 visits the slabs order[0..nslabs-1]
+ * one after the other; schedule 1 computes every slab's step from the sweep's
+ * iterate and adds them all.  state: 2 * nslabs doubles (direction 2), zero at
+ * the start.  f_trace (optional, n_sweeps + 1) as in orc_3mg. */
+void orc_3mg_v(const orc_problem *p, const orc_variant *v, const float *y, double *x, double *d, int n_sweeps,
+               int nslabs, const int *bounds, const int *order, double pinv_rtol, double *state, double *f_trace) {
+    long long n = nvox(p);
+    double *xk = (double *)malloc(sizeof(double) * n);
+    for (int k = 0; k < n_sweeps; ++k) {
+        if (f_trace) f_trace[k] = orc_objective(p, y, x, NULL);
+        if (v->schedule == 1) memcpy(xk, x, sizeof(double) * n);
+        for (int s = 0; s < nslabs; ++s) {
+            int b = order ? order[s] : s;
+            orc_3mg_step_v(p, v, y, v->schedule == 1 ? xk : x, x, d, bounds[b], bounds[b + 1], pinv_rtol,
+                           state + 2 * b, NULL);
+        }
+    }
+    if (f_trace) f_trace[n_sweeps] = orc_objective(p, y, x, NULL);
+    free(xk);
+}
