@@ -99,6 +99,39 @@ enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1 };
  * Every volume of a batch must use the same penalty mode. */
 enum { BD3MG_PENALTY_PER_AXIS = 0, BD3MG_PENALTY_JOINT_XY = 1, BD3MG_PENALTY_ISOTROPIC = 2 };
 
+/* Ablation variants of the ablation study (Section 3.2, Table 1), as switches
+ * on the same kernels.  The paper's methods map to:
+ *   BD3MG / 3MG:  METRIC_MAJORANT, DIR_MEMORY_GRADIENT, SCHEDULE_COLOURED (defaults)
+ *   BP3MG:        METRIC_MAJORANT, DIR_MEMORY_GRADIENT, SCHEDULE_JACOBI
+ *   Async-GD:     METRIC_LIPSCHITZ, DIR_GRADIENT
+ *   Async-CG:     METRIC_LIPSCHITZ, DIR_CONJUGATE
+ * (Async-MM, whose worker inverts A(x) with an inner BiCG solve, is not built.)
+ * metric: the block majorant's curvature matrix.  METRIC_MAJORANT: the
+ *   half-quadratic A(x) of bd3mg_create; METRIC_LIPSCHITZ: A = L I with L the
+ *   caller's lipschitz, or (lipschitz = 0) the library's bound on the
+ *   Lipschitz constant of grad f, ||H||_1 ||H||_inf + 2 eta + the penalty's
+ *   Hessian bound (12 lambda / delta; mode 1: 8 lambda / delta + 8 kappa).
+ * direction: DIR_MEMORY_GRADIENT, D = [-g, d] and the 2x2 minimiser;
+ *   DIR_GRADIENT, D = -g (one-dimensional minimiser, u = ||g||^2 / g^T A g);
+ *   DIR_CONJUGATE, p = -g + beta p_prev with the Fletcher-Reeves beta =
+ *   ||g||^2 / ||g_prev||^2 of the slab and the step minimising the majorant
+ *   along p, restarted along -g when p is not a descent direction.  (Read
+ *   literally, D = [-g, d] with A = L I minimises an isotropic quadratic over a
+ *   subspace that contains g, which gives the gradient step whatever d is; the
+ *   conjugate direction is the reading that keeps the memory term.)
+ * schedule: SCHEDULE_COLOURED, the colour-major sweep (equal to visiting the
+ *   slabs one after the other); SCHEDULE_JACOBI, every slab's step computed
+ *   from the same iterate and all applied together (the parallel block update
+ *   without delay of BP3MG); r and H d_S are then recomputed exactly after
+ *   every sweep.
+ * inflation: the subspace matrix is multiplied by this factor >= 1 (Assumption
+ *   C: the block curvature must dominate what the delayed or simultaneous
+ *   updates need; m slabs updated from one iterate descend when it is >= m).
+ *   0 -> 1 for SCHEDULE_COLOURED, the number of slabs for SCHEDULE_JACOBI. */
+enum { BD3MG_METRIC_MAJORANT = 0, BD3MG_METRIC_LIPSCHITZ = 1 };
+enum { BD3MG_DIR_MEMORY_GRADIENT = 0, BD3MG_DIR_GRADIENT = 1, BD3MG_DIR_CONJUGATE = 2 };
+enum { BD3MG_SCHEDULE_COLOURED = 0, BD3MG_SCHEDULE_JACOBI = 1 };
+
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
     int px, py, pz;           /* PSF extents, odd, >= 1 */
@@ -125,6 +158,11 @@ typedef struct {
                                  each iteration's update inside the next gradient pass (two passes
                                  per iteration, see bd3mg_create); 1: separate objective and update
                                  passes, as the slab form always runs.  Taken from p[0] of a batch */
+    int metric;               /* BD3MG_METRIC_MAJORANT (default) or BD3MG_METRIC_LIPSCHITZ */
+    double lipschitz;         /* L of BD3MG_METRIC_LIPSCHITZ (> 0), or 0: the library's bound */
+    int direction;            /* BD3MG_DIR_MEMORY_GRADIENT (default), BD3MG_DIR_GRADIENT, BD3MG_DIR_CONJUGATE */
+    int schedule;             /* BD3MG_SCHEDULE_COLOURED (default) or BD3MG_SCHEDULE_JACOBI (from p[0]) */
+    double inflation;         /* >= 1, or 0: 1 (coloured) / the number of slabs (Jacobi) */
 } bd3mg_params;
 
 /* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,
@@ -379,6 +417,11 @@ bd3mg_status bd3mg_autotune(int nvol, const bd3mg_params *p, const float *const 
  * z-chunks, or more than a few thousand depth slices). */
 bd3mg_status bd3mg_objective_noalloc(const bd3mg_params *p, const float *x, const float *y, double *f_out,
                                      void *stream, char *err, size_t err_len);
+
+/* The metric constant L of each volume (nvol doubles): the caller's lipschitz
+ * or the library's bound for BD3MG_METRIC_LIPSCHITZ (computed at creation from
+ * the factored PSF), and that bound also when the volume uses the majorant. */
+bd3mg_status bd3mg_lipschitz(bd3mg_ctx *ctx, double *L);
 
 const char *bd3mg_error_string(bd3mg_ctx *ctx);
 const char *bd3mg_status_string(bd3mg_status s);

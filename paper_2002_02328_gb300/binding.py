@@ -26,6 +26,9 @@ STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
 FP32, BF16_GRADIENT = 0, 1
 PENALTY_PER_AXIS, PENALTY_JOINT_XY, PENALTY_ISOTROPIC = 0, 1, 2
+METRIC_MAJORANT, METRIC_LIPSCHITZ = 0, 1
+DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2
+SCHEDULE_COLOURED, SCHEDULE_JACOBI = 0, 1
 FAULT_NONE, FAULT_SKIP_COPY = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
@@ -36,7 +39,7 @@ EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iter
             "bd3mg_batch_create", "bd3mg_volume_count", "bd3mg_objectives", "bd3mg_get_volume", "bd3mg_set_stopping",
             "bd3mg_stopped", "bd3mg_set_escalation", "bd3mg_escalated", "bd3mg_save", "bd3mg_load",
             "bd3mg_autotune", "bd3mg_inject_fault", "bd3mg_error_string",
-            "bd3mg_status_string", "bd3mg_destroy"]
+            "bd3mg_status_string", "bd3mg_destroy", "bd3mg_lipschitz"]
 
 
 class Bd3mgError(RuntimeError):
@@ -55,7 +58,9 @@ class Params(ctypes.Structure):
                 ("pinv_rtol", ctypes.c_double), ("zchunk", ctypes.c_int),
                 ("penalty", ctypes.c_int), ("kappa", ctypes.c_double),
                 ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
-                ("separate_update", ctypes.c_int)]
+                ("separate_update", ctypes.c_int),
+                ("metric", ctypes.c_int), ("lipschitz", ctypes.c_double), ("direction", ctypes.c_int),
+                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -109,6 +114,7 @@ def load(path: str = LIB_PATH):
             "bd3mg_load": (ip, [vp, ctypes.c_char_p]),
             "bd3mg_autotune": (ip, [ip, P, vp, ip, vp, ip, ctypes.c_char_p, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
+            "bd3mg_lipschitz": (ip, [vp, ctypes.c_void_p]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
             "bd3mg_destroy": (None, [vp]),
         }
@@ -156,7 +162,8 @@ def _torch_allocator():
 def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
                 zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
-                barrier_timeout_ms: int = 0, separate_update: int = 0):
+                barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
+                direction: int = 0, schedule: int = 0, inflation: float = 0.0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -173,6 +180,8 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.penalty, p.kappa = int(penalty), float(kappa)
     p.refresh_every, p.barrier_timeout_ms = int(refresh_every), int(barrier_timeout_ms)
     p.separate_update = int(separate_update)
+    p.metric, p.lipschitz, p.direction = int(metric), float(lipschitz), int(direction)
+    p.schedule, p.inflation = int(schedule), float(inflation)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -263,13 +272,15 @@ class Solver:
     def __init__(self, shape, psf, y, x0=None, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0,
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
                  use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
-                 barrier_timeout_ms: int = 0, separate_update: int = 0):
+                 barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
+                 direction: int = 0, schedule: int = 0, inflation: float = 0.0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
-                                   penalty, kappa, refresh_every, barrier_timeout_ms, separate_update)
+                                   penalty, kappa, refresh_every, barrier_timeout_ms, separate_update, metric,
+                                   lipschitz, direction, schedule, inflation)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -406,6 +417,12 @@ class Solver:
         cnt = np.zeros(5, np.int32)
         self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
+
+    def lipschitz(self) -> float:
+        """The metric constant L (the caller's, else the library's Lipschitz bound)."""
+        L = np.zeros(1)
+        self._c(self._lib.bd3mg_lipschitz(self._ctx, L.ctypes.data))
+        return float(L[0])
 
     def launches_per_iteration(self) -> int:
         return int(self._lib.bd3mg_launches_per_iteration(self._ctx))
@@ -547,6 +564,12 @@ class BatchSolver:
         cnt = np.zeros(5, np.int32)
         self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(Solver.KERNEL_CLASSES)}
+
+    def lipschitz(self) -> np.ndarray:
+        """The metric constant L of each volume."""
+        L = np.zeros(self.nvol)
+        self._c(self._lib.bd3mg_lipschitz(self._ctx, L.ctypes.data))
+        return L
 
     def launches_per_iteration(self) -> int:
         return int(self._lib.bd3mg_launches_per_iteration(self._ctx))

@@ -56,6 +56,7 @@ struct VolState {
     __nv_bfloat16 *gh1 = nullptr;
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev dev{};                   // host copy of the device descriptor
+    double lip = 0.0;               // metric constant L (caller's, else the library's bound)
     std::vector<int> bounds;        // slab bounds
     std::vector<int> colour;        // per slab
     int seg0 = 0;                   // index of its first slab segment
@@ -96,6 +97,7 @@ struct bd3mg_ctx {
     // fused-update iteration (no slabs): the gradient pass applies the previous
     // update; a second buffer set (x1.., zone_hg1, zone_hd1) takes what it writes
     bool lazy = false;
+    bool jacobi = false;            // every slab's step from the same iterate (BD3MG_SCHEDULE_JACOBI)
     bool pending = false;           // some graph launch may have left an update or set 1 state behind
     float *zone_hg1 = nullptr, *zone_hd1 = nullptr;
     int *flush_list = nullptr;      // every slab segment (one per volume), for k_flush
@@ -443,7 +445,7 @@ bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     return check_launch(c);
 }
 
-bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
+bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour, bool zone = true) {
     const int off = c->seg_list_off[colour], cnt = c->seg_list_off[colour + 1] - off;
     if (cnt == 0) return BD3MG_OK;
     long long maxlen = 0;
@@ -458,7 +460,7 @@ bd3mg_status run_update(bd3mg_ctx *c, cudaStream_t s, int colour) {
     dim3 grid((unsigned)blocks, (unsigned)cnt);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_UPDATE);
     if (st) return st;
-    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, c->run, grid, s, c->bf);
+    launch_update(c->vols, c->segs, c->seg_lists + off, c->u, c->run, grid, s, c->bf, zone);
     return check_launch(c);
 }
 
@@ -496,7 +498,12 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
         if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
         if (branch && col == 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
-        if ((st = run_update(c, s, col))) return st;
+        if ((st = run_update(c, s, col, !c->jacobi))) return st;
+    }
+    if (c->jacobi) {
+        // the slabs' zones overlap, so r and H d_S are recomputed, not carried
+        if ((st = run_residual(c, s, c->L_res_full, M_STORE_R))) return st;
+        if ((st = run_residual(c, s, c->L_hd, M_STORE_R | M_ZONE))) return st;
     }
     return BD3MG_OK;
 }
@@ -616,6 +623,10 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
         d.lam_d = p.lambda; d.eta_d = p.eta;
+        d.metric = p.metric;
+        d.direction = p.direction;
+        d.lip = vs.lip;
+        d.infl = p.inflation > 0 ? p.inflation : (c->jacobi ? (double)(vs.bounds.size() - 1) : 1.0);
         if (p.penalty == BD3MG_PENALTY_JOINT_XY) {
             d.kl = (float)(p.kappa / p.lambda);
             d.kl2 = (float)(2.0 * p.kappa / p.lambda);
@@ -803,6 +814,14 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
         return fail(c, BD3MG_EINVAL, "volume %d: unknown penalty mode %d", vi, p.penalty);
     if (!(p.kappa >= 0) || !std::isfinite(p.kappa))
         return fail(c, BD3MG_EINVAL, "volume %d: kappa must be finite and >= 0", vi);
+    if ((p.metric != BD3MG_METRIC_MAJORANT && p.metric != BD3MG_METRIC_LIPSCHITZ) ||
+        (p.direction != BD3MG_DIR_MEMORY_GRADIENT && p.direction != BD3MG_DIR_GRADIENT &&
+         p.direction != BD3MG_DIR_CONJUGATE) ||
+        (p.schedule != BD3MG_SCHEDULE_COLOURED && p.schedule != BD3MG_SCHEDULE_JACOBI))
+        return fail(c, BD3MG_EINVAL, "volume %d: unknown metric, direction or schedule", vi);
+    if (!(p.lipschitz >= 0) || !std::isfinite(p.lipschitz) || !(p.inflation == 0 || p.inflation >= 1) ||
+        !std::isfinite(p.inflation))
+        return fail(c, BD3MG_EINVAL, "volume %d: lipschitz must be finite and >= 0, inflation 0 or >= 1", vi);
     if ((long long)p.nx * p.ny * p.nz > (1LL << 34)) return fail(c, BD3MG_EINVAL, "volume %d too large", vi);
     v.p = p;
     const int ns = p.nslabs <= 1 ? 1 : p.nslabs;
@@ -862,16 +881,20 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
                         "volume %d: PSF is not separable per depth (relative rank-1 residual %.3g > 1e-6); "
                         "only separable PSFs are implemented", v, worst);
         c->V[v].p.psf = nullptr;
+        c->V[v].lip = pp[v].lipschitz > 0 ? pp[v].lipschitz
+                                          : lipschitz_bound(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v]);
     }
 
     // segments and colouring: slabs of one volume and colour are >= max(pz-1, 1)
     // slices apart, so their zones [z0 - max(rz, 1), z1 + rz) (the slab widened
     // by the volume's own PSF z radius rz) are disjoint
     c->ncolours = 1;
+    c->jacobi = pp[0].schedule == BD3MG_SCHEDULE_JACOBI;
     for (int v = 0; v < nvol; ++v) {
         VolState &vs = c->V[v];
         const int rz = (vs.p.pz - 1) / 2, nz = vs.p.nz;
-        c->ncolours = std::max(c->ncolours, colour_slabs(vs.bounds, std::max(2 * rz, 1), vs.colour));
+        if (c->jacobi) vs.colour.assign(vs.bounds.size() - 1, 0);      // every slab at once
+        else c->ncolours = std::max(c->ncolours, colour_slabs(vs.bounds, std::max(2 * rz, 1), vs.colour));
         vs.seg0 = (int)c->segs_h.size();
         for (size_t s = 0; s + 1 < vs.bounds.size(); ++s) {
             const int z0 = vs.bounds[s], z1 = vs.bounds[s + 1];
@@ -1626,7 +1649,14 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
     if (!c) return 0;
-    return c->lazy ? 2 : 1 + 3 * c->ncolours;
+    return c->lazy ? 2 : 1 + 3 * c->ncolours + (c->jacobi ? 2 : 0);
+}
+
+bd3mg_status bd3mg_lipschitz(bd3mg_ctx *c, double *L) {
+    GUARD(c);
+    if (!L) return fail(c, BD3MG_EINVAL, "L is NULL");
+    for (int v = 0; v < c->nvol; ++v) L[v] = c->V[v].lip;
+    return BD3MG_OK;
 }
 
 }  // extern "C"

@@ -33,9 +33,9 @@ struct KernelSet {
 const KernelSet *find_kernel_set(int R, int RZ, int pm);
 
 // Block update over the slabs listed in seg_list (grid.y = number of slabs);
-// run (nullable) marks stopped volumes.
+// run (nullable) marks stopped volumes; zone = false leaves r and H d_S alone.
 void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
-                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16);
+                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16, bool zone = true);
 // Objective of every volume from the carried residual (no convolution),
 // penalty mode pm: a.nitems CTAs, volume slot sl owning CTAs
 // [slot_beg[sl], slot_beg[sl+1]); same reduction and finish as k_residual's

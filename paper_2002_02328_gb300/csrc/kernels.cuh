@@ -106,6 +106,11 @@ struct VolDev {
     // 2 kappa/lambda, 2 kappa (zero in mode 0)
     float kl, kl2, kap2;
     double lam_d, eta_d;
+    // ablation variants (Section 3.2): metric 0 = half-quadratic majorant, 1 = L I;
+    // direction 0 = [-g, d], 1 = -g, 2 = Fletcher-Reeves conjugate direction;
+    // the subspace matrix is scaled by infl (curvature inflation, >= 1)
+    int metric, direction;
+    double lip, infl;
 };
 
 // TMA descriptors of one volume (global memory, 64-byte aligned).
@@ -1282,20 +1287,54 @@ static __device__ __forceinline__ void curvature_finish(const KArgs &a) {
         if (tid == 0) {
             const VolDev &vv = a.vols[ss.vol];
             const double e2 = 2.0 * vv.eta_d, lam = vv.lam_d;
-            const double b00 = tot[3] + e2 * tot[0] + lam * tot[6];
-            const double b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
-            const double b11 = tot[5] + e2 * tot[2] + lam * tot[8];
+            double b00, b01, b11;
+            if (vv.metric == 1) {           // A = L I: B = L D^T D
+                b00 = vv.lip * tot[0];
+                b01 = -vv.lip * tot[1];
+                b11 = vv.lip * tot[2];
+            } else {                        // half-quadratic majorant A(x)
+                b00 = tot[3] + e2 * tot[0] + lam * tot[6];
+                b01 = -(tot[4] + e2 * tot[1] + lam * tot[7]);
+                b11 = tot[5] + e2 * tot[2] + lam * tot[8];
+            }
+            b00 *= vv.infl;
+            b01 *= vv.infl;
+            b11 *= vv.infl;
             const double c0 = -tot[0], c1 = tot[1];
+            double *inf = a.info + 8 * slot;
             double u0 = 0.0, u1 = 0.0;
             int rank = 0;
             if (isfinite(b00) && isfinite(b01) && isfinite(b11) && isfinite(c0) && isfinite(c1)) {
-                rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
+                if (vv.direction == 0) {
+                    rank = solve2x2_pinv(b00, b01, b11, c0, c1, a.pinv_rtol, &u0, &u1);
+                } else if (vv.direction == 1) {     // D = -g: one-dimensional minimiser
+                    if (b00 > 0.0) {
+                        u0 = -c0 / b00;
+                        rank = 1;
+                    }
+                } else {
+                    // p = -g + beta p_prev with beta = ||g||^2 / ||g_prev||^2, p_prev = d / alpha_prev
+                    // (this slab's previous gradient norm and step, kept in its info record),
+                    // the step minimising the majorant along p; restart along -g when p does not descend
+                    const double gg_prev = -inf[3], a_prev = inf[5];
+                    double bp = (gg_prev > 0.0 && a_prev > 0.0) ? (tot[0] / gg_prev) / a_prev : 0.0;
+                    double slope = c0 + bp * c1, curv = b00 + 2.0 * bp * b01 + bp * bp * b11;
+                    if (!(slope < 0.0) || !(curv > 0.0)) {
+                        bp = 0.0;
+                        slope = c0;
+                        curv = b00;
+                    }
+                    if (curv > 0.0) {
+                        u0 = -slope / curv;
+                        u1 = u0 * bp;
+                        rank = 1;
+                    }
+                }
             } else {
                 atomicOr(a.sh->status, ST_NONFINITE);
             }
             a.u[2 * slot] = u0;
             a.u[2 * slot + 1] = u1;
-            double *inf = a.info + 8 * slot;
             inf[0] = b00; inf[1] = b01; inf[2] = b11; inf[3] = c0; inf[4] = c1;
             inf[5] = u0; inf[6] = u1; inf[7] = (double)rank;
             // Slab S of the sweep from x^k: x_S still holds x^k_S (only its own

@@ -100,6 +100,41 @@ bool factor_psf(const bd3mg_params &p, int R, int RZ, std::vector<float> &fx, st
     return factor_psf_into(p, R, RZ, fx.data(), fy.data(), fz.data(), worst);
 }
 
+// Bound on the Lipschitz constant of grad f from the factored PSF of one volume
+// (factor rows of length 2R+1, 2RZ+1 per output depth): ||H||_2^2 <= ||H||_1 ||H||_inf,
+// the largest absolute column sum (every output depth z = zi + c reading input
+// depth zi) times the largest absolute row sum; plus 2 eta and the penalty's
+// Hessian bound lambda / delta times sum_a ||V^a||^2 <= 12 (8 for the joint X-Y
+// term of mode 1, which adds 2 kappa ||V^Z||^2 <= 8 kappa).
+double lipschitz_bound(const bd3mg_params &p, int R, int RZ, const std::vector<float> &fx,
+                       const std::vector<float> &fy, const std::vector<float> &fz) {
+    const int kxy = 2 * R + 1, kz = 2 * RZ + 1;
+    auto absum = [](const float *v, int n) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += std::fabs((double)v[i]);
+        return s;
+    };
+    std::vector<double> sxy(p.nz);
+    double rowmax = 0.0;
+    for (int z = 0; z < p.nz; ++z) {
+        sxy[z] = absum(&fx[(size_t)z * kxy], kxy) * absum(&fy[(size_t)z * kxy], kxy);
+        rowmax = std::max(rowmax, sxy[z] * absum(&fz[(size_t)z * kz], kz));
+    }
+    double colmax = 0.0;
+    for (int zi = 0; zi < p.nz; ++zi) {
+        double s = 0.0;
+        for (int c = -RZ; c <= RZ; ++c) {
+            const int z = zi + c;
+            if (z < 0 || z >= p.nz) continue;
+            s += sxy[z] * std::fabs((double)fz[(size_t)z * kz + c + RZ]);
+        }
+        colmax = std::max(colmax, s);
+    }
+    const double pen = p.penalty == BD3MG_PENALTY_JOINT_XY ? 8.0 * p.lambda / p.delta + 8.0 * p.kappa
+                                                            : 12.0 * p.lambda / p.delta;
+    return rowmax * colmax + 2.0 * p.eta + pen;
+}
+
 // Greedy colouring in increasing z: a slab takes the first colour whose slabs
 // all end at least `gap` slices before it starts.  Slabs of one colour then
 // read and write disjoint data, so updating them together equals updating them

@@ -36,6 +36,11 @@ bool factor_psf_into(const bd3mg_params &p, int R, int RZ, float *fx, float *fy,
 bool factor_psf(const bd3mg_params &p, int R, int RZ, std::vector<float> &fx, std::vector<float> &fy,
                 std::vector<float> &fz, double *worst);
 
+// Bound on the Lipschitz constant of grad f from a volume's PSF factors (rows
+// zero padded to radii R, RZ) and its parameters.
+double lipschitz_bound(const bd3mg_params &p, int R, int RZ, const std::vector<float> &fx,
+                       const std::vector<float> &fy, const std::vector<float> &fz);
+
 // Greedy slab colouring (see bd3mg_plan_slab_colours); returns the colour count.
 int colour_slabs(const std::vector<int> &bounds, int gap, std::vector<int> &colour);
 

@@ -18,10 +18,12 @@ namespace bd3mg {
 // voxel.  Planes are multiples of 8 elements, so every range starts on a
 // 16-byte boundary of every array.
 // BF: g stored as BF16 (widened to FP32; d, x, r and the zone buffers are FP32).
+// zone = false (the Jacobi schedule, whose slabs' zones overlap): x_S and d_S
+// only; r and H d_S are then recomputed exactly after the update.
 // ---------------------------------------------------------------------------
 template <bool BF>
 __global__ void __launch_bounds__(NT) k_update(const VolDev *vols, const SegDev *segs, const int *seg_list,
-                                               const double *u, const VolRun *run) {
+                                               const double *u, const VolRun *run, bool zone) {
     const SegDev sg = segs[seg_list[blockIdx.y]];
     if (run && run[sg.vol].stopped) return;
     const VolDev &v = vols[sg.vol];
@@ -53,7 +55,7 @@ __global__ void __launch_bounds__(NT) k_update(const VolDev *vols, const SegDev 
             d4[i] = nd;
         }
     }
-    {
+    if (zone) {
         const long long n4 = ((long long)(sg.hz1 - sg.hz0) * v.plane) >> 2;
         const float4 *hg4 = reinterpret_cast<const float4 *>(sg.hg);
         float4 *hd4 = reinterpret_cast<float4 *>(sg.hd);
@@ -210,9 +212,9 @@ __global__ void __launch_bounds__(NT) k_dir_to_float(const __nv_bfloat16 *src, f
 }
 
 void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
-                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16) {
-    if (bf16) k_update<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
-    else k_update<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+                   const VolRun *run, dim3 grid, cudaStream_t s, bool bf16, bool zone) {
+    if (bf16) k_update<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run, zone);
+    else k_update<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run, zone);
 }
 
 void launch_objective(const KArgs &a, cudaStream_t s, int pm) {
