@@ -461,6 +461,40 @@ def batch_extra(iters, stream):
             "stopped_after": k_stop}
 
 
+def ablation_extra(prob, fstar, stream, flush, steps, max_iters=3000):
+    """The methods of the paper's ablation study (Section 3.2, Table 1) on the block
+    workload, as switches on the same kernels: sweeps/s (L2 flushed before every
+    step) and sweeps and device time to the relative gap 1e-4 against the
+    workload's f*.  Async-MM (inner BiCG solves) is not built."""
+    from paper_2002_02328_gb300 import binding
+    variants = {
+        "BD3MG (colour-major sweep)": {},
+        "BP3MG (Jacobi, curvature x slab count)": {"schedule": binding.SCHEDULE_JACOBI},
+        "Async-GD (A = L I, D = -g)": {"metric": binding.METRIC_LIPSCHITZ, "direction": binding.DIR_GRADIENT},
+        "Async-CG (A = L I, conjugate direction)": {"metric": binding.METRIC_LIPSCHITZ,
+                                                    "direction": binding.DIR_CONJUGATE},
+    }
+    out = {"fstar": fstar, "max_sweeps": max_iters}
+    for name, kw in variants.items():
+        with binding.Solver.from_problem(prob, **kw) as s:
+            for _ in range(3):
+                flush.fill_(1.0)
+                s.iterate_async(1)
+            ms = time_steps(s, steps, flush, stream)
+            L = s.lipschitz()
+        rec = {"sweeps_per_s": 1e3 * steps / ms, "lipschitz": L if kw.get("metric") else None}
+        if fstar is not None:
+            with binding.Solver.from_problem(prob, **kw) as s:
+                tr = s.iterate(max_iters)
+            gap = (tr - fstar) / abs(fstar)
+            hit = np.nonzero(gap <= GAP)[0]
+            rec["sweeps_to_gap"] = int(hit[0]) if hit.size else None
+            rec["seconds_to_gap"] = rec["sweeps_to_gap"] * ms / steps / 1e3 if hit.size else None
+            rec["gap_after_max_sweeps"] = float(gap[-1])
+        out[name] = rec
+    return out
+
+
 def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
     """The plain FP32 iteration on the 512x512x128 recipe (PSF 9x9x7), where the
     HBM roofline target is set: iterations/s of the fused-update form (two
@@ -816,6 +850,7 @@ def ours(args):
                                 "normalized_gap": {"definition": "(f - f*) / (f0 - f*) <= 1e-4",
                                                    "block": {"iterations": k_bn, "seconds": t_bn},
                                                    "plain_fp32": {"iterations": k_pn, "seconds": t_pn}}}
+        extra["ablation"] = ablation_extra(prob, fstar, stream, flush, max(10, args.steps // 2))
         extra["batched"] = batch_extra(min(args.fstar_iters, 3000), stream)
         extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
         if not args.no_warm_start:

@@ -132,6 +132,18 @@ enum { BD3MG_METRIC_MAJORANT = 0, BD3MG_METRIC_LIPSCHITZ = 1 };
 enum { BD3MG_DIR_MEMORY_GRADIENT = 0, BD3MG_DIR_GRADIENT = 1, BD3MG_DIR_CONJUGATE = 2 };
 enum { BD3MG_SCHEDULE_COLOURED = 0, BD3MG_SCHEDULE_JACOBI = 1 };
 
+/* Blur path.  The separable path factors each depth's PSF as fx(a) fy(b)
+ * fz(c) and convolves axis by axis inside the tile kernels.  The dense path
+ * (a PSF that does not factor, such as the rotated Gaussians of Section 3.1,
+ * or radii beyond the separable kernels) applies the taps as given with a
+ * direct convolution per output depth: PSF extents up to 11 x 11 in x, y and
+ * 21 in z (the paper's 11 x 11 x 21 and 5 x 5 x 11), FP32 gradient only; the
+ * iteration, slab form, batches, variants and stopping are the same.  With a
+ * dense PSF, bd3mg_objective and bd3mg_gradient first recompute r and H d_S
+ * exactly (the refresh an iteration does every refresh_every sweeps).  The
+ * allocation-free objective takes separable PSFs only. */
+enum { BD3MG_PSF_AUTO = 0, BD3MG_PSF_DENSE = 1 };
+
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
     int px, py, pz;           /* PSF extents, odd, >= 1 */
@@ -163,6 +175,9 @@ typedef struct {
     int direction;            /* BD3MG_DIR_MEMORY_GRADIENT (default), BD3MG_DIR_GRADIENT, BD3MG_DIR_CONJUGATE */
     int schedule;             /* BD3MG_SCHEDULE_COLOURED (default) or BD3MG_SCHEDULE_JACOBI (from p[0]) */
     double inflation;         /* >= 1, or 0: 1 (coloured) / the number of slabs (Jacobi) */
+    int psf_mode;             /* BD3MG_PSF_AUTO (default): the separable fast path when every depth's PSF
+                                 factors and its radii are compiled (xy <= 5, z <= 5), else the dense path;
+                                 BD3MG_PSF_DENSE: the dense path always (taken from p[0]) */
 } bd3mg_params;
 
 /* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,

@@ -29,6 +29,7 @@ PENALTY_PER_AXIS, PENALTY_JOINT_XY, PENALTY_ISOTROPIC = 0, 1, 2
 METRIC_MAJORANT, METRIC_LIPSCHITZ = 0, 1
 DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2
 SCHEDULE_COLOURED, SCHEDULE_JACOBI = 0, 1
+PSF_AUTO, PSF_DENSE = 0, 1
 FAULT_NONE, FAULT_SKIP_COPY = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
@@ -60,7 +61,7 @@ class Params(ctypes.Structure):
                 ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
                 ("separate_update", ctypes.c_int),
                 ("metric", ctypes.c_int), ("lipschitz", ctypes.c_double), ("direction", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double)]
+                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double), ("psf_mode", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -163,7 +164,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
                 zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                 barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
-                direction: int = 0, schedule: int = 0, inflation: float = 0.0):
+                direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -182,6 +183,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.separate_update = int(separate_update)
     p.metric, p.lipschitz, p.direction = int(metric), float(lipschitz), int(direction)
     p.schedule, p.inflation = int(schedule), float(inflation)
+    p.psf_mode = int(psf_mode)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -273,14 +275,14 @@ class Solver:
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
                  use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                  barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
-                 direction: int = 0, schedule: int = 0, inflation: float = 0.0):
+                 direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
                                    penalty, kappa, refresh_every, barrier_timeout_ms, separate_update, metric,
-                                   lipschitz, direction, schedule, inflation)
+                                   lipschitz, direction, schedule, inflation, psf_mode)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):

@@ -57,6 +57,10 @@ struct VolState {
     float *fx = nullptr, *fy = nullptr, *fz = nullptr;
     VolDev dev{};                   // host copy of the device descriptor
     double lip = 0.0;               // metric constant L (caller's, else the library's bound)
+    // dense PSF path: padded taps (host copy until upload), device taps, H^T r scratch
+    std::vector<float> h3_host;
+    float *h3 = nullptr, *q = nullptr;
+    int rz3 = 0;
     std::vector<int> bounds;        // slab bounds
     std::vector<int> colour;        // per slab
     int seg0 = 0;                   // index of its first slab segment
@@ -98,6 +102,9 @@ struct bd3mg_ctx {
     // update; a second buffer set (x1.., zone_hg1, zone_hd1) takes what it writes
     bool lazy = false;
     bool jacobi = false;            // every slab's step from the same iterate (BD3MG_SCHEDULE_JACOBI)
+    bool dense = false;             // dense PSF path (direct convolutions, identity-factor tile kernels)
+    int dense_R = 1;                // xy radius of the dense kernels' padded taps
+    std::vector<Launch> L_dzone;    // dense path: per colour, 32-row tiles over the slabs' zones
     bool pending = false;           // some graph launch may have left an update or set 1 state behind
     float *zone_hg1 = nullptr, *zone_hd1 = nullptr;
     int *flush_list = nullptr;      // every slab segment (one per volume), for k_flush
@@ -436,9 +443,23 @@ bd3mg_status run_gradlazy(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
     return check_launch(c);
 }
 
+// Dense-PSF convolution over a launch's items: src (DS_*) into dst (DD_*),
+// forward H (optionally minus y) or adjoint H^T, input masked to each
+// segment's slab if asked; iter: items of stopped volumes exit.
+bd3mg_status run_dense(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int src, int dst, bool adj, bool sub_y,
+                       bool mask, bool iter, const VolDev *vols = nullptr) {
+    if (L.nitems == 0) return BD3MG_OK;
+    DenseArgs a{vols ? vols : c->vols, c->segs, c->items + L.item_off, L.nitems, src, dst, sub_y ? 1 : 0,
+                mask ? 1 : 0, iter ? 1 : 0, c->run};
+    bd3mg_status st = prof_mark(c, s, adj ? BD3MG_K_GRADIENT : (dst == DD_HG ? BD3MG_K_CURVATURE : BD3MG_K_RESIDUAL));
+    if (st) return st;
+    launch_dense(a, c->dense_R, adj, s);
+    return check_launch(c);
+}
+
 bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     if (L.nitems == 0) return BD3MG_OK;
-    KArgs a = make_args(c, L, c->lazy ? (M_ITER | M_PAR) : M_ITER, nullptr);
+    KArgs a = make_args(c, L, (c->lazy ? (M_ITER | M_PAR) : M_ITER) | (c->dense ? M_HG_GIVEN : 0), nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
     (c->bf ? c->ks->curvature_bf : c->ks->curvature)(a, s);
@@ -495,17 +516,41 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
         if ((st = run_objective(c, s, c->L_objc, M_OBJ | M_TRACE | M_ADVANCE | M_ITER))) return st;
     }
     for (int col = 0; col < c->ncolours; ++col) {
-        if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
+        if (c->dense) {
+            // q = H^T r on the colour's slabs, then the tile gradient pass adds the penalty terms
+            if ((st = run_dense(c, s, c->L_grad[col], DS_R, DD_Q, true, false, false, true))) return st;
+            if ((st = run_gradient(c, s, c->L_grad[col], M_ITER | M_QSRC))) return st;
+            // H g_S (g masked to the slab) over each slab's zone, read by the curvature pass
+            if ((st = run_dense(c, s, c->L_dzone[col], DS_G, DD_HG, false, false, true, true))) return st;
+        } else {
+            if ((st = run_gradient(c, s, c->L_grad[col], M_ITER))) return st;
+        }
         if ((st = run_curvature(c, s, c->L_curv[col]))) return st;
         if (branch && col == 0) CK(cudaStreamWaitEvent(s, c->ev_join, 0));
         if ((st = run_update(c, s, col, !c->jacobi))) return st;
     }
     if (c->jacobi) {
         // the slabs' zones overlap, so r and H d_S are recomputed, not carried
-        if ((st = run_residual(c, s, c->L_res_full, M_STORE_R))) return st;
-        if ((st = run_residual(c, s, c->L_hd, M_STORE_R | M_ZONE))) return st;
+        if (c->dense) {
+            if ((st = run_dense(c, s, c->L_res_full, DS_X, DD_R, false, true, false, false))) return st;
+            if ((st = run_dense(c, s, c->L_hd, DS_D, DD_HD, false, false, true, false))) return st;
+        } else {
+            if ((st = run_residual(c, s, c->L_res_full, M_STORE_R))) return st;
+            if ((st = run_residual(c, s, c->L_hd, M_STORE_R | M_ZONE))) return st;
+        }
     }
     return BD3MG_OK;
+}
+
+// f(x) of every volume into fout, with the blur applied afresh: the separable
+// path convolves x inside the objective kernel; the dense path recomputes r and
+// H d_S exactly (a refresh) and reads the objective from r.
+bd3mg_status refresh_products(bd3mg_ctx *c);
+bd3mg_status fresh_objective(bd3mg_ctx *c) {
+    bd3mg_status st;
+    if (!c->dense) return run_residual(c, c->stream, c->L_obj, M_OBJ);
+    if ((st = refresh_products(c))) return st;
+    return run_objective(c, c->stream, c->L_objc, M_OBJ);
 }
 
 // Exact r = H x - y of every volume and H d_S of every slab (d masked to the
@@ -513,8 +558,13 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
 bd3mg_status refresh_products(bd3mg_ctx *c) {
     NvtxRange nvtx_("bd3mg refresh r, H d_S");
     bd3mg_status st;
-    if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
-    if ((st = run_residual(c, c->stream, c->L_hd, M_STORE_R | M_ZONE))) return st;
+    if (c->dense) {
+        if ((st = run_dense(c, c->stream, c->L_res_full, DS_X, DD_R, false, true, false, false))) return st;
+        if ((st = run_dense(c, c->stream, c->L_hd, DS_D, DD_HD, false, false, true, false))) return st;
+    } else {
+        if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
+        if ((st = run_residual(c, c->stream, c->L_hd, M_STORE_R | M_ZONE))) return st;
+    }
     c->stale = false;
     c->since_refresh = 0;
     return BD3MG_OK;
@@ -619,6 +669,7 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         d.plane = (long long)vs.pitch * p.ny;
         d.x = vs.x; d.d = vs.d; d.g = vs.g; d.r = vs.r; d.y = vs.y; d.gh = vs.gh;
         d.x1 = vs.x1; d.d1 = vs.d1; d.g1 = vs.g1; d.r1 = vs.r1; d.gh1 = vs.gh1;
+        d.h3 = vs.h3; d.rz3 = vs.rz3; d.q = vs.q;
         d.fx = vs.fx; d.fy = vs.fy; d.fz = vs.fz;
         d.lam = (float)p.lambda; d.delta2 = (float)(p.delta * p.delta); d.eta2 = (float)(2.0 * p.eta);
         d.xmin = (float)p.xmin; d.xmax = (float)p.xmax;
@@ -637,6 +688,9 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
                               : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
         if (ok && c->lazy) ok = encode_lazy_maps(&vm[v], c, vs);
+        if (ok && c->dense)
+            ok = encode_map(&vm[v].m[TM_Q_R], vs.q, 4, p.nx, p.ny, p.nz, vs.pitch, TX + 2 * set_xh(c->ks),
+                            TY_A + 2 * c->ks->R);
         if (!ok)
             return fail(c, BD3MG_ECUDA, "cuTensorMapEncodeTiled failed (driver entry point unavailable?)");
     }
@@ -724,6 +778,7 @@ void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
     c->seg_list_off.assign(1, 0);
     c->L_grad.clear();
     c->L_curv.clear();
+    c->L_dzone.clear();
     if (c->colour_zc.empty()) c->colour_zc.assign(2 * (size_t)c->ncolours, 0);
     for (int col = 0; col < c->ncolours; ++col) {
         std::vector<int> segs, gsegs;
@@ -743,6 +798,9 @@ void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
             *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_PER_SEGMENT, 2, zc + 1));
         for (int s : segs) c->seg_lists_h.push_back(s);
         c->seg_list_off.push_back((int)c->seg_lists_h.size());
+        if (c->dense)
+            c->L_dzone.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
+                *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_NONE, 1));
     }
     c->plan_active = active;
 }
@@ -769,6 +827,8 @@ bool work_lists_fit(const bd3mg_ctx *c) {
     for (const Launch &L : c->L_grad)
         if (L.nitems > c->items_per_launch_cap) return false;
     for (const Launch &L : c->L_curv)
+        if (L.nitems > c->items_per_launch_cap) return false;
+    for (const Launch &L : c->L_dzone)
         if (L.nitems > c->items_per_launch_cap) return false;
     return true;
 }
@@ -870,19 +930,63 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     for (int v = 1; v < nvol; ++v)
         if (pp[v].penalty != pp[0].penalty) return fail(c, BD3MG_EINVAL, "volumes must share one penalty mode");
 
-    // kernels for the PSF radii (all volumes share one compiled set; smaller PSFs are zero padded)
-    c->ks = find_kernel_set(R, RZ, pp[0].penalty);
-    if (!c->ks) return fail(c, BD3MG_EUNSUPPORTED, "no kernels for PSF radii (%d, %d); max 5", R, RZ);
+    // kernels for the PSF radii (all volumes share one compiled set; smaller PSFs
+    // are zero padded).  The separable path needs every depth's PSF to factor and
+    // a compiled set for its radii; otherwise (or when asked) the dense path runs
+    // the tile kernels with identity factors around direct convolutions.
+    if (pp[0].psf_mode != BD3MG_PSF_AUTO && pp[0].psf_mode != BD3MG_PSF_DENSE)
+        return fail(c, BD3MG_EINVAL, "psf_mode must be BD3MG_PSF_AUTO or BD3MG_PSF_DENSE");
     std::vector<std::vector<float>> FX(nvol), FY(nvol), FZ(nvol);
-    for (int v = 0; v < nvol; ++v) {
-        double worst = 0.0;
-        if (!factor_psf(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v], &worst))
+    c->dense = pp[0].psf_mode == BD3MG_PSF_DENSE;
+    double worst_any = 0.0;
+    if (!c->dense) {
+        c->ks = find_kernel_set(R, RZ, pp[0].penalty);
+        for (int v = 0; v < nvol && c->ks && !c->dense; ++v) {
+            double worst = 0.0;
+            if (!factor_psf(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v], &worst)) c->dense = true;
+            worst_any = std::max(worst_any, worst);
+        }
+        if (!c->ks) c->dense = true;
+    }
+    if (c->dense) {
+        if (R > 5 || RZ > 10)
             return fail(c, BD3MG_EUNSUPPORTED,
-                        "volume %d: PSF is not separable per depth (relative rank-1 residual %.3g > 1e-6); "
-                        "only separable PSFs are implemented", v, worst);
-        c->V[v].p.psf = nullptr;
+                        "PSF radii (%d, %d) beyond the dense kernels (xy <= 5, z <= 10); PSF factor residual %.3g",
+                        R, RZ, worst_any);
+        if (pp[0].precision != BD3MG_FP32)
+            return fail(c, BD3MG_EUNSUPPORTED, "the dense PSF path runs with an FP32 gradient only");
+        c->ks = find_kernel_set(1, 1, pp[0].penalty);
+        if (!c->ks) return fail(c, BD3MG_EUNSUPPORTED, "no identity kernel set");
+        c->dense_R = R;
+        const int kxy = 2 * c->ks->R + 1, kz = 2 * c->ks->RZ + 1;
+        for (int v = 0; v < nvol; ++v) {
+            // identity factors: the tile kernels pass their staged input through unchanged
+            FX[v].assign((size_t)pp[v].nz * kxy, 0.f);
+            FY[v].assign((size_t)pp[v].nz * kxy, 0.f);
+            FZ[v].assign((size_t)pp[v].nz * kz, 0.f);
+            for (int z = 0; z < pp[v].nz; ++z) {
+                FX[v][(size_t)z * kxy + c->ks->R] = 1.f;
+                FY[v][(size_t)z * kxy + c->ks->R] = 1.f;
+                FZ[v][(size_t)z * kz + c->ks->RZ] = 1.f;
+            }
+            // taps [z][c][b][a] zero padded to (2R+1) x (2R+1) in x and y
+            VolState &vs = c->V[v];
+            const int K = 2 * R + 1, rx = (pp[v].px - 1) / 2, ry = (pp[v].py - 1) / 2;
+            vs.rz3 = (pp[v].pz - 1) / 2;
+            vs.h3_host.assign((size_t)pp[v].nz * pp[v].pz * K * K, 0.f);
+            for (int z = 0; z < pp[v].nz; ++z)
+                for (int cc = 0; cc < pp[v].pz; ++cc)
+                    for (int b = 0; b < pp[v].py; ++b)
+                        for (int a = 0; a < pp[v].px; ++a)
+                            vs.h3_host[(((size_t)z * pp[v].pz + cc) * K + (b - ry + R)) * K + (a - rx + R)] =
+                                pp[v].psf[(((size_t)z * pp[v].pz + cc) * pp[v].py + b) * pp[v].px + a];
+        }
+    }
+    for (int v = 0; v < nvol; ++v) {
         c->V[v].lip = pp[v].lipschitz > 0 ? pp[v].lipschitz
-                                          : lipschitz_bound(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v]);
+                      : c->dense      ? lipschitz_bound_dense(pp[v])
+                                      : lipschitz_bound(pp[v], c->ks->R, c->ks->RZ, FX[v], FY[v], FZ[v]);
+        c->V[v].p.psf = nullptr;
     }
 
     // segments and colouring: slabs of one volume and colour are >= max(pz-1, 1)
@@ -905,7 +1009,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->nslab_segs = (int)c->segs_h.size();
     // without slabs, each update is applied inside the next gradient pass
-    c->lazy = !c->any_slabs && pp[0].separate_update == 0;
+    c->lazy = !c->any_slabs && pp[0].separate_update == 0 && !c->dense;
     for (int v = 0; v < nvol; ++v)
         c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size(), 0, 0, nullptr, nullptr});
 
@@ -976,6 +1080,10 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
             }
         }
         AL(vs.fx, FX[v].size()); AL(vs.fy, FY[v].size()); AL(vs.fz, FZ[v].size());
+        if (c->dense) {
+            AL(vs.h3, vs.h3_host.size());
+            AL(vs.q, vs.np);
+        }
     }
     // zone buffers of the slabs, one after another (every zone a whole number of planes)
     c->zone_elems = 0;
@@ -1044,6 +1152,10 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         CK(cudaMemcpyAsync(vs.fx, FX[v].data(), FX[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fy, FY[v].data(), FY[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
         CK(cudaMemcpyAsync(vs.fz, FZ[v].data(), FZ[v].size() * 4, cudaMemcpyHostToDevice, c->stream));
+        if (c->dense) {
+            CK(cudaMemcpyAsync(vs.h3, vs.h3_host.data(), vs.h3_host.size() * 4, cudaMemcpyHostToDevice, c->stream));
+            CK(cudaMemsetAsync(vs.q, 0, vs.np * 4, c->stream));
+        }
     }
     CK(cudaMemsetAsync(c->zone_hg, 0, c->zone_elems * 4, c->stream));
     CK(cudaMemsetAsync(c->zone_hd, 0, c->zone_elems * 4, c->stream));
@@ -1126,7 +1238,18 @@ bd3mg_status apply_op(bd3mg_ctx *c, const float *in, float *out, bool adjoint) {
     v.y = nullptr;
     VolMaps vm;
     bool ok;
-    if (adjoint) {
+    if (c->dense) {
+        // the dense kernels read x (forward) or r (adjoint) and write r or q directly
+        if (adjoint) {
+            v.r = c->scr_in;
+            v.q = c->scr_out;
+        } else {
+            v.x = c->scr_in;
+            v.r = c->scr_out;
+        }
+        ok = true;
+        std::memset(&vm, 0, sizeof(vm));
+    } else if (adjoint) {
         v.r = c->scr_in;
         v.g = c->scr_out;
         ok = encode_vol_maps(&vm, c, v0, nullptr, c->scr_in, nullptr, nullptr);
@@ -1146,8 +1269,12 @@ bd3mg_status apply_op(bd3mg_ctx *c, const float *in, float *out, bool adjoint) {
     while (n0 < L.nitems && c->segs_h[c->items_h[L.item_off + n0].seg].vol == 0) ++n0;
     L.nitems = n0;
     L.nslots = 0;
-    st = adjoint ? run_gradient(c, c->stream, L, M_HT_ONLY, c->vols + sv)
-                 : run_residual(c, c->stream, L, M_STORE_R, c->vols + sv);
+    if (c->dense)
+        st = adjoint ? run_dense(c, c->stream, L, DS_R, DD_Q, true, false, false, false, c->vols + sv)
+                     : run_dense(c, c->stream, L, DS_X, DD_R, false, false, false, false, c->vols + sv);
+    else
+        st = adjoint ? run_gradient(c, c->stream, L, M_HT_ONLY, c->vols + sv)
+                     : run_residual(c, c->stream, L, M_STORE_R, c->vols + sv);
     if (st) return st;
     if ((st = copy_vol(c, v0, out, c->scr_out, 1, false))) return st;
     return check_status(c);
@@ -1353,7 +1480,7 @@ bd3mg_status bd3mg_objective(bd3mg_ctx *c, double *f, double *parts) {
     GUARD(c);
     bd3mg_status st;
     if ((st = settle(c))) return st;
-    if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ))) return st;
+    if ((st = fresh_objective(c))) return st;
     double h[4];
     CK(cudaMemcpyAsync(h, c->fout, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     if ((st = check_status(c))) return st;
@@ -1367,7 +1494,7 @@ bd3mg_status bd3mg_objectives(bd3mg_ctx *c, double *f) {
     if (!f) return fail(c, BD3MG_EINVAL, "f is NULL");
     bd3mg_status st;
     if ((st = settle(c))) return st;
-    if ((st = run_residual(c, c->stream, c->L_obj, M_OBJ))) return st;
+    if ((st = fresh_objective(c))) return st;
     std::vector<double> h(4 * (size_t)c->nvol);
     CK(cudaMemcpyAsync(h.data(), c->fout, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
     if ((st = check_status(c))) return st;
@@ -1379,8 +1506,15 @@ bd3mg_status bd3mg_gradient(bd3mg_ctx *c, float *g, int on_device, double *f) {
     GUARD(c);
     bd3mg_status st;
     if ((st = settle(c))) return st;
-    if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R | M_OBJ))) return st;
-    if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
+    if (c->dense) {
+        if ((st = refresh_products(c))) return st;
+        if ((st = run_objective(c, c->stream, c->L_objc, M_OBJ))) return st;
+        if ((st = run_dense(c, c->stream, c->L_grad_full, DS_R, DD_Q, true, false, false, false))) return st;
+        if ((st = run_gradient(c, c->stream, c->L_grad_full, M_QSRC))) return st;
+    } else {
+        if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R | M_OBJ))) return st;
+        if ((st = run_gradient(c, c->stream, c->L_grad_full, 0))) return st;
+    }
     if (g) {
         const VolState &v = c->V[0];
         const float *src = v.g;

@@ -48,6 +48,10 @@ int objective_occupancy(int pm);
 void launch_flush(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, const VolRun *run,
                   dim3 grid, cudaStream_t s, bool bf16);
 void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s);
+// Dense-PSF blur (dense.cu) with xy radius R (1..5) of the padded taps, forward
+// (H) or adjoint (H^T), over a.nitems work items.
+struct DenseArgs;
+void launch_dense(const DenseArgs &a, int R, bool adj, cudaStream_t s);
 // dst[i] = float(src[i]) for n BF16 elements.
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
 

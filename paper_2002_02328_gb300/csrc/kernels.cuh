@@ -84,6 +84,10 @@ constexpr int M_LAZY = 128;       // objective finish of k_gradlazy: a volume wh
                                   // now lives in its other buffer set (VolRun::par flips)
 constexpr int M_PAR = 256;        // k_curvature: read the volume's current buffer set (VolRun::par) and mark
                                   // the new update pending (VolRun::pending)
+constexpr int M_QSRC = 512;       // k_gradient (dense PSF): stage q = H^T r (TM_Q_R) in place of r; the
+                                  // kernel's own factors are the identity
+constexpr int M_HG_GIVEN = 1024;  // k_curvature (dense PSF): H g_S is already in the zone buffer; read it
+                                  // instead of forming and storing it
 
 // Status bits (device word)
 constexpr int ST_NONFINITE = 1;
@@ -111,6 +115,12 @@ struct VolDev {
     // the subspace matrix is scaled by infl (curvature inflation, >= 1)
     int metric, direction;
     double lip, infl;
+    // dense PSF (non-separable blur): taps [nz][2 rz3 + 1][K][K], K = 2R+1 of the
+    // dense kernels (zero padded), and q, the scratch that takes H^T r; null when
+    // the context uses the separable factors
+    const float *h3;
+    int rz3;
+    float *q;
 };
 
 // TMA descriptors of one volume (global memory, 64-byte aligned).
@@ -118,9 +128,10 @@ struct VolDev {
 //   G_R: g, halo R, 16-row tiles (k_curvature)   D_X: d, halo R, 32-row tiles (k_residual, M_ZONE)
 //   HG_R, HD_R: H g and H d of a whole-volume zone, halo R, 32-row tiles (k_gradlazy)
 //   *1_*: the same maps over the second buffer set (fused-update iteration)
+//   Q_R: q = H^T r of the dense-PSF path, halo R, 32-row tiles (k_gradient, M_QSRC)
 enum {
     TM_X_R = 0, TM_R_R = 1, TM_G_R = 2, TM_D_X = 3, TM_HG_R = 4, TM_HD_R = 5,
-    TM_R1_R = 6, TM_G1_R = 7, TM_HG1_R = 8, TM_HD1_R = 9, TM_COUNT = 10
+    TM_R1_R = 6, TM_G1_R = 7, TM_HG1_R = 8, TM_HD1_R = 9, TM_Q_R = 10, TM_COUNT = 11
 };
 struct VolMaps { CUtensorMap m[TM_COUNT]; };
 
@@ -135,6 +146,21 @@ struct SegDev {
     float *hg1, *hd1;             // zone buffers of the second buffer set (fused-update iteration), or null
 };
 struct Item { int seg, tx0, ty0, zo0, zo1; };
+
+// Work of one k_dense launch (dense.cu): input and output selectors, whether y
+// is subtracted (r = H x - y), whether the input is masked to each segment's
+// slab, and whether items of stopped volumes exit (an iteration launch).
+enum { DS_X = 0, DS_R = 1, DS_G = 2, DS_D = 3 };
+enum { DD_R = 0, DD_Q = 1, DD_HG = 2, DD_HD = 3 };
+struct VolRun;
+struct DenseArgs {
+    const VolDev *vols;
+    const SegDev *segs;
+    const Item *items;
+    int nitems;
+    int src, dst, sub_y, mask, iter;
+    const VolRun *run;
+};
 
 // Per-volume stopping state (device).  The objective launch that opens a
 // sweep tests the volume: it stops once the last sweep moved x by at most
@@ -1133,7 +1159,7 @@ __global__ void __launch_bounds__(NT, 3) k_gradient(KArgs a) {
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
     if (!init_bars(bar, NS, smem, a.sh->status)) return;
     const int rlo = max(0, zbeg), rhi = min(nz, zend);
-    const CUtensorMap *mr = &a.maps[sg.vol].m[TM_R_R];
+    const CUtensorMap *mr = &a.maps[sg.vol].m[(a.mode & M_QSRC) ? TM_Q_R : TM_R_R];
     if (tid == 0)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mr)) : "memory");
     const uint32_t nb = (uint32_t)(BX * BY * sizeof(float));
@@ -1444,6 +1470,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
     const float delta2 = V.delta2, kl2 = V.kl2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
+    const bool hg_given = (a.mode & M_HG_GIVEN) != 0;
     // A stopped volume's item gets an empty range: no copies, no loop, zero
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
@@ -1674,8 +1701,12 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curva
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 if (!rok[k]) continue;
-                if (c1ok) *reinterpret_cast<float2 *>(hgz + orow[k]) = hg[k];
-                else hgz[orow[k]] = hg[k].x;
+                if (hg_given) {
+                    hg[k] = __ldg(reinterpret_cast<const float2 *>(hgz + orow[k]));
+                } else {
+                    if (c1ok) *reinterpret_cast<float2 *>(hgz + orow[k]) = hg[k];
+                    else hgz[orow[k]] = hg[k].x;
+                }
                 acc[3] = fmaf(hg[k].x, hg[k].x, acc[3]);
                 acc[4] = fmaf(hg[k].x, hd[k].x, acc[4]);
                 acc[5] = fmaf(hd[k].x, hd[k].x, acc[5]);

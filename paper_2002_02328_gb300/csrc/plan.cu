@@ -135,6 +135,38 @@ double lipschitz_bound(const bd3mg_params &p, int R, int RZ, const std::vector<f
     return rowmax * colmax + 2.0 * p.eta + pen;
 }
 
+// The same bound from the dense PSF (host taps [nz][pz][py][px]): the row sum of
+// output depth z is sum |h_z|, the column sum of input depth zi sums the taps
+// h_{zi+c}(., ., c) of every output depth that reads it.
+double lipschitz_bound_dense(const bd3mg_params &p) {
+    const size_t per = (size_t)p.px * p.py;
+    const int rz = (p.pz - 1) / 2;
+    double rowmax = 0.0, colmax = 0.0;
+    std::vector<double> plane_sum((size_t)p.nz * p.pz, 0.0);     // [z][c]: sum over a, b of |h_z(a, b, c)|
+    for (int z = 0; z < p.nz; ++z) {
+        double row = 0.0;
+        for (int c = 0; c < p.pz; ++c) {
+            double t = 0.0;
+            const float *h = p.psf + ((size_t)z * p.pz + c) * per;
+            for (size_t k = 0; k < per; ++k) t += std::fabs((double)h[k]);
+            plane_sum[(size_t)z * p.pz + c] = t;
+            row += t;
+        }
+        rowmax = std::max(rowmax, row);
+    }
+    for (int zi = 0; zi < p.nz; ++zi) {
+        double col = 0.0;
+        for (int c = -rz; c <= rz; ++c) {
+            const int z = zi + c;
+            if (z >= 0 && z < p.nz) col += plane_sum[(size_t)z * p.pz + c + rz];
+        }
+        colmax = std::max(colmax, col);
+    }
+    const double pen = p.penalty == BD3MG_PENALTY_JOINT_XY ? 8.0 * p.lambda / p.delta + 8.0 * p.kappa
+                                                            : 12.0 * p.lambda / p.delta;
+    return rowmax * colmax + 2.0 * p.eta + pen;
+}
+
 // Greedy colouring in increasing z: a slab takes the first colour whose slabs
 // all end at least `gap` slices before it starts.  Slabs of one colour then
 // read and write disjoint data, so updating them together equals updating them

@@ -41,6 +41,8 @@ bool factor_psf(const bd3mg_params &p, int R, int RZ, std::vector<float> &fx, st
 double lipschitz_bound(const bd3mg_params &p, int R, int RZ, const std::vector<float> &fx,
                        const std::vector<float> &fy, const std::vector<float> &fz);
 
+double lipschitz_bound_dense(const bd3mg_params &p);
+
 // Greedy slab colouring (see bd3mg_plan_slab_colours); returns the colour count.
 int colour_slabs(const std::vector<int> &bounds, int gap, std::vector<int> &colour);
 

@@ -243,6 +243,75 @@ def tiny_problem(shape=(6, 10, 12), psf_shape=(3, 3, 3), sxy=(0.6, 1.2), sz=0.8,
     return make_problem(f"tiny-{shape}", shape, n_ellipsoids, psf_shape, sxy, sz, noise, seed, **kw)
 
 
+def rotated_gaussian_psf(nz: int, psf_shape, seed: int, sxy=(0.5, 2.5), sz=(1.0, 3.0)) -> np.ndarray:
+    """Depth-variant rotated Gaussian PSF (float32 [nz][pz][py][px]), one per
+    output depth: standard deviations sigma_x, sigma_y ~ U[sxy], sigma_z ~ U[sz]
+    and an xy rotation theta ~ U[0, pi) drawn per depth, taps sampled at integer
+    offsets and normalised to sum 1 in FP64.  Not separable in x and y."""
+    px, py, pz = psf_shape
+    rng = np.random.default_rng([seed, 7])
+    rx, ry, rz = (px - 1) // 2, (py - 1) // 2, (pz - 1) // 2
+    c, b, a = np.meshgrid(np.arange(-rz, rz + 1), np.arange(-ry, ry + 1), np.arange(-rx, rx + 1), indexing="ij")
+    out = np.zeros((nz, pz, py, px))
+    for z in range(nz):
+        sx, sy = rng.uniform(*sxy, size=2)
+        szz = rng.uniform(*sz)
+        th = rng.uniform(0.0, np.pi)
+        u = np.cos(th) * a + np.sin(th) * b
+        v = -np.sin(th) * a + np.cos(th) * b
+        h = np.exp(-0.5 * (u * u / (sx * sx) + v * v / (sy * sy) + c * c / (szz * szz)))
+        out[z] = h / h.sum()
+    return out.astype(np.float32)
+
+
+def blur_dense(x: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """H x in FP64 for a dense PSF of the output depth (data synthesis only):
+    out[z] = sum_c conv2d(x[z - c], h_z[c]), zero outside the volume."""
+    from scipy.ndimage import convolve
+    nz = x.shape[0]
+    pz = psf.shape[1]
+    rz = (pz - 1) // 2
+    xd = x.astype(np.float64)
+    out = np.zeros_like(xd)
+    for z in range(nz):
+        for ci in range(pz):
+            zs = z - (ci - rz)
+            if 0 <= zs < nz:
+                out[z] += convolve(xd[zs], psf[z, ci].astype(np.float64), mode="constant", cval=0.0)
+    return out
+
+
+def make_problem_dense(name: str, shape, n_ellipsoids: int, psf: np.ndarray, noise: float, seed: int,
+                       lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0, xmax=1.0, slabs=None) -> Problem:
+    """A problem whose observation is blurred by a given dense PSF."""
+    xt = phantom(shape, n_ellipsoids, seed)
+    rng = np.random.default_rng([seed, 1])
+    y = blur_dense(xt, psf)
+    if noise > 0:
+        y = y + rng.normal(0.0, noise, size=y.shape)
+    return Problem(name=name, shape=tuple(shape), psf=np.ascontiguousarray(psf, np.float32),
+                   y=y.astype(np.float32), x_true=xt.astype(np.float32), lam=lam, delta=delta, eta=eta,
+                   xmin=xmin, xmax=xmax, slabs=slabs,
+                   meta=dict(n_ellipsoids=n_ellipsoids, psf_shape=tuple(psf.shape[1:][::-1]), noise=noise,
+                             seed=seed, psf="rotated Gaussian per depth"))
+
+
+def workload_rotated_256x256x24(seed: int = 0, slabs=None) -> Problem:
+    """The shape of the paper's comparison experiment (Section 3.2): 256x256x24
+    volume, depth-variant rotated Gaussian PSF of 11x11x21 taps, noise 0.04; a
+    phantom of 200 ellipsoids per 256x256x64 (75 here) stands in for FlyBrain."""
+    psf = rotated_gaussian_psf(24, (11, 11, 21), seed, sxy=(0.5, 2.5), sz=(1.0, 4.0))
+    return make_problem_dense("rotated-256x256x24", (24, 256, 256), 75, psf, 0.04, seed, slabs=slabs)
+
+
+def workload_rotated_155x154x79(seed: int = 0, slabs=None) -> Problem:
+    """The shape of the paper's scaling experiment (Section 3.3): 155x154x79
+    volume (x, y, z), depth-variant rotated Gaussian PSF of 5x5x11 taps, noise
+    0.04; a phantom of 90 ellipsoids stands in for Aneurysm."""
+    psf = rotated_gaussian_psf(79, (5, 5, 11), seed, sxy=(0.4, 1.2), sz=(1.0, 2.5))
+    return make_problem_dense("rotated-155x154x79", (79, 154, 155), 90, psf, 0.04, seed, slabs=slabs)
+
+
 def random_psf(nz: int, psf_shape, seed: int) -> np.ndarray:
     """A non-separable, non-symmetric positive PSF per depth (float32), each summing to 1."""
     px, py, pz = psf_shape

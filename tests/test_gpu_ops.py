@@ -96,14 +96,16 @@ def test_objective_and_gradient_match_oracle(cuda_lib, shape, psf_shape):
     assert _maxrel(g, g_ref) <= 2e-5
 
 
-def test_non_separable_psf_is_rejected(cuda_lib):
+def test_non_separable_psf_takes_the_dense_path(cuda_lib):
     import torch
     shape = (4, 16, 16)
     psf = synth.random_psf(4, (3, 3, 3), seed=1)
-    y = torch.zeros(shape, device="cuda")
-    with pytest.raises(cuda_lib.Bd3mgError) as e:
-        cuda_lib.Solver(shape, psf, y)
-    assert e.value.status == 7
+    y = np.random.default_rng(2).uniform(0, 1, size=shape).astype(np.float32)
+    op = oracle.OracleProblem(shape, psf)
+    with cuda_lib.Solver(shape, psf, torch.from_numpy(y).cuda()) as s:
+        f = s.objective()
+    f_ref = oracle.objective(op, y, y)
+    assert abs(f - f_ref) <= 1e-5 * abs(f_ref)
 
 
 def test_invalid_arguments_are_rejected(cuda_lib):
