@@ -297,11 +297,12 @@ def algorithmic_bytes(prob, slabs, rz, g_bytes=4, fused=False):
     n = prob.n
     if fused:
         return {"objective": 0.0, "residual": 0.0, "gradient": (36.0 + 2 * g_bytes) * n,
-                "curvature": (g_bytes + 16.0) * n, "update": 0.0}
+                "curvature": (g_bytes + 16.0) * n, "update": 0.0, "dense": 0.0}
     b = list(slabs) if slabs is not None and len(slabs) > 2 else [0, nz]
     zone = sum(min(nz, b[s + 1] + rz) - max(0, b[s] - max(rz, 1)) for s in range(len(b) - 1)) * plane
     return {"objective": 8.0 * n, "residual": 0.0, "gradient": (8.0 + g_bytes) * n,
-            "curvature": (g_bytes + 8.0) * n + 8.0 * zone, "update": (16.0 + g_bytes) * n + 20.0 * zone}
+            "curvature": (g_bytes + 8.0) * n + 8.0 * zone, "update": (16.0 + g_bytes) * n + 20.0 * zone,
+            "dense": 0.0}
 
 
 def refresh_launches(first: int, count: int, every: int = 256) -> int:
@@ -491,6 +492,88 @@ def ablation_extra(prob, fstar, stream, flush, steps, max_iters=3000):
             rec["sweeps_to_gap"] = int(hit[0]) if hit.size else None
             rec["seconds_to_gap"] = rec["sweeps_to_gap"] * ms / steps / 1e3 if hit.size else None
             rec["gap_after_max_sweeps"] = float(gap[-1])
+        out[name] = rec
+    return out
+
+
+def fp32_fma_peak(sm_mhz: float) -> float:
+    """FP32 FMA issue peak of the GPU in TFLOP/s: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def dense_taps(shape, psf_shape, slabs=None):
+    """Multiply-adds of one dense-PSF iteration: H^T r over every voxel and H g_S
+    over every slab's zone (g masked to the slab), counting only taps whose input
+    lies in the volume (and, for H g_S, in the slab).  Per axis the valid taps
+    are independent, so a count is a product of per-axis counts."""
+    nz, ny, nx = shape
+    px, py, pz = psf_shape
+
+    def axis(n, p, lo=0, hi=None, out=None):
+        hi = n if hi is None else hi
+        r = (p - 1) // 2
+        o = np.arange(n) if out is None else np.arange(*out)
+        i = o[:, None] - np.arange(-r, r + 1)[None, :]
+        return float(np.count_nonzero((i >= lo) & (i < hi)))
+    xy = axis(nx, px) * axis(ny, py)
+    total = xy * axis(nz, pz)                                   # H^T r (the adjoint has the same tap count)
+    b = list(slabs) if slabs is not None and len(slabs) > 2 else [0, nz]
+    rz = (pz - 1) // 2
+    for s in range(len(b) - 1):
+        z0, z1 = b[s], b[s + 1]
+        zone = (max(0, z0 - max(rz, 1)), min(nz, z1 + rz))
+        total += xy * axis(nz, pz, z0, z1, zone)
+    return total
+
+
+def dense_extra(stream, flush, steps, sm_mhz):
+    """The dense (non-separable) PSF path on the shapes of the paper's experiments:
+    256x256x24 with an 11x11x21 rotated Gaussian per depth (Section 3.2) and
+    155x154x79 with 5x5x11 (Section 3.3), noise 0.04, synthetic phantoms standing
+    in for FlyBrain and Aneurysm.  Iterations/s (L2 flushed before every step),
+    the dense kernels' FP32 FMA roofline, and, on the second, sweeps and time to
+    the paper's stopping rule ||x^{k+1} - x^k|| <= 1e-6 ||x^k|| in the plain and
+    8-slab forms, with the restored SNR."""
+    from paper_2002_02328_gb300 import binding, synth
+    peak = fp32_fma_peak(sm_mhz)
+    out = {"fp32_fma_peak_tflops": peak, "peak_kind": f"derived: 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+    cases = [("rotated_256x256x24_psf11x11x21", synth.workload_rotated_256x256x24(seed=0), (11, 11, 21)),
+             ("rotated_155x154x79_psf5x5x11", synth.workload_rotated_155x154x79(seed=0), (5, 5, 11))]
+    for name, prob, psf_shape in cases:
+        rec = {"voxels": prob.n}
+        with binding.Solver.from_problem(prob, slabs=None) as s:
+            for _ in range(3):
+                flush.fill_(1.0)
+                s.iterate_async(1)
+            ms = time_steps(s, steps, flush, stream)
+            prof = s.profile_iteration()
+        dense_ms = prof["dense"][0]
+        fma = dense_taps(prob.shape, psf_shape)
+        rec.update({"iterations_per_s": 1e3 * steps / ms, "ms_per_iteration": ms / steps,
+                    "kernel_ms_per_iteration": {k: v[0] for k, v in prof.items()},
+                    "roofline_dense": {"bound": "alu", "kernel": "k_dense", "achieved": 2 * fma / (dense_ms * 1e-3) / 1e12,
+                                       "peak": peak, "unit": "TFLOP/s",
+                                       "frac": 2 * fma / (dense_ms * 1e-3) / 1e12 / peak,
+                                       "fma_per_iteration": fma, "launches": prof["dense"][1]}})
+        if name.startswith("rotated_155"):
+            nz = prob.shape[0]
+            bounds = [round(nz * k / 8) for k in range(9)]
+            for form, slabs in (("plain", None), ("slabs8", bounds)):
+                with binding.Solver.from_problem(prob, slabs=slabs) as s:
+                    s.set_stopping(1e-6)
+                    s.iterate(2, trace=False)             # graph and kernels warm
+                    s.set_x(__import__("torch").from_numpy(prob.y).cuda())
+                    t0 = time.perf_counter()
+                    k, done = -1, 0
+                    while k < 0 and done < 5000:          # chunks of 25 sweeps, then read the stop flag
+                        s.iterate(25, trace=False)
+                        done += 25
+                        k = s.stopped()
+                    dt = time.perf_counter() - t0
+                    x = s.get_x().cpu().numpy()
+                rec[f"to_paper_stopping_rule_{form}"] = {"sweeps": int(k), "seconds": dt,
+                                                         "snr_db": snr_db(x, prob.x_true),
+                                                         "snr_db_observation": snr_db(prob.y, prob.x_true)}
         out[name] = rec
     return out
 
@@ -851,6 +934,7 @@ def ours(args):
                                                    "block": {"iterations": k_bn, "seconds": t_bn},
                                                    "plain_fp32": {"iterations": k_pn, "seconds": t_pn}}}
         extra["ablation"] = ablation_extra(prob, fstar, stream, flush, max(10, args.steps // 2))
+        extra["dense_psf"] = dense_extra(stream, flush, 10, float(peaks.get("sm_max_mhz", 2070.0)))
         extra["batched"] = batch_extra(min(args.fstar_iters, 3000), stream)
         extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
         if not args.no_warm_start:

@@ -326,7 +326,8 @@ enum {
     BD3MG_K_GRADIENT = 2,    /* g = H^T r + box + penalty gradient */
     BD3MG_K_CURVATURE = 3,   /* H g_S, weights, inner products, 2x2 solve */
     BD3MG_K_UPDATE = 4,      /* x_S += D u, d_S = D u; H d_S and r on the slab's zone */
-    BD3MG_K_CLASSES = 5
+    BD3MG_K_DENSE = 5,       /* dense-PSF convolutions (H^T r and H g_S of the dense path) */
+    BD3MG_K_CLASSES = 6
 };
 
 /* Run ONE iteration without the CUDA graph, with CUDA events recorded on the

@@ -411,12 +411,12 @@ class Solver:
         self._c(self._lib.bd3mg_slab_colours(self._ctx, col.ctypes.data, ctypes.byref(nc)))
         return col, nc.value
 
-    KERNEL_CLASSES = ("objective", "residual", "gradient", "curvature", "update")
+    KERNEL_CLASSES = ("objective", "residual", "gradient", "curvature", "update", "dense")
 
     def profile_iteration(self):
         """One iteration with CUDA events around every launch: {class: (ms, launches)}."""
-        ms = np.zeros(5)
-        cnt = np.zeros(5, np.int32)
+        ms = np.zeros(len(Solver.KERNEL_CLASSES))
+        cnt = np.zeros(len(Solver.KERNEL_CLASSES), np.int32)
         self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES)}
 
@@ -562,8 +562,8 @@ class BatchSolver:
         self._c(self._lib.bd3mg_load(self._ctx, os.fsencode(path)))
 
     def profile_iteration(self):
-        ms = np.zeros(5)
-        cnt = np.zeros(5, np.int32)
+        ms = np.zeros(len(Solver.KERNEL_CLASSES))
+        cnt = np.zeros(len(Solver.KERNEL_CLASSES), np.int32)
         self._c(self._lib.bd3mg_profile_iteration(self._ctx, ms.ctypes.data, cnt.ctypes.data))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(Solver.KERNEL_CLASSES)}
 

@@ -451,7 +451,7 @@ bd3mg_status run_dense(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int src, i
     if (L.nitems == 0) return BD3MG_OK;
     DenseArgs a{vols ? vols : c->vols, c->segs, c->items + L.item_off, L.nitems, src, dst, sub_y ? 1 : 0,
                 mask ? 1 : 0, iter ? 1 : 0, c->run};
-    bd3mg_status st = prof_mark(c, s, adj ? BD3MG_K_GRADIENT : (dst == DD_HG ? BD3MG_K_CURVATURE : BD3MG_K_RESIDUAL));
+    bd3mg_status st = prof_mark(c, s, iter ? BD3MG_K_DENSE : BD3MG_K_RESIDUAL);
     if (st) return st;
     launch_dense(a, c->dense_R, adj, s);
     return check_launch(c);
