@@ -30,7 +30,8 @@ def test_plain_iteration_moves_80_bytes_per_voxel():
     p = _prob((128, 512, 512))
     b = bench.algorithmic_bytes(p, None, 3)
     per_voxel = {k: v / p.n for k, v in b.items()}
-    assert per_voxel == {"objective": 8.0, "residual": 0.0, "gradient": 12.0, "curvature": 20.0, "update": 40.0}
+    assert per_voxel == {"objective": 8.0, "residual": 0.0, "gradient": 12.0, "curvature": 20.0, "update": 40.0,
+                         "dense": 0.0}
     assert sum(per_voxel.values()) == 80.0
     bf = bench.algorithmic_bytes(p, None, 3, g_bytes=2)
     assert bf["gradient"] / p.n == 10.0 and bf["curvature"] / p.n == 18.0 and bf["update"] / p.n == 38.0
@@ -42,7 +43,8 @@ def test_fused_iteration_moves_64_bytes_per_voxel():
     p = _prob((128, 512, 512))
     b = bench.algorithmic_bytes(p, None, 4, fused=True)
     per_voxel = {k: v / p.n for k, v in b.items()}
-    assert per_voxel == {"objective": 0.0, "residual": 0.0, "gradient": 44.0, "curvature": 20.0, "update": 0.0}
+    assert per_voxel == {"objective": 0.0, "residual": 0.0, "gradient": 44.0, "curvature": 20.0, "update": 0.0,
+                         "dense": 0.0}
     bf = bench.algorithmic_bytes(p, None, 4, g_bytes=2, fused=True)
     assert bf["gradient"] / p.n == 40.0 and bf["curvature"] / p.n == 18.0
 
@@ -73,3 +75,21 @@ def test_snr_db():
     ref = np.random.default_rng(0).uniform(0.5, 1.5, size=(4, 5, 6))
     assert abs(bench.snr_db(0.9 * ref, ref) - 20.0) < 1e-12      # ||ref||^2 / ||0.1 ref||^2 = 100
     assert abs(bench.snr_db(np.zeros_like(ref), ref)) < 1e-12
+
+
+def test_dense_tap_count():
+    """Valid taps of one dense-PSF iteration, by brute force on a tiny shape."""
+    shape, psf = (5, 4, 6), (3, 3, 5)
+    nz, ny, nx = shape
+    px, py, pz = psf
+
+    def valid(n, p, lo, hi, outs):
+        r = (p - 1) // 2
+        return sum(1 for o in outs for a in range(-r, r + 1) if lo <= o - a < hi)
+    xy = valid(nx, px, 0, nx, range(nx)) * valid(ny, py, 0, ny, range(ny))
+    want = xy * valid(nz, pz, 0, nz, range(nz))
+    bounds = [0, 2, 5]
+    for z0, z1 in zip(bounds[:-1], bounds[1:]):
+        want += xy * valid(nz, pz, z0, z1, range(max(0, z0 - 2), min(nz, z1 + 2)))
+    assert bench.dense_taps(shape, psf, bounds) == want
+    assert bench.fp32_fma_peak(2070.0) == 152 * 128 * 2 * 2070e6 / 1e12
