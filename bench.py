@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=1)
     ap.add_argument("--ws-train-seconds", type=float, default=60.0, help="warm start: training time budget")
     ap.add_argument("--no-warm-start", action="store_true")
-    ap.add_argument("--profile-case", choices=["plain512", "unet-train"], default=None,
+    ap.add_argument("--profile-case", choices=["plain512", "unet-train", "dense256"], default=None,
                     help="run a small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
@@ -588,7 +588,7 @@ def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
     from paper_2002_02328_gb300 import binding, synth
     prob = synth.workload_mixed(seed=0)
     rates, profs = {}, {}
-    for name, sep in (("fused", 0), ("separate", 1)):
+    for name, sep in (("fused", 2), ("separate", 1)):
         with binding.Solver.from_problem(prob, slabs=None, separate_update=sep) as s:
             for _ in range(3):
                 flush.fill_(1.0)
@@ -973,10 +973,23 @@ def profile_case(name):
     """Small fixed workloads for ncu captures (no timing contract).
     plain512: plain FP32 context on a 512x512x128 volume (uniform random y, PSF 9x9x7 with the
       0.5 -> 3.0 ramp), 3 iterations, 20 more, then one per-launch profiled iteration.
-    unet-train: the U-Net (16/32/64/128) on 8 crops of 128x128x48, 3 training steps of batch 4."""
+    unet-train: the U-Net (16/32/64/128) on 8 crops of 128x128x48, 3 training steps of batch 4.
+    dense256: plain FP32 context on the 256x256x24 volume with the 11x11x21 rotated Gaussian
+      PSF (dense path), 3 iterations, 10 more, then one per-launch profiled iteration."""
     import torch
     from paper_2002_02328_gb300 import binding, synth
     torch.cuda.set_device(0)
+    if name == "dense256":
+        prob = synth.workload_rotated_256x256x24(seed=0)
+        with binding.Solver.from_problem(prob, slabs=None) as s:
+            s.iterate(3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.iterate(10)
+            torch.cuda.synchronize()
+            print("iterations/s", 10 / (time.perf_counter() - t0))
+            print(s.profile_iteration())
+        return 0
     if name == "plain512":
         shape = (128, 512, 512)
         fx, fy, fz = synth.gaussian_factors(shape[0], 9, 9, 7, 0.5, 3.0, 1.0)

@@ -144,6 +144,9 @@ enum { BD3MG_SCHEDULE_COLOURED = 0, BD3MG_SCHEDULE_JACOBI = 1 };
  * allocation-free objective takes separable PSFs only. */
 enum { BD3MG_PSF_AUTO = 0, BD3MG_PSF_DENSE = 1 };
 
+/* How an iteration without slabs applies its update (bd3mg_params.separate_update). */
+enum { BD3MG_UPDATE_AUTO = 0, BD3MG_UPDATE_SEPARATE = 1, BD3MG_UPDATE_FUSED = 2 };
+
 typedef struct {
     int nx, ny, nz;           /* volume extents, each >= 1 */
     int px, py, pz;           /* PSF extents, odd, >= 1 */
@@ -166,10 +169,13 @@ typedef struct {
     int refresh_every;        /* >= 0: iterations between exact recomputations of r and H d_S; 0 -> 256 */
     int barrier_timeout_ms;   /* 0..600000: limit of every bounded device wait (TMA slice copies);
                                  0 -> 2000.  A wait that runs out makes the call return BD3MG_ETIMEOUT */
-    int separate_update;      /* 0 (default): a context whose volumes are not split into slabs applies
-                                 each iteration's update inside the next gradient pass (two passes
-                                 per iteration, see bd3mg_create); 1: separate objective and update
-                                 passes, as the slab form always runs.  Taken from p[0] of a batch */
+    int separate_update;      /* BD3MG_UPDATE_AUTO (0, default), BD3MG_UPDATE_SEPARATE (1) or
+                                 BD3MG_UPDATE_FUSED (2); taken from p[0] of a batch.  FUSED: a
+                                 context whose volumes are not split into slabs (separable PSF)
+                                 applies each iteration's update inside the next gradient pass (two
+                                 passes per iteration, see bd3mg_create); SEPARATE: objective,
+                                 gradient, curvature and update passes, as the slab form always
+                                 runs; AUTO: FUSED from 2^24 voxels in the context, else SEPARATE */
     int metric;               /* BD3MG_METRIC_MAJORANT (default) or BD3MG_METRIC_LIPSCHITZ */
     double lipschitz;         /* L of BD3MG_METRIC_LIPSCHITZ (> 0), or 0: the library's bound */
     int direction;            /* BD3MG_DIR_MEMORY_GRADIENT (default), BD3MG_DIR_GRADIENT, BD3MG_DIR_CONJUGATE */
@@ -197,7 +203,7 @@ void bd3mg_params_default(bd3mg_params *p);
  * iteration after creation or bd3mg_set_x, and every refresh_every (256)
  * iterations; bd3mg_load restores them with the refresh schedule.  Each
  * sweep's objective takes its data term from the carried r.
- * Without slabs (and separate_update = 0) an iteration is two kernel passes:
+ * Without slabs, in the fused form (separate_update, below) an iteration is two kernel passes:
  * the gradient pass first applies the previous iteration's update (x, d, r
  * and H d) as it reads them, forms g and the objective of the new iterate,
  * and writes the new state into a second buffer set; the curvature pass then

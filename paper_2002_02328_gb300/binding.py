@@ -30,6 +30,7 @@ METRIC_MAJORANT, METRIC_LIPSCHITZ = 0, 1
 DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2
 SCHEDULE_COLOURED, SCHEDULE_JACOBI = 0, 1
 PSF_AUTO, PSF_DENSE = 0, 1
+UPDATE_AUTO, UPDATE_SEPARATE, UPDATE_FUSED = 0, 1, 2
 FAULT_NONE, FAULT_SKIP_COPY = 0, 1
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).

@@ -105,6 +105,7 @@ struct bd3mg_ctx {
     bool dense = false;             // dense PSF path (direct convolutions, identity-factor tile kernels)
     int dense_R = 1;                // xy radius of the dense kernels' padded taps
     std::vector<Launch> L_dzone;    // dense path: per colour, 32-row tiles over the slabs' zones
+    std::vector<Launch> L_dht;      // dense path: per colour, 32-row tiles over the slabs (H^T r)
     bool pending = false;           // some graph launch may have left an update or set 1 state behind
     float *zone_hg1 = nullptr, *zone_hd1 = nullptr;
     int *flush_list = nullptr;      // every slab segment (one per volume), for k_flush
@@ -157,6 +158,9 @@ struct bd3mg_ctx {
 };
 
 namespace {
+
+// Smallest context (total voxels) for which BD3MG_UPDATE_AUTO fuses the update.
+constexpr long long kFusedMinVoxels = 1LL << 24;
 
 bd3mg_status fail(bd3mg_ctx *c, bd3mg_status s, const char *fmt, ...) {
     char buf[512];
@@ -290,6 +294,35 @@ int choose_zc(const bd3mg_ctx *c, const std::vector<std::array<int, 3>> &ranges 
 }
 
 enum SlotMode { SLOTS_NONE, SLOTS_PER_VOLUME, SLOTS_PER_SEGMENT };
+
+// z-chunk of a dense-PSF launch: its output slices are independent and cost the
+// same, so minimise (waves of resident CTAs) x (longest chunk); ties to longer
+// chunks.  Resident CTAs: four per SM (the dense kernels' launch bound).
+template <typename F>
+int dense_zc(const bd3mg_ctx *c, const std::vector<int> &segs, F range) {
+    const long long slots = (long long)c->sms * 4;
+    long long best_cost = -1;
+    int best = 1;
+    for (int zc = 1; zc <= ZC_MAX; ++zc) {
+        long long items = 0;
+        int longest = 0;
+        for (int s : segs) {
+            int lo, hi;
+            range(s, &lo, &hi);
+            const int len = hi - lo;
+            if (len <= 0) continue;
+            const int nch = (len + zc - 1) / zc;
+            items += (long long)nch * ntiles_of(c->V[c->segs_h[s].vol], TY_A);
+            longest = std::max(longest, (len + nch - 1) / nch);
+        }
+        const long long cost = ((items + slots - 1) / slots) * longest;
+        if (best_cost < 0 || cost <= best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
+}
 
 // One launch over the given segments, each with output range range(seg).
 // Segments must be grouped by volume when slots are per volume.
@@ -518,7 +551,7 @@ bd3mg_status enqueue_iteration(bd3mg_ctx *c, cudaStream_t s) {
     for (int col = 0; col < c->ncolours; ++col) {
         if (c->dense) {
             // q = H^T r on the colour's slabs, then the tile gradient pass adds the penalty terms
-            if ((st = run_dense(c, s, c->L_grad[col], DS_R, DD_Q, true, false, false, true))) return st;
+            if ((st = run_dense(c, s, c->L_dht[col], DS_R, DD_Q, true, false, false, true))) return st;
             if ((st = run_gradient(c, s, c->L_grad[col], M_ITER | M_QSRC))) return st;
             // H g_S (g masked to the slab) over each slab's zone, read by the curvature pass
             if ((st = run_dense(c, s, c->L_dzone[col], DS_G, DD_HG, false, false, true, true))) return st;
@@ -779,6 +812,7 @@ void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
     c->L_grad.clear();
     c->L_curv.clear();
     c->L_dzone.clear();
+    c->L_dht.clear();
     if (c->colour_zc.empty()) c->colour_zc.assign(2 * (size_t)c->ncolours, 0);
     for (int col = 0; col < c->ncolours; ++col) {
         std::vector<int> segs, gsegs;
@@ -798,9 +832,16 @@ void build_colour_launches(bd3mg_ctx *c, const std::vector<char> &active) {
             *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_PER_SEGMENT, 2, zc + 1));
         for (int s : segs) c->seg_lists_h.push_back(s);
         c->seg_list_off.push_back((int)c->seg_lists_h.size());
-        if (c->dense)
-            c->L_dzone.push_back(make_launch(c, segs, [&](int s, int *lo, int *hi) {
-                *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; }, SLOTS_NONE, 1));
+        if (c->dense) {
+            // every output slice of a dense item costs the same and needs no z halo:
+            // short chunks that fill the resident slots
+            auto slab = [&](int s, int *lo, int *hi) { *lo = c->segs_h[s].z0; *hi = c->segs_h[s].z1; };
+            auto zone = [&](int s, int *lo, int *hi) { *lo = c->segs_h[s].hz0; *hi = c->segs_h[s].hz1; };
+            int zd = dense_zc(c, segs, slab);
+            c->L_dht.push_back(make_launch(c, segs, slab, SLOTS_NONE, 1, &zd));
+            zd = dense_zc(c, segs, zone);
+            c->L_dzone.push_back(make_launch(c, segs, zone, SLOTS_NONE, 1, &zd));
+        }
     }
     c->plan_active = active;
 }
@@ -829,6 +870,8 @@ bool work_lists_fit(const bd3mg_ctx *c) {
     for (const Launch &L : c->L_curv)
         if (L.nitems > c->items_per_launch_cap) return false;
     for (const Launch &L : c->L_dzone)
+        if (L.nitems > c->items_per_launch_cap) return false;
+    for (const Launch &L : c->L_dht)
         if (L.nitems > c->items_per_launch_cap) return false;
     return true;
 }
@@ -917,8 +960,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
     if (pp[0].refresh_every < 0) return fail(c, BD3MG_EINVAL, "refresh_every must be >= 0 (0: every 256 iterations)");
-    if (pp[0].separate_update != 0 && pp[0].separate_update != 1)
-        return fail(c, BD3MG_EINVAL, "separate_update must be 0 or 1");
+    if (pp[0].separate_update < BD3MG_UPDATE_AUTO || pp[0].separate_update > BD3MG_UPDATE_FUSED)
+        return fail(c, BD3MG_EINVAL, "separate_update must be BD3MG_UPDATE_AUTO, _SEPARATE or _FUSED");
     if (pp[0].barrier_timeout_ms < 0 || pp[0].barrier_timeout_ms > 600000)
         return fail(c, BD3MG_EINVAL, "barrier_timeout_ms must be in [0, 600000] (0: 2000)");
     c->refresh_every = pp[0].refresh_every > 0 ? pp[0].refresh_every : 256;
@@ -1009,7 +1052,18 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->nslab_segs = (int)c->segs_h.size();
     // without slabs, each update is applied inside the next gradient pass
-    c->lazy = !c->any_slabs && pp[0].separate_update == 0 && !c->dense;
+    {
+        // without slabs the update can ride on the next gradient pass; measured on
+        // GB300 this pays from a few tens of millions of voxels (512x512x128: 0.81
+        // against 0.87 ms per iteration), while below that the separate form, whose
+        // objective pass runs beside the gradient pass, is faster (256x256x64: 0.151
+        // against 0.166 ms)
+        long long vox = 0;
+        for (int v = 0; v < nvol; ++v) vox += (long long)pp[v].nx * pp[v].ny * pp[v].nz;
+        const bool can = !c->any_slabs && !c->dense;
+        c->lazy = can && (pp[0].separate_update == BD3MG_UPDATE_FUSED ||
+                          (pp[0].separate_update == BD3MG_UPDATE_AUTO && vox >= kFusedMinVoxels));
+    }
     for (int v = 0; v < nvol; ++v)
         c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size(), 0, 0, nullptr, nullptr});
 

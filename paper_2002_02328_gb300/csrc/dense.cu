@@ -11,9 +11,11 @@
 // xy halo (zero outside the volume, or outside the segment's slab when the
 // input is masked to it) and the tap plane of that (output, input) depth pair
 // are staged in shared memory; the next pair is fetched into registers while
-// the current one is used.  Each thread owns four adjacent outputs of a row and
-// sweeps the tap rows: one row window of 4 + 2 R staged values (float4 loads)
-// and one tap row serve 4 (2R + 1) fused multiply-adds.  The kernel is bound
+// the current one is used.  Each of 128 threads owns a 2 x 4 block of outputs
+// and walks the 2R + 2 staged rows they read: one row window of 4 + 2R staged
+// values (float4 loads) serves both output rows, with the tap row of each (the
+// second row's is the first row's of the step before, kept in registers), 8 (2R
+// + 1) fused multiply-adds per window.  The kernel is bound
 // by FP32 FMA throughput (2541 taps per voxel for the paper's 11 x 11 x 21
 // PSF), not by memory.
 //
@@ -33,6 +35,8 @@ constexpr int DT = 32;             // output tile (x and y)
 constexpr int DXO = 8;             // staged column of tile column 0 (>= R, multiple of 4)
 constexpr int DSW = DT + 2 * DXO;  // staged row width (48 floats)
 
+constexpr int DNT = 128;           // threads of a dense CTA: 8 x 16, each 2 rows x 4 columns of outputs
+
 template <int R>
 struct DenseGeo {
     static constexpr int K = 2 * R + 1;
@@ -40,17 +44,17 @@ struct DenseGeo {
     static constexpr int TILE = SH * DSW;           // floats per staged slice
     static constexpr int KP = (K + 3) & ~3;         // tap row padded to a float4 multiple
     static constexpr int COEF = K * KP;             // floats per staged tap plane
-    static constexpr int PER = (TILE + NT - 1) / NT;    // staged values per thread
-    static constexpr int CPER = (COEF + NT - 1) / NT;
-    static constexpr int NW = (4 + DXO + R + 3) / 4;    // float4 of a row window
+    static constexpr int PER = (TILE + DNT - 1) / DNT;    // staged values per thread
+    static constexpr int CPER = (COEF + DNT - 1) / DNT;
+    static constexpr int NW = (4 + DXO + R + 3) / 4;      // float4 of a row window
 };
 
 }  // namespace
 
 template <int R, bool ADJ>
-__global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
+__global__ void __launch_bounds__(DNT, 4) k_dense(DenseArgs a) {
     using DG = DenseGeo<R>;
-    constexpr int K = DG::K, SH = DG::SH, TILE = DG::TILE, KP = DG::KP, COEF = DG::COEF;
+    constexpr int K = DG::K, TILE = DG::TILE, KP = DG::KP, COEF = DG::COEF;
     __shared__ __align__(16) float st[2][TILE];
     __shared__ __align__(16) float co[2][COEF];
 
@@ -72,7 +76,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
     const float *yv = a.sub_y ? V.y : nullptr;
     const int mlo = a.mask ? max(0, sg.z0) : 0, mhi = a.mask ? min(nz, sg.z1) : nz;
     const int tid = threadIdx.x;
-    const int lx = 4 * (tid & 7), ly = tid >> 3;            // outputs (lx .. lx+3, ly) of the tile
+    const int lx = 4 * (tid & 7), ly = 2 * (tid >> 3);     // outputs (lx .. lx+3, ly .. ly+1) of the tile
     const int gx = it.tx0 + lx, gy = it.ty0 + ly;
 
     // the (output, input) depth pairs of the item, in order: input depth of pair
@@ -90,7 +94,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
         const float *sp = src + (long long)zi * plane;
 #pragma unroll
         for (int j = 0; j < DG::PER; ++j) {
-            const int e = tid + j * NT;
+            const int e = tid + j * DNT;
             float v = 0.f;
             if (e < TILE) {
                 const int row = e / DSW, col = e - row * DSW;
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
         const float *hp = V.h3 + ((long long)zc * kz + c + rz) * K * K;
 #pragma unroll
         for (int j = 0; j < DG::CPER; ++j) {
-            const int e = tid + j * NT;
+            const int e = tid + j * DNT;
             float v = 0.f;
             if (e < COEF) {
                 const int b = e / KP, aa = e - b * KP;
@@ -116,10 +120,10 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
     auto store = [&](int buf) {
 #pragma unroll
         for (int j = 0; j < DG::PER; ++j)
-            if (tid + j * NT < TILE) st[buf][tid + j * NT] = pv[j];
+            if (tid + j * DNT < TILE) st[buf][tid + j * DNT] = pv[j];
 #pragma unroll
         for (int j = 0; j < DG::CPER; ++j)
-            if (tid + j * NT < COEF) co[buf][tid + j * NT] = pc[j];
+            if (tid + j * DNT < COEF) co[buf][tid + j * DNT] = pc[j];
     };
     // next valid pair after (zo, c)
     auto advance = [&](int &zo, int &c) {
@@ -139,19 +143,23 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
         store(0);
     }
     __syncthreads();
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
     int zcur = it.zo0;                  // output slice being accumulated
-    // outputs of slices without a single valid pair are zero: write them as the walk passes them
+    // outputs of slices without a single valid pair are zero: written as the walk passes them
     auto emit = [&](int z) {
-        if (gy < ny && gx < nx) {
-            float *op = dst + (z - dz0) * plane + (long long)gy * pitch + gx;
-            const float *yp = yv ? yv + (long long)z * plane + (long long)gy * pitch + gx : nullptr;
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (gx + i < nx) op[i] = yp ? acc[i] - yp[i] : acc[i];
+        for (int k = 0; k < 2; ++k) {
+            if (gy + k < ny && gx < nx) {
+                const long long o = (long long)(gy + k) * pitch + gx;
+                float *op = dst + (z - dz0) * plane + o;
+                const float *yp = yv ? yv + (long long)z * plane + o : nullptr;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (gx + i < nx) op[i] = yp ? acc[k][i] - yp[i] : acc[k][i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[k][i] = 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] = 0.f;
     };
     while (zo < it.zo1) {
         while (zcur < zo) emit(zcur++);
@@ -159,13 +167,14 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
         advance(zn, cn);
         if (zn < it.zo1) fetch(zn, cn);                 // the next pair, in flight during the sums
         const float *sb = st[buf], *cb = co[buf];
+        // Staged rows ly .. ly + 2R + 1 in turn: staged row ly + j feeds output row 0
+        // with tap row b0 (forward 2R - j, adjoint j) and output row 1 with the tap
+        // row of the previous j, kept in registers (forward b0 + 1, adjoint b0 - 1).
+        float hprev[KP];
 #pragma unroll
-        for (int b = 0; b < K; ++b) {
-            // tap row b (offset b - R): forward reads input row y - (b - R), staged row
-            // ly + 2R - b; adjoint reads y + (b - R), staged row ly + b
-            const int sr = ADJ ? ly + b : ly + 2 * R - b;
+        for (int j = 0; j <= 2 * R + 1; ++j) {
             float w[4 * DG::NW];
-            const float4 *wp = reinterpret_cast<const float4 *>(sb + sr * DSW + lx);
+            const float4 *wp = reinterpret_cast<const float4 *>(sb + (ly + j) * DSW + lx);
 #pragma unroll
             for (int v = 0; v < DG::NW; ++v) {
                 const float4 q = wp[v];
@@ -174,22 +183,32 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
                 w[4 * v + 2] = q.z;
                 w[4 * v + 3] = q.w;
             }
-            float h[KP];
-            const float4 *hp4 = reinterpret_cast<const float4 *>(cb + b * KP);
+            float hcur[KP];
+            if (j <= 2 * R) {
+                const int b0 = ADJ ? j : 2 * R - j;
+                const float4 *hp4 = reinterpret_cast<const float4 *>(cb + b0 * KP);
 #pragma unroll
-            for (int v = 0; v < KP / 4; ++v) {
-                const float4 q = hp4[v];
-                h[4 * v] = q.x;
-                h[4 * v + 1] = q.y;
-                h[4 * v + 2] = q.z;
-                h[4 * v + 3] = q.w;
+                for (int v = 0; v < KP / 4; ++v) {
+                    const float4 q = hp4[v];
+                    hcur[4 * v] = q.x;
+                    hcur[4 * v + 1] = q.y;
+                    hcur[4 * v + 2] = q.z;
+                    hcur[4 * v + 3] = q.w;
+                }
             }
 #pragma unroll
             for (int aa = 0; aa < K; ++aa) {
                 // tap offset a = aa - R: forward reads column x - a, adjoint x + a
                 const int off = ADJ ? DXO + aa - R : DXO - (aa - R);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc[i] = fmaf(h[aa], w[i + off], acc[i]);
+                for (int i = 0; i < 4; ++i) {
+                    if (j <= 2 * R) acc[0][i] = fmaf(hcur[aa], w[i + off], acc[0][i]);
+                    if (j >= 1) acc[1][i] = fmaf(hprev[aa], w[i + off], acc[1][i]);
+                }
+            }
+            if (j <= 2 * R) {
+#pragma unroll
+                for (int v = 0; v < KP; ++v) hprev[v] = hcur[v];
             }
         }
         // the other buffer was last read before the previous barrier
@@ -204,8 +223,8 @@ __global__ void __launch_bounds__(NT, 2) k_dense(DenseArgs a) {
 
 template <int R>
 static void launch_dense_r(const DenseArgs &a, bool adj, cudaStream_t s) {
-    if (adj) k_dense<R, true><<<a.nitems, NT, 0, s>>>(a);
-    else k_dense<R, false><<<a.nitems, NT, 0, s>>>(a);
+    if (adj) k_dense<R, true><<<a.nitems, DNT, 0, s>>>(a);
+    else k_dense<R, false><<<a.nitems, DNT, 0, s>>>(a);
 }
 
 void launch_dense(const DenseArgs &a, int R, bool adj, cudaStream_t s) {

@@ -5,10 +5,10 @@ previous iteration's update (x, d, r, H d) as it reads the state and writes
 the new state into a second buffer set, then the curvature pass builds and
 solves the 2x2 system.  The update arithmetic is that of the separate update
 pass, so the iterates must be the same bits as a context created with
-separate_update = 1; only the objective's summation order differs (both sum
+separate_update = 1 (the fused form is forced with separate_update = 2;
+contexts below 2^24 voxels do not take it by default); only the objective's summation order differs (both sum
 FP32 per-thread partials of up to a few hundred terms and FP64 across threads:
-trace within 1e-6 relative).  The oracle parity of the plain form is covered by the
-other test files, which run this form by default.
+trace within 1e-6 relative).
 """
 import dataclasses
 
@@ -20,11 +20,14 @@ from paper_2002_02328_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
+FUSED = 2          # BD3MG_UPDATE_FUSED (the automatic choice fuses only large contexts)
+
+
 def _pair(cuda_lib, p, n, **kw):
     out = []
-    for sep in (0, 1):
+    for sep in (FUSED, 1):
         with cuda_lib.Solver.from_problem(p, separate_update=sep, **kw) as s:
-            assert s.launches_per_iteration() == (2 if sep == 0 else 4)
+            assert s.launches_per_iteration() == (2 if sep == FUSED else 4)
             tr = s.iterate(n)
             out.append((tr, s.get_x().cpu().numpy(), s.get_d().cpu().numpy()))
     return out
@@ -56,7 +59,8 @@ def test_pending_update_is_applied_before_reads(cuda_lib):
     """iterate_async leaves the last update pending; every reader applies it first."""
     import torch
     p = synth.tiny_problem(shape=(11, 30, 44), psf_shape=(5, 5, 5), seed=23, n_ellipsoids=6)
-    with cuda_lib.Solver.from_problem(p) as a, cuda_lib.Solver.from_problem(p) as b:
+    with cuda_lib.Solver.from_problem(p, separate_update=FUSED) as a, \
+            cuda_lib.Solver.from_problem(p, separate_update=FUSED) as b:
         a.iterate(6)
         xa, fa = a.get_x().cpu().numpy(), a.objective()
         b.iterate_async(3)
@@ -93,7 +97,7 @@ def test_fused_batch_with_stopping_equals_separate(cuda_lib):
     stop_at = [8, 13, 21]
     target = np.array([0.5 * (t0[v, k - 1] + t0[v, k]) for v, k in enumerate(stop_at)])
     res = []
-    for sep in (0, 1):
+    for sep in (FUSED, 1):
         with cuda_lib.BatchSolver(probs, separate_update=sep, zchunk=8) as b:
             b.set_stopping(0.0, target)
             tr = b.iterate(30)
@@ -108,13 +112,13 @@ def test_fused_batch_with_stopping_equals_separate(cuda_lib):
 def test_fused_checkpoint_resume(cuda_lib, tmp_path):
     p = synth.tiny_problem(shape=(9, 28, 36), psf_shape=(5, 5, 5), seed=24, n_ellipsoids=6)
     path = str(tmp_path / "ck.bin")
-    with cuda_lib.Solver.from_problem(p) as a:
+    with cuda_lib.Solver.from_problem(p, separate_update=FUSED) as a:
         ta = a.iterate(12)
         xa = a.get_x().cpu().numpy()
-    with cuda_lib.Solver.from_problem(p) as b:
+    with cuda_lib.Solver.from_problem(p, separate_update=FUSED) as b:
         b.iterate_async(5)                 # pending update at the save
         b.save(path)
-    with cuda_lib.Solver.from_problem(p) as c:
+    with cuda_lib.Solver.from_problem(p, separate_update=FUSED) as c:
         c.load(path)
         tc = c.iterate(7)
         xc = c.get_x().cpu().numpy()

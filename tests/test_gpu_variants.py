@@ -48,7 +48,7 @@ def test_plain_variants_match_oracle(cuda_lib, metric, direction, n):
     op = oracle.OracleProblem.from_synth(p)
     L = oracle.lipschitz_bound(op)
     xr, _, fr = oracle.run_variant(op, p.y, p.y, n, metric=metric, lipschitz=L, direction=direction)
-    for sep in (0, 1):            # fused-update and separate-update iterations
+    for sep in (2, 1):            # fused-update and separate-update iterations
         with cuda_lib.Solver.from_problem(p, metric=metric, lipschitz=L, direction=direction,
                                           separate_update=sep) as s:
             tr = s.iterate(n)
