@@ -416,14 +416,14 @@ def batch_extra(iters, stream):
         return a.elapsed_time(b) / reps / 1e3
 
     # z-chunk from the library's autotuner (timed on this GPU for these volumes)
-    zc, zc_ms = binding.autotune(probs, iters=10)
+    zc, zrows, zc_ms = binding.autotune(probs, iters=10)
     with binding.BatchSolver(probs) as bs:
         bs.iterate_async(3)
         t_default = timed(lambda: bs.iterate_async(1), 20)
-    with binding.BatchSolver(probs, zchunk=zc) as bs:
+    with binding.BatchSolver(probs, zchunk=zc, curv_rows=zrows) as bs:
         bs.iterate_async(3)
         t_batch = timed(lambda: bs.iterate_async(1), 20)
-        with binding.BatchSolver(probs, zchunk=zc) as b2:
+        with binding.BatchSolver(probs, zchunk=zc, curv_rows=zrows) as b2:
             tr = b2.iterate(iters)
     fstar = tr[:, -1]
     settle = float(np.max((tr[:, int(0.9 * iters)] - tr[:, -1]) / np.abs(fstar)))
@@ -439,7 +439,7 @@ def batch_extra(iters, stream):
     # reaches its target drops out of every later launch
     t_stop, k_stop, t_stop_model = None, None, None
     if ok:
-        with binding.BatchSolver(probs, zchunk=zc) as bs:
+        with binding.BatchSolver(probs, zchunk=zc, curv_rows=zrows) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
             # the synchronous call drops stopped volumes from the work lists between chunks
             t_stop = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
@@ -451,7 +451,8 @@ def batch_extra(iters, stream):
             t_stop_model = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,
-            "autotuned_zchunk": zc, "lockstep_iterations_per_s_default_zchunk": 1.0 / t_default,
+            "autotuned_zchunk": zc, "autotuned_curvature_rows": zrows,
+            "lockstep_iterations_per_s_default_zchunk": 1.0 / t_default,
             "sequential_iterations_per_s": 1.0 / sum(t_seq),
             "fstar_iters": iters, "fstar_settle_rel": settle,
             "iters_to_gap": k,

@@ -181,6 +181,9 @@ typedef struct {
     int direction;            /* BD3MG_DIR_MEMORY_GRADIENT (default), BD3MG_DIR_GRADIENT, BD3MG_DIR_CONJUGATE */
     int schedule;             /* BD3MG_SCHEDULE_COLOURED (default) or BD3MG_SCHEDULE_JACOBI (from p[0]) */
     double inflation;         /* >= 1, or 0: 1 (coloured) / the number of slabs (Jacobi) */
+    int curv_rows;            /* output rows of a curvature tile: 0 (default: 16 with an FP32 gradient, 32
+                                 with BF16), 16 or 32 (32 only with BF16); taken from p[0].  The
+                                 autotuner times both shapes with every z-chunk */
     int psf_mode;             /* BD3MG_PSF_AUTO (default): the separable fast path when every depth's PSF
                                  factors and its radii are compiled (xy <= 5, z <= 5), else the dense path;
                                  BD3MG_PSF_DENSE: the dense path always (taken from p[0]) */
@@ -383,20 +386,22 @@ bd3mg_status bd3mg_inject_fault(bd3mg_ctx *ctx, int kind);
 bd3mg_status bd3mg_save(bd3mg_ctx *ctx, const char *path);
 bd3mg_status bd3mg_load(bd3mg_ctx *ctx, const char *path);
 
-/* z-chunk autotuner of the tile kernels.  Times `iters` lockstep iterations
- * (after 2 untimed ones) of contexts built like bd3mg_batch_create(nvol, p, y,
- * NULL, data_on_device, stream, NULL, ...) with zchunk = 0 (the library's cost
- * model) and 4, 6, 8, 12, 16, 24, 32, 48 output slices per work item, and
- * returns the fastest in *zchunk (give it to bd3mg_params.zchunk) and its
- * device time per iteration in *ms_per_iteration (may be NULL).  Candidates
- * that do not fit in device memory are skipped.  cache_path (may be NULL):
- * a JSON-lines file; when it holds an entry for the same shape class (SM
- * count, precision, every volume's extents, PSF extents and slab bounds) that
- * entry is returned without timing (*ms_per_iteration = -1), otherwise the
- * result is appended.  The contexts are created and destroyed on `stream`;
- * the caller's data is only read. */
+/* Autotuner of the tile kernels' work shape.  Times `iters` lockstep
+ * iterations (after 2 untimed ones) of contexts built like
+ * bd3mg_batch_create(nvol, p, y, NULL, data_on_device, stream, NULL, ...) for
+ * every pair of a z-chunk (0 = the library's cost model, and 4, 6, 8, 12, 16,
+ * 24, 32, 48 output slices per work item) and a curvature tile height (16 and
+ * 32 rows with an FP32 gradient, 32 with BF16), and returns the fastest pair in
+ * *zchunk and *curv_rows (give them to bd3mg_params.zchunk and .curv_rows;
+ * curv_rows may be NULL) and its device time per iteration in
+ * *ms_per_iteration (may be NULL).  Candidates that do not fit in device memory
+ * are skipped.  cache_path (may be NULL): a JSON-lines file; when it holds an
+ * entry for the same shape class (SM count, precision, every volume's extents,
+ * PSF extents and slab bounds) that entry is returned without timing
+ * (*ms_per_iteration = -1), otherwise the result is appended.  The contexts are
+ * created and destroyed on `stream`; the caller's data is only read. */
 bd3mg_status bd3mg_autotune(int nvol, const bd3mg_params *p, const float *const *y, int data_on_device, void *stream,
-                            int iters, const char *cache_path, int *zchunk, double *ms_per_iteration);
+                            int iters, const char *cache_path, int *zchunk, int *curv_rows, double *ms_per_iteration);
 
 /* Size of the device array behind bd3mg_objective_noalloc (bytes). */
 #define BD3MG_STATIC_SCRATCH_BYTES (1u << 20)

@@ -62,7 +62,8 @@ class Params(ctypes.Structure):
                 ("refresh_every", ctypes.c_int), ("barrier_timeout_ms", ctypes.c_int),
                 ("separate_update", ctypes.c_int),
                 ("metric", ctypes.c_int), ("lipschitz", ctypes.c_double), ("direction", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double), ("psf_mode", ctypes.c_int)]
+                ("schedule", ctypes.c_int), ("inflation", ctypes.c_double), ("curv_rows", ctypes.c_int),
+                ("psf_mode", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -114,7 +115,8 @@ def load(path: str = LIB_PATH):
             "bd3mg_inject_fault": (ip, [vp, ip]),
             "bd3mg_save": (ip, [vp, ctypes.c_char_p]),
             "bd3mg_load": (ip, [vp, ctypes.c_char_p]),
-            "bd3mg_autotune": (ip, [ip, P, vp, ip, vp, ip, ctypes.c_char_p, ctypes.POINTER(ip), ctypes.POINTER(dp)]),
+            "bd3mg_autotune": (ip, [ip, P, vp, ip, vp, ip, ctypes.c_char_p, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                    ctypes.POINTER(dp)]),
             "bd3mg_error_string": (ctypes.c_char_p, [vp]),
             "bd3mg_lipschitz": (ip, [vp, ctypes.c_void_p]),
             "bd3mg_status_string": (ctypes.c_char_p, [ip]),
@@ -165,7 +167,8 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
                 slabs: Optional[Sequence[int]] = None, precision: int = FP32, pinv_rtol: float = 1e-12,
                 zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                 barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
-                direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0):
+                direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0,
+                curv_rows: int = 0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -185,6 +188,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.metric, p.lipschitz, p.direction = int(metric), float(lipschitz), int(direction)
     p.schedule, p.inflation = int(schedule), float(inflation)
     p.psf_mode = int(psf_mode)
+    p.curv_rows = int(curv_rows)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -276,14 +280,15 @@ class Solver:
                  slabs=None, precision: int = FP32, pinv_rtol: float = 1e-12, zchunk: int = 0, stream=None,
                  use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                  barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
-                 direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0):
+                 direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0,
+                 curv_rows: int = 0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
                                    penalty, kappa, refresh_every, barrier_timeout_ms, separate_update, metric,
-                                   lipschitz, direction, schedule, inflation, psf_mode)
+                                   lipschitz, direction, schedule, inflation, psf_mode, curv_rows)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -447,7 +452,8 @@ class BatchSolver:
     """Many independent volumes iterated in lockstep by one context (plain 3MG each)."""
 
     def __init__(self, problems, x0s=None, device="cuda", zchunk: int = 0, stream=None,
-                 use_torch_allocator: bool = True, precision: int = FP32, separate_update: int = 0):
+                 use_torch_allocator: bool = True, precision: int = FP32, separate_update: int = 0,
+                 curv_rows: int = 0):
         torch = _torch()
         lib = load()
         self.shapes = [tuple(int(s) for s in p.shape) for p in problems]
@@ -459,7 +465,7 @@ class BatchSolver:
         for v, p in enumerate(problems):
             prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precs[v], 1e-12,
                                  zchunk, getattr(p, "penalty", 0), getattr(p, "kappa", 0.0),
-                                 separate_update=separate_update)
+                                 separate_update=separate_update, curv_rows=curv_rows)
             arr[v] = prm
             keep.append(k)
             yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)
@@ -579,7 +585,8 @@ class BatchSolver:
 
 
 def autotune(problems, iters: int = 10, cache_path: Optional[str] = None, precision: int = FP32):
-    """Fastest z-chunk for these volumes (bd3mg_autotune): (zchunk, ms per iteration or -1 if cached)."""
+    """Fastest work shape for these volumes (bd3mg_autotune): (zchunk, curvature tile rows, ms per
+    iteration or -1 if cached)."""
     torch = _torch()
     lib = load()
     n = len(problems)
@@ -592,10 +599,12 @@ def autotune(problems, iters: int = 10, cache_path: Optional[str] = None, precis
         ys.append(torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).cuda())
     yptr = (ctypes.c_void_p * n)(*[_ptr(t) for t in ys])
     z = ctypes.c_int()
+    rows = ctypes.c_int()
     ms = ctypes.c_double()
     s = torch.cuda.current_stream().cuda_stream
     st = lib.bd3mg_autotune(n, arr, yptr, 1, ctypes.c_void_p(int(s)), int(iters),
-                            os.fsencode(cache_path) if cache_path else None, ctypes.byref(z), ctypes.byref(ms))
+                            os.fsencode(cache_path) if cache_path else None, ctypes.byref(z), ctypes.byref(rows),
+                            ctypes.byref(ms))
     if st != 0:
         raise Bd3mgError(st, lib.bd3mg_status_string(st).decode())
-    return int(z.value), float(ms.value)
+    return int(z.value), int(rows.value), float(ms.value)

@@ -143,7 +143,8 @@ struct bd3mg_ctx {
     std::vector<Launch> L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
-    int occ[7] = {1, 1, 1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
+    int occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
+    bool t32 = false;               // FP32 curvature pass with 32-row tiles (curv_rows = 32)
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -207,7 +208,7 @@ int set_xh(const KernelSet *k, int esize = 4) { return (esize == 4 && k->R <= 4)
 
 // Tile height of the curvature kernel for a gradient of g_esize bytes (must
 // match CurvRing<R,RZ,EB>::TY in kernels.cuh).
-int curv_ty(int g_esize) { return g_esize == 2 ? 2 * TY_C : TY_C; }
+int curv_ty(const bd3mg_ctx *c, int g_esize);
 
 // g: FP32 or (g_esize 2) BF16 gradient; d: FP32 memory direction.
 bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const float *x, const float *r,
@@ -218,7 +219,7 @@ bool encode_vol_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v, const f
     bool ok = true;
     if (x) ok = ok && encode_map(&vm->m[TM_X_R], x, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
     if (r) ok = ok && encode_map(&vm->m[TM_R_R], r, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
-    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, g_esize, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(g_esize) + 2 * R);
+    if (g) ok = ok && encode_map(&vm->m[TM_G_R], g, g_esize, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(c, g_esize) + 2 * R);
     if (d) ok = ok && encode_map(&vm->m[TM_D_X], d, 4, p.nx, p.ny, p.nz, v.pitch, bx, TY_A + 2 * R);
     return ok;
 }
@@ -234,19 +235,25 @@ bool encode_lazy_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v) {
     return encode_map(&vm->m[TM_HG_R], sg.hg, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
            encode_map(&vm->m[TM_HD_R], sg.hd, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
            encode_map(&vm->m[TM_R1_R], v.r1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
-           encode_map(&vm->m[TM_G1_R], g1, ge, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(ge) + 2 * R) &&
+           encode_map(&vm->m[TM_G1_R], g1, ge, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(c, ge) + 2 * R) &&
            encode_map(&vm->m[TM_HG1_R], sg.hg1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
            encode_map(&vm->m[TM_HD1_R], sg.hd1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by);
 }
 
 // Kernel kind used for occupancy: BF16-gradient gradient/curvature have their own.
+// Tile height of the curvature kernel for a gradient of g_esize bytes (must
+// match CurvRing<R,RZ,EB,RPT>::TY in kernels.cuh): 32 rows with a BF16
+// gradient or when the context asked for 32-row FP32 tiles, else 16.
+int curv_ty(const bd3mg_ctx *c, int g_esize) { return (g_esize == 2 || c->t32) ? 2 * TY_C : TY_C; }
+
 int occ_kind(const bd3mg_ctx *c, int kind) {
+    if (kind == 2 && !c->bf && c->t32) return 7;
     if (c->lazy && kind == 1) return c->bf ? 6 : 5;
     return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind;
 }
 
 // Tile height of the kernel kind (0 residual, 1 gradient, 2 curvature).
-int tile_y(const bd3mg_ctx *c, int kind) { return kind == 2 ? curv_ty(c->bf ? 2 : 4) : TY_A; }
+int tile_y(const bd3mg_ctx *c, int kind) { return kind == 2 ? curv_ty(c, c->bf ? 2 : 4) : TY_A; }
 
 int ntiles_of(const VolState &v, int ty) { return ((v.p.nx + TX - 1) / TX) * ((v.p.ny + ty - 1) / ty); }
 
@@ -495,7 +502,7 @@ bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     KArgs a = make_args(c, L, (c->lazy ? (M_ITER | M_PAR) : M_ITER) | (c->dense ? M_HG_GIVEN : 0), nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
-    (c->bf ? c->ks->curvature_bf : c->ks->curvature)(a, s);
+    (c->bf ? c->ks->curvature_bf : c->t32 ? c->ks->curvature_t32 : c->ks->curvature)(a, s);
     return check_launch(c);
 }
 
@@ -960,6 +967,11 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     }
     c->pinv_rtol = pp[0].pinv_rtol > 0 ? pp[0].pinv_rtol : 1e-12;
     if (pp[0].refresh_every < 0) return fail(c, BD3MG_EINVAL, "refresh_every must be >= 0 (0: every 256 iterations)");
+    if (pp[0].curv_rows != 0 && pp[0].curv_rows != 16 && pp[0].curv_rows != 32)
+        return fail(c, BD3MG_EINVAL, "curv_rows must be 0, 16 or 32");
+    if (pp[0].curv_rows == 16 && pp[0].precision == BD3MG_BF16_GRADIENT)
+        return fail(c, BD3MG_EINVAL, "a BF16 gradient runs 32-row curvature tiles only");
+    c->t32 = pp[0].curv_rows == 32;
     if (pp[0].separate_update < BD3MG_UPDATE_AUTO || pp[0].separate_update > BD3MG_UPDATE_FUSED)
         return fail(c, BD3MG_EINVAL, "separate_update must be BD3MG_UPDATE_AUTO, _SEPARATE or _FUSED");
     if (pp[0].barrier_timeout_ms < 0 || pp[0].barrier_timeout_ms > 600000)
@@ -1074,7 +1086,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = c->ks->prepare();
         if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e));
-        for (int k = 0; k < 7; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+        for (int k = 0; k < 8; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
     }
 
     // work lists

@@ -21,10 +21,12 @@ struct KernelSet {
     launch_fn residual, gradient, curvature;        // FP32 gradient
     launch_fn gradient_bf, curvature_bf;            // BF16 gradient
     launch_fn gradlazy, gradlazy_bf;                // fused-update gradient pass (FP32 / BF16 gradient)
+    launch_fn curvature_t32;                        // FP32 gradient, 32-row curvature tiles
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
     // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
     // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient), 5 fused-update
-    // gradient, 6 fused-update gradient (BF16 gradient)
+    // gradient, 6 fused-update gradient (BF16 gradient), 7 curvature (FP32
+    // gradient, 32-row tiles)
     int (*occupancy)(int kind);
 };
 

@@ -252,9 +252,9 @@ struct Geo {
 // two with a BF16 gradient (32-row tiles; half the per-step overhead per voxel,
 // three CTAs).  The ring holds KZ + PF slots of g, two slices in flight where
 // that keeps the CTA count, else one.
-template <int R, int RZ, int EB>
+template <int R, int RZ, int EB, int RPT_ = (EB == 2 ? 2 : 1)>
 struct CurvRing {
-    static constexpr int RPT = EB == 2 ? 2 : 1;
+    static constexpr int RPT = RPT_;
     static constexpr int TY = TY_C * RPT;
     using C = Geo<R, RZ, TY, EB>;
     static constexpr size_t bytes(int pf) {
@@ -284,6 +284,8 @@ struct Smem {
     static constexpr size_t curvature = CurvRing<R, RZ, 4>::SMEM;
     // BF16 gradient: g slots hold 2-byte elements (slot sizes are multiples of 128 bytes)
     static constexpr size_t curvature_bf = CurvRing<R, RZ, 2>::SMEM;
+    // FP32 gradient with 32-row tiles (two rows per thread), a shape the autotuner may pick
+    static constexpr size_t curvature_t32 = CurvRing<R, RZ, 4, 2>::SMEM;
 };
 
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -1437,10 +1439,10 @@ __device__ __forceinline__ void pen_quad(float vg, float vd, float kl2, float *a
 // half-quadratic terms are formed between the two barriers of a step, before
 // the convolution's registers are needed; with one, after the y-pass.
 // ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF, int PM>
-__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4>::CTAS) k_curvature(KArgs a) {
+template <int R, int RZ, bool BF, int PM, int RPT_ = (BF ? 2 : 1)>
+__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k_curvature(KArgs a) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
-    using CR = CurvRing<R, RZ, sizeof(T)>;
+    using CR = CurvRing<R, RZ, sizeof(T), RPT_>;
     using G = typename CR::C;
     constexpr int PF = CR::PF;                        // slices in flight ahead of the consumer
     constexpr int RPT = CR::RPT;                      // output rows per thread

@@ -23,6 +23,10 @@ void launch_gradlazy(const KArgs &a, cudaStream_t s) {
     k_gradlazy<R, RZ, BF, PM><<<a.nitems, NT, LazyGeo<R, RZ>::SMEM, s>>>(a);
 }
 template <int R, int RZ, int PM>
+void launch_curvature_t32(const KArgs &a, cudaStream_t s) {
+    k_curvature<R, RZ, false, PM, 2><<<a.nitems, NT, Smem<R, RZ>::curvature_t32, s>>>(a);
+}
+template <int R, int RZ, int PM>
 cudaError_t prepare_set() {
     cudaError_t e = cudaFuncSetAttribute(k_residual<R, RZ, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)Smem<R, RZ>::residual);
@@ -38,6 +42,9 @@ cudaError_t prepare_set() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_curvature<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)Smem<R, RZ>::curvature_bf);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_curvature<R, RZ, false, PM, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)Smem<R, RZ>::curvature_t32);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gradlazy<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)LazyGeo<R, RZ>::SMEM);
@@ -58,6 +65,7 @@ int occupancy_of(int kind) {
         case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, true, PM>, NT, Smem<R, RZ>::curvature_bf); break;
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, false, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, true, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
+        case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM, 2>, NT, Smem<R, RZ>::curvature_t32); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM>, NT, Smem<R, RZ>::curvature); break;
     }
     return e == cudaSuccess ? n : 0;
@@ -69,4 +77,5 @@ int occupancy_of(int kind) {
     {R, RZ, PM, &bd3mg::launch_residual<R, RZ, PM>, &bd3mg::launch_gradient<R, RZ, false, PM>,              \
      &bd3mg::launch_curvature<R, RZ, false, PM>, &bd3mg::launch_gradient<R, RZ, true, PM>,                  \
      &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::launch_gradlazy<R, RZ, false, PM>,                  \
-     &bd3mg::launch_gradlazy<R, RZ, true, PM>, &bd3mg::prepare_set<R, RZ, PM>, &bd3mg::occupancy_of<R, RZ, PM>}
+     &bd3mg::launch_gradlazy<R, RZ, true, PM>, &bd3mg::launch_curvature_t32<R, RZ, PM>,                     \
+     &bd3mg::prepare_set<R, RZ, PM>, &bd3mg::occupancy_of<R, RZ, PM>}

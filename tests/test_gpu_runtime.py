@@ -72,13 +72,28 @@ def test_autotune_returns_a_candidate_and_caches_it(cuda_lib, tmp_path):
     from paper_2002_02328_gb300 import synth
     probs = [_prob(seed=3), synth.tiny_problem(shape=(12, 33, 29), psf_shape=(5, 5, 5), seed=4)]
     cache = str(tmp_path / "tune.jsonl")
-    z, ms = cuda_lib.autotune(probs, iters=3, cache_path=cache)
-    assert z in (0, 4, 6, 8, 12, 16, 24, 32, 48) and ms > 0
+    z, rows, ms = cuda_lib.autotune(probs, iters=3, cache_path=cache)
+    assert z in (0, 4, 6, 8, 12, 16, 24, 32, 48) and rows in (16, 32) and ms > 0
     lines = [json.loads(l) for l in open(cache)]
-    assert len(lines) == 1 and lines[0]["zchunk"] == z and len(lines[0]["candidates"]) >= 2
-    z2, ms2 = cuda_lib.autotune(probs, iters=3, cache_path=cache)
-    assert z2 == z and ms2 == -1.0
-    # the tuned chunk gives the same iterates as the default (the chunking only moves work)
-    with cuda_lib.BatchSolver(probs) as a, cuda_lib.BatchSolver(probs, zchunk=z) as b:
+    assert len(lines) == 1 and lines[0]["zchunk"] == z and lines[0]["curv_rows"] == rows
+    assert len(lines[0]["candidates (chunk/rows)"]) == 18          # 9 chunks x 2 tile shapes
+    z2, rows2, ms2 = cuda_lib.autotune(probs, iters=3, cache_path=cache)
+    assert (z2, rows2, ms2) == (z, rows, -1.0)
+    # the tuned shape gives the same iterates as the default (the work split only
+    # regroups the partial sums)
+    with cuda_lib.BatchSolver(probs) as a, cuda_lib.BatchSolver(probs, zchunk=z, curv_rows=rows) as b:
         ta, tb = a.iterate(5), b.iterate(5)
     np.testing.assert_allclose(ta, tb, rtol=1e-6)
+
+
+@pytest.mark.parametrize("slabs", [False, True])
+def test_32_row_curvature_tiles_match_16_row(cuda_lib, slabs):
+    """The two FP32 curvature tile shapes compute the same sums in another grouping."""
+    from paper_2002_02328_gb300 import synth
+    bounds = [0, 4, 11, 13, 20] if slabs else None
+    p = synth.tiny_problem(shape=(20, 45, 70), psf_shape=(7, 7, 7), seed=6, n_ellipsoids=8, slabs=bounds)
+    with cuda_lib.Solver.from_problem(p, curv_rows=16) as a, cuda_lib.Solver.from_problem(p, curv_rows=32) as b:
+        ta, tb = a.iterate(10), b.iterate(10)
+        xa, xb = a.get_x().cpu().numpy(), b.get_x().cpu().numpy()
+    np.testing.assert_allclose(tb, ta, rtol=1e-6)
+    assert np.linalg.norm(xb - xa) <= 1e-5 * np.linalg.norm(xa)
