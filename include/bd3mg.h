@@ -187,6 +187,12 @@ typedef struct {
     int psf_mode;             /* BD3MG_PSF_AUTO (default): the separable fast path when every depth's PSF
                                  factors and its radii are compiled (xy <= 5, z <= 5), else the dense path;
                                  BD3MG_PSF_DENSE: the dense path always (taken from p[0]) */
+    int persistent;           /* 0 (default): every iteration is a replay of the captured iteration
+                                 graph; 1: the fused form runs its iterations inside one persistent
+                                 cooperative launch per refresh period (see bd3mg_iterate).  Needs
+                                 the fused form (no slabs, separable PSF, coloured schedule;
+                                 separate_update AUTO or FUSED), an FP32 gradient and 16-row
+                                 curvature tiles, else BD3MG_EUNSUPPORTED.  Taken from p[0]. */
 } bd3mg_params;
 
 /* Fill *p with defaults (plain FP32, per-axis penalty, lambda = delta = 1e-2,
@@ -242,7 +248,14 @@ int bd3mg_volume_count(bd3mg_ctx *ctx);
  * Every entry takes its data term 1/2 ||r||^2 from the carried residual r
  * (bd3mg_objective applies H to x afresh; the two agree to ~1e-8 relative, the
  * FP32 evaluation accuracy), so a run split across calls reports the same
- * trace.  Synchronises the stream. */
+ * trace.  Synchronises the stream.
+ * With bd3mg_params.persistent = 1, the iterations between two exact
+ * refreshes run in one cooperative launch (k_persist): all its CTAs are
+ * resident, take the work items of each pass from a queue and wait at a
+ * grid-wide barrier (bounded by barrier_timeout_ms) between passes.  Volumes
+ * of a batch stop inside the launch (no host round trip between iterations,
+ * no re-planning of the work lists).  The iterates and the trace are the bits
+ * of the graph form with the same work items. */
 bd3mg_status bd3mg_iterate(bd3mg_ctx *ctx, int n, double *f_trace);
 
 /* Enqueue n iterations without synchronising and without reading anything back
@@ -346,7 +359,8 @@ enum {
  * bd3mg_iterate_async(ctx, 1). */
 bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
 
-/* Number of kernel launches one iteration enqueues. */
+/* Number of kernel launches one iteration enqueues (a persistent context:
+ * 1, an upper bound, since one launch runs up to refresh_every iterations). */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
 /* Precision escalation of the BF16-gradient form (Section 2.3's subspace D =
@@ -369,8 +383,12 @@ bd3mg_status bd3mg_escalated(bd3mg_ctx *ctx, long long *at);
  * out after barrier_timeout_ms, the CTA waits (again bounded) for its other
  * copies and returns, and the call reports BD3MG_ETIMEOUT (the context is then
  * poisoned; the CUDA context stays usable).  Nothing traps, faults or hangs.
+ * BD3MG_FAULT_SKIP_ARRIVE (persistent contexts): CTA 0 of the persistent
+ * launch leaves without arriving at its first grid-wide barrier; every other
+ * CTA's barrier wait runs out after barrier_timeout_ms and the call reports
+ * BD3MG_ETIMEOUT in the same way.
  * BD3MG_FAULT_NONE turns it off.  Takes effect at the next launch. */
-enum { BD3MG_FAULT_NONE = 0, BD3MG_FAULT_SKIP_COPY = 1 };
+enum { BD3MG_FAULT_NONE = 0, BD3MG_FAULT_SKIP_COPY = 1, BD3MG_FAULT_SKIP_ARRIVE = 2 };
 bd3mg_status bd3mg_inject_fault(bd3mg_ctx *ctx, int kind);
 
 /* Checkpoint / resume.  bd3mg_save writes the state an iteration starts from

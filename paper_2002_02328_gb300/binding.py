@@ -31,7 +31,7 @@ DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2
 SCHEDULE_COLOURED, SCHEDULE_JACOBI = 0, 1
 PSF_AUTO, PSF_DENSE = 0, 1
 UPDATE_AUTO, UPDATE_SEPARATE, UPDATE_FUSED = 0, 1, 2
-FAULT_NONE, FAULT_SKIP_COPY = 0, 1
+FAULT_NONE, FAULT_SKIP_COPY, FAULT_SKIP_ARRIVE = 0, 1, 2
 
 # Every symbol include/bd3mg.h declares (checked by the CPU test-suite).
 EXPORTED = ["bd3mg_params_default", "bd3mg_create", "bd3mg_iterate", "bd3mg_iterate_async", "bd3mg_objective",
@@ -63,7 +63,7 @@ class Params(ctypes.Structure):
                 ("separate_update", ctypes.c_int),
                 ("metric", ctypes.c_int), ("lipschitz", ctypes.c_double), ("direction", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("inflation", ctypes.c_double), ("curv_rows", ctypes.c_int),
-                ("psf_mode", ctypes.c_int)]
+                ("psf_mode", ctypes.c_int), ("persistent", ctypes.c_int)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -168,7 +168,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
                 zchunk: int = 0, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                 barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
                 direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0,
-                curv_rows: int = 0):
+                curv_rows: int = 0, persistent: int = 0):
     """Build a Params struct; returns (params, keepalive) -- keep both alive until create returns."""
     nz, ny, nx = (int(s) for s in shape)
     psf = np.ascontiguousarray(psf, dtype=np.float32)
@@ -189,6 +189,7 @@ def make_params(shape, psf: np.ndarray, lam=1e-2, delta=1e-2, eta=1.0, xmin=0.0,
     p.schedule, p.inflation = int(schedule), float(inflation)
     p.psf_mode = int(psf_mode)
     p.curv_rows = int(curv_rows)
+    p.persistent = int(persistent)
     keep = [psf]
     if slabs is not None and len(slabs) > 2:
         b = np.ascontiguousarray(slabs, dtype=np.int32)
@@ -281,14 +282,14 @@ class Solver:
                  use_torch_allocator: bool = True, penalty: int = 0, kappa: float = 0.0, refresh_every: int = 0,
                  barrier_timeout_ms: int = 0, separate_update: int = 0, metric: int = 0, lipschitz: float = 0.0,
                  direction: int = 0, schedule: int = 0, inflation: float = 0.0, psf_mode: int = 0,
-                 curv_rows: int = 0):
+                 curv_rows: int = 0, persistent: int = 0):
         torch = _torch()
         self.shape = tuple(int(s) for s in shape)
         self.n = int(np.prod(self.shape))
         self.nslabs = 1 if slabs is None or len(slabs) <= 2 else len(slabs) - 1
         params, keep = make_params(shape, psf, lam, delta, eta, xmin, xmax, slabs, precision, pinv_rtol, zchunk,
                                    penalty, kappa, refresh_every, barrier_timeout_ms, separate_update, metric,
-                                   lipschitz, direction, schedule, inflation, psf_mode, curv_rows)
+                                   lipschitz, direction, schedule, inflation, psf_mode, curv_rows, persistent)
         if not isinstance(y, torch.Tensor):
             y = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32))
         if x0 is not None and not isinstance(x0, torch.Tensor):
@@ -453,7 +454,7 @@ class BatchSolver:
 
     def __init__(self, problems, x0s=None, device="cuda", zchunk: int = 0, stream=None,
                  use_torch_allocator: bool = True, precision: int = FP32, separate_update: int = 0,
-                 curv_rows: int = 0):
+                 curv_rows: int = 0, persistent: int = 0):
         torch = _torch()
         lib = load()
         self.shapes = [tuple(int(s) for s in p.shape) for p in problems]
@@ -465,7 +466,7 @@ class BatchSolver:
         for v, p in enumerate(problems):
             prm, k = make_params(p.shape, p.psf, p.lam, p.delta, p.eta, p.xmin, p.xmax, p.slabs, precs[v], 1e-12,
                                  zchunk, getattr(p, "penalty", 0), getattr(p, "kappa", 0.0),
-                                 separate_update=separate_update, curv_rows=curv_rows)
+                                 separate_update=separate_update, curv_rows=curv_rows, persistent=persistent)
             arr[v] = prm
             keep.append(k)
             yt = torch.from_numpy(np.ascontiguousarray(p.y, np.float32)).to(device)

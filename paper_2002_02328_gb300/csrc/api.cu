@@ -33,6 +33,7 @@
 #include "../../include/bd3mg.h"
 #include "kernel_sets.h"
 #include "kernels.cuh"
+#include "persist.cuh"
 #include "plan.h"
 
 using namespace bd3mg;
@@ -143,8 +144,13 @@ struct bd3mg_ctx {
     std::vector<Launch> L_grad, L_curv;
     int max_items = 0;
     int sms = 152;                  // SM count of the device
-    int occ[8] = {1, 1, 1, 1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
+    int occ[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};   // resident CTAs per SM by kernel kind (see KernelSet::occupancy)
     bool t32 = false;               // FP32 curvature pass with 32-row tiles (curv_rows = 32)
+    // persistent fused-update iteration: one cooperative launch of pgrid CTAs
+    // per refresh period; pwords: its barrier and item-queue words
+    bool persist = false;
+    int pgrid = 0;
+    unsigned int *pwords = nullptr;
 
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -247,6 +253,7 @@ bool encode_lazy_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v) {
 int curv_ty(const bd3mg_ctx *c, int g_esize) { return (g_esize == 2 || c->t32) ? 2 * TY_C : TY_C; }
 
 int occ_kind(const bd3mg_ctx *c, int kind) {
+    if (c->persist && (kind == 1 || kind == 2)) return 8;     // both passes run in the persistent kernel
     if (kind == 2 && !c->bf && c->t32) return 7;
     if (c->lazy && kind == 1) return c->bf ? 6 : 5;
     return c->bf && (kind == 1 || kind == 2) ? kind + 2 : kind;
@@ -631,8 +638,32 @@ bd3mg_status settle(bd3mg_ctx *c) {
     return BD3MG_OK;
 }
 
+// n iterations of a persistent context: one cooperative launch per stretch
+// between the exact refreshes that are due.
+bd3mg_status launch_persistent(bd3mg_ctx *c, int n) {
+    int k = 0;
+    while (k < n) {
+        if (c->stale || c->since_refresh >= c->refresh_every) {
+            bd3mg_status st = settle(c);
+            if (!st) st = refresh_products(c);
+            if (st) return st;
+        }
+        const int m = (int)std::min<long long>(n - k, c->refresh_every - c->since_refresh);
+        CK(cudaMemsetAsync(c->pwords, 0, sizeof(unsigned int) * PERSIST_WORDS, c->stream));
+        PersistArgs pa{make_args(c, c->L_grad[0], M_TRACE | M_ADVANCE | M_ITER | M_OBJ | M_LAZY, nullptr),
+                       make_args(c, c->L_curv[0], M_ITER | M_PAR, nullptr), c->pwords, m};
+        const cudaError_t e = c->ks->persist(pa, c->pgrid, c->stream);
+        if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "persistent launch: %s", cudaGetErrorString(e));
+        c->pending = true;
+        c->since_refresh += m;
+        k += m;
+    }
+    return BD3MG_OK;
+}
+
 // n graph launches of one iteration each, with the refreshes they are due.
 bd3mg_status launch_iterations(bd3mg_ctx *c, int n) {
+    if (c->persist) return launch_persistent(c, n);
     for (int k = 0; k < n; ++k) {
         if (c->stale || c->since_refresh >= c->refresh_every) {
             bd3mg_status st = settle(c);
@@ -1075,6 +1106,17 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         const bool can = !c->any_slabs && !c->dense;
         c->lazy = can && (pp[0].separate_update == BD3MG_UPDATE_FUSED ||
                           (pp[0].separate_update == BD3MG_UPDATE_AUTO && vox >= kFusedMinVoxels));
+        if (pp[0].persistent != 0 && pp[0].persistent != 1) return fail(c, BD3MG_EINVAL, "persistent must be 0 or 1");
+        if (pp[0].persistent) {
+            if (!can || pp[0].separate_update == BD3MG_UPDATE_SEPARATE)
+                return fail(c, BD3MG_EUNSUPPORTED, "the persistent iteration is the fused form: no slabs, "
+                                                   "a separable PSF, separate_update AUTO or FUSED");
+            if (c->bf || c->t32)
+                return fail(c, BD3MG_EUNSUPPORTED, "the persistent iteration runs an FP32 gradient with 16-row "
+                                                   "curvature tiles");
+            c->lazy = true;
+            c->persist = true;
+        }
     }
     for (int v = 0; v < nvol; ++v)
         c->segs_h.push_back(SegDev{v, 0, c->V[v].p.nz, (int)c->segs_h.size(), 0, 0, nullptr, nullptr});
@@ -1086,7 +1128,14 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess) e = c->ks->prepare();
         if (e != cudaSuccess) return fail(c, BD3MG_ECUDA, "device query: %s", cudaGetErrorString(e));
-        for (int k = 0; k < 8; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+        for (int k = 0; k < 9; ++k) c->occ[k] = std::max(1, c->ks->occupancy(k));
+        if (c->persist) {
+            // all CTAs of the cooperative launch must be resident at once
+            const int per_sm = c->ks->occupancy(8);
+            if (per_sm < 1) return fail(c, BD3MG_EUNSUPPORTED, "the persistent kernel does not fit on an SM");
+            c->pgrid = per_sm * c->sms;
+            if ((st = dalloc_n(c, &c->pwords, PERSIST_WORDS))) return st;
+        }
     }
 
     // work lists
@@ -1453,7 +1502,8 @@ bd3mg_status bd3mg_iterate(bd3mg_ctx *c, int n, double *f_trace) {
     if ((st = ensure_trace(c, n + 1))) return st;
     CK(cudaMemsetAsync(c->counter, 0, sizeof(int), c->stream));
     const long long base = c->iterations;
-    const bool compact = c->nvol > 1 && stopping_enabled(c);
+    // (a persistent launch skips stopped volumes by itself)
+    const bool compact = c->nvol > 1 && stopping_enabled(c) && !c->persist;
     if ((c->bf && c->esc_tol > 0.0) || compact) {
         // run in chunks of 4 iterations, reading state between them:
         //  - escalation: switch to an FP32 gradient once some volume decreases by
@@ -1638,9 +1688,9 @@ bd3mg_status bd3mg_set_escalation(bd3mg_ctx *c, double tol) {
 
 bd3mg_status bd3mg_inject_fault(bd3mg_ctx *c, int kind) {
     GUARD(c);
-    if (kind != BD3MG_FAULT_NONE && kind != BD3MG_FAULT_SKIP_COPY)
+    if (kind != BD3MG_FAULT_NONE && kind != BD3MG_FAULT_SKIP_COPY && kind != BD3MG_FAULT_SKIP_ARRIVE)
         return fail(c, BD3MG_EINVAL, "unknown fault kind %d", kind);
-    c->fault = kind == BD3MG_FAULT_SKIP_COPY ? FAULT_SKIP_COPY : 0;
+    c->fault = kind == BD3MG_FAULT_SKIP_COPY ? FAULT_SKIP_COPY : kind == BD3MG_FAULT_SKIP_ARRIVE ? FAULT_SKIP_ARRIVE : 0;
     return upload_shared(c);
 }
 
@@ -1849,6 +1899,7 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *c, double *ms, int *launches) {
 
 int bd3mg_launches_per_iteration(bd3mg_ctx *c) {
     if (!c) return 0;
+    if (c->persist) return 1;       // at most: one launch covers up to refresh_every iterations
     return c->lazy ? 2 : 1 + 3 * c->ncolours + (c->jacobi ? 2 : 0);
 }
 

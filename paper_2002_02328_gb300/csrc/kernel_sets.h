@@ -15,6 +15,8 @@ struct SegDev;
 struct VolRun;
 typedef void (*launch_fn)(const KArgs &, cudaStream_t);
 typedef cudaError_t (*prep_fn)();
+struct PersistArgs;
+typedef cudaError_t (*persist_fn)(const PersistArgs &, int grid, cudaStream_t);
 
 struct KernelSet {
     int R, RZ, PM;
@@ -22,11 +24,12 @@ struct KernelSet {
     launch_fn gradient_bf, curvature_bf;            // BF16 gradient
     launch_fn gradlazy, gradlazy_bf;                // fused-update gradient pass (FP32 / BF16 gradient)
     launch_fn curvature_t32;                        // FP32 gradient, 32-row curvature tiles
+    persist_fn persist;                             // persistent fused-update iteration, FP32 gradient (cooperative launch)
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
     // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
     // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient), 5 fused-update
     // gradient, 6 fused-update gradient (BF16 gradient), 7 curvature (FP32
-    // gradient, 32-row tiles)
+    // gradient, 32-row tiles), 8 persistent iteration (FP32 gradient)
     int (*occupancy)(int kind);
 };
 

@@ -357,10 +357,13 @@ __device__ __forceinline__ bool init_bars(uint64_t *bar, int n, const void *smem
     return true;
 }
 
-// FP64 CTA reduction of NP per-thread FP32 partials into partials[blockIdx.x],
-// then the ticket: returns true in the last CTA to finish (all threads).
+// FP64 CTA reduction of NP per-thread FP32 partials into partials[idx] (idx:
+// the work item, blockIdx.x when negative), then the ticket: returns true in
+// the last CTA to finish (all threads).
 template <int NP>
-__device__ bool publish_partials(const float (&acc)[NP], double *partials, unsigned int *ticket, int nitems) {
+__device__ bool publish_partials(const float (&acc)[NP], double *partials, unsigned int *ticket, int nitems,
+                                 int idx = -1) {
+    const size_t row = idx < 0 ? (size_t)blockIdx.x : (size_t)idx;
     __shared__ double red[NWARP][NP];
     __shared__ int is_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -376,7 +379,7 @@ __device__ bool publish_partials(const float (&acc)[NP], double *partials, unsig
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < NWARP; ++w) s += red[w][threadIdx.x];
-        partials[(size_t)blockIdx.x * NP + threadIdx.x] = s;
+        partials[row * NP + threadIdx.x] = s;
         __threadfence();
     }
     __syncthreads();
@@ -392,9 +395,10 @@ __device__ bool publish_partials(const float (&acc)[NP], double *partials, unsig
 // Item of a stopped volume: zero partials and the ticket only (all threads
 // call; true in the last CTA to finish).
 template <int NP>
-__device__ bool publish_zero(double *partials, unsigned int *ticket, int nitems) {
+__device__ bool publish_zero(double *partials, unsigned int *ticket, int nitems, int idx = -1) {
     __shared__ int last_z;
-    if (threadIdx.x < NP) partials[(size_t)blockIdx.x * NP + threadIdx.x] = 0.0;
+    const size_t row = idx < 0 ? (size_t)blockIdx.x : (size_t)idx;
+    if (threadIdx.x < NP) partials[row * NP + threadIdx.x] = 0.0;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last_z = atomicAdd(ticket, 1u) == (unsigned int)(nitems - 1);
@@ -418,13 +422,39 @@ __device__ void sum_slot(const double *partials, int ib, int ie, double *out) {
 }
 
 // True when this launch is part of an iteration and the volume has stopped.
-// The flag changes only in the last CTA of an objective launch, after every
-// CTA of that launch has read it, so the read-only path is coherent here (and
-// keeps the tile loops' registers at their count without the test).
+// The flag changes only in the last CTA of an objective pass, after every CTA
+// of that pass has read it.  The load goes to L2 (the point of coherence):
+// in the persistent iteration the pass that set the flag ran earlier in the
+// same launch, which the read-only path does not see.
 __device__ __forceinline__ bool vol_stopped(const KArgs &a, int vol) {
     int v = 0;
-    if ((a.mode & M_ITER) && a.sh->run) v = __ldg(&a.sh->run[vol].stopped);
+    if ((a.mode & M_ITER) && a.sh->run) v = __ldcg(&a.sh->run[vol].stopped);
     return v != 0;
+}
+
+// Load of iteration state (x, d, H g_S, ...) by a tile pass.  Separate
+// launches read it through the read-only path; in the persistent iteration
+// (PERS) an earlier pass of the same launch wrote it, so the load goes to L2.
+template <bool PERS, class T>
+__device__ __forceinline__ T ldm(const T *p) {
+    if constexpr (PERS) return __ldcg(p);
+    else return __ldg(p);
+}
+
+// End of one work item of a persistent pass: the CTA's generic shared-memory
+// writes are ordered before the next item's TMA writes into the same bytes,
+// and the item's n mbarriers are invalidated so that the next item (whose
+// layout may differ) can reuse the memory.  Nothing in separate launches.
+template <bool PERS>
+__device__ __forceinline__ void item_end(uint64_t *bar, int n) {
+    if constexpr (PERS) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int i = 0; i < n; ++i)
+                asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar + i)) : "memory");
+        __syncthreads();
+    }
 }
 
 // u = -B^+ c for the symmetric 2x2 B = [[b00, b01], [b01, b11]] (Moore-Penrose
@@ -1438,9 +1468,13 @@ __device__ __forceinline__ void pen_quad(float vg, float vd, float kl2, float *a
 // rows of a pair of adjacent columns (CurvRing).  With two rows the
 // half-quadratic terms are formed between the two barriers of a step, before
 // the convolution's registers are needed; with one, after the y-pass.
+//
+// curvature_item processes work item `item` and returns false when a bounded
+// wait ran out; k_curvature runs item blockIdx.x, the persistent iteration
+// (PERS) every item a CTA takes from the pass's queue.
 // ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF, int PM, int RPT_ = (BF ? 2 : 1)>
-__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k_curvature(KArgs a) {
+template <int R, int RZ, bool BF, int PM, int RPT_, bool PERS>
+__device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
     using CR = CurvRing<R, RZ, sizeof(T), RPT_>;
     using G = typename CR::C;
@@ -1454,7 +1488,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
     float *CF = T1 + BY * TX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_OUT_FLOATS);
 
-    const Item it = a.items[blockIdx.x];
+    const Item it = a.items[item];
     const unsigned long long wait_ns = a.sh->wait_ns;
     SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
@@ -1462,7 +1496,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
     const long long plane = V.plane;
     const float *xg = V.x, *dg = V.d;
     // fused-update iteration: the volume's state may live in its second buffer set
-    const bool set1 = (a.mode & M_PAR) && a.sh->run && __ldg(&a.sh->run[sg.vol].par) != 0;
+    const bool set1 = (a.mode & M_PAR) && a.sh->run && __ldcg(&a.sh->run[sg.vol].par) != 0;
     if (set1) {
         xg = V.x1;
         dg = V.d1;
@@ -1477,13 +1511,13 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
     // partials, but it still takes its ticket.
     const bool stopped = vol_stopped(a, sg.vol);
     if (stopped) {
-        if (publish_zero<10>(a.partials, a.ticket, a.nitems)) curvature_finish(a);
-        return;
+        if (publish_zero<10>(a.partials, a.ticket, a.nitems, item)) curvature_finish(a);
+        return true;
     }
 
     const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, it.zo0, it.zo1 - it.zo0);   // rows of the output slices only
-    if (!init_bars(bar, NS, smem, a.sh->status)) return;
+    if (!init_bars(bar, NS, smem, a.sh->status)) return false;
     const int glo = max(max(0, sg.z0), zbeg), ghi = min(min(nz, sg.z1), zend);
     const CUtensorMap *mg = &a.maps[sg.vol].m[set1 ? TM_G1_R : TM_G_R];
     if (tid == 0)   // the descriptor sits in global memory and may have been rewritten since an earlier launch
@@ -1493,7 +1527,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
     constexpr int FILL = (int)(SLOT * sizeof(T) / 16);
     // slice z of g_S into ring slot s: a TMA copy when z is a slab slice, else zeros
     // (FAULT_SKIP_COPY: CTA 0 leaves the copy of its first slab slice out)
-    const bool skip_first = a.sh->fault == FAULT_SKIP_COPY && blockIdx.x == 0;
+    const bool skip_first = a.sh->fault == FAULT_SKIP_COPY && item == 0;
     auto issue = [&](int z, int s) {
         if (z >= glo && z < ghi) {
             if (tid == 0 && !(skip_first && z == glo)) {
@@ -1574,22 +1608,22 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
             const bool dlo = zo >= sg.z0, dhi = zo + 1 < sg.z1;     // d_S at zo, at zo + 1
 #pragma unroll
             for (int k = 0; k <= RPT; ++k) {
-                xa[k] = __ldg(reinterpret_cast<const float2 *>(xp + orow[k]));
-                if (dlo) da[k] = __ldg(reinterpret_cast<const float2 *>(dp + orow[k]));
+                xa[k] = ldm<PERS>(reinterpret_cast<const float2 *>(xp + orow[k]));
+                if (dlo) da[k] = ldm<PERS>(reinterpret_cast<const float2 *>(dp + orow[k]));
             }
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
-                xev[k] = __ldg(xp + oe[k]);
-                xz[k] = __ldg(reinterpret_cast<const float2 *>(xp + zn + orow[k]));
-                if (dlo) dev[k] = __ldg(dp + oe[k]);
-                if (dhi) dz[k] = __ldg(reinterpret_cast<const float2 *>(dp + zn + orow[k]));
+                xev[k] = ldm<PERS>(xp + oe[k]);
+                xz[k] = ldm<PERS>(reinterpret_cast<const float2 *>(xp + zn + orow[k]));
+                if (dlo) dev[k] = ldm<PERS>(dp + oe[k]);
+                if (dhi) dz[k] = ldm<PERS>(reinterpret_cast<const float2 *>(dp + zn + orow[k]));
             }
         }
         const long long zz = (long long)(zo - sg.hz0) * plane;       // slice zo in the zone buffers
         if (emit && v00) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k)
-                if (rok[k]) hd[k] = __ldg(reinterpret_cast<const float2 *>(sg.hd + zz + orow[k]));
+                if (rok[k]) hd[k] = ldm<PERS>(reinterpret_cast<const float2 *>(sg.hd + zz + orow[k]));
         }
         // half-quadratic terms and g, d products of the thread's voxels at zo
         auto terms = [&]() {
@@ -1704,7 +1738,7 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
             for (int k = 0; k < RPT; ++k) {
                 if (!rok[k]) continue;
                 if (hg_given) {
-                    hg[k] = __ldg(reinterpret_cast<const float2 *>(hgz + orow[k]));
+                    hg[k] = ldm<PERS>(reinterpret_cast<const float2 *>(hgz + orow[k]));
                 } else {
                     if (c1ok) *reinterpret_cast<float2 *>(hgz + orow[k]) = hg[k];
                     else hgz[orow[k]] = hg[k].x;
@@ -1736,9 +1770,16 @@ __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k
             }
             atomicOr(a.sh->status, ST_TIMEOUT);
         }
-        return;
+        return false;
     }
-    if (publish_partials<10>(acc, a.partials, a.ticket, a.nitems)) curvature_finish(a);
+    item_end<PERS>(bar, NS);
+    if (publish_partials<10>(acc, a.partials, a.ticket, a.nitems, item)) curvature_finish(a);
+    return true;
+}
+
+template <int R, int RZ, bool BF, int PM, int RPT_ = (BF ? 2 : 1)>
+__global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k_curvature(KArgs a) {
+    curvature_item<R, RZ, BF, PM, RPT_, false>(a, blockIdx.x);
 }
 
 }  // namespace bd3mg

@@ -3,6 +3,7 @@
 #include "kernel_sets.h"
 #include "kernels.cuh"
 #include "lazy.cuh"
+#include "persist.cuh"
 
 namespace bd3mg {
 
@@ -25,6 +26,19 @@ void launch_gradlazy(const KArgs &a, cudaStream_t s) {
 template <int R, int RZ, int PM>
 void launch_curvature_t32(const KArgs &a, cudaStream_t s) {
     k_curvature<R, RZ, false, PM, 2><<<a.nitems, NT, Smem<R, RZ>::curvature_t32, s>>>(a);
+}
+template <int R, int RZ, bool BF>
+constexpr size_t persist_smem() {
+    return LazyGeo<R, RZ>::SMEM > (BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature)
+               ? LazyGeo<R, RZ>::SMEM
+               : (BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature);
+}
+// Cooperative launch of the persistent iteration: grid CTAs, all resident.
+template <int R, int RZ, bool BF, int PM>
+cudaError_t launch_persist(const PersistArgs &p, int grid, cudaStream_t s) {
+    void *args[] = {const_cast<PersistArgs *>(&p)};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(&k_persist<R, RZ, BF, PM>), dim3(grid),
+                                       dim3(NT), args, persist_smem<R, RZ, BF>(), s);
 }
 template <int R, int RZ, int PM>
 cudaError_t prepare_set() {
@@ -51,6 +65,9 @@ cudaError_t prepare_set() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_gradlazy<R, RZ, true, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)LazyGeo<R, RZ>::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_persist<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)persist_smem<R, RZ, false>());
     return e;
 }
 
@@ -66,6 +83,7 @@ int occupancy_of(int kind) {
         case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, false, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gradlazy<R, RZ, true, PM>, NT, LazyGeo<R, RZ>::SMEM); break;
         case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM, 2>, NT, Smem<R, RZ>::curvature_t32); break;
+        case 8: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_persist<R, RZ, false, PM>, NT, persist_smem<R, RZ, false>()); break;
         default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_curvature<R, RZ, false, PM>, NT, Smem<R, RZ>::curvature); break;
     }
     return e == cudaSuccess ? n : 0;
@@ -78,4 +96,5 @@ int occupancy_of(int kind) {
      &bd3mg::launch_curvature<R, RZ, false, PM>, &bd3mg::launch_gradient<R, RZ, true, PM>,                  \
      &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::launch_gradlazy<R, RZ, false, PM>,                  \
      &bd3mg::launch_gradlazy<R, RZ, true, PM>, &bd3mg::launch_curvature_t32<R, RZ, PM>,                     \
+     &bd3mg::launch_persist<R, RZ, false, PM>,                                                              \
      &bd3mg::prepare_set<R, RZ, PM>, &bd3mg::occupancy_of<R, RZ, PM>}

@@ -46,8 +46,11 @@ struct LazyGeo {
     static_assert((3 * XTS) % 4 == 0, "the x-pass output must stay 16-byte aligned");
 };
 
-template <int R, int RZ, bool BF, int PM>
-__global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
+// gradlazy_item processes work item `item` and returns false when a bounded
+// wait ran out; k_gradlazy runs item blockIdx.x, the persistent iteration
+// (PERS) every item a CTA takes from the pass's queue.
+template <int R, int RZ, bool BF, int PM, bool PERS>
+__device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
     using G = Geo<R, RZ, TY_A>;
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
     constexpr int KZ = G::KZ, NS = LazyGeo<R, RZ>::NS, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
@@ -62,7 +65,7 @@ __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
     float *CF = T1 + BY * TX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
 
-    const Item it = a.items[blockIdx.x];
+    const Item it = a.items[item];
     const unsigned long long wait_ns = a.sh->wait_ns;
     const SegDev sg = a.segs[it.seg];
     const VolDev &V = a.vols[sg.vol];
@@ -71,13 +74,13 @@ __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
     const float delta2 = V.delta2, xmin = V.xmin, xmax = V.xmax, lam = V.lam, eta2 = V.eta2, kap2 = V.kap2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (vol_stopped(a, sg.vol)) {
-        if (publish_zero<3>(a.partials, a.ticket, a.nitems)) objective_finish(a);
-        return;
+        if (publish_zero<3>(a.partials, a.ticket, a.nitems, item)) objective_finish(a);
+        return true;
     }
     // the volume's current buffer set, and whether the last solve's update is still to be applied
     const VolRun &rv = a.sh->run[sg.vol];
-    const bool set1 = __ldg(&rv.par) != 0;
-    const bool apply = __ldg(&rv.pending) != 0;
+    const bool set1 = __ldcg(&rv.par) != 0;
+    const bool apply = __ldcg(&rv.pending) != 0;
     float u0 = 0.f, u1 = 0.f;
     if (apply) {
         u0 = (float)a.u[2 * sg.slot];
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
 
     const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
-    if (!init_bars(bar, NS, smem, a.sh->status)) return;
+    if (!init_bars(bar, NS, smem, a.sh->status)) return false;
     const int rlo = max(0, zbeg), rhi = min(nz, zend);
     const VolMaps &vm = a.maps[sg.vol];
     const CUtensorMap *mr = &vm.m[set1 ? TM_R1_R : TM_R_R];
@@ -211,22 +214,22 @@ __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
         if (build) {
             const long long zoff = (long long)zt * plane;
             if (own) {
-                bx[0] = __ldg(reinterpret_cast<const float2 *>(xs + zoff + o0));
-                if (r1ok) bx[1] = __ldg(reinterpret_cast<const float2 *>(xs + zoff + o1));
+                bx[0] = ldm<PERS>(reinterpret_cast<const float2 *>(xs + zoff + o0));
+                if (r1ok) bx[1] = ldm<PERS>(reinterpret_cast<const float2 *>(xs + zoff + o1));
                 if (apply) {
                     bg[0] = ld2(gs + zoff + o0);
-                    bd[0] = __ldg(reinterpret_cast<const float2 *>(ds + zoff + o0));
+                    bd[0] = ldm<PERS>(reinterpret_cast<const float2 *>(ds + zoff + o0));
                     if (r1ok) {
                         bg[1] = ld2(gs + zoff + o1);
-                        bd[1] = __ldg(reinterpret_cast<const float2 *>(ds + zoff + o1));
+                        bd[1] = ldm<PERS>(reinterpret_cast<const float2 *>(ds + zoff + o1));
                     }
                 }
             }
             if (hin) {
-                hxv = __ldg(xs + zoff + hoff);
+                hxv = ldm<PERS>(xs + zoff + hoff);
                 if (apply) {
                     hgv = to_f(gs[zoff + hoff]);
-                    hdv = __ldg(ds + zoff + hoff);
+                    hdv = ldm<PERS>(ds + zoff + hoff);
                 }
             }
         }
@@ -374,9 +377,16 @@ __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
             }
             atomicOr(a.sh->status, ST_TIMEOUT);
         }
-        return;
+        return false;
     }
-    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems)) objective_finish(a);
+    item_end<PERS>(bar, NS);
+    if (publish_partials<3>(acc, a.partials, a.ticket, a.nitems, item)) objective_finish(a);
+    return true;
+}
+
+template <int R, int RZ, bool BF, int PM>
+__global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
+    gradlazy_item<R, RZ, BF, PM, false>(a, blockIdx.x);
 }
 
 }  // namespace bd3mg

@@ -44,7 +44,9 @@ def test_status_strings(lib):
 def test_params_default(lib):
     p = binding.Params()
     p.penalty, p.kappa, p.barrier_timeout_ms = 7, 3.5, 9   # the defaults must reach the struct's last fields
+    p.psf_mode, p.persistent = 3, 5
     lib.bd3mg_params_default(ctypes.byref(p))
+    assert p.psf_mode == binding.PSF_AUTO and p.persistent == 0
     assert p.lambda_ == 1e-2 and p.delta == 1e-2 and p.eta == 1.0 and p.xmax == 1.0 and p.nslabs == 1
     assert p.penalty == binding.PENALTY_PER_AXIS and p.kappa == 0.0
     assert p.refresh_every == 0 and p.barrier_timeout_ms == 0      # library defaults: 256 iterations, 2 s
