@@ -437,7 +437,10 @@ def batch_extra(iters, stream):
     ok = all(v is not None for v in k)
     # lockstep with per-volume stopping at f <= f* + gap |f*|: a volume that
     # reaches its target drops out of every later launch
-    t_stop, k_stop, t_stop_model = None, None, None
+    t_stop, k_stop, t_stop_model, t_stop_pers = None, None, None, None
+    with binding.BatchSolver(probs, persistent=1) as bs:
+        bs.iterate_async(3)
+        t_pers = timed(lambda: bs.iterate_async(20), 1) / 20
     if ok:
         with binding.BatchSolver(probs, zchunk=zc, curv_rows=zrows) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
@@ -449,15 +452,21 @@ def batch_extra(iters, stream):
         with binding.BatchSolver(probs) as bs:
             bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
             t_stop_model = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
+        # one persistent launch per refresh period: volumes stop inside the launch
+        with binding.BatchSolver(probs, persistent=1) as bs:
+            bs.set_stopping(0.0, fstar + GAP * np.abs(fstar))
+            t_stop_pers = timed(lambda: bs.iterate(max(k) + 1, trace=False), 1)
     return {"volumes": len(probs), "voxels": nvox, "step": "one lockstep iteration of all volumes",
             "lockstep_iterations_per_s": 1.0 / t_batch,
             "autotuned_zchunk": zc, "autotuned_curvature_rows": zrows,
             "lockstep_iterations_per_s_default_zchunk": 1.0 / t_default,
+            "lockstep_iterations_per_s_persistent": 1.0 / t_pers,
             "sequential_iterations_per_s": 1.0 / sum(t_seq),
             "fstar_iters": iters, "fstar_settle_rel": settle,
             "iters_to_gap": k,
             "time_to_gap_s": {"batched_with_stopping": t_stop,
                               "batched_with_stopping_model_zchunk": t_stop_model,
+                              "batched_with_stopping_persistent": t_stop_pers,
                               "batched_lockstep": (max(k) * t_batch) if ok else None,
                               "sequential": (sum(kv * tv for kv, tv in zip(k, t_seq))) if ok else None},
             "stopped_after": k_stop}
@@ -579,6 +588,11 @@ def dense_extra(stream, flush, steps, sm_mhz):
     return out
 
 
+def torch_events():
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
 def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
     """The plain FP32 iteration on the 512x512x128 recipe (PSF 9x9x7), where the
     HBM roofline target is set: iterations/s of the fused-update form (two
@@ -605,6 +619,16 @@ def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
         profs[name] = {k: v[0] / profile_iters for k, v in prof.items()}
         if name == "fused":
             prof_f = prof
+    # the same iterations in one persistent cooperative launch per refresh period
+    # (every array is 128 MiB, so the L2 holds nothing between iterations)
+    with binding.Solver.from_problem(prob, slabs=None, persistent=1) as s:
+        s.iterate_async(3)
+        a, b = torch_events()
+        a.record(stream)
+        s.iterate_async(steps)
+        b.record(stream)
+        b.synchronize()
+        rates["persistent"] = (a.elapsed_time(b) / steps, 1e3 * steps / a.elapsed_time(b))
     alg = algorithmic_bytes(prob, None, 4, fused=True)
     per_it = profs["fused"]
     dom = max(per_it, key=per_it.get)
@@ -620,6 +644,7 @@ def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
             "alg_bytes_per_launch": alg[dom] / launches, "avg_launch_ms": avg_ms,
             "iterations_per_s": rates["fused"][1], "ms_per_iteration": ms_it,
             "iterations_per_s_separate_update": rates["separate"][1],
+            "iterations_per_s_persistent": rates["persistent"][1],
             "kernel_ms_per_iteration": per_it, "kernel_ms_per_iteration_separate_update": profs["separate"],
             "iteration_vs_28B_bound": 28.0 * prob.n / (ms_it * 1e-3) / 1e9 / peak,
             "own_bytes_per_voxel": own / prob.n,
@@ -628,13 +653,16 @@ def plain512_roofline(stream, flush, steps, profile_iters, peak, peak_kind):
 
 def mixed_extra(fstar_iters, stream, flush, steps):
     """512x512x128 volume, 800 ellipsoids + texture, PSF 9x9x7 (sigma_xy 0.5->3.0), noise 0.01:
-    plain 3MG with an FP32 gradient against a BF16 gradient (iterations/s with the L2 flushed
-    before every step, and device time to gap 1e-4; f* from a long FP32 run)."""
+    plain 3MG with an FP32 gradient against a BF16 gradient and against BF16 g, d, H g and H d
+    (iterations/s with the L2 flushed before every step, and device time to gap 1e-4; f* from a
+    long FP32 run)."""
     from paper_2002_02328_gb300 import binding, synth
     prob = synth.workload_mixed(seed=0)
     out = {"workload": "plain 3MG 512x512x128, PSF 9x9x7 depth-variant Gaussian, 800 ellipsoids + texture",
            "voxels": prob.n}
-    for name, prec in (("fp32", binding.FP32), ("bf16_gradient", binding.BF16_GRADIENT)):
+    forms = (("fp32", binding.FP32), ("bf16_gradient", binding.BF16_GRADIENT),
+             ("bf16_directions", binding.BF16_DIRECTIONS))
+    for name, prec in forms:
         with binding.Solver.from_problem(prob, slabs=None, precision=prec) as s:
             for _ in range(3):
                 flush.fill_(1.0)
@@ -645,19 +673,21 @@ def mixed_extra(fstar_iters, stream, flush, steps):
                      "kernel_ms_per_iteration": {k: v[0] for k, v in prof.items()}}
     fstar, settle = fstar_of(prob, fstar_iters)
     out.update({"fstar": fstar, "fstar_iters": fstar_iters, "fstar_settle_rel": settle})
-    # BF16 gradient with precision escalation (switch to an FP32 gradient once f decreases by
+    # BF16 forms with precision escalation (switch to FP32 storage once f decreases by
     # <= 1e-9 |f| per iteration): iterations of the escalating run to each gap level
-    with binding.Solver.from_problem(prob, slabs=None, precision=binding.BF16_GRADIENT) as s:
-        s.set_escalation(1e-9)
-        tr = s.iterate(400)
-        at = s.escalated()
-    esc = {"tol": 1e-9, "escalated_at_iteration": at}
-    for name, den in (("rel_1e-7", abs(fstar)), ("normalized_1e-6", tr[0] - fstar)):
-        lvl = 1e-7 if name.startswith("rel") else 1e-6
-        hit = np.nonzero((tr - fstar) / den <= lvl)[0]
-        esc[name + "_iterations"] = int(hit[0]) if hit.size else None
-    out["bf16_escalating"] = esc
-    for name, prec in (("fp32", binding.FP32), ("bf16_gradient", binding.BF16_GRADIENT)):
+    for key, prec in (("bf16_escalating", binding.BF16_GRADIENT),
+                      ("bf16_directions_escalating", binding.BF16_DIRECTIONS)):
+        with binding.Solver.from_problem(prob, slabs=None, precision=prec) as s:
+            s.set_escalation(1e-9)
+            tr = s.iterate(400)
+            at = s.escalated()
+        esc = {"tol": 1e-9, "escalated_at_iteration": at}
+        for name, den in (("rel_1e-7", abs(fstar)), ("normalized_1e-6", tr[0] - fstar)):
+            lvl = 1e-7 if name.startswith("rel") else 1e-6
+            hit = np.nonzero((tr - fstar) / den <= lvl)[0]
+            esc[name + "_iterations"] = int(hit[0]) if hit.size else None
+        out[key] = esc
+    for name, prec in forms:
         k, t, g = time_to_gap(prob, None, fstar, 3000, stream, prec)
         kn, tn, gn = time_to_gap(prob, None, fstar, 3000, stream, prec, normalized=True)
         out[name]["time_to_gap"] = {"iterations": k, "seconds": t, "gap_reached": g}

@@ -79,8 +79,21 @@ typedef struct {
  *   [-g_bf16, d]: B = D^T A D and D^T grad f are formed from it (the gradient
  *   term as -||g_bf16||^2), and x moves by the FP32 step -u0 g_bf16 + u1 d.
  *   bd3mg_gradient and bd3mg_get_volume return g widened to FP32.
- *   Every volume of a batch must use the same mode. */
-enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1 };
+ * BD3MG_BF16_DIRECTIONS: g, the memory direction d and the images H g and H d
+ *   stored in BF16 (round to nearest even); x, y and the residual r stay
+ *   FP32, arithmetic FP32, reductions and the 2x2 solve FP64.  The update
+ *   n = -u0 g + u1 d and H n = -u0 H g + u1 H d are formed in FP32 from the
+ *   stored values: x += n and r += H n in FP32, d and H d take n and H n
+ *   rounded.  r therefore drifts from H x - y by the rounding of H g and H d;
+ *   the exact refresh every refresh_every iterations bounds the drift.  Runs
+ *   in the fused form only (volumes without slabs, a separable PSF, the
+ *   per-axis penalty, separate_update AUTO or FUSED, not persistent), else
+ *   BD3MG_EUNSUPPORTED.  bd3mg_get_volume returns d widened to FP32;
+ *   checkpoints hold the BF16 bits (bit-exact resume in the same mode).
+ *   bd3mg_set_escalation switches it to FP32 g, d, H g and H d (the stored
+ *   values widened).
+ * Every volume of a batch must use the same mode. */
+enum { BD3MG_FP32 = 0, BD3MG_BF16_GRADIENT = 1, BD3MG_BF16_DIRECTIONS = 2 };
 
 /* Penalty term f3 of the objective (Section 3.1, Eq. "crit"), with forward
  * differences [V^a x]_n = x_{n+e_a} - x_n, zero on the last plane of axis a.
@@ -155,7 +168,7 @@ typedef struct {
     double delta;             /* > 0 hyperbolic smoothing */
     double eta;               /* >= 0 box weight */
     double xmin, xmax;        /* box bounds, xmin <= xmax */
-    int precision;            /* BD3MG_FP32 or BD3MG_BF16_GRADIENT */
+    int precision;            /* BD3MG_FP32, BD3MG_BF16_GRADIENT or BD3MG_BF16_DIRECTIONS */
     int nslabs;               /* number of depth blocks; 0 or 1 = plain 3MG on the whole volume */
     const int *slab_bounds;   /* HOST, nslabs+1 increasing slice indices from 0 to nz (ignored if nslabs <= 1) */
     double pinv_rtol;         /* eigenvalues <= rtol*max are dropped in the 2x2 pseudo-inverse; 0 -> 1e-12 */
@@ -363,12 +376,13 @@ bd3mg_status bd3mg_profile_iteration(bd3mg_ctx *ctx, double *ms, int *launches);
  * 1, an upper bound, since one launch runs up to refresh_every iterations). */
 int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
 
-/* Precision escalation of the BF16-gradient form (Section 2.3's subspace D =
- * [-g, d] with g stored in BF16).  With tol > 0, bd3mg_iterate runs
- * in chunks of 4 iterations and reads the objective trace between chunks;
+/* Precision escalation of the BF16 forms (Section 2.3's subspace D = [-g, d]
+ * with g, or g, d, H g and H d, stored in BF16).  With tol > 0, bd3mg_iterate
+ * runs in chunks of 4 iterations and reads the objective trace between chunks;
  * once some volume's objective decreases by at most tol * |f| from one
- * iteration to the next, the context switches for good to an FP32 gradient
- * (g recomputed by the next iteration) and a new iteration graph.
+ * iteration to the next, the context switches for good to FP32 storage (g
+ * recomputed by the next iteration; d and H d widened from their BF16 values)
+ * and a new iteration graph.
  * bd3mg_iterate_async never escalates.  tol = 0 turns it off (the default);
  * no effect on FP32 contexts.  bd3mg_escalated: *at = the iteration count at
  * which the switch happened, -1 if it has not.  Errors: BD3MG_EINVAL for a

@@ -24,7 +24,7 @@ _lib = None
 
 STATUS = {0: "BD3MG_OK", 1: "BD3MG_EINVAL", 2: "BD3MG_ENOMEM", 3: "BD3MG_ECUDA", 4: "BD3MG_ETIMEOUT",
           5: "BD3MG_ENONFINITE", 6: "BD3MG_ESTATE", 7: "BD3MG_EUNSUPPORTED"}
-FP32, BF16_GRADIENT = 0, 1
+FP32, BF16_GRADIENT, BF16_DIRECTIONS = 0, 1, 2
 PENALTY_PER_AXIS, PENALTY_JOINT_XY, PENALTY_ISOTROPIC = 0, 1, 2
 METRIC_MAJORANT, METRIC_LIPSCHITZ = 0, 1
 DIR_MEMORY_GRADIENT, DIR_GRADIENT, DIR_CONJUGATE = 0, 1, 2

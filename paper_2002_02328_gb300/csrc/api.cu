@@ -97,6 +97,7 @@ struct bd3mg_ctx {
     int zchunk = 0;                 // user override (0 = automatic)
     double pinv_rtol = 1e-12;
     bool bf = false;                // gradient g stored as BF16
+    bool bfd = false;               // d, H g, H d stored as BF16 too (BD3MG_BF16_DIRECTIONS; implies bf)
     float *zone_hg = nullptr, *zone_hd = nullptr;   // H g_S, H d_S of every slab over its zone
     size_t zone_elems = 0;
     // fused-update iteration (no slabs): the gradient pass applies the previous
@@ -237,13 +238,15 @@ bool encode_lazy_maps(VolMaps *vm, const bd3mg_ctx *c, const VolState &v) {
     const SegDev &sg = c->segs_h[v.seg0];
     const int R = c->ks->R, bx = TX + 2 * set_xh(c->ks), ge = c->bf ? 2 : 4, bxg = TX + 2 * set_xh(c->ks, ge);
     const int by = TY_A + 2 * R;
+    // H g and H d: FP32 tiles like r's, or BF16 tiles with an 8-column halo (BF16 directions)
+    const int he = c->bfd ? 2 : 4, bxh = c->bfd ? TX + 16 : bx;
     const void *g1 = c->bf ? static_cast<const void *>(v.gh1) : static_cast<const void *>(v.g1);
-    return encode_map(&vm->m[TM_HG_R], sg.hg, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
-           encode_map(&vm->m[TM_HD_R], sg.hd, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
+    return encode_map(&vm->m[TM_HG_R], sg.hg, he, p.nx, p.ny, p.nz, v.pitch, bxh, by) &&
+           encode_map(&vm->m[TM_HD_R], sg.hd, he, p.nx, p.ny, p.nz, v.pitch, bxh, by) &&
            encode_map(&vm->m[TM_R1_R], v.r1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
            encode_map(&vm->m[TM_G1_R], g1, ge, p.nx, p.ny, p.nz, v.pitch, bxg, curv_ty(c, ge) + 2 * R) &&
-           encode_map(&vm->m[TM_HG1_R], sg.hg1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by) &&
-           encode_map(&vm->m[TM_HD1_R], sg.hd1, 4, p.nx, p.ny, p.nz, v.pitch, bx, by);
+           encode_map(&vm->m[TM_HG1_R], sg.hg1, he, p.nx, p.ny, p.nz, v.pitch, bxh, by) &&
+           encode_map(&vm->m[TM_HD1_R], sg.hd1, he, p.nx, p.ny, p.nz, v.pitch, bxh, by);
 }
 
 // Kernel kind used for occupancy: BF16-gradient gradient/curvature have their own.
@@ -486,7 +489,7 @@ bd3mg_status run_gradlazy(bd3mg_ctx *c, cudaStream_t s, const Launch &L, int mod
     KArgs a = make_args(c, L, mode | M_OBJ | M_LAZY, nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_GRADIENT);
     if (st) return st;
-    (c->bf ? c->ks->gradlazy_bf : c->ks->gradlazy)(a, s);
+    (c->bfd ? c->ks->gradlazy_bd : c->bf ? c->ks->gradlazy_bf : c->ks->gradlazy)(a, s);
     return check_launch(c);
 }
 
@@ -509,7 +512,10 @@ bd3mg_status run_curvature(bd3mg_ctx *c, cudaStream_t s, const Launch &L) {
     KArgs a = make_args(c, L, (c->lazy ? (M_ITER | M_PAR) : M_ITER) | (c->dense ? M_HG_GIVEN : 0), nullptr);
     bd3mg_status st = prof_mark(c, s, BD3MG_K_CURVATURE);
     if (st) return st;
-    (c->bf ? c->ks->curvature_bf : c->t32 ? c->ks->curvature_t32 : c->ks->curvature)(a, s);
+    (c->bfd  ? c->ks->curvature_bd
+     : c->bf ? c->ks->curvature_bf
+     : c->t32 ? c->ks->curvature_t32
+              : c->ks->curvature)(a, s);
     return check_launch(c);
 }
 
@@ -605,6 +611,23 @@ bd3mg_status fresh_objective(bd3mg_ctx *c) {
 bd3mg_status refresh_products(bd3mg_ctx *c) {
     NvtxRange nvtx_("bd3mg refresh r, H d_S");
     bd3mg_status st;
+    if (c->bfd) {
+        // BF16 directions (fused form, state settled in set 0): blur an FP32 copy of
+        // d (in d1) into the FP32 zone buffer, then round it into place through hd1
+        for (const VolState &v : c->V) launch_dir_to_float(v.d, v.d1, (long long)v.np, c->stream);
+        if ((st = check_launch(c))) return st;
+        if ((st = run_residual(c, c->stream, c->L_res_full, M_STORE_R))) return st;
+        if ((st = run_residual(c, c->stream, c->L_hd, M_STORE_R | M_ZONE))) return st;
+        for (const VolState &v : c->V) {
+            const SegDev &sg = c->segs_h[v.seg0];
+            launch_float_to_dir(sg.hd, sg.hd1, (long long)v.np, c->stream);
+            CK(cudaMemcpyAsync(sg.hd, sg.hd1, v.np * 2, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if ((st = check_launch(c))) return st;
+        c->stale = false;
+        c->since_refresh = 0;
+        return BD3MG_OK;
+    }
     if (c->dense) {
         if ((st = run_dense(c, c->stream, c->L_res_full, DS_X, DD_R, false, true, false, false))) return st;
         if ((st = run_dense(c, c->stream, c->L_hd, DS_D, DD_HD, false, false, true, false))) return st;
@@ -627,7 +650,7 @@ bd3mg_status settle(bd3mg_ctx *c) {
     long long blocks = (maxlen / 4 + NT - 1) / NT;
     blocks = std::max<long long>(1, std::min<long long>(blocks, 2048));
     launch_flush(c->vols, c->segs, c->flush_list, c->u, c->run, dim3((unsigned)blocks, (unsigned)c->nslab_segs),
-                 c->stream, c->bf);
+                 c->stream, c->bf, c->bfd);
     bd3mg_status st = check_launch(c);
     if (!st) {
         launch_clear_pending(c->run, c->nvol, c->stream);
@@ -756,8 +779,10 @@ bd3mg_status upload_descriptors(bd3mg_ctx *c) {
         }
         vs.dev = d;
         vd[v] = d;
-        bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, vs.d, 2)
-                              : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, vs.d, 4);
+        // with BF16 directions the exact refresh blurs an FP32 copy of d made in d1
+        const float *dmap = c->bfd ? vs.d1 : vs.d;
+        bool ok = c->bf ? encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.gh, dmap, 2)
+                        : encode_vol_maps(&vm[v], c, vs, vs.x, vs.r, vs.g, dmap, 4);
         if (ok && c->lazy) ok = encode_lazy_maps(&vm[v], c, vs);
         if (ok && c->dense)
             ok = encode_map(&vm[v].m[TM_Q_R], vs.q, 4, p.nx, p.ny, p.nz, vs.pitch, TX + 2 * set_xh(c->ks),
@@ -819,6 +844,19 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
     if (!c->bf) return BD3MG_OK;
     bd3mg_status st;
     if ((st = settle(c))) return st;
+    if (c->bfd) {
+        // d and H d widened in place through the free second buffer set (H g is
+        // recomputed before it is read again)
+        for (VolState &vs : c->V) {
+            const SegDev &sg = c->segs_h[vs.seg0];
+            launch_dir_to_float(vs.d, vs.d1, (long long)vs.np, c->stream);
+            launch_dir_to_float(sg.hd, sg.hd1, (long long)vs.np, c->stream);
+            CK(cudaMemcpyAsync(vs.d, vs.d1, vs.np * 4, cudaMemcpyDeviceToDevice, c->stream));
+            CK(cudaMemcpyAsync(sg.hd, sg.hd1, vs.np * 4, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        if ((st = check_launch(c))) return st;
+        c->bfd = false;
+    }
     for (VolState &vs : c->V) {
         if (!vs.g && (st = dalloc_n(c, &vs.g, vs.np))) return st;
         CK(cudaMemsetAsync(vs.g, 0, vs.np * 4, c->stream));
@@ -948,7 +986,7 @@ bd3mg_status validate_volume(bd3mg_ctx *c, const bd3mg_params &p, int vi, VolSta
     if (!p.psf) return fail(c, BD3MG_EINVAL, "volume %d: psf is NULL", vi);
     if (!(p.lambda > 0) || !(p.delta > 0) || !(p.eta >= 0) || !(p.xmin <= p.xmax))
         return fail(c, BD3MG_EINVAL, "volume %d: need lambda > 0, delta > 0, eta >= 0, xmin <= xmax", vi);
-    if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_GRADIENT)
+    if (p.precision != BD3MG_FP32 && p.precision != BD3MG_BF16_GRADIENT && p.precision != BD3MG_BF16_DIRECTIONS)
         return fail(c, BD3MG_EINVAL, "volume %d: unknown precision mode %d", vi, p.precision);
     if (p.penalty != BD3MG_PENALTY_PER_AXIS && p.penalty != BD3MG_PENALTY_JOINT_XY &&
         p.penalty != BD3MG_PENALTY_ISOTROPIC)
@@ -1000,7 +1038,7 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     if (pp[0].refresh_every < 0) return fail(c, BD3MG_EINVAL, "refresh_every must be >= 0 (0: every 256 iterations)");
     if (pp[0].curv_rows != 0 && pp[0].curv_rows != 16 && pp[0].curv_rows != 32)
         return fail(c, BD3MG_EINVAL, "curv_rows must be 0, 16 or 32");
-    if (pp[0].curv_rows == 16 && pp[0].precision == BD3MG_BF16_GRADIENT)
+    if (pp[0].curv_rows == 16 && pp[0].precision != BD3MG_FP32)
         return fail(c, BD3MG_EINVAL, "a BF16 gradient runs 32-row curvature tiles only");
     c->t32 = pp[0].curv_rows == 32;
     if (pp[0].separate_update < BD3MG_UPDATE_AUTO || pp[0].separate_update > BD3MG_UPDATE_FUSED)
@@ -1010,7 +1048,8 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
     c->refresh_every = pp[0].refresh_every > 0 ? pp[0].refresh_every : 256;
     if (pp[0].barrier_timeout_ms > 0) c->wait_ns = 1000000ull * (unsigned long long)pp[0].barrier_timeout_ms;
     c->zchunk = pp[0].zchunk;
-    c->bf = pp[0].precision == BD3MG_BF16_GRADIENT;
+    c->bf = pp[0].precision == BD3MG_BF16_GRADIENT || pp[0].precision == BD3MG_BF16_DIRECTIONS;
+    c->bfd = pp[0].precision == BD3MG_BF16_DIRECTIONS;
     for (int v = 1; v < nvol; ++v)
         if (pp[v].precision != pp[0].precision) return fail(c, BD3MG_EINVAL, "volumes must share one precision mode");
     for (int v = 1; v < nvol; ++v)
@@ -1116,6 +1155,12 @@ bd3mg_status create_impl(bd3mg_ctx *c, int nvol, const bd3mg_params *pp, const f
                                                    "curvature tiles");
             c->lazy = true;
             c->persist = true;
+        }
+        if (c->bfd) {
+            if (!can || pp[0].separate_update == BD3MG_UPDATE_SEPARATE || !c->ks->gradlazy_bd || !c->ks->curvature_bd)
+                return fail(c, BD3MG_EUNSUPPORTED, "BF16 directions run in the fused form only: no slabs, a "
+                                                   "separable PSF, the per-axis penalty, separate_update AUTO or FUSED");
+            c->lazy = true;
         }
     }
     for (int v = 0; v < nvol; ++v)
@@ -1656,8 +1701,9 @@ bd3mg_status bd3mg_get_volume(bd3mg_ctx *c, int vol, int which, float *dst, int 
     if (sst) return sst;
     const VolState &v = c->V[vol];
     const float *src = which == 0 ? v.x : which == 1 ? v.d : v.g;
-    if (c->bf && which == 2) {
-        bd3mg_status st = dir_as_float(c, v, v.gh, &src);
+    if ((c->bf && which == 2) || (c->bfd && which == 1)) {
+        bd3mg_status st =
+            dir_as_float(c, v, which == 2 ? v.gh : reinterpret_cast<const __nv_bfloat16 *>(v.d), &src);
         if (st) return st;
     }
     return copy_vol(c, v, dst, src, on_device, false);
@@ -1741,7 +1787,7 @@ bd3mg_status bd3mg_save(bd3mg_ctx *c, const char *path) {
     std::memcpy(h.magic, kCkptMagic, 8);
     h.version = 2;
     h.nvol = c->nvol;
-    h.bf = c->bf ? 1 : 0;
+    h.bf = c->bfd ? 2 : c->bf ? 1 : 0;
     h.stale = c->stale ? 1 : 0;
     h.iterations = c->iterations;
     h.since_refresh = c->since_refresh;
@@ -1772,9 +1818,10 @@ bd3mg_status bd3mg_load(bd3mg_ctx *c, const char *path) {
     f.read(reinterpret_cast<char *>(&h), sizeof(h));
     if (!f || std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 2)
         return fail(c, BD3MG_EINVAL, "%s is not a checkpoint of this library", path);
-    if (h.nvol != c->nvol || h.bf != (c->bf ? 1 : 0) || h.zone_elems != (int64_t)c->zone_elems)
+    const int prec = c->bfd ? 2 : c->bf ? 1 : 0;
+    if (h.nvol != c->nvol || h.bf != prec || h.zone_elems != (int64_t)c->zone_elems)
         return fail(c, BD3MG_EINVAL, "checkpoint has %d volume(s), precision %d; the context has %d, %d (or other slabs)",
-                    h.nvol, h.bf, c->nvol, c->bf ? 1 : 0);
+                    h.nvol, h.bf, c->nvol, prec);
     std::vector<char> buf;
     for (VolState &v : c->V) {
         int32_t dims[4];

@@ -25,6 +25,7 @@ struct KernelSet {
     launch_fn gradlazy, gradlazy_bf;                // fused-update gradient pass (FP32 / BF16 gradient)
     launch_fn curvature_t32;                        // FP32 gradient, 32-row curvature tiles
     persist_fn persist;                             // persistent fused-update iteration, FP32 gradient (cooperative launch)
+    launch_fn gradlazy_bd, curvature_bd;            // BF16 g, d, H g, H d (per-axis penalty sets only, else null)
     prep_fn prepare;               // raises the dynamic shared-memory limit of all of them
     // resident CTAs per SM of kernel kind: 0 residual, 1 gradient, 2 curvature,
     // 3 gradient (BF16 gradient), 4 curvature (BF16 gradient), 5 fused-update
@@ -51,14 +52,15 @@ int objective_occupancy(int pm);
 // bring its state to buffer set 0 (grid.y = number of volumes), then clear
 // every volume's set index and pending flag.
 void launch_flush(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, const VolRun *run,
-                  dim3 grid, cudaStream_t s, bool bf16);
+                  dim3 grid, cudaStream_t s, bool bf16, bool dir16);
 void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s);
 // Dense-PSF blur (dense.cu) with xy radius R (1..5) of the padded taps, forward
 // (H) or adjoint (H^T), over a.nitems work items.
 struct DenseArgs;
 void launch_dense(const DenseArgs &a, int R, bool adj, cudaStream_t s);
-// dst[i] = float(src[i]) for n BF16 elements.
+// dst[i] = float(src[i]) for n BF16 elements; dst[i] = bf16(src[i]) (round to nearest even).
 void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t s);
+void launch_float_to_dir(const float *src, void *dst, long long n, cudaStream_t s);
 
 int kernel_sets_r1(const KernelSet **out);
 int kernel_sets_r2(const KernelSet **out);

@@ -645,6 +645,26 @@ __device__ __forceinline__ float2 ld2(const __nv_bfloat16 *p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
 }
 
+// Global pair / single loads and stores of a direction (d, H g_S, H d_S) held
+// in FP32 or BF16 (BD3MG_BF16_DIRECTIONS); values are FP32 in registers and
+// stores round to nearest.  Loads go through ldm (PERS: coherent L2 loads).
+template <bool PERS>
+__device__ __forceinline__ float2 ldp(const float *p) { return ldm<PERS>(reinterpret_cast<const float2 *>(p)); }
+template <bool PERS>
+__device__ __forceinline__ float2 ldp(const __nv_bfloat16 *p) {
+    return __bfloat1622float2(ldm<PERS>(reinterpret_cast<const __nv_bfloat162 *>(p)));
+}
+template <bool PERS>
+__device__ __forceinline__ float lds(const float *p) { return ldm<PERS>(p); }
+template <bool PERS>
+__device__ __forceinline__ float lds(const __nv_bfloat16 *p) { return __bfloat162float(ldm<PERS>(p)); }
+__device__ __forceinline__ void stp(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+__device__ __forceinline__ void stp(__nv_bfloat16 *p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(v.x, v.y);
+}
+__device__ __forceinline__ void sts(float *p, float v) { *p = v; }
+__device__ __forceinline__ void sts(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
 // Forward z-combine of one unit of 4 staged columns with paired FP32 FMAs:
 // W = sum_t fz[t] v(zi - t), slice zi - t held in ring slot (S - t) mod NS.
 // Per component: two partial sums over the even and the odd taps, each a
@@ -1473,9 +1493,10 @@ __device__ __forceinline__ void pen_quad(float vg, float vd, float kl2, float *a
 // wait ran out; k_curvature runs item blockIdx.x, the persistent iteration
 // (PERS) every item a CTA takes from the pass's queue.
 // ---------------------------------------------------------------------------
-template <int R, int RZ, bool BF, int PM, int RPT_, bool PERS>
+template <int R, int RZ, bool BF, int PM, int RPT_, bool PERS, bool BD = false>
 __device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
+    using DT = typename std::conditional<BD, __nv_bfloat16, float>::type;  // storage of d, H g_S, H d_S
     using CR = CurvRing<R, RZ, sizeof(T), RPT_>;
     using G = typename CR::C;
     constexpr int PF = CR::PF;                        // slices in flight ahead of the consumer
@@ -1494,15 +1515,18 @@ __device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
     const VolDev &V = a.vols[sg.vol];
     const int nx = V.nx, ny = V.ny, nz = V.nz, pitch = V.pitch;
     const long long plane = V.plane;
-    const float *xg = V.x, *dg = V.d;
+    const float *xg = V.x;
+    const DT *dg = reinterpret_cast<const DT *>(V.d);
     // fused-update iteration: the volume's state may live in its second buffer set
     const bool set1 = (a.mode & M_PAR) && a.sh->run && __ldcg(&a.sh->run[sg.vol].par) != 0;
     if (set1) {
         xg = V.x1;
-        dg = V.d1;
+        dg = reinterpret_cast<const DT *>(V.d1);
         sg.hg = sg.hg1;
         sg.hd = sg.hd1;
     }
+    DT *const zhg = reinterpret_cast<DT *>(sg.hg);
+    const DT *const zhd = reinterpret_cast<const DT *>(sg.hd);
     const float delta2 = V.delta2, kl2 = V.kl2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int pen_lo = sg.z0 - 1, pen_hi = sg.z1;
@@ -1603,27 +1627,28 @@ __device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
 #pragma unroll
         for (int k = 0; k <= RPT; ++k) xa[k] = da[k] = make_float2(0.f, 0.f);
         if (pen) {
-            const float *xp = xg + (long long)zo * plane, *dp = dg + (long long)zo * plane;
+            const float *xp = xg + (long long)zo * plane;
+            const DT *dp = dg + (long long)zo * plane;
             const long long zn = zo + 1 < nz ? plane : 0;
             const bool dlo = zo >= sg.z0, dhi = zo + 1 < sg.z1;     // d_S at zo, at zo + 1
 #pragma unroll
             for (int k = 0; k <= RPT; ++k) {
                 xa[k] = ldm<PERS>(reinterpret_cast<const float2 *>(xp + orow[k]));
-                if (dlo) da[k] = ldm<PERS>(reinterpret_cast<const float2 *>(dp + orow[k]));
+                if (dlo) da[k] = ldp<PERS>(dp + orow[k]);
             }
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 xev[k] = ldm<PERS>(xp + oe[k]);
                 xz[k] = ldm<PERS>(reinterpret_cast<const float2 *>(xp + zn + orow[k]));
-                if (dlo) dev[k] = ldm<PERS>(dp + oe[k]);
-                if (dhi) dz[k] = ldm<PERS>(reinterpret_cast<const float2 *>(dp + zn + orow[k]));
+                if (dlo) dev[k] = lds<PERS>(dp + oe[k]);
+                if (dhi) dz[k] = ldp<PERS>(dp + zn + orow[k]);
             }
         }
         const long long zz = (long long)(zo - sg.hz0) * plane;       // slice zo in the zone buffers
         if (emit && v00) {
 #pragma unroll
             for (int k = 0; k < RPT; ++k)
-                if (rok[k]) hd[k] = ldm<PERS>(reinterpret_cast<const float2 *>(sg.hd + zz + orow[k]));
+                if (rok[k]) hd[k] = ldp<PERS>(zhd + zz + orow[k]);
         }
         // half-quadratic terms and g, d products of the thread's voxels at zo
         auto terms = [&]() {
@@ -1733,15 +1758,15 @@ __device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
         if constexpr (RPT == 2) ypass_pair2<R>(T1, yo, c, fyc, hg[0], hg[RPT - 1]);
         else hg[0] = ypass_pair<R>(T1, yo, c, fyc);
         if (v00) {
-            float *hgz = sg.hg + zz;
+            DT *hgz = zhg + zz;
 #pragma unroll
             for (int k = 0; k < RPT; ++k) {
                 if (!rok[k]) continue;
                 if (hg_given) {
-                    hg[k] = ldm<PERS>(reinterpret_cast<const float2 *>(hgz + orow[k]));
+                    hg[k] = ldp<PERS>(hgz + orow[k]);
                 } else {
-                    if (c1ok) *reinterpret_cast<float2 *>(hgz + orow[k]) = hg[k];
-                    else hgz[orow[k]] = hg[k].x;
+                    if (c1ok) stp(hgz + orow[k], hg[k]);
+                    else sts(hgz + orow[k], hg[k].x);
                 }
                 acc[3] = fmaf(hg[k].x, hg[k].x, acc[3]);
                 acc[4] = fmaf(hg[k].x, hd[k].x, acc[4]);
@@ -1777,9 +1802,9 @@ __device__ __forceinline__ bool curvature_item(const KArgs &a, int item) {
     return true;
 }
 
-template <int R, int RZ, bool BF, int PM, int RPT_ = (BF ? 2 : 1)>
+template <int R, int RZ, bool BF, int PM, int RPT_ = (BF ? 2 : 1), bool BD = false>
 __global__ void __launch_bounds__(NT, CurvRing<R, RZ, BF ? 2 : 4, RPT_>::CTAS) k_curvature(KArgs a) {
-    curvature_item<R, RZ, BF, PM, RPT_, false>(a, blockIdx.x);
+    curvature_item<R, RZ, BF, PM, RPT_, false, BD>(a, blockIdx.x);
 }
 
 }  // namespace bd3mg

@@ -27,6 +27,25 @@ template <int R, int RZ, int PM>
 void launch_curvature_t32(const KArgs &a, cudaStream_t s) {
     k_curvature<R, RZ, false, PM, 2><<<a.nitems, NT, Smem<R, RZ>::curvature_t32, s>>>(a);
 }
+// BF16 directions (BD3MG_BF16_DIRECTIONS): compiled for the per-axis penalty only
+template <int R, int RZ>
+void launch_gradlazy_bd(const KArgs &a, cudaStream_t s) {
+    k_gradlazy<R, RZ, true, 0, true><<<a.nitems, NT, LazyGeo<R, RZ>::SMEM, s>>>(a);
+}
+template <int R, int RZ>
+void launch_curvature_bd(const KArgs &a, cudaStream_t s) {
+    k_curvature<R, RZ, true, 0, 2, true><<<a.nitems, NT, Smem<R, RZ>::curvature_bf, s>>>(a);
+}
+template <int R, int RZ, int PM>
+constexpr launch_fn gradlazy_bd_fn() {
+    if constexpr (PM == 0) return &launch_gradlazy_bd<R, RZ>;
+    else return nullptr;
+}
+template <int R, int RZ, int PM>
+constexpr launch_fn curvature_bd_fn() {
+    if constexpr (PM == 0) return &launch_curvature_bd<R, RZ>;
+    else return nullptr;
+}
 template <int R, int RZ, bool BF>
 constexpr size_t persist_smem() {
     return LazyGeo<R, RZ>::SMEM > (BF ? Smem<R, RZ>::curvature_bf : Smem<R, RZ>::curvature)
@@ -68,6 +87,14 @@ cudaError_t prepare_set() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_persist<R, RZ, false, PM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)persist_smem<R, RZ, false>());
+    if constexpr (PM == 0) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_gradlazy<R, RZ, true, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)LazyGeo<R, RZ>::SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_curvature<R, RZ, true, 0, 2, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Smem<R, RZ>::curvature_bf);
+    }
     return e;
 }
 
@@ -97,4 +124,5 @@ int occupancy_of(int kind) {
      &bd3mg::launch_curvature<R, RZ, true, PM>, &bd3mg::launch_gradlazy<R, RZ, false, PM>,                  \
      &bd3mg::launch_gradlazy<R, RZ, true, PM>, &bd3mg::launch_curvature_t32<R, RZ, PM>,                     \
      &bd3mg::launch_persist<R, RZ, false, PM>,                                                              \
+     bd3mg::gradlazy_bd_fn<R, RZ, PM>(), bd3mg::curvature_bd_fn<R, RZ, PM>(),                                \
      &bd3mg::prepare_set<R, RZ, PM>, &bd3mg::occupancy_of<R, RZ, PM>}

@@ -30,7 +30,9 @@
 namespace bd3mg {
 
 // Shared memory of k_gradlazy: rings of PREF + 1 slices for r, H g and H d
-// (r is combined into r + H n in place), a ring of three slices of the updated
+// (r is combined into r + H n in place; with BF16 directions the H g and H d
+// slots hold BF16 tiles of their own geometry, inside the same bytes), a ring
+// of three slices of the updated
 // iterate x + n over the tile and a one-voxel halo (rows -1 .. 32 of width
 // XTW: column col at index col + 2, so the thread's column pair is 8-byte
 // aligned), the x-pass output and the PSF rows.
@@ -49,18 +51,27 @@ struct LazyGeo {
 // gradlazy_item processes work item `item` and returns false when a bounded
 // wait ran out; k_gradlazy runs item blockIdx.x, the persistent iteration
 // (PERS) every item a CTA takes from the pass's queue.
-template <int R, int RZ, bool BF, int PM, bool PERS>
+//
+// BD (BD3MG_BF16_DIRECTIONS, with BF): d, H g and H d are stored as BF16.  Their
+// staged tiles start 8 columns left of the tile (a TMA box of 16-bit elements
+// must start on a 16-byte boundary), HOFF columns left of r's.
+template <int R, int RZ, bool BF, int PM, bool PERS, bool BD = false>
 __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
     using G = Geo<R, RZ, TY_A>;
     using T = typename std::conditional<BF, __nv_bfloat16, float>::type;   // storage of g
+    using DT = typename std::conditional<BD, __nv_bfloat16, float>::type;  // storage of d, H g, H d
     constexpr int KZ = G::KZ, NS = LazyGeo<R, RZ>::NS, BX = G::BX, BY = G::BY, SLOT = G::SLOT, XH = G::XH;
+    // staged H g / H d tiles: halo XHB columns, width BXB, SLOTB elements per slot (128-byte multiple)
+    constexpr int XHB = BD ? 8 : XH, BXB = TX + 2 * XHB, HOFF = XHB - XH;
+    constexpr int SLOTB = BD ? ((BXB * BY * 2 + 127) / 128 * 128) / 2 : SLOT;
+    static_assert(SLOTB * sizeof(DT) <= SLOT * sizeof(float), "the H g / H d slots must fit the FP32 layout");
     extern __shared__ __align__(128) float smem[];
     float *sr = smem;                                    // NS * SLOT: r, then r + H n in place
-    float *shg = sr + NS * SLOT;                         // NS * SLOT: H g
-    float *shd = shg + NS * SLOT;                        // NS * SLOT: H d
+    DT *shg = reinterpret_cast<DT *>(sr + NS * SLOT);   // NS * SLOTB: H g
+    DT *shd = shg + NS * SLOTB;                          // NS * SLOTB: H d
     using LG = LazyGeo<R, RZ>;
     constexpr int XTW = LG::XTW, XTS = LG::XTS;
-    float *xt = shd + NS * SLOT;                         // 3 * XTS: x + n of slices z (slot (z - zo0 + 1) mod 3)
+    float *xt = sr + 3 * NS * SLOT;                      // 3 * XTS: x + n of slices z (slot (z - zo0 + 1) mod 3)
     float *T1 = xt + 3 * XTS;
     float *CF = T1 + BY * TX;
     uint64_t *bar = reinterpret_cast<uint64_t *>(CF + G::CF_FLOATS);
@@ -87,7 +98,8 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
         u1 = (float)a.u[2 * sg.slot + 1];
     }
     // source set (read) and destination set (written; the same when nothing is applied)
-    const float *xs = set1 ? V.x1 : V.x, *ds = set1 ? V.d1 : V.d;
+    const float *xs = set1 ? V.x1 : V.x;
+    const DT *ds = reinterpret_cast<const DT *>(set1 ? V.d1 : V.d);
     const T *gs;
     T *gd;
     if constexpr (BF) {
@@ -98,8 +110,9 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
         gd = (set1 != apply) ? V.g1 : V.g;
     }
     const bool dset1 = set1 != apply;
-    float *xd = dset1 ? V.x1 : V.x, *dd = dset1 ? V.d1 : V.d, *rd = dset1 ? V.r1 : V.r;
-    float *hdd = dset1 ? sg.hd1 : sg.hd;
+    float *xd = dset1 ? V.x1 : V.x, *rd = dset1 ? V.r1 : V.r;
+    DT *dd = reinterpret_cast<DT *>(dset1 ? V.d1 : V.d);
+    DT *hdd = reinterpret_cast<DT *>(dset1 ? sg.hd1 : sg.hd);
 
     const int zbeg = it.zo0 - RZ, zend = it.zo1 + RZ;
     stage_coeffs<G>(CF, V, zbeg, zend - zbeg);
@@ -116,16 +129,16 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(mhd)) : "memory");
         }
     }
-    const uint32_t nb = (uint32_t)(BX * BY * sizeof(float));
+    const uint32_t nb = (uint32_t)(BX * BY * sizeof(float)), nbh = (uint32_t)(BXB * BY * sizeof(DT));
     const int bx0 = it.tx0 - XH, by0 = it.ty0 - R;
     // slice z of r (and of H g, H d when an update is applied) into ring slot s
     auto issue = [&](int z, int s) {
         if (tid == 0 && z >= rlo && z < rhi) {
-            mbar_expect_tx(bar + s, apply ? 3u * nb : nb);
+            mbar_expect_tx(bar + s, apply ? nb + 2u * nbh : nb);
             tma_load_3d(sr + s * SLOT, mr, bx0, by0, z, bar + s);
             if (apply) {
-                tma_load_3d(shg + s * SLOT, mhg, bx0, by0, z, bar + s);
-                tma_load_3d(shd + s * SLOT, mhd, bx0, by0, z, bar + s);
+                tma_load_3d(shg + s * SLOTB, mhg, it.tx0 - XHB, by0, z, bar + s);
+                tma_load_3d(shd + s * SLOTB, mhd, it.tx0 - XHB, by0, z, bar + s);
             }
         }
     };
@@ -184,11 +197,24 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
             if (ok) par ^= 1u << sl;
             if (ok && apply) {
                 // r + H n over the staged tile, in place
-                const float4 *h4 = reinterpret_cast<const float4 *>(shg + sl * SLOT);
-                const float4 *d4 = reinterpret_cast<const float4 *>(shd + sl * SLOT);
+                const DT *hgt = shg + sl * SLOTB, *hdt = shd + sl * SLOTB;
                 float4 *r4 = reinterpret_cast<float4 *>(rs);
                 for (int i = tid; i < BX * BY / 4; i += NT) {
-                    const float4 h = h4[i], d = d4[i];
+                    float4 h, d;
+                    if constexpr (BD) {
+                        const int row = i / (BX / 4), e = row * BXB + 4 * (i - row * (BX / 4)) + HOFF;
+                        const uint2 hq = *reinterpret_cast<const uint2 *>(hgt + e);
+                        const uint2 dq = *reinterpret_cast<const uint2 *>(hdt + e);
+                        const float2 h0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hq.x));
+                        const float2 h1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&hq.y));
+                        const float2 d0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&dq.x));
+                        const float2 d1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&dq.y));
+                        h = make_float4(h0.x, h0.y, h1.x, h1.y);
+                        d = make_float4(d0.x, d0.y, d1.x, d1.y);
+                    } else {
+                        h = reinterpret_cast<const float4 *>(hgt)[i];
+                        d = reinterpret_cast<const float4 *>(hdt)[i];
+                    }
                     float4 r = r4[i];
                     r.x += fmaf(-u0, h.x, u1 * d.x);
                     r.y += fmaf(-u0, h.y, u1 * d.y);
@@ -218,10 +244,10 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
                 if (r1ok) bx[1] = ldm<PERS>(reinterpret_cast<const float2 *>(xs + zoff + o1));
                 if (apply) {
                     bg[0] = ld2(gs + zoff + o0);
-                    bd[0] = ldm<PERS>(reinterpret_cast<const float2 *>(ds + zoff + o0));
+                    bd[0] = ldp<PERS>(ds + zoff + o0);
                     if (r1ok) {
                         bg[1] = ld2(gs + zoff + o1);
-                        bd[1] = ldm<PERS>(reinterpret_cast<const float2 *>(ds + zoff + o1));
+                        bd[1] = ldp<PERS>(ds + zoff + o1);
                     }
                 }
             }
@@ -229,7 +255,7 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
                 hxv = ldm<PERS>(xs + zoff + hoff);
                 if (apply) {
                     hgv = to_f(gs[zoff + hoff]);
-                    hdv = ldm<PERS>(ds + zoff + hoff);
+                    hdv = lds<PERS>(ds + zoff + hoff);
                 }
             }
         }
@@ -244,24 +270,25 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
                     if (c1ok) acc[0] = fmaf(0.5f * rb.y, rb.y, acc[0]);
                 }
                 if (apply) {
-                    const float *hgs = shg + sl * SLOT + ci, *hds = shd + sl * SLOT + ci;
-                    const float2 ga = ld2(hgs), gb = ld2(hgs + BX), da = ld2(hds), db = ld2(hds + BX);
+                    const int cih = (yo + R) * BXB + XHB + c;                 // staged index of (yo, c), H tiles
+                    const DT *hgs = shg + sl * SLOTB + cih, *hds = shd + sl * SLOTB + cih;
+                    const float2 ga = ld2(hgs), gb = ld2(hgs + BXB), da = ld2(hds), db = ld2(hds + BXB);
                     const float2 na = make_float2(fmaf(-u0, ga.x, u1 * da.x), fmaf(-u0, ga.y, u1 * da.y));
                     const float2 nb2 = make_float2(fmaf(-u0, gb.x, u1 * db.x), fmaf(-u0, gb.y, u1 * db.y));
                     const long long zoff = (long long)zi * plane;   // the zone of a whole volume starts at 0
                     if (c1ok) {
                         *reinterpret_cast<float2 *>(rd + zoff + o0) = ra;
-                        *reinterpret_cast<float2 *>(hdd + zoff + o0) = na;
+                        stp(hdd + zoff + o0, na);
                         if (r1ok) {
                             *reinterpret_cast<float2 *>(rd + zoff + o1) = rb;
-                            *reinterpret_cast<float2 *>(hdd + zoff + o1) = nb2;
+                            stp(hdd + zoff + o1, nb2);
                         }
                     } else {
                         rd[zoff + o0] = ra.x;
-                        hdd[zoff + o0] = na.x;
+                        sts(hdd + zoff + o0, na.x);
                         if (r1ok) {
                             rd[zoff + o1] = rb.x;
-                            hdd[zoff + o1] = nb2.x;
+                            sts(hdd + zoff + o1, nb2.x);
                         }
                     }
                 }
@@ -290,17 +317,17 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
                 const long long zoff = (long long)zt * plane;
                 if (c1ok) {
                     *reinterpret_cast<float2 *>(xd + zoff + o0) = xn[0];
-                    *reinterpret_cast<float2 *>(dd + zoff + o0) = nn[0];
+                    stp(dd + zoff + o0, nn[0]);
                     if (r1ok) {
                         *reinterpret_cast<float2 *>(xd + zoff + o1) = xn[1];
-                        *reinterpret_cast<float2 *>(dd + zoff + o1) = nn[1];
+                        stp(dd + zoff + o1, nn[1]);
                     }
                 } else {
                     xd[zoff + o0] = xn[0].x;
-                    dd[zoff + o0] = nn[0].x;
+                    sts(dd + zoff + o0, nn[0].x);
                     if (r1ok) {
                         xd[zoff + o1] = xn[1].x;
-                        dd[zoff + o1] = nn[1].x;
+                        sts(dd + zoff + o1, nn[1].x);
                     }
                 }
             }
@@ -384,9 +411,9 @@ __device__ __forceinline__ bool gradlazy_item(const KArgs &a, int item) {
     return true;
 }
 
-template <int R, int RZ, bool BF, int PM>
+template <int R, int RZ, bool BF, int PM, bool BD = false>
 __global__ void __launch_bounds__(NT, 2) k_gradlazy(KArgs a) {
-    gradlazy_item<R, RZ, BF, PM, false>(a, blockIdx.x);
+    gradlazy_item<R, RZ, BF, PM, false, BD>(a, blockIdx.x);
 }
 
 }  // namespace bd3mg

@@ -137,9 +137,30 @@ __global__ void __launch_bounds__(NT, 6) k_objective(KArgs a) {
 // k_flush over plain volumes (blockIdx.y = volume's segment): a pending update
 // is applied with k_update's arithmetic, and the state moves from the volume's
 // current buffer set to set 0 (x, d, r, H d; g too when it was in set 1).
-// k_clear_pending then marks every volume settled.
+// k_clear_pending then marks every volume settled.  BD: d, H g, H d in BF16
+// (BD3MG_BF16_DIRECTIONS), rounded as k_gradlazy rounds them.
 // ---------------------------------------------------------------------------
-template <bool BF>
+__device__ __forceinline__ float4 bf4_to_f4(uint2 q) {
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ uint2 f4_to_bf4(float4 v) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y), b = __floats2bfloat162_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<const unsigned int *>(&a), *reinterpret_cast<const unsigned int *>(&b));
+}
+template <bool BD>
+__device__ __forceinline__ float4 ld_dir4(const float *base, long long i) {
+    if constexpr (BD) return bf4_to_f4(reinterpret_cast<const uint2 *>(base)[i]);
+    else return reinterpret_cast<const float4 *>(base)[i];
+}
+template <bool BD>
+__device__ __forceinline__ void st_dir4(float *base, long long i, float4 v) {
+    if constexpr (BD) reinterpret_cast<uint2 *>(base)[i] = f4_to_bf4(v);
+    else reinterpret_cast<float4 *>(base)[i] = v;
+}
+
+template <bool BF, bool BD>
 __global__ void __launch_bounds__(NT) k_flush(const VolDev *vols, const SegDev *segs, const int *seg_list,
                                               const double *u, const VolRun *run) {
     const SegDev sg = segs[seg_list[blockIdx.y]];
@@ -149,12 +170,10 @@ __global__ void __launch_bounds__(NT) k_flush(const VolDev *vols, const SegDev *
     const float u0 = apply ? (float)u[2 * sg.slot] : 0.f, u1 = apply ? (float)u[2 * sg.slot + 1] : 0.f;
     const long long n4 = ((long long)v.nz * v.plane) >> 2, stride = (long long)gridDim.x * NT;
     const float4 *xs = reinterpret_cast<const float4 *>(set1 ? v.x1 : v.x);
-    const float4 *ds = reinterpret_cast<const float4 *>(set1 ? v.d1 : v.d);
+    const float *ds = set1 ? v.d1 : v.d;
     const float4 *rs = reinterpret_cast<const float4 *>(set1 ? v.r1 : v.r);
-    const float4 *hgs = reinterpret_cast<const float4 *>(set1 ? sg.hg1 : sg.hg);
-    const float4 *hds = reinterpret_cast<const float4 *>(set1 ? sg.hd1 : sg.hd);
-    float4 *xd = reinterpret_cast<float4 *>(v.x), *dd = reinterpret_cast<float4 *>(v.d);
-    float4 *rd = reinterpret_cast<float4 *>(v.r), *hdd = reinterpret_cast<float4 *>(sg.hd);
+    const float *hgs = set1 ? sg.hg1 : sg.hg, *hds = set1 ? sg.hd1 : sg.hd;
+    float4 *xd = reinterpret_cast<float4 *>(v.x), *rd = reinterpret_cast<float4 *>(v.r);
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
         float4 g;
         if constexpr (BF) {
@@ -167,9 +186,9 @@ __global__ void __launch_bounds__(NT) k_flush(const VolDev *vols, const SegDev *
             g = reinterpret_cast<const float4 *>(set1 ? v.g1 : v.g)[i];
             if (set1) reinterpret_cast<float4 *>(v.g)[i] = g;
         }
-        float4 x = xs[i], d = ds[i], r = rs[i], hd = hds[i];
+        float4 x = xs[i], d = ld_dir4<BD>(ds, i), r = rs[i], hd = ld_dir4<BD>(hds, i);
         if (apply) {
-            const float4 hg = hgs[i];
+            const float4 hg = ld_dir4<BD>(hgs, i);
             float4 nd, nh;
             nd.x = fmaf(-u0, g.x, u1 * d.x);
             nd.y = fmaf(-u0, g.y, u1 * d.y);
@@ -185,9 +204,9 @@ __global__ void __launch_bounds__(NT) k_flush(const VolDev *vols, const SegDev *
             hd = nh;
         }
         xd[i] = x;
-        dd[i] = d;
+        st_dir4<BD>(v.d, i, d);
         rd[i] = r;
-        hdd[i] = hd;
+        st_dir4<BD>(sg.hd, i, hd);
     }
 }
 
@@ -199,9 +218,10 @@ __global__ void k_clear_pending(VolRun *run, int nvol) {
 }
 
 void launch_flush(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u, const VolRun *run,
-                  dim3 grid, cudaStream_t s, bool bf16) {
-    if (bf16) k_flush<true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
-    else k_flush<false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+                  dim3 grid, cudaStream_t s, bool bf16, bool dir16) {
+    if (dir16) k_flush<true, true><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+    else if (bf16) k_flush<true, false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
+    else k_flush<false, false><<<grid, NT, 0, s>>>(vols, segs, seg_list, u, run);
 }
 
 void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s) { k_clear_pending<<<1, 128, 0, s>>>(run, nvol); }
@@ -209,6 +229,10 @@ void launch_clear_pending(VolRun *run, int nvol, cudaStream_t s) { k_clear_pendi
 __global__ void __launch_bounds__(NT) k_dir_to_float(const __nv_bfloat16 *src, float *dst, long long n) {
     for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
         dst[i] = __bfloat162float(src[i]);
+}
+__global__ void __launch_bounds__(NT) k_float_to_dir(const float *src, __nv_bfloat16 *dst, long long n) {
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        dst[i] = __float2bfloat16_rn(src[i]);
 }
 
 void launch_update(const VolDev *vols, const SegDev *segs, const int *seg_list, const double *u,
@@ -235,6 +259,11 @@ void launch_dir_to_float(const void *src, float *dst, long long n, cudaStream_t 
     const long long blocks = std::min<long long>(4096, (n + NT - 1) / NT);
     k_dir_to_float<<<(unsigned)std::max<long long>(1, blocks), NT, 0, s>>>(
         static_cast<const __nv_bfloat16 *>(src), dst, n);
+}
+
+void launch_float_to_dir(const float *src, void *dst, long long n, cudaStream_t s) {
+    const long long blocks = std::min<long long>(4096, (n + NT - 1) / NT);
+    k_float_to_dir<<<(unsigned)std::max<long long>(1, blocks), NT, 0, s>>>(src, static_cast<__nv_bfloat16 *>(dst), n);
 }
 
 }  // namespace bd3mg
