@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--ws-epochs", type=int, default=1)
     ap.add_argument("--ws-train-seconds", type=float, default=60.0, help="warm start: training time budget")
     ap.add_argument("--no-warm-start", action="store_true")
-    ap.add_argument("--profile-case", choices=["plain512", "unet-train", "dense256"], default=None,
+    ap.add_argument("--profile-case", choices=["plain512", "unet-train", "unet-infer", "conv3", "dense256"], default=None,
                     help="run a small fixed workload for an ncu capture and exit")
     return ap.parse_args()
 
@@ -1005,6 +1005,8 @@ def profile_case(name):
     plain512: plain FP32 context on a 512x512x128 volume (uniform random y, PSF 9x9x7 with the
       0.5 -> 3.0 ramp), 3 iterations, 20 more, then one per-launch profiled iteration.
     unet-train: the U-Net (16/32/64/128) on 8 crops of 128x128x48, 3 training steps of batch 4.
+    unet-infer: the U-Net (16/32/64/128, He-initialised) predicting the 512x512x128 volume twice.
+    conv3: one 16 -> 16 channel 3x3x3 convolution on a 256x256x32 grid, three times.
     dense256: plain FP32 context on the 256x256x24 volume with the 11x11x21 rotated Gaussian
       PSF (dense path), 3 iterations, 10 more, then one per-launch profiled iteration."""
     import torch
@@ -1033,6 +1035,27 @@ def profile_case(name):
             torch.cuda.synchronize()
             print("iterations/s", 20 / (time.perf_counter() - t0))
             print(s.profile_iteration())
+    elif name == "conv3":
+        from paper_2002_02328_gb300 import unet_binding as ub
+        rng = np.random.default_rng(0)
+        x = torch.from_numpy(rng.normal(size=(1, 32, 256, 256, 16)).astype(np.float32)).to(torch.bfloat16).cuda()
+        w = torch.from_numpy(rng.normal(0, 0.05, size=(27, 16, 16)).astype(np.float32)).to(torch.bfloat16).cuda()
+        b = torch.zeros(16, device="cuda")
+        for _ in range(3):
+            out = ub.conv3(x, w, b, relu=True)
+        torch.cuda.synchronize()
+        print("ok", float(out.float().sum()))
+    elif name == "unet-infer":
+        from paper_2002_02328_gb300 import unet_binding as ub, warmstart as ws
+        widths = (16, 32, 64, 128)
+        prob = synth.workload_mixed(seed=0)
+        y = torch.from_numpy(prob.y).cuda()
+        with ub.UNet(widths, 2) as net:
+            net.set_params(ub.he_init(widths, 2, 0))
+            for _ in range(2):
+                ws.predict(net, y, ws.C2_SXY)
+            torch.cuda.synchronize()
+        print("ok")
     else:
         from paper_2002_02328_gb300 import unet_binding as ub, warmstart as ws
         widths = (16, 32, 64, 128)

@@ -100,7 +100,9 @@ bd3mg_status bd3mg_unet_train_step(bd3mg_unet *net, int B, int D, int H, int W, 
  *   bd3mg_unet_conv3_wgrad: dw[t][co][ci] = sum_v dz[v][co] x[v + s_t][ci]
  *     (FP32 out, DEVICE).
  *   bd3mg_unet_up: out (grid [B][2D][2H][2W]) = up(x) + bias.
- * cin, cout multiples of 16; cin <= 256, cout <= 128 (wgrad), cout <= 256. */
+ * cin, cout multiples of 16; cin <= 256, cout <= 128 (wgrad), cout <= 256.
+ * Each call synchronises the stream and returns BD3MG_ETIMEOUT if one of the
+ * kernel's bounded waits (TMA copies, MMA completion) ran out. */
 bd3mg_status bd3mg_unet_conv3(int B, int D, int H, int W, const void *x, int ldx, int cin, const void *w, int cout,
                               const float *bias, int relu, const void *mask, int ldm, void *out, int ldo,
                               void *stream);
@@ -108,6 +110,17 @@ bd3mg_status bd3mg_unet_conv3_wgrad(int B, int D, int H, int W, const void *x, i
                                     int ldz, int cout, float *dw, void *stream);
 bd3mg_status bd3mg_unet_up(int B, int D, int H, int W, const void *x, int ldx, int cin, const void *w, int cout,
                            const float *bias, void *out, int ldo, void *stream);
+
+/* Process-wide choice of the 3x3x3 convolution kernel (not thread-safe; set it
+ * before launching work).  1 (the default): a convolution whose operands fit
+ * (cout a multiple of 16 up to 64, cin a multiple of 16, the 27 taps' weights
+ * and a ring of six staged input slices within 200 KB of shared memory, x
+ * 16-byte aligned) runs the TMA-staged kernel, which marches along z, copies
+ * each input slice of an 8 x 16 column once and reads the 27 taps from the
+ * staged slices; the others run the row-gather implicit GEMM.  0: the row-gather implicit GEMM for every convolution.  Both
+ * issue the same MMA sequence (tap-major, then channel), so their outputs are
+ * the same bits.  Returns the previous setting. */
+int bd3mg_unet_set_tma_conv(int enable);
 
 const char *bd3mg_unet_error_string(bd3mg_unet *net);
 void bd3mg_unet_destroy(bd3mg_unet *net);

@@ -43,6 +43,24 @@ bool encode_map(CUtensorMap *m, const void *base, int esize, int nx, int ny, int
 }
 
 
+// 5-D tile map over channels-last BF16 activations [B][D][H][W][ld] reading
+// channels [0, C) of each row: box 8 channels x bx x by x bz x 1, zero fill
+// outside the volume (the zero padding of a 3x3x3 convolution).
+bool encode_act_map(CUtensorMap *m, const void *base, int C, int ld, int W, int H, int D, int B, int bx, int by,
+                    int bz) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t row = (cuuint64_t)ld * 2;
+    cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    cuuint64_t strides[4] = {row, row * W, row * W * H, row * W * H * D};
+    cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
+    cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void *>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // Rank-1 factoring of each depth's PSF in FP64: with m_x(a) = sum_{b,c} h,
 // m_y, m_z the marginals and S = sum h, a rank-1 tensor satisfies
 // h = m_x m_y m_z / S^2.  Factors: fx = m_x / S, fy = m_y / S, fz = m_z,

@@ -26,6 +26,11 @@ struct NvtxRange {
 // elements: dims (nx, ny, nz), row pitch in elements (pitch*esize a multiple
 // of 16), box (bx, by, 1), zero fill outside the volume.
 bool encode_map(CUtensorMap *m, const void *base, int esize, int nx, int ny, int nz, int pitch, int bx, int by);
+// 5-D tile map over channels-last BF16 activations [B][D][H][W][ld] (ld a
+// multiple of 8) reading channels [0, C): box 8 channels x bx x by x bz x 1,
+// zero fill outside the volume.
+bool encode_act_map(CUtensorMap *m, const void *base, int C, int ld, int W, int H, int D, int B, int bx, int by,
+                    int bz);
 
 constexpr int kMaxPsfExtent = 11;        // largest PSF extent the compiled kernels cover
 

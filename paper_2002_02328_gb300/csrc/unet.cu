@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <vector>
 
 #include "../../include/bd3mg_unet.h"
+#include "plan.h"
 #include "unet_kernels.cuh"
 
 using namespace bd3mg::unet;
@@ -95,6 +97,8 @@ int L_up(const bd3mg_unet *n, int l) { return 2 * n->L + 3 * (n->L - 2 - l); }
 int L_dec(const bd3mg_unet *n, int l, int b) { return L_up(n, l) + 1 + b; }
 int L_head(const bd3mg_unet *n) { return (int)n->layers.size() - 1; }
 
+constexpr size_t kConv3SmemMax = 200 * 1024;   // shared memory of k_conv3 at most (weights + slice ring)
+
 size_t gemm_smem(int KC, int N) { return (size_t)STAGES * (GM * KC * 2 + (size_t)N * KC * 2) + STAGES * 8 + 16; }
 size_t wgrad_smem(int Cin) { return WSTAGES * ((size_t)GM * KV * 2 + (size_t)Cin * KV * 2) + WSTAGES * 8 + 16; }
 
@@ -105,6 +109,8 @@ cudaError_t prepare_kernels() {
     res = cudaFuncSetAttribute(k_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem(64, 256));
     if (res == cudaSuccess)
         res = cudaFuncSetAttribute(k_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_smem(256));
+    if (res == cudaSuccess)
+        res = cudaFuncSetAttribute(k_conv3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConv3SmemMax);
     done = true;
     return res;
 }
@@ -113,12 +119,62 @@ cudaError_t prepare_kernels() {
 // taps of K channels as fit in 64 (never more than T taps)
 int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
+// The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
+// multiple of 16 up to 64, K a multiple of 16, the 27 taps' weights and the
+// ring of input slices within kConv3SmemMax, rows 16-byte aligned.
+// Process-wide switch (bd3mg_unet_set_tma_conv).
+bool g_tma_conv = true;
+
+bool conv3_fits(const bf16 *A, int lda, int K, int N) {
+    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 64 && K % 16 == 0 && K >= 16 && lda % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_smem(K, N) <= kConv3SmemMax;
+}
+
+cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt, int N,
+                      const float *bias, int relu, const bf16 *mask, int ldm, bf16 *out, int ldo, int *status) {
+    CUtensorMap map;
+    if (!bd3mg::encode_act_map(&map, A, K, lda, W, H, D, B, C3_BX, C3_BY, 1)) return cudaErrorInvalidValue;
+    Conv3Args a{};
+    a.B = B; a.D = D; a.H = H; a.W = W;
+    a.K = K; a.N = N; a.Wt = Wt;
+    a.bias = bias; a.relu = relu; a.mask = mask; a.ldm = ldm;
+    a.out = out; a.ldo = ldo; a.status = status;
+    a.tiles_x = (W + C3_TX - 1) / C3_TX;
+    a.tiles_y = (H + C3_TY - 1) / C3_TY;
+    const size_t smem = conv3_smem(K, N);
+    // one wave of CTAs looping over the work items: as many per SM as shared
+    // memory and tensor memory (C3_NACC accumulators of N columns) hold
+    int dev = 0, sms = 0, smem_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e != cudaSuccess) return e;
+    const int need = C3_NACC * N;
+    const int ncols = need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+    const int per_sm = std::max(1, std::min({(int)(smem_sm / (smem + 1024)), 512 / ncols, 8}));
+    const long long slots = (long long)per_sm * sms;
+    // z-chunks: about four items per resident CTA, at least 8 output depths each
+    const long long cols = (long long)B * a.tiles_x * a.tiles_y;
+    const long long want = std::max<long long>(1, (4 * slots + cols - 1) / cols);
+    a.zc = std::max(std::min(8, D), (int)((D + want - 1) / want));
+    a.nchunks = (D + a.zc - 1) / a.zc;
+    const long long nitems = cols * a.nchunks;
+    if (nitems > INT_MAX) return cudaErrorInvalidValue;
+    a.nitems = (int)nitems;
+    const long long grid = std::min<long long>(a.nitems, slots);
+    k_conv3<<<(unsigned)std::max<long long>(1, grid), C3_THREADS, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
 // Launch one implicit GEMM (see GemmArgs).  UPFWD launches 8 grid rows (taps).
+// A 3x3x3 convolution whose operands fit runs k_conv3 instead.
 cudaError_t gemm(cudaStream_t s, int mode, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt,
                  int N, int T, const float *bias, int relu, const bf16 *mask, int ldm, bf16 *out, int ldo,
                  int *status) {
     cudaError_t e = prepare_kernels();
     if (e != cudaSuccess) return e;
+    if (mode == G_CONV3 && T == 27 && conv3_fits(A, lda, K, N))
+        return conv3_tma(s, B, D, H, W, A, lda, K, Wt, N, bias, relu, mask, ldm, out, ldo, status);
     GemmArgs a{};
     a.mode = mode;
     a.B = B; a.D = D; a.H = H; a.W = W;
@@ -589,6 +645,23 @@ static int *layer_status() {
     return st;
 }
 
+// Outcome of a single-layer call: the launch error, else the device status word
+// (a bounded wait that ran out) read back after the stream's work.
+static bd3mg_status layer_result(cudaError_t e, const int *st, cudaStream_t s) {
+    if (e != cudaSuccess) return BD3MG_ECUDA;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return BD3MG_ECUDA;
+    return h ? BD3MG_ETIMEOUT : BD3MG_OK;
+}
+
+int bd3mg_unet_set_tma_conv(int enable) {
+    const int prev = g_tma_conv ? 1 : 0;
+    g_tma_conv = enable != 0;
+    return prev;
+}
+
 bd3mg_status bd3mg_unet_conv3(int B, int D, int H, int W, const void *x, int ldx, int cin, const void *w, int cout,
                               const float *bias, int relu, const void *mask, int ldm, void *out, int ldo,
                               void *stream) {
@@ -598,7 +671,7 @@ bd3mg_status bd3mg_unet_conv3(int B, int D, int H, int W, const void *x, int ldx
     cudaError_t e = gemm(static_cast<cudaStream_t>(stream), G_CONV3, B, D, H, W, static_cast<const bf16 *>(x), ldx,
                          cin, static_cast<const bf16 *>(w), cout, 27, bias, relu, static_cast<const bf16 *>(mask), ldm,
                          static_cast<bf16 *>(out), ldo, st);
-    return e == cudaSuccess ? BD3MG_OK : BD3MG_ECUDA;
+    return layer_result(e, st, static_cast<cudaStream_t>(stream));
 }
 
 bd3mg_status bd3mg_unet_conv3_wgrad(int B, int D, int H, int W, const void *x, int ldx, int cin, const void *dz,
@@ -617,7 +690,7 @@ bd3mg_status bd3mg_unet_conv3_wgrad(int B, int D, int H, int W, const void *x, i
     cudaError_t e = wgrad(s, W_CONV3, B, D, H, W, static_cast<const bf16 *>(dz), ldz, cout,
                           static_cast<const bf16 *>(x), ldx, cin, 27, part, part_floats, sms, dw, cin, st);
     cudaFreeAsync(part, s);
-    return e == cudaSuccess ? BD3MG_OK : BD3MG_ECUDA;
+    return layer_result(e, st, s);
 }
 
 bd3mg_status bd3mg_unet_up(int B, int D, int H, int W, const void *x, int ldx, int cin, const void *w, int cout,
@@ -628,7 +701,7 @@ bd3mg_status bd3mg_unet_up(int B, int D, int H, int W, const void *x, int ldx, i
     cudaError_t e = gemm(static_cast<cudaStream_t>(stream), G_UPFWD, B, D, H, W, static_cast<const bf16 *>(x), ldx,
                          cin, static_cast<const bf16 *>(w), cout, 1, bias, 0, nullptr, 0, static_cast<bf16 *>(out), ldo,
                          st);
-    return e == cudaSuccess ? BD3MG_OK : BD3MG_ECUDA;
+    return layer_result(e, st, static_cast<cudaStream_t>(stream));
 }
 
 const char *bd3mg_unet_error_string(bd3mg_unet *n) {

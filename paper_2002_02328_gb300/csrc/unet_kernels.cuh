@@ -240,6 +240,300 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// k_conv3: the 3x3x3 convolution (zero padding) marching along z, with each
+// input slice staged once by TMA and the 27 taps read from the staged slices
+// through shifted operand descriptors.
+//
+// A work item is one 8 (x) x 16 (y) column of one volume over a range of
+// output depths.  Output tile (x0, y0, z) has M = 128 rows (row m is voxel
+// (x0 + m % 8, y0 + m / 8)).  Input slice zi of the column, x0-1 .. x0+8 by
+// y0-1 .. y0+16, is staged in a ring slot as one plane per group of 8
+// channels, [y][x][8 channels]: 16 bytes per voxel, so 8 consecutive x of one
+// y form one 8-row core matrix of a K-major operand, the next y row sits 160
+// bytes further (SBO), the next channel group one plane further (LBO).  The A
+// operand of tap (dz, dy, dx) of output z is the slot of slice z + dz - 1 read
+// from byte offset (dy * 10 + dx) * 16: no gather, and each input slice is
+// copied once per column (180 voxels per 128 outputs).  Taps reading a slice
+// outside the volume are left out (their contribution is zero).  The weights
+// of all 27 taps stay in shared memory ([tap][channel group][n][16 bytes]).
+//
+// Warp roles: lane 0 of warp 4 issues the slice copies and the MMAs; warps
+// 0-3 run the epilogue (bias, ReLU, mask, BF16 rounding; the k_gemm
+// epilogue), warp w on TMEM lanes 32w .. 32w+31.  The 27 dependent MMAs of an
+// output accumulate into one of C3_NACC TMEM accumulators; full_bar[a] (MMA
+// commit) hands it to the epilogue and empty_bar[a] (one arrival per
+// epilogue warp) back to the issuer, so the issuer runs up to C3_NACC
+// outputs ahead.  A ring slot is refilled once the MMAs of the last output
+// reading it have completed.  Every wait is bounded; a wait that runs out
+// sets ST_MMA_TIMEOUT and a shared abort flag that every loop checks.
+// ---------------------------------------------------------------------------
+constexpr int C3_TX = 8, C3_TY = 16;                       // output tile (x, y)
+constexpr int C3_BX = C3_TX + 2, C3_BY = C3_TY + 2;
+constexpr int C3_SLICE = C3_BX * C3_BY * 16;               // bytes of one channel group of one slice (2880)
+constexpr int C3_SPL = ((C3_SLICE + 127) / 128) * 128;     // its plane stride in a slot (2944)
+constexpr int C3_G = 1;                                    // outputs whose MMAs are issued interleaved
+constexpr int C3_RS = 6;                                   // ring slots (input slices)
+constexpr int C3_NACC = 4;                                 // TMEM accumulators (outputs in flight)
+constexpr int C3_THREADS = 160;                            // four epilogue warps and the issuing warp
+
+struct Conv3Args {
+    int B, D, H, W;
+    int K;                       // input channels (multiple of 16)
+    int N;                       // output channels (multiple of 16, <= 64)
+    const bf16 *Wt;              // [27][N][K]
+    const float *bias;           // [N] or null
+    int relu;
+    const bf16 *mask;            // out *= (mask > 0) per element, rows of ldm; or null
+    int ldm;
+    bf16 *out;                   // rows of ldo elements
+    int ldo;
+    int tiles_x, tiles_y;
+    int zc;                      // output depths per work item
+    int nchunks;                 // work items per column: ceil(D / zc)
+    int nitems;                  // B * tiles_y * tiles_x * nchunks
+    int *status;
+};
+
+__host__ __device__ constexpr size_t conv3_smem(int K, int N) {
+    return (size_t)27 * K * N * 2 + (size_t)C3_RS * (K / 8) * C3_SPL + (C3_RS + 2 * C3_NACC) * 8 + 32;
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// The (b, z, x0, y0) of every output of a CTA in issue order: work items
+// blockIdx.x, + gridDim.x, ..., each its z range in order.
+struct Conv3Walk {
+    const Conv3Args &a;
+    int item, z, z1, b, x0, y0;
+    __device__ explicit Conv3Walk(const Conv3Args &a_) : a(a_), item((int)blockIdx.x - (int)gridDim.x), z(0), z1(0) {}
+    // advance to the next output; false when the CTA has none left
+    __device__ bool next() {
+        if (++z < z1) return true;
+        item += gridDim.x;
+        if (item >= a.nitems) return false;
+        const int col = item / a.nchunks, ch = item - col * a.nchunks, tpz = a.tiles_x * a.tiles_y;
+        b = col / tpz;
+        const int r = col - b * tpz, ty = r / a.tiles_x;
+        x0 = (r - ty * a.tiles_x) * C3_TX;
+        y0 = ty * C3_TY;
+        z = ch * a.zc;
+        z1 = min(a.D, z + a.zc);
+        return true;
+    }
+    __device__ bool first_of_item() const { return z == (item % a.nchunks) * a.zc; }
+};
+
+// map: 5-D over [B][D][H][W][ld] reading channels [0, K), box (8, 10, 18, 1, 1).
+__global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    const int K = a.K, N = a.N, KG = K / 8, KS = K / 16;
+    const uint32_t w_bytes = 27u * (uint32_t)K * (uint32_t)N * 2u, slot_bytes = (uint32_t)KG * C3_SPL;
+    uint8_t *Ws = sm;
+    uint8_t *RING = sm + w_bytes;
+    uint64_t *in_bar = reinterpret_cast<uint64_t *>(RING + C3_RS * slot_bytes);
+    uint64_t *full_bar = in_bar + C3_RS;
+    uint64_t *empty_bar = full_bar + C3_NACC;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(empty_bar + C3_NACC);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t need_cols = (uint32_t)(C3_NACC * N);
+    const uint32_t ncols = need_cols <= 64u ? 64u : need_cols <= 128u ? 128u : need_cols <= 256u ? 256u : 512u;
+
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int i = 0; i < C3_RS + C3_NACC; ++i) mbar_init(in_bar + i, 1);
+        for (int i = 0; i < C3_NACC; ++i) mbar_init(empty_bar + i, 4);
+        fence_barrier_init();
+    }
+    if (warp == 0) umma::tmem_alloc(tslot, ncols);
+    // weights of all taps: [t][kg][n][16 bytes] from [t][n][K]
+    for (int q = tid; q < 27 * KG * N; q += C3_THREADS) {
+        const int n = q % N, tk = q / N, kg = tk % KG, t = tk / KG;
+        umma::cp_async16(Ws + (size_t)q * 16, a.Wt + ((size_t)t * N + n) * K + kg * 8, 16u);
+    }
+    umma::cp_async_commit();
+    umma::cp_async_wait<0>();
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    auto fail = [&]() {
+        atomicOr(a.status, ST_MMA_TIMEOUT);
+        *abort_flag = 1;
+    };
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // ---- copies and MMAs ----
+            const uint32_t idesc = umma::idesc_bf16(GM, N);
+            // descriptors of slot 0, tap (0, 0), channel group 0 / weight slab 0; a slot,
+            // tap, channel step or weight slab only moves the start address (bits 0-13,
+            // in 16-byte units; every address stays below 256 KB)
+            const uint64_t a_desc0 = umma::desc(umma::smem_addr(RING), C3_SPL, C3_BX * 16);
+            const uint64_t b_desc0 = umma::desc(umma::smem_addr(Ws), (uint32_t)N * 16, 128);
+            // go: outputs issued; gs: slices loaded (slot gs % C3_RS, in_bar phase gs / C3_RS);
+            // reader[s]: the last output reading slot s (-1: none); done: every output up to
+            // it has completed (the issuer saw its epilogue release the accumulator).  A
+            // reader after done is waited for; its barrier has no later phase in flight,
+            // since output reader + C3_NACC is issued only after that release.
+            int go = 0, gs = 0, gs0 = 0, slo = 0, shi = 0, loaded = 0, done = -1;
+            int reader[C3_RS];
+#pragma unroll
+            for (int s = 0; s < C3_RS; ++s) reader[s] = -1;
+            Conv3Walk wk(a);
+            bool ok = true;
+            auto slot_ready = [&](bool can_wait) -> int {   // 1 free, 0 not known, -1 wait ran out
+                const int rd = reader[gs % C3_RS];
+                if (rd <= done) return 1;
+                if (!can_wait) return 0;
+                return mbar_wait(full_bar + rd % C3_NACC, (uint32_t)((rd / C3_NACC) & 1)) ? 1 : -1;
+            };
+            auto load = [&]() {
+                const int s = gs % C3_RS, zi = slo + loaded;
+                reader[s] = -1;
+                mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
+                for (int kg = 0; kg < KG; ++kg)
+                    tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, wk.x0 - 1, wk.y0 - 1, zi, wk.b,
+                                in_bar + s);
+                ++loaded;
+                ++gs;
+            };
+            // Outputs are issued in groups of up to C3_G consecutive depths of one item:
+            // tap by tap, the group's outputs in turn (independent accumulators), so
+            // the tensor cores overlap the groups' accumulation chains.
+            bool more = wk.next();
+            while (ok && more) {
+                if (*abort_flag) break;
+                const int z = wk.z;
+                if (wk.first_of_item()) {
+                    slo = max(0, z - 1);
+                    shi = min(a.D, wk.z1 + 1);
+                    gs0 = gs;
+                    loaded = 0;
+                }
+                const int g = min(C3_G, wk.z1 - z);
+                // the group's accumulators have been read out
+                for (int k = 0; k < g && ok; ++k) {
+                    const int o = go + k;
+                    if (o < C3_NACC) continue;
+                    if (!mbar_wait(empty_bar + o % C3_NACC, (uint32_t)((o / C3_NACC - 1) & 1))) ok = false;
+                    else done = o - C3_NACC;
+                }
+                // slices z - 1 .. z + g in flight
+                while (ok && loaded < min(shi, z + g + 1) - slo) {
+                    const int f = slot_ready(true);
+                    if (f < 0) ok = false;
+                    else load();
+                }
+                for (int zi = max(0, z - 1); zi < min(a.D, z + g + 1) && ok; ++zi) {
+                    const int li = gs0 + (zi - slo), sl = li % C3_RS;
+                    if (!mbar_wait(in_bar + sl, (uint32_t)((li / C3_RS) & 1))) ok = false;
+                    reader[sl] = go + g - 1;              // every MMA of the group completes together
+                }
+                if (!ok) break;
+                umma::fence_after_sync();
+                uint32_t started = 0u;                    // bit k: output go + k has an MMA
+                uint64_t bq = b_desc0;
+                for (int dz = 0; dz < 3; ++dz)
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int dx = 0; dx < 3; ++dx) {
+                            const uint32_t tap = (uint32_t)(dy * C3_BX + dx);
+                            for (int j = 0; j < KS; ++j) {
+#pragma unroll
+                                for (int k = 0; k < C3_G; ++k) {
+                                    const int zi = z + k + dz - 1;
+                                    if (k >= g || zi < 0 || zi >= a.D) continue;   // zero padding
+                                    const int sl = (gs0 + (zi - slo)) % C3_RS;
+                                    const uint64_t at = a_desc0 + (uint64_t)((uint32_t)sl * (slot_bytes >> 4) + tap +
+                                                                             (uint32_t)j * 2 * (C3_SPL >> 4));
+                                    umma::mma_bf16(tmem + (uint32_t)(((go + k) % C3_NACC) * N), at, bq, idesc,
+                                                   (started >> k) & 1u);
+                                    started |= 1u << k;
+                                }
+                                bq += (uint64_t)(2 * N);
+                            }
+                        }
+                for (int k = 0; k < g; ++k) umma::commit(full_bar + (go + k) % C3_NACC);
+                go += g;
+                for (int k = 0; k < g; ++k) more = wk.next();
+                // copy further slices of the item into slots already known free
+                while (slo + loaded < shi && slot_ready(false) == 1) load();
+            }
+            if (!ok) fail();
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32w .. 32w+31 ----
+        Conv3Walk wk(a);
+        int go = 0;
+        while (wk.next()) {
+            if (*abort_flag) break;
+            const int acc_i = go % C3_NACC;
+            if (!mbar_wait(full_bar + acc_i, (uint32_t)((go / C3_NACC) & 1))) {
+                if (lane == 0) fail();
+                break;
+            }
+            umma::fence_after_sync();
+            const int m = warp * 32 + lane, x = wk.x0 + (m & 7), y = wk.y0 + (m >> 3);
+            const bool ok = x < a.W && y < a.H;
+            const long long o = (((long long)wk.b * a.D + wk.z) * a.H + y) * a.W + x;
+            bf16 *orow = a.out + o * a.ldo;
+            const bf16 *mrow = a.mask ? a.mask + o * a.ldm : nullptr;
+            for (int c = 0; c < N; c += 16) {
+                float acc[16];
+                umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc_i * N + c), acc);
+                if (!ok) continue;
+                if (a.bias) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
+                }
+                if (a.relu) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[i] = fmaxf(acc[i], 0.f);
+                }
+                if (mrow) {
+                    const uint4 m0v = *reinterpret_cast<const uint4 *>(mrow + c);
+                    const uint4 m1v = *reinterpret_cast<const uint4 *>(mrow + c + 8);
+                    const bf16 *mh0 = reinterpret_cast<const bf16 *>(&m0v);
+                    const bf16 *mh1 = reinterpret_cast<const bf16 *>(&m1v);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (!(__bfloat162float(mh0[i]) > 0.f)) acc[i] = 0.f;
+                        if (!(__bfloat162float(mh1[i]) > 0.f)) acc[8 + i] = 0.f;
+                    }
+                }
+                uint4 o0, o1;
+                o0.x = pack2(acc[0], acc[1]);   o0.y = pack2(acc[2], acc[3]);
+                o0.z = pack2(acc[4], acc[5]);   o0.w = pack2(acc[6], acc[7]);
+                o1.x = pack2(acc[8], acc[9]);   o1.y = pack2(acc[10], acc[11]);
+                o1.z = pack2(acc[12], acc[13]); o1.w = pack2(acc[14], acc[15]);
+                *reinterpret_cast<uint4 *>(orow + c) = o0;
+                *reinterpret_cast<uint4 *>(orow + c + 8) = o1;
+            }
+            // the accumulator goes back to the issuer once this warp's TMEM reads are done
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty_bar + acc_i);
+            ++go;
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+}
+
+// ---------------------------------------------------------------------------
 // k_wgrad: dW[t][co][ci] = sum_v dZ[v][co] * X[src(v, t)][ci] over this CTA's
 // voxel range (blockIdx.x = split, blockIdx.y = tap), FP32 partial out.
 //   CONV3: v over the conv's grid, src = v shifted by tap t (zero outside).

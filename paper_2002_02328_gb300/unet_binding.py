@@ -16,7 +16,7 @@ from . import binding
 EXPORTED = ["bd3mg_unet_create", "bd3mg_unet_param_count", "bd3mg_unet_set_params", "bd3mg_unet_get_params",
             "bd3mg_unet_get_grads", "bd3mg_unet_forward", "bd3mg_unet_loss_grad", "bd3mg_unet_train_step",
             "bd3mg_unet_conv3", "bd3mg_unet_conv3_wgrad", "bd3mg_unet_up", "bd3mg_unet_error_string",
-            "bd3mg_unet_destroy"]
+            "bd3mg_unet_destroy", "bd3mg_unet_set_tma_conv"]
 
 _bound = False
 
@@ -48,6 +48,7 @@ def load():
         "bd3mg_unet_up": (ip, [ip, ip, ip, ip, vp, ip, ip, vp, ip, vp, vp, ip, vp]),
         "bd3mg_unet_error_string": (ctypes.c_char_p, [vp]),
         "bd3mg_unet_destroy": (None, [vp]),
+        "bd3mg_unet_set_tma_conv": (ip, [ip]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -205,6 +206,12 @@ class UNet:
                                                _p(base.contiguous()) if base is not None else None,
                                                _p(target.contiguous()), ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
+
+
+def set_tma_conv(enable: bool) -> bool:
+    """Choose the TMA-staged 3x3x3 convolution (True, the default) or the row-gather
+    implicit GEMM for every convolution; returns the previous setting."""
+    return bool(load().bd3mg_unet_set_tma_conv(int(bool(enable))))
 
 
 def conv3(x, w, bias=None, relu=False, mask=None, cout=None, out=None):

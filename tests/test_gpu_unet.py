@@ -56,6 +56,49 @@ def test_conv3_matches_oracle(ub, cin, cout, relu, masked):
         assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
 
 
+@pytest.mark.parametrize("cin,cout,relu,masked,strided", [
+    (16, 16, True, False, False), (32, 16, False, True, True), (16, 32, True, True, False),
+    (32, 32, False, False, True), (32, 64, True, False, False)])
+def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, masked, strided):
+    """The TMA-staged convolution (input block per 8x16 output tile, taps read
+    through shifted descriptors) on a grid with ragged x and y tiles: within the
+    oracle bound, and the same bits as the row-gather kernel (same MMA order).
+    strided: x is the second half of rows of 2 cin channels and out the first
+    cout channels of rows of 2 cout (the concatenation buffers' layout)."""
+    import torch
+    r = _rng(7 * cin + cout)
+    B, D, H, W = 2, 3, 21, 13
+    xs = _bf(r.normal(size=(B, D, H, W, 2 * cin if strided else cin))).cuda()
+    x = xs[..., cin:] if strided else xs
+    w = _bf(r.normal(0, (27 * cin) ** -0.5, size=(27, cout, cin))).cuda()
+    b = torch.from_numpy(r.normal(size=cout).astype(np.float32)).cuda()
+    mask = _bf(r.normal(size=(B, D, H, W, cout))).cuda() if masked else None
+    outs = []
+    for tma in (True, False):
+        prev = ub.set_tma_conv(tma)
+        try:
+            full = torch.zeros((B, D, H, W, 2 * cout if strided else cout), device="cuda", dtype=torch.bfloat16)
+            o = full[..., :cout] if strided else full
+            ub.conv3(x, w, b, relu=relu, mask=mask, out=o)
+            torch.cuda.synchronize()
+            outs.append(full)
+        finally:
+            ub.set_tma_conv(prev)
+    assert torch.equal(outs[0], outs[1])
+    if strided:
+        assert not torch.any(outs[0][..., cout:] != 0)             # nothing written past the output channels
+    got = _np(outs[0][..., :cout])
+    xd, wd, bd = _np(x), _np(w), _np(b)
+    for k in range(B):
+        ref = U.conv3(xd[k], wd, bd)
+        if relu:
+            ref = np.maximum(ref, 0.0)
+        if masked:
+            ref = ref * (_np(mask)[k] > 0)
+        err = np.abs(got[k] - ref)
+        assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (256, 128)])
 def test_conv3_weight_gradient_matches_oracle(ub, cin, cout):
     import torch
