@@ -97,7 +97,7 @@ int L_up(const bd3mg_unet *n, int l) { return 2 * n->L + 3 * (n->L - 2 - l); }
 int L_dec(const bd3mg_unet *n, int l, int b) { return L_up(n, l) + 1 + b; }
 int L_head(const bd3mg_unet *n) { return (int)n->layers.size() - 1; }
 
-constexpr size_t kConv3SmemMax = 200 * 1024;   // shared memory of k_conv3 at most (weights + slice ring)
+constexpr size_t kConv3SmemMax = 224 * 1024;   // shared memory of k_conv3 at most (weights + slice ring)
 
 size_t gemm_smem(int KC, int N) { return (size_t)STAGES * (GM * KC * 2 + (size_t)N * KC * 2) + STAGES * 8 + 16; }
 size_t wgrad_smem(int Cin) { return WSTAGES * ((size_t)GM * KV * 2 + (size_t)Cin * KV * 2) + WSTAGES * 8 + 16; }
@@ -120,14 +120,21 @@ cudaError_t prepare_kernels() {
 int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
 // The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
-// multiple of 16 up to 64, K a multiple of 16, the 27 taps' weights and the
+// multiple of 16 up to 64, K of 16, 32 or 64 channels, the 27 taps' weights and the
 // ring of input slices within kConv3SmemMax, rows 16-byte aligned.
 // Process-wide switch (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
+// Ring slots of k_conv3: the most (up to C3_RS, at least 4) whose shared memory fits.
+int conv3_ring(int K, int N) {
+    for (int rs = C3_RS; rs >= 4; --rs)
+        if (conv3_smem(K, N, rs) <= kConv3SmemMax) return rs;
+    return 0;
+}
+
 bool conv3_fits(const bf16 *A, int lda, int K, int N) {
-    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 64 && K % 16 == 0 && K >= 16 && lda % 8 == 0 &&
-           (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_smem(K, N) <= kConv3SmemMax;
+    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 64 && (K == 16 || K == 32 || K == 64) && lda % 8 == 0 &&
+           (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_ring(K, N) > 0;
 }
 
 cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt, int N,
@@ -141,7 +148,8 @@ cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A,
     a.out = out; a.ldo = ldo; a.status = status;
     a.tiles_x = (W + C3_TX - 1) / C3_TX;
     a.tiles_y = (H + C3_TY - 1) / C3_TY;
-    const size_t smem = conv3_smem(K, N);
+    a.rs = conv3_ring(K, N);
+    const size_t smem = conv3_smem(K, N, a.rs);
     // one wave of CTAs looping over the work items: as many per SM as shared
     // memory and tensor memory (C3_NACC accumulators of N columns) hold
     int dev = 0, sms = 0, smem_sm = 0;
@@ -183,8 +191,16 @@ cudaError_t gemm(cudaStream_t s, int mode, int B, int D, int H, int W, const bf1
     a.Wt = Wt; a.N = N; a.T = T;
     a.bias = bias; a.relu = relu; a.mask = mask; a.ldm = ldm;
     a.out = out; a.ldo = ldo; a.status = status;
-    dim3 grid((unsigned)((a.M + GM - 1) / GM), mode == G_UPFWD ? 8u : 1u);
-    k_gemm<<<grid, GT, gemm_smem(a.KC, N), s>>>(a);
+    // UPFWD: every tap reads the same coarse row, so with 8 N <= 256 the 8 taps'
+    // weights ([8][N][K], contiguous) form one N' = 8 N operand and one launch row
+    // writes all 8 fine voxels of its coarse voxels
+    const bool stack = mode == G_UPFWD && 8 * N <= 256 && !mask && !relu;
+    if (stack) {
+        a.nsub = N;
+        a.N = 8 * N;
+    }
+    dim3 grid((unsigned)((a.M + GM - 1) / GM), mode == G_UPFWD && !stack ? 8u : 1u);
+    k_gemm<<<grid, GT, gemm_smem(a.KC, a.N), s>>>(a);
     return cudaGetLastError();
 }
 

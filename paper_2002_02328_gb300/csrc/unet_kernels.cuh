@@ -55,6 +55,7 @@ struct GemmArgs {
     const bf16 *Wt;              // [T][N][K]
     int N;                       // output channels (multiple of 16, <= 256)
     int T;                       // taps reduced in this launch (CONV3 27, UPBWD 8, UPFWD 1)
+    int nsub;                    // UPFWD with the 8 taps stacked along N: channels per tap (N = 8 nsub); else 0
     const float *bias;           // [N] or null
     int relu;
     const bf16 *mask;            // out *= (mask > 0) per element, rows of ldm; or null
@@ -208,9 +209,19 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
         float acc[16];
         umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, acc);
         if (!row_ok) continue;
+        int cc = c;                                   // output channel of column c
+        bf16 *orow_c = orow;
+        if (a.nsub) {
+            // columns [tap * nsub, (tap + 1) * nsub): the fine voxel of that tap
+            const int tap = c / a.nsub, az = tap >> 2, ay = (tap >> 1) & 1, ax = tap & 1;
+            cc = c - tap * a.nsub;
+            const long long o =
+                (((long long)bb * 2 * a.D + 2 * zb + az) * (2LL * a.H) + 2 * yb + ay) * (2LL * a.W) + 2 * xb + ax;
+            orow_c = a.out + o * a.ldo;
+        }
         if (a.bias) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
+            for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + cc + i);
         }
         if (a.relu) {
 #pragma unroll
@@ -231,8 +242,8 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
         o0.z = pack2(acc[4], acc[5]);   o0.w = pack2(acc[6], acc[7]);
         o1.x = pack2(acc[8], acc[9]);   o1.y = pack2(acc[10], acc[11]);
         o1.z = pack2(acc[12], acc[13]); o1.w = pack2(acc[14], acc[15]);
-        *reinterpret_cast<uint4 *>(orow + c) = o0;
-        *reinterpret_cast<uint4 *>(orow + c + 8) = o1;
+        *reinterpret_cast<uint4 *>(orow_c + cc) = o0;
+        *reinterpret_cast<uint4 *>(orow_c + cc + 8) = o1;
     }
     umma::fence_before_sync();
     __syncthreads();
@@ -271,8 +282,7 @@ constexpr int C3_TX = 8, C3_TY = 16;                       // output tile (x, y)
 constexpr int C3_BX = C3_TX + 2, C3_BY = C3_TY + 2;
 constexpr int C3_SLICE = C3_BX * C3_BY * 16;               // bytes of one channel group of one slice (2880)
 constexpr int C3_SPL = ((C3_SLICE + 127) / 128) * 128;     // its plane stride in a slot (2944)
-constexpr int C3_G = 1;                                    // outputs whose MMAs are issued interleaved
-constexpr int C3_RS = 6;                                   // ring slots (input slices)
+constexpr int C3_RS = 6;                                   // ring slots (input slices) at most; at least 4
 constexpr int C3_NACC = 4;                                 // TMEM accumulators (outputs in flight)
 constexpr int C3_THREADS = 160;                            // four epilogue warps and the issuing warp
 
@@ -291,11 +301,12 @@ struct Conv3Args {
     int zc;                      // output depths per work item
     int nchunks;                 // work items per column: ceil(D / zc)
     int nitems;                  // B * tiles_y * tiles_x * nchunks
+    int rs;                      // ring slots (4 .. C3_RS)
     int *status;
 };
 
-__host__ __device__ constexpr size_t conv3_smem(int K, int N) {
-    return (size_t)27 * K * N * 2 + (size_t)C3_RS * (K / 8) * C3_SPL + (C3_RS + 2 * C3_NACC) * 8 + 32;
+__host__ __device__ constexpr size_t conv3_smem(int K, int N, int rs) {
+    return (size_t)27 * K * N * 2 + (size_t)rs * (K / 8) * C3_SPL + (C3_RS + 2 * C3_NACC) * 8 + 32;
 }
 
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
@@ -333,14 +344,39 @@ struct Conv3Walk {
     __device__ bool first_of_item() const { return z == (item % a.nchunks) * a.zc; }
 };
 
+// The 27 * KS MMAs of one output, unrolled: the A descriptor of tap (dz, dy, dx)
+// and channel step j is a_lo[dz] + (dy * 10 + dx) + j * 2 * C3_SPL / 16 (low
+// word; slices outside the volume have a_lo[dz] = 0 and are skipped), the B
+// descriptor b_lo + ((tap * KS + j) * 2 N) (16-byte units).
+template <int KS>
+__device__ __forceinline__ void conv3_mmas(uint32_t dt, const uint32_t (&a_lo)[3], uint32_t a_hi, uint32_t b_lo,
+                                           uint32_t b_hi, uint32_t bstep, uint32_t idesc) {
+    uint32_t accum = 0u;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        if (a_lo[dz] == 0u) continue;
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int j = 0; j < KS; ++j) {
+                const uint32_t al = a_lo[dz] + (uint32_t)((t / 3) * C3_BX + t % 3 + j * 2 * (C3_SPL >> 4));
+                const uint32_t bl = b_lo + (uint32_t)((dz * 9 + t) * KS + j) * bstep;
+                const uint64_t ad = ((uint64_t)a_hi << 32) | al, bd = ((uint64_t)b_hi << 32) | bl;
+                umma::mma_bf16(dt, ad, bd, idesc, accum);
+                accum = 1u;
+            }
+    }
+}
+
 // map: 5-D over [B][D][H][W][ld] reading channels [0, K), box (8, 10, 18, 1, 1).
-__global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
+__global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int K = a.K, N = a.N, KG = K / 8, KS = K / 16;
     const uint32_t w_bytes = 27u * (uint32_t)K * (uint32_t)N * 2u, slot_bytes = (uint32_t)KG * C3_SPL;
     uint8_t *Ws = sm;
     uint8_t *RING = sm + w_bytes;
-    uint64_t *in_bar = reinterpret_cast<uint64_t *>(RING + C3_RS * slot_bytes);
+    const int RS = a.rs;
+    uint64_t *in_bar = reinterpret_cast<uint64_t *>(RING + RS * slot_bytes);
     uint64_t *full_bar = in_bar + C3_RS;
     uint64_t *empty_bar = full_bar + C3_NACC;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(empty_bar + C3_NACC);
@@ -382,7 +418,9 @@ __global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__
             // in 16-byte units; every address stays below 256 KB)
             const uint64_t a_desc0 = umma::desc(umma::smem_addr(RING), C3_SPL, C3_BX * 16);
             const uint64_t b_desc0 = umma::desc(umma::smem_addr(Ws), (uint32_t)N * 16, 128);
-            // go: outputs issued; gs: slices loaded (slot gs % C3_RS, in_bar phase gs / C3_RS);
+            const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
+            const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32), bstep = 2u * (uint32_t)N;
+            // go: outputs issued; gs: slices loaded (slot gs % RS, in_bar phase gs / RS);
             // reader[s]: the last output reading slot s (-1: none); done: every output up to
             // it has completed (the issuer saw its epilogue release the accumulator).  A
             // reader after done is waited for; its barrier has no later phase in flight,
@@ -390,17 +428,17 @@ __global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__
             int go = 0, gs = 0, gs0 = 0, slo = 0, shi = 0, loaded = 0, done = -1;
             int reader[C3_RS];
 #pragma unroll
-            for (int s = 0; s < C3_RS; ++s) reader[s] = -1;
+            for (int s = 0; s < C3_RS; ++s) reader[s] = -1;       // slots RS .. C3_RS - 1 unused
             Conv3Walk wk(a);
             bool ok = true;
             auto slot_ready = [&](bool can_wait) -> int {   // 1 free, 0 not known, -1 wait ran out
-                const int rd = reader[gs % C3_RS];
+                const int rd = reader[gs % RS];
                 if (rd <= done) return 1;
                 if (!can_wait) return 0;
                 return mbar_wait(full_bar + rd % C3_NACC, (uint32_t)((rd / C3_NACC) & 1)) ? 1 : -1;
             };
             auto load = [&]() {
-                const int s = gs % C3_RS, zi = slo + loaded;
+                const int s = gs % RS, zi = slo + loaded;
                 reader[s] = -1;
                 mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
                 for (int kg = 0; kg < KG; ++kg)
@@ -409,9 +447,6 @@ __global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__
                 ++loaded;
                 ++gs;
             };
-            // Outputs are issued in groups of up to C3_G consecutive depths of one item:
-            // tap by tap, the group's outputs in turn (independent accumulators), so
-            // the tensor cores overlap the groups' accumulation chains.
             bool more = wk.next();
             while (ok && more) {
                 if (*abort_flag) break;
@@ -422,51 +457,40 @@ __global__ void __launch_bounds__(C3_THREADS, 1) k_conv3(const __grid_constant__
                     gs0 = gs;
                     loaded = 0;
                 }
-                const int g = min(C3_G, wk.z1 - z);
-                // the group's accumulators have been read out
-                for (int k = 0; k < g && ok; ++k) {
-                    const int o = go + k;
-                    if (o < C3_NACC) continue;
-                    if (!mbar_wait(empty_bar + o % C3_NACC, (uint32_t)((o / C3_NACC - 1) & 1))) ok = false;
-                    else done = o - C3_NACC;
+                // the accumulator has been read out
+                if (go >= C3_NACC) {
+                    if (!mbar_wait(empty_bar + go % C3_NACC, (uint32_t)((go / C3_NACC - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    done = go - C3_NACC;
                 }
-                // slices z - 1 .. z + g in flight
-                while (ok && loaded < min(shi, z + g + 1) - slo) {
+                // slices z - 1 .. z + 1 in flight, then landed
+                while (ok && loaded < min(shi, z + 2) - slo) {
                     const int f = slot_ready(true);
                     if (f < 0) ok = false;
                     else load();
                 }
-                for (int zi = max(0, z - 1); zi < min(a.D, z + g + 1) && ok; ++zi) {
-                    const int li = gs0 + (zi - slo), sl = li % C3_RS;
-                    if (!mbar_wait(in_bar + sl, (uint32_t)((li / C3_RS) & 1))) ok = false;
-                    reader[sl] = go + g - 1;              // every MMA of the group completes together
+                uint32_t a_lo[3];                                // descriptor low words (0: outside the volume)
+#pragma unroll
+                for (int dz = 0; dz < 3; ++dz) {
+                    const int zi = z + dz - 1;
+                    a_lo[dz] = 0u;
+                    if (!ok || zi < 0 || zi >= a.D) continue;
+                    const int li = gs0 + (zi - slo), sl = li % RS;
+                    if (!mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
+                    reader[sl] = go;
+                    a_lo[dz] = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
                 }
                 if (!ok) break;
                 umma::fence_after_sync();
-                uint32_t started = 0u;                    // bit k: output go + k has an MMA
-                uint64_t bq = b_desc0;
-                for (int dz = 0; dz < 3; ++dz)
-                    for (int dy = 0; dy < 3; ++dy)
-                        for (int dx = 0; dx < 3; ++dx) {
-                            const uint32_t tap = (uint32_t)(dy * C3_BX + dx);
-                            for (int j = 0; j < KS; ++j) {
-#pragma unroll
-                                for (int k = 0; k < C3_G; ++k) {
-                                    const int zi = z + k + dz - 1;
-                                    if (k >= g || zi < 0 || zi >= a.D) continue;   // zero padding
-                                    const int sl = (gs0 + (zi - slo)) % C3_RS;
-                                    const uint64_t at = a_desc0 + (uint64_t)((uint32_t)sl * (slot_bytes >> 4) + tap +
-                                                                             (uint32_t)j * 2 * (C3_SPL >> 4));
-                                    umma::mma_bf16(tmem + (uint32_t)(((go + k) % C3_NACC) * N), at, bq, idesc,
-                                                   (started >> k) & 1u);
-                                    started |= 1u << k;
-                                }
-                                bq += (uint64_t)(2 * N);
-                            }
-                        }
-                for (int k = 0; k < g; ++k) umma::commit(full_bar + (go + k) % C3_NACC);
-                go += g;
-                for (int k = 0; k < g; ++k) more = wk.next();
+                const uint32_t dt = tmem + (uint32_t)((go % C3_NACC) * N);
+                if (KS == 1) conv3_mmas<1>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                else if (KS == 2) conv3_mmas<2>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                else conv3_mmas<4>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                umma::commit(full_bar + go % C3_NACC);
+                ++go;
+                more = wk.next();
                 // copy further slices of the item into slots already known free
                 while (slo + loaded < shi && slot_ready(false) == 1) load();
             }

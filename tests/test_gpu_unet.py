@@ -58,7 +58,7 @@ def test_conv3_matches_oracle(ub, cin, cout, relu, masked):
 
 @pytest.mark.parametrize("cin,cout,relu,masked,strided", [
     (16, 16, True, False, False), (32, 16, False, True, True), (16, 32, True, True, False),
-    (32, 32, False, False, True), (32, 64, True, False, False)])
+    (32, 32, False, False, True), (32, 64, True, False, False), (64, 32, True, False, False)])
 def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, masked, strided):
     """The TMA-staged convolution (input block per 8x16 output tile, taps read
     through shifted descriptors) on a grid with ragged x and y tiles: within the
@@ -116,7 +116,7 @@ def test_conv3_weight_gradient_matches_oracle(ub, cin, cout):
     assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max() + 1e-6
 
 
-@pytest.mark.parametrize("cin,cout", [(32, 16), (128, 64)])
+@pytest.mark.parametrize("cin,cout", [(32, 16), (64, 32), (128, 64)])
 def test_up_matches_oracle(ub, cin, cout):
     import torch
     r = _rng(3 * cin + cout)
