@@ -681,7 +681,11 @@ def mixed_extra(fstar_iters, stream, flush, steps):
             s.set_escalation(1e-9)
             tr = s.iterate(400)
             at = s.escalated()
-        esc = {"tol": 1e-9, "escalated_at_iteration": at}
+            f_fresh = s.objective()
+        # the trace takes f from the carried residual; its last entry against f with H
+        # applied afresh shows the drift a gap read from the trace carries
+        esc = {"tol": 1e-9, "escalated_at_iteration": at,
+               "trace_drift_rel_at_end": float((tr[-1] - f_fresh) / abs(f_fresh))}
         for name, den in (("rel_1e-7", abs(fstar)), ("normalized_1e-6", tr[0] - fstar)):
             lvl = 1e-7 if name.startswith("rel") else 1e-6
             hit = np.nonzero((tr - fstar) / den <= lvl)[0]

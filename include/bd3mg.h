@@ -381,8 +381,8 @@ int bd3mg_launches_per_iteration(bd3mg_ctx *ctx);
  * runs in chunks of 4 iterations and reads the objective trace between chunks;
  * once some volume's objective decreases by at most tol * |f| from one
  * iteration to the next, the context switches for good to FP32 storage (g
- * recomputed by the next iteration; d and H d widened from their BF16 values)
- * and a new iteration graph.
+ * recomputed by the next iteration; d and H d widened from their BF16 values,
+ * then r and H d recomputed exactly) and a new iteration graph.
  * bd3mg_iterate_async never escalates.  tol = 0 turns it off (the default);
  * no effect on FP32 contexts.  bd3mg_escalated: *at = the iteration count at
  * which the switch happened, -1 if it has not.  Errors: BD3MG_EINVAL for a

@@ -856,6 +856,9 @@ bd3mg_status escalate_to_fp32(bd3mg_ctx *c) {
         }
         if ((st = check_launch(c))) return st;
         c->bfd = false;
+        // r carries the rounding of H g and H d since the last refresh: recompute it
+        // (and H d) exactly before the first FP32 iteration
+        c->stale = true;
     }
     for (VolState &vs : c->V) {
         if (!vs.g && (st = dalloc_n(c, &vs.g, vs.np))) return st;
