@@ -339,19 +339,19 @@ def fstar_of(prob, iters):
     return f, settle
 
 
-def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0, normalized=False):
+def time_to_gap(prob, slabs, fstar, max_iters, stream, precision=0, normalized=False, **kw):
     """Iterations to gap <= 1e-4 (from the trace), then the device time of exactly that many.
     gap = (f - f*)/|f*|, or (f - f*)/(f0 - f*) when normalized."""
     import torch
     from paper_2002_02328_gb300 import binding
-    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision) as s:
+    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision, **kw) as s:
         tr = s.iterate(max_iters)
     gap = (tr - fstar) / (abs(tr[0] - fstar) if normalized else abs(fstar))
     hit = np.nonzero(gap <= GAP)[0]
     if hit.size == 0:
         return None, None, float(gap[-1])
     k = int(hit[0])
-    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision) as s:
+    with binding.Solver.from_problem(prob, slabs=slabs, precision=precision, **kw) as s:
         s.iterate(2)                         # warm the graph, then restart from y
         s.set_x(torch.from_numpy(prob.y).cuda())
         torch.cuda.synchronize()
@@ -789,7 +789,7 @@ def warm_start_extra(args, stream, fstar):
     return out
 
 
-def e2e_run(prob, n_iter, stream):
+def e2e_run(prob, n_iter, stream, **kw):
     """Whole solve through the public API with host buffers: H2D of y from pinned memory,
     context creation, n_iter sweeps with the f trace read back, D2H of x to pinned memory."""
     import torch
@@ -799,7 +799,7 @@ def e2e_run(prob, n_iter, stream):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     with binding.Solver(prob.shape, prob.psf, y_host, lam=prob.lam, delta=prob.delta, eta=prob.eta,
-                        xmin=prob.xmin, xmax=prob.xmax, slabs=prob.slabs) as s:
+                        xmin=prob.xmin, xmax=prob.xmax, slabs=prob.slabs, **kw) as s:
         tr = s.iterate(n_iter)
         s.get_x(x_host)
     torch.cuda.synchronize()
@@ -861,7 +861,10 @@ def ours(args):
     sampler = ClockSampler(gpu_id_for(dev)) if rank == 0 else None
     time.sleep(0.3)
 
-    with binding.Solver.from_problem(prob) as s:
+    # the work shape (z-chunk, curvature tile rows) the library's autotuner picks on this GPU
+    tuned_zc, tuned_rows, _ = binding.autotune([prob], iters=10)
+    tuned = {"zchunk": tuned_zc, "curv_rows": tuned_rows}
+    with binding.Solver.from_problem(prob, **tuned) as s:
         lpi = s.launches_per_iteration()
         for _ in range(args.warmup):
             flush.fill_(1.0)
@@ -953,11 +956,11 @@ def ours(args):
     cpu = None
     if not args.quick:
         fstar, settle = fstar_of(prob, args.fstar_iters)
-        k_b, t_b, g_b = time_to_gap(prob, prob.slabs, fstar, 3000, stream)
+        k_b, t_b, g_b = time_to_gap(prob, prob.slabs, fstar, 3000, stream, **tuned)
         k_p, t_p, g_p = time_to_gap(prob, None, fstar, 3000, stream)
         k_m, t_m, g_m = time_to_gap(prob, prob.slabs, fstar, 3000, stream, binding.BF16_GRADIENT)
         k_mp, t_mp, g_mp = time_to_gap(prob, None, fstar, 3000, stream, binding.BF16_GRADIENT)
-        k_bn, t_bn, _ = time_to_gap(prob, prob.slabs, fstar, 3000, stream, normalized=True)
+        k_bn, t_bn, _ = time_to_gap(prob, prob.slabs, fstar, 3000, stream, normalized=True, **tuned)
         k_pn, t_pn, _ = time_to_gap(prob, None, fstar, 3000, stream, normalized=True)
         extra["time_to_gap"] = {"gap": GAP, "fstar": fstar, "fstar_iters": args.fstar_iters,
                                 "fstar_settle_rel": settle,
@@ -974,7 +977,7 @@ def ours(args):
         extra["mixed_512x512x128"] = mixed_extra(args.fstar_iters, stream, flush, 20)
         if not args.no_warm_start:
             extra["warm_start_512x512x128"] = warm_start_extra(args, stream, extra["mixed_512x512x128"]["fstar"])
-        e2e_rate, h2d, d2h, e2e_s, x500 = e2e_run(prob, 500, stream)
+        e2e_rate, h2d, d2h, e2e_s, x500 = e2e_run(prob, 500, stream, **tuned)
         e2e = {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "what": f"500-sweep solve through the C ABI from pinned host y to pinned host x ({e2e_s:.3f} s)"}
         # the workload's box [xmin, xmax] clips the phantom's overlapping ellipsoids
@@ -992,7 +995,9 @@ def ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(prob, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}),
+            "config": workload_config(prob, {"parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                                             "autotuned": {"zchunk": tuned_zc or "cost model",
+                                                           "curvature_rows": tuned_rows}}),
             "roofline": roofline, "roofline_plain_512": roof512, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * lpi + refresh_launches(args.warmup, args.steps), "clocks": clocks,
             "extra": extra}

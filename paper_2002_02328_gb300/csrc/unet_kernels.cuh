@@ -426,20 +426,33 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
             // reader after done is waited for; its barrier has no later phase in flight,
             // since output reader + C3_NACC is issued only after that release.
             int go = 0, gs = 0, gs0 = 0, slo = 0, shi = 0, loaded = 0, done = -1;
+            // (kept in registers: every access selects its slot with unrolled compares)
             int reader[C3_RS];
 #pragma unroll
             for (int s = 0; s < C3_RS; ++s) reader[s] = -1;       // slots RS .. C3_RS - 1 unused
+            auto reader_of = [&](int slot) {
+                int r = -1;
+#pragma unroll
+                for (int s = 0; s < C3_RS; ++s)
+                    if (s == slot) r = reader[s];
+                return r;
+            };
+            auto set_reader = [&](int slot, int v) {
+#pragma unroll
+                for (int s = 0; s < C3_RS; ++s)
+                    if (s == slot) reader[s] = v;
+            };
             Conv3Walk wk(a);
             bool ok = true;
             auto slot_ready = [&](bool can_wait) -> int {   // 1 free, 0 not known, -1 wait ran out
-                const int rd = reader[gs % RS];
+                const int rd = reader_of(gs % RS);
                 if (rd <= done) return 1;
                 if (!can_wait) return 0;
                 return mbar_wait(full_bar + rd % C3_NACC, (uint32_t)((rd / C3_NACC) & 1)) ? 1 : -1;
             };
             auto load = [&]() {
                 const int s = gs % RS, zi = slo + loaded;
-                reader[s] = -1;
+                set_reader(s, -1);
                 mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
                 for (int kg = 0; kg < KG; ++kg)
                     tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, wk.x0 - 1, wk.y0 - 1, zi, wk.b,
@@ -479,7 +492,7 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                     if (!ok || zi < 0 || zi >= a.D) continue;
                     const int li = gs0 + (zi - slo), sl = li % RS;
                     if (!mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
-                    reader[sl] = go;
+                    set_reader(sl, go);
                     a_lo[dz] = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
                 }
                 if (!ok) break;
@@ -499,6 +512,8 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
         __syncwarp();
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32w .. 32w+31 ----
+        const bool b16 = a.bias && (reinterpret_cast<uintptr_t>(a.bias) & 15u) == 0;
+        const float4 *bias4 = b16 ? reinterpret_cast<const float4 *>(a.bias) : nullptr;
         Conv3Walk wk(a);
         int go = 0;
         while (wk.next()) {
@@ -518,7 +533,16 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                 float acc[16];
                 umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc_i * N + c), acc);
                 if (!ok) continue;
-                if (a.bias) {
+                if (bias4) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 bv = __ldg(bias4 + c / 4 + i);
+                        acc[4 * i] += bv.x;
+                        acc[4 * i + 1] += bv.y;
+                        acc[4 * i + 2] += bv.z;
+                        acc[4 * i + 3] += bv.w;
+                    }
+                } else if (a.bias) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
                 }
