@@ -271,10 +271,11 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 // Warp roles: lane 0 of warp 4 issues the slice copies and the MMAs; warps
 // 0-3 run the epilogue (bias, ReLU, mask, BF16 rounding; the k_gemm
 // epilogue), warp w on TMEM lanes 32w .. 32w+31.  The 27 dependent MMAs of an
-// output accumulate into one of C3_NACC TMEM accumulators; full_bar[a] (MMA
-// commit) hands it to the epilogue and empty_bar[a] (one arrival per
-// epilogue warp) back to the issuer, so the issuer runs up to C3_NACC
-// outputs ahead.  A ring slot is refilled once the MMAs of the last output
+// output accumulate into one of C3_NACC TMEM accumulators; two consecutive
+// outputs of an item are issued together, tap by tap in turn, so the tensor
+// cores run two independent chains; full_bar[a] (MMA commit) hands an
+// accumulator to the epilogue and empty_bar[a] (one arrival per epilogue
+// warp) back to the issuer, so the issuer runs up to C3_NACC outputs ahead.  A ring slot is refilled once the MMAs of the last output
 // reading it have completed.  Every wait is bounded; a wait that runs out
 // sets ST_MMA_TIMEOUT and a shared abort flag that every loop checks.
 // ---------------------------------------------------------------------------
@@ -351,6 +352,7 @@ struct Conv3Walk {
 template <int KS>
 __device__ __forceinline__ void conv3_mmas(uint32_t dt, const uint32_t (&a_lo)[3], uint32_t a_hi, uint32_t b_lo,
                                            uint32_t b_hi, uint32_t bstep, uint32_t idesc) {
+    asm volatile("" : "+r"(b_lo), "+r"(bstep));
     uint32_t accum = 0u;
 #pragma unroll
     for (int dz = 0; dz < 3; ++dz) {
@@ -364,6 +366,39 @@ __device__ __forceinline__ void conv3_mmas(uint32_t dt, const uint32_t (&a_lo)[3
                 const uint64_t ad = ((uint64_t)a_hi << 32) | al, bd = ((uint64_t)b_hi << 32) | bl;
                 umma::mma_bf16(dt, ad, bd, idesc, accum);
                 accum = 1u;
+            }
+    }
+}
+
+// The MMAs of two consecutive outputs (slices z-1 .. z+1 and z .. z+2), tap by
+// tap in turn: their accumulators are independent, so the tensor cores run
+// the two accumulation chains side by side.  a_lo[dz] for output 0 is slice z +
+// dz - 1, for output 1 slice z + dz (a_lo[3]); 0 = outside the volume.
+template <int KS>
+__device__ __forceinline__ void conv3_mmas2(uint32_t dt0, uint32_t dt1, const uint32_t (&a_lo)[4], uint32_t a_hi,
+                                            uint32_t b_lo, uint32_t b_hi, uint32_t bstep, uint32_t idesc) {
+    // an opaque copy of the weight base: the per-tap descriptors are formed here, not hoisted
+    // out of the caller's loop into registers (108 of them with 64 channels)
+    asm volatile("" : "+r"(b_lo), "+r"(bstep));
+    uint32_t acc0 = 0u, acc1 = 0u;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+        const bool v0 = a_lo[dz] != 0u, v1 = a_lo[dz + 1] != 0u;
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+#pragma unroll
+            for (int j = 0; j < KS; ++j) {
+                const uint32_t off = (uint32_t)((t / 3) * C3_BX + t % 3 + j * 2 * (C3_SPL >> 4));
+                const uint32_t bl = b_lo + (uint32_t)((dz * 9 + t) * KS + j) * bstep;
+                const uint64_t bd = ((uint64_t)b_hi << 32) | bl;
+                if (v0) {
+                    umma::mma_bf16(dt0, ((uint64_t)a_hi << 32) | (a_lo[dz] + off), bd, idesc, acc0);
+                    acc0 = 1u;
+                }
+                if (v1) {
+                    umma::mma_bf16(dt1, ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + off), bd, idesc, acc1);
+                    acc1 = 1u;
+                }
             }
     }
 }
@@ -470,40 +505,49 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                     gs0 = gs;
                     loaded = 0;
                 }
-                // the accumulator has been read out
-                if (go >= C3_NACC) {
-                    if (!mbar_wait(empty_bar + go % C3_NACC, (uint32_t)((go / C3_NACC - 1) & 1))) {
-                        ok = false;
-                        break;
-                    }
-                    done = go - C3_NACC;
+                // outputs z and, within the item, z + 1 are issued together
+                const int g = min(2, wk.z1 - z);
+                // their accumulators have been read out
+                for (int k = 0; k < g && ok; ++k) {
+                    const int o = go + k;
+                    if (o < C3_NACC) continue;
+                    if (!mbar_wait(empty_bar + o % C3_NACC, (uint32_t)((o / C3_NACC - 1) & 1))) ok = false;
+                    else done = o - C3_NACC;
                 }
-                // slices z - 1 .. z + 1 in flight, then landed
-                while (ok && loaded < min(shi, z + 2) - slo) {
+                // slices z - 1 .. z + g in flight, then landed
+                while (ok && loaded < min(shi, z + g + 1) - slo) {
                     const int f = slot_ready(true);
                     if (f < 0) ok = false;
                     else load();
                 }
-                uint32_t a_lo[3];                                // descriptor low words (0: outside the volume)
+                uint32_t a_lo[4];                                // slices z-1 .. z+2 (0: outside or not used)
 #pragma unroll
-                for (int dz = 0; dz < 3; ++dz) {
-                    const int zi = z + dz - 1;
-                    a_lo[dz] = 0u;
-                    if (!ok || zi < 0 || zi >= a.D) continue;
+                for (int q = 0; q < 4; ++q) {
+                    const int zi = z + q - 1;
+                    a_lo[q] = 0u;
+                    if (!ok || zi < 0 || zi >= a.D || q > g + 1) continue;
                     const int li = gs0 + (zi - slo), sl = li % RS;
                     if (!mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
-                    set_reader(sl, go);
-                    a_lo[dz] = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
+                    set_reader(sl, go + g - 1);                 // the group's MMAs complete together
+                    a_lo[q] = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
                 }
                 if (!ok) break;
                 umma::fence_after_sync();
-                const uint32_t dt = tmem + (uint32_t)((go % C3_NACC) * N);
-                if (KS == 1) conv3_mmas<1>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                else if (KS == 2) conv3_mmas<2>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                else conv3_mmas<4>(dt, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                umma::commit(full_bar + go % C3_NACC);
-                ++go;
-                more = wk.next();
+                const uint32_t dt0 = tmem + (uint32_t)((go % C3_NACC) * N);
+                if (g == 2) {
+                    const uint32_t dt1 = tmem + (uint32_t)(((go + 1) % C3_NACC) * N);
+                    if (KS == 1) conv3_mmas2<1>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                    else if (KS == 2) conv3_mmas2<2>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                    else conv3_mmas2<4>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
+                } else {
+                    const uint32_t a3[3] = {a_lo[0], a_lo[1], a_lo[2]};
+                    if (KS == 1) conv3_mmas<1>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
+                    else if (KS == 2) conv3_mmas<2>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
+                    else conv3_mmas<4>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
+                }
+                for (int k = 0; k < g; ++k) umma::commit(full_bar + (go + k) % C3_NACC);
+                go += g;
+                for (int k = 0; k < g; ++k) more = wk.next();
                 // copy further slices of the item into slots already known free
                 while (slo + loaded < shi && slot_ready(false) == 1) load();
             }
@@ -517,9 +561,10 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
         Conv3Walk wk(a);
         int go = 0;
         while (wk.next()) {
-            if (*abort_flag) break;
+            // warp-uniform decisions: the TMEM loads below are warp-collective
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
             const int acc_i = go % C3_NACC;
-            if (!mbar_wait(full_bar + acc_i, (uint32_t)((go / C3_NACC) & 1))) {
+            if (!__all_sync(0xffffffffu, mbar_wait(full_bar + acc_i, (uint32_t)((go / C3_NACC) & 1)))) {
                 if (lane == 0) fail();
                 break;
             }
