@@ -149,16 +149,16 @@ cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A,
     a.tiles_x = (W + C3_TX - 1) / C3_TX;
     a.tiles_y = (H + C3_TY - 1) / C3_TY;
     a.rs = conv3_ring(K, N);
+    a.nacc = conv3_nacc(N);
     const size_t smem = conv3_smem(K, N, a.rs);
     // one wave of CTAs looping over the work items: as many per SM as shared
-    // memory and tensor memory (C3_NACC accumulators of N columns) hold
+    // memory and tensor memory (nacc accumulators of N columns) hold
     int dev = 0, sms = 0, smem_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    const int need = C3_NACC * N;
-    const int ncols = need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+    const int ncols = conv3_cols(N);
     const int per_sm = std::max(1, std::min({(int)(smem_sm / (smem + 1024)), 512 / ncols, 8}));
     const long long slots = (long long)per_sm * sms;
     // z-chunks: about four items per resident CTA, at least 8 output depths each

@@ -252,8 +252,8 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 
 // ---------------------------------------------------------------------------
 // k_conv3: the 3x3x3 convolution (zero padding) marching along z, with each
-// input slice staged once by TMA and the 27 taps read from the staged slices
-// through shifted operand descriptors.
+// input slice staged once by TMA and read by one group of MMAs that applies
+// all three of its z-taps at once.
 //
 // A work item is one 8 (x) x 16 (y) column of one volume over a range of
 // output depths.  Output tile (x0, y0, z) has M = 128 rows (row m is voxel
@@ -262,29 +262,39 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 // channels, [y][x][8 channels]: 16 bytes per voxel, so 8 consecutive x of one
 // y form one 8-row core matrix of a K-major operand, the next y row sits 160
 // bytes further (SBO), the next channel group one plane further (LBO).  The A
-// operand of tap (dz, dy, dx) of output z is the slot of slice z + dz - 1 read
-// from byte offset (dy * 10 + dx) * 16: no gather, and each input slice is
-// copied once per column (180 voxels per 128 outputs).  Taps reading a slice
-// outside the volume are left out (their contribution is zero).  The weights
-// of all 27 taps stay in shared memory ([tap][channel group][n][16 bytes]).
+// operand of in-plane tap (dy, dx) is the slot read from byte offset
+// (dy * 10 + dx) * 16: no gather, and each input slice is copied once per
+// column (180 voxels per 128 outputs).
+//
+// Slice zi feeds outputs zi - 1, zi and zi + 1 through z-taps dz = 2, 1, 0.
+// The weights sit in shared memory as [in-plane tap][channel group][n'][16
+// bytes] with n' = (2 - dz) N + n, so the B operand of one in-plane tap is
+// the three z-taps' N x K blocks stacked along N in output-depth order, and
+// the output accumulators sit side by side in TMEM in the same order: one MMA
+// of N' = 3N adds slice zi's contribution to all three outputs (9 MMA groups
+// per input slice instead of 27 per output).  Accumulator a of NACC (N
+// columns each) holds output number q of the CTA with q % NACC = a; where
+// the three outputs' blocks wrap around the end of the ring, the group is two
+// MMAs (N' = N and 2N).  Outputs outside the item or taps reading slices
+// outside the volume are left out.  Since one MMA adds to three outputs at
+// once, none of them starts from "overwrite": the epilogue zeroes an
+// accumulator (tcgen05.st) when it has read it, and all of them at the start.
 //
 // Warp roles: lane 0 of warp 4 issues the slice copies and the MMAs; warps
 // 0-3 run the epilogue (bias, ReLU, mask, BF16 rounding; the k_gemm
-// epilogue), warp w on TMEM lanes 32w .. 32w+31.  The 27 dependent MMAs of an
-// output accumulate into one of C3_NACC TMEM accumulators; two consecutive
-// outputs of an item are issued together, tap by tap in turn, so the tensor
-// cores run two independent chains; full_bar[a] (MMA commit) hands an
-// accumulator to the epilogue and empty_bar[a] (one arrival per epilogue
-// warp) back to the issuer, so the issuer runs up to C3_NACC outputs ahead.  A ring slot is refilled once the MMAs of the last output
-// reading it have completed.  Every wait is bounded; a wait that runs out
-// sets ST_MMA_TIMEOUT and a shared abort flag that every loop checks.
+// epilogue), warp w on TMEM lanes 32w .. 32w+31.  full_bar[a] (MMA commit
+// after the last slice an output reads) hands an accumulator to the
+// epilogue, empty_bar[a] (one arrival per epilogue warp, after the zeroing)
+// back to the issuer; free_bar[s] (MMA commit after a slice's group) frees
+// ring slot s for the next copy.  Every wait is bounded; a wait that runs
+// out sets ST_MMA_TIMEOUT and a shared abort flag that every loop checks.
 // ---------------------------------------------------------------------------
 constexpr int C3_TX = 8, C3_TY = 16;                       // output tile (x, y)
 constexpr int C3_BX = C3_TX + 2, C3_BY = C3_TY + 2;
 constexpr int C3_SLICE = C3_BX * C3_BY * 16;               // bytes of one channel group of one slice (2880)
 constexpr int C3_SPL = ((C3_SLICE + 127) / 128) * 128;     // its plane stride in a slot (2944)
 constexpr int C3_RS = 6;                                   // ring slots (input slices) at most; at least 4
-constexpr int C3_NACC = 4;                                 // TMEM accumulators (outputs in flight)
+constexpr int C3_NACC = 8;                                 // TMEM accumulators at most (4 .. 8 by N)
 constexpr int C3_THREADS = 160;                            // four epilogue warps and the issuing warp
 
 struct Conv3Args {
@@ -303,11 +313,19 @@ struct Conv3Args {
     int nchunks;                 // work items per column: ceil(D / zc)
     int nitems;                  // B * tiles_y * tiles_x * nchunks
     int rs;                      // ring slots (4 .. C3_RS)
+    int nacc;                    // TMEM accumulators (4 .. C3_NACC)
     int *status;
 };
 
+// Accumulators of k_conv3 for N output channels: eight of 16 columns, else four.
+__host__ __device__ constexpr int conv3_nacc(int N) { return N <= 16 ? 8 : 4; }
+// TMEM columns k_conv3 allocates (a power of two >= 32).
+__host__ __device__ constexpr int conv3_cols(int N) {
+    return conv3_nacc(N) * N <= 64 ? 64 : conv3_nacc(N) * N <= 128 ? 128 : conv3_nacc(N) * N <= 256 ? 256 : 512;
+}
+
 __host__ __device__ constexpr size_t conv3_smem(int K, int N, int rs) {
-    return (size_t)27 * K * N * 2 + (size_t)rs * (K / 8) * C3_SPL + (C3_RS + 2 * C3_NACC) * 8 + 32;
+    return (size_t)27 * K * N * 2 + (size_t)rs * (K / 8) * C3_SPL + (2 * C3_RS + 2 * C3_NACC + 1) * 8 + 32;
 }
 
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
@@ -321,116 +339,87 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, i
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// Non-blocking test: has the phase with this parity completed?
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 
-// The (b, z, x0, y0) of every output of a CTA in issue order: work items
-// blockIdx.x, + gridDim.x, ..., each its z range in order.
-struct Conv3Walk {
-    const Conv3Args &a;
-    int item, z, z1, b, x0, y0;
-    __device__ explicit Conv3Walk(const Conv3Args &a_) : a(a_), item((int)blockIdx.x - (int)gridDim.x), z(0), z1(0) {}
-    // advance to the next output; false when the CTA has none left
-    __device__ bool next() {
-        if (++z < z1) return true;
-        item += gridDim.x;
-        if (item >= a.nitems) return false;
+// Item `item` of k_conv3: volume b, column (x0, y0), output depths [z0, z1).
+struct Conv3Item {
+    int b, x0, y0, z0, z1;
+    __device__ Conv3Item(const Conv3Args &a, int item) {
         const int col = item / a.nchunks, ch = item - col * a.nchunks, tpz = a.tiles_x * a.tiles_y;
         b = col / tpz;
         const int r = col - b * tpz, ty = r / a.tiles_x;
         x0 = (r - ty * a.tiles_x) * C3_TX;
         y0 = ty * C3_TY;
-        z = ch * a.zc;
-        z1 = min(a.D, z + a.zc);
-        return true;
+        z0 = ch * a.zc;
+        z1 = min(a.D, z0 + a.zc);
     }
-    __device__ bool first_of_item() const { return z == (item % a.nchunks) * a.zc; }
 };
 
-// The 27 * KS MMAs of one output, unrolled: the A descriptor of tap (dz, dy, dx)
-// and channel step j is a_lo[dz] + (dy * 10 + dx) + j * 2 * C3_SPL / 16 (low
-// word; slices outside the volume have a_lo[dz] = 0 and are skipped), the B
-// descriptor b_lo + ((tap * KS + j) * 2 N) (16-byte units).
-template <int KS>
-__device__ __forceinline__ void conv3_mmas(uint32_t dt, const uint32_t (&a_lo)[3], uint32_t a_hi, uint32_t b_lo,
-                                           uint32_t b_hi, uint32_t bstep, uint32_t idesc) {
-    asm volatile("" : "+r"(b_lo), "+r"(bstep));
-    uint32_t accum = 0u;
-#pragma unroll
-    for (int dz = 0; dz < 3; ++dz) {
-        if (a_lo[dz] == 0u) continue;
-#pragma unroll
-        for (int t = 0; t < 9; ++t)
-#pragma unroll
-            for (int j = 0; j < KS; ++j) {
-                const uint32_t al = a_lo[dz] + (uint32_t)((t / 3) * C3_BX + t % 3 + j * 2 * (C3_SPL >> 4));
-                const uint32_t bl = b_lo + (uint32_t)((dz * 9 + t) * KS + j) * bstep;
-                const uint64_t ad = ((uint64_t)a_hi << 32) | al, bd = ((uint64_t)b_hi << 32) | bl;
-                umma::mma_bf16(dt, ad, bd, idesc, accum);
-                accum = 1u;
-            }
-    }
-}
-
-// The MMAs of two consecutive outputs (slices z-1 .. z+1 and z .. z+2), tap by
-// tap in turn: their accumulators are independent, so the tensor cores run
-// the two accumulation chains side by side.  a_lo[dz] for output 0 is slice z +
-// dz - 1, for output 1 slice z + dz (a_lo[3]); 0 = outside the volume.
-template <int KS>
-__device__ __forceinline__ void conv3_mmas2(uint32_t dt0, uint32_t dt1, const uint32_t (&a_lo)[4], uint32_t a_hi,
-                                            uint32_t b_lo, uint32_t b_hi, uint32_t bstep, uint32_t idesc) {
+// The MMA group of one input slice: for each in-plane tap t = 3 dy + dx and
+// channel step j, NR MMAs (the run of accumulators before and after the
+// ring's wrap).  A: a_lo + (dy * 10 + dx) + j * 2 * C3_SPL / 16 (low word, 16-byte
+// units); B: b_lo + (t * KS + j) * bstep + bo[r]; D: dt[r], shape id[r].
+template <int KS, int NR>
+__device__ __forceinline__ void conv3_group(uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi,
+                                            uint32_t bstep, const uint32_t (&dt)[2], const uint32_t (&bo)[2],
+                                            const uint32_t (&id)[2]) {
     // an opaque copy of the weight base: the per-tap descriptors are formed here, not hoisted
-    // out of the caller's loop into registers (108 of them with 64 channels)
+    // out of the caller's loop into registers
     asm volatile("" : "+r"(b_lo), "+r"(bstep));
-    uint32_t acc0 = 0u, acc1 = 0u;
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz) {
-        const bool v0 = a_lo[dz] != 0u, v1 = a_lo[dz + 1] != 0u;
+    for (int t = 0; t < 9; ++t)
 #pragma unroll
-        for (int t = 0; t < 9; ++t)
+        for (int j = 0; j < KS; ++j) {
+            const uint64_t ad =
+                ((uint64_t)a_hi << 32) | (a_lo + (uint32_t)((t / 3) * C3_BX + t % 3 + j * 2 * (C3_SPL >> 4)));
+            const uint32_t bl = b_lo + (uint32_t)(t * KS + j) * bstep;
 #pragma unroll
-            for (int j = 0; j < KS; ++j) {
-                const uint32_t off = (uint32_t)((t / 3) * C3_BX + t % 3 + j * 2 * (C3_SPL >> 4));
-                const uint32_t bl = b_lo + (uint32_t)((dz * 9 + t) * KS + j) * bstep;
-                const uint64_t bd = ((uint64_t)b_hi << 32) | bl;
-                if (v0) {
-                    umma::mma_bf16(dt0, ((uint64_t)a_hi << 32) | (a_lo[dz] + off), bd, idesc, acc0);
-                    acc0 = 1u;
-                }
-                if (v1) {
-                    umma::mma_bf16(dt1, ((uint64_t)a_hi << 32) | (a_lo[dz + 1] + off), bd, idesc, acc1);
-                    acc1 = 1u;
-                }
-            }
-    }
+            for (int r = 0; r < NR; ++r) umma::mma_bf16(dt[r], ad, ((uint64_t)b_hi << 32) | (bl + bo[r]), id[r], 1u);
+        }
 }
 
 // map: 5-D over [B][D][H][W][ld] reading channels [0, K), box (8, 10, 18, 1, 1).
 __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
     extern __shared__ __align__(1024) uint8_t sm[];
-    const int K = a.K, N = a.N, KG = K / 8, KS = K / 16;
+    const int K = a.K, N = a.N, KG = K / 8, KS = K / 16, NA = a.nacc;
     const uint32_t w_bytes = 27u * (uint32_t)K * (uint32_t)N * 2u, slot_bytes = (uint32_t)KG * C3_SPL;
     uint8_t *Ws = sm;
     uint8_t *RING = sm + w_bytes;
     const int RS = a.rs;
     uint64_t *in_bar = reinterpret_cast<uint64_t *>(RING + RS * slot_bytes);
-    uint64_t *full_bar = in_bar + C3_RS;
+    uint64_t *free_bar = in_bar + C3_RS;
+    uint64_t *full_bar = free_bar + C3_RS;
     uint64_t *empty_bar = full_bar + C3_NACC;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(empty_bar + C3_NACC);
+    uint64_t *last_bar = empty_bar + C3_NACC;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(last_bar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t need_cols = (uint32_t)(C3_NACC * N);
-    const uint32_t ncols = need_cols <= 64u ? 64u : need_cols <= 128u ? 128u : need_cols <= 256u ? 256u : 512u;
+    const uint32_t ncols = (uint32_t)conv3_cols(N);
 
     if (tid == 0) {
         *abort_flag = 0;
-        for (int i = 0; i < C3_RS + C3_NACC; ++i) mbar_init(in_bar + i, 1);
+        for (int i = 0; i < 2 * C3_RS + C3_NACC; ++i) mbar_init(in_bar + i, 1);   // in, free, full
         for (int i = 0; i < C3_NACC; ++i) mbar_init(empty_bar + i, 4);
+        mbar_init(last_bar, 1);
         fence_barrier_init();
     }
     if (warp == 0) umma::tmem_alloc(tslot, ncols);
-    // weights of all taps: [t][kg][n][16 bytes] from [t][n][K]
+    // weights: [t9][kg][n' = (2 - dz) N + n][16 bytes] from [dz * 9 + t9][n][K]
     for (int q = tid; q < 27 * KG * N; q += C3_THREADS) {
-        const int n = q % N, tk = q / N, kg = tk % KG, t = tk / KG;
-        umma::cp_async16(Ws + (size_t)q * 16, a.Wt + ((size_t)t * N + n) * K + kg * 8, 16u);
+        const int np = q % (3 * N), tk = q / (3 * N), kg = tk % KG, t9 = tk / KG;
+        const int dz = 2 - np / N, n = np - (2 - dz) * N;
+        umma::cp_async16(Ws + (size_t)q * 16, a.Wt + ((size_t)(dz * 9 + t9) * N + n) * K + kg * 8, 16u);
     }
     umma::cp_async_commit();
     umma::cp_async_wait<0>();
@@ -439,6 +428,14 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
     __syncthreads();
     umma::fence_after_sync();
     const uint32_t tmem = *tslot;
+    // every accumulator starts at zero (the MMAs only add)
+    if (warp < 4) {
+        for (int c = 0; c < NA * N; c += 16) umma::tmem_st16_zero(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c);
+        umma::tmem_st_wait();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
     auto fail = [&]() {
         atomicOr(a.status, ST_MMA_TIMEOUT);
         *abort_flag = 1;
@@ -447,178 +444,175 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
     if (warp == 4) {
         if (lane == 0) {
             // ---- copies and MMAs ----
-            const uint32_t idesc = umma::idesc_bf16(GM, N);
-            // descriptors of slot 0, tap (0, 0), channel group 0 / weight slab 0; a slot,
-            // tap, channel step or weight slab only moves the start address (bits 0-13,
-            // in 16-byte units; every address stays below 256 KB)
+            const uint32_t id1 = umma::idesc_bf16(GM, N), id2 = umma::idesc_bf16(GM, 2 * N),
+                           id3 = umma::idesc_bf16(GM, 3 * N);
+            auto idn = [&](int k) { return k == 1 ? id1 : k == 2 ? id2 : id3; };   // N' = k N
+            // descriptors of slot 0, tap (0, 0), channel group 0 / weight plane 0, row 0; a
+            // slot, tap, channel step, weight plane or row block only moves the start
+            // address (bits 0-13, in 16-byte units; every address stays below 256 KB)
             const uint64_t a_desc0 = umma::desc(umma::smem_addr(RING), C3_SPL, C3_BX * 16);
-            const uint64_t b_desc0 = umma::desc(umma::smem_addr(Ws), (uint32_t)N * 16, 128);
+            const uint64_t b_desc0 = umma::desc(umma::smem_addr(Ws), 3u * (uint32_t)N * 16, 128);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
-            const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32), bstep = 2u * (uint32_t)N;
-            // go: outputs issued; gs: slices loaded (slot gs % RS, in_bar phase gs / RS);
-            // reader[s]: the last output reading slot s (-1: none); done: every output up to
-            // it has completed (the issuer saw its epilogue release the accumulator).  A
-            // reader after done is waited for; its barrier has no later phase in flight,
-            // since output reader + C3_NACC is issued only after that release.
-            int go = 0, gs = 0, gs0 = 0, slo = 0, shi = 0, loaded = 0, done = -1;
-            // (kept in registers: every access selects its slot with unrolled compares)
-            int reader[C3_RS];
-#pragma unroll
-            for (int s = 0; s < C3_RS; ++s) reader[s] = -1;       // slots RS .. C3_RS - 1 unused
-            auto reader_of = [&](int slot) {
-                int r = -1;
-#pragma unroll
-                for (int s = 0; s < C3_RS; ++s)
-                    if (s == slot) r = reader[s];
-                return r;
-            };
-            auto set_reader = [&](int slot, int v) {
-#pragma unroll
-                for (int s = 0; s < C3_RS; ++s)
-                    if (s == slot) reader[s] = v;
-            };
-            Conv3Walk wk(a);
-            bool ok = true;
-            auto slot_ready = [&](bool can_wait) -> int {   // 1 free, 0 not known, -1 wait ran out
-                const int rd = reader_of(gs % RS);
-                if (rd <= done) return 1;
-                if (!can_wait) return 0;
-                return mbar_wait(full_bar + rd % C3_NACC, (uint32_t)((rd / C3_NACC) & 1)) ? 1 : -1;
-            };
-            auto load = [&]() {
-                const int s = gs % RS, zi = slo + loaded;
-                set_reader(s, -1);
-                mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
-                for (int kg = 0; kg < KG; ++kg)
-                    tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, wk.x0 - 1, wk.y0 - 1, zi, wk.b,
-                                in_bar + s);
-                ++loaded;
-                ++gs;
-            };
-            bool more = wk.next();
-            while (ok && more) {
-                if (*abort_flag) break;
-                const int z = wk.z;
-                if (wk.first_of_item()) {
-                    slo = max(0, z - 1);
-                    shi = min(a.D, wk.z1 + 1);
-                    gs0 = gs;
-                    loaded = 0;
+            const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32), bstep = 6u * (uint32_t)N;
+            // gs: slices copied by this CTA (slice g in slot g % RS, its use g / RS of the
+            // slot); gw: slices whose copy has been waited for; q0: outputs of earlier items
+            int gs = 0, gw = 0, q0 = 0;
+            bool ok = true, issued = false;
+            for (int item = blockIdx.x; ok && item < a.nitems; item += gridDim.x) {
+                const Conv3Item wk(a, item);
+                const int lo = max(0, wk.z0 - 1), hi = min(a.D, wk.z1 + 1);   // input slices
+                const int gs0 = gs;
+                int alloc = wk.z0 - 1;            // outputs up to alloc hold an accumulator
+                auto load = [&]() {
+                    const int s = gs % RS, zi = lo + (gs - gs0);
+                    mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
+                    for (int kg = 0; kg < KG; ++kg)
+                        tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, wk.x0 - 1, wk.y0 - 1, zi, wk.b,
+                                    in_bar + s);
+                    ++gs;
+                };
+                // the slot of the next copy is free: its previous slice's MMAs have completed
+                // (1 free, 0 not yet, -1 the wait ran out)
+                auto slot_free = [&](bool wait) -> int {
+                    const int u = gs / RS;
+                    if (u == 0) return 1;
+                    uint64_t *fb = free_bar + gs % RS;
+                    const uint32_t par = (uint32_t)((u - 1) & 1);
+                    if (!wait) return mbar_test(fb, par) ? 1 : 0;
+                    return mbar_wait(fb, par) ? 1 : -1;
+                };
+                for (int zi = lo; zi < hi; ++zi) {
+                    if (*abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const int oa = max(wk.z0, zi - 1), ob = min(wk.z1 - 1, zi + 1);   // outputs slice zi feeds
+                    // accumulators of the outputs it feeds first, once the epilogue has released them
+                    while (ok && alloc < ob) {
+                        const int q = q0 + (++alloc - wk.z0);
+                        if (q >= NA && !mbar_wait(empty_bar + q % NA, (uint32_t)((q / NA - 1) & 1))) ok = false;
+                    }
+                    // slice zi copied and landed
+                    while (ok && gs - gs0 <= zi - lo) {
+                        const int f = slot_free(true);
+                        if (f < 0) ok = false;
+                        else load();
+                    }
+                    const int li = gs0 + (zi - lo), sl = li % RS;
+                    if (ok && !mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
+                    if (!ok) break;
+                    gw = li + 1;
+                    umma::fence_after_sync();
+                    // outputs oa .. ob in accumulators (q0 + o - z0) % NA, split where the ring wraps
+                    const int n = ob - oa + 1, c0 = (q0 + oa - wk.z0) % NA, n1 = min(n, NA - c0);
+                    const uint32_t al = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
+                    const uint32_t bo0 = (uint32_t)((oa - zi + 1) * N);
+                    const uint32_t dt[2] = {tmem + (uint32_t)(c0 * N), tmem};
+                    const uint32_t bo[2] = {bo0, bo0 + (uint32_t)(n1 * N)};
+                    const uint32_t id[2] = {idn(n1), idn(n - n1)};
+                    if (n1 == n) {
+                        if (KS == 1) conv3_group<1, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else if (KS == 2) conv3_group<2, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else conv3_group<4, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                    } else {
+                        if (KS == 1) conv3_group<1, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else if (KS == 2) conv3_group<2, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else conv3_group<4, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                    }
+                    issued = true;
+                    umma::commit(free_bar + sl);
+                    // outputs whose last input slice is zi: zi - 1, and zi itself at the volume's end
+                    if (zi - 1 >= wk.z0) umma::commit(full_bar + (q0 + zi - 1 - wk.z0) % NA);
+                    if (zi == a.D - 1 && zi >= wk.z0 && zi < wk.z1) umma::commit(full_bar + (q0 + zi - wk.z0) % NA);
+                    // further slices of the item into slots already free
+                    while (lo + (gs - gs0) < hi && slot_free(false) == 1) load();
                 }
-                // outputs z and, within the item, z + 1 are issued together
-                const int g = min(2, wk.z1 - z);
-                // their accumulators have been read out
-                for (int k = 0; k < g && ok; ++k) {
-                    const int o = go + k;
-                    if (o < C3_NACC) continue;
-                    if (!mbar_wait(empty_bar + o % C3_NACC, (uint32_t)((o / C3_NACC - 1) & 1))) ok = false;
-                    else done = o - C3_NACC;
-                }
-                // slices z - 1 .. z + g in flight, then landed
-                while (ok && loaded < min(shi, z + g + 1) - slo) {
-                    const int f = slot_ready(true);
-                    if (f < 0) ok = false;
-                    else load();
-                }
-                uint32_t a_lo[4];                                // slices z-1 .. z+2 (0: outside or not used)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int zi = z + q - 1;
-                    a_lo[q] = 0u;
-                    if (!ok || zi < 0 || zi >= a.D || q > g + 1) continue;
-                    const int li = gs0 + (zi - slo), sl = li % RS;
-                    if (!mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
-                    set_reader(sl, go + g - 1);                 // the group's MMAs complete together
-                    a_lo[q] = a_lo0 + (uint32_t)sl * (slot_bytes >> 4);
-                }
-                if (!ok) break;
-                umma::fence_after_sync();
-                const uint32_t dt0 = tmem + (uint32_t)((go % C3_NACC) * N);
-                if (g == 2) {
-                    const uint32_t dt1 = tmem + (uint32_t)(((go + 1) % C3_NACC) * N);
-                    if (KS == 1) conv3_mmas2<1>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                    else if (KS == 2) conv3_mmas2<2>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                    else conv3_mmas2<4>(dt0, dt1, a_lo, a_hi, b_lo0, b_hi, bstep, idesc);
-                } else {
-                    const uint32_t a3[3] = {a_lo[0], a_lo[1], a_lo[2]};
-                    if (KS == 1) conv3_mmas<1>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
-                    else if (KS == 2) conv3_mmas<2>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
-                    else conv3_mmas<4>(dt0, a3, a_hi, b_lo0, b_hi, bstep, idesc);
-                }
-                for (int k = 0; k < g; ++k) umma::commit(full_bar + (go + k) % C3_NACC);
-                go += g;
-                for (int k = 0; k < g; ++k) more = wk.next();
-                // copy further slices of the item into slots already known free
-                while (slo + loaded < shi && slot_ready(false) == 1) load();
+                q0 += wk.z1 - wk.z0;
             }
             if (!ok) fail();
+            // leave only after the copies in flight have landed and the MMAs have completed
+            for (; gw < gs; ++gw) mbar_wait(in_bar + gw % RS, (uint32_t)((gw / RS) & 1));
+            if (issued) {
+                umma::commit(last_bar);
+                mbar_wait(last_bar, 0u);
+            }
         }
         __syncwarp();
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32w .. 32w+31 ----
         const bool b16 = a.bias && (reinterpret_cast<uintptr_t>(a.bias) & 15u) == 0;
         const float4 *bias4 = b16 ? reinterpret_cast<const float4 *>(a.bias) : nullptr;
-        Conv3Walk wk(a);
-        int go = 0;
-        while (wk.next()) {
-            // warp-uniform decisions: the TMEM loads below are warp-collective
-            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
-            const int acc_i = go % C3_NACC;
-            if (!__all_sync(0xffffffffu, mbar_wait(full_bar + acc_i, (uint32_t)((go / C3_NACC) & 1)))) {
-                if (lane == 0) fail();
-                break;
-            }
-            umma::fence_after_sync();
-            const int m = warp * 32 + lane, x = wk.x0 + (m & 7), y = wk.y0 + (m >> 3);
-            const bool ok = x < a.W && y < a.H;
-            const long long o = (((long long)wk.b * a.D + wk.z) * a.H + y) * a.W + x;
-            bf16 *orow = a.out + o * a.ldo;
-            const bf16 *mrow = a.mask ? a.mask + o * a.ldm : nullptr;
-            for (int c = 0; c < N; c += 16) {
-                float acc[16];
-                umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc_i * N + c), acc);
-                if (!ok) continue;
-                if (bias4) {
+        int q = 0;                                    // outputs of this CTA so far (issue order)
+        bool stop = false;
+        for (int item = blockIdx.x; !stop && item < a.nitems; item += gridDim.x) {
+            const Conv3Item wk(a, item);
+            for (int z = wk.z0; z < wk.z1; ++z, ++q) {
+                // warp-uniform decisions: the TMEM loads and stores below are warp-collective
+                if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                    stop = true;
+                    break;
+                }
+                const int acc_i = q % NA;
+                if (!__all_sync(0xffffffffu, mbar_wait(full_bar + acc_i, (uint32_t)((q / NA) & 1)))) {
+                    if (lane == 0) fail();
+                    stop = true;
+                    break;
+                }
+                umma::fence_after_sync();
+                const int m = warp * 32 + lane, x = wk.x0 + (m & 7), y = wk.y0 + (m >> 3);
+                const bool ok = x < a.W && y < a.H;
+                const long long o = (((long long)wk.b * a.D + z) * a.H + y) * a.W + x;
+                bf16 *orow = a.out + o * a.ldo;
+                const bf16 *mrow = a.mask ? a.mask + o * a.ldm : nullptr;
+                for (int c = 0; c < N; c += 16) {
+                    float acc[16];
+                    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc_i * N + c);
+                    umma::tmem_ld16(ta, acc);
+                    umma::tmem_st16_zero(ta);             // ready for the accumulator's next output
+                    if (!ok) continue;
+                    if (bias4) {
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 bv = __ldg(bias4 + c / 4 + i);
-                        acc[4 * i] += bv.x;
-                        acc[4 * i + 1] += bv.y;
-                        acc[4 * i + 2] += bv.z;
-                        acc[4 * i + 3] += bv.w;
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 bv = __ldg(bias4 + c / 4 + i);
+                            acc[4 * i] += bv.x;
+                            acc[4 * i + 1] += bv.y;
+                            acc[4 * i + 2] += bv.z;
+                            acc[4 * i + 3] += bv.w;
+                        }
+                    } else if (a.bias) {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
                     }
-                } else if (a.bias) {
+                    if (a.relu) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[i] += __ldg(a.bias + c + i);
-                }
-                if (a.relu) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[i] = fmaxf(acc[i], 0.f);
-                }
-                if (mrow) {
-                    const uint4 m0v = *reinterpret_cast<const uint4 *>(mrow + c);
-                    const uint4 m1v = *reinterpret_cast<const uint4 *>(mrow + c + 8);
-                    const bf16 *mh0 = reinterpret_cast<const bf16 *>(&m0v);
-                    const bf16 *mh1 = reinterpret_cast<const bf16 *>(&m1v);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        if (!(__bfloat162float(mh0[i]) > 0.f)) acc[i] = 0.f;
-                        if (!(__bfloat162float(mh1[i]) > 0.f)) acc[8 + i] = 0.f;
+                        for (int i = 0; i < 16; ++i) acc[i] = fmaxf(acc[i], 0.f);
                     }
+                    if (mrow) {
+                        const uint4 m0v = *reinterpret_cast<const uint4 *>(mrow + c);
+                        const uint4 m1v = *reinterpret_cast<const uint4 *>(mrow + c + 8);
+                        const bf16 *mh0 = reinterpret_cast<const bf16 *>(&m0v);
+                        const bf16 *mh1 = reinterpret_cast<const bf16 *>(&m1v);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            if (!(__bfloat162float(mh0[i]) > 0.f)) acc[i] = 0.f;
+                            if (!(__bfloat162float(mh1[i]) > 0.f)) acc[8 + i] = 0.f;
+                        }
+                    }
+                    uint4 o0, o1;
+                    o0.x = pack2(acc[0], acc[1]);   o0.y = pack2(acc[2], acc[3]);
+                    o0.z = pack2(acc[4], acc[5]);   o0.w = pack2(acc[6], acc[7]);
+                    o1.x = pack2(acc[8], acc[9]);   o1.y = pack2(acc[10], acc[11]);
+                    o1.z = pack2(acc[12], acc[13]); o1.w = pack2(acc[14], acc[15]);
+                    *reinterpret_cast<uint4 *>(orow + c) = o0;
+                    *reinterpret_cast<uint4 *>(orow + c + 8) = o1;
                 }
-                uint4 o0, o1;
-                o0.x = pack2(acc[0], acc[1]);   o0.y = pack2(acc[2], acc[3]);
-                o0.z = pack2(acc[4], acc[5]);   o0.w = pack2(acc[6], acc[7]);
-                o1.x = pack2(acc[8], acc[9]);   o1.y = pack2(acc[10], acc[11]);
-                o1.z = pack2(acc[12], acc[13]); o1.w = pack2(acc[14], acc[15]);
-                *reinterpret_cast<uint4 *>(orow + c) = o0;
-                *reinterpret_cast<uint4 *>(orow + c + 8) = o1;
+                // the accumulator goes back to the issuer once this warp's TMEM reads and
+                // zeroing are done
+                umma::tmem_st_wait();
+                umma::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty_bar + acc_i);
             }
-            // the accumulator goes back to the issuer once this warp's TMEM reads are done
-            umma::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(empty_bar + acc_i);
-            ++go;
         }
     }
     umma::fence_before_sync();

@@ -99,6 +99,47 @@ def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, mas
         assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
 
 
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 32), (16, 64)])
+def test_tma_conv3_accumulator_ring_on_a_large_volume(ub, cin, cout):
+    """A 48x128x128 volume: 768 work items of 8 output depths, more than the
+    resident CTAs, so CTAs take several items and the MMA groups that add one
+    input slice to three outputs' accumulators meet the end of the TMEM ring
+    (two MMAs there).  The same bits as the row-gather kernel, and outputs
+    sampled over the volume (its faces, edges and corners included) within the
+    oracle bound, each from the oracle's convolution of its 3x3x3 neighbourhood."""
+    import torch
+    r = _rng(11 * cin + cout)
+    B, D, H, W = 1, 48, 128, 128
+    x = _bf(r.normal(size=(B, D, H, W, cin))).cuda()
+    w = _bf(r.normal(0, (27 * cin) ** -0.5, size=(27, cout, cin))).cuda()
+    b = torch.from_numpy(r.normal(size=cout).astype(np.float32)).cuda()
+    outs = []
+    for tma in (True, False):
+        prev = ub.set_tma_conv(tma)
+        try:
+            outs.append(ub.conv3(x, w, b, relu=False))
+            torch.cuda.synchronize()
+        finally:
+            ub.set_tma_conv(prev)
+    assert torch.equal(outs[0], outs[1])
+    zs = np.concatenate([[0, D - 1, 7, 8, 15, 16], r.integers(0, D, 250)])
+    ys = np.concatenate([[0, H - 1, 15, 16, 0, H - 1], r.integers(0, H, 250)])
+    xs = np.concatenate([[0, W - 1, 7, 8, W - 1, 0], r.integers(0, W, 250)])
+    xd = x[0].float().cpu().numpy().astype(np.float64)
+    got = outs[0][0].float().cpu().numpy().astype(np.float64)
+    wd, bd = _np(w), _np(b)
+    refs, gots = [], []
+    for z, y, xx in zip(zs, ys, xs):
+        crop = np.zeros((3, 3, 3, cin))
+        z0, z1, y0, y1, x0, x1 = max(z - 1, 0), min(z + 2, D), max(y - 1, 0), min(y + 2, H), max(xx - 1, 0), min(xx + 2, W)
+        crop[z0 - z + 1:z1 - z + 1, y0 - y + 1:y1 - y + 1, x0 - xx + 1:x1 - xx + 1] = xd[z0:z1, y0:y1, x0:x1]
+        refs.append(U.conv3(crop, wd, bd)[1, 1, 1])
+        gots.append(got[z, y, xx])
+    refs, gots = np.array(refs), np.array(gots)
+    err = np.abs(gots - refs)
+    assert np.all(err <= 2.0 ** -8 * np.abs(refs) + 1e-5 * np.abs(refs).max()), err.max()
+
+
 @pytest.mark.parametrize("cin,cout", [(16, 16), (32, 64), (256, 128)])
 def test_conv3_weight_gradient_matches_oracle(ub, cin, cout):
     import torch
