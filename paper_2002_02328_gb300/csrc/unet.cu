@@ -120,46 +120,58 @@ cudaError_t prepare_kernels() {
 int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
 // The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
-// multiple of 16 up to 64, K of 16, 32 or 64 channels, the 27 taps' weights and the
-// ring of input slices within kConv3SmemMax, rows 16-byte aligned.
-// Process-wide switch (bd3mg_unet_set_tma_conv).
+// multiple of 16 up to 64, K of 16, 32 or 64 channels, the 27 taps' weights of
+// N (or, in two launches, N / 2) output channels and a ring of four input
+// slices within kConv3SmemMax, rows 16-byte aligned.  Process-wide switch
+// (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
-// Ring slots of k_conv3: the most (up to C3_RS, at least 4) whose shared memory fits.
-int conv3_ring(int K, int N) {
-    for (int rs = C3_RS; rs >= 4; --rs)
-        if (conv3_smem(K, N, rs) <= kConv3SmemMax) return rs;
+// Launches over the output channels: one, or two of N / 2 where the weights of
+// all N do not fit beside the ring (0: neither fits).
+int conv3_parts(int K, int N) {
+    for (int parts = 1; parts <= 2; parts *= 2)
+        if ((N / parts) % 16 == 0 && conv3_smem(K, N / parts, 4) <= kConv3SmemMax) return parts;
     return 0;
 }
 
 bool conv3_fits(const bf16 *A, int lda, int K, int N) {
     return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 64 && (K == 16 || K == 32 || K == 64) && lda % 8 == 0 &&
-           (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_ring(K, N) > 0;
+           (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_parts(K, N) > 0;
 }
 
-cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt, int N,
-                      const float *bias, int relu, const bf16 *mask, int ldm, bf16 *out, int ldo, int *status) {
-    CUtensorMap map;
-    if (!bd3mg::encode_act_map(&map, A, K, lda, W, H, D, B, C3_BX, C3_BY, 1)) return cudaErrorInvalidValue;
+// One k_conv3 launch over output channels [0, N) of weights with wn rows per tap.
+cudaError_t conv3_launch(cudaStream_t s, const CUtensorMap &map, int B, int D, int H, int W, int K, const bf16 *Wt,
+                         int wn, int N, const float *bias, int relu, const bf16 *mask, int ldm, bf16 *out, int ldo,
+                         int *status) {
     Conv3Args a{};
     a.B = B; a.D = D; a.H = H; a.W = W;
-    a.K = K; a.N = N; a.Wt = Wt;
+    a.K = K; a.N = N; a.Wt = Wt; a.wn = wn;
     a.bias = bias; a.relu = relu; a.mask = mask; a.ldm = ldm;
     a.out = out; a.ldo = ldo; a.status = status;
     a.tiles_x = (W + C3_TX - 1) / C3_TX;
     a.tiles_y = (H + C3_TY - 1) / C3_TY;
-    a.rs = conv3_ring(K, N);
     a.nacc = conv3_nacc(N);
-    const size_t smem = conv3_smem(K, N, a.rs);
-    // one wave of CTAs looping over the work items: as many per SM as shared
-    // memory and tensor memory (nacc accumulators of N columns) hold
     int dev = 0, sms = 0, smem_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    const int ncols = conv3_cols(N);
-    const int per_sm = std::max(1, std::min({(int)(smem_sm / (smem + 1024)), 512 / ncols, 8}));
+    // one wave of CTAs looping over the work items: the ring size (4 .. C3_RS
+    // slices) that gives the most CTAs per SM that shared memory and tensor
+    // memory (nacc accumulators of N columns) hold, the largest ring among those
+    int per_sm = 0;
+    a.rs = 0;
+    for (int rs = 4; rs <= C3_RS; ++rs) {
+        const size_t sm = conv3_smem(K, N, rs);
+        if (sm > kConv3SmemMax) break;
+        const int c = std::max(1, std::min({(int)(smem_sm / (sm + 1024)), 512 / conv3_cols(N), 8}));
+        if (c >= per_sm) {
+            per_sm = c;
+            a.rs = rs;
+        }
+    }
+    if (a.rs == 0) return cudaErrorInvalidValue;
+    const size_t smem = conv3_smem(K, N, a.rs);
     const long long slots = (long long)per_sm * sms;
     // z-chunks: about four items per resident CTA, at least 8 output depths each
     const long long cols = (long long)B * a.tiles_x * a.tiles_y;
@@ -172,6 +184,22 @@ cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A,
     const long long grid = std::min<long long>(a.nitems, slots);
     k_conv3<<<(unsigned)std::max<long long>(1, grid), C3_THREADS, smem, s>>>(map, a);
     return cudaGetLastError();
+}
+
+cudaError_t conv3_tma(cudaStream_t s, int B, int D, int H, int W, const bf16 *A, int lda, int K, const bf16 *Wt, int N,
+                      const float *bias, int relu, const bf16 *mask, int ldm, bf16 *out, int ldo, int *status) {
+    CUtensorMap map;
+    if (!bd3mg::encode_act_map(&map, A, K, lda, W, H, D, B, C3_BX, C3_BY, 1)) return cudaErrorInvalidValue;
+    const int parts = conv3_parts(K, N);
+    if (parts == 0) return cudaErrorInvalidValue;
+    const int np = N / parts;
+    for (int p = 0; p < parts; ++p) {
+        const int n0 = p * np;
+        const cudaError_t e = conv3_launch(s, map, B, D, H, W, K, Wt + (size_t)n0 * K, N, np, bias ? bias + n0 : nullptr,
+                                           relu, mask ? mask + n0 : nullptr, ldm, out + n0, ldo, status);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // Launch one implicit GEMM (see GemmArgs).  UPFWD launches 8 grid rows (taps).

@@ -301,7 +301,8 @@ struct Conv3Args {
     int B, D, H, W;
     int K;                       // input channels (multiple of 16)
     int N;                       // output channels (multiple of 16, <= 64)
-    const bf16 *Wt;              // [27][N][K]
+    const bf16 *Wt;              // [27][wn][K]: rows 0 .. N-1 of each tap
+    int wn;                      // rows of Wt per tap (>= N)
     const float *bias;           // [N] or null
     int relu;
     const bf16 *mask;            // out *= (mask > 0) per element, rows of ldm; or null
@@ -415,11 +416,11 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
         fence_barrier_init();
     }
     if (warp == 0) umma::tmem_alloc(tslot, ncols);
-    // weights: [t9][kg][n' = (2 - dz) N + n][16 bytes] from [dz * 9 + t9][n][K]
+    // weights: [t9][kg][n' = (2 - dz) N + n][16 bytes] from [dz * 9 + t9][n][K] (rows of wn)
     for (int q = tid; q < 27 * KG * N; q += C3_THREADS) {
         const int np = q % (3 * N), tk = q / (3 * N), kg = tk % KG, t9 = tk / KG;
         const int dz = 2 - np / N, n = np - (2 - dz) * N;
-        umma::cp_async16(Ws + (size_t)q * 16, a.Wt + ((size_t)(dz * 9 + t9) * N + n) * K + kg * 8, 16u);
+        umma::cp_async16(Ws + (size_t)q * 16, a.Wt + ((size_t)(dz * 9 + t9) * a.wn + n) * K + kg * 8, 16u);
     }
     umma::cp_async_commit();
     umma::cp_async_wait<0>();
