@@ -375,7 +375,7 @@ bd3mg_status forward(bd3mg_unet *n, int B, int D, int H, int W, const float *inp
     const int L = n->L;
     auto dims = [&](int l, int &d, int &h, int &w) { d = D >> l; h = H >> l; w = W >> l; };
     const long long V0 = (long long)B * D * H * W;
-    k_pack_input<<<grid_for(V0 * 16), 256, 0, s>>>(inp, n->p.cin, V0, b.in0);
+    k_pack_input<<<grid_for(V0), 256, 0, s>>>(inp, n->p.cin, V0, b.in0);
     UCK(cudaGetLastError());
     for (int l = 0; l < L; ++l) {
         int d, h, w;
@@ -386,7 +386,11 @@ bd3mg_status forward(bd3mg_unet *n, int B, int D, int H, int W, const float *inp
         if (l > 0) {
             const int cp = n->c[l - 1];
             const long long cnt = (long long)B * d * h * w * cp;
-            k_maxpool<<<grid_for(cnt), 256, 0, s>>>(b.cat[l - 1], 2 * cp, cp, B, d, h, w, b.pool[l], b.arg[l]);
+            if (cp % 8 == 0 && (reinterpret_cast<uintptr_t>(b.cat[l - 1]) & 15u) == 0 &&
+                (reinterpret_cast<uintptr_t>(b.pool[l]) & 15u) == 0 && (reinterpret_cast<uintptr_t>(b.arg[l]) & 7u) == 0)
+                k_maxpool8<<<grid_for(cnt / 8), 256, 0, s>>>(b.cat[l - 1], 2 * cp, cp, B, d, h, w, b.pool[l], b.arg[l]);
+            else
+                k_maxpool<<<grid_for(cnt), 256, 0, s>>>(b.cat[l - 1], 2 * cp, cp, B, d, h, w, b.pool[l], b.arg[l]);
             UCK(cudaGetLastError());
             src = b.pool[l];
             ldsrc = cp;

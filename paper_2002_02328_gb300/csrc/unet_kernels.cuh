@@ -820,6 +820,52 @@ __global__ void k_maxpool(const bf16 *in, int ld, int C, int B, int D, int H, in
     }
 }
 
+// k_maxpool over 8 channels per thread (C and ld multiples of 8, in 16-byte
+// aligned): the same comparisons in the same tap order, one 16-byte load per tap.
+__global__ void k_maxpool8(const bf16 *in, int ld, int C, int B, int D, int H, int W, bf16 *out, uint8_t *arg) {
+    const int G = C / 8;
+    const long long n = (long long)B * D * H * W * G;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(i % G);
+        long long v = i / G;
+        const long long vo = v;
+        const int x = (int)(v % W); v /= W;
+        const int y = (int)(v % H); v /= H;
+        const int z = (int)(v % D);
+        const int b = (int)(v / D);
+        float best[8];
+        uint32_t bi[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            best[c] = -INFINITY;
+            bi[c] = 0u;
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int az = a >> 2, ay = (a >> 1) & 1, ax = a & 1;
+            const long long u = (((long long)b * 2 * D + 2 * z + az) * (2LL * H) + 2 * y + ay) * (2LL * W) + 2 * x + ax;
+            const uint4 q = *reinterpret_cast<const uint4 *>(in + u * ld + 8 * g);
+            const bf16 *hv = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float val = __bfloat162float(hv[c]);
+                if (val > best[c]) {
+                    best[c] = val;
+                    bi[c] = (uint32_t)a;
+                }
+            }
+        }
+        uint4 o;
+        o.x = pack2(best[0], best[1]); o.y = pack2(best[2], best[3]);
+        o.z = pack2(best[4], best[5]); o.w = pack2(best[6], best[7]);
+        *reinterpret_cast<uint4 *>(out + vo * C + 8 * g) = o;
+        uint2 ar;
+        ar.x = bi[0] | (bi[1] << 8) | (bi[2] << 16) | (bi[3] << 24);
+        ar.y = bi[4] | (bi[5] << 8) | (bi[6] << 16) | (bi[7] << 24);
+        *reinterpret_cast<uint2 *>(arg + vo * C + 8 * g) = ar;
+    }
+}
+
 // Gradient at the output of a ReLU layer whose activation act (rows of lda)
 // feeds both a skip path (gradient dskip, rows of lds, may be null) and a 2x2x2
 // max pooling (gradient dpool on the coarse grid, argmax arg; may be null):
@@ -850,19 +896,41 @@ __global__ void k_pool_bwd(const bf16 *dskip, int lds, const bf16 *dpool, const 
 
 // Network input [V][cin] FP32 -> BF16 rows of 16 channels (zero padded).
 __global__ void k_pack_input(const float *inp, int cin, long long V, bf16 *out) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i & 15);
-        const long long v = i >> 4;
-        out[i] = __float2bfloat16_rn(c < cin ? inp[v * cin + c] : 0.f);
+    // one voxel per thread: its 16 channels (cin <= 16 given, the rest zero) as two
+    // 16-byte stores
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        float f[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) f[c] = c < cin ? inp[v * cin + c] : 0.f;
+        uint4 o0, o1;
+        o0.x = pack2(f[0], f[1]);   o0.y = pack2(f[2], f[3]);
+        o0.z = pack2(f[4], f[5]);   o0.w = pack2(f[6], f[7]);
+        o1.x = pack2(f[8], f[9]);   o1.y = pack2(f[10], f[11]);
+        o1.z = pack2(f[12], f[13]); o1.w = pack2(f[14], f[15]);
+        uint4 *op = reinterpret_cast<uint4 *>(out + v * 16);
+        op[0] = o0;
+        op[1] = o1;
     }
 }
 
 // Head: pred[v] = base[v] + b + sum_c w[c] h[v][c] (1x1x1 convolution, residual output).
 __global__ void k_head_fwd(const bf16 *h, int C, long long V, const float *w, const float *b, const float *base,
                            float *pred) {
+    // rows of 8-channel multiples on 16-byte boundaries are read 8 channels per load
+    const bool vec = (C & 7) == 0 && (reinterpret_cast<uintptr_t>(h) & 15u) == 0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
         float s = 0.f;
-        for (int c = 0; c < C; ++c) s = fmaf(w[c], __bfloat162float(h[v * C + c]), s);
+        if (vec) {
+            const uint4 *hp = reinterpret_cast<const uint4 *>(h + v * C);
+            for (int c = 0; c < C; c += 8) {
+                const uint4 q = hp[c / 8];
+                const bf16 *hv = reinterpret_cast<const bf16 *>(&q);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) s = fmaf(__ldg(w + c + i), __bfloat162float(hv[i]), s);
+            }
+        } else {
+            for (int c = 0; c < C; ++c) s = fmaf(w[c], __bfloat162float(h[v * C + c]), s);
+        }
         pred[v] = (base ? base[v] : 0.f) + b[0] + s;
     }
 }
