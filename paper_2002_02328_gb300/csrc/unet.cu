@@ -120,22 +120,24 @@ cudaError_t prepare_kernels() {
 int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
 // The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
-// multiple of 16 up to 64, K of 16, 32 or 64 channels, the 27 taps' weights of
-// N (or, in two launches, N / 2) output channels and a ring of four input
-// slices within kConv3SmemMax, rows 16-byte aligned.  Process-wide switch
-// (bd3mg_unet_set_tma_conv).
+// multiple of 16 up to 128, K of 16, 32 or 64 channels, the 27 taps' weights of
+// N (or, in two or four launches, N / 2 or N / 4 <= 64) output channels and a
+// ring of four input slices within kConv3SmemMax, rows 16-byte aligned.
+// Process-wide switch (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
-// Launches over the output channels: one, or two of N / 2 where the weights of
-// all N do not fit beside the ring (0: neither fits).
+// Launches over the output channels: the fewest (1, 2 or 4) whose share of N
+// (a multiple of 16, at most 64) has its weights fit beside the ring (0: none).
 int conv3_parts(int K, int N) {
-    for (int parts = 1; parts <= 2; parts *= 2)
-        if ((N / parts) % 16 == 0 && conv3_smem(K, N / parts, 4) <= kConv3SmemMax) return parts;
+    for (int parts = 1; parts <= 4; parts *= 2)
+        if (N % parts == 0 && (N / parts) % 16 == 0 && N / parts <= 64 &&
+            conv3_smem(K, N / parts, 4) <= kConv3SmemMax)
+            return parts;
     return 0;
 }
 
 bool conv3_fits(const bf16 *A, int lda, int K, int N) {
-    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 64 && (K == 16 || K == 32 || K == 64) && lda % 8 == 0 &&
+    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 128 && (K == 16 || K == 32 || K == 64) && lda % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_parts(K, N) > 0;
 }
 
