@@ -120,24 +120,28 @@ cudaError_t prepare_kernels() {
 int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K, T)); }
 
 // The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
-// multiple of 16 up to 128, K of 16, 32 or 64 channels, the 27 taps' weights of
-// N (or, in two or four launches, N / 2 or N / 4 <= 64) output channels and a
-// ring of four input slices within kConv3SmemMax, rows 16-byte aligned.
-// Process-wide switch (bd3mg_unet_set_tma_conv).
+// multiple of 16 up to 128, K of 16, 32, 64 or 128 channels, the 27 taps'
+// weights of N (or, in 2, 4 or 8 launches, N / parts <= 64) output channels
+// and a ring of four input slices (two where four do not fit with any split)
+// within kConv3SmemMax, rows 16-byte aligned.  Process-wide switch
+// (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
-// Launches over the output channels: the fewest (1, 2 or 4) whose share of N
-// (a multiple of 16, at most 64) has its weights fit beside the ring (0: none).
+// Launches over the output channels: the fewest (1, 2, 4 or 8) whose share of
+// N (a multiple of 16, at most 64) has its weights fit beside a ring of four
+// slices, else beside a ring of two (0: none).
 int conv3_parts(int K, int N) {
-    for (int parts = 1; parts <= 4; parts *= 2)
-        if (N % parts == 0 && (N / parts) % 16 == 0 && N / parts <= 64 &&
-            conv3_smem(K, N / parts, 4) <= kConv3SmemMax)
-            return parts;
+    for (int rmin = 4; rmin >= 2; rmin -= 2)
+        for (int parts = 1; parts <= 8; parts *= 2)
+            if (N % parts == 0 && (N / parts) % 16 == 0 && N / parts <= 64 &&
+                conv3_smem(K, N / parts, rmin) <= kConv3SmemMax)
+                return parts;
     return 0;
 }
 
 bool conv3_fits(const bf16 *A, int lda, int K, int N) {
-    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 128 && (K == 16 || K == 32 || K == 64) && lda % 8 == 0 &&
+    return g_tma_conv && N % 16 == 0 && N >= 16 && N <= 128 && (K == 16 || K == 32 || K == 64 || K == 128) &&
+           lda % 8 == 0 &&
            (reinterpret_cast<uintptr_t>(A) & 15u) == 0 && conv3_parts(K, N) > 0;
 }
 
@@ -159,11 +163,12 @@ cudaError_t conv3_launch(cudaStream_t s, const CUtensorMap &map, int B, int D, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
     // one wave of CTAs looping over the work items: the ring size (4 .. C3_RS
-    // slices) that gives the most CTAs per SM that shared memory and tensor
-    // memory (nacc accumulators of N columns) hold, the largest ring among those
+    // slices, or 2 .. 3 where four do not fit) that gives the most CTAs per SM
+    // that shared memory and tensor memory (nacc accumulators of N columns)
+    // hold, the largest ring among those
     int per_sm = 0;
     a.rs = 0;
-    for (int rs = 4; rs <= C3_RS; ++rs) {
+    for (int rs = conv3_smem(K, N, 4) <= kConv3SmemMax ? 4 : 2; rs <= C3_RS; ++rs) {
         const size_t sm = conv3_smem(K, N, rs);
         if (sm > kConv3SmemMax) break;
         const int c = std::max(1, std::min({(int)(smem_sm / (sm + 1024)), 512 / conv3_cols(N), 8}));

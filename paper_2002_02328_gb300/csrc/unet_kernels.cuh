@@ -293,13 +293,13 @@ constexpr int C3_TX = 8, C3_TY = 16;                       // output tile (x, y)
 constexpr int C3_BX = C3_TX + 2, C3_BY = C3_TY + 2;
 constexpr int C3_SLICE = C3_BX * C3_BY * 16;               // bytes of one channel group of one slice (2880)
 constexpr int C3_SPL = ((C3_SLICE + 127) / 128) * 128;     // its plane stride in a slot (2944)
-constexpr int C3_RS = 6;                                   // ring slots (input slices) at most; at least 4
+constexpr int C3_RS = 6;                                   // ring slots (input slices) at most; at least 2
 constexpr int C3_NACC = 8;                                 // TMEM accumulators at most (4 .. 8 by N)
 constexpr int C3_THREADS = 160;                            // four epilogue warps and the issuing warp
 
 struct Conv3Args {
     int B, D, H, W;
-    int K;                       // input channels (multiple of 16)
+    int K;                       // input channels (16, 32, 64 or 128)
     int N;                       // output channels (multiple of 16, <= 64)
     const bf16 *Wt;              // [27][wn][K]: rows 0 .. N-1 of each tap
     int wn;                      // rows of Wt per tap (>= N)
@@ -313,7 +313,7 @@ struct Conv3Args {
     int zc;                      // output depths per work item
     int nchunks;                 // work items per column: ceil(D / zc)
     int nitems;                  // B * tiles_y * tiles_x * nchunks
-    int rs;                      // ring slots (4 .. C3_RS)
+    int rs;                      // ring slots (2 .. C3_RS)
     int nacc;                    // TMEM accumulators (4 .. C3_NACC)
     int *status;
 };
@@ -514,11 +514,13 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                     if (n1 == n) {
                         if (KS == 1) conv3_group<1, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
                         else if (KS == 2) conv3_group<2, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
-                        else conv3_group<4, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else if (KS == 4) conv3_group<4, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else conv3_group<8, 1>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
                     } else {
                         if (KS == 1) conv3_group<1, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
                         else if (KS == 2) conv3_group<2, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
-                        else conv3_group<4, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else if (KS == 4) conv3_group<4, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
+                        else conv3_group<8, 2>(al, a_hi, b_lo0, b_hi, bstep, dt, bo, id);
                     }
                     issued = true;
                     umma::commit(free_bar + sl);

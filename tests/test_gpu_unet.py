@@ -59,15 +59,16 @@ def test_conv3_matches_oracle(ub, cin, cout, relu, masked):
 @pytest.mark.parametrize("cin,cout,relu,masked,strided", [
     (16, 16, True, False, False), (32, 16, False, True, True), (16, 32, True, True, False),
     (32, 32, False, False, True), (32, 64, True, False, False), (64, 32, True, False, False),
-    (64, 64, True, True, True), (64, 128, False, True, True)])
+    (64, 64, True, True, True), (64, 128, False, True, True), (128, 64, True, False, True)])
 def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, masked, strided):
     """The TMA-staged convolution (input block per 8x16 output tile, taps read
     through shifted descriptors) on a grid with ragged x and y tiles: within the
     oracle bound, and the same bits as the row-gather kernel (same MMA order).
     strided: x is the second half of rows of 2 cin channels and out the first
     cout channels of rows of 2 cout (the concatenation buffers' layout).  64 ->
-    64 and 64 -> 128 run as two and four launches of 32 output channels (the
-    weights of all of them do not fit in shared memory beside the slice ring)."""
+    64 and 64 -> 128 run as two and four launches of 32 output channels, 128 ->
+    64 as four launches of 16 with a ring of two slices (the weights of all of
+    them do not fit in shared memory beside the slice ring)."""
     import torch
     r = _rng(7 * cin + cout)
     B, D, H, W = 2, 3, 21, 13
@@ -102,7 +103,7 @@ def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, mas
         assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 32), (16, 64), (64, 64)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 32), (16, 64), (64, 64), (128, 64)])
 def test_tma_conv3_accumulator_ring_on_a_large_volume(ub, cin, cout):
     """A 48x128x128 volume: 768 work items of 8 output depths, more than the
     resident CTAs, so CTAs take several items and the MMA groups that add one
