@@ -115,8 +115,8 @@ bd3mg_status bd3mg_unet_up(int B, int D, int H, int W, const void *x, int ldx, i
  * before launching work).  1 (the default): a convolution whose operands fit
  * (cout a multiple of 16 up to 128, cin of 16, 32, 64 or 128 channels, the 27
  * taps' weights of cout output channels, or of cout / parts <= 64 in 2, 4 or 8
- * launches, and a ring of four to six staged input slices, or of two where
- * four do not fit, within 224 KB of shared memory, x 16-byte aligned) runs
+ * launches, and a ring of four staged input slices, or of two where four do
+ * not fit, within 224 KB of shared memory, x 16-byte aligned) runs
  * the TMA-staged kernel, which
  * marches along z, copies each input slice of an 8 x 16 column once and adds
  * it to the three outputs it feeds with one group of MMAs; the others run the

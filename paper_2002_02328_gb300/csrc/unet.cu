@@ -123,7 +123,8 @@ int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K,
 // multiple of 16 up to 128, K of 16, 32, 64 or 128 channels, the 27 taps'
 // weights of N (or, in 2, 4 or 8 launches, N / parts <= 64) output channels
 // and a ring of four input slices (two where four do not fit with any split)
-// within kConv3SmemMax, rows 16-byte aligned.  Process-wide switch
+// within kConv3SmemMax, rows 16-byte aligned; the launch then takes the ring
+// size of two to six slices that gives the most resident CTAs.  Process-wide switch
 // (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
@@ -162,13 +163,12 @@ cudaError_t conv3_launch(cudaStream_t s, const CUtensorMap &map, int B, int D, i
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    // one wave of CTAs looping over the work items: the ring size (4 .. C3_RS
-    // slices, or 2 .. 3 where four do not fit) that gives the most CTAs per SM
-    // that shared memory and tensor memory (nacc accumulators of N columns)
-    // hold, the largest ring among those
+    // one wave of CTAs looping over the work items: the ring size (2 .. C3_RS
+    // slices) that gives the most CTAs per SM that shared memory and tensor
+    // memory (nacc accumulators of N columns) hold, the largest ring among those
     int per_sm = 0;
     a.rs = 0;
-    for (int rs = conv3_smem(K, N, 4) <= kConv3SmemMax ? 4 : 2; rs <= C3_RS; ++rs) {
+    for (int rs = 2; rs <= C3_RS; ++rs) {
         const size_t sm = conv3_smem(K, N, rs);
         if (sm > kConv3SmemMax) break;
         const int c = std::max(1, std::min({(int)(smem_sm / (sm + 1024)), 512 / conv3_cols(N), 8}));
