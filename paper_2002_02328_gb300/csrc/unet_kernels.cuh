@@ -286,7 +286,8 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 // after the last slice an output reads) hands an accumulator to the
 // epilogue, empty_bar[a] (one arrival per epilogue warp, after the zeroing)
 // back to the issuer; free_bar[s] (MMA commit after a slice's group) frees
-// ring slot s for the next copy.  Every wait is bounded; a wait that runs
+// ring slot s for the next copy, which may already be the first slices of the
+// CTA's next item.  Every wait is bounded; a wait that runs
 // out sets ST_MMA_TIMEOUT and a shared abort flag that every loop checks.
 // ---------------------------------------------------------------------------
 constexpr int C3_TX = 8, C3_TY = 16;                       // output tile (x, y)
@@ -455,20 +456,30 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
             const uint64_t b_desc0 = umma::desc(umma::smem_addr(Ws), 3u * (uint32_t)N * 16, 128);
             const uint32_t a_lo0 = (uint32_t)a_desc0, a_hi = (uint32_t)(a_desc0 >> 32);
             const uint32_t b_lo0 = (uint32_t)b_desc0, b_hi = (uint32_t)(b_desc0 >> 32), bstep = 6u * (uint32_t)N;
-            // gs: slices copied by this CTA (slice g in slot g % RS, its use g / RS of the
-            // slot); gw: slices whose copy has been waited for; q0: outputs of earlier items
-            int gs = 0, gw = 0, q0 = 0;
+            // Ring index g numbers the slices this CTA copies, its items' slices in
+            // order (slot g % RS, use g / RS of the slot).  gs: slices copied; gw:
+            // slices whose copy has been waited for; gb: ring index of the current
+            // item's first slice; q0: outputs of earlier items.  Once its own slices
+            // are copied, an item copies the next item's into slots already free.
+            int gs = 0, gw = 0, gb = 0, q0 = 0;
             bool ok = true, issued = false;
             for (int item = blockIdx.x; ok && item < a.nitems; item += gridDim.x) {
                 const Conv3Item wk(a, item);
                 const int lo = max(0, wk.z0 - 1), hi = min(a.D, wk.z1 + 1);   // input slices
-                const int gs0 = gs;
+                const int nsl = hi - lo;
+                const bool has_next = item + (int)gridDim.x < a.nitems;
+                const Conv3Item wn(a, has_next ? item + (int)gridDim.x : item);
+                const int lo_n = max(0, wn.z0 - 1), nsl_n = has_next ? min(a.D, wn.z1 + 1) - lo_n : 0;
+                const int gend = gb + nsl + nsl_n;
                 int alloc = wk.z0 - 1;            // outputs up to alloc hold an accumulator
                 auto load = [&]() {
-                    const int s = gs % RS, zi = lo + (gs - gs0);
+                    const int s = gs % RS;
+                    const bool own = gs < gb + nsl;
+                    const Conv3Item &w = own ? wk : wn;
+                    const int zi = own ? lo + (gs - gb) : lo_n + (gs - gb - nsl);
                     mbar_expect_tx(in_bar + s, (uint32_t)(KG * C3_SLICE));
                     for (int kg = 0; kg < KG; ++kg)
-                        tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, wk.x0 - 1, wk.y0 - 1, zi, wk.b,
+                        tma_load_5d(RING + s * slot_bytes + kg * C3_SPL, &map, kg * 8, w.x0 - 1, w.y0 - 1, zi, w.b,
                                     in_bar + s);
                     ++gs;
                 };
@@ -494,12 +505,12 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                         if (q >= NA && !mbar_wait(empty_bar + q % NA, (uint32_t)((q / NA - 1) & 1))) ok = false;
                     }
                     // slice zi copied and landed
-                    while (ok && gs - gs0 <= zi - lo) {
+                    while (ok && gs <= gb + (zi - lo)) {
                         const int f = slot_free(true);
                         if (f < 0) ok = false;
                         else load();
                     }
-                    const int li = gs0 + (zi - lo), sl = li % RS;
+                    const int li = gb + (zi - lo), sl = li % RS;
                     if (ok && !mbar_wait(in_bar + sl, (uint32_t)((li / RS) & 1))) ok = false;
                     if (!ok) break;
                     gw = li + 1;
@@ -527,10 +538,11 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
                     // outputs whose last input slice is zi: zi - 1, and zi itself at the volume's end
                     if (zi - 1 >= wk.z0) umma::commit(full_bar + (q0 + zi - 1 - wk.z0) % NA);
                     if (zi == a.D - 1 && zi >= wk.z0 && zi < wk.z1) umma::commit(full_bar + (q0 + zi - wk.z0) % NA);
-                    // further slices of the item into slots already free
-                    while (lo + (gs - gs0) < hi && slot_free(false) == 1) load();
+                    // further slices of this item, then of the next, into slots already free
+                    while (gs < gend && slot_free(false) == 1) load();
                 }
                 q0 += wk.z1 - wk.z0;
+                gb += nsl;
             }
             if (!ok) fail();
             // leave only after the copies in flight have landed and the MMAs have completed
