@@ -157,24 +157,38 @@ cudaError_t conv3_launch(cudaStream_t s, const CUtensorMap &map, int B, int D, i
     a.out = out; a.ldo = ldo; a.status = status;
     a.tiles_x = (W + C3_TX - 1) / C3_TX;
     a.tiles_y = (H + C3_TY - 1) / C3_TY;
-    a.nacc = conv3_nacc(N);
     int dev = 0, sms = 0, smem_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_conv3);
     if (e != cudaSuccess) return e;
-    // one wave of CTAs looping over the work items: the ring size (2 .. C3_RS
-    // slices) that gives the most CTAs per SM that shared memory and tensor
-    // memory (nacc accumulators of N columns) hold, the largest ring among those
+    // registers: allocated per warp in units of 256, five warps per CTA
+    const int warp_regs = (std::max(1, fa.numRegs) * 32 + 255) / 256 * 256;
+    const int reg_cap = std::max(1, 65536 / (warp_regs * (C3_THREADS / 32)));
+    // one wave of CTAs looping over the work items: the accumulator count (the
+    // default for N, else four) and ring size (2 .. C3_RS slices) that give the
+    // most CTAs per SM that shared memory, tensor memory (nacc accumulators of
+    // N columns) and registers hold; among those the default count, then the
+    // largest ring
     int per_sm = 0;
     a.rs = 0;
-    for (int rs = 2; rs <= C3_RS; ++rs) {
-        const size_t sm = conv3_smem(K, N, rs);
-        if (sm > kConv3SmemMax) break;
-        const int c = std::max(1, std::min({(int)(smem_sm / (sm + 1024)), 512 / conv3_cols(N), 8}));
-        if (c >= per_sm) {
-            per_sm = c;
-            a.rs = rs;
+    a.nacc = conv3_nacc(N);
+    const int nacc_opt[2] = {conv3_nacc(N), 4};
+    for (int oi = 0; oi < 2; ++oi) {
+        const int na = nacc_opt[oi];
+        if (oi == 1 && na == nacc_opt[0]) break;
+        for (int rs = 2; rs <= C3_RS; ++rs) {
+            const size_t sm = conv3_smem(K, N, rs);
+            if (sm > kConv3SmemMax) break;
+            const int c =
+                std::max(1, std::min({(int)(smem_sm / (sm + 1024)), 512 / conv3_cols(na, N), reg_cap, 8}));
+            if (c > per_sm || (c == per_sm && na == a.nacc && rs > a.rs)) {
+                per_sm = c;
+                a.rs = rs;
+                a.nacc = na;
+            }
         }
     }
     if (a.rs == 0) return cudaErrorInvalidValue;

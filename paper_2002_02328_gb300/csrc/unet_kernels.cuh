@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(GT, 1) k_gemm(GemmArgs a) {
 // per input slice instead of 27 per output).  Accumulator a of NACC (N
 // columns each) holds output number q of the CTA with q % NACC = a; where
 // the three outputs' blocks wrap around the end of the ring, the group is two
-// MMAs (N' = N and 2N).  Outputs outside the item or taps reading slices
+// MMAs (N' = N and 2N); the launch picks NACC (four, or eight for N = 16)
+// together with the ring size for the most resident CTAs.  Outputs outside the item or taps reading slices
 // outside the volume are left out.  Since one MMA adds to three outputs at
 // once, none of them starts from "overwrite": the epilogue zeroes an
 // accumulator (tcgen05.st) when it has read it, and all of them at the start.
@@ -319,11 +320,13 @@ struct Conv3Args {
     int *status;
 };
 
-// Accumulators of k_conv3 for N output channels: eight of 16 columns, else four.
+// Accumulators of k_conv3 for N output channels where TMEM does not limit the
+// resident CTAs: eight of 16 columns, else four (four or more: the issuer
+// holds three outputs' accumulators while the epilogue drains a fourth).
 __host__ __device__ constexpr int conv3_nacc(int N) { return N <= 16 ? 8 : 4; }
-// TMEM columns k_conv3 allocates (a power of two >= 32).
-__host__ __device__ constexpr int conv3_cols(int N) {
-    return conv3_nacc(N) * N <= 64 ? 64 : conv3_nacc(N) * N <= 128 ? 128 : conv3_nacc(N) * N <= 256 ? 256 : 512;
+// TMEM columns k_conv3 allocates for nacc accumulators (a power of two >= 32).
+__host__ __device__ constexpr int conv3_cols(int nacc, int N) {
+    return nacc * N <= 32 ? 32 : nacc * N <= 64 ? 64 : nacc * N <= 128 ? 128 : nacc * N <= 256 ? 256 : 512;
 }
 
 __host__ __device__ constexpr size_t conv3_smem(int K, int N, int rs) {
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__
     uint32_t *tslot = reinterpret_cast<uint32_t *>(last_bar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t ncols = (uint32_t)conv3_cols(N);
+    const uint32_t ncols = (uint32_t)conv3_cols(NA, N);
 
     if (tid == 0) {
         *abort_flag = 0;

@@ -103,7 +103,7 @@ def test_tma_conv3_matches_oracle_and_the_gather_kernel(ub, cin, cout, relu, mas
         assert np.all(err <= 2.0 ** -8 * np.abs(ref) + 1e-5 * np.abs(ref).max()), err.max()
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 32), (16, 64), (64, 64), (128, 64)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (32, 16), (32, 32), (16, 64), (64, 64), (128, 64)])
 def test_tma_conv3_accumulator_ring_on_a_large_volume(ub, cin, cout):
     """A 48x128x128 volume: 768 work items of 8 output depths, more than the
     resident CTAs, so CTAs take several items and the MMA groups that add one
