@@ -395,7 +395,7 @@ __device__ __forceinline__ void conv3_group(uint32_t a_lo, uint32_t a_hi, uint32
 }
 
 // map: 5-D over [B][D][H][W][ld] reading channels [0, K), box (8, 10, 18, 1, 1).
-__global__ void __launch_bounds__(C3_THREADS, 4) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
+__global__ void __launch_bounds__(C3_THREADS, 6) k_conv3(const __grid_constant__ CUtensorMap map, const Conv3Args a) {
     extern __shared__ __align__(1024) uint8_t sm[];
     const int K = a.K, N = a.N, KG = K / 8, KS = K / 16, NA = a.nacc;
     const uint32_t w_bytes = 27u * (uint32_t)K * (uint32_t)N * 2u, slot_bytes = (uint32_t)KG * C3_SPL;
