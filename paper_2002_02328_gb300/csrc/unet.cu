@@ -194,10 +194,23 @@ cudaError_t conv3_launch(cudaStream_t s, const CUtensorMap &map, int B, int D, i
     if (a.rs == 0) return cudaErrorInvalidValue;
     const size_t smem = conv3_smem(K, N, a.rs);
     const long long slots = (long long)per_sm * sms;
-    // z-chunks: about four items per resident CTA, at least 8 output depths each
+    // z-chunks: the chunk count whose rounds of items over the resident CTAs
+    // times the slices an item copies (its depths plus two) is least, at least 8
+    // output depths an item (fewer chunks on a tie)
     const long long cols = (long long)B * a.tiles_x * a.tiles_y;
-    const long long want = std::max<long long>(1, (4 * slots + cols - 1) / cols);
-    a.zc = std::max(std::min(8, D), (int)((D + want - 1) / want));
+    long long best = -1;
+    a.zc = D;
+    for (int nch = 1; nch <= D; ++nch) {
+        const int zc = (D + nch - 1) / nch;
+        if (zc < std::min(8, D)) break;
+        if ((D + zc - 1) / zc != nch) continue;          // the same chunks as a smaller count
+        const long long rounds = (cols * nch + slots - 1) / slots;
+        const long long cost = rounds * (zc + 2);
+        if (best < 0 || cost < best) {
+            best = cost;
+            a.zc = zc;
+        }
+    }
     a.nchunks = (D + a.zc - 1) / a.zc;
     const long long nitems = cols * a.nchunks;
     if (nitems > INT_MAX) return cudaErrorInvalidValue;
