@@ -114,7 +114,7 @@ bd3mg_status bd3mg_unet_up(int B, int D, int H, int W, const void *x, int ldx, i
 /* Process-wide choice of the 3x3x3 convolution kernel (not thread-safe; set it
  * before launching work).  1 (the default): a convolution whose operands fit
  * (cout a multiple of 16 up to 128, cin of 16, 32, 64 or 128 channels, the 27
- * taps' weights of cout output channels, or of cout / parts <= 64 in 2, 4 or 8
+ * taps' weights of cout output channels, or of cout / parts <= 64 in 2 or 4
  * launches, and a ring of four staged input slices, or of two where four do
  * not fit, within 224 KB of shared memory, x 16-byte aligned) runs
  * the TMA-staged kernel, which

@@ -121,19 +121,20 @@ int kc_of(int K, int T) { return K >= 64 ? 64 : K * std::max(1, std::min(64 / K,
 
 // The TMA-staged 3x3x3 convolution (k_conv3) where its operands fit: N a
 // multiple of 16 up to 128, K of 16, 32, 64 or 128 channels, the 27 taps'
-// weights of N (or, in 2, 4 or 8 launches, N / parts <= 64) output channels
+// weights of N (or, in 2 or 4 launches, N / parts <= 64) output channels
 // and a ring of four input slices (two where four do not fit with any split)
 // within kConv3SmemMax, rows 16-byte aligned; the launch then takes the ring
 // size of two to six slices that gives the most resident CTAs.  Process-wide switch
 // (bd3mg_unet_set_tma_conv).
 bool g_tma_conv = true;
 
-// Launches over the output channels: the fewest (1, 2, 4 or 8) whose share of
-// N (a multiple of 16, at most 64) has its weights fit beside a ring of four
-// slices, else beside a ring of two (0: none).
+// Launches over the output channels: the fewest (1, 2 or 4) whose share of N
+// (a multiple of 16, at most 64) has its weights fit beside a ring of four
+// slices, else beside a ring of two (0: none; 128 -> 128 would take eight
+// launches of 16 channels, measured slower than the row-gather kernel).
 int conv3_parts(int K, int N) {
     for (int rmin = 4; rmin >= 2; rmin -= 2)
-        for (int parts = 1; parts <= 8; parts *= 2)
+        for (int parts = 1; parts <= 4; parts *= 2)
             if (N % parts == 0 && (N / parts) % 16 == 0 && N / parts <= 64 &&
                 conv3_smem(K, N / parts, rmin) <= kConv3SmemMax)
                 return parts;
